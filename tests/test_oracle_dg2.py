@@ -1,0 +1,156 @@
+"""Pins of the oracle's DG2 step (Eq. 1-4, Sect. 2.1.1, 2.2.1, 2.3) against
+what the mathematics fixes: lake at rest over rough terrain (C-property, also
+with emerging islands and on static / adaptive grids), Ritter and Stoker
+dam-break closed forms, D4 symmetry and volume conservation of the circular
+dam break, the mass budget with inflow and rain, MWDG2 at epsilon = 0 against
+uniform DG2, and the friction ODE's closed-form decay."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2107_02750_gb300 import synth as S
+from util import oracle_sim, ritter_depth, stoker_depth
+
+G = 9.80665
+
+
+@pytest.mark.parametrize("islands", [False, True])
+def test_lake_at_rest_uniform(islands):
+    p = S.lake_at_rest(n=32, islands=islands)
+    s = oracle_sim(p)
+    _, _, _, c0 = s.leaves()
+    for _ in range(1000):
+        s.step()
+    _, _, _, c = s.leaves()
+    h = c[:, 0]
+    wet = h > 1e-3
+    assert np.abs(c[:, 3:]).max() <= 1e-12
+    assert np.abs(h[wet] - c0[wet, 0]).max() <= 1e-12
+    if islands:
+        assert (~wet).sum() > 0
+
+
+@pytest.mark.parametrize("mode", [S.STATIC, S.ADAPTIVE])
+def test_lake_at_rest_nonuniform(mode):
+    p = S.lake_at_rest(n=32, L=3, islands=True, mode=mode, eps=1e-2)
+    s = oracle_sim(p)
+    for _ in range(300):
+        s.step()
+    lev, _, _, c = s.leaves()
+    assert np.abs(c[:, 3:]).max() <= 1e-12
+    if mode == S.STATIC:
+        assert len(np.unique(lev)) > 1
+
+
+def _strip_profile(s, p):
+    h, _, _ = s.fields()
+    return h.mean(axis=0)
+
+
+@pytest.mark.parametrize("kind", ["ritter", "stoker"])
+def test_dam_break_closed_forms(kind):
+    hR = 0.0 if kind == "ritter" else 0.1
+    errs = []
+    for nx, dx in ((100, 1.0), (200, 0.5)):
+        p = S.dam_break_strip(nx=nx, ny=4, dx=dx, h_left=1.0, h_right=hR)
+        s = oracle_sim(p, dt_max=1.0)
+        T = 6.0
+        s.run_to(T)
+        x = (np.arange(nx) + 0.5) * dx
+        prof = _strip_profile(s, p)
+        if kind == "ritter":
+            exact = ritter_depth(x, T, 50.0, 1.0, G)
+        else:
+            exact = stoker_depth(x, T, 50.0, 1.0, hR, G)
+        errs.append(np.mean(np.abs(prof - exact)))
+        # y-invariance of the strip
+        h, _, _ = s.fields()
+        assert np.abs(h - h[0:1, :]).max() < 1e-12
+    assert errs[1] < errs[0]
+    assert errs[1] < (0.0045 if kind == "ritter" else 0.0035)
+    assert errs[1] < 0.75 * errs[0]
+
+
+def test_circular_dam_break_symmetry_and_volume():
+    p = S.dam_break_circular()
+    s = oracle_sim(p)
+    v0 = s.diag()["volume"]
+    s.run_to(5.0)
+    d = s.diag()
+    assert abs(d["volume"] - v0) <= 1e-12 * v0
+    assert d["n_clip"] == 0
+    h, _, _ = s.fields()
+    assert np.abs(h - h.T).max() <= 1e-12
+    assert np.abs(h - h[:, ::-1]).max() <= 1e-12
+    assert np.abs(h - h[::-1, :]).max() <= 1e-12
+    assert 60 <= s.steps <= 90
+
+
+def test_mass_budget_with_inflow_and_rain():
+    p = S.valley(n=64, L=6, mode=S.UNIFORM, dx=10.0, peak_Q=50.0, t_peak=60.0)
+    p.rain_rate, p.rain_t_end = 1e-4, 40.0
+    s = oracle_sim(p)
+    v0 = s.diag()["volume"]
+    s.run_to(120.0)
+    d = s.diag()
+    budget = v0 + d["v_in"] - d["v_out"] + d["v_rain"] + d["v_clip"]
+    assert abs(d["volume"] - budget) <= 1e-12 * max(1.0, d["volume"])
+    assert d["v_in"] > 0 and d["v_rain"] > 0
+
+
+def test_mwdg2_at_zero_epsilon_equals_uniform():
+    pu = S.dam_break_circular(n=64, radius=6.0, L=6, mode=S.UNIFORM)
+    pa = S.dam_break_circular(n=64, radius=6.0, L=6, mode=S.ADAPTIVE, eps=0.0)
+    su, sa = oracle_sim(pu), oracle_sim(pa)
+    for _ in range(20):
+        dtu = su.step()
+        dta = sa.step()
+        assert abs(dtu - dta) <= 1e-13 * dtu
+    lu, iu, ju, cu = su.leaves()
+    la, ia, ja, ca = sa.leaves()
+    np.testing.assert_array_equal(la, lu)
+    np.testing.assert_array_equal(ia, iu)
+    np.testing.assert_array_equal(ja, ju)
+    assert np.abs(ca - cu).max() <= 1e-12
+
+
+def test_friction_decay_matches_ode():
+    """Uniform state, open boundaries: only friction acts.  The exact solution
+    of dq/dt = -g n^2 q |q| / h^(7/3) at constant depth is
+    1/q = 1/q0 + g n^2 t / h^(7/3); the split linearised-implicit update
+    reproduces it exactly at any time step (1/q grows by dt g n^2 / h^(7/3)
+    per step), so it must match to round-off for two step sizes."""
+    n, h, q0, T = 0.05, 2.0, 1.5, 40.0
+    for dtm in (0.7, 0.1):
+        nv = 9
+        p = S.Problem("fr", 8, 8, 0, 10.0, np.zeros((nv, nv)), np.full((nv, nv), h),
+                      np.full((nv, nv), q0), np.zeros((nv, nv)), n_manning=n,
+                      bc=(S.OPEN,) * 4, dt_max=dtm)
+        s = oracle_sim(p)
+        s.run_to(T)
+        _, _, _, c = s.leaves()
+        q_exact = 1.0 / (1.0 / q0 + G * n * n * T / h ** (7.0 / 3.0))
+        assert abs(s.t - T) < 1e-12
+        assert np.abs(c[:, 0] - h).max() < 1e-12
+        assert np.abs(c[:, 3] - q_exact).max() < 1e-12
+        assert q_exact < 0.9 * q0
+
+
+def test_limiter_keeps_averages_within_initial_bounds():
+    """Wet-bed dam break with the minmod limiter: no new extrema of the cell
+    averages of h (and no clipping)."""
+    p = S.dam_break_strip(nx=120, ny=4, dx=0.5, h_left=2.0, h_right=0.5)
+    s = oracle_sim(p)
+    s.run_to(3.0)
+    _, _, _, c = s.leaves()
+    assert c[:, 0].max() <= 2.0 + 1e-12 and c[:, 0].min() >= 0.5 - 1e-12
+    assert s.diag()["n_clip"] == 0
+
+
+def test_metrics():
+    assert O.rmse([1, 2, 3], [1, 2, 3]) == 0.0
+    assert abs(O.rmse([0, 0], [3, 4]) - np.sqrt(12.5)) < 1e-15
+    h = np.array([[0, 1], [1, 1]], float)
+    r = np.array([[1, 1], [0, 1]], float)
+    H, F, C = O.extent_scores(h, r)
+    assert (H, F, C) == (2 / 3, 1 / 3, 2 / 4)
