@@ -1,0 +1,194 @@
+/*
+ * mwdg.h -- C ABI of the GB300 (sm_103a) DG2 / multiwavelet-MRA flood solver.
+ *
+ * Method: Sharifian & Kesserwani, "Benchmarking (multi)wavelet-based dynamic
+ * and static non-uniform grid solvers for flood inundation modelling",
+ * arXiv 2107.02750.  Every computation behind these calls runs in CUDA
+ * kernels of this library on one GPU; there is no CPU fallback.
+ *
+ * Conventions
+ *  - SI units.  Rasters are row-major with row j running south to north and
+ *    column i west to east.  A grid has nx = M 2^L by ny = N 2^L finest
+ *    cells of size dx (Sect. 2.2); vertex rasters are (ny+1) x (nx+1).
+ *  - Host pointers are owned by the caller and only read or written during
+ *    the call (the data are copied).  Functions with the _dev suffix take
+ *    device pointers that must stay valid until the work queued on
+ *    params.cuda_stream has finished; the caller keeps ownership.
+ *  - All device work is queued on params.cuda_stream (NULL: the legacy
+ *    default stream).  Functions that return host data synchronise it.
+ *  - Every function returns an mwdg_status; nothing throws or aborts across
+ *    the boundary.  After MWDG_ERR_CUDA or MWDG_ERR_NONFINITE the context is
+ *    in an error state: later calls on it return MWDG_ERR_STATE.
+ *    mwdg_last_error() describes the most recent failure.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef MWDG_H
+#define MWDG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MWDG_API __attribute__((visibility("default")))
+#else
+#define MWDG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mwdg_ctx mwdg_ctx;
+
+typedef enum {
+  MWDG_OK = 0,
+  MWDG_ERR_ARG = -1,       /* invalid argument or NULL pointer            */
+  MWDG_ERR_DIMS = -2,      /* sizes inconsistent with nx = M 2^L etc.     */
+  MWDG_ERR_CUDA = -3,      /* a CUDA call failed                          */
+  MWDG_ERR_NONFINITE = -4, /* non-finite input value or state             */
+  MWDG_ERR_TIMEOUT = -5,   /* a bounded device wait ran out               */
+  MWDG_ERR_STATE = -6,     /* call not valid in the current state         */
+  MWDG_ERR_CAPACITY = -7   /* caller buffer or fixed capacity too small   */
+} mwdg_status;
+
+/* grid modes: uniform DG2 on the finest grid; static non-uniform DG2 on the
+ * graded grid from one MRA of the topography (Sect. 2.2, 2.2.1); adaptive
+ * MWDG2 with the MRA of flow and topography at every step (Sect. 2.3) */
+enum { MWDG_UNIFORM = 0, MWDG_STATIC = 1, MWDG_ADAPTIVE = 2 };
+/* arithmetic: FP64 coefficients (depth form), or FP32 coefficients in
+ * free-surface form eta = h + z with FP64 time, volume sums and
+ * detail-threshold comparisons */
+enum { MWDG_F64 = 0, MWDG_F32 = 1 };
+enum { MWDG_WALL = 0, MWDG_OPEN = 1 };
+enum { MWDG_WEST = 0, MWDG_EAST = 1, MWDG_SOUTH = 2, MWDG_NORTH = 3 };
+#define MWDG_LMAX 15
+
+typedef struct {
+  int32_t M, N, L;     /* coarsest grid and maximum refinement level        */
+  int32_t mode;        /* MWDG_UNIFORM / MWDG_STATIC / MWDG_ADAPTIVE        */
+  int32_t precision;   /* MWDG_F64 / MWDG_F32                               */
+  int32_t limiter;     /* 0 off, 1 minmod slope limiter                     */
+  int32_t bc[4];       /* per edge (west, east, south, north): wall / open  */
+  double dx;           /* finest resolution R (m)                           */
+  double eps;          /* MRA threshold (Sect. 2.2; 1e-3 recommended)      */
+  double cfl;          /* Courant number (0.33 for DG2, Sect. 2.1.1)        */
+  double g;            /* gravity (m/s^2)                                   */
+  double h_dry;        /* dry-depth tolerance (m)                           */
+  double dt_max;       /* upper bound on the time step (s)                  */
+  void *cuda_stream;   /* cudaStream_t for all device work                  */
+} mwdg_params;
+
+/* Fills defaults: M=N=1, L=0, uniform, FP64, minmod, walls, dx=1, eps=1e-3,
+ * cfl=0.33, g=9.80665, h_dry=1e-3, dt_max=1, default stream. */
+MWDG_API mwdg_status mwdg_params_default(mwdg_params *p);
+
+/* Creates a context and allocates its device memory (dense per-level
+ * coefficient pyramids, about 4/3 of the finest grid per array).
+ * MWDG_ERR_DIMS if L > MWDG_LMAX, M or N < 1, or dx <= 0. */
+MWDG_API mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out);
+MWDG_API void mwdg_destroy(mwdg_ctx *ctx);
+
+/* Topography from a vertex raster z_vert[(ny+1)(nx+1)] (host): planar
+ * coefficients by Eq. 8 on the finest grid (the interface-centre values are
+ * means of the two vertices, so z is continuous at interface centres), the
+ * full static pyramid by Eq. 9 and each node's normalised topography detail
+ * max|d| / max(1, max|z0|) (Sect. 2.2).  MWDG_ERR_NONFINITE on NaN/Inf. */
+MWDG_API mwdg_status mwdg_load_dem(mwdg_ctx *ctx, const double *z_vert);
+
+/* Manning coefficient n_M (Eq. 1) per finest cell, n_cell[ny*nx] (host);
+ * coarser elements use the mean of their finest cells. */
+MWDG_API mwdg_status mwdg_load_roughness(mwdg_ctx *ctx, const double *n_cell);
+MWDG_API mwdg_status mwdg_set_roughness_scalar(mwdg_ctx *ctx, double n);
+
+/* Initial condition from vertex rasters (host, (ny+1)(nx+1) each) of depth
+ * h (or free surface eta = h + z when is_eta != 0) and discharges qx, qy,
+ * projected like the topography (Sect. 2.1.4).  With is_eta, elements whose
+ * average free surface is not above their average bed start dry.  Requires
+ * mwdg_load_dem first.  Uniform and adaptive runs start on the finest grid;
+ * a static run builds its graded grid here from the topography (as
+ * mwdg_mra_adapt does) and encodes the state onto it.  Resets time to 0. */
+MWDG_API mwdg_status mwdg_load_initial(mwdg_ctx *ctx, const double *h_vert, const double *qx_vert,
+                              const double *qy_vert, int32_t is_eta);
+
+/* Inflow hydrograph Q(t) (m^3/s, piecewise linear through nknots knots,
+ * held constant outside) entering through finest cells c0..c1 of an edge;
+ * each boundary face carries Q times its overlap with those cells divided
+ * by their total width, as a critical-depth ghost state.  Faces of that
+ * edge outside c0..c1 keep their bc.  nknots = 0 removes the inflow. */
+MWDG_API mwdg_status mwdg_set_inflow(mwdg_ctx *ctx, int32_t edge, int32_t c0, int32_t c1, const double *t,
+                            const double *Q, int32_t nknots);
+
+/* Uniform rain rate (m/s) added to the depth at the start of each step
+ * that begins before t_stop. */
+MWDG_API mwdg_status mwdg_set_rain(mwdg_ctx *ctx, double rate, double t_stop);
+
+/* Eq. 9 on the current flow state: scale coefficients of every refined node
+ * (local encoding of its active leaves) and, per node, the flow details'
+ * normalised maximum max_v max|d_v| / max(1, max|v0|) over h, qx, qy.
+ * Adaptive mode only (MWDG_ERR_STATE otherwise). */
+MWDG_API mwdg_status mwdg_mra_encode(mwdg_ctx *ctx);
+
+/* Threshold, regularise and decode (Sect. 2.2, 2.3) with threshold eps:
+ *  adaptive: after mwdg_mra_encode, a node is significant when its
+ *    topography or flow normalised detail is >= eps; significant nodes flag
+ *    their eight same-level neighbours; parents of flagged nodes are flagged;
+ *    new active leaves take encoded or prolonged coefficients (Eq. 10).
+ *  static: rebuilds the graded grid from the topography details alone
+ *    (closure and 2:1 grading) and re-encodes the loaded initial state;
+ *    valid only before the first step.
+ * *n_active (may be NULL) receives the number of active leaves.  Synchronises. */
+MWDG_API mwdg_status mwdg_mra_adapt(mwdg_ctx *ctx, double eps, int64_t *n_active);
+
+/* One time step (Sect. 2.1.1, Eq. 4): [adaptive: encode + adapt], CFL time
+ * step over the active leaves, rain, split implicit friction, RK2 stage 1 and
+ * stage 2.  dt_out (may be NULL; if given the call synchronises) receives
+ * the step's dt. */
+MWDG_API mwdg_status mwdg_dg2_step(mwdg_ctx *ctx, double *dt_out);
+
+/* nsteps steps queued without any host synchronisation. */
+MWDG_API mwdg_status mwdg_run_steps(mwdg_ctx *ctx, int64_t nsteps);
+
+/* Steps until the simulated time reaches t_end (the last step is shortened
+ * to land on it).  *steps_out (may be NULL) receives the number of steps. */
+MWDG_API mwdg_status mwdg_run_to_time(mwdg_ctx *ctx, double t_end, int64_t *steps_out);
+
+/* Finest-resolution fields h, u, v (host, ny*nx each; any may be NULL):
+ * each active leaf's plane evaluated at the centres of the finest cells it
+ * covers; velocities are q/h where h > h_dry, else 0. */
+MWDG_API mwdg_status mwdg_read_fields(mwdg_ctx *ctx, double *h, double *u, double *v);
+/* Same into device buffers (FP64, ny*nx each, any may be NULL). */
+MWDG_API mwdg_status mwdg_read_fields_dev(mwdg_ctx *ctx, double *h, double *u, double *v);
+
+/* Active leaves ordered by level, then row-major: level, i, j (any may be
+ * NULL) and their nine coefficients (h0 h1x h1y qx0 qx1x qx1y qy0 qy1x qy1y,
+ * depth form, may be NULL).  cap is the capacity of the buffers in leaves;
+ * *n receives the count (MWDG_ERR_CAPACITY, with *n set, if cap < count). */
+MWDG_API mwdg_status mwdg_read_active(mwdg_ctx *ctx, int32_t *level, int32_t *i, int32_t *j, double *coeffs,
+                             int64_t cap, int64_t *n);
+
+MWDG_API mwdg_status mwdg_get_time(mwdg_ctx *ctx, double *t, int64_t *steps);
+
+/* Volume sum over active leaves of h0 * area (FP64, fixed summation order)
+ * and the mass budget terms since mwdg_load_initial: boundary inflow and
+ * outflow volumes, rain volume, volume added by clipping negative depths and
+ * the number of clipped leaves.  Any pointer may be NULL.  Synchronises. */
+MWDG_API mwdg_status mwdg_get_volume(mwdg_ctx *ctx, double *V, double *V_in, double *V_out, double *V_rain,
+                            double *V_clip, int64_t *n_clip);
+
+/* Per-kernel timing with CUDA events on the context stream: enable != 0
+ * starts recording (and clears the totals).  mwdg_kernel_times fills up to
+ * cap entries of names (static strings), total milliseconds and launch
+ * counts, and returns the number of kernel classes in *n.  Synchronises. */
+MWDG_API mwdg_status mwdg_profile(mwdg_ctx *ctx, int32_t enable);
+MWDG_API mwdg_status mwdg_kernel_times(mwdg_ctx *ctx, const char **names, double *ms, int64_t *launches,
+                              int32_t cap, int32_t *n);
+
+/* Number of kernel launches this context has queued since creation. */
+MWDG_API mwdg_status mwdg_launch_count(mwdg_ctx *ctx, int64_t *n);
+
+MWDG_API const char *mwdg_last_error(const mwdg_ctx *ctx);
+MWDG_API const char *mwdg_status_string(mwdg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MWDG_H */

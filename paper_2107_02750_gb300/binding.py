@@ -1,0 +1,277 @@
+"""ctypes binding of libmwdg (include/mwdg.h).  Argument marshalling only:
+every step of the solver runs in the library's CUDA kernels.  The method
+names follow the C entry points (``mwdg_load_dem`` -> ``Solver.load_dem``)."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+UNIFORM, STATIC, ADAPTIVE = 0, 1, 2
+F64, F32 = 0, 1
+WALL, OPEN = 0, 1
+WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
+
+EXPORTS = (
+    "mwdg_params_default", "mwdg_create", "mwdg_destroy", "mwdg_load_dem", "mwdg_load_roughness",
+    "mwdg_set_roughness_scalar", "mwdg_load_initial", "mwdg_set_inflow", "mwdg_set_rain",
+    "mwdg_mra_encode", "mwdg_mra_adapt", "mwdg_dg2_step", "mwdg_run_steps", "mwdg_run_to_time",
+    "mwdg_read_fields", "mwdg_read_fields_dev", "mwdg_read_active", "mwdg_get_time",
+    "mwdg_get_volume", "mwdg_profile", "mwdg_kernel_times", "mwdg_launch_count",
+    "mwdg_last_error", "mwdg_status_string",
+)
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("M", C.c_int32), ("N", C.c_int32), ("L", C.c_int32), ("mode", C.c_int32),
+        ("precision", C.c_int32), ("limiter", C.c_int32), ("bc", C.c_int32 * 4),
+        ("dx", C.c_double), ("eps", C.c_double), ("cfl", C.c_double), ("g", C.c_double),
+        ("h_dry", C.c_double), ("dt_max", C.c_double), ("cuda_stream", C.c_void_p),
+    ]
+
+
+class MwdgError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where} failed with status {status}"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def lib(build: bool = True):
+    """Load libmwdg (compiling it in-tree first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.lib_path()
+    if not path.exists():
+        raise RuntimeError(f"libmwdg is not built ({path}); call __graft_entry__.build()")
+    L = C.CDLL(str(path))
+    vp, dp, ip, lp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    sig = {
+        "mwdg_params_default": [C.POINTER(Params)],
+        "mwdg_create": [C.POINTER(Params), C.POINTER(C.c_void_p)],
+        "mwdg_load_dem": [vp, dp],
+        "mwdg_load_roughness": [vp, dp],
+        "mwdg_set_roughness_scalar": [vp, C.c_double],
+        "mwdg_load_initial": [vp, dp, dp, dp, C.c_int32],
+        "mwdg_set_inflow": [vp, C.c_int32, C.c_int32, C.c_int32, dp, dp, C.c_int32],
+        "mwdg_set_rain": [vp, C.c_double, C.c_double],
+        "mwdg_mra_encode": [vp],
+        "mwdg_mra_adapt": [vp, C.c_double, lp],
+        "mwdg_dg2_step": [vp, dp],
+        "mwdg_run_steps": [vp, C.c_int64],
+        "mwdg_run_to_time": [vp, C.c_double, lp],
+        "mwdg_read_fields": [vp, dp, dp, dp],
+        "mwdg_read_fields_dev": [vp, vp, vp, vp],
+        "mwdg_read_active": [vp, ip, ip, ip, dp, C.c_int64, lp],
+        "mwdg_get_time": [vp, dp, lp],
+        "mwdg_get_volume": [vp, dp, dp, dp, dp, dp, lp],
+        "mwdg_profile": [vp, C.c_int32],
+        "mwdg_kernel_times": [vp, C.POINTER(C.c_char_p), dp, lp, C.c_int32, ip],
+        "mwdg_launch_count": [vp, lp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.mwdg_destroy.argtypes = [vp]
+    L.mwdg_destroy.restype = None
+    L.mwdg_last_error.argtypes = [vp]
+    L.mwdg_last_error.restype = C.c_char_p
+    L.mwdg_status_string.argtypes = [C.c_int]
+    L.mwdg_status_string.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Solver:
+    """One simulation context (mwdg_ctx) on the current CUDA device."""
+
+    def __init__(self, *, M, N, L, dx, mode=UNIFORM, precision=F64, eps=1e-3, cfl=0.33,
+                 g=9.80665, h_dry=1e-3, dt_max=1.0, limiter=1, bc=(WALL,) * 4, stream=None):
+        self._lib = lib()
+        p = Params()
+        self._lib.mwdg_params_default(C.byref(p))
+        p.M, p.N, p.L, p.mode, p.precision, p.limiter = M, N, L, mode, precision, limiter
+        for k in range(4):
+            p.bc[k] = bc[k]
+        p.dx, p.eps, p.cfl, p.g, p.h_dry, p.dt_max = dx, eps, cfl, g, h_dry, dt_max
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        p.cuda_stream = stream
+        self.p = p
+        self.nx, self.ny = M << L, N << L
+        h = C.c_void_p()
+        st = self._lib.mwdg_create(C.byref(p), C.byref(h))
+        if st != 0:
+            raise MwdgError(st, "mwdg_create", self._lib.mwdg_status_string(st).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mwdg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st, where):
+        if st != 0:
+            raise MwdgError(st, where, self._lib.mwdg_last_error(self._h).decode())
+
+    # --- inputs --------------------------------------------------------------
+    def load_dem(self, z_vert):
+        z = _f64(z_vert)
+        assert z.shape == (self.ny + 1, self.nx + 1)
+        self._ck(self._lib.mwdg_load_dem(self._h, _dp(z)), "mwdg_load_dem")
+
+    def load_roughness(self, n_cell):
+        a = _f64(np.broadcast_to(np.asarray(n_cell, np.float64), (self.ny, self.nx)))
+        self._ck(self._lib.mwdg_load_roughness(self._h, _dp(a)), "mwdg_load_roughness")
+
+    def set_roughness_scalar(self, n):
+        self._ck(self._lib.mwdg_set_roughness_scalar(self._h, float(n)), "mwdg_set_roughness_scalar")
+
+    def load_initial(self, h_vert, qx_vert=None, qy_vert=None, is_eta=False):
+        shape = (self.ny + 1, self.nx + 1)
+        h = _f64(h_vert)
+        qx = _f64(np.zeros(shape) if qx_vert is None else qx_vert)
+        qy = _f64(np.zeros(shape) if qy_vert is None else qy_vert)
+        self._ck(self._lib.mwdg_load_initial(self._h, _dp(h), _dp(qx), _dp(qy), int(is_eta)),
+                 "mwdg_load_initial")
+
+    def set_inflow(self, edge, c0, c1, t, Q):
+        t, Q = _f64(t), _f64(Q)
+        self._ck(self._lib.mwdg_set_inflow(self._h, edge, c0, c1, _dp(t), _dp(Q), len(t)),
+                 "mwdg_set_inflow")
+
+    def set_rain(self, rate, t_stop):
+        self._ck(self._lib.mwdg_set_rain(self._h, float(rate), float(t_stop)), "mwdg_set_rain")
+
+    # --- MRA and stepping ----------------------------------------------------
+    def mra_encode(self):
+        self._ck(self._lib.mwdg_mra_encode(self._h), "mwdg_mra_encode")
+
+    def mra_adapt(self, eps) -> int:
+        n = C.c_int64()
+        self._ck(self._lib.mwdg_mra_adapt(self._h, float(eps), C.byref(n)), "mwdg_mra_adapt")
+        return n.value
+
+    def dg2_step(self) -> float:
+        dt = C.c_double()
+        self._ck(self._lib.mwdg_dg2_step(self._h, C.byref(dt)), "mwdg_dg2_step")
+        return dt.value
+
+    def run_steps(self, n):
+        self._ck(self._lib.mwdg_run_steps(self._h, int(n)), "mwdg_run_steps")
+
+    def run_to_time(self, t_end) -> int:
+        n = C.c_int64()
+        self._ck(self._lib.mwdg_run_to_time(self._h, float(t_end), C.byref(n)), "mwdg_run_to_time")
+        return n.value
+
+    # --- outputs -------------------------------------------------------------
+    def read_fields(self):
+        h, u, v = (np.empty((self.ny, self.nx)) for _ in range(3))
+        self._ck(self._lib.mwdg_read_fields(self._h, _dp(h), _dp(u), _dp(v)), "mwdg_read_fields")
+        return h, u, v
+
+    def read_fields_dev(self, h=None, u=None, v=None):
+        """fill FP64 CUDA tensors of shape (ny, nx) (any may be None)"""
+        ptr = lambda x: None if x is None else C.c_void_p(x.data_ptr())
+        self._ck(self._lib.mwdg_read_fields_dev(self._h, ptr(h), ptr(u), ptr(v)), "mwdg_read_fields_dev")
+
+    def read_active(self):
+        n = C.c_int64()
+        self._ck(self._lib.mwdg_read_active(self._h, None, None, None, None, 0, C.byref(n)),
+                 "mwdg_read_active")
+        cnt = n.value
+        lev = np.empty(cnt, np.int32)
+        ii = np.empty(cnt, np.int32)
+        jj = np.empty(cnt, np.int32)
+        co = np.empty((cnt, 9))
+        self._ck(self._lib.mwdg_read_active(self._h, _ip(lev), _ip(ii), _ip(jj), _dp(co), cnt,
+                                            C.byref(n)), "mwdg_read_active")
+        return lev, ii, jj, co
+
+    def n_active(self) -> int:
+        n = C.c_int64()
+        self._ck(self._lib.mwdg_read_active(self._h, None, None, None, None, 0, C.byref(n)),
+                 "mwdg_read_active")
+        return n.value
+
+    def get_time(self):
+        t, s = C.c_double(), C.c_int64()
+        self._ck(self._lib.mwdg_get_time(self._h, C.byref(t), C.byref(s)), "mwdg_get_time")
+        return t.value, s.value
+
+    def get_volume(self) -> dict:
+        v = [C.c_double() for _ in range(5)]
+        n = C.c_int64()
+        self._ck(self._lib.mwdg_get_volume(self._h, *(C.byref(x) for x in v), C.byref(n)),
+                 "mwdg_get_volume")
+        return dict(volume=v[0].value, v_in=v[1].value, v_out=v[2].value, v_rain=v[3].value,
+                    v_clip=v[4].value, n_clip=n.value)
+
+    def profile(self, enable: bool):
+        self._ck(self._lib.mwdg_profile(self._h, int(enable)), "mwdg_profile")
+
+    def kernel_times(self) -> dict:
+        cap = 32
+        names = (C.c_char_p * cap)()
+        ms = np.zeros(cap)
+        cnt = np.zeros(cap, np.int64)
+        n = C.c_int32()
+        self._ck(self._lib.mwdg_kernel_times(self._h, names, _dp(ms),
+                                             cnt.ctypes.data_as(C.POINTER(C.c_int64)), cap,
+                                             C.byref(n)), "mwdg_kernel_times")
+        return {names[k].decode(): (float(ms[k]), int(cnt[k])) for k in range(n.value)}
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self._ck(self._lib.mwdg_launch_count(self._h, C.byref(n)), "mwdg_launch_count")
+        return n.value
+
+
+def solver_from_problem(p, precision=F64, stream=None, **over) -> Solver:
+    """A Solver loaded with a synthetic problem (paper_2107_02750_gb300.synth)."""
+    kw = dict(M=p.M, N=p.N, L=p.L, dx=p.dx, mode=p.mode, precision=precision, eps=p.eps,
+              limiter=p.limiter, bc=p.bc, dt_max=p.dt_max, stream=stream)
+    kw.update(over)
+    s = Solver(**kw)
+    s.load_dem(p.z_vert)
+    nm = np.asarray(p.n_manning)
+    if nm.ndim == 0:
+        s.set_roughness_scalar(float(nm))
+    else:
+        s.load_roughness(p.n_cell())
+    if len(p.inflow_t):
+        s.set_inflow(p.inflow_edge, p.inflow_c0, p.inflow_c1, p.inflow_t, p.inflow_Q)
+    if p.rain_rate > 0:
+        s.set_rain(p.rain_rate, p.rain_t_end)
+    s.load_initial(p.h_vert, p.qx_vert, p.qy_vert, p.is_eta)
+    return s

@@ -1,0 +1,202 @@
+// Device arithmetic of the DG2 shallow-water operator and the multiwavelet
+// filters (Sharifian & Kesserwani, arXiv 2107.02750, Sect. 2.1.1-2.3).
+//
+// Template parameters: T is the coefficient type (double or float); ETA
+// selects the storage form of the first variable: depth h (false) or free
+// surface eta = h + z (true, used by the FP32 path so that a flat surface is
+// stored exactly).  The FP64 build of this header is compiled without FMA
+// contraction so that every expression rounds as written.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mwdg {
+
+enum : uint8_t { K_BELOW = 0, K_LEAF = 1, K_SIG = 2 };
+
+template <typename T> __device__ __forceinline__ T s3v();
+template <> __device__ __forceinline__ double s3v<double>() { return 1.7320508075688772; }
+template <> __device__ __forceinline__ float s3v<float>() { return 1.7320508f; }
+
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return fmax(a, b); }
+template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return fmin(a, b); }
+template <typename T> __device__ __forceinline__ T tsqrt(T a) { return sqrt(a); }
+template <typename T> __device__ __forceinline__ T tcbrt(T a) { return cbrt(a); }
+template <typename T> __device__ __forceinline__ T tabs(T a) { return fabs(a); }
+
+// Limit of a plane (Eq. 2-3) at the interface centre of face f:
+// 0 east (+x), 1 west, 2 north (+y), 3 south.
+template <typename T>
+__device__ __forceinline__ T face_value(T c0, T c1x, T c1y, int f) {
+  const T s3 = s3v<T>();
+  switch (f) {
+    case 0: return c0 + s3 * c1x;
+    case 1: return c0 - s3 * c1x;
+    case 2: return c0 + s3 * c1y;
+    default: return c0 - s3 * c1y;
+  }
+}
+
+// One side of an interface after the wet/dry, well-balanced revision:
+// interface bed zf = max of the two sides' beds, revised depth
+// h* = max(0, eta - zf), velocities from the unrevised limit (zero when it is
+// not wetter than h_dry), and the bed the source term sees, min(zf, eta).
+template <typename T>
+struct Side {
+  T hs, u, v, zr;
+};
+
+// depth-form limit (h, qx, qy, z)
+template <typename T>
+__device__ __forceinline__ Side<T> revise_h(T h, T qx, T qy, T z, T zf, T hd) {
+  Side<T> s;
+  T eta = h + z;
+  s.hs = tmax(T(0), eta - zf);
+  if (h > hd) {
+    s.u = qx / h;
+    s.v = qy / h;
+  } else {
+    s.u = T(0);
+    s.v = T(0);
+  }
+  s.zr = tmin(zf, eta);
+  return s;
+}
+
+// free-surface-form limit (eta, qx, qy, z)
+template <typename T>
+__device__ __forceinline__ Side<T> revise_eta(T eta, T qx, T qy, T z, T zf, T hd) {
+  Side<T> s;
+  T h = eta - z;
+  s.hs = tmax(T(0), eta - zf);
+  if (h > hd) {
+    s.u = qx / h;
+    s.v = qy / h;
+  } else {
+    s.u = T(0);
+    s.v = T(0);
+  }
+  s.zr = tmin(zf, eta);
+  return s;
+}
+
+// HLL flux in the interface-normal frame (normal velocity un, tangential ut);
+// F = (mass, normal momentum, tangential momentum).  Wave speeds are the
+// two-rarefaction estimates with the dry-bed forms on a dry side.
+template <typename T>
+__device__ __forceinline__ void hll(T hL, T unL, T utL, T hR, T unR, T utR, T g, T hd, T F[3]) {
+  const bool dryL = !(hL > hd), dryR = !(hR > hd);
+  if (dryL && dryR) {
+    F[0] = F[1] = F[2] = T(0);
+    return;
+  }
+  const T cL = tsqrt(g * hL), cR = tsqrt(g * hR);
+  T sL, sR;
+  if (dryL) {
+    sL = unR - T(2) * cR;
+    sR = unR + cR;
+  } else if (dryR) {
+    sL = unL - cL;
+    sR = unL + T(2) * cL;
+  } else {
+    const T us = T(0.5) * (unL + unR) + cL - cR;
+    const T cs = T(0.5) * (cL + cR) + T(0.25) * (unL - unR);
+    sL = tmin(unL - cL, us - cs);
+    sR = tmax(unR + cR, us + cs);
+  }
+  const T qL = hL * unL, qR = hR * unR;
+  const T FL0 = qL, FL1 = qL * unL + T(0.5) * g * hL * hL, FL2 = qL * utL;
+  const T FR0 = qR, FR1 = qR * unR + T(0.5) * g * hR * hR, FR2 = qR * utR;
+  if (sL >= T(0)) {
+    F[0] = FL0; F[1] = FL1; F[2] = FL2;
+  } else if (sR <= T(0)) {
+    F[0] = FR0; F[1] = FR1; F[2] = FR2;
+  } else {
+    const T UL1 = qL, UL2 = hL * utL, UR1 = qR, UR2 = hR * utR;
+    const T den = sR - sL;
+    F[0] = (sR * FL0 - sL * FR0 + sL * sR * (hR - hL)) / den;
+    F[1] = (sR * FL1 - sL * FR1 + sL * sR * (UR1 - UL1)) / den;
+    F[2] = (sR * FL2 - sL * FR2 + sL * sR * (UR2 - UL2)) / den;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T minmod3(T a, T b, T c) {
+  if (a > T(0) && b > T(0) && c > T(0)) return tmin(a, tmin(b, c));
+  if (a < T(0) && b < T(0) && c < T(0)) return tmax(a, tmax(b, c));
+  return T(0);
+}
+
+// ---------------------------------------------------------------------------
+// Multiwavelet filters (Eq. 9-10) for one variable's three coefficients.
+// Children c = ix + 2 iy; sigma_x = +-1 is the sign of the child centre's x
+// offset.  Low pass: parent = 1/4 sum_c A_c child_c with
+//   A_c = [[1,0,0],[sqrt3/2 sx, 1/2, 0],[sqrt3/2 sy, 0, 1/2]].
+// High pass (orthonormal completion of the parent rows, Haar patterns H =
+// sign(y), V = sign(x), D = product on each child basis function):
+//   d_H = sum_c (sy/4 s0 - sqrt3/4 s1y, sy/2 s1x, sy/2 s1y)
+//   d_V = sum_c (sx/4 s0 - sqrt3/4 s1x, sx/2 s1x, sx/2 s1y)
+//   d_D = sum_c (sx sy/2 s0, sx sy/2 s1x, sx sy/2 s1y)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void encode3(const T (&ch)[4][3], T sp[3]) {
+  const T hs3 = T(0.5) * s3v<T>();
+  T a0 = ch[0][0];
+  a0 = a0 + ch[1][0];
+  a0 = a0 + ch[2][0];
+  a0 = a0 + ch[3][0];
+  T a1 = T(0), a2 = T(0);
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    const T sx = (c & 1) ? hs3 : -hs3, sy = (c & 2) ? hs3 : -hs3;
+    a1 = a1 + sx * ch[c][0];
+    a1 = a1 + T(0.5) * ch[c][1];
+    a2 = a2 + sy * ch[c][0];
+    a2 = a2 + T(0.5) * ch[c][2];
+  }
+  sp[0] = T(0.25) * a0;
+  sp[1] = T(0.25) * a1;
+  sp[2] = T(0.25) * a2;
+}
+
+// largest |detail| of one variable over the nine details
+template <typename T>
+__device__ __forceinline__ T detail_max3(const T (&ch)[4][3]) {
+  const T q3 = T(0.25) * s3v<T>();
+  T dH0 = 0, dH1 = 0, dH2 = 0, dV0 = 0, dV1 = 0, dV2 = 0, dD0 = 0, dD1 = 0, dD2 = 0;
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    const T sx = (c & 1) ? T(1) : T(-1), sy = (c & 2) ? T(1) : T(-1);
+    dH0 += T(0.25) * sy * ch[c][0] - q3 * ch[c][2];
+    dH1 += T(0.5) * sy * ch[c][1];
+    dH2 += T(0.5) * sy * ch[c][2];
+    dV0 += T(0.25) * sx * ch[c][0] - q3 * ch[c][1];
+    dV1 += T(0.5) * sx * ch[c][1];
+    dV2 += T(0.5) * sx * ch[c][2];
+    dD0 += T(0.5) * sx * sy * ch[c][0];
+    dD1 += T(0.5) * sx * sy * ch[c][1];
+    dD2 += T(0.5) * sx * sy * ch[c][2];
+  }
+  T m = tabs(dH0);
+  m = tmax(m, tabs(dH1));
+  m = tmax(m, tabs(dH2));
+  m = tmax(m, tabs(dV0));
+  m = tmax(m, tabs(dV1));
+  m = tmax(m, tabs(dV2));
+  m = tmax(m, tabs(dD0));
+  m = tmax(m, tabs(dD1));
+  m = tmax(m, tabs(dD2));
+  return m;
+}
+
+// prolongation of a plane to child c (Eq. 10 with zero details)
+template <typename T>
+__device__ __forceinline__ void prolong3(T s0, T s1x, T s1y, int c, T out[3]) {
+  const T hs3 = T(0.5) * s3v<T>();
+  const T ax = (c & 1) ? hs3 : -hs3, ay = (c & 2) ? hs3 : -hs3;
+  out[0] = (s0 + ax * s1x) + ay * s1y;
+  out[1] = T(0.5) * s1x;
+  out[2] = T(0.5) * s1y;
+}
+
+}  // namespace mwdg

@@ -1,0 +1,740 @@
+// C ABI of the GB300 DG2 / multiwavelet-MRA flood solver (include/mwdg.h):
+// context, device memory, host orchestration of the kernels in
+// mwdg_kernels.cuh.  Method: Sharifian & Kesserwani, arXiv 2107.02750.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "mwdg_internal.h"
+
+using namespace mwdg;
+
+namespace {
+
+constexpr int KNOT_CAP = 4096;
+
+const char *kclass_name(int c) {
+  static const char *names[KC_COUNT] = {"mra_encode", "mra_flags",  "mra_decode", "compact",
+                                        "dt_reduce",  "control",    "friction",   "limit",
+                                        "view_encode", "dg2_update_stage1", "dg2_update_stage2"};
+  return (c >= 0 && c < KC_COUNT) ? names[c] : "?";
+}
+
+}  // namespace
+
+struct mwdg_ctx {
+  mwdg_params p{};
+  cudaStream_t st = nullptr;
+  Geo g{};
+  Ptrs<double> pd{};
+  Ptrs<float> pf{};
+  std::vector<void *> allocs;
+  Ctl *ctl = nullptr;
+  double *d_vert = nullptr;
+  double *d_knot_t = nullptr, *d_knot_Q = nullptr;
+  double *d_fields = nullptr;    // 3 finest rasters for read-back
+  int32_t *d_active = nullptr;   // level, i, j for read-back
+  double *d_coef = nullptr;      // coefficients for read-back
+  int grid_leaves = 0;
+  bool dem = false, initial = false, stepped = false, failed = false, encoded = false;
+  int static_eta = 0;   // static run with a free-surface initial state
+  int64_t launches = 0;
+  std::string err;
+  // per-kernel timing
+  bool prof = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  double kms[KC_COUNT] = {};
+  int64_t kcount[KC_COUNT] = {};
+};
+
+namespace {
+
+mwdg_status fail(mwdg_ctx *c, mwdg_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = buf;
+    if (s == MWDG_ERR_CUDA || s == MWDG_ERR_NONFINITE) c->failed = true;
+  }
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(c, MWDG_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+#define CHECK_LAUNCH()                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                  \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(c, MWDG_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_),  \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+#define LIVE(c)                                                                           \
+  do {                                                                                    \
+    if (!(c)) return MWDG_ERR_ARG;                                                        \
+    if ((c)->failed) return MWDG_ERR_STATE;                                               \
+  } while (0)
+
+bool all_finite(const double *a, size_t n) {
+  for (size_t k = 0; k < n; k++)
+    if (!std::isfinite(a[k])) return false;
+  return true;
+}
+
+template <typename T>
+mwdg_status alloc(mwdg_ctx *c, T **p, size_t n) {
+  void *q = nullptr;
+  CK(cudaMalloc(&q, n * sizeof(T)));
+  c->allocs.push_back(q);
+  *p = (T *)q;
+  return MWDG_OK;
+}
+
+void mark_cb(void *arg, int cls) {
+  mwdg_ctx *c = (mwdg_ctx *)arg;
+  if (!c->prof) return;
+  cudaEvent_t ev;
+  if (!c->pool.empty()) {
+    ev = c->pool.back();
+    c->pool.pop_back();
+  } else if (cudaEventCreate(&ev) != cudaSuccess) {
+    return;
+  }
+  cudaEventRecord(ev, c->st);
+  c->marks.emplace_back(cls, ev);
+}
+
+// attribute the time between consecutive marks to the earlier mark's class
+mwdg_status flush_marks(mwdg_ctx *c) {
+  if (c->marks.empty()) return MWDG_OK;
+  CK(cudaStreamSynchronize(c->st));
+  for (size_t q = 0; q + 1 < c->marks.size(); q++) {
+    int cls = c->marks[q].first;
+    if (cls < 0) continue;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->marks[q].second, c->marks[q + 1].second));
+    c->kms[cls] += ms;
+    c->kcount[cls] += 1;
+  }
+  for (size_t q = 0; q + 1 < c->marks.size(); q++) c->pool.push_back(c->marks[q].second);
+  auto last = c->marks.back();
+  c->marks.clear();
+  c->marks.push_back(last);
+  return MWDG_OK;
+}
+
+template <typename T> Ptrs<T> &ptrs(mwdg_ctx *c);
+template <> Ptrs<double> &ptrs<double>(mwdg_ctx *c) { return c->pd; }
+template <> Ptrs<float> &ptrs<float>(mwdg_ctx *c) { return c->pf; }
+
+template <typename T>
+mwdg_status allocate_state(mwdg_ctx *c) {
+  Ptrs<T> &p = ptrs<T>(c);
+  const size_t P = (size_t)c->g.P;
+  mwdg_status s;
+  if ((s = alloc(c, &p.U, 9 * P)) || (s = alloc(c, &p.Ui, 9 * P)) || (s = alloc(c, &p.Wn, 9 * P)) ||
+      (s = alloc(c, &p.Wi, 9 * P)) || (s = alloc(c, &p.F, 9 * P)) || (s = alloc(c, &p.Z, 3 * P)) ||
+      (s = alloc(c, &p.Ze, 3 * P)) || (s = alloc(c, &p.NM, P)) || (s = alloc(c, &p.DZ, P)) ||
+      (s = alloc(c, &p.kind, P)) || (s = alloc(c, &p.kind_old, P)) || (s = alloc(c, &p.flag, P)) ||
+      (s = alloc(c, &p.flag2, P)) || (s = alloc(c, &p.leaves, P)) || (s = alloc(c, &p.nleaf, 1)))
+    return s;
+  const size_t nb = (P + 2048 - 1) / 2048 + 1;
+  if ((s = alloc(c, &p.blk, nb)) || (s = alloc(c, &p.part, (size_t)c->grid_leaves))) return s;
+  CK(cudaMemsetAsync(p.U, 0, 9 * P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.Ui, 0, 9 * P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.Wn, 0, 9 * P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.Wi, 0, 9 * P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.F, 0, 9 * P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.Z, 0, 3 * P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.Ze, 0, 3 * P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.NM, 0, P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.DZ, 0, P * sizeof(double), c->st));
+  CK(cudaMemsetAsync(p.flag, 0, P, c->st));
+  CK(cudaMemsetAsync(p.flag2, 0, P, c->st));
+  p.ctl = c->ctl;
+  p.knot_t = c->d_knot_t;
+  p.knot_Q = c->d_knot_Q;
+  return MWDG_OK;
+}
+
+// run a launcher on the context's precision
+template <typename F>
+int dispatch(mwdg_ctx *c, F &&f) {
+  if (c->g.prec == MWDG_F64) return f(c->pd, (double *)nullptr);
+  return f(c->pf, (float *)nullptr);
+}
+
+Ctl fresh_ctl() {
+  Ctl h{};
+  h.t = 0.0;
+  h.dt = 0.0;
+  h.t_end = 1e300;
+  h.dtmin = 0x7ff0000000000000ULL;
+  return h;
+}
+
+mwdg_status read_ctl(mwdg_ctx *c, Ctl *h) {
+  CK(cudaMemcpyAsync(h, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (h->nonfinite) return fail(c, MWDG_ERR_NONFINITE, "non-finite value in the solution");
+  return MWDG_OK;
+}
+
+// queue the regridding of a static run from the topography details: flags,
+// closure, 2:1 grading to a fixed point, kinds, encode of the finest state
+mwdg_status build_static_grid(mwdg_ctx *c, int is_eta_encoded) {
+  const Geo &g = c->g;
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::static_flags(g, p, c->st) + Launch<T>::closure(g, p.flag, c->st);
+  });
+  for (int it = 0; it < 4 * (g.L + 2); it++) {
+    int zero = 0, changed = 0;
+    CK(cudaMemcpyAsync(&c->ctl->changed, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    c->launches += dispatch(c, [&](auto &p, auto *) {
+      using T = std::remove_pointer_t<decltype(p.U)>;
+      return Launch<T>::grading_sweep(g, p, c->st);
+    });
+    CHECK_LAUNCH();
+    CK(cudaMemcpyAsync(&changed, &c->ctl->changed, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (!changed) break;
+  }
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    int n = Launch<T>::kinds(g, p, p.flag, 0, c->st) + Launch<T>::encode_dense_U(g, p, c->st);
+    if (is_eta_encoded) n += Launch<T>::eta_rule_leaves(g, p, c->st);
+    return n + Launch<T>::compact(g, p, c->st);
+  });
+  CHECK_LAUNCH();
+  return MWDG_OK;
+}
+
+mwdg_status queue_step(mwdg_ctx *c) {
+  const Geo &g = c->g;
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    int n = 0;
+    if (g.mode == MWDG_ADAPTIVE) n += Launch<T>::adapt(g, p, 0, 0, c->st, mark_cb, c);
+    n += Launch<T>::step(g, p, c->grid_leaves, c->st, mark_cb, c);
+    return n;
+  });
+  CHECK_LAUNCH();
+  c->stepped = true;
+  c->encoded = false;
+  return MWDG_OK;
+}
+
+template <typename T>
+__global__ void k_fill_nm(T *nm, long long off, long long n, const double *src, double val) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  nm[off + k] = (T)(src ? src[k] : val);
+}
+
+__global__ void k_set_tend(Ctl *c, double t_end) { c->t_end = t_end; }
+
+}  // namespace
+
+extern "C" {
+
+const char *mwdg_status_string(mwdg_status s) {
+  switch (s) {
+    case MWDG_OK: return "ok";
+    case MWDG_ERR_ARG: return "invalid argument";
+    case MWDG_ERR_DIMS: return "invalid dimensions";
+    case MWDG_ERR_CUDA: return "CUDA error";
+    case MWDG_ERR_NONFINITE: return "non-finite value";
+    case MWDG_ERR_TIMEOUT: return "device wait timed out";
+    case MWDG_ERR_STATE: return "invalid state";
+    case MWDG_ERR_CAPACITY: return "capacity exceeded";
+  }
+  return "unknown status";
+}
+
+mwdg_status mwdg_params_default(mwdg_params *p) {
+  if (!p) return MWDG_ERR_ARG;
+  memset(p, 0, sizeof *p);
+  p->M = p->N = 1;
+  p->L = 0;
+  p->mode = MWDG_UNIFORM;
+  p->precision = MWDG_F64;
+  p->limiter = 1;
+  for (int e = 0; e < 4; e++) p->bc[e] = MWDG_WALL;
+  p->dx = 1.0;
+  p->eps = 1e-3;
+  p->cfl = 0.33;
+  p->g = 9.80665;
+  p->h_dry = 1e-3;
+  p->dt_max = 1.0;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
+  if (!p || !out) return MWDG_ERR_ARG;
+  *out = nullptr;
+  if (p->L < 0 || p->L > MWDG_LMAX || p->M < 1 || p->N < 1 || !(p->dx > 0.0)) return MWDG_ERR_DIMS;
+  if ((int64_t)p->M << p->L > (1 << 20) || (int64_t)p->N << p->L > (1 << 20)) return MWDG_ERR_DIMS;
+  if (p->mode < MWDG_UNIFORM || p->mode > MWDG_ADAPTIVE || p->precision < MWDG_F64 ||
+      p->precision > MWDG_F32 || !(p->cfl > 0.0) || !(p->g > 0.0) || !(p->h_dry >= 0.0) ||
+      !(p->dt_max > 0.0) || !std::isfinite(p->eps) || p->eps < 0.0)
+    return MWDG_ERR_ARG;
+  mwdg_ctx *c = new mwdg_ctx();
+  c->p = *p;
+  c->st = (cudaStream_t)p->cuda_stream;
+  Geo &g = c->g;
+  g.mode = p->mode;
+  g.prec = p->precision;
+  g.limiter = p->limiter;
+  if (p->mode == MWDG_UNIFORM) {  // a uniform grid is the single level of an L = 0 hierarchy
+    g.L = 0;
+    g.M = p->M << p->L;
+    g.N = p->N << p->L;
+  } else {
+    g.L = p->L;
+    g.M = p->M;
+    g.N = p->N;
+  }
+  g.off[0] = 0;
+  for (int l = 0; l <= g.L; l++) {
+    g.nxl[l] = g.M << l;
+    g.nyl[l] = g.N << l;
+    g.dxl[l] = p->dx * (double)(1LL << (g.L - l));
+    g.off[l + 1] = g.off[l] + (long long)g.nxl[l] * g.nyl[l];
+  }
+  g.P = g.off[g.L + 1];
+  g.g = p->g;
+  g.hd = p->h_dry;
+  g.cfl = p->cfl;
+  g.dt_max = p->dt_max;
+  g.eps = p->eps;
+  g.area = (double)g.nxl[g.L] * g.dxl[g.L] * (double)g.nyl[g.L] * g.dxl[g.L];
+  for (int e = 0; e < 4; e++) g.bc[e] = p->bc[e];
+  g.inflow_edge = -1;
+  g.inflow_c0 = 0;
+  g.inflow_c1 = -1;
+  g.nknots = 0;
+  g.rain_rate = 0.0;
+  g.rain_t_end = 0.0;
+  c->grid_leaves = (int)std::min<long long>((g.P + 255) / 256, 152 * 8);
+  mwdg_status s;
+  if ((s = alloc(c, &c->ctl, 1)) || (s = alloc(c, &c->d_knot_t, KNOT_CAP)) ||
+      (s = alloc(c, &c->d_knot_Q, KNOT_CAP)) ||
+      (s = alloc(c, &c->d_vert, (size_t)(g.nxl[g.L] + 1) * (g.nyl[g.L] + 1)))) {
+    mwdg_destroy(c);
+    return s;
+  }
+  s = (g.prec == MWDG_F64) ? allocate_state<double>(c) : allocate_state<float>(c);
+  if (s) {
+    mwdg_destroy(c);
+    return s;
+  }
+  Ctl h = fresh_ctl();
+  if (cudaMemcpyAsync(c->ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->st) != cudaSuccess) {
+    mwdg_destroy(c);
+    return MWDG_ERR_CUDA;
+  }
+  c->launches += dispatch(c, [&](auto &pp, auto *) {
+    using T = std::remove_pointer_t<decltype(pp.U)>;
+    int n = (g.L == 0) ? Launch<T>::kinds(g, pp, pp.flag, 0, c->st) : Launch<T>::all_finest(g, pp, c->st);
+    return n + Launch<T>::compact(g, pp, c->st);
+  });
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->st) != cudaSuccess) {
+    mwdg_destroy(c);
+    return MWDG_ERR_CUDA;
+  }
+  *out = c;
+  return MWDG_OK;
+}
+
+void mwdg_destroy(mwdg_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  for (void *q : c->allocs) cudaFree(q);
+  for (auto &m : c->marks) cudaEventDestroy(m.second);
+  for (auto ev : c->pool) cudaEventDestroy(ev);
+  delete c;
+}
+
+mwdg_status mwdg_load_dem(mwdg_ctx *c, const double *z_vert) {
+  LIVE(c);
+  if (!z_vert) return fail(c, MWDG_ERR_ARG, "z_vert is NULL");
+  const Geo &g = c->g;
+  const size_t nv = (size_t)(g.nxl[g.L] + 1) * (g.nyl[g.L] + 1);
+  if (!all_finite(z_vert, nv)) return fail(c, MWDG_ERR_NONFINITE, "non-finite DEM value");
+  CK(cudaMemcpyAsync(c->d_vert, z_vert, nv * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  unsigned long long zero = 0;
+  CK(cudaMemcpyAsync(&c->ctl->vmax[0], &zero, sizeof zero, cudaMemcpyHostToDevice, c->st));
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    const long long P = g.P, o = g.off[g.L];
+    return Launch<T>::project(g, p, c->d_vert, p.Z + o, p.Z + P + o, p.Z + 2 * P + o, c->st) +
+           Launch<T>::load_dem_pyramid(g, p, c->st);
+  });
+  CHECK_LAUNCH();
+  CK(cudaMemcpyAsync(&c->ctl->vmax[0], &zero, sizeof zero, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->dem = true;
+  c->initial = false;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_load_roughness(mwdg_ctx *c, const double *n_cell) {
+  LIVE(c);
+  if (!n_cell) return fail(c, MWDG_ERR_ARG, "n_cell is NULL");
+  const Geo &g = c->g;
+  const size_t n = (size_t)g.nxl[g.L] * g.nyl[g.L];
+  if (!all_finite(n_cell, n)) return fail(c, MWDG_ERR_NONFINITE, "non-finite roughness");
+  CK(cudaMemcpyAsync(c->d_vert, n_cell, n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    k_fill_nm<T><<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(p.NM, g.off[g.L], (long long)n, c->d_vert, 0.0);
+    return 1 + Launch<T>::roughness_pyramid(g, p, c->st);
+  });
+  CHECK_LAUNCH();
+  CK(cudaStreamSynchronize(c->st));
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_set_roughness_scalar(mwdg_ctx *c, double nval) {
+  LIVE(c);
+  if (!std::isfinite(nval) || nval < 0.0) return fail(c, MWDG_ERR_ARG, "invalid roughness");
+  const Geo &g = c->g;
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    k_fill_nm<T><<<(unsigned)((g.P + 255) / 256), 256, 0, c->st>>>(p.NM, 0, g.P, nullptr, nval);
+    return 1;
+  });
+  CHECK_LAUNCH();
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_load_initial(mwdg_ctx *c, const double *h_vert, const double *qx_vert,
+                              const double *qy_vert, int32_t is_eta) {
+  LIVE(c);
+  if (!h_vert || !qx_vert || !qy_vert) return fail(c, MWDG_ERR_ARG, "NULL initial raster");
+  if (!c->dem) return fail(c, MWDG_ERR_STATE, "mwdg_load_dem must come first");
+  const Geo &g = c->g;
+  const size_t nv = (size_t)(g.nxl[g.L] + 1) * (g.nyl[g.L] + 1);
+  const double *src[3] = {h_vert, qx_vert, qy_vert};
+  for (int v = 0; v < 3; v++)
+    if (!all_finite(src[v], nv)) return fail(c, MWDG_ERR_NONFINITE, "non-finite initial value");
+  for (int v = 0; v < 3; v++) {
+    CK(cudaMemcpyAsync(c->d_vert, src[v], nv * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    c->launches += dispatch(c, [&](auto &p, auto *) {
+      using T = std::remove_pointer_t<decltype(p.U)>;
+      const long long P = g.P, o = g.off[g.L];
+      T *b = p.U + 3 * v * P;
+      int n = Launch<T>::project(g, p, c->d_vert, b + o, b + P + o, b + 2 * P + o, c->st);
+      if (v == 0 && is_eta && g.mode == MWDG_STATIC) {
+        // keep the projected free surface for the per-leaf wet/dry split
+        for (int m = 0; m < 3; m++)
+          cudaMemcpyAsync(p.Wn + m * P + o, b + m * P + o, (size_t)(P - o) * sizeof(T),
+                          cudaMemcpyDeviceToDevice, c->st);
+      }
+      return n;
+    });
+    CHECK_LAUNCH();
+  }
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::initial_finest(g, p, is_eta ? 1 : 0, c->st);
+  });
+  CHECK_LAUNCH();
+  mwdg_status s = MWDG_OK;
+  if (g.mode == MWDG_STATIC) {
+    c->static_eta = (is_eta && g.L > 0) ? 1 : 0;
+    s = build_static_grid(c, c->static_eta);
+  } else {
+    c->launches += dispatch(c, [&](auto &p, auto *) {
+      using T = std::remove_pointer_t<decltype(p.U)>;
+      int n = (g.L == 0) ? Launch<T>::kinds(g, p, p.flag, 0, c->st) : Launch<T>::all_finest(g, p, c->st);
+      return n + Launch<T>::compact(g, p, c->st);
+    });
+    CHECK_LAUNCH();
+  }
+  if (s) return s;
+  Ctl h = fresh_ctl();
+  CK(cudaMemcpyAsync(c->ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->initial = true;
+  c->stepped = false;
+  c->encoded = false;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_set_inflow(mwdg_ctx *c, int32_t edge, int32_t c0, int32_t c1, const double *t,
+                            const double *Q, int32_t nknots) {
+  LIVE(c);
+  Geo &g = c->g;
+  if (nknots == 0) {
+    g.inflow_edge = -1;
+    g.nknots = 0;
+    return MWDG_OK;
+  }
+  if (edge < 0 || edge > 3 || nknots < 1 || nknots > KNOT_CAP || !t || !Q)
+    return fail(c, MWDG_ERR_ARG, "invalid inflow arguments");
+  const int len = (edge < 2) ? g.nyl[g.L] : g.nxl[g.L];
+  if (c0 < 0 || c1 < c0 || c1 >= len) return fail(c, MWDG_ERR_DIMS, "inflow cells outside the edge");
+  if (!all_finite(t, nknots) || !all_finite(Q, nknots)) return fail(c, MWDG_ERR_NONFINITE, "non-finite hydrograph");
+  for (int k = 1; k < nknots; k++)
+    if (!(t[k] > t[k - 1])) return fail(c, MWDG_ERR_ARG, "hydrograph times must increase");
+  CK(cudaMemcpyAsync(c->d_knot_t, t, nknots * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->d_knot_Q, Q, nknots * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  g.inflow_edge = edge;
+  g.inflow_c0 = c0;
+  g.inflow_c1 = c1;
+  g.nknots = nknots;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_set_rain(mwdg_ctx *c, double rate, double t_stop) {
+  LIVE(c);
+  if (!std::isfinite(rate) || rate < 0.0 || std::isnan(t_stop)) return fail(c, MWDG_ERR_ARG, "invalid rain");
+  c->g.rain_rate = rate;
+  c->g.rain_t_end = t_stop;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_mra_encode(mwdg_ctx *c) {
+  LIVE(c);
+  if (c->g.mode != MWDG_ADAPTIVE) return fail(c, MWDG_ERR_STATE, "encode needs adaptive mode");
+  if (!c->initial) return fail(c, MWDG_ERR_STATE, "no initial state");
+  const Geo &g = c->g;
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::adapt(g, p, 1, 0, c->st, mark_cb, c);
+  });
+  CHECK_LAUNCH();
+  c->encoded = true;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_mra_adapt(mwdg_ctx *c, double eps, int64_t *n_active) {
+  LIVE(c);
+  if (!std::isfinite(eps) || eps < 0.0) return fail(c, MWDG_ERR_ARG, "invalid epsilon");
+  if (!c->initial) return fail(c, MWDG_ERR_STATE, "no initial state");
+  Geo &g = c->g;
+  if (g.mode == MWDG_UNIFORM) return fail(c, MWDG_ERR_STATE, "uniform grids do not adapt");
+  g.eps = eps;
+  if (g.mode == MWDG_STATIC) {
+    if (c->stepped) return fail(c, MWDG_ERR_STATE, "a static grid is fixed once stepping started");
+    mwdg_status s = build_static_grid(c, c->static_eta);
+    if (s) return s;
+  } else {
+    // full encode with this epsilon, then threshold, regularise, decode
+    c->launches += dispatch(c, [&](auto &p, auto *) {
+      using T = std::remove_pointer_t<decltype(p.U)>;
+      return Launch<T>::adapt(g, p, 0, 0, c->st, mark_cb, c);
+    });
+    CHECK_LAUNCH();
+    c->encoded = false;
+  }
+  if (n_active) {
+    int n = 0;
+    CK(cudaMemcpyAsync(&n, (g.prec == MWDG_F64) ? c->pd.nleaf : c->pf.nleaf, sizeof(int),
+                       cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    *n_active = n;
+  }
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_dg2_step(mwdg_ctx *c, double *dt_out) {
+  LIVE(c);
+  if (!c->initial) return fail(c, MWDG_ERR_STATE, "no initial state");
+  mwdg_status s = queue_step(c);
+  if (s) return s;
+  if (dt_out) {
+    Ctl h;
+    if ((s = read_ctl(c, &h))) return s;
+    *dt_out = h.dt;
+  }
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_run_steps(mwdg_ctx *c, int64_t nsteps) {
+  LIVE(c);
+  if (!c->initial) return fail(c, MWDG_ERR_STATE, "no initial state");
+  if (nsteps < 0) return fail(c, MWDG_ERR_ARG, "negative step count");
+  for (int64_t k = 0; k < nsteps; k++) {
+    mwdg_status s = queue_step(c);
+    if (s) return s;
+  }
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_run_to_time(mwdg_ctx *c, double t_end, int64_t *steps_out) {
+  LIVE(c);
+  if (!c->initial) return fail(c, MWDG_ERR_STATE, "no initial state");
+  if (std::isnan(t_end)) return fail(c, MWDG_ERR_ARG, "t_end is NaN");
+  Ctl h;
+  mwdg_status s;
+  if ((s = read_ctl(c, &h))) return s;
+  const long long start = h.steps;
+  k_set_tend<<<1, 1, 0, c->st>>>(c->ctl, t_end);
+  c->launches++;
+  int batch = 8;
+  while (h.t < t_end) {
+    const long long before = h.steps;
+    for (int k = 0; k < batch; k++)
+      if ((s = queue_step(c))) return s;
+    if ((s = read_ctl(c, &h))) return s;
+    if (h.steps == before) break;  // dt reached zero
+    batch = std::min(batch * 2, 256);
+  }
+  k_set_tend<<<1, 1, 0, c->st>>>(c->ctl, 1e300);
+  c->launches++;
+  CHECK_LAUNCH();
+  if (steps_out) *steps_out = h.steps - start;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_read_fields_dev(mwdg_ctx *c, double *h, double *u, double *v) {
+  LIVE(c);
+  const Geo &g = c->g;
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::fields(g, p, h, u, v, c->st);
+  });
+  CHECK_LAUNCH();
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_read_fields(mwdg_ctx *c, double *h, double *u, double *v) {
+  LIVE(c);
+  const Geo &g = c->g;
+  const size_t n = (size_t)g.nxl[g.L] * g.nyl[g.L];
+  if (!c->d_fields) {
+    mwdg_status s = alloc(c, &c->d_fields, 3 * n);
+    if (s) return s;
+  }
+  mwdg_status s = mwdg_read_fields_dev(c, c->d_fields, c->d_fields + n, c->d_fields + 2 * n);
+  if (s) return s;
+  double *dst[3] = {h, u, v};
+  for (int q = 0; q < 3; q++)
+    if (dst[q]) CK(cudaMemcpyAsync(dst[q], c->d_fields + q * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_read_active(mwdg_ctx *c, int32_t *level, int32_t *i, int32_t *j, double *coeffs,
+                             int64_t cap, int64_t *n) {
+  LIVE(c);
+  if (!n) return fail(c, MWDG_ERR_ARG, "n is NULL");
+  const Geo &g = c->g;
+  int cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, (g.prec == MWDG_F64) ? c->pd.nleaf : c->pf.nleaf, sizeof(int),
+                     cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *n = cnt;
+  if (!level && !i && !j && !coeffs) return MWDG_OK;
+  if (cap < cnt) return fail(c, MWDG_ERR_CAPACITY, "capacity %lld < %d leaves", (long long)cap, cnt);
+  if (!c->d_active) {
+    mwdg_status s;
+    if ((s = alloc(c, &c->d_active, 3 * (size_t)g.P)) || (s = alloc(c, &c->d_coef, 9 * (size_t)g.P))) return s;
+  }
+  const size_t P = (size_t)g.P;
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::read_active(g, p, c->d_active, c->d_active + P, c->d_active + 2 * P, c->d_coef, c->st);
+  });
+  CHECK_LAUNCH();
+  if (cnt > 0) {
+    if (level) CK(cudaMemcpyAsync(level, c->d_active, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+    if (i) CK(cudaMemcpyAsync(i, c->d_active + P, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+    if (j) CK(cudaMemcpyAsync(j, c->d_active + 2 * P, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+    if (coeffs) CK(cudaMemcpyAsync(coeffs, c->d_coef, 9 * (size_t)cnt * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  if (g.mode == MWDG_UNIFORM && level)
+    for (int q = 0; q < cnt; q++) level[q] = c->p.L;  // reported on the finest level of the parameters
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_get_time(mwdg_ctx *c, double *t, int64_t *steps) {
+  LIVE(c);
+  Ctl h;
+  mwdg_status s = read_ctl(c, &h);
+  if (s) return s;
+  if (t) *t = h.t;
+  if (steps) *steps = h.steps;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_get_volume(mwdg_ctx *c, double *V, double *V_in, double *V_out, double *V_rain,
+                            double *V_clip, int64_t *n_clip) {
+  LIVE(c);
+  const Geo &g = c->g;
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::volume(g, p, c->grid_leaves, c->st);
+  });
+  CHECK_LAUNCH();
+  Ctl h;
+  mwdg_status s = read_ctl(c, &h);
+  if (s) return s;
+  if (V) *V = h.volume;
+  if (V_in) *V_in = h.v_in;
+  if (V_out) *V_out = h.v_out;
+  if (V_rain) *V_rain = h.v_rain;
+  if (V_clip) *V_clip = h.v_clip;
+  if (n_clip) *n_clip = (int64_t)h.n_clip;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_profile(mwdg_ctx *c, int32_t enable) {
+  LIVE(c);
+  mwdg_status s = flush_marks(c);
+  if (s) return s;
+  for (auto &m : c->marks) c->pool.push_back(m.second);
+  c->marks.clear();
+  if (enable) {
+    for (int k = 0; k < KC_COUNT; k++) {
+      c->kms[k] = 0.0;
+      c->kcount[k] = 0;
+    }
+  }
+  c->prof = enable != 0;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_kernel_times(mwdg_ctx *c, const char **names, double *ms, int64_t *launches, int32_t cap,
+                              int32_t *n) {
+  LIVE(c);
+  mwdg_status s = flush_marks(c);
+  if (s) return s;
+  for (int k = 0; k < KC_COUNT && k < cap; k++) {
+    if (names) names[k] = kclass_name(k);
+    if (ms) ms[k] = c->kms[k];
+    if (launches) launches[k] = c->kcount[k];
+  }
+  if (n) *n = KC_COUNT;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_launch_count(mwdg_ctx *c, int64_t *n) {
+  if (!c || !n) return MWDG_ERR_ARG;
+  *n = c->launches;
+  return MWDG_OK;
+}
+
+const char *mwdg_last_error(const mwdg_ctx *c) { return c ? c->err.c_str() : "no context"; }
+
+}  // extern "C"

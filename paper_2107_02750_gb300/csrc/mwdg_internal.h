@@ -1,0 +1,97 @@
+// Internal types shared by the host orchestration (mwdg_api.cu) and the
+// per-precision kernel translation units (mwdg_f64.cu, mwdg_f32.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mwdg.h"
+
+namespace mwdg {
+
+// Step control and diagnostics, resident in device memory so that a run of
+// steps needs no host synchronisation.
+struct Ctl {
+  double t, dt, t_end;
+  unsigned long long dtmin;    // bits of the smallest CFL candidate (positive double)
+  unsigned long long vmax[3];  // bits of max |h0|, |qx0|, |qy0| over the leaves
+  double bnd[2];               // outward boundary mass flux of each RK stage (m^3/s)
+  double v_in, v_out, v_rain, v_clip;
+  double volume;
+  unsigned long long n_clip;
+  long long steps;
+  int nonfinite;
+  int changed;                 // grading sweep made a change
+};
+
+// Geometry and parameters of the level hierarchy (passed by value).
+struct Geo {
+  int L, M, N, mode, limiter, prec;
+  int nxl[MWDG_LMAX + 1], nyl[MWDG_LMAX + 1];
+  long long off[MWDG_LMAX + 2];
+  long long P;                 // nodes over all levels
+  double dxl[MWDG_LMAX + 1];   // element size per level
+  double g, hd, cfl, dt_max, eps, area;
+  int bc[4];
+  int inflow_edge, inflow_c0, inflow_c1, nknots;
+  double rain_rate, rain_t_end;
+};
+
+// Device arrays.  Coefficient arrays are component-major with stride P:
+// component m of node k is at [m * P + k]; node (l, i, j) is
+// k = off[l] + j * nxl[l] + i.
+template <typename T>
+struct Ptrs {
+  T *U;     // state (9): leaves hold the solution, refined nodes its encoding
+  T *Ui;    // RK2 intermediate state (9)
+  T *Wn;    // limited stage-1 input in the stored view (9)
+  T *Wi;    // limited stage-2 input in the stored view (9)
+  T *F;     // limited stage input in the flux view (9); refined nodes: encoding
+  T *Z;     // static topography pyramid (3)
+  T *Ze;    // bed planes of the flux view (3)
+  T *NM;    // Manning n per node (1)
+  double *DZ;   // normalised topography detail per node
+  uint8_t *kind, *kind_old, *flag, *flag2;
+  int *leaves, *nleaf;
+  int *blk;         // compaction scratch: per-block counts / offsets
+  double *part;     // volume partial sums
+  Ctl *ctl;
+  const double *knot_t, *knot_Q;
+};
+
+// Launchers implemented per precision (explicit instantiations in
+// mwdg_f64.cu and mwdg_f32.cu).  All queue work on `st` and return the
+// number of kernels they launched.
+template <typename T> struct Launch {
+  static int project(const Geo &g, const Ptrs<T> &p, const double *vert, T *c0, T *c1x, T *c1y,
+                     cudaStream_t st);
+  static int load_dem_pyramid(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
+  static int roughness_pyramid(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
+  static int initial_finest(const Geo &g, const Ptrs<T> &p, int is_eta, cudaStream_t st);
+  static int encode_dense_U(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
+  static int eta_rule_leaves(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
+  static int static_flags(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
+  static int closure(const Geo &g, uint8_t *flag, cudaStream_t st);
+  static int grading_sweep(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
+  static int kinds(const Geo &g, const Ptrs<T> &p, const uint8_t *flag, int keep_old,
+                   cudaStream_t st);
+  static int all_finest(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
+  static int compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
+  static int adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int decode_only,
+                   cudaStream_t st, void (*mark)(void *, int), void *mark_arg);
+  static int step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st,
+                  void (*mark)(void *, int), void *mark_arg);
+  static int fields(const Geo &g, const Ptrs<T> &p, double *h, double *u, double *v,
+                    cudaStream_t st);
+  static int read_active(const Geo &g, const Ptrs<T> &p, int32_t *lev, int32_t *i, int32_t *j,
+                         double *coef, cudaStream_t st);
+  static int volume(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st);
+  static int dt_only(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st);
+};
+
+// kernel classes reported by the per-kernel timer
+enum KClass {
+  KC_ENCODE = 0, KC_FLAGS, KC_DECODE, KC_COMPACT, KC_DT, KC_CONTROL, KC_FRICTION, KC_LIMIT,
+  KC_VIEW, KC_UPDATE1, KC_UPDATE2, KC_COUNT
+};
+
+}  // namespace mwdg

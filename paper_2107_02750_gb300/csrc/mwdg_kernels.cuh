@@ -1,0 +1,1229 @@
+// Kernels of the DG2 / multiwavelet-MRA flood solver (arXiv 2107.02750) and
+// their launchers, templated on the coefficient type.  Included once per
+// precision (mwdg_f64.cu without FMA contraction, mwdg_f32.cu with it).
+//
+// Data layout: dense per-level pyramids, component-major (see
+// mwdg_internal.h).  Active leaves are listed, level-major and row-major
+// within a level, in p.leaves; leaf kernels run a fixed grid that strides
+// over the device-side count, so a step needs no host synchronisation.
+#pragma once
+#include <cstdint>
+#include <algorithm>
+#include <type_traits>
+
+#include "dg2_math.cuh"
+#include "mwdg_internal.h"
+
+namespace mwdg {
+
+constexpr int TPB = 256;
+
+template <typename T> struct Form { static constexpr bool eta = std::is_same<T, float>::value; };
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+__device__ __forceinline__ void atomic_min_pos(unsigned long long *a, double x) {
+  atomicMin(a, dbits(x));  // ordering of positive doubles equals that of their bits
+}
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double x) {
+  atomicMax(a, dbits(x));
+}
+
+__device__ __forceinline__ void node_of(const Geo &g, long long k, int &l, int &i, int &j) {
+  l = 0;
+  while (l < g.L && k >= g.off[l + 1]) l++;
+  long long r = k - g.off[l];
+  j = (int)(r / g.nxl[l]);
+  i = (int)(r - (long long)j * g.nxl[l]);
+}
+__device__ __forceinline__ long long nid(const Geo &g, int l, int i, int j) {
+  return g.off[l] + (long long)j * g.nxl[l] + i;
+}
+
+// ---------------------------------------------------------------------------
+// Set-up
+// ---------------------------------------------------------------------------
+
+// Eq. 8 (in FP64): interface-centre values are vertex means, average and
+// slopes from them.  The printed four-vertex form of Eq. 8a has 1/2 where the
+// E/W and N/S forms on the same line give 1/4; 1/4 is used.
+template <typename T>
+__global__ void k_project(const double *vert, int nx, int ny, T *c0, T *c1x, T *c1y) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= (long long)nx * ny) return;
+  int j = (int)(k / nx), i = (int)(k - (long long)j * nx);
+  const double s3 = 1.7320508075688772;
+  double sw = vert[(long long)j * (nx + 1) + i], se = vert[(long long)j * (nx + 1) + i + 1];
+  double nw = vert[(long long)(j + 1) * (nx + 1) + i], ne = vert[(long long)(j + 1) * (nx + 1) + i + 1];
+  double zn = 0.5 * (nw + ne), zs = 0.5 * (sw + se);
+  double ze = 0.5 * (ne + se), zw = 0.5 * (nw + sw);
+  c0[k] = (T)(0.5 * (ze + zw));
+  c1x[k] = (T)((ze - zw) / (2.0 * s3));
+  c1y[k] = (T)((zn - zs) / (2.0 * s3));
+}
+
+// max |z0| on the finest level (normalisation of topography details)
+template <typename T>
+__global__ void k_zmax(Geo g, Ptrs<T> p) {
+  long long n = (long long)g.nxl[g.L] * g.nyl[g.L];
+  double m = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs((double)p.Z[g.off[g.L] + k]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_pos(&p.ctl->vmax[0], m);
+}
+
+// z pyramid level l from level l+1 (Eq. 9) and each node's normalised detail
+template <typename T>
+__global__ void k_encode_z(Geo g, Ptrs<T> p, int l) {
+  long long n = (long long)g.nxl[l] * g.nyl[l];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+  const long long P = g.P;
+  T ch[4][3];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    long long kc = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
+#pragma unroll
+    for (int m = 0; m < 3; m++) ch[c][m] = p.Z[m * P + kc];
+  }
+  T sp[3];
+  encode3(ch, sp);
+  long long k = g.off[l] + r;
+#pragma unroll
+  for (int m = 0; m < 3; m++) p.Z[m * P + k] = sp[m];
+  double norm = fmax(1.0, __longlong_as_double((long long)p.ctl->vmax[0]));
+  p.DZ[k] = (double)detail_max3(ch) / norm;
+}
+
+// Manning n: coarser nodes hold the mean of their children
+template <typename T>
+__global__ void k_nm_level(Geo g, Ptrs<T> p, int l) {
+  long long n = (long long)g.nxl[l] * g.nyl[l];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+  T acc = T(0);
+  for (int c = 0; c < 4; c++) acc = acc + p.NM[nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1))];
+  p.NM[g.off[l] + r] = T(0.25) * acc;
+}
+
+// Finest-level initial state.  On entry the first three components hold the
+// projected depth (is_eta = 0) or free surface (is_eta = 1).  Depth form
+// (FP64): with is_eta, wet elements get h = eta - z, others are dry.  Free
+// surface form (FP32): eta is stored; dry elements get eta = z.
+template <typename T>
+__global__ void k_initial_finest(Geo g, Ptrs<T> p, int is_eta) {
+  const int L = g.L;
+  long long n = (long long)g.nxl[L] * g.nyl[L];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const long long P = g.P, k = g.off[L] + r;
+  T *U = p.U;
+  if (Form<T>::eta) {
+    if (!is_eta) {
+      for (int m = 0; m < 3; m++) U[m * P + k] = U[m * P + k] + p.Z[m * P + k];
+    } else if (!(U[k] > p.Z[k])) {
+      for (int m = 0; m < 3; m++) U[m * P + k] = p.Z[m * P + k];
+      for (int m = 3; m < 9; m++) U[m * P + k] = T(0);
+    }
+  } else if (is_eta) {
+    if (U[k] > p.Z[k]) {
+      for (int m = 0; m < 3; m++) U[m * P + k] = U[m * P + k] - p.Z[m * P + k];
+    } else {
+      for (int m = 0; m < 9; m++) U[m * P + k] = T(0);
+    }
+  }
+}
+
+// dense Eq. 9 of `ncomp` components of X from level l+1 to level l
+template <typename T>
+__global__ void k_encode_dense(Geo g, T *X, int ncomp, int l) {
+  long long n = (long long)g.nxl[l] * g.nyl[l];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+  const long long P = g.P, k = g.off[l] + r;
+  for (int v = 0; v < ncomp / 3; v++) {
+    T ch[4][3], sp[3];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      long long kc = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
+#pragma unroll
+      for (int m = 0; m < 3; m++) ch[c][m] = X[(3 * v + m) * P + kc];
+    }
+    encode3(ch, sp);
+#pragma unroll
+    for (int m = 0; m < 3; m++) X[(3 * v + m) * P + k] = sp[m];
+  }
+}
+
+// static grid, free-surface initial state: the encoded free surface (held in
+// Wn[0..2]) is split into depth per leaf with the wet/dry rule
+template <typename T>
+__global__ void k_eta_rule_leaves(Geo g, Ptrs<T> p) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= g.P || p.kind[k] != K_LEAF) return;
+  const long long P = g.P;
+  const T *E = p.Wn;
+  if (E[k] > p.Z[k]) {
+    for (int m = 0; m < 3; m++)
+      p.U[m * P + k] = Form<T>::eta ? E[m * P + k] : E[m * P + k] - p.Z[m * P + k];
+  } else {
+    for (int m = 0; m < 3; m++) p.U[m * P + k] = Form<T>::eta ? p.Z[m * P + k] : T(0);
+    for (int m = 3; m < 9; m++) p.U[m * P + k] = T(0);
+  }
+}
+
+// static grid: significant topography details (Sect. 2.2)
+template <typename T>
+__global__ void k_static_flags(Geo g, Ptrs<T> p) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= g.P) return;
+  p.flag[k] = (k < g.off[g.L]) ? (uint8_t)(p.DZ[k] >= g.eps) : (uint8_t)0;
+}
+
+// parent closure from level l to l-1: a flagged child flags its parent
+static __global__ void k_closure(Geo g, uint8_t *flag, int l) {
+  long long n = (long long)g.nxl[l] * g.nyl[l];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  if (!flag[g.off[l] + r]) return;
+  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+  flag[nid(g, l - 1, i >> 1, j >> 1)] = 1;
+}
+
+// 2:1 grading (Sect. 2.2.1, Fig. 2b): the face neighbours of a flagged node
+// at level l >= 1 must exist, so their parents are flagged
+template <typename T>
+__global__ void k_grading(Geo g, Ptrs<T> p, int l) {
+  long long n = (long long)g.nxl[l] * g.nyl[l];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  if (!p.flag[g.off[l] + r]) return;
+  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+  const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+  for (int f = 0; f < 4; f++) {
+    int a = i + di[f], b = j + dj[f];
+    if (a < 0 || b < 0 || a >= g.nxl[l] || b >= g.nyl[l]) continue;
+    long long kp = nid(g, l - 1, a >> 1, b >> 1);
+    if (!p.flag[kp]) {
+      p.flag[kp] = 1;
+      p.ctl->changed = 1;
+    }
+  }
+}
+
+// node kinds from flags (flags already closed under parents): refined,
+// active leaf (parent refined or root, not refined itself) or below a leaf
+template <typename T>
+__global__ void k_kinds(Geo g, Ptrs<T> p, const uint8_t *flag, int keep_old) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= g.P) return;
+  int l, i, j;
+  node_of(g, k, l, i, j);
+  int f = (l < g.L) ? flag[k] : 0;
+  int parent = (l == 0) ? 1 : flag[nid(g, l - 1, i >> 1, j >> 1)];
+  if (keep_old) p.kind_old[k] = p.kind[k];
+  p.kind[k] = f ? K_SIG : (parent ? K_LEAF : K_BELOW);
+}
+
+template <typename T>
+__global__ void k_all_finest(Geo g, Ptrs<T> p) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= g.P) return;
+  p.kind[k] = (k >= g.off[g.L]) ? K_LEAF : K_SIG;
+}
+
+// ---------------------------------------------------------------------------
+// Ballot / prefix-sum compaction of the active leaves (order preserved)
+// ---------------------------------------------------------------------------
+constexpr int CPT = 8;                 // nodes per thread
+constexpr int CTILE = TPB * CPT;       // nodes per block
+
+static __global__ void k_compact_count(long long P, const uint8_t *kind, int *blk) {
+  long long base = (long long)blockIdx.x * CTILE;
+  int c = 0;
+  for (int q = 0; q < CPT; q++) {
+    long long k = base + q * TPB + threadIdx.x;
+    c += (k < P && kind[k] == K_LEAF);
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ int ws[TPB / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < TPB / 32; w++) s += ws[w];
+    blk[blockIdx.x] = s;
+  }
+}
+
+// exclusive scan of the block counts (one block) and the total
+static __global__ void k_compact_scan(int nb, int *blk, int *total) {
+  __shared__ int carry;
+  __shared__ int ws[1024 / 32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += blockDim.x) {
+    int idx = base + threadIdx.x;
+    int v = (idx < nb) ? blk[idx] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int w = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (threadIdx.x >= o) w += y;
+      }
+      ws[threadIdx.x] = w;
+    }
+    __syncthreads();
+    int warp_off = (threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0;
+    int incl = x + warp_off + carry;
+    if (idx < nb) blk[idx] = incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+static __global__ void k_compact_scatter(long long P, const uint8_t *kind, const int *blk, int *leaves) {
+  long long base = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
+  int c = 0;
+  for (int q = 0; q < CPT; q++) {
+    long long k = base + q;
+    c += (k < P && kind[k] == K_LEAF);
+  }
+  // block-wide exclusive scan of per-thread counts
+  int x = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) >= o) x += y;
+  }
+  __shared__ int ws[TPB / 32];
+  if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int w = (threadIdx.x < TPB / 32) ? ws[threadIdx.x] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (threadIdx.x >= o) w += y;
+    }
+    if (threadIdx.x < TPB / 32) ws[threadIdx.x] = w;
+  }
+  __syncthreads();
+  int pos = blk[blockIdx.x] + x - c + ((threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0);
+  for (int q = 0; q < CPT; q++) {
+    long long k = base + q;
+    if (k < P && kind[k] == K_LEAF) leaves[pos++] = (int)k;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary forcing
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double inflow_Q(const Geo &g, const double *kt, const double *kQ, double t) {
+  int n = g.nknots;
+  if (n <= 0) return 0.0;
+  if (t <= kt[0]) return kQ[0];
+  if (t >= kt[n - 1]) return kQ[n - 1];
+  int k = 0;
+  while (k + 1 < n && !(t < kt[k + 1])) k++;
+  double tk = kt[k], tk1 = kt[k + 1], Qk = kQ[k], Qk1 = kQ[k + 1];
+  return Qk + (Qk1 - Qk) * (t - tk) / (tk1 - tk);
+}
+
+// unit discharge through the boundary face of a leaf (level l, index k along
+// edge e): the hydrograph spread over the inflow cells times the overlap
+__device__ __forceinline__ double inflow_q(const Geo &g, const double *kt, const double *kQ, int e, int l,
+                                           int k, double t) {
+  if (g.inflow_edge != e) return 0.0;
+  int sh = g.L - l;
+  long long a = (long long)k << sh, b = (long long)(k + 1) << sh;
+  long long lo = a > g.inflow_c0 ? a : g.inflow_c0;
+  long long hi = b < (long long)g.inflow_c1 + 1 ? b : (long long)g.inflow_c1 + 1;
+  long long ov = hi - lo;
+  if (ov <= 0) return 0.0;
+  long long nin = (long long)g.inflow_c1 - g.inflow_c0 + 1;
+  return inflow_Q(g, kt, kQ, t) * (double)ov / ((double)nin * g.dxl[l]);
+}
+
+// ---------------------------------------------------------------------------
+// Step kernels (leaf-list, fixed grid striding over the device count)
+// ---------------------------------------------------------------------------
+#define FOR_LEAVES(p)                                                              \
+  const int _nl = *(p).nleaf;                                                      \
+  for (int _q = blockIdx.x * blockDim.x + threadIdx.x; _q < _nl; _q += gridDim.x * blockDim.x)
+
+// max |v0| over the leaves of h, qx, qy (normalisation of flow details)
+template <typename T>
+__global__ void k_leaf_maxabs(Geo g, Ptrs<T> p) {
+  double m0 = 0, m1 = 0, m2 = 0;
+  const long long P = g.P;
+  FOR_LEAVES(p) {
+    long long k = p.leaves[_q];
+    T h0 = Form<T>::eta ? p.U[k] - p.Z[k] : p.U[k];
+    m0 = fmax(m0, (double)tabs(h0));
+    m1 = fmax(m1, (double)tabs(p.U[3 * P + k]));
+    m2 = fmax(m2, (double)tabs(p.U[6 * P + k]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_pos(&p.ctl->vmax[0], m0);
+    atomic_max_pos(&p.ctl->vmax[1], m1);
+    atomic_max_pos(&p.ctl->vmax[2], m2);
+  }
+}
+
+// MWDG2 encode of level l (Sect. 2.3): refined nodes get the scale
+// coefficients of their children (Eq. 9) and are flagged when their largest
+// normalised flow or topography detail reaches epsilon; other nodes carry
+// no flow details, so only their topography detail counts.
+template <typename T>
+__global__ void k_encode_flow(Geo g, Ptrs<T> p, int l) {
+  long long n = (long long)g.nxl[l] * g.nyl[l];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const long long P = g.P, k = g.off[l] + r;
+  double dmax = p.DZ[k];
+  if (p.kind[k] == K_SIG) {
+    int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+    long long kc[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) kc[c] = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
+    for (int v = 0; v < 3; v++) {
+      T ch[4][3], sp[3];
+#pragma unroll
+      for (int c = 0; c < 4; c++)
+#pragma unroll
+        for (int m = 0; m < 3; m++) ch[c][m] = p.U[(3 * v + m) * P + kc[c]];
+      encode3(ch, sp);
+#pragma unroll
+      for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sp[m];
+      if (Form<T>::eta && v == 0) {  // details of the depth h = eta - z
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+#pragma unroll
+          for (int m = 0; m < 3; m++) ch[c][m] = ch[c][m] - p.Z[m * P + kc[c]];
+      }
+      double dm = (double)detail_max3(ch);
+      double mx = __longlong_as_double((long long)p.ctl->vmax[v]);
+      dmax = fmax(dmax, dm / fmax(1.0, mx));
+    }
+  }
+  p.flag[k] = (l < g.L) ? (uint8_t)(dmax >= g.eps) : (uint8_t)0;
+}
+
+// prediction: a significant node flags its eight same-level neighbours
+template <typename T>
+__global__ void k_predict(Geo g, Ptrs<T> p, int l) {
+  long long n = (long long)g.nxl[l] * g.nyl[l];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+  uint8_t f = 0;
+  for (int b = j - 1; b <= j + 1; b++)
+    for (int a = i - 1; a <= i + 1; a++)
+      if (a >= 0 && b >= 0 && a < g.nxl[l] && b < g.nyl[l]) f |= p.flag[nid(g, l, a, b)];
+  p.flag2[g.off[l] + r] = f;
+}
+
+// new leaves that were below an old leaf take the prolongation of its plane
+// (Eq. 10 with zero details, one level at a time)
+template <typename T>
+__global__ void k_decode_new(Geo g, Ptrs<T> p) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= g.P || p.kind[k] != K_LEAF || p.kind_old[k] != K_BELOW) return;
+  int l, i, j;
+  node_of(g, k, l, i, j);
+  int path[MWDG_LMAX + 1];
+  int d = 0, a = i, b = j, la = l;
+  long long ka = k;
+  while (la > 0 && p.kind_old[ka] == K_BELOW) {
+    path[d++] = (a & 1) + 2 * (b & 1);
+    a >>= 1;
+    b >>= 1;
+    la--;
+    ka = nid(g, la, a, b);
+  }
+  const long long P = g.P;
+  for (int v = 0; v < 3; v++) {
+    T s[3];
+    for (int m = 0; m < 3; m++) s[m] = p.U[(3 * v + m) * P + ka];
+    for (int q = d - 1; q >= 0; q--) {
+      T o[3];
+      prolong3(s[0], s[1], s[2], path[q], o);
+      s[0] = o[0]; s[1] = o[1]; s[2] = o[2];
+    }
+    for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = s[m];
+  }
+}
+
+// CFL candidates over the leaves (Courant number applied in k_begin_step)
+template <typename T>
+__global__ void k_leaf_dt(Geo g, Ptrs<T> p) {
+  const long long P = g.P;
+  const T gg = (T)g.g, hd = (T)g.hd;
+  const double t = p.ctl->t;
+  double best = __longlong_as_double(0x7ff0000000000000LL);
+  FOR_LEAVES(p) {
+    long long k = p.leaves[_q];
+    int l, i, j;
+    node_of(g, k, l, i, j);
+    const T dxl = (T)g.dxl[l];
+    T h0 = Form<T>::eta ? p.U[k] - p.Z[k] : p.U[k];
+    if (h0 > hd) {
+      T u = p.U[3 * P + k] / h0, v = p.U[6 * P + k] / h0;
+      T c = tsqrt(gg * h0);
+      best = fmin(best, (double)tmin(dxl / (tabs(u) + c), dxl / (tabs(v) + c)));
+    }
+    if (g.inflow_edge >= 0) {
+      for (int e = 0; e < 4; e++) {
+        bool on = (e == 0 && i == 0) || (e == 1 && i == g.nxl[l] - 1) || (e == 2 && j == 0) ||
+                  (e == 3 && j == g.nyl[l] - 1);
+        if (!on) continue;
+        double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, t);
+        if (q > 0.0) {
+          T qt = (T)q;
+          T hc = tcbrt(qt * qt / gg);
+          if (hc > hd) best = fmin(best, (double)(dxl / (qt / hc + tsqrt(gg * hc))));
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomic_min_pos(&p.ctl->dtmin, best);
+}
+
+// dt = min(C * min candidate, dt_max, t_end - t) and per-step resets
+static __global__ void k_begin_step(Geo g, Ctl *c) {
+  double best = __longlong_as_double((long long)c->dtmin);
+  double dt = g.dt_max;
+  if (best < __longlong_as_double(0x7ff0000000000000LL)) dt = fmin(dt, g.cfl * best);
+  dt = fmin(dt, c->t_end - c->t);
+  c->dt = dt > 0.0 ? dt : 0.0;
+  c->bnd[0] = 0.0;
+  c->bnd[1] = 0.0;
+}
+
+static __global__ void k_end_step(Geo g, Ctl *c) {
+  double dt = c->dt;
+  if (!(dt > 0.0)) return;
+  double net = 0.5 * dt * (c->bnd[0] + c->bnd[1]);
+  if (net >= 0.0) c->v_out += net;
+  else c->v_in += -net;
+  if (c->t < g.rain_t_end && g.rain_rate > 0.0) c->v_rain += g.rain_rate * dt * g.area;
+  c->t = c->t + dt;
+  c->steps += 1;
+  c->dtmin = 0x7ff0000000000000ULL;
+  c->vmax[0] = c->vmax[1] = c->vmax[2] = 0ULL;
+}
+
+// rain, then split implicit friction (Sect. 2.1.1): linearised backward
+// Euler of dq/dt = -g n^2 |u| q / h^(4/3), the same factor on averages and
+// slopes; dry leaves lose their discharge
+template <typename T>
+__global__ void k_rain_friction(Geo g, Ptrs<T> p) {
+  const long long P = g.P;
+  const double dtd = p.ctl->dt;
+  if (!(dtd > 0.0)) return;
+  const T dt = (T)dtd, gg = (T)g.g, hd = (T)g.hd;
+  const bool rain = p.ctl->t < g.rain_t_end && g.rain_rate > 0.0;
+  const T rdt = (T)(g.rain_rate * dtd);
+  FOR_LEAVES(p) {
+    long long k = p.leaves[_q];
+    T w0 = p.U[k];
+    if (rain) {
+      w0 = w0 + (Form<T>::eta ? rdt : (T)(g.rain_rate) * dt);
+      p.U[k] = w0;
+    }
+    T h0 = Form<T>::eta ? w0 - p.Z[k] : w0;
+    if (h0 > hd) {
+      T u = p.U[3 * P + k] / h0, v = p.U[6 * P + k] / h0;
+      T sp = tsqrt(u * u + v * v);
+      T nm = p.NM[k];
+      T den = T(1) + dt * gg * nm * nm * sp / (h0 * tcbrt(h0));
+      T f = T(1) / den;
+      for (int m = 3; m < 9; m++) p.U[m * P + k] = p.U[m * P + k] * f;
+    } else {
+      for (int m = 3; m < 9; m++) p.U[m * P + k] = T(0);
+    }
+  }
+}
+
+// Stage-input limiting of each leaf, giving the stored view Wst (used by
+// the RK2 combination) and the flux view F with its bed planes Ze.
+// Partially wet leaves (average, any interface depth of the plane, or any
+// interface depth under a flat free surface h0 + z0, not wetter than h_dry)
+// drop to first order: stored as a flat free surface over the planar bed,
+// seen by the fluxes as flat depth over a flat bed.  Other leaves on the
+// finest level with wet finest-level neighbours on both sides get the minmod
+// limiter on eta, qx, qy per direction.
+template <typename T>
+__global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
+  const long long P = g.P;
+  const T hd = (T)g.hd, s3 = s3v<T>();
+  FOR_LEAVES(p) {
+    long long k = p.leaves[_q];
+    T w[9], zp[3];
+#pragma unroll
+    for (int m = 0; m < 9; m++) w[m] = X[m * P + k];
+#pragma unroll
+    for (int m = 0; m < 3; m++) zp[m] = p.Z[m * P + k];
+    T h0, eta0;
+    if (Form<T>::eta) {
+      eta0 = w[0];
+      h0 = eta0 - zp[0];
+    } else {
+      h0 = w[0];
+      eta0 = h0 + zp[0];
+    }
+    bool reduced = !(h0 > hd);
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+      T hf = Form<T>::eta ? face_value(w[0], w[1], w[2], f) - face_value(zp[0], zp[1], zp[2], f)
+                          : face_value(w[0], w[1], w[2], f);
+      if (!(hf > hd)) reduced = true;
+      if (!(eta0 - face_value(zp[0], zp[1], zp[2], f) > hd)) reduced = true;
+    }
+    T ws[9], wf[9], ze[3];
+    if (reduced) {
+#pragma unroll
+      for (int m = 0; m < 9; m++) ws[m] = w[m];
+      if (Form<T>::eta) {
+        ws[1] = T(0); ws[2] = T(0);
+      } else {
+        ws[1] = -zp[1]; ws[2] = -zp[2];
+      }
+      ws[4] = ws[5] = ws[7] = ws[8] = T(0);
+#pragma unroll
+      for (int m = 0; m < 9; m++) wf[m] = ws[m];
+      if (!Form<T>::eta) {
+        wf[1] = T(0); wf[2] = T(0);
+      }
+      ze[0] = zp[0]; ze[1] = T(0); ze[2] = T(0);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 9; m++) ws[m] = w[m];
+      ze[0] = zp[0]; ze[1] = zp[1]; ze[2] = zp[2];
+      int l, i, j;
+      node_of(g, k, l, i, j);
+      if (g.limiter && l == g.L) {
+        for (int dir = 0; dir < 2; dir++) {
+          int ia = i + (dir == 0), ja = j + (dir == 1), ib = i - (dir == 0), jb = j - (dir == 1);
+          if (ib < 0 || jb < 0 || ia >= g.nxl[l] || ja >= g.nyl[l]) continue;
+          long long ka = nid(g, l, ia, ja), kb = nid(g, l, ib, jb);
+          if (p.kind[ka] != K_LEAF || p.kind[kb] != K_LEAF) continue;
+          T hC = h0;
+          T hA = Form<T>::eta ? X[ka] - p.Z[ka] : X[ka];
+          T hB = Form<T>::eta ? X[kb] - p.Z[kb] : X[kb];
+          if (!(hC > hd && hA > hd && hB > hd)) continue;
+          const int cs = 1 + dir;
+          for (int v = 0; v < 3; v++) {
+            T a0, aC, aB, slope;
+            const T zs = zp[cs];
+            if (v == 0) {
+              if (Form<T>::eta) {
+                aC = w[0]; a0 = X[ka]; aB = X[kb];
+                slope = w[cs];
+              } else {
+                aC = hC + zp[0];
+                a0 = hA + p.Z[ka];
+                aB = hB + p.Z[kb];
+                slope = w[cs] + zs;
+              }
+            } else {
+              aC = w[3 * v];
+              a0 = X[3 * v * P + ka];
+              aB = X[3 * v * P + kb];
+              slope = w[3 * v + cs];
+            }
+            T a = s3 * slope, b = a0 - aC, c = aC - aB;
+            T mm = minmod3(a, b, c);
+            if (mm != a) {
+              T ns = mm / s3;
+              if (v == 0) ws[cs] = Form<T>::eta ? ns : ns - zs;
+              else ws[3 * v + cs] = ns;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 9; m++) wf[m] = ws[m];
+    }
+#pragma unroll
+    for (int m = 0; m < 9; m++) {
+      Wst[m * P + k] = ws[m];
+      p.F[m * P + k] = wf[m];
+    }
+#pragma unroll
+    for (int m = 0; m < 3; m++) p.Ze[m * P + k] = ze[m];
+  }
+}
+
+// local encoding (Eq. 9) of the flux view and its beds onto the refined
+// nodes of level l (MWDG2 interfaces, Sect. 2.3)
+template <typename T>
+__global__ void k_encode_view(Geo g, Ptrs<T> p, int l) {
+  long long n = (long long)g.nxl[l] * g.nyl[l];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const long long P = g.P, k = g.off[l] + r;
+  if (p.kind[k] != K_SIG) return;
+  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+  long long kc[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) kc[c] = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
+  for (int v = 0; v < 4; v++) {
+    T *X = (v < 3) ? p.F + 3 * v * P : p.Ze;
+    T ch[4][3], sp[3];
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+#pragma unroll
+      for (int m = 0; m < 3; m++) ch[c][m] = X[m * P + kc[c]];
+    encode3(ch, sp);
+#pragma unroll
+    for (int m = 0; m < 3; m++) X[m * P + k] = sp[m];
+  }
+}
+
+// limit (first variable, qx, qy, z) of the same-level view of the neighbour
+// across face f of leaf (l, i, j); false on the domain boundary
+template <typename T>
+__device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, T out[4]) {
+  const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
+  if (a < 0 || b < 0 || a >= g.nxl[l] || b >= g.nyl[l]) return false;
+  const int fo = f ^ 1;
+  const long long P = g.P;
+  long long k = nid(g, l, a, b);
+  const uint8_t kd = p.kind[k];
+  if (kd == K_SIG && g.mode == MWDG_STATIC) {
+    // Sect. 2.2.1: the coarse side interpolates the limit from the two finer
+    // interface centres (graded grid: both are level l+1 leaves)
+    int c1, c2;
+    if (f == 0) { c1 = 0; c2 = 2; }
+    else if (f == 1) { c1 = 1; c2 = 3; }
+    else if (f == 2) { c1 = 0; c2 = 1; }
+    else { c1 = 2; c2 = 3; }
+    long long k1 = nid(g, l + 1, 2 * a + (c1 & 1), 2 * b + (c1 >> 1));
+    long long k2 = nid(g, l + 1, 2 * a + (c2 & 1), 2 * b + (c2 >> 1));
+    for (int v = 0; v < 3; v++) {
+      const T *X = p.F + 3 * v * P;
+      out[v] = T(0.5) * (face_value(X[k1], X[P + k1], X[2 * P + k1], fo) +
+                         face_value(X[k2], X[P + k2], X[2 * P + k2], fo));
+    }
+    out[3] = T(0.5) * (face_value(p.Ze[k1], p.Ze[P + k1], p.Ze[2 * P + k1], fo) +
+                       face_value(p.Ze[k2], p.Ze[P + k2], p.Ze[2 * P + k2], fo));
+    return true;
+  }
+  if (kd == K_BELOW) {
+    // prolongation of the covering coarser leaf's plane down to this node
+    int path[MWDG_LMAX + 1];
+    int d = 0, aa = a, bb = b, la = l;
+    long long ka = k;
+    while (la > 0 && p.kind[ka] == K_BELOW) {
+      path[d++] = (aa & 1) + 2 * (bb & 1);
+      aa >>= 1;
+      bb >>= 1;
+      la--;
+      ka = nid(g, la, aa, bb);
+    }
+    for (int v = 0; v < 4; v++) {
+      const T *X = (v < 3) ? p.F + 3 * v * P : p.Ze;
+      T s[3] = {X[ka], X[P + ka], X[2 * P + ka]};
+      for (int q = d - 1; q >= 0; q--) {
+        T o[3];
+        prolong3(s[0], s[1], s[2], path[q], o);
+        s[0] = o[0]; s[1] = o[1]; s[2] = o[2];
+      }
+      out[v] = face_value(s[0], s[1], s[2], fo);
+    }
+    return true;
+  }
+  for (int v = 0; v < 3; v++) {
+    const T *X = p.F + 3 * v * P;
+    out[v] = face_value(X[k], X[P + k], X[2 * P + k], fo);
+  }
+  out[3] = face_value(p.Ze[k], p.Ze[P + k], p.Ze[2 * P + k], fo);
+  return true;
+}
+
+// One RK2 stage on every leaf (Eq. 4a for STAGE 1, Eq. 4b for STAGE 2):
+// the DG2 operator L = [L0, L1x, L1y] from the flux view (interface fluxes
+// of the revised limits by HLL, bed source with the revised interface beds,
+// two-point interface rule for the slope volume integrals with the bed
+// source S1 = -(2 sqrt3 g / dx) h1 (h1 + z1) that cancels its hydrostatic
+// error at rest), then the update, the positivity clip and the dry reset.
+template <typename T, int STAGE>
+__global__ void k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out) {
+  const long long P = g.P;
+  const double dtd = p.ctl->dt;
+  if (!(dtd > 0.0)) return;
+  const T dt = (T)dtd, gg = (T)g.g, hd = (T)g.hd, s3 = s3v<T>();
+  const double tf = (STAGE == 1) ? p.ctl->t : p.ctl->t + dtd;
+  double bsum = 0.0, csum = 0.0;
+  unsigned long long ncl = 0;
+  bool bad = false;
+  FOR_LEAVES(p) {
+    long long k = p.leaves[_q];
+    int l, i, j;
+    node_of(g, k, l, i, j);
+    const T dxl = (T)g.dxl[l];
+    T w[9], zc[3];
+#pragma unroll
+    for (int m = 0; m < 9; m++) w[m] = p.F[m * P + k];
+#pragma unroll
+    for (int m = 0; m < 3; m++) zc[m] = p.Ze[m * P + k];
+    T Fh[4][3], hs[4], us[4], vs[4], zr[4];
+    double bout = 0.0;
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+      T own[4], nb[4];
+      own[0] = face_value(w[0], w[1], w[2], f);
+      own[1] = face_value(w[3], w[4], w[5], f);
+      own[2] = face_value(w[6], w[7], w[8], f);
+      own[3] = face_value(zc[0], zc[1], zc[2], f);
+      bool inside = nbr_limit(g, p, l, i, j, f, nb);
+      if (!inside) {
+        // ghost: wall mirror, open copy, or critical-depth inflow
+        const int e = (f == 0) ? 1 : (f == 1) ? 0 : (f == 2) ? 3 : 2;
+        double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, tf);
+        nb[3] = own[3];
+        if (q > 0.0) {
+          T qt = (T)q;
+          T hc = tcbrt(qt * qt / gg);
+          T hown = Form<T>::eta ? own[0] - own[3] : own[0];
+          T hg = tmax(hown, hc);
+          nb[0] = Form<T>::eta ? hg + own[3] : hg;
+          T qn = (e == 0 || e == 2) ? qt : -qt;
+          if (e < 2) { nb[1] = qn; nb[2] = T(0); }
+          else { nb[1] = T(0); nb[2] = qn; }
+        } else if (g.bc[e] == MWDG_OPEN) {
+          nb[0] = own[0]; nb[1] = own[1]; nb[2] = own[2];
+        } else {
+          nb[0] = own[0];
+          if (e < 2) { nb[1] = -own[1]; nb[2] = own[2]; }
+          else { nb[1] = own[1]; nb[2] = -own[2]; }
+        }
+      }
+      const T zf = tmax(own[3], nb[3]);
+      Side<T> so, sn;
+      if (Form<T>::eta) {
+        so = revise_eta(own[0], own[1], own[2], own[3], zf, hd);
+        sn = revise_eta(nb[0], nb[1], nb[2], nb[3], zf, hd);
+      } else {
+        so = revise_h(own[0], own[1], own[2], own[3], zf, hd);
+        sn = revise_h(nb[0], nb[1], nb[2], nb[3], zf, hd);
+      }
+      hs[f] = so.hs; us[f] = so.u; vs[f] = so.v; zr[f] = so.zr;
+      T F3[3];
+      if (f == 0) {
+        hll(so.hs, so.u, so.v, sn.hs, sn.u, sn.v, gg, hd, F3);
+        Fh[f][0] = F3[0]; Fh[f][1] = F3[1]; Fh[f][2] = F3[2];
+      } else if (f == 1) {
+        hll(sn.hs, sn.u, sn.v, so.hs, so.u, so.v, gg, hd, F3);
+        Fh[f][0] = F3[0]; Fh[f][1] = F3[1]; Fh[f][2] = F3[2];
+      } else if (f == 2) {
+        hll(so.hs, so.v, so.u, sn.hs, sn.v, sn.u, gg, hd, F3);
+        Fh[f][0] = F3[0]; Fh[f][1] = F3[2]; Fh[f][2] = F3[1];
+      } else {
+        hll(sn.hs, sn.v, sn.u, so.hs, so.v, so.u, gg, hd, F3);
+        Fh[f][0] = F3[0]; Fh[f][1] = F3[2]; Fh[f][2] = F3[1];
+      }
+      if (!inside) {
+        double outward = (f == 0 || f == 2) ? (double)Fh[f][0] : -(double)Fh[f][0];
+        bout += outward * (double)dxl;
+      }
+    }
+    // physical fluxes of the own revised limits
+    T Fx[2][3], Gy[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+      int f = a;
+      T q = hs[f] * us[f];
+      Fx[a][0] = q;
+      Fx[a][1] = q * us[f] + T(0.5) * gg * hs[f] * hs[f];
+      Fx[a][2] = q * vs[f];
+      f = 2 + a;
+      T r = hs[f] * vs[f];
+      Gy[a][0] = r;
+      Gy[a][1] = r * us[f];
+      Gy[a][2] = r * vs[f] + T(0.5) * gg * hs[f] * hs[f];
+    }
+    T Lo[9];
+    // slopes of the depth for the bed source: h1 and eta1 = h1 + z1
+    T h1x, h1y, e1x, e1y;
+    if (Form<T>::eta) {
+      e1x = w[1]; e1y = w[2];
+      h1x = w[1] - zc[1]; h1y = w[2] - zc[2];
+    } else {
+      h1x = w[1]; h1y = w[2];
+      e1x = w[1] + zc[1]; e1y = w[2] + zc[2];
+    }
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+      T L0 = -(Fh[0][v] - Fh[1][v]) / dxl - (Fh[2][v] - Fh[3][v]) / dxl;
+      if (v == 1) L0 = L0 + -gg * T(0.5) * (hs[0] + hs[1]) * (zr[0] - zr[1]) / dxl;
+      if (v == 2) L0 = L0 + -gg * T(0.5) * (hs[2] + hs[3]) * (zr[2] - zr[3]) / dxl;
+      T L1x = -(s3 / dxl) * (Fh[0][v] + Fh[1][v] - Fx[0][v] - Fx[1][v]);
+      T L1y = -(s3 / dxl) * (Fh[2][v] + Fh[3][v] - Gy[0][v] - Gy[1][v]);
+      if (v == 1) L1x = L1x + -(T(2) * s3 * gg / dxl) * h1x * e1x;
+      if (v == 2) L1y = L1y + -(T(2) * s3 * gg / dxl) * h1y * e1y;
+      Lo[3 * v + 0] = L0;
+      Lo[3 * v + 1] = L1x;
+      Lo[3 * v + 2] = L1y;
+    }
+    T o[9];
+    if (STAGE == 1) {
+#pragma unroll
+      for (int m = 0; m < 9; m++) o[m] = Wst[m * P + k] + dt * Lo[m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < 9; m++) o[m] = T(0.5) * (Wcomb[m * P + k] + Wst[m * P + k] + dt * Lo[m]);
+    }
+    // positivity clip and dry reset
+    const double area = g.dxl[l] * g.dxl[l];
+    if (Form<T>::eta) {
+      const T z0 = p.Z[k];
+      T h0 = o[0] - z0;
+      if (h0 < T(0)) {
+        ncl++;
+        csum += -(double)h0 * area;
+        o[0] = z0;
+        h0 = T(0);
+      }
+      if (!(h0 > hd)) {
+        o[1] = p.Z[P + k];
+        o[2] = p.Z[2 * P + k];
+        for (int m = 3; m < 9; m++) o[m] = T(0);
+      }
+    } else {
+      if (o[0] < T(0)) {
+        ncl++;
+        csum += -(double)o[0] * area;
+        o[0] = T(0);
+      }
+      if (!(o[0] > hd)) {
+        o[1] = T(0); o[2] = T(0);
+        for (int m = 3; m < 9; m++) o[m] = T(0);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 9; m++) {
+      if (!isfinite(o[m])) bad = true;
+      Out[m * P + k] = o[m];
+    }
+    bsum += bout;
+  }
+  if (bad) p.ctl->nonfinite = 1;
+  for (int o = 16; o > 0; o >>= 1) {
+    bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+    csum += __shfl_xor_sync(0xffffffffu, csum, o);
+    ncl += __shfl_xor_sync(0xffffffffu, ncl, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bsum != 0.0) atomicAdd(&p.ctl->bnd[STAGE - 1], bsum);
+    if (ncl) {
+      atomicAdd(&p.ctl->n_clip, ncl);
+      atomicAdd(&p.ctl->v_clip, csum);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Read-back
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fields(Geo g, Ptrs<T> p, double *h, double *u, double *v) {
+  const int L = g.L;
+  long long n = (long long)g.nxl[L] * g.nyl[L];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int J = (int)(r / g.nxl[L]), I = (int)(r - (long long)J * g.nxl[L]);
+  int l = L, a = I, b = J;
+  long long k = nid(g, l, a, b);
+  while (l > 0 && p.kind[k] != K_LEAF) {
+    a >>= 1; b >>= 1; l--;
+    k = nid(g, l, a, b);
+  }
+  const int w = 1 << (L - l);
+  const double s3 = 1.7320508075688772;
+  double xi = ((double)(I - a * w) + 0.5) / (double)w - 0.5;
+  double et = ((double)(J - b * w) + 0.5) / (double)w - 0.5;
+  const long long P = g.P;
+  double val[3];
+  for (int q = 0; q < 3; q++) {
+    double c0 = (double)p.U[3 * q * P + k], c1 = (double)p.U[(3 * q + 1) * P + k],
+           c2 = (double)p.U[(3 * q + 2) * P + k];
+    if (Form<T>::eta && q == 0) {
+      c0 -= (double)p.Z[k]; c1 -= (double)p.Z[P + k]; c2 -= (double)p.Z[2 * P + k];
+    }
+    val[q] = c0 + 2.0 * s3 * xi * c1 + 2.0 * s3 * et * c2;
+  }
+  if (h) h[r] = val[0];
+  double uu = 0.0, vv = 0.0;
+  if (val[0] > g.hd) {
+    uu = val[1] / val[0];
+    vv = val[2] / val[0];
+  }
+  if (u) u[r] = uu;
+  if (v) v[r] = vv;
+}
+
+template <typename T>
+__global__ void k_read_active(Geo g, Ptrs<T> p, int32_t *lev, int32_t *ii, int32_t *jj, double *coef) {
+  const int n = *p.nleaf;
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  long long k = p.leaves[q];
+  int l, i, j;
+  node_of(g, k, l, i, j);
+  if (lev) lev[q] = l;
+  if (ii) ii[q] = i;
+  if (jj) jj[q] = j;
+  if (coef) {
+    const long long P = g.P;
+    for (int m = 0; m < 9; m++) {
+      double c = (double)p.U[m * P + k];
+      if (Form<T>::eta && m < 3) c -= (double)p.Z[m * P + k];
+      coef[9 * (long long)q + m] = c;
+    }
+  }
+}
+
+// volume: per-block partial sums in a fixed order, then one block sums the
+// partials in a fixed order (deterministic FP64)
+template <typename T>
+__global__ void k_volume_part(Geo g, Ptrs<T> p) {
+  const int n = *p.nleaf;
+  double acc = 0.0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    long long k = p.leaves[q];
+    int l, i, j;
+    node_of(g, k, l, i, j);
+    double h0 = Form<T>::eta ? (double)p.U[k] - (double)p.Z[k] : (double)p.U[k];
+    acc += h0 * (g.dxl[l] * g.dxl[l]);
+  }
+  __shared__ double sh[TPB];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = TPB / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) p.part[blockIdx.x] = sh[0];
+}
+
+static __global__ void k_volume_final(const double *part, int nb, Ctl *c) {
+  __shared__ double sh[TPB];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += TPB) acc += part[b];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = TPB / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) c->volume = sh[0];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+inline unsigned nblk(long long n) { return (unsigned)((n + TPB - 1) / TPB); }
+inline long long lvl(const Geo &g, int l) { return (long long)g.nxl[l] * g.nyl[l]; }
+
+#define MARK(c) \
+  do {          \
+    if (mark) mark(mark_arg, (c)); \
+  } while (0)
+
+template <typename T>
+int Launch<T>::project(const Geo &g, const Ptrs<T> &, const double *vert, T *c0, T *c1x, T *c1y,
+                       cudaStream_t st) {
+  const int L = g.L;
+  k_project<T><<<nblk(lvl(g, L)), TPB, 0, st>>>(vert, g.nxl[L], g.nyl[L], c0, c1x, c1y);
+  return 1;
+}
+
+template <typename T>
+int Launch<T>::load_dem_pyramid(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
+  int n = 0;
+  k_zmax<T><<<152 * 4, TPB, 0, st>>>(g, p);
+  n++;
+  for (int l = g.L - 1; l >= 0; l--, n++) k_encode_z<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+  return n;
+}
+
+template <typename T>
+int Launch<T>::roughness_pyramid(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
+  int n = 0;
+  for (int l = g.L - 1; l >= 0; l--, n++) k_nm_level<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+  return n;
+}
+
+template <typename T>
+int Launch<T>::initial_finest(const Geo &g, const Ptrs<T> &p, int is_eta, cudaStream_t st) {
+  k_initial_finest<T><<<nblk(lvl(g, g.L)), TPB, 0, st>>>(g, p, is_eta);
+  return 1;
+}
+
+template <typename T>
+int Launch<T>::encode_dense_U(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
+  int n = 0;
+  for (int l = g.L - 1; l >= 0; l--, n++) k_encode_dense<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p.U, 9, l);
+  return n;
+}
+
+template <typename T>
+int Launch<T>::eta_rule_leaves(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
+  int n = 0;
+  for (int l = g.L - 1; l >= 0; l--, n++) k_encode_dense<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p.Wn, 3, l);
+  k_eta_rule_leaves<T><<<nblk(g.P), TPB, 0, st>>>(g, p);
+  return n + 1;
+}
+
+template <typename T>
+int Launch<T>::static_flags(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
+  k_static_flags<T><<<nblk(g.P), TPB, 0, st>>>(g, p);
+  return 1;
+}
+
+template <typename T>
+int Launch<T>::closure(const Geo &g, uint8_t *flag, cudaStream_t st) {
+  int n = 0;
+  for (int l = g.L - 1; l >= 1; l--, n++) k_closure<<<nblk(lvl(g, l)), TPB, 0, st>>>(g, flag, l);
+  return n;
+}
+
+template <typename T>
+int Launch<T>::grading_sweep(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
+  int n = 0;
+  for (int l = g.L - 1; l >= 1; l--, n++) k_grading<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+  return n + closure(g, p.flag, st);
+}
+
+template <typename T>
+int Launch<T>::kinds(const Geo &g, const Ptrs<T> &p, const uint8_t *flag, int keep_old, cudaStream_t st) {
+  k_kinds<T><<<nblk(g.P), TPB, 0, st>>>(g, p, flag, keep_old);
+  return 1;
+}
+
+template <typename T>
+int Launch<T>::all_finest(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
+  k_all_finest<T><<<nblk(g.P), TPB, 0, st>>>(g, p);
+  return 1;
+}
+
+template <typename T>
+int Launch<T>::compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
+  const int nb = (int)((g.P + CTILE - 1) / CTILE);
+  k_compact_count<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk);
+  k_compact_scan<<<1, 1024, 0, st>>>(nb, p.blk, p.nleaf);
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk, p.leaves);
+  return 3;
+}
+
+template <typename T>
+int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int decode_only, cudaStream_t st,
+                     void (*mark)(void *, int), void *mark_arg) {
+  int n = 0;
+  const int grid = (int)std::min<long long>(nblk(g.P), 152 * 8);
+  if (!decode_only) {
+    MARK(KC_ENCODE);
+    k_leaf_maxabs<T><<<grid, TPB, 0, st>>>(g, p);
+    n++;
+    for (int l = g.L - 1; l >= 0; l--, n++) k_encode_flow<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+  }
+  if (encode_only) return n;
+  MARK(KC_FLAGS);
+  for (int l = 0; l < g.L; l++, n++) k_predict<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+  n += closure(g, p.flag2, st);
+  n += kinds(g, p, p.flag2, 1, st);
+  MARK(KC_DECODE);
+  k_decode_new<T><<<nblk(g.P), TPB, 0, st>>>(g, p);
+  n++;
+  MARK(KC_COMPACT);
+  n += compact(g, p, st);
+  return n;
+}
+
+template <typename T>
+int Launch<T>::dt_only(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st) {
+  k_leaf_dt<T><<<grid_leaves, TPB, 0, st>>>(g, p);
+  return 1;
+}
+
+template <typename T>
+int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st,
+                    void (*mark)(void *, int), void *mark_arg) {
+  int n = 0;
+  const bool view = (g.mode == MWDG_ADAPTIVE);
+  MARK(KC_DT);
+  k_leaf_dt<T><<<grid_leaves, TPB, 0, st>>>(g, p);
+  MARK(KC_CONTROL);
+  k_begin_step<<<1, 1, 0, st>>>(g, p.ctl);
+  MARK(KC_FRICTION);
+  k_rain_friction<T><<<grid_leaves, TPB, 0, st>>>(g, p);
+  n += 3;
+  for (int stage = 1; stage <= 2; stage++) {
+    const T *X = (stage == 1) ? p.U : p.Ui;
+    T *Wst = (stage == 1) ? p.Wn : p.Wi;
+    MARK(KC_LIMIT);
+    k_leaf_limit<T><<<grid_leaves, TPB, 0, st>>>(g, p, X, Wst);
+    n++;
+    if (view) {
+      MARK(KC_VIEW);
+      for (int l = g.L - 1; l >= 0; l--, n++) k_encode_view<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+    }
+    if (stage == 1) {
+      MARK(KC_UPDATE1);
+      k_leaf_update<T, 1><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui);
+    } else {
+      MARK(KC_UPDATE2);
+      k_leaf_update<T, 2><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U);
+    }
+    n++;
+  }
+  MARK(KC_CONTROL);
+  k_end_step<<<1, 1, 0, st>>>(g, p.ctl);
+  n++;
+  MARK(-1);
+  return n;
+}
+
+template <typename T>
+int Launch<T>::fields(const Geo &g, const Ptrs<T> &p, double *h, double *u, double *v, cudaStream_t st) {
+  k_fields<T><<<nblk(lvl(g, g.L)), TPB, 0, st>>>(g, p, h, u, v);
+  return 1;
+}
+
+template <typename T>
+int Launch<T>::read_active(const Geo &g, const Ptrs<T> &p, int32_t *lev, int32_t *i, int32_t *j,
+                           double *coef, cudaStream_t st) {
+  k_read_active<T><<<nblk(g.P), TPB, 0, st>>>(g, p, lev, i, j, coef);
+  return 1;
+}
+
+template <typename T>
+int Launch<T>::volume(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st) {
+  k_volume_part<T><<<grid_leaves, TPB, 0, st>>>(g, p);
+  k_volume_final<<<1, TPB, 0, st>>>(p.part, grid_leaves, p.ctl);
+  return 2;
+}
+
+#undef MARK
+
+}  // namespace mwdg

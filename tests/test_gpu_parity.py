@@ -1,0 +1,246 @@
+"""GPU (sm_103a) parity against the FP64 CPU oracle, through the C ABI.
+
+FP64 path: every active leaf's nine coefficients within 1e-9 (m, m^2/s) of
+the oracle and identical active-cell sets, step by step.  FP32 free-surface
+path: depth within 1e-3 m of the FP64 oracle and wet-extent CSI >= 0.99.
+Sizes span several blocks with ragged tails; full-size runs (1024 x 1024
+valley, the benchmark workload) are checked on properties that hold at any
+size and on the static active set, which the oracle computes at full size."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2107_02750_gb300 import synth as S
+from util import oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+TOL32_H = 1e-3
+
+
+def gpu_sim(p, precision=0, **over):
+    import paper_2107_02750_gb300 as M
+    return M.solver_from_problem(p, precision=precision, **over)
+
+
+def assert_same_leaves(g, o, tol=TOL64, what=""):
+    lg, ig, jg, cg = g.read_active()
+    lo, io, jo, co = o.leaves()
+    assert len(lg) == len(lo), f"{what}: {len(lg)} active leaves on the GPU, {len(lo)} in the oracle"
+    np.testing.assert_array_equal(lg, lo)
+    np.testing.assert_array_equal(ig, io)
+    np.testing.assert_array_equal(jg, jo)
+    err = np.abs(cg - co).max() if len(cg) else 0.0
+    assert err <= tol, f"{what}: max |GPU - oracle| = {err:.3e}"
+    return err
+
+
+def run_parity(p, nsteps, check_every=1, precision=0):
+    g, o = gpu_sim(p, precision), oracle_sim(p)
+    assert_same_leaves(g, o, what="initial")
+    for k in range(nsteps):
+        dg = g.dg2_step()
+        do = o.step()
+        assert abs(dg - do) <= 1e-12 * max(do, 1e-300), (k, dg, do)
+        if (k + 1) % check_every == 0 or k + 1 == nsteps:
+            assert_same_leaves(g, o, what=f"step {k + 1}")
+    return g, o
+
+
+def test_config1_uniform_dam_break_f64_full_run():
+    """128 x 128 circular dam break to t = 5 s (about 77 steps): lockstep for
+    the first 60 steps, then both run to 5 s (last step clamped)."""
+    p = S.dam_break_circular()
+    g, o = run_parity(p, 60, check_every=10)
+    g.run_to_time(5.0)
+    o.run_to(5.0)
+    t, steps = g.get_time()
+    assert steps == o.steps and abs(t - 5.0) < 1e-12
+    assert_same_leaves(g, o, what="t = 5 s")
+    v = g.get_volume()
+    assert abs(v["volume"] - o.diag()["volume"]) <= 1e-12 * v["volume"]
+    assert v["n_clip"] == 0
+
+
+def test_config1_mra_lossless_at_zero_epsilon():
+    """MRA at L = 7, epsilon = 0: encode then decode keeps every finest
+    coefficient (the GPU gathers scale coefficients, so exactly)."""
+    p = S.dam_break_circular(L=7, eps=0.0, mode=S.ADAPTIVE)
+    g = gpu_sim(p)
+    l0, i0, j0, c0 = g.read_active()
+    g.mra_encode()
+    n = g.mra_adapt(0.0)
+    l1, i1, j1, c1 = g.read_active()
+    assert n == 128 * 128 and (l1 == 7).all()
+    np.testing.assert_array_equal(c1, c0)
+    o = oracle_sim(p)
+    o.adapt()
+    assert_same_leaves(g, o, tol=1e-13, what="after adapt")
+
+
+@pytest.mark.parametrize("islands", [False, True])
+def test_lake_at_rest_uniform_f64(islands):
+    p = S.lake_at_rest(n=48, islands=islands)
+    g, o = run_parity(p, 60, check_every=20)
+    _, _, _, c = g.read_active()
+    assert np.abs(c[:, 3:]).max() <= 1e-12
+
+
+def test_uniform_valley_inflow_rain_f64():
+    p = S.valley(n=96, L=5, mode=S.UNIFORM, peak_Q=120.0, t_peak=100.0)
+    p.rain_rate, p.rain_t_end = 2e-4, 50.0
+    g, o = run_parity(p, 150, check_every=25)
+    vg, vo = g.get_volume(), o.diag()
+    for key in ("volume", "v_in", "v_out", "v_rain"):
+        assert abs(vg[key] - vo[key]) <= 1e-9 * max(1.0, abs(vo[key])), key
+    assert vg["v_in"] > 0
+
+
+def test_static_valley_f64():
+    p = S.valley(n=128, L=7, mode=S.STATIC, eps=1e-3, peak_Q=200.0, t_peak=100.0)
+    g, o = run_parity(p, 120, check_every=20)
+    lev, _, _, _ = g.read_active()
+    assert len(np.unique(lev)) >= 3
+
+
+def test_adaptive_valley_f64():
+    p = S.valley(n=128, L=7, mode=S.ADAPTIVE, eps=1e-3, peak_Q=200.0, t_peak=100.0)
+    g, o = run_parity(p, 120, check_every=5)
+    lev, _, _, c = g.read_active()
+    assert len(np.unique(lev)) >= 3 and len(lev) < 128 * 128
+    assert (c[:, 0] > 1e-3).sum() > 20  # the flood has entered
+
+
+def test_adaptive_lake_at_rest_islands_f64():
+    p = S.lake_at_rest(n=64, L=4, islands=True, mode=S.ADAPTIVE, eps=1e-2)
+    g, o = run_parity(p, 40, check_every=10)
+    _, _, _, c = g.read_active()
+    assert np.abs(c[:, 3:]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("mode", [S.UNIFORM, S.STATIC, S.ADAPTIVE])
+def test_ragged_non_square_grid_f64(mode):
+    """M x N = 25 x 9 coarsest elements at L = 2 (100 x 36 finest): level
+    sizes are not multiples of any block size, and M != N."""
+    base = S.valley(n=128, L=7, mode=mode, peak_Q=100.0, t_peak=60.0)
+    p = S.crop(base, 0, 40, 100, 36, L=2)
+    p.mode = mode
+    run_parity(p, 40, check_every=10)
+
+
+def test_degenerate_grids_f64():
+    # a single element, wet, with friction and walls
+    nv = np.ones((2, 2))
+    p = S.Problem("one", 1, 1, 0, 5.0, np.zeros((2, 2)), 2.0 * nv, 0.5 * nv, np.zeros((2, 2)),
+                  n_manning=0.03)
+    run_parity(p, 10)
+    # a dry domain: nothing moves, dt is dt_max
+    p = S.Problem("dry", 4, 4, 2, 1.0, np.random.default_rng(0).uniform(0, 1, (17, 17)),
+                  np.zeros((17, 17)), np.zeros((17, 17)), np.zeros((17, 17)), mode=S.ADAPTIVE)
+    g, o = run_parity(p, 5)
+    t, _ = g.get_time()
+    assert abs(t - 5 * p.dt_max) < 1e-12
+
+
+def test_invalid_inputs_are_rejected():
+    import paper_2107_02750_gb300 as M
+    with pytest.raises(M.MwdgError) as e:
+        M.Solver(M=1, N=1, L=16, dx=1.0)
+    assert e.value.status == -2
+    s = M.Solver(M=2, N=2, L=2, dx=1.0)
+    z = np.zeros((9, 9))
+    z[3, 3] = np.nan
+    with pytest.raises(M.MwdgError) as e:
+        s.load_dem(z)
+    assert e.value.status == -4
+    with pytest.raises(M.MwdgError) as e:
+        s.dg2_step()
+    assert e.value.status == -6
+
+
+# ---------------------------------------------------------------------------
+# FP32 free-surface path against the FP64 oracle
+# ---------------------------------------------------------------------------
+def _depths_close(g, o, wet=0.01):
+    hg, _, _ = g.read_fields()
+    ho, _, _ = o.fields()
+    err = np.abs(hg - ho).max()
+    _, _, csi = O.extent_scores(hg, ho, wet)
+    return err, csi
+
+
+def test_f32_uniform_dam_break():
+    p = S.dam_break_circular()
+    g, o = gpu_sim(p, precision=1), oracle_sim(p)
+    g.run_to_time(5.0)
+    o.run_to(5.0)
+    err, csi = _depths_close(g, o)
+    assert err <= TOL32_H and csi >= 0.99
+
+
+@pytest.mark.parametrize("mode", [S.STATIC, S.ADAPTIVE])
+def test_f32_valley(mode):
+    p = S.valley(n=128, L=7, mode=mode, eps=1e-3, peak_Q=200.0, t_peak=100.0)
+    g, o = gpu_sim(p, precision=1), oracle_sim(p)
+    g.run_to_time(80.0)
+    o.run_to(80.0)
+    err, csi = _depths_close(g, o)
+    assert err <= TOL32_H, err
+    assert csi >= 0.99, csi
+
+
+def test_f32_lake_at_rest_islands_stays_at_rest():
+    p = S.lake_at_rest(n=64, islands=True)
+    g = gpu_sim(p, precision=1)
+    g.run_steps(500)
+    _, u, v = g.read_fields()
+    assert np.abs(u).max() < 1e-4 and np.abs(v).max() < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Full size: the 1024 x 1024 valley of the benchmark
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def valley_full():
+    return S.valley(n=1024, L=10, mode=S.STATIC, eps=1e-3)
+
+
+def test_full_size_static_active_set_matches_oracle(valley_full):
+    p = valley_full
+    g = gpu_sim(p)
+    o = oracle_sim(p)
+    lg, ig, jg, _ = g.read_active()
+    lo, io, jo, _ = o.leaves()
+    np.testing.assert_array_equal(lg, lo)
+    np.testing.assert_array_equal(ig, io)
+    np.testing.assert_array_equal(jg, jo)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_adaptive_mass_budget(valley_full, precision):
+    p = S.valley(n=1024, L=10, mode=S.ADAPTIVE, eps=1e-3, peak_Q=400.0, t_peak=120.0)
+    g = gpu_sim(p, precision=precision)
+    v0 = g.get_volume()["volume"]
+    g.run_to_time(90.0)
+    v = g.get_volume()
+    budget = v0 + v["v_in"] - v["v_out"] + v["v_rain"] + v["v_clip"]
+    tol = 1e-9 if precision == 0 else 1e-4
+    assert abs(v["volume"] - budget) <= tol * max(1.0, v["volume"]), (v, budget)
+    assert v["v_in"] > 0
+    # active leaves tile the domain
+    lev, i, j, _ = g.read_active()
+    area = np.sum(4.0 ** (10 - lev.astype(np.float64)))
+    assert area == 1024 * 1024
+
+
+def test_full_size_f32_matches_f64_gpu():
+    p = S.valley(n=1024, L=10, mode=S.ADAPTIVE, eps=1e-3, peak_Q=400.0, t_peak=120.0)
+    a, b = gpu_sim(p, precision=0), gpu_sim(p, precision=1)
+    a.run_to_time(60.0)
+    b.run_to_time(60.0)
+    ha, _, _ = a.read_fields()
+    hb, _, _ = b.read_fields()
+    assert np.abs(ha - hb).max() <= TOL32_H
+    _, _, csi = O.extent_scores(hb, ha)
+    assert csi >= 0.99
