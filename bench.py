@@ -1,0 +1,359 @@
+"""Benchmark: MWDG2 active-cell updates/s on the 1024 x 1024 fractal-valley
+workload (dx = 10 m, L = 10, epsilon = 1e-3, Manning n = 0.035, triangular
+inflow peaking at 400 m^3/s at 30 min on the west edge), FP32 free-surface
+path, with the FP64 path, the FP32-vs-FP64 depth error and CSI, the
+roofline of the dominant kernel and the CPU oracle beside it.
+
+One step = one full MWDG2 time step (MRA encode, threshold, regularise,
+decode, CFL dt, friction, both RK2 stages) on the state reached after a
+spin-up of `--spinup` simulated seconds; one update = one active leaf
+advanced one step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs one independent replica per GPU (launched with
+torch.distributed.run); the per-replica work is fixed (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MWDG2/DG2 active-cell updates/s & % HBM roofline, FP32 vs FP64 at <=1e-3 m"
+UNIT = "active-cell updates/s"
+WORKLOAD = "MWDG2 1024x1024 fractal valley, dx=10 m, L=10, eps=1e-3, n=0.035, 400 m3/s inflow"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--spinup", type=float, default=1800.0, help="simulated seconds before timing")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def cpu_baseline(n_full, budget_s=15.0):
+    """The FP64 oracle, as it stands, single-threaded on this host: a 256 x 256
+    crop (L = 8) of the same valley through the inflow, MWDG2 from t = 0,
+    stepping until about budget_s seconds of CPU time have passed."""
+    import oracle as O
+    from paper_2107_02750_gb300 import synth as S
+    full = S.valley(n=n_full)
+    p = S.crop(full, 0, n_full // 2 - 128, 256, 256, L=8)
+    s = O.Sim(M=p.M, N=p.N, L=p.L, R=p.dx, mode=p.mode, eps=p.eps, bc=p.bc,
+              inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1,
+              limiter=p.limiter, dt_max=p.dt_max)
+    s.load_dem(p.z_vert)
+    s.load_roughness(p.n_cell())
+    s.load_initial(p.h_vert, p.qx_vert, p.qy_vert, p.is_eta)
+    s.set_inflow(p.inflow_t, p.inflow_Q)
+    s.init_grid()
+    t0 = time.perf_counter()
+    upd = 0
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        s.step()
+        upd += len(s.leaves()[0])
+        steps += 1
+    el = time.perf_counter() - t0
+    return {"value": upd / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, 256x256 crop (L=8) of the valley through the inflow, MWDG2 from t=0, "
+                      f"{steps} steps ({upd} updates) in {el:.1f} s on 1 host thread"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def make_solver(p, precision, stream):
+    import paper_2107_02750_gb300 as M
+    return M.solver_from_problem(p, precision=precision, stream=stream)
+
+
+def timed_steps(solver, K, W, flush, stream, prof=False):
+    """W untimed steps, then K steps each bracketed by CUDA events on the
+    solver's stream with an L2 flush before each; returns (ms list, updates
+    list, launches in the timed region, kernel times)."""
+    import torch
+    for _ in range(W):
+        solver.run_steps(1)
+    torch.cuda.synchronize()
+    ms, upd = [], []
+    l0 = solver.launch_count()
+    if prof:
+        solver.profile(True)
+    evs = []
+    for _ in range(K):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        solver.run_steps(1)
+        b.record(stream)
+        evs.append((a, b))
+        b.synchronize()
+        upd.append(solver.n_active())
+    torch.cuda.synchronize()
+    for a, b in evs:
+        ms.append(a.elapsed_time(b))
+    kt = solver.kernel_times() if prof else {}
+    if prof:
+        solver.profile(False)
+    launches = solver.launch_count() - l0
+    return ms, upd, launches, kt
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import paper_2107_02750_gb300 as M
+    from paper_2107_02750_gb300 import synth as S
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+    p = S.valley(n=args.n, L=args.n.bit_length() - 1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # FP32 free-surface path (headline)
+    s32 = make_solver(p, M.F32, sptr)
+    s32.run_to_time(args.spinup)
+    t_spin, _ = s32.get_time()
+    ckpt = s32.save_state()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        ms, upd, launches, kt = timed_steps(s32, args.steps, args.warmup, flush, stream, prof=True)
+    total_ms = sum(ms)
+    updates = sum(upd)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([float(updates)], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+        updates_all = float(u.item())
+    else:
+        updates_all = float(updates)
+    value = updates_all / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel
+    peak_gbs, peak_kind = peaks()
+    dom = max(kt.items(), key=lambda kv: kv[1][0]) if kt else ("?", (0.0, 0))
+    dom_name, (dom_ms, dom_n) = dom
+    mean_leaves = float(np.mean(upd))
+    bpl = kernel_bytes_per_leaf(dom_name, 4)
+    achieved = (bpl * mean_leaves) / (dom_ms / max(dom_n, 1) * 1e-3) / 1e9 if dom_n else None
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs,
+                "unit": "GB/s", "frac": (achieved / peak_gbs) if achieved else None,
+                "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_leaf": bpl, "share_of_step": dom_ms / max(sum(v[0] for v in kt.values()), 1e-9),
+                "kernel_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in kt.items() if v[1]}}
+
+    # end to end through the public API: resume from a host checkpoint in
+    # pinned memory, K steps, depth and velocity maps back to the host
+    pinned = torch.from_numpy(ckpt).pin_memory()
+    hbuf = [torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory() for _ in range(3)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s32.load_state(pinned)
+    n_e2e = 0
+    for _ in range(args.steps):
+        s32.run_steps(1)
+        n_e2e += s32.n_active()
+    import ctypes as C
+    st = s32._lib.mwdg_read_fields(s32._h, *(C.cast(C.c_void_p(b.data_ptr()), C.POINTER(C.c_double)) for b in hbuf))
+    if st:
+        raise RuntimeError("mwdg_read_fields failed")
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": n_e2e / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(ckpt.nbytes // args.steps),
+           "d2h_bytes_per_step": int(3 * p.nx * p.ny * 8 // args.steps),
+           "what": "mwdg_load_state from pinned host checkpoint + K x mwdg_dg2_step + mwdg_read_fields to pinned host"}
+
+    out = {"value": value, "ms_per_step": total_ms / len(ms), "updates": updates_all,
+           "mean_active": mean_leaves, "roofline": roofline, "clocks": clk.summary(), "e2e": e2e,
+           "gpu_launches": int(launches) * world, "t_spinup": t_spin}
+
+    # FP64 path and FP32-vs-FP64 accuracy at the same simulated time
+    if not args.no_fp64 and rank == 0:
+        s64 = make_solver(p, M.F64, sptr)
+        s64.run_to_time(args.spinup)
+        ms64, upd64, _, _ = timed_steps(s64, max(4, args.steps // 4), 2, flush, stream)
+        out["fp64"] = {"value": sum(upd64) / (sum(ms64) * 1e-3), "unit": UNIT,
+                       "ms_per_step": sum(ms64) / len(ms64), "dtype": "f64"}
+        tcmp = max(s64.get_time()[0], s32.get_time()[0]) + 1.0
+        s32.run_to_time(tcmp)
+        s64.run_to_time(tcmp)
+        h32, _, _ = s32.read_fields()
+        h64, _, _ = s64.read_fields()
+        wet32, wet64 = h32 > 0.01, h64 > 0.01
+        A = int(np.sum(wet32 & wet64)); B = int(np.sum(wet32 & ~wet64)); Cc = int(np.sum(~wet32 & wet64))
+        out["accuracy_f32_vs_f64"] = {"t": tcmp, "max_depth_err_m": float(np.abs(h32 - h64).max()),
+                                      "csi": A / max(A + B + Cc, 1)}
+    return out
+
+
+def reference_arm(args):
+    """The reference arm is the FP64 CPU oracle as it stands (single host
+    thread): W untimed then K timed MWDG2 steps on a 256 x 256 crop (L = 8) of
+    the same valley through the inflow, from t = 0."""
+    import oracle as O
+    from paper_2107_02750_gb300 import synth as S
+    full = S.valley(n=args.n, L=args.n.bit_length() - 1)
+    p = S.crop(full, 0, args.n // 2 - 128, 256, 256, L=8)
+    s = O.Sim(M=p.M, N=p.N, L=p.L, R=p.dx, mode=p.mode, eps=p.eps, bc=p.bc,
+              inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1,
+              limiter=p.limiter, dt_max=p.dt_max)
+    s.load_dem(p.z_vert)
+    s.load_roughness(p.n_cell())
+    s.load_initial(p.h_vert, p.qx_vert, p.qy_vert, p.is_eta)
+    s.set_inflow(p.inflow_t, p.inflow_Q)
+    s.init_grid()
+    for _ in range(args.warmup):
+        s.step()
+    upd = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+        upd += len(s.leaves()[0])
+    el = time.perf_counter() - t0
+    v = upd / el
+    sample = (f"FP64 oracle on 1 host thread: {args.steps} MWDG2 steps ({upd} updates) of a 256x256 crop "
+              f"(L=8) of the valley through the inflow, from t=0, in {el:.1f} s")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def kernel_bytes_per_leaf(name, ts):
+    """Algorithmic HBM bytes per active leaf of each kernel class (values of
+    ts bytes; neighbour reads served from L2 are not counted)."""
+    vals = {
+        "dg2_update_stage1": 9 + 3 + 9 + 1 + 9,      # F, Ze, Wn, z0 read; Ui written
+        "dg2_update_stage2": 9 + 3 + 9 + 9 + 1 + 9,  # F, Ze, Wi, Wn, z0 read; U written
+        "limit": 9 + 3 + 9 + 9 + 3,                  # X, Z read; Wst, F, Ze written
+        "friction": 9 + 1 + 7,                       # U, n read; q (6) + eta0 written
+        "dt_reduce": 4,
+        "mra_encode": 9 + 3,
+    }
+    return vals.get(name, 0) * ts + (4 if name.startswith("dg2") or name == "limit" else 0)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(reference_arm(args)))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_gpu(args, rank, world)
+    if rank == 0:
+        cb = None if args.no_cpu else cpu_baseline(args.n)
+        line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "L": args.n.bit_length() - 1,
+                           "eps": 1e-3, "spinup_s": out["t_spinup"], "mean_active_leaves": out["mean_active"],
+                           "l2": "flushed (256 MB write) before every timed step",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "roofline": out["roofline"], "cpu_baseline": cb, "e2e": out["e2e"], "clocks": out["clocks"],
+                "gpu_launches": out["gpu_launches"]}
+        for k in ("fp64", "accuracy_f32_vs_f64"):
+            if k in out:
+                line[k] = out[k]
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

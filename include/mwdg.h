@@ -174,6 +174,17 @@ MWDG_API mwdg_status mwdg_get_time(mwdg_ctx *ctx, double *t, int64_t *steps);
 MWDG_API mwdg_status mwdg_get_volume(mwdg_ctx *ctx, double *V, double *V_in, double *V_out, double *V_rain,
                             double *V_clip, int64_t *n_clip);
 
+/* Checkpoint / resume.  The state is the node kinds (the active tree), the
+ * coefficients of every node, the static beds and roughness it was built
+ * with, the simulated time and the mass-budget counters; a context with the
+ * same parameters can resume from it.  mwdg_state_bytes gives the buffer
+ * size; save writes into a host buffer of at least that size (synchronises);
+ * load reads one (MWDG_ERR_DIMS if it belongs to another grid or precision,
+ * MWDG_ERR_ARG if the buffer is not a state of this library). */
+MWDG_API mwdg_status mwdg_state_bytes(mwdg_ctx *ctx, int64_t *bytes);
+MWDG_API mwdg_status mwdg_save_state(mwdg_ctx *ctx, void *buf, int64_t cap);
+MWDG_API mwdg_status mwdg_load_state(mwdg_ctx *ctx, const void *buf, int64_t size);
+
 /* Per-kernel timing with CUDA events on the context stream: enable != 0
  * starts recording (and clears the totals).  mwdg_kernel_times fills up to
  * cap entries of names (static strings), total milliseconds and launch

@@ -661,6 +661,12 @@ void orc_adapt(orc_sim *s) {
 /* ------------------------------------------------------------------------ */
 /* DG2 operator pieces (Sect. 2.1.1)                                         */
 /* ------------------------------------------------------------------------ */
+static double minmod2(double a, double b) {
+  if (a > 0.0 && b > 0.0) return fmin(a, b);
+  if (a < 0.0 && b < 0.0) return fmax(a, b);
+  return 0.0;
+}
+
 static double minmod3(double a, double b, double c) {
   if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
   if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
@@ -669,13 +675,23 @@ static double minmod3(double a, double b, double c) {
 
 /* Revision of one side's limit at an interface (wet/dry, well-balanced):
  * hydrostatic reconstruction with the interface bed z_f = max(z_L, z_R):
- * h* = max(0, eta - z_f), velocities from the unrevised limit (zero when the
- * limit is not wetter than h_dry), bed seen by the source term
- * z' = min(z_f, eta). */
+ * h* = eta - z_f where that exceeds h_dry, else 0 (a face not wetter than
+ * h_dry is dry for the flux and the source alike); the bed seen by the
+ * source term is z' = z_f on a wet face and eta on a dry one, so that
+ * h* + z' = eta and the pressure and bed-slope terms cancel at rest;
+ * velocities come from the unrevised limit (zero when it is not wetter
+ * than h_dry). */
 static void revise(double h, double qx, double qy, double z, double zf, double hd,
                    double *hs, double *u, double *v, double *zr) {
   double eta = h + z;
-  *hs = fmax(0.0, eta - zf);
+  double d = eta - zf;
+  if (d > hd) {
+    *hs = d;
+    *zr = zf;
+  } else {
+    *hs = 0.0;
+    *zr = eta;
+  }
   if (h > hd) {
     *u = qx / h;
     *v = qy / h;
@@ -683,7 +699,6 @@ static void revise(double h, double qx, double qy, double z, double zf, double h
     *u = 0.0;
     *v = 0.0;
   }
-  *zr = fmin(zf, eta);
 }
 
 /* HLL flux in the interface-normal frame (un normal, ut tangential);
@@ -840,17 +855,21 @@ static void post_stage(orc_sim *s, double *w, double area) {
  *     when its average is not wetter than h_dry, when the depth limit of
  *     its plane at any interface centre is not wetter than h_dry, or when a
  *     flat free surface h0 + z0 would leave any interface centre of its
- *     planar bed not wetter than h_dry.  Such a leaf stores a flat free
- *     surface over its planar bed (h1 = -z1, discharge slopes zero) and is
- *     seen by the fluxes as flat depth over a flat bed (z0, 0, 0), so its
- *     interface depths are its average and a shoreline leaf at rest stays
- *     at rest.  The paper delegates its wet/dry treatment to cited works;
+ *     planar bed not wetter than h_dry (water shallower than the leaf's own
+ *     bed relief, e.g. a rain film on a slope).  Such a leaf stores a flat
+ *     free surface over its planar bed (h1 = -z1, discharge slopes zero)
+ *     and is seen by the fluxes as flat depth over a flat bed (z0, 0, 0), so
+ *     its interface depths are its average and a shoreline leaf at rest
+ *     stays at rest.  The paper delegates its wet/dry treatment to cited works;
  *     this is the reading used here.
  * (2) Otherwise, the slope limiter (the paper names none; the benchmark spec asks
  *     for one): minmod on the face-limit offsets sqrt3*v1 of eta, qx and qy
- *     against the differences of neighbour averages, per direction, only for
- *     leaves on the finest level whose two neighbours in that direction are
- *     finest-level leaves and wet. */
+ *     against the differences of the averages of the same-level leaf
+ *     neighbours, per direction (two-argument minmod against the one
+ *     difference where only one such neighbour exists: domain edges and
+ *     level transitions); eta only where the leaf and its neighbours are
+ *     wet, the discharges also next to dry neighbours (whose discharge is
+ *     zero), so that slopes at wet/dry fronts and edges stay bounded. */
 static void limit_leaf(const orc_sim *s, double *const *X, int l, int i, int j, const double *w_in,
                        double *w_st, double *w_fx, double *ze) {
   double s3 = S3();
@@ -876,16 +895,18 @@ static void limit_leaf(const orc_sim *s, double *const *X, int l, int i, int j, 
     return;
   }
   for (int m = 0; m < 9; m++) w_fx[m] = w_in[m];
-  if (!s->p.limiter || l != s->L) return;
+  if (!s->p.limiter) return;
   for (int dir = 0; dir < 2; dir++) {
     int ia = i + (dir == 0), ja = j + (dir == 1), ib = i - (dir == 0), jb = j - (dir == 1);
-    if (!in_dom(s, l, ia, ja) || !in_dom(s, l, ib, jb)) continue;
-    size_t ka = id(s, l, ia, ja), kb = id(s, l, ib, jb);
-    if (s->kind[l][ka] != K_LEAF || s->kind[l][kb] != K_LEAF) continue;
+    int hasA = in_dom(s, l, ia, ja) && s->kind[l][id(s, l, ia, ja)] == K_LEAF;
+    int hasB = in_dom(s, l, ib, jb) && s->kind[l][id(s, l, ib, jb)] == K_LEAF;
+    if (!hasA && !hasB) continue;
+    size_t ka = hasA ? id(s, l, ia, ja) : kc, kb = hasB ? id(s, l, ib, jb) : kc;
     double hC = X[l][kc], hA = X[l][ka], hB = X[l][kb];
-    if (!(hC > hd && hA > hd && hB > hd)) continue;
+    int wet = (hC > hd) && (!hasA || hA > hd) && (!hasB || hB > hd);
     int cs = 1 + dir; /* slope coefficient index */
     for (int v = 0; v < 3; v++) {
+      if (v == 0 && !wet) continue;
       double a0, aC, aB, slope, zs = s->z[l][cs * n + kc];
       if (v == 0) {
         aC = hC + s->z[l][kc];
@@ -898,8 +919,10 @@ static void limit_leaf(const orc_sim *s, double *const *X, int l, int i, int j, 
         aB = X[l][3 * v * n + kb];
         slope = w_in[3 * v + cs];
       }
-      double a = s3 * slope, b = a0 - aC, c = aC - aB;
-      double mm = minmod3(a, b, c);
+      double a = s3 * slope, mm;
+      if (hasA && hasB) mm = minmod3(a, a0 - aC, aC - aB);
+      else if (hasA) mm = minmod2(a, a0 - aC);
+      else mm = minmod2(a, aC - aB);
       if (mm != a) {
         double ns = mm / s3;
         if (v == 0) w_st[cs] = ns - zs;

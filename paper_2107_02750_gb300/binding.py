@@ -20,7 +20,8 @@ EXPORTS = (
     "mwdg_mra_encode", "mwdg_mra_adapt", "mwdg_dg2_step", "mwdg_run_steps", "mwdg_run_to_time",
     "mwdg_read_fields", "mwdg_read_fields_dev", "mwdg_read_active", "mwdg_get_time",
     "mwdg_get_volume", "mwdg_profile", "mwdg_kernel_times", "mwdg_launch_count",
-    "mwdg_last_error", "mwdg_status_string",
+    "mwdg_last_error", "mwdg_status_string", "mwdg_state_bytes", "mwdg_save_state",
+    "mwdg_load_state",
 )
 
 
@@ -77,6 +78,9 @@ def lib(build: bool = True):
         "mwdg_profile": [vp, C.c_int32],
         "mwdg_kernel_times": [vp, C.POINTER(C.c_char_p), dp, lp, C.c_int32, ip],
         "mwdg_launch_count": [vp, lp],
+        "mwdg_state_bytes": [vp, lp],
+        "mwdg_save_state": [vp, vp, C.c_int64],
+        "mwdg_load_state": [vp, vp, C.c_int64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -250,6 +254,26 @@ class Solver:
                                              cnt.ctypes.data_as(C.POINTER(C.c_int64)), cap,
                                              C.byref(n)), "mwdg_kernel_times")
         return {names[k].decode(): (float(ms[k]), int(cnt[k])) for k in range(n.value)}
+
+    def state_bytes(self) -> int:
+        n = C.c_int64()
+        self._ck(self._lib.mwdg_state_bytes(self._h, C.byref(n)), "mwdg_state_bytes")
+        return n.value
+
+    def save_state(self, buf=None):
+        """checkpoint into a host buffer (numpy uint8, or a pinned torch uint8
+        tensor); returns the buffer"""
+        n = self.state_bytes()
+        if buf is None:
+            buf = np.empty(n, np.uint8)
+        ptr = buf.ctypes.data if isinstance(buf, np.ndarray) else buf.data_ptr()
+        self._ck(self._lib.mwdg_save_state(self._h, C.c_void_p(ptr), n), "mwdg_save_state")
+        return buf
+
+    def load_state(self, buf):
+        ptr = buf.ctypes.data if isinstance(buf, np.ndarray) else buf.data_ptr()
+        n = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel()
+        self._ck(self._lib.mwdg_load_state(self._h, C.c_void_p(ptr), n), "mwdg_load_state")
 
     def launch_count(self) -> int:
         n = C.c_int64()

@@ -39,8 +39,10 @@ __device__ __forceinline__ T face_value(T c0, T c1x, T c1y, int f) {
 
 // One side of an interface after the wet/dry, well-balanced revision:
 // interface bed zf = max of the two sides' beds, revised depth
-// h* = max(0, eta - zf), velocities from the unrevised limit (zero when it is
-// not wetter than h_dry), and the bed the source term sees, min(zf, eta).
+// h* = eta - zf where that exceeds h_dry, else 0 (dry for flux and source
+// alike), the bed the source term sees (zf on a wet face, eta on a dry one,
+// so h* + z' = eta), and velocities from the unrevised limit (zero when it is
+// not wetter than h_dry).
 template <typename T>
 struct Side {
   T hs, u, v, zr;
@@ -51,7 +53,14 @@ template <typename T>
 __device__ __forceinline__ Side<T> revise_h(T h, T qx, T qy, T z, T zf, T hd) {
   Side<T> s;
   T eta = h + z;
-  s.hs = tmax(T(0), eta - zf);
+  T d = eta - zf;
+  if (d > hd) {
+    s.hs = d;
+    s.zr = zf;
+  } else {
+    s.hs = T(0);
+    s.zr = eta;
+  }
   if (h > hd) {
     s.u = qx / h;
     s.v = qy / h;
@@ -59,7 +68,6 @@ __device__ __forceinline__ Side<T> revise_h(T h, T qx, T qy, T z, T zf, T hd) {
     s.u = T(0);
     s.v = T(0);
   }
-  s.zr = tmin(zf, eta);
   return s;
 }
 
@@ -68,7 +76,14 @@ template <typename T>
 __device__ __forceinline__ Side<T> revise_eta(T eta, T qx, T qy, T z, T zf, T hd) {
   Side<T> s;
   T h = eta - z;
-  s.hs = tmax(T(0), eta - zf);
+  T d = eta - zf;
+  if (d > hd) {
+    s.hs = d;
+    s.zr = zf;
+  } else {
+    s.hs = T(0);
+    s.zr = eta;
+  }
   if (h > hd) {
     s.u = qx / h;
     s.v = qy / h;
@@ -76,7 +91,6 @@ __device__ __forceinline__ Side<T> revise_eta(T eta, T qx, T qy, T z, T zf, T hd
     s.u = T(0);
     s.v = T(0);
   }
-  s.zr = tmin(zf, eta);
   return s;
 }
 
@@ -118,6 +132,13 @@ __device__ __forceinline__ void hll(T hL, T unL, T utL, T hR, T unR, T utR, T g,
     F[1] = (sR * FL1 - sL * FR1 + sL * sR * (UR1 - UL1)) / den;
     F[2] = (sR * FL2 - sL * FR2 + sL * sR * (UR2 - UL2)) / den;
   }
+}
+
+template <typename T>
+__device__ __forceinline__ T minmod2(T a, T b) {
+  if (a > T(0) && b > T(0)) return tmin(a, b);
+  if (a < T(0) && b < T(0)) return tmax(a, b);
+  return T(0);
 }
 
 template <typename T>

@@ -699,6 +699,107 @@ mwdg_status mwdg_get_volume(mwdg_ctx *c, double *V, double *V_in, double *V_out,
   return MWDG_OK;
 }
 
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t version, prec, L, M, N, mode;
+  int64_t P;
+  Ctl ctl;
+};
+constexpr char kMagic[8] = {'M', 'W', 'D', 'G', 'S', 'T', '0', '1'};
+
+size_t state_bytes(const mwdg_ctx *c) {
+  const size_t P = (size_t)c->g.P, ts = (c->g.prec == MWDG_F64) ? 8 : 4;
+  return sizeof(StateHeader) + P + 9 * P * ts + 3 * P * ts + P * ts + P * 8;
+}
+}  // namespace
+
+mwdg_status mwdg_state_bytes(mwdg_ctx *c, int64_t *bytes) {
+  LIVE(c);
+  if (!bytes) return fail(c, MWDG_ERR_ARG, "bytes is NULL");
+  *bytes = (int64_t)state_bytes(c);
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_save_state(mwdg_ctx *c, void *buf, int64_t cap) {
+  LIVE(c);
+  if (!buf) return fail(c, MWDG_ERR_ARG, "buffer is NULL");
+  if (cap < (int64_t)state_bytes(c)) return fail(c, MWDG_ERR_CAPACITY, "state buffer too small");
+  const Geo &g = c->g;
+  StateHeader h{};
+  memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.prec = g.prec;
+  h.L = g.L;
+  h.M = g.M;
+  h.N = g.N;
+  h.mode = g.mode;
+  h.P = g.P;
+  mwdg_status s = read_ctl(c, &h.ctl);
+  if (s) return s;
+  char *b = (char *)buf;
+  memcpy(b, &h, sizeof h);
+  b += sizeof h;
+  const size_t P = (size_t)g.P, ts = (g.prec == MWDG_F64) ? 8 : 4;
+  const void *kind = (g.prec == MWDG_F64) ? (void *)c->pd.kind : (void *)c->pf.kind;
+  const void *U = (g.prec == MWDG_F64) ? (void *)c->pd.U : (void *)c->pf.U;
+  const void *Z = (g.prec == MWDG_F64) ? (void *)c->pd.Z : (void *)c->pf.Z;
+  const void *NM = (g.prec == MWDG_F64) ? (void *)c->pd.NM : (void *)c->pf.NM;
+  const void *DZ = (g.prec == MWDG_F64) ? (void *)c->pd.DZ : (void *)c->pf.DZ;
+  CK(cudaMemcpyAsync(b, kind, P, cudaMemcpyDeviceToHost, c->st));
+  b += P;
+  CK(cudaMemcpyAsync(b, U, 9 * P * ts, cudaMemcpyDeviceToHost, c->st));
+  b += 9 * P * ts;
+  CK(cudaMemcpyAsync(b, Z, 3 * P * ts, cudaMemcpyDeviceToHost, c->st));
+  b += 3 * P * ts;
+  CK(cudaMemcpyAsync(b, NM, P * ts, cudaMemcpyDeviceToHost, c->st));
+  b += P * ts;
+  CK(cudaMemcpyAsync(b, DZ, P * 8, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_load_state(mwdg_ctx *c, const void *buf, int64_t size) {
+  LIVE(c);
+  if (!buf || size < (int64_t)sizeof(StateHeader)) return fail(c, MWDG_ERR_ARG, "not a state buffer");
+  const Geo &g = c->g;
+  StateHeader h;
+  memcpy(&h, buf, sizeof h);
+  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return fail(c, MWDG_ERR_ARG, "not a state buffer");
+  if (h.prec != g.prec || h.L != g.L || h.M != g.M || h.N != g.N || h.P != g.P || h.mode != g.mode)
+    return fail(c, MWDG_ERR_DIMS, "state belongs to another grid or precision");
+  if (size < (int64_t)state_bytes(c)) return fail(c, MWDG_ERR_ARG, "state buffer truncated");
+  const char *b = (const char *)buf + sizeof h;
+  const size_t P = (size_t)g.P, ts = (g.prec == MWDG_F64) ? 8 : 4;
+  void *kind = (g.prec == MWDG_F64) ? (void *)c->pd.kind : (void *)c->pf.kind;
+  void *U = (g.prec == MWDG_F64) ? (void *)c->pd.U : (void *)c->pf.U;
+  void *Z = (g.prec == MWDG_F64) ? (void *)c->pd.Z : (void *)c->pf.Z;
+  void *NM = (g.prec == MWDG_F64) ? (void *)c->pd.NM : (void *)c->pf.NM;
+  void *DZ = (g.prec == MWDG_F64) ? (void *)c->pd.DZ : (void *)c->pf.DZ;
+  CK(cudaMemcpyAsync(kind, b, P, cudaMemcpyHostToDevice, c->st));
+  b += P;
+  CK(cudaMemcpyAsync(U, b, 9 * P * ts, cudaMemcpyHostToDevice, c->st));
+  b += 9 * P * ts;
+  CK(cudaMemcpyAsync(Z, b, 3 * P * ts, cudaMemcpyHostToDevice, c->st));
+  b += 3 * P * ts;
+  CK(cudaMemcpyAsync(NM, b, P * ts, cudaMemcpyHostToDevice, c->st));
+  b += P * ts;
+  CK(cudaMemcpyAsync(DZ, b, P * 8, cudaMemcpyHostToDevice, c->st));
+  Ctl ctl = h.ctl;
+  ctl.t_end = 1e300;
+  CK(cudaMemcpyAsync(c->ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, c->st));
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::compact(g, p, c->st);
+  });
+  CHECK_LAUNCH();
+  CK(cudaStreamSynchronize(c->st));
+  c->dem = c->initial = true;
+  c->stepped = true;
+  c->encoded = false;
+  return MWDG_OK;
+}
+
 mwdg_status mwdg_profile(mwdg_ctx *c, int32_t enable) {
   LIVE(c);
   mwdg_status s = flush_marks(c);

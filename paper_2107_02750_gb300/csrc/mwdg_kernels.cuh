@@ -441,7 +441,8 @@ __global__ void k_predict(Geo g, Ptrs<T> p, int l) {
 }
 
 // new leaves that were below an old leaf take the prolongation of its plane
-// (Eq. 10 with zero details, one level at a time)
+// (Eq. 10 with zero details, one level at a time); the flow is prolonged in
+// depth form in both precisions
 template <typename T>
 __global__ void k_decode_new(Geo g, Ptrs<T> p) {
   long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -462,11 +463,17 @@ __global__ void k_decode_new(Geo g, Ptrs<T> p) {
   for (int v = 0; v < 3; v++) {
     T s[3];
     for (int m = 0; m < 3; m++) s[m] = p.U[(3 * v + m) * P + ka];
+    // the free-surface form prolongs the depth h = eta - z of the old leaf
+    // and adds the new leaf's own bed, as the depth form does implicitly
+    if (Form<T>::eta && v == 0)
+      for (int m = 0; m < 3; m++) s[m] = s[m] - p.Z[m * P + ka];
     for (int q = d - 1; q >= 0; q--) {
       T o[3];
       prolong3(s[0], s[1], s[2], path[q], o);
       s[0] = o[0]; s[1] = o[1]; s[2] = o[2];
     }
+    if (Form<T>::eta && v == 0)
+      for (int m = 0; m < 3; m++) s[m] = s[m] + p.Z[m * P + k];
     for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = s[m];
   }
 }
@@ -566,11 +573,13 @@ __global__ void k_rain_friction(Geo g, Ptrs<T> p) {
 // Stage-input limiting of each leaf, giving the stored view Wst (used by
 // the RK2 combination) and the flux view F with its bed planes Ze.
 // Partially wet leaves (average, any interface depth of the plane, or any
-// interface depth under a flat free surface h0 + z0, not wetter than h_dry)
-// drop to first order: stored as a flat free surface over the planar bed,
-// seen by the fluxes as flat depth over a flat bed.  Other leaves on the
-// finest level with wet finest-level neighbours on both sides get the minmod
-// limiter on eta, qx, qy per direction.
+// interface depth under a flat free surface h0 + z0, not wetter than h_dry:
+// water shallower than the leaf's own bed relief) drop to first order: stored as a flat free surface over the planar bed,
+// seen by the fluxes as flat depth over a flat bed.  Other leaves get the
+// minmod limiter per direction against their same-level leaf neighbours
+// (two-argument minmod where only one exists): on qx and qy always (a dry
+// neighbour has zero discharge), on eta where the leaf and its neighbours
+// are wet.
 template <typename T>
 __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   const long long P = g.P;
@@ -620,18 +629,20 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
       ze[0] = zp[0]; ze[1] = zp[1]; ze[2] = zp[2];
       int l, i, j;
       node_of(g, k, l, i, j);
-      if (g.limiter && l == g.L) {
+      if (g.limiter) {
         for (int dir = 0; dir < 2; dir++) {
-          int ia = i + (dir == 0), ja = j + (dir == 1), ib = i - (dir == 0), jb = j - (dir == 1);
-          if (ib < 0 || jb < 0 || ia >= g.nxl[l] || ja >= g.nyl[l]) continue;
-          long long ka = nid(g, l, ia, ja), kb = nid(g, l, ib, jb);
-          if (p.kind[ka] != K_LEAF || p.kind[kb] != K_LEAF) continue;
+          const int ia = i + (dir == 0), ja = j + (dir == 1), ib = i - (dir == 0), jb = j - (dir == 1);
+          const bool hasA = ia < g.nxl[l] && ja < g.nyl[l] && p.kind[nid(g, l, ia, ja)] == K_LEAF;
+          const bool hasB = ib >= 0 && jb >= 0 && p.kind[nid(g, l, ib, jb)] == K_LEAF;
+          if (!hasA && !hasB) continue;
+          const long long ka = hasA ? nid(g, l, ia, ja) : k, kb = hasB ? nid(g, l, ib, jb) : k;
           T hC = h0;
           T hA = Form<T>::eta ? X[ka] - p.Z[ka] : X[ka];
           T hB = Form<T>::eta ? X[kb] - p.Z[kb] : X[kb];
-          if (!(hC > hd && hA > hd && hB > hd)) continue;
+          const bool wet = (hC > hd) && (!hasA || hA > hd) && (!hasB || hB > hd);
           const int cs = 1 + dir;
           for (int v = 0; v < 3; v++) {
+            if (v == 0 && !wet) continue;
             T a0, aC, aB, slope;
             const T zs = zp[cs];
             if (v == 0) {
@@ -650,8 +661,10 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
               aB = X[3 * v * P + kb];
               slope = w[3 * v + cs];
             }
-            T a = s3 * slope, b = a0 - aC, c = aC - aB;
-            T mm = minmod3(a, b, c);
+            T a = s3 * slope, mm;
+            if (hasA && hasB) mm = minmod3(a, a0 - aC, aC - aB);
+            else if (hasA) mm = minmod2(a, a0 - aC);
+            else mm = minmod2(a, aC - aB);
             if (mm != a) {
               T ns = mm / s3;
               if (v == 0) ws[cs] = Form<T>::eta ? ns : ns - zs;
