@@ -18,7 +18,28 @@ namespace mwdg {
 
 constexpr int TPB = 256;
 
+// Storage of the first variable's three coefficients.  Depth form (FP64):
+// (h0, h1x, h1y).  Free-surface form (FP32): (h0, eta1x, eta1y), the average
+// as depth and the slopes of the free surface eta = h + z, so that a flat
+// surface is stored with exactly zero slopes while rain and flux increments
+// keep the precision of the depth.
 template <typename T> struct Form { static constexpr bool eta = std::is_same<T, float>::value; };
+
+// stored slopes -> depth slopes, and back, given the bed slopes
+template <typename T>
+__device__ __forceinline__ void slopes_to_h(T &s1, T &s2, T z1, T z2) {
+  if (Form<T>::eta) {
+    s1 = s1 - z1;
+    s2 = s2 - z2;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void slopes_from_h(T &s1, T &s2, T z1, T z2) {
+  if (Form<T>::eta) {
+    s1 = s1 + z1;
+    s2 = s2 + z2;
+  }
+}
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
@@ -110,9 +131,9 @@ __global__ void k_nm_level(Geo g, Ptrs<T> p, int l) {
 }
 
 // Finest-level initial state.  On entry the first three components hold the
-// projected depth (is_eta = 0) or free surface (is_eta = 1).  Depth form
-// (FP64): with is_eta, wet elements get h = eta - z, others are dry.  Free
-// surface form (FP32): eta is stored; dry elements get eta = z.
+// projected depth (is_eta = 0) or free surface (is_eta = 1).  With is_eta,
+// wet elements (average free surface above the average bed) get h = eta - z,
+// others are dry.  The free-surface form stores free-surface slopes.
 template <typename T>
 __global__ void k_initial_finest(Geo g, Ptrs<T> p, int is_eta) {
   const int L = g.L;
@@ -123,9 +144,12 @@ __global__ void k_initial_finest(Geo g, Ptrs<T> p, int is_eta) {
   T *U = p.U;
   if (Form<T>::eta) {
     if (!is_eta) {
-      for (int m = 0; m < 3; m++) U[m * P + k] = U[m * P + k] + p.Z[m * P + k];
-    } else if (!(U[k] > p.Z[k])) {
-      for (int m = 0; m < 3; m++) U[m * P + k] = p.Z[m * P + k];
+      for (int m = 1; m < 3; m++) U[m * P + k] = U[m * P + k] + p.Z[m * P + k];
+    } else if (U[k] > p.Z[k]) {
+      U[k] = U[k] - p.Z[k];
+    } else {
+      U[k] = T(0);
+      for (int m = 1; m < 3; m++) U[m * P + k] = p.Z[m * P + k];
       for (int m = 3; m < 9; m++) U[m * P + k] = T(0);
     }
   } else if (is_eta) {
@@ -137,9 +161,11 @@ __global__ void k_initial_finest(Geo g, Ptrs<T> p, int is_eta) {
   }
 }
 
-// dense Eq. 9 of `ncomp` components of X from level l+1 to level l
+// dense Eq. 9 of `ncomp` components of X from level l+1 to level l; with a
+// bed pyramid Zb the first variable is in storage form and is encoded as
+// depth
 template <typename T>
-__global__ void k_encode_dense(Geo g, T *X, int ncomp, int l) {
+__global__ void k_encode_dense(Geo g, T *X, int ncomp, int l, const T *Zb) {
   long long n = (long long)g.nxl[l] * g.nyl[l];
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= n) return;
@@ -152,8 +178,10 @@ __global__ void k_encode_dense(Geo g, T *X, int ncomp, int l) {
       long long kc = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
 #pragma unroll
       for (int m = 0; m < 3; m++) ch[c][m] = X[(3 * v + m) * P + kc];
+      if (Zb && v == 0) slopes_to_h(ch[c][1], ch[c][2], Zb[P + kc], Zb[2 * P + kc]);
     }
     encode3(ch, sp);
+    if (Zb && v == 0) slopes_from_h(sp[1], sp[2], Zb[P + k], Zb[2 * P + k]);
 #pragma unroll
     for (int m = 0; m < 3; m++) X[(3 * v + m) * P + k] = sp[m];
   }
@@ -168,10 +196,12 @@ __global__ void k_eta_rule_leaves(Geo g, Ptrs<T> p) {
   const long long P = g.P;
   const T *E = p.Wn;
   if (E[k] > p.Z[k]) {
-    for (int m = 0; m < 3; m++)
+    p.U[k] = E[k] - p.Z[k];
+    for (int m = 1; m < 3; m++)
       p.U[m * P + k] = Form<T>::eta ? E[m * P + k] : E[m * P + k] - p.Z[m * P + k];
   } else {
-    for (int m = 0; m < 3; m++) p.U[m * P + k] = Form<T>::eta ? p.Z[m * P + k] : T(0);
+    p.U[k] = T(0);
+    for (int m = 1; m < 3; m++) p.U[m * P + k] = Form<T>::eta ? p.Z[m * P + k] : T(0);
     for (int m = 3; m < 9; m++) p.U[m * P + k] = T(0);
   }
 }
@@ -370,7 +400,7 @@ __global__ void k_leaf_maxabs(Geo g, Ptrs<T> p) {
   const long long P = g.P;
   FOR_LEAVES(p) {
     long long k = p.leaves[_q];
-    T h0 = Form<T>::eta ? p.U[k] - p.Z[k] : p.U[k];
+    T h0 = p.U[k];
     m0 = fmax(m0, (double)tabs(h0));
     m1 = fmax(m1, (double)tabs(p.U[3 * P + k]));
     m2 = fmax(m2, (double)tabs(p.U[6 * P + k]));
@@ -406,18 +436,15 @@ __global__ void k_encode_flow(Geo g, Ptrs<T> p, int l) {
     for (int v = 0; v < 3; v++) {
       T ch[4][3], sp[3];
 #pragma unroll
-      for (int c = 0; c < 4; c++)
+      for (int c = 0; c < 4; c++) {
 #pragma unroll
         for (int m = 0; m < 3; m++) ch[c][m] = p.U[(3 * v + m) * P + kc[c]];
+        if (v == 0) slopes_to_h(ch[c][1], ch[c][2], p.Z[P + kc[c]], p.Z[2 * P + kc[c]]);
+      }
       encode3(ch, sp);
+      if (v == 0) slopes_from_h(sp[1], sp[2], p.Z[P + k], p.Z[2 * P + k]);
 #pragma unroll
       for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sp[m];
-      if (Form<T>::eta && v == 0) {  // details of the depth h = eta - z
-#pragma unroll
-        for (int c = 0; c < 4; c++)
-#pragma unroll
-          for (int m = 0; m < 3; m++) ch[c][m] = ch[c][m] - p.Z[m * P + kc[c]];
-      }
       double dm = (double)detail_max3(ch);
       double mx = __longlong_as_double((long long)p.ctl->vmax[v]);
       dmax = fmax(dmax, dm / fmax(1.0, mx));
@@ -463,17 +490,15 @@ __global__ void k_decode_new(Geo g, Ptrs<T> p) {
   for (int v = 0; v < 3; v++) {
     T s[3];
     for (int m = 0; m < 3; m++) s[m] = p.U[(3 * v + m) * P + ka];
-    // the free-surface form prolongs the depth h = eta - z of the old leaf
-    // and adds the new leaf's own bed, as the depth form does implicitly
-    if (Form<T>::eta && v == 0)
-      for (int m = 0; m < 3; m++) s[m] = s[m] - p.Z[m * P + ka];
+    // the depth plane of the old leaf is prolonged; the free-surface form
+    // then takes the new leaf's own bed slopes
+    if (v == 0) slopes_to_h(s[1], s[2], p.Z[P + ka], p.Z[2 * P + ka]);
     for (int q = d - 1; q >= 0; q--) {
       T o[3];
       prolong3(s[0], s[1], s[2], path[q], o);
       s[0] = o[0]; s[1] = o[1]; s[2] = o[2];
     }
-    if (Form<T>::eta && v == 0)
-      for (int m = 0; m < 3; m++) s[m] = s[m] + p.Z[m * P + k];
+    if (v == 0) slopes_from_h(s[1], s[2], p.Z[P + k], p.Z[2 * P + k]);
     for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = s[m];
   }
 }
@@ -490,7 +515,7 @@ __global__ void k_leaf_dt(Geo g, Ptrs<T> p) {
     int l, i, j;
     node_of(g, k, l, i, j);
     const T dxl = (T)g.dxl[l];
-    T h0 = Form<T>::eta ? p.U[k] - p.Z[k] : p.U[k];
+    T h0 = p.U[k];
     if (h0 > hd) {
       T u = p.U[3 * P + k] / h0, v = p.U[6 * P + k] / h0;
       T c = tsqrt(gg * h0);
@@ -556,7 +581,7 @@ __global__ void k_rain_friction(Geo g, Ptrs<T> p) {
       w0 = w0 + (Form<T>::eta ? rdt : (T)(g.rain_rate) * dt);
       p.U[k] = w0;
     }
-    T h0 = Form<T>::eta ? w0 - p.Z[k] : w0;
+    const T h0 = w0;
     if (h0 > hd) {
       T u = p.U[3 * P + k] / h0, v = p.U[6 * P + k] / h0;
       T sp = tsqrt(u * u + v * v);
@@ -591,24 +616,20 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
     for (int m = 0; m < 9; m++) w[m] = X[m * P + k];
 #pragma unroll
     for (int m = 0; m < 3; m++) zp[m] = p.Z[m * P + k];
-    T h0, eta0;
-    if (Form<T>::eta) {
-      eta0 = w[0];
-      h0 = eta0 - zp[0];
-    } else {
-      h0 = w[0];
-      eta0 = h0 + zp[0];
-    }
+    const T h0 = w[0];
+    const T eta0 = h0 + zp[0];
+    T h1x = w[1], h1y = w[2];
+    slopes_to_h(h1x, h1y, zp[1], zp[2]);
     bool reduced = !(h0 > hd);
 #pragma unroll
     for (int f = 0; f < 4; f++) {
-      T hf = Form<T>::eta ? face_value(w[0], w[1], w[2], f) - face_value(zp[0], zp[1], zp[2], f)
-                          : face_value(w[0], w[1], w[2], f);
-      if (!(hf > hd)) reduced = true;
+      if (!(face_value(h0, h1x, h1y, f) > hd)) reduced = true;
       if (!(eta0 - face_value(zp[0], zp[1], zp[2], f) > hd)) reduced = true;
     }
     T ws[9], wf[9], ze[3];
     if (reduced) {
+      // stored: flat free surface over the planar bed; flux view: flat depth
+      // over a flat bed (the same numbers in the free-surface form)
 #pragma unroll
       for (int m = 0; m < 9; m++) ws[m] = w[m];
       if (Form<T>::eta) {
@@ -619,9 +640,7 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
       ws[4] = ws[5] = ws[7] = ws[8] = T(0);
 #pragma unroll
       for (int m = 0; m < 9; m++) wf[m] = ws[m];
-      if (!Form<T>::eta) {
-        wf[1] = T(0); wf[2] = T(0);
-      }
+      wf[1] = T(0); wf[2] = T(0);
       ze[0] = zp[0]; ze[1] = T(0); ze[2] = T(0);
     } else {
 #pragma unroll
@@ -637,8 +656,8 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
           if (!hasA && !hasB) continue;
           const long long ka = hasA ? nid(g, l, ia, ja) : k, kb = hasB ? nid(g, l, ib, jb) : k;
           T hC = h0;
-          T hA = Form<T>::eta ? X[ka] - p.Z[ka] : X[ka];
-          T hB = Form<T>::eta ? X[kb] - p.Z[kb] : X[kb];
+          T hA = X[ka];
+          T hB = X[kb];
           const bool wet = (hC > hd) && (!hasA || hA > hd) && (!hasB || hB > hd);
           const int cs = 1 + dir;
           for (int v = 0; v < 3; v++) {
@@ -646,15 +665,10 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
             T a0, aC, aB, slope;
             const T zs = zp[cs];
             if (v == 0) {
-              if (Form<T>::eta) {
-                aC = w[0]; a0 = X[ka]; aB = X[kb];
-                slope = w[cs];
-              } else {
-                aC = hC + zp[0];
-                a0 = hA + p.Z[ka];
-                aB = hB + p.Z[kb];
-                slope = w[cs] + zs;
-              }
+              aC = hC + zp[0];
+              a0 = hA + p.Z[ka];
+              aB = hB + p.Z[kb];
+              slope = Form<T>::eta ? w[cs] : w[cs] + zs;
             } else {
               aC = w[3 * v];
               a0 = X[3 * v * P + ka];
@@ -699,17 +713,35 @@ __global__ void k_encode_view(Geo g, Ptrs<T> p, int l) {
   long long kc[4];
 #pragma unroll
   for (int c = 0; c < 4; c++) kc[c] = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
-  for (int v = 0; v < 4; v++) {
-    T *X = (v < 3) ? p.F + 3 * v * P : p.Ze;
+  T zc[4][3], zpar[3];
+#pragma unroll
+  for (int c = 0; c < 4; c++)
+#pragma unroll
+    for (int m = 0; m < 3; m++) zc[c][m] = p.Ze[m * P + kc[c]];
+  encode3(zc, zpar);
+#pragma unroll
+  for (int m = 0; m < 3; m++) p.Ze[m * P + k] = zpar[m];
+  for (int v = 0; v < 3; v++) {
+    T *X = p.F + 3 * v * P;
     T ch[4][3], sp[3];
 #pragma unroll
-    for (int c = 0; c < 4; c++)
+    for (int c = 0; c < 4; c++) {
 #pragma unroll
       for (int m = 0; m < 3; m++) ch[c][m] = X[m * P + kc[c]];
+      if (v == 0) slopes_to_h(ch[c][1], ch[c][2], zc[c][1], zc[c][2]);
+    }
     encode3(ch, sp);
+    if (v == 0) slopes_from_h(sp[1], sp[2], zpar[1], zpar[2]);
 #pragma unroll
     for (int m = 0; m < 3; m++) X[m * P + k] = sp[m];
   }
+}
+
+// interface-centre limit of the first variable of a flux-view plane: the
+// depth (depth form) or the free surface (free-surface form)
+template <typename T>
+__device__ __forceinline__ T first_face(T c0, T c1, T c2, T ze0, int f) {
+  return Form<T>::eta ? face_value(c0 + ze0, c1, c2, f) : face_value(c0, c1, c2, f);
 }
 
 // limit (first variable, qx, qy, z) of the same-level view of the neighbour
@@ -732,7 +764,10 @@ __device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, i
     else { c1 = 2; c2 = 3; }
     long long k1 = nid(g, l + 1, 2 * a + (c1 & 1), 2 * b + (c1 >> 1));
     long long k2 = nid(g, l + 1, 2 * a + (c2 & 1), 2 * b + (c2 >> 1));
-    for (int v = 0; v < 3; v++) {
+    const T *F = p.F;
+    out[0] = T(0.5) * (first_face(F[k1], F[P + k1], F[2 * P + k1], p.Ze[k1], fo) +
+                       first_face(F[k2], F[P + k2], F[2 * P + k2], p.Ze[k2], fo));
+    for (int v = 1; v < 3; v++) {
       const T *X = p.F + 3 * v * P;
       out[v] = T(0.5) * (face_value(X[k1], X[P + k1], X[2 * P + k1], fo) +
                          face_value(X[k2], X[P + k2], X[2 * P + k2], fo));
@@ -753,9 +788,12 @@ __device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, i
       la--;
       ka = nid(g, la, aa, bb);
     }
-    for (int v = 0; v < 4; v++) {
+    // beds (v = 3) first, then the flow planes in depth form
+    T zb[3] = {p.Ze[ka], p.Ze[P + ka], p.Ze[2 * P + ka]};
+    for (int v = 3; v >= 0; v--) {
       const T *X = (v < 3) ? p.F + 3 * v * P : p.Ze;
       T s[3] = {X[ka], X[P + ka], X[2 * P + ka]};
+      if (v == 0) slopes_to_h(s[1], s[2], zb[1], zb[2]);
       for (int q = d - 1; q >= 0; q--) {
         T o[3];
         prolong3(s[0], s[1], s[2], path[q], o);
@@ -763,9 +801,11 @@ __device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, i
       }
       out[v] = face_value(s[0], s[1], s[2], fo);
     }
+    if (Form<T>::eta) out[0] = out[0] + out[3];  // depth + bed = free surface
     return true;
   }
-  for (int v = 0; v < 3; v++) {
+  out[0] = first_face(p.F[k], p.F[P + k], p.F[2 * P + k], p.Ze[k], fo);
+  for (int v = 1; v < 3; v++) {
     const T *X = p.F + 3 * v * P;
     out[v] = face_value(X[k], X[P + k], X[2 * P + k], fo);
   }
@@ -804,7 +844,7 @@ __global__ void k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T 
 #pragma unroll
     for (int f = 0; f < 4; f++) {
       T own[4], nb[4];
-      own[0] = face_value(w[0], w[1], w[2], f);
+      own[0] = first_face(w[0], w[1], w[2], zc[0], f);
       own[1] = face_value(w[3], w[4], w[5], f);
       own[2] = face_value(w[6], w[7], w[8], f);
       own[3] = face_value(zc[0], zc[1], zc[2], f);
@@ -908,30 +948,15 @@ __global__ void k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T 
     }
     // positivity clip and dry reset
     const double area = g.dxl[l] * g.dxl[l];
-    if (Form<T>::eta) {
-      const T z0 = p.Z[k];
-      T h0 = o[0] - z0;
-      if (h0 < T(0)) {
-        ncl++;
-        csum += -(double)h0 * area;
-        o[0] = z0;
-        h0 = T(0);
-      }
-      if (!(h0 > hd)) {
-        o[1] = p.Z[P + k];
-        o[2] = p.Z[2 * P + k];
-        for (int m = 3; m < 9; m++) o[m] = T(0);
-      }
-    } else {
-      if (o[0] < T(0)) {
-        ncl++;
-        csum += -(double)o[0] * area;
-        o[0] = T(0);
-      }
-      if (!(o[0] > hd)) {
-        o[1] = T(0); o[2] = T(0);
-        for (int m = 3; m < 9; m++) o[m] = T(0);
-      }
+    if (o[0] < T(0)) {
+      ncl++;
+      csum += -(double)o[0] * area;
+      o[0] = T(0);
+    }
+    if (!(o[0] > hd)) {  // dry: flat zero depth (free-surface slopes = bed slopes)
+      o[1] = Form<T>::eta ? p.Z[P + k] : T(0);
+      o[2] = Form<T>::eta ? p.Z[2 * P + k] : T(0);
+      for (int m = 3; m < 9; m++) o[m] = T(0);
     }
 #pragma unroll
     for (int m = 0; m < 9; m++) {
@@ -981,7 +1006,7 @@ __global__ void k_fields(Geo g, Ptrs<T> p, double *h, double *u, double *v) {
     double c0 = (double)p.U[3 * q * P + k], c1 = (double)p.U[(3 * q + 1) * P + k],
            c2 = (double)p.U[(3 * q + 2) * P + k];
     if (Form<T>::eta && q == 0) {
-      c0 -= (double)p.Z[k]; c1 -= (double)p.Z[P + k]; c2 -= (double)p.Z[2 * P + k];
+      c1 -= (double)p.Z[P + k]; c2 -= (double)p.Z[2 * P + k];
     }
     val[q] = c0 + 2.0 * s3 * xi * c1 + 2.0 * s3 * et * c2;
   }
@@ -1010,7 +1035,7 @@ __global__ void k_read_active(Geo g, Ptrs<T> p, int32_t *lev, int32_t *ii, int32
     const long long P = g.P;
     for (int m = 0; m < 9; m++) {
       double c = (double)p.U[m * P + k];
-      if (Form<T>::eta && m < 3) c -= (double)p.Z[m * P + k];
+      if (Form<T>::eta && (m == 1 || m == 2)) c -= (double)p.Z[m * P + k];
       coef[9 * (long long)q + m] = c;
     }
   }
@@ -1026,7 +1051,7 @@ __global__ void k_volume_part(Geo g, Ptrs<T> p) {
     long long k = p.leaves[q];
     int l, i, j;
     node_of(g, k, l, i, j);
-    double h0 = Form<T>::eta ? (double)p.U[k] - (double)p.Z[k] : (double)p.U[k];
+    double h0 = (double)p.U[k];
     acc += h0 * (g.dxl[l] * g.dxl[l]);
   }
   __shared__ double sh[TPB];
@@ -1096,14 +1121,14 @@ int Launch<T>::initial_finest(const Geo &g, const Ptrs<T> &p, int is_eta, cudaSt
 template <typename T>
 int Launch<T>::encode_dense_U(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
   int n = 0;
-  for (int l = g.L - 1; l >= 0; l--, n++) k_encode_dense<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p.U, 9, l);
+  for (int l = g.L - 1; l >= 0; l--, n++) k_encode_dense<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p.U, 9, l, p.Z);
   return n;
 }
 
 template <typename T>
 int Launch<T>::eta_rule_leaves(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
   int n = 0;
-  for (int l = g.L - 1; l >= 0; l--, n++) k_encode_dense<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p.Wn, 3, l);
+  for (int l = g.L - 1; l >= 0; l--, n++) k_encode_dense<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p.Wn, 3, l, (const T *)nullptr);
   k_eta_rule_leaves<T><<<nblk(g.P), TPB, 0, st>>>(g, p);
   return n + 1;
 }
