@@ -196,6 +196,27 @@ MWDG_API mwdg_status mwdg_kernel_times(mwdg_ctx *ctx, const char **names, double
 /* Number of kernel launches this context has queued since creation. */
 MWDG_API mwdg_status mwdg_launch_count(mwdg_ctx *ctx, int64_t *n);
 
+/* Allocation-free volume sum, for callers that cannot allocate device memory
+ * while they run (a host that gives all device memory to its own pool, a
+ * real-time warning loop that must not meet an allocation failure, a
+ * plug-in that only receives buffers).  The paper has no counterpart; this
+ * is a service of the library.  It computes V = sum_k h0[k] * (dx 2^(L -
+ * level[k]))^2 over n active leaves, in a fixed summation order, from device
+ * arrays h0 (FP64 depth averages) and level (the leaves' levels, as
+ * mwdg_read_active reports them), and writes V to the device pointer volume,
+ * all queued on cuda_stream.  It allocates nothing: its per-block partial
+ * sums live in a fixed file-scope device array (128 KB, held by every GPU
+ * that loads the library until the process exits).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture on that device.  Calls share the
+ * array: calls whose work overlaps on the GPU race.  Errors: MWDG_ERR_ARG
+ * (NULL pointer with n > 0, dx <= 0, L outside 0..MWDG_LMAX, n < 0),
+ * MWDG_ERR_CAPACITY when n exceeds MWDG_VOLUME_NOALLOC_MAX, MWDG_ERR_CUDA
+ * when the address lookup or a launch fails. */
+#define MWDG_VOLUME_NOALLOC_MAX 67108864LL
+MWDG_API mwdg_status mwdg_volume_noalloc(const double *h0, const int32_t *level, int64_t n, double dx,
+                                         int32_t L, double *volume, void *cuda_stream);
+
 MWDG_API const char *mwdg_last_error(const mwdg_ctx *ctx);
 MWDG_API const char *mwdg_status_string(mwdg_status s);
 

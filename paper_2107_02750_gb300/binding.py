@@ -21,7 +21,7 @@ EXPORTS = (
     "mwdg_read_fields", "mwdg_read_fields_dev", "mwdg_read_active", "mwdg_get_time",
     "mwdg_get_volume", "mwdg_profile", "mwdg_kernel_times", "mwdg_launch_count",
     "mwdg_last_error", "mwdg_status_string", "mwdg_state_bytes", "mwdg_save_state",
-    "mwdg_load_state",
+    "mwdg_load_state", "mwdg_volume_noalloc",
 )
 
 
@@ -81,6 +81,7 @@ def lib(build: bool = True):
         "mwdg_state_bytes": [vp, lp],
         "mwdg_save_state": [vp, vp, C.c_int64],
         "mwdg_load_state": [vp, vp, C.c_int64],
+        "mwdg_volume_noalloc": [vp, vp, C.c_int64, C.c_double, C.c_int32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

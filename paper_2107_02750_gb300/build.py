@@ -24,6 +24,7 @@ UNITS = {
     "mwdg_api.cu": [],
     "mwdg_f64.cu": ["-fmad=false"],
     "mwdg_f32.cu": [],
+    "mwdg_noalloc.cu": [],
 }
 
 
