@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <string>
@@ -42,6 +43,12 @@ struct mwdg_ctx {
   double *d_coef = nullptr;      // coefficients for read-back
   int grid_leaves = 0;
   bool dem = false, initial = false, stepped = false, failed = false, encoded = false;
+  bool vmax_fresh = false;   // max |v0| on the device is that of the current leaves
+  // one captured step (CUDA graph), replayed while the parameters it bakes in
+  // are unchanged; not used on the legacy default stream or while profiling
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  int graph_launches = 0;
   int static_eta = 0;   // static run with a free-surface initial state
   int64_t launches = 0;
   std::string err;
@@ -225,18 +232,65 @@ mwdg_status build_static_grid(mwdg_ctx *c, int is_eta_encoded) {
   return MWDG_OK;
 }
 
-mwdg_status queue_step(mwdg_ctx *c) {
+void drop_graph(mwdg_ctx *c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+}
+
+// the kernels of one step: [adaptive: encode, flags, decode, compaction],
+// time step, both RK2 stages (the last block closes the step)
+int launch_step(mwdg_ctx *c, int with_maxabs) {
   const Geo &g = c->g;
-  c->launches += dispatch(c, [&](auto &p, auto *) {
+  return dispatch(c, [&](auto &p, auto *) {
     using T = std::remove_pointer_t<decltype(p.U)>;
     int n = 0;
-    if (g.mode == MWDG_ADAPTIVE) n += Launch<T>::adapt(g, p, 0, 0, c->st, mark_cb, c);
+    if (g.mode == MWDG_ADAPTIVE) n += Launch<T>::adapt(g, p, 0, with_maxabs, c->st, mark_cb, c);
     n += Launch<T>::step(g, p, c->grid_leaves, c->st, mark_cb, c);
     return n;
   });
-  CHECK_LAUNCH();
+}
+
+mwdg_status queue_step(mwdg_ctx *c) {
+  const bool adaptive = c->g.mode == MWDG_ADAPTIVE;
+  const bool graphable = c->use_graph && !c->prof && c->st != nullptr && (c->vmax_fresh || !adaptive);
+  if (graphable) {
+    if (!c->graph) {
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+      c->graph_launches = launch_step(c, 0);
+      cudaError_t e1 = cudaStreamEndCapture(c->st, &gr);
+      if (e1 != cudaSuccess || !gr)
+        return fail(c, MWDG_ERR_CUDA, "step capture: %s", cudaGetErrorString(e1));
+      cudaError_t e2 = cudaGraphInstantiate(&c->graph, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e2 != cudaSuccess) return fail(c, MWDG_ERR_CUDA, "step graph: %s", cudaGetErrorString(e2));
+    }
+    CK(cudaGraphLaunch(c->graph, c->st));
+    c->launches += c->graph_launches;
+  } else {
+    c->launches += launch_step(c, adaptive && !c->vmax_fresh);
+    CHECK_LAUNCH();
+  }
   c->stepped = true;
   c->encoded = false;
+  c->vmax_fresh = true;
+  return MWDG_OK;
+}
+
+__global__ void k_reset_reductions(Ctl *c) {
+  c->dtmin = 0x7ff0000000000000ULL;
+  c->vmax[0] = c->vmax[1] = c->vmax[2] = 0ULL;
+}
+
+// the reductions a step starts from, over the current leaves
+mwdg_status prime(mwdg_ctx *c) {
+  k_reset_reductions<<<1, 1, 0, c->st>>>(c->ctl);
+  c->launches += 1 + dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::prime(c->g, p, c->grid_leaves, c->st);
+  });
+  CHECK_LAUNCH();
+  c->vmax_fresh = true;
   return MWDG_OK;
 }
 
@@ -296,6 +350,7 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
     return MWDG_ERR_ARG;
   mwdg_ctx *c = new mwdg_ctx();
   c->p = *p;
+  if (const char *e = getenv("MWDG_NO_GRAPH")) c->use_graph = !(e[0] == '1');
   c->st = (cudaStream_t)p->cuda_stream;
   Geo &g = c->g;
   g.mode = p->mode;
@@ -331,6 +386,8 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
   g.nknots = 0;
   g.rain_rate = 0.0;
   g.rain_t_end = 0.0;
+  g.coarse_nodes = 256;
+  if (const char *e = getenv("MWDG_COARSE_NODES")) g.coarse_nodes = atoll(e);
   c->grid_leaves = (int)std::min<long long>((g.P + 255) / 256, 152 * 8);
   mwdg_status s;
   if ((s = alloc(c, &c->ctl, 1)) || (s = alloc(c, &c->d_knot_t, KNOT_CAP)) ||
@@ -365,6 +422,7 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
 void mwdg_destroy(mwdg_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
+  drop_graph(c);
   for (void *q : c->allocs) cudaFree(q);
   for (auto &m : c->marks) cudaEventDestroy(m.second);
   for (auto ev : c->pool) cudaEventDestroy(ev);
@@ -471,6 +529,7 @@ mwdg_status mwdg_load_initial(mwdg_ctx *c, const double *h_vert, const double *q
   if (s) return s;
   Ctl h = fresh_ctl();
   CK(cudaMemcpyAsync(c->ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->st));
+  if ((s = prime(c))) return s;
   CK(cudaStreamSynchronize(c->st));
   c->initial = true;
   c->stepped = false;
@@ -485,6 +544,7 @@ mwdg_status mwdg_set_inflow(mwdg_ctx *c, int32_t edge, int32_t c0, int32_t c1, c
   if (nknots == 0) {
     g.inflow_edge = -1;
     g.nknots = 0;
+    drop_graph(c);
     return MWDG_OK;
   }
   if (edge < 0 || edge > 3 || nknots < 1 || nknots > KNOT_CAP || !t || !Q)
@@ -501,6 +561,7 @@ mwdg_status mwdg_set_inflow(mwdg_ctx *c, int32_t edge, int32_t c0, int32_t c1, c
   g.inflow_c0 = c0;
   g.inflow_c1 = c1;
   g.nknots = nknots;
+  drop_graph(c);
   return MWDG_OK;
 }
 
@@ -509,6 +570,7 @@ mwdg_status mwdg_set_rain(mwdg_ctx *c, double rate, double t_stop) {
   if (!std::isfinite(rate) || rate < 0.0 || std::isnan(t_stop)) return fail(c, MWDG_ERR_ARG, "invalid rain");
   c->g.rain_rate = rate;
   c->g.rain_t_end = t_stop;
+  drop_graph(c);
   return MWDG_OK;
 }
 
@@ -519,10 +581,11 @@ mwdg_status mwdg_mra_encode(mwdg_ctx *c) {
   const Geo &g = c->g;
   c->launches += dispatch(c, [&](auto &p, auto *) {
     using T = std::remove_pointer_t<decltype(p.U)>;
-    return Launch<T>::adapt(g, p, 1, 0, c->st, mark_cb, c);
+    return Launch<T>::adapt(g, p, 1, c->vmax_fresh ? 0 : 1, c->st, mark_cb, c);
   });
   CHECK_LAUNCH();
   c->encoded = true;
+  c->vmax_fresh = true;
   return MWDG_OK;
 }
 
@@ -533,18 +596,23 @@ mwdg_status mwdg_mra_adapt(mwdg_ctx *c, double eps, int64_t *n_active) {
   Geo &g = c->g;
   if (g.mode == MWDG_UNIFORM) return fail(c, MWDG_ERR_STATE, "uniform grids do not adapt");
   g.eps = eps;
+  drop_graph(c);
   if (g.mode == MWDG_STATIC) {
     if (c->stepped) return fail(c, MWDG_ERR_STATE, "a static grid is fixed once stepping started");
     mwdg_status s = build_static_grid(c, c->static_eta);
     if (s) return s;
+    if ((s = prime(c))) return s;
   } else {
     // full encode with this epsilon, then threshold, regularise, decode
+    const int with_max = c->vmax_fresh ? 0 : 1;
     c->launches += dispatch(c, [&](auto &p, auto *) {
       using T = std::remove_pointer_t<decltype(p.U)>;
-      return Launch<T>::adapt(g, p, 0, 0, c->st, mark_cb, c);
+      return Launch<T>::adapt(g, p, 0, with_max, c->st, mark_cb, c);
     });
     CHECK_LAUNCH();
     c->encoded = false;
+    mwdg_status s = prime(c);  // max |v0| and dt over the new leaves
+    if (s) return s;
   }
   if (n_active) {
     int n = 0;
@@ -597,7 +665,9 @@ mwdg_status mwdg_run_to_time(mwdg_ctx *c, double t_end, int64_t *steps_out) {
       if ((s = queue_step(c))) return s;
     if ((s = read_ctl(c, &h))) return s;
     if (h.steps == before) break;  // dt reached zero
-    batch = std::min(batch * 2, 256);
+    // queue about as many steps as the last step length says are left
+    double left = (h.dt > 0.0) ? (t_end - h.t) / h.dt : 1.0;
+    batch = (int)std::max(1.0, std::min(256.0, std::ceil(left * 1.05) + 1.0));
   }
   k_set_tend<<<1, 1, 0, c->st>>>(c->ctl, 1e300);
   c->launches++;
@@ -787,12 +857,15 @@ mwdg_status mwdg_load_state(mwdg_ctx *c, const void *buf, int64_t size) {
   CK(cudaMemcpyAsync(DZ, b, P * 8, cudaMemcpyHostToDevice, c->st));
   Ctl ctl = h.ctl;
   ctl.t_end = 1e300;
+  ctl.blocks_done = 0u;
   CK(cudaMemcpyAsync(c->ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, c->st));
   c->launches += dispatch(c, [&](auto &p, auto *) {
     using T = std::remove_pointer_t<decltype(p.U)>;
     return Launch<T>::compact(g, p, c->st);
   });
   CHECK_LAUNCH();
+  mwdg_status sp = prime(c);
+  if (sp) return sp;
   CK(cudaStreamSynchronize(c->st));
   c->dem = c->initial = true;
   c->stepped = true;
@@ -813,6 +886,7 @@ mwdg_status mwdg_profile(mwdg_ctx *c, int32_t enable) {
     }
   }
   c->prof = enable != 0;
+  drop_graph(c);
   return MWDG_OK;
 }
 

@@ -21,6 +21,8 @@ struct Ctl {
   long long steps;
   int nonfinite;
   int changed;                 // grading sweep made a change
+  unsigned int blocks_done;    // completion tickets of the last kernel of a step
+  int pad_;
 };
 
 // Geometry and parameters of the level hierarchy (passed by value).
@@ -34,6 +36,7 @@ struct Geo {
   int bc[4];
   int inflow_edge, inflow_c0, inflow_c1, nknots;
   double rain_rate, rain_t_end;
+  long long coarse_nodes;      // MRA levels up to this size run in one block
 };
 
 // Device arrays.  Coefficient arrays are component-major with stride P:
@@ -76,10 +79,13 @@ template <typename T> struct Launch {
                    cudaStream_t st);
   static int all_finest(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
   static int compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
-  static int adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int decode_only,
+  static int adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_maxabs,
                    cudaStream_t st, void (*mark)(void *, int), void *mark_arg);
   static int step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st,
                   void (*mark)(void *, int), void *mark_arg);
+  // max |v0| and the CFL candidate over the current leaves (after a load,
+  // a checkpoint restore or a stand-alone adaptation)
+  static int prime(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st);
   static int fields(const Geo &g, const Ptrs<T> &p, double *h, double *u, double *v,
                     cudaStream_t st);
   static int read_active(const Geo &g, const Ptrs<T> &p, int32_t *lev, int32_t *i, int32_t *j,

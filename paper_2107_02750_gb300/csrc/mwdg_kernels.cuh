@@ -250,6 +250,7 @@ __global__ void k_grading(Geo g, Ptrs<T> p, int l) {
 template <typename T>
 __global__ void k_kinds(Geo g, Ptrs<T> p, const uint8_t *flag, int keep_old) {
   long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (keep_old && k == 0) p.ctl->dtmin = 0x7ff0000000000000ULL;  // the decode pass refills it
   if (k >= g.P) return;
   int l, i, j;
   node_of(g, k, l, i, j);
@@ -417,19 +418,65 @@ __global__ void k_leaf_maxabs(Geo g, Ptrs<T> p) {
   }
 }
 
-// MWDG2 encode of level l (Sect. 2.3): refined nodes get the scale
-// coefficients of their children (Eq. 9) and are flagged when their largest
-// normalised flow or topography detail reaches epsilon; other nodes carry
-// no flow details, so only their topography detail counts.
+// CFL candidate of one leaf (Courant number applied in k_begin_step):
+// min over x and y of dx / (|u| + sqrt(g h)) when wet, and the inflow ghost
+// states at the critical depth on inflow faces; +inf when there is none
 template <typename T>
-__global__ void k_encode_flow(Geo g, Ptrs<T> p, int l) {
-  long long n = (long long)g.nxl[l] * g.nyl[l];
-  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const long long P = g.P, k = g.off[l] + r;
+__device__ __forceinline__ double leaf_dt_candidate(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
+                                                    T h0, T qx0, T qy0, double t) {
+  const T gg = (T)g.g, hd = (T)g.hd;
+  const T dxl = (T)g.dxl[l];
+  double best = __longlong_as_double(0x7ff0000000000000LL);
+  if (h0 > hd) {
+    T u = qx0 / h0, v = qy0 / h0;
+    T c = tsqrt(gg * h0);
+    best = (double)tmin(dxl / (tabs(u) + c), dxl / (tabs(v) + c));
+  }
+  if (g.inflow_edge >= 0) {
+    for (int e = 0; e < 4; e++) {
+      bool on = (e == 0 && i == 0) || (e == 1 && i == g.nxl[l] - 1) || (e == 2 && j == 0) ||
+                (e == 3 && j == g.nyl[l] - 1);
+      if (!on) continue;
+      double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, t);
+      if (q > 0.0) {
+        T qt = (T)q;
+        T hc = tcbrt(qt * qt / gg);
+        if (hc > hd) best = fmin(best, (double)(dxl / (qt / hc + tsqrt(gg * hc))));
+      }
+    }
+  }
+  return best;
+}
+
+__device__ __forceinline__ void warp_min_to(unsigned long long *dst, double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v < __longlong_as_double(0x7ff0000000000000LL)) atomic_min_pos(dst, v);
+}
+
+// CFL candidates over the leaves
+template <typename T>
+__global__ void k_leaf_dt(Geo g, Ptrs<T> p) {
+  const long long P = g.P;
+  const double t = p.ctl->t;
+  double best = __longlong_as_double(0x7ff0000000000000LL);
+  FOR_LEAVES(p) {
+    long long k = p.leaves[_q];
+    int l, i, j;
+    node_of(g, k, l, i, j);
+    best = fmin(best, leaf_dt_candidate(g, p, l, i, j, p.U[k], p.U[3 * P + k], p.U[6 * P + k], t));
+  }
+  warp_min_to(&p.ctl->dtmin, best);
+}
+
+// MWDG2 encode of one node of level l (Sect. 2.3): a refined node gets the
+// scale coefficients of its children (Eq. 9) and is flagged when its largest
+// normalised flow or topography detail reaches epsilon; other nodes carry no
+// flow details, so only their topography detail counts.
+template <typename T>
+__device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
+  const long long P = g.P, k = nid(g, l, i, j);
   double dmax = p.DZ[k];
   if (p.kind[k] == K_SIG) {
-    int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
     long long kc[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) kc[c] = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
@@ -450,93 +497,122 @@ __global__ void k_encode_flow(Geo g, Ptrs<T> p, int l) {
       dmax = fmax(dmax, dm / fmax(1.0, mx));
     }
   }
-  p.flag[k] = (l < g.L) ? (uint8_t)(dmax >= g.eps) : (uint8_t)0;
+  p.flag[k] = (uint8_t)(dmax >= g.eps);
 }
 
-// prediction: a significant node flags its eight same-level neighbours
+// regularised flag of node (m, a, b): prediction (the node or one of its
+// eight same-level neighbours is significant) or closure (a child is
+// refined; children's regularised flags are final by then)
 template <typename T>
-__global__ void k_predict(Geo g, Ptrs<T> p, int l) {
+__device__ __forceinline__ uint8_t regular_flag(const Geo &g, const Ptrs<T> &p, int m, int a, int b) {
+  uint8_t f = 0;
+  for (int bb = b - 1; bb <= b + 1; bb++)
+    for (int aa = a - 1; aa <= a + 1; aa++)
+      if (aa >= 0 && bb >= 0 && aa < g.nxl[m] && bb < g.nyl[m]) f |= p.flag[nid(g, m, aa, bb)];
+  if (m + 1 < g.L)
+    for (int c = 0; c < 4; c++) f |= p.flag2[nid(g, m + 1, 2 * a + (c & 1), 2 * b + (c >> 1))];
+  return f;
+}
+
+// one bottom-up pass at level l: the regularised flags of the children
+// (level l+1, whose significance flags are final) and the encode/flag of
+// the node itself
+template <typename T>
+__device__ __forceinline__ void adapt_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
+  if (l + 1 < g.L)
+    for (int c = 0; c < 4; c++) {
+      int a = 2 * i + (c & 1), b = 2 * j + (c >> 1);
+      p.flag2[nid(g, l + 1, a, b)] = regular_flag(g, p, l + 1, a, b);
+    }
+  encode_flag_node(g, p, l, i, j);
+}
+
+// adaptation runs only while there is time left to step (steps queued
+// beyond the end time are no-ops, as on the host side)
+#define ADAPT_LIVE(p) ((p).ctl->t < (p).ctl->t_end)
+
+template <typename T>
+__global__ void k_adapt_level(Geo g, Ptrs<T> p, int l) {
   long long n = (long long)g.nxl[l] * g.nyl[l];
   long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (r >= n) return;
+  if (r >= n || !ADAPT_LIVE(p)) return;
   int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
-  uint8_t f = 0;
-  for (int b = j - 1; b <= j + 1; b++)
-    for (int a = i - 1; a <= i + 1; a++)
-      if (a >= 0 && b >= 0 && a < g.nxl[l] && b < g.nyl[l]) f |= p.flag[nid(g, l, a, b)];
-  p.flag2[g.off[l] + r] = f;
+  adapt_node(g, p, l, i, j);
 }
 
-// new leaves that were below an old leaf take the prolongation of its plane
-// (Eq. 10 with zero details, one level at a time); the flow is prolonged in
-// depth form in both precisions
+// levels lc..0 in one block (barrier between levels), then the regularised
+// flags of level 0
 template <typename T>
-__global__ void k_decode_new(Geo g, Ptrs<T> p) {
-  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (k >= g.P || p.kind[k] != K_LEAF || p.kind_old[k] != K_BELOW) return;
-  int l, i, j;
-  node_of(g, k, l, i, j);
-  int path[MWDG_LMAX + 1];
-  int d = 0, a = i, b = j, la = l;
-  long long ka = k;
-  while (la > 0 && p.kind_old[ka] == K_BELOW) {
-    path[d++] = (a & 1) + 2 * (b & 1);
-    a >>= 1;
-    b >>= 1;
-    la--;
-    ka = nid(g, la, a, b);
-  }
-  const long long P = g.P;
-  for (int v = 0; v < 3; v++) {
-    T s[3];
-    for (int m = 0; m < 3; m++) s[m] = p.U[(3 * v + m) * P + ka];
-    // the depth plane of the old leaf is prolonged; the free-surface form
-    // then takes the new leaf's own bed slopes
-    if (v == 0) slopes_to_h(s[1], s[2], p.Z[P + ka], p.Z[2 * P + ka]);
-    for (int q = d - 1; q >= 0; q--) {
-      T o[3];
-      prolong3(s[0], s[1], s[2], path[q], o);
-      s[0] = o[0]; s[1] = o[1]; s[2] = o[2];
+__global__ void k_adapt_coarse(Geo g, Ptrs<T> p, int lc) {
+  if (!ADAPT_LIVE(p)) return;
+  for (int l = lc; l >= 0; l--) {
+    long long n = (long long)g.nxl[l] * g.nyl[l];
+    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
+      int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+      adapt_node(g, p, l, i, j);
     }
-    if (v == 0) slopes_from_h(s[1], s[2], p.Z[P + k], p.Z[2 * P + k]);
-    for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = s[m];
+    __syncthreads();
+  }
+  long long n0 = (long long)g.nxl[0] * g.nyl[0];
+  for (long long r = threadIdx.x; r < n0; r += blockDim.x) {
+    int j = (int)(r / g.nxl[0]), i = (int)(r - (long long)j * g.nxl[0]);
+    p.flag2[nid(g, 0, i, j)] = regular_flag(g, p, 0, i, j);
   }
 }
 
-// CFL candidates over the leaves (Courant number applied in k_begin_step)
+// Eq. 10 for the new active set: every new leaf that was below an old leaf
+// takes the prolongation of that leaf's plane (one level at a time, flow in
+// depth form); each block counts its active leaves for the compaction, and
+// every leaf contributes its CFL candidate for the coming step
 template <typename T>
-__global__ void k_leaf_dt(Geo g, Ptrs<T> p) {
+__global__ void k_decode_count(Geo g, Ptrs<T> p) {
   const long long P = g.P;
-  const T gg = (T)g.g, hd = (T)g.hd;
+  const long long base = (long long)blockIdx.x * CTILE;
   const double t = p.ctl->t;
+  int cnt = 0;
   double best = __longlong_as_double(0x7ff0000000000000LL);
-  FOR_LEAVES(p) {
-    long long k = p.leaves[_q];
+  for (int q = 0; q < CPT; q++) {
+    long long k = base + q * TPB + threadIdx.x;
+    if (k >= P || p.kind[k] != K_LEAF) continue;
+    cnt++;
     int l, i, j;
     node_of(g, k, l, i, j);
-    const T dxl = (T)g.dxl[l];
-    T h0 = p.U[k];
-    if (h0 > hd) {
-      T u = p.U[3 * P + k] / h0, v = p.U[6 * P + k] / h0;
-      T c = tsqrt(gg * h0);
-      best = fmin(best, (double)tmin(dxl / (tabs(u) + c), dxl / (tabs(v) + c)));
-    }
-    if (g.inflow_edge >= 0) {
-      for (int e = 0; e < 4; e++) {
-        bool on = (e == 0 && i == 0) || (e == 1 && i == g.nxl[l] - 1) || (e == 2 && j == 0) ||
-                  (e == 3 && j == g.nyl[l] - 1);
-        if (!on) continue;
-        double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, t);
-        if (q > 0.0) {
-          T qt = (T)q;
-          T hc = tcbrt(qt * qt / gg);
-          if (hc > hd) best = fmin(best, (double)(dxl / (qt / hc + tsqrt(gg * hc))));
+    if (p.kind_old[k] == K_BELOW) {
+      int path[MWDG_LMAX + 1];
+      int d = 0, a = i, b = j, la = l;
+      long long ka = k;
+      while (la > 0 && p.kind_old[ka] == K_BELOW) {
+        path[d++] = (a & 1) + 2 * (b & 1);
+        a >>= 1;
+        b >>= 1;
+        la--;
+        ka = nid(g, la, a, b);
+      }
+      for (int v = 0; v < 3; v++) {
+        T sv[3];
+        for (int m = 0; m < 3; m++) sv[m] = p.U[(3 * v + m) * P + ka];
+        if (v == 0) slopes_to_h(sv[1], sv[2], p.Z[P + ka], p.Z[2 * P + ka]);
+        for (int qq = d - 1; qq >= 0; qq--) {
+          T o[3];
+          prolong3(sv[0], sv[1], sv[2], path[qq], o);
+          sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
         }
+        if (v == 0) slopes_from_h(sv[1], sv[2], p.Z[P + k], p.Z[2 * P + k]);
+        for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sv[m];
       }
     }
+    best = fmin(best, leaf_dt_candidate(g, p, l, i, j, p.U[k], p.U[3 * P + k], p.U[6 * P + k], t));
   }
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) atomic_min_pos(&p.ctl->dtmin, best);
+  warp_min_to(&p.ctl->dtmin, best);
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  __shared__ int ws[TPB / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int sum = 0;
+    for (int w = 0; w < TPB / 32; w++) sum += ws[w];
+    p.blk[blockIdx.x] = sum;
+  }
 }
 
 // dt = min(C * min candidate, dt_max, t_end - t) and per-step resets
@@ -548,51 +624,39 @@ static __global__ void k_begin_step(Geo g, Ctl *c) {
   c->dt = dt > 0.0 ? dt : 0.0;
   c->bnd[0] = 0.0;
   c->bnd[1] = 0.0;
+  c->blocks_done = 0u;
+  // the reductions that the last kernel of this step accumulates for the
+  // next; a zero step changes nothing, so the current ones stay valid
+  if (c->dt > 0.0) {
+    c->dtmin = 0x7ff0000000000000ULL;
+    c->vmax[0] = c->vmax[1] = c->vmax[2] = 0ULL;
+  }
 }
 
-static __global__ void k_end_step(Geo g, Ctl *c) {
+// end of a step: mass budget, time and step count (run once, by the last
+// block of the stage-2 update to finish)
+__device__ __forceinline__ void end_step(const Geo &g, Ctl *c) {
   double dt = c->dt;
   if (!(dt > 0.0)) return;
-  double net = 0.5 * dt * (c->bnd[0] + c->bnd[1]);
+  double b0 = atomicAdd(&c->bnd[0], 0.0), b1 = atomicAdd(&c->bnd[1], 0.0);
+  double net = 0.5 * dt * (b0 + b1);
   if (net >= 0.0) c->v_out += net;
   else c->v_in += -net;
   if (c->t < g.rain_t_end && g.rain_rate > 0.0) c->v_rain += g.rain_rate * dt * g.area;
   c->t = c->t + dt;
   c->steps += 1;
-  c->dtmin = 0x7ff0000000000000ULL;
-  c->vmax[0] = c->vmax[1] = c->vmax[2] = 0ULL;
 }
 
-// rain, then split implicit friction (Sect. 2.1.1): linearised backward
-// Euler of dq/dt = -g n^2 |u| q / h^(4/3), the same factor on averages and
-// slopes; dry leaves lose their discharge
+// Split implicit friction (Sect. 2.1.1): the factor of the linearised
+// backward Euler step of dq/dt = -g n^2 |u| q / h^(4/3), applied to the
+// average and slope coefficients of the discharges (rain has been added to
+// the depth first); dry leaves lose their discharge.
 template <typename T>
-__global__ void k_rain_friction(Geo g, Ptrs<T> p) {
-  const long long P = g.P;
-  const double dtd = p.ctl->dt;
-  if (!(dtd > 0.0)) return;
-  const T dt = (T)dtd, gg = (T)g.g, hd = (T)g.hd;
-  const bool rain = p.ctl->t < g.rain_t_end && g.rain_rate > 0.0;
-  const T rdt = (T)(g.rain_rate * dtd);
-  FOR_LEAVES(p) {
-    long long k = p.leaves[_q];
-    T w0 = p.U[k];
-    if (rain) {
-      w0 = w0 + (Form<T>::eta ? rdt : (T)(g.rain_rate) * dt);
-      p.U[k] = w0;
-    }
-    const T h0 = w0;
-    if (h0 > hd) {
-      T u = p.U[3 * P + k] / h0, v = p.U[6 * P + k] / h0;
-      T sp = tsqrt(u * u + v * v);
-      T nm = p.NM[k];
-      T den = T(1) + dt * gg * nm * nm * sp / (h0 * tcbrt(h0));
-      T f = T(1) / den;
-      for (int m = 3; m < 9; m++) p.U[m * P + k] = p.U[m * P + k] * f;
-    } else {
-      for (int m = 3; m < 9; m++) p.U[m * P + k] = T(0);
-    }
-  }
+__device__ __forceinline__ T friction_factor(T h0, T qx0, T qy0, T nm, T dt, T gg) {
+  T u = qx0 / h0, v = qy0 / h0;
+  T sp = tsqrt(u * u + v * v);
+  T den = T(1) + dt * gg * nm * nm * sp / (h0 * tcbrt(h0));
+  return T(1) / den;
 }
 
 // Stage-input limiting of each leaf, giving the stored view Wst (used by
@@ -605,10 +669,17 @@ __global__ void k_rain_friction(Geo g, Ptrs<T> p) {
 // (two-argument minmod where only one exists): on qx and qy always (a dry
 // neighbour has zero discharge), on eta where the leaf and its neighbours
 // are wet.
-template <typename T>
+// With FRIC (stage 1), the stage input is U after rain and friction, which
+// are applied here to the leaf and, for the limiter, to its neighbours'
+// averages (both are pointwise, so every leaf sees the same values).
+template <typename T, bool FRIC>
 __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   const long long P = g.P;
-  const T hd = (T)g.hd, s3 = s3v<T>();
+  const T hd = (T)g.hd, s3 = s3v<T>(), gg = (T)g.g;
+  const double dtd = p.ctl->dt;
+  const T dt = (T)dtd;
+  const bool rain = FRIC && p.ctl->t < g.rain_t_end && g.rain_rate > 0.0;
+  const T rinc = Form<T>::eta ? (T)(g.rain_rate * dtd) : (T)(g.rain_rate) * dt;
   FOR_LEAVES(p) {
     long long k = p.leaves[_q];
     T w[9], zp[3];
@@ -616,6 +687,17 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
     for (int m = 0; m < 9; m++) w[m] = X[m * P + k];
 #pragma unroll
     for (int m = 0; m < 3; m++) zp[m] = p.Z[m * P + k];
+    if (FRIC) {
+      if (rain) w[0] = w[0] + rinc;
+      if (w[0] > hd) {
+        const T f = friction_factor(w[0], w[3], w[6], p.NM[k], dt, gg);
+#pragma unroll
+        for (int m = 3; m < 9; m++) w[m] = w[m] * f;
+      } else {
+#pragma unroll
+        for (int m = 3; m < 9; m++) w[m] = T(0);
+      }
+    }
     const T h0 = w[0];
     const T eta0 = h0 + zp[0];
     T h1x = w[1], h1y = w[2];
@@ -658,6 +740,16 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
           T hC = h0;
           T hA = X[ka];
           T hB = X[kb];
+          if (rain) {
+            hA = hA + rinc;
+            hB = hB + rinc;
+          }
+          // neighbours' friction factors (stage 1), for their discharge averages
+          T fA = T(1), fB = T(1);
+          if (FRIC) {
+            fA = (hA > hd) ? friction_factor(hA, X[3 * P + ka], X[6 * P + ka], p.NM[ka], dt, gg) : T(0);
+            fB = (hB > hd) ? friction_factor(hB, X[3 * P + kb], X[6 * P + kb], p.NM[kb], dt, gg) : T(0);
+          }
           const bool wet = (hC > hd) && (!hasA || hA > hd) && (!hasB || hB > hd);
           const int cs = 1 + dir;
           for (int v = 0; v < 3; v++) {
@@ -673,6 +765,10 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
               aC = w[3 * v];
               a0 = X[3 * v * P + ka];
               aB = X[3 * v * P + kb];
+              if (FRIC) {
+                a0 = (hA > hd) ? a0 * fA : T(0);
+                aB = (hB > hd) ? aB * fB : T(0);
+              }
               slope = w[3 * v + cs];
             }
             T a = s3 * slope, mm;
@@ -700,16 +796,12 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   }
 }
 
-// local encoding (Eq. 9) of the flux view and its beds onto the refined
-// nodes of level l (MWDG2 interfaces, Sect. 2.3)
+// local encoding (Eq. 9) of the flux view and its beds onto a refined node
+// (MWDG2 interfaces, Sect. 2.3)
 template <typename T>
-__global__ void k_encode_view(Geo g, Ptrs<T> p, int l) {
-  long long n = (long long)g.nxl[l] * g.nyl[l];
-  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const long long P = g.P, k = g.off[l] + r;
+__device__ __forceinline__ void encode_view_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
+  const long long P = g.P, k = nid(g, l, i, j);
   if (p.kind[k] != K_SIG) return;
-  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
   long long kc[4];
 #pragma unroll
   for (int c = 0; c < 4; c++) kc[c] = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
@@ -734,6 +826,28 @@ __global__ void k_encode_view(Geo g, Ptrs<T> p, int l) {
     if (v == 0) slopes_from_h(sp[1], sp[2], zpar[1], zpar[2]);
 #pragma unroll
     for (int m = 0; m < 3; m++) X[m * P + k] = sp[m];
+  }
+}
+
+template <typename T>
+__global__ void k_encode_view(Geo g, Ptrs<T> p, int l) {
+  long long n = (long long)g.nxl[l] * g.nyl[l];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+  encode_view_node(g, p, l, i, j);
+}
+
+// levels lc..0 in one block, barrier between levels
+template <typename T>
+__global__ void k_encode_view_coarse(Geo g, Ptrs<T> p, int lc) {
+  for (int l = lc; l >= 0; l--) {
+    long long n = (long long)g.nxl[l] * g.nyl[l];
+    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
+      int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
+      encode_view_node(g, p, l, i, j);
+    }
+    __syncthreads();
   }
 }
 
@@ -823,12 +937,17 @@ template <typename T, int STAGE>
 __global__ void k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out) {
   const long long P = g.P;
   const double dtd = p.ctl->dt;
-  if (!(dtd > 0.0)) return;
+  if (!(dtd > 0.0)) return;  // a zero step changes nothing (end_step ignores it too)
   const T dt = (T)dtd, gg = (T)g.g, hd = (T)g.hd, s3 = s3v<T>();
   const double tf = (STAGE == 1) ? p.ctl->t : p.ctl->t + dtd;
   double bsum = 0.0, csum = 0.0;
   unsigned long long ncl = 0;
   bool bad = false;
+  // stage 2 also reduces, over the new state, what the next step needs:
+  // max |v0| (adaptive: the next encode's normalisation) or the CFL
+  // candidate (fixed grids: the next time step)
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  double best = __longlong_as_double(0x7ff0000000000000LL);
   FOR_LEAVES(p) {
     long long k = p.leaves[_q];
     int l, i, j;
@@ -964,6 +1083,15 @@ __global__ void k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T 
       Out[m * P + k] = o[m];
     }
     bsum += bout;
+    if (STAGE == 2) {
+      if (g.mode == MWDG_ADAPTIVE) {
+        m0 = fmax(m0, (double)tabs(o[0]));
+        m1 = fmax(m1, (double)tabs(o[3]));
+        m2 = fmax(m2, (double)tabs(o[6]));
+      } else {
+        best = fmin(best, leaf_dt_candidate(g, p, l, i, j, o[0], o[3], o[6], tf));
+      }
+    }
   }
   if (bad) p.ctl->nonfinite = 1;
   for (int o = 16; o > 0; o >>= 1) {
@@ -976,6 +1104,33 @@ __global__ void k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T 
     if (ncl) {
       atomicAdd(&p.ctl->n_clip, ncl);
       atomicAdd(&p.ctl->v_clip, csum);
+    }
+  }
+  if (STAGE == 2) {
+    if (g.mode == MWDG_ADAPTIVE) {
+      for (int o = 16; o > 0; o >>= 1) {
+        m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(&p.ctl->vmax[0], m0);
+        atomic_max_pos(&p.ctl->vmax[1], m1);
+        atomic_max_pos(&p.ctl->vmax[2], m2);
+      }
+    } else {
+      warp_min_to(&p.ctl->dtmin, best);
+    }
+    // the last block to finish closes the step (no waiting: each block takes
+    // a ticket after its own atomics are visible)
+    if ((threadIdx.x & 31) == 0) __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = (atomicAdd(&p.ctl->blocks_done, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+      __threadfence();
+      end_step(g, p.ctl);
     }
   }
 }
@@ -1174,28 +1329,47 @@ int Launch<T>::compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
   return 3;
 }
 
+// coarsest levels handled by one block of the MRA kernels (levels with at
+// most g.coarse_nodes nodes)
+constexpr int COARSE_TPB = 1024;
+inline int coarse_top(const Geo &g) {
+  int lc = -1;
+  while (lc + 1 < g.L && lvl(g, lc + 1) <= g.coarse_nodes) lc++;
+  return lc;  // levels 0..lc in one block (-1: none)
+}
+
 template <typename T>
-int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int decode_only, cudaStream_t st,
+int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_maxabs, cudaStream_t st,
                      void (*mark)(void *, int), void *mark_arg) {
   int n = 0;
   const int grid = (int)std::min<long long>(nblk(g.P), 152 * 8);
-  if (!decode_only) {
-    MARK(KC_ENCODE);
+  MARK(KC_ENCODE);
+  if (with_maxabs) {
     k_leaf_maxabs<T><<<grid, TPB, 0, st>>>(g, p);
     n++;
-    for (int l = g.L - 1; l >= 0; l--, n++) k_encode_flow<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
   }
+  // bottom-up: encode + significance of level l, regularised flags of l+1
+  const int lc = coarse_top(g);
+  for (int l = g.L - 1; l > lc; l--, n++) k_adapt_level<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+  k_adapt_coarse<T><<<1, COARSE_TPB, 0, st>>>(g, p, lc);
+  n++;
   if (encode_only) return n;
   MARK(KC_FLAGS);
-  for (int l = 0; l < g.L; l++, n++) k_predict<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
-  n += closure(g, p.flag2, st);
   n += kinds(g, p, p.flag2, 1, st);
   MARK(KC_DECODE);
-  k_decode_new<T><<<nblk(g.P), TPB, 0, st>>>(g, p);
-  n++;
+  const int nb = (int)((g.P + CTILE - 1) / CTILE);
+  k_decode_count<T><<<nb, TPB, 0, st>>>(g, p);
   MARK(KC_COMPACT);
-  n += compact(g, p, st);
-  return n;
+  k_compact_scan<<<1, 1024, 0, st>>>(nb, p.blk, p.nleaf);
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk, p.leaves);
+  return n + 3;
+}
+
+template <typename T>
+int Launch<T>::prime(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st) {
+  k_leaf_maxabs<T><<<grid_leaves, TPB, 0, st>>>(g, p);
+  k_leaf_dt<T><<<grid_leaves, TPB, 0, st>>>(g, p);
+  return 2;
 }
 
 template <typename T>
@@ -1209,22 +1383,22 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
                     void (*mark)(void *, int), void *mark_arg) {
   int n = 0;
   const bool view = (g.mode == MWDG_ADAPTIVE);
-  MARK(KC_DT);
-  k_leaf_dt<T><<<grid_leaves, TPB, 0, st>>>(g, p);
+  const int lc = coarse_top(g);
   MARK(KC_CONTROL);
   k_begin_step<<<1, 1, 0, st>>>(g, p.ctl);
-  MARK(KC_FRICTION);
-  k_rain_friction<T><<<grid_leaves, TPB, 0, st>>>(g, p);
-  n += 3;
+  n++;
   for (int stage = 1; stage <= 2; stage++) {
-    const T *X = (stage == 1) ? p.U : p.Ui;
-    T *Wst = (stage == 1) ? p.Wn : p.Wi;
     MARK(KC_LIMIT);
-    k_leaf_limit<T><<<grid_leaves, TPB, 0, st>>>(g, p, X, Wst);
+    if (stage == 1) k_leaf_limit<T, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+    else k_leaf_limit<T, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
     n++;
     if (view) {
       MARK(KC_VIEW);
-      for (int l = g.L - 1; l >= 0; l--, n++) k_encode_view<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+      for (int l = g.L - 1; l > lc; l--, n++) k_encode_view<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+      if (lc >= 0) {
+        k_encode_view_coarse<T><<<1, COARSE_TPB, 0, st>>>(g, p, lc);
+        n++;
+      }
     }
     if (stage == 1) {
       MARK(KC_UPDATE1);
@@ -1235,9 +1409,6 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
     }
     n++;
   }
-  MARK(KC_CONTROL);
-  k_end_step<<<1, 1, 0, st>>>(g, p.ctl);
-  n++;
   MARK(-1);
   return n;
 }

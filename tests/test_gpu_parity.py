@@ -112,6 +112,27 @@ def test_adaptive_valley_f64():
     assert (c[:, 0] > 1e-3).sum() > 20  # the flood has entered
 
 
+@pytest.mark.parametrize("mode", [S.UNIFORM, S.STATIC, S.ADAPTIVE])
+def test_graph_replay_on_own_stream_f64(mode):
+    """On a non-default stream each step is one captured CUDA graph replay;
+    the results are those of the oracle (and of direct launches)."""
+    import torch
+    st = torch.cuda.Stream()
+    p = S.valley(n=128, L=7, mode=mode, eps=1e-2, peak_Q=200.0, t_peak=100.0)
+    g, o = gpu_sim(p, stream=st.cuda_stream), oracle_sim(p)
+    for k in range(60):
+        dg = g.dg2_step()
+        do = o.step()
+        assert abs(dg - do) <= 1e-9 * do, (k, dg, do)
+    assert_same_leaves(g, o, what="after 60 graph steps")
+    # a run of queued steps without host synchronisation, then the budget
+    g.run_steps(20)
+    for _ in range(20):
+        o.step()
+    assert_same_leaves(g, o, what="after 20 queued steps")
+    assert g.launch_count() > 0
+
+
 def test_adaptive_lake_at_rest_islands_f64():
     p = S.lake_at_rest(n=64, L=4, islands=True, mode=S.ADAPTIVE, eps=1e-2)
     g, o = run_parity(p, 40, check_every=10)
