@@ -38,7 +38,7 @@ WORKLOAD = "MWDG2 1024x1024 fractal valley, dx=10 m, L=10, eps=1e-3, n=0.035, 40
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--spinup", type=float, default=1800.0, help="simulated seconds before timing")
@@ -146,16 +146,20 @@ def make_solver(p, precision, stream):
     return M.solver_from_problem(p, precision=precision, stream=stream)
 
 
-def timed_steps(solver, K, W, flush, stream, prof=False):
+def timed_steps(solver, K, W, flush, stream, prof=False, profiler_range=False):
     """W untimed steps, then K steps each bracketed by CUDA events on the
-    solver's stream with an L2 flush before each; returns (ms list, updates
-    list, launches in the timed region, kernel times)."""
+    solver's stream with an L2 flush before each (no host synchronisation
+    inside the loop); returns (ms per step, active-leaf updates, launches in
+    the timed region, kernel times).  With profiler_range the K steps are the
+    range an external profiler started with --profile-from-start off records."""
     import torch
     for _ in range(W):
         solver.run_steps(1)
     torch.cuda.synchronize()
-    ms, upd = [], []
+    _, u0 = solver.get_counters()
     l0 = solver.launch_count()
+    if profiler_range:
+        torch.cuda.profiler.start()
     if prof:
         solver.profile(True)
     evs = []
@@ -167,16 +171,31 @@ def timed_steps(solver, K, W, flush, stream, prof=False):
         solver.run_steps(1)
         b.record(stream)
         evs.append((a, b))
-        b.synchronize()
-        upd.append(solver.n_active())
     torch.cuda.synchronize()
-    for a, b in evs:
-        ms.append(a.elapsed_time(b))
+    if profiler_range:
+        torch.cuda.profiler.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    _, u1 = solver.get_counters()
     kt = solver.kernel_times() if prof else {}
     if prof:
         solver.profile(False)
     launches = solver.launch_count() - l0
-    return ms, upd, launches, kt
+    return ms, u1 - u0, launches, kt
+
+
+def reduce_over_ranks(total_ms, updates, world, device):
+    """Whole-job figures of independent replicas: the slowest rank's timed
+    milliseconds and the updates of all ranks (no data-path collective; the
+    replicas exchange only these two numbers)."""
+    if world <= 1:
+        return float(total_ms), float(updates)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], device=device, dtype=torch.float64)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def run_gpu(args, rank, world):
@@ -201,32 +220,32 @@ def run_gpu(args, rank, world):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with Clocks(dev) as clk:
-        ms, upd, launches, kt = timed_steps(s32, args.steps, args.warmup, flush, stream, prof=True)
+        ms, upd, launches, _ = timed_steps(s32, args.steps, args.warmup, flush, stream, prof=False,
+                                           profiler_range=True)
+    # per-kernel durations: steps again with CUDA events between the kernels
+    # on the solver's stream (direct launches)
+    kms, kupd, _, kt = timed_steps(s32, min(args.steps, 200), 0, flush, stream, prof=True)
     total_ms = sum(ms)
-    updates = sum(upd)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([float(updates)], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
-        updates_all = float(u.item())
-    else:
-        updates_all = float(updates)
+    updates = upd
+    total_ms, updates_all = reduce_over_ranks(total_ms, updates, world, "cuda")
     value = updates_all / (total_ms * 1e-3)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: the kernel with the longest average
+    # launch (each MRA level is its own launch)
     peak_gbs, peak_kind = peaks()
-    dom = max(kt.items(), key=lambda kv: kv[1][0]) if kt else ("?", (0.0, 0))
-    dom_name, (dom_ms, dom_n) = dom
-    mean_leaves = float(np.mean(upd))
+    per_launch = {k: v[0] / v[1] for k, v in kt.items() if v[1]}
+    dom_name = max(per_launch, key=per_launch.get)
+    dom_ms, dom_n = kt[dom_name]
+    mean_leaves = kupd / len(kms)
     bpl = kernel_bytes_per_leaf(dom_name, 4)
-    achieved = (bpl * mean_leaves) / (dom_ms / max(dom_n, 1) * 1e-3) / 1e9 if dom_n else None
+    achieved = (bpl * mean_leaves) / (dom_ms / dom_n * 1e-3) / 1e9 if bpl else None
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs,
                 "unit": "GB/s", "frac": (achieved / peak_gbs) if achieved else None,
-                "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_leaf": bpl, "share_of_step": dom_ms / max(sum(v[0] for v in kt.values()), 1e-9),
-                "kernel_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in kt.items() if v[1]}}
+                "traffic": TRAFFIC.get(dom_name), "peak_kind": peak_kind,
+                "algorithmic_bytes_per_leaf": bpl, "launches": dom_n,
+                "share_of_step": dom_ms / max(sum(v[0] for v in kt.values()), 1e-9),
+                "step_ms_by_class": {k: round(v[0] / len(kms), 5) for k, v in kt.items() if v[1]},
+                "ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()}}
 
     # end to end through the public API: resume from a host checkpoint in
     # pinned memory, K steps, depth and velocity maps back to the host
@@ -236,9 +255,10 @@ def run_gpu(args, rank, world):
     t0 = time.perf_counter()
     s32.load_state(pinned)
     n_e2e = 0
-    for _ in range(args.steps):
-        s32.run_steps(1)
-        n_e2e += s32.n_active()
+    _, u0 = s32.get_counters()
+    s32.run_steps(args.steps)
+    _, u1 = s32.get_counters()
+    n_e2e = u1 - u0
     import ctypes as C
     st = s32._lib.mwdg_read_fields(s32._h, *(C.cast(C.c_void_p(b.data_ptr()), C.POINTER(C.c_double)) for b in hbuf))
     if st:
@@ -250,7 +270,7 @@ def run_gpu(args, rank, world):
            "what": "mwdg_load_state from pinned host checkpoint + K x mwdg_dg2_step + mwdg_read_fields to pinned host"}
 
     out = {"value": value, "ms_per_step": total_ms / len(ms), "updates": updates_all,
-           "mean_active": mean_leaves, "roofline": roofline, "clocks": clk.summary(), "e2e": e2e,
+           "mean_active": updates / len(ms), "roofline": roofline, "clocks": clk.summary(), "e2e": e2e,
            "gpu_launches": int(launches) * world, "t_spinup": t_spin}
 
     # FP64 path and FP32-vs-FP64 accuracy at the same simulated time
@@ -258,7 +278,7 @@ def run_gpu(args, rank, world):
         s64 = make_solver(p, M.F64, sptr)
         s64.run_to_time(args.spinup)
         ms64, upd64, _, _ = timed_steps(s64, max(4, args.steps // 4), 2, flush, stream)
-        out["fp64"] = {"value": sum(upd64) / (sum(ms64) * 1e-3), "unit": UNIT,
+        out["fp64"] = {"value": upd64 / (sum(ms64) * 1e-3), "unit": UNIT,
                        "ms_per_step": sum(ms64) / len(ms64), "dtype": "f64"}
         tcmp = max(s64.get_time()[0], s32.get_time()[0]) + 1.0
         s32.run_to_time(tcmp)
@@ -308,17 +328,22 @@ def reference_arm(args):
 
 
 def kernel_bytes_per_leaf(name, ts):
-    """Algorithmic HBM bytes per active leaf of each kernel class (values of
-    ts bytes; neighbour reads served from L2 are not counted)."""
+    """Algorithmic HBM bytes per active leaf of a kernel class (values of ts
+    bytes plus the 8-byte active-list entry; neighbour reads served from L2
+    are not counted).  MRA classes are per node, not per leaf: None."""
     vals = {
-        "dg2_update_stage1": 9 + 3 + 9 + 1 + 9,      # F, Ze, Wn, z0 read; Ui written
-        "dg2_update_stage2": 9 + 3 + 9 + 9 + 1 + 9,  # F, Ze, Wi, Wn, z0 read; U written
-        "limit": 9 + 3 + 9 + 9 + 3,                  # X, Z read; Wst, F, Ze written
-        "friction": 9 + 1 + 7,                       # U, n read; q (6) + eta0 written
-        "dt_reduce": 4,
-        "mra_encode": 9 + 3,
+        "dg2_update_stage1": 9 + 3 + 9 + 9,      # F, Ze, Wn read; Ui written
+        "dg2_update_stage2": 9 + 3 + 9 + 9 + 9,  # F, Ze, Wi, Wn read; U written
+        "limit": 9 + 3 + 9 + 9 + 3,              # X, Z read; Wst, F, Ze written
     }
-    return vals.get(name, 0) * ts + (4 if name.startswith("dg2") or name == "limit" else 0)
+    if name not in vals:
+        return None
+    return vals[name] * ts + 8
+
+
+# DRAM bytes (read + write) per launch measured by ncu for a kernel, when the
+# kernel has not changed since (see profiles/); None otherwise
+TRAFFIC = {"dg2_update_stage2": 55_167_744 + 2_086_912}  # profiles/k_leaf_update_valley1024_f32.md
 
 
 def main():

@@ -166,6 +166,10 @@ MWDG_API mwdg_status mwdg_read_active(mwdg_ctx *ctx, int32_t *level, int32_t *i,
                              int64_t cap, int64_t *n);
 
 MWDG_API mwdg_status mwdg_get_time(mwdg_ctx *ctx, double *t, int64_t *steps);
+/* Steps taken and active-leaf updates (one leaf advanced one step) summed
+ * over them since mwdg_load_initial; either pointer may be NULL.
+ * Synchronises. */
+MWDG_API mwdg_status mwdg_get_counters(mwdg_ctx *ctx, int64_t *steps, int64_t *updates);
 
 /* Volume sum over active leaves of h0 * area (FP64, fixed summation order)
  * and the mass budget terms since mwdg_load_initial: boundary inflow and

@@ -21,7 +21,7 @@ EXPORTS = (
     "mwdg_read_fields", "mwdg_read_fields_dev", "mwdg_read_active", "mwdg_get_time",
     "mwdg_get_volume", "mwdg_profile", "mwdg_kernel_times", "mwdg_launch_count",
     "mwdg_last_error", "mwdg_status_string", "mwdg_state_bytes", "mwdg_save_state",
-    "mwdg_load_state", "mwdg_volume_noalloc",
+    "mwdg_load_state", "mwdg_volume_noalloc", "mwdg_get_counters",
 )
 
 
@@ -74,6 +74,7 @@ def lib(build: bool = True):
         "mwdg_read_fields_dev": [vp, vp, vp, vp],
         "mwdg_read_active": [vp, ip, ip, ip, dp, C.c_int64, lp],
         "mwdg_get_time": [vp, dp, lp],
+        "mwdg_get_counters": [vp, lp, lp],
         "mwdg_get_volume": [vp, dp, dp, dp, dp, dp, lp],
         "mwdg_profile": [vp, C.c_int32],
         "mwdg_kernel_times": [vp, C.POINTER(C.c_char_p), dp, lp, C.c_int32, ip],
@@ -233,6 +234,12 @@ class Solver:
         t, s = C.c_double(), C.c_int64()
         self._ck(self._lib.mwdg_get_time(self._h, C.byref(t), C.byref(s)), "mwdg_get_time")
         return t.value, s.value
+
+    def get_counters(self):
+        """(steps, active-leaf updates) since the initial state"""
+        s, u = C.c_int64(), C.c_int64()
+        self._ck(self._lib.mwdg_get_counters(self._h, C.byref(s), C.byref(u)), "mwdg_get_counters")
+        return s.value, u.value
 
     def get_volume(self) -> dict:
         v = [C.c_double() for _ in range(5)]

@@ -748,6 +748,16 @@ mwdg_status mwdg_get_time(mwdg_ctx *c, double *t, int64_t *steps) {
   return MWDG_OK;
 }
 
+mwdg_status mwdg_get_counters(mwdg_ctx *c, int64_t *steps, int64_t *updates) {
+  LIVE(c);
+  Ctl h;
+  mwdg_status s = read_ctl(c, &h);
+  if (s) return s;
+  if (steps) *steps = h.steps;
+  if (updates) *updates = h.updates;
+  return MWDG_OK;
+}
+
 mwdg_status mwdg_get_volume(mwdg_ctx *c, double *V, double *V_in, double *V_out, double *V_rain,
                             double *V_clip, int64_t *n_clip) {
   LIVE(c);

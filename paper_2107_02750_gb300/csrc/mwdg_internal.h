@@ -19,6 +19,7 @@ struct Ctl {
   double volume;
   unsigned long long n_clip;
   long long steps;
+  long long updates;           // active leaves advanced, summed over steps
   int nonfinite;
   int changed;                 // grading sweep made a change
   unsigned int blocks_done;    // completion tickets of the last kernel of a step
@@ -54,7 +55,8 @@ struct Ptrs {
   T *NM;    // Manning n per node (1)
   double *DZ;   // normalised topography detail per node
   uint8_t *kind, *kind_old, *flag, *flag2;
-  int *leaves, *nleaf;
+  long long *leaves;  // active leaves, packed (level << 56 | j << 28 | i)
+  int *nleaf;
   int *blk;         // compaction scratch: per-block counts / offsets
   double *part;     // volume partial sums
   Ctl *ctl;

@@ -60,6 +60,16 @@ __device__ __forceinline__ void node_of(const Geo &g, long long k, int &l, int &
 __device__ __forceinline__ long long nid(const Geo &g, int l, int i, int j) {
   return g.off[l] + (long long)j * g.nxl[l] + i;
 }
+// active-list entries carry the leaf's level and indices
+__device__ __forceinline__ long long pack_leaf(int l, int i, int j) {
+  return ((long long)l << 56) | ((long long)j << 28) | (long long)i;
+}
+__device__ __forceinline__ long long unpack_leaf(const Geo &g, long long v, int &l, int &i, int &j) {
+  l = (int)(v >> 56);
+  j = (int)((v >> 28) & 0xFFFFFFFLL);
+  i = (int)(v & 0xFFFFFFFLL);
+  return nid(g, l, i, j);
+}
 
 // ---------------------------------------------------------------------------
 // Set-up
@@ -326,7 +336,8 @@ static __global__ void k_compact_scan(int nb, int *blk, int *total) {
   if (threadIdx.x == 0) *total = carry;
 }
 
-static __global__ void k_compact_scatter(long long P, const uint8_t *kind, const int *blk, int *leaves) {
+static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *blk, long long *leaves) {
+  const long long P = g.P;
   long long base = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
   int c = 0;
   for (int q = 0; q < CPT; q++) {
@@ -354,7 +365,11 @@ static __global__ void k_compact_scatter(long long P, const uint8_t *kind, const
   int pos = blk[blockIdx.x] + x - c + ((threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0);
   for (int q = 0; q < CPT; q++) {
     long long k = base + q;
-    if (k < P && kind[k] == K_LEAF) leaves[pos++] = (int)k;
+    if (k < P && kind[k] == K_LEAF) {
+      int l, i, j;
+      node_of(g, k, l, i, j);
+      leaves[pos++] = pack_leaf(l, i, j);
+    }
   }
 }
 
@@ -400,7 +415,8 @@ __global__ void k_leaf_maxabs(Geo g, Ptrs<T> p) {
   double m0 = 0, m1 = 0, m2 = 0;
   const long long P = g.P;
   FOR_LEAVES(p) {
-    long long k = p.leaves[_q];
+    int l, i, j;
+    long long k = unpack_leaf(g, p.leaves[_q], l, i, j);
     T h0 = p.U[k];
     m0 = fmax(m0, (double)tabs(h0));
     m1 = fmax(m1, (double)tabs(p.U[3 * P + k]));
@@ -460,9 +476,8 @@ __global__ void k_leaf_dt(Geo g, Ptrs<T> p) {
   const double t = p.ctl->t;
   double best = __longlong_as_double(0x7ff0000000000000LL);
   FOR_LEAVES(p) {
-    long long k = p.leaves[_q];
     int l, i, j;
-    node_of(g, k, l, i, j);
+    long long k = unpack_leaf(g, p.leaves[_q], l, i, j);
     best = fmin(best, leaf_dt_candidate(g, p, l, i, j, p.U[k], p.U[3 * P + k], p.U[6 * P + k], t));
   }
   warp_min_to(&p.ctl->dtmin, best);
@@ -616,7 +631,7 @@ __global__ void k_decode_count(Geo g, Ptrs<T> p) {
 }
 
 // dt = min(C * min candidate, dt_max, t_end - t) and per-step resets
-static __global__ void k_begin_step(Geo g, Ctl *c) {
+static __global__ void k_begin_step(Geo g, Ctl *c, const int *nleaf) {
   double best = __longlong_as_double((long long)c->dtmin);
   double dt = g.dt_max;
   if (best < __longlong_as_double(0x7ff0000000000000LL)) dt = fmin(dt, g.cfl * best);
@@ -628,6 +643,7 @@ static __global__ void k_begin_step(Geo g, Ctl *c) {
   // the reductions that the last kernel of this step accumulates for the
   // next; a zero step changes nothing, so the current ones stay valid
   if (c->dt > 0.0) {
+    c->updates += *nleaf;
     c->dtmin = 0x7ff0000000000000ULL;
     c->vmax[0] = c->vmax[1] = c->vmax[2] = 0ULL;
   }
@@ -681,7 +697,8 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   const bool rain = FRIC && p.ctl->t < g.rain_t_end && g.rain_rate > 0.0;
   const T rinc = Form<T>::eta ? (T)(g.rain_rate * dtd) : (T)(g.rain_rate) * dt;
   FOR_LEAVES(p) {
-    long long k = p.leaves[_q];
+    int l, i, j;
+    long long k = unpack_leaf(g, p.leaves[_q], l, i, j);
     T w[9], zp[3];
 #pragma unroll
     for (int m = 0; m < 9; m++) w[m] = X[m * P + k];
@@ -728,8 +745,6 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
 #pragma unroll
       for (int m = 0; m < 9; m++) ws[m] = w[m];
       ze[0] = zp[0]; ze[1] = zp[1]; ze[2] = zp[2];
-      int l, i, j;
-      node_of(g, k, l, i, j);
       if (g.limiter) {
         for (int dir = 0; dir < 2; dir++) {
           const int ia = i + (dir == 0), ja = j + (dir == 1), ib = i - (dir == 0), jb = j - (dir == 1);
@@ -927,14 +942,202 @@ __device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, i
   return true;
 }
 
+// Interface f of a leaf: its own limit, the neighbour's (same-level view or
+// boundary ghost), both revised, and the HLL flux in (h, qx, qy) order.
+template <typename T>
+struct FaceOut {
+  T F0, F1, F2;       // numerical flux
+  T hs, us, vs, zr;   // own revised limit
+  double bout;        // outward boundary mass flux (m^3/s), 0 inside
+};
+
+template <typename T>
+__device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
+                                                const T (&w)[9], const T (&zc)[3], int f, double tf) {
+  const T gg = (T)g.g, hd = (T)g.hd;
+  T own[4], nb[4];
+  own[0] = first_face(w[0], w[1], w[2], zc[0], f);
+  own[1] = face_value(w[3], w[4], w[5], f);
+  own[2] = face_value(w[6], w[7], w[8], f);
+  own[3] = face_value(zc[0], zc[1], zc[2], f);
+  const bool inside = nbr_limit(g, p, l, i, j, f, nb);
+  if (!inside) {
+    // ghost: wall mirror, open copy, or critical-depth inflow
+    const int e = (f == 0) ? 1 : (f == 1) ? 0 : (f == 2) ? 3 : 2;
+    double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, tf);
+    nb[3] = own[3];
+    if (q > 0.0) {
+      T qt = (T)q;
+      T hc = tcbrt(qt * qt / gg);
+      T hown = Form<T>::eta ? own[0] - own[3] : own[0];
+      T hg = tmax(hown, hc);
+      nb[0] = Form<T>::eta ? hg + own[3] : hg;
+      T qn = (e == 0 || e == 2) ? qt : -qt;
+      if (e < 2) { nb[1] = qn; nb[2] = T(0); }
+      else { nb[1] = T(0); nb[2] = qn; }
+    } else if (g.bc[e] == MWDG_OPEN) {
+      nb[0] = own[0]; nb[1] = own[1]; nb[2] = own[2];
+    } else {
+      nb[0] = own[0];
+      if (e < 2) { nb[1] = -own[1]; nb[2] = own[2]; }
+      else { nb[1] = own[1]; nb[2] = -own[2]; }
+    }
+  }
+  const T zf = tmax(own[3], nb[3]);
+  Side<T> so, sn;
+  if (Form<T>::eta) {
+    so = revise_eta(own[0], own[1], own[2], own[3], zf, hd);
+    sn = revise_eta(nb[0], nb[1], nb[2], nb[3], zf, hd);
+  } else {
+    so = revise_h(own[0], own[1], own[2], own[3], zf, hd);
+    sn = revise_h(nb[0], nb[1], nb[2], nb[3], zf, hd);
+  }
+  FaceOut<T> o;
+  o.hs = so.hs; o.us = so.u; o.vs = so.v; o.zr = so.zr;
+  T F3[3];
+  if (f == 0) {
+    hll(so.hs, so.u, so.v, sn.hs, sn.u, sn.v, gg, hd, F3);
+    o.F0 = F3[0]; o.F1 = F3[1]; o.F2 = F3[2];
+  } else if (f == 1) {
+    hll(sn.hs, sn.u, sn.v, so.hs, so.u, so.v, gg, hd, F3);
+    o.F0 = F3[0]; o.F1 = F3[1]; o.F2 = F3[2];
+  } else if (f == 2) {
+    hll(so.hs, so.v, so.u, sn.hs, sn.v, sn.u, gg, hd, F3);
+    o.F0 = F3[0]; o.F1 = F3[2]; o.F2 = F3[1];
+  } else {
+    hll(sn.hs, sn.v, sn.u, so.hs, so.v, so.u, gg, hd, F3);
+    o.F0 = F3[0]; o.F1 = F3[2]; o.F2 = F3[1];
+  }
+  o.bout = 0.0;
+  if (!inside) {
+    double outward = (f == 0 || f == 2) ? (double)o.F0 : -(double)o.F0;
+    o.bout = outward * g.dxl[l];
+  }
+  return o;
+}
+
+// The operator and update of variable v (0 h, 1 qx, 2 qy) of one leaf from
+// its four interfaces (flux component v, own revised limits): L0 from the
+// flux difference and the bed source with the revised interface beds, the
+// slopes from the two-point interface rule with the bed source
+// S1 = -(2 sqrt3 g / dx) h1 (h1 + z1) that cancels its hydrostatic error at
+// rest, then Eq. 4a (STAGE 1) or Eq. 4b (STAGE 2).
+template <typename T, int STAGE>
+__device__ __forceinline__ void finish_var(const Geo &g, const Ptrs<T> &p, int v, long long k, int l,
+                                           const T (&w)[9], const T (&zc)[3], const T (&Fv)[4],
+                                           const T (&hs)[4], const T (&us)[4], const T (&vs)[4],
+                                           const T (&zr)[4], T dt, const T *Wst, const T *Wcomb,
+                                           T &o0, T &o1, T &o2) {
+  const long long P = g.P;
+  const T gg = (T)g.g, s3 = s3v<T>();
+  const T dxl = (T)g.dxl[l];
+  // physical fluxes of the own revised limits, component v
+  T Fx0, Fx1, Gy0, Gy1;
+  {
+    T q0 = hs[0] * us[0], q1 = hs[1] * us[1], r2 = hs[2] * vs[2], r3 = hs[3] * vs[3];
+    if (v == 0) {
+      Fx0 = q0; Fx1 = q1; Gy0 = r2; Gy1 = r3;
+    } else if (v == 1) {
+      Fx0 = q0 * us[0] + T(0.5) * gg * hs[0] * hs[0];
+      Fx1 = q1 * us[1] + T(0.5) * gg * hs[1] * hs[1];
+      Gy0 = r2 * us[2];
+      Gy1 = r3 * us[3];
+    } else {
+      Fx0 = q0 * vs[0];
+      Fx1 = q1 * vs[1];
+      Gy0 = r2 * vs[2] + T(0.5) * gg * hs[2] * hs[2];
+      Gy1 = r3 * vs[3] + T(0.5) * gg * hs[3] * hs[3];
+    }
+  }
+  // slopes of the depth for the bed source: h1 and eta1 = h1 + z1
+  T h1x, h1y, e1x, e1y;
+  if (Form<T>::eta) {
+    e1x = w[1]; e1y = w[2];
+    h1x = w[1] - zc[1]; h1y = w[2] - zc[2];
+  } else {
+    h1x = w[1]; h1y = w[2];
+    e1x = w[1] + zc[1]; e1y = w[2] + zc[2];
+  }
+  T L0 = -(Fv[0] - Fv[1]) / dxl - (Fv[2] - Fv[3]) / dxl;
+  if (v == 1) L0 = L0 + -gg * T(0.5) * (hs[0] + hs[1]) * (zr[0] - zr[1]) / dxl;
+  if (v == 2) L0 = L0 + -gg * T(0.5) * (hs[2] + hs[3]) * (zr[2] - zr[3]) / dxl;
+  T L1x = -(s3 / dxl) * (Fv[0] + Fv[1] - Fx0 - Fx1);
+  T L1y = -(s3 / dxl) * (Fv[2] + Fv[3] - Gy0 - Gy1);
+  if (v == 1) L1x = L1x + -(T(2) * s3 * gg / dxl) * h1x * e1x;
+  if (v == 2) L1y = L1y + -(T(2) * s3 * gg / dxl) * h1y * e1y;
+  const long long b0 = (long long)(3 * v) * P + k;
+  if (STAGE == 1) {
+    o0 = Wst[b0] + dt * L0;
+    o1 = Wst[b0 + P] + dt * L1x;
+    o2 = Wst[b0 + 2 * P] + dt * L1y;
+  } else {
+    o0 = T(0.5) * (Wcomb[b0] + Wst[b0] + dt * L0);
+    o1 = T(0.5) * (Wcomb[b0 + P] + Wst[b0 + P] + dt * L1x);
+    o2 = T(0.5) * (Wcomb[b0 + 2 * P] + Wst[b0 + 2 * P] + dt * L1y);
+  }
+}
+
+// positivity clip (h, counted) and dry reset of variable v given the
+// leaf's updated depth average h0n
+template <typename T>
+__device__ __forceinline__ void post_var(const Geo &g, const Ptrs<T> &p, int v, long long k, int l, T h0n,
+                                         T &o0, T &o1, T &o2, unsigned long long &ncl, double &csum,
+                                         bool &bad) {
+  const long long P = g.P;
+  const T h0c = (h0n < T(0)) ? T(0) : h0n;
+  const bool dry = !(h0c > (T)g.hd);
+  if (v == 0) {
+    if (h0n < T(0)) {
+      ncl++;
+      csum += -(double)h0n * (g.dxl[l] * g.dxl[l]);
+      o0 = T(0);
+    }
+    if (dry) {  // flat zero depth (free-surface slopes = bed slopes)
+      o1 = Form<T>::eta ? p.Z[P + k] : T(0);
+      o2 = Form<T>::eta ? p.Z[2 * P + k] : T(0);
+    }
+  } else if (dry) {
+    o0 = o1 = o2 = T(0);
+  }
+  if (!isfinite(o0) || !isfinite(o1) || !isfinite(o2)) bad = true;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_var(long long P, int v, long long k, T *Out, T o0, T o1, T o2) {
+  const long long b0 = (long long)(3 * v) * P + k;
+  Out[b0] = o0;
+  Out[b0 + P] = o1;
+  Out[b0 + 2 * P] = o2;
+}
+
+// what the next step needs from the new state: max |v0| (adaptive) or the
+// CFL candidate (fixed grids)
+template <typename T>
+__device__ __forceinline__ void next_step_reduce(const Geo &g, const Ptrs<T> &p, int l, int i, int j, T h0,
+                                                 T qx0, T qy0, double tf, double &m0, double &m1,
+                                                 double &m2, double &best) {
+  if (g.mode == MWDG_ADAPTIVE) {
+    m0 = fmax(m0, (double)tabs(h0));
+    m1 = fmax(m1, (double)tabs(qx0));
+    m2 = fmax(m2, (double)tabs(qy0));
+  } else {
+    best = fmin(best, leaf_dt_candidate(g, p, l, i, j, h0, qx0, qy0, tf));
+  }
+}
+
 // One RK2 stage on every leaf (Eq. 4a for STAGE 1, Eq. 4b for STAGE 2):
 // the DG2 operator L = [L0, L1x, L1y] from the flux view (interface fluxes
 // of the revised limits by HLL, bed source with the revised interface beds,
 // two-point interface rule for the slope volume integrals with the bed
 // source S1 = -(2 sqrt3 g / dx) h1 (h1 + z1) that cancels its hydrostatic
 // error at rest), then the update, the positivity clip and the dry reset.
+// FP32: four lanes share a leaf, one per interface (E, W, N, S), and lanes
+// 0-2 then finish h, qx, qy after a warp-shuffle exchange.  FP64 (whose
+// arithmetic units are few on this GPU): one thread per leaf.
+template <typename T> struct Lanes { static constexpr int per_leaf = std::is_same<T, float>::value ? 4 : 1; };
+
 template <typename T, int STAGE>
-__global__ void k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out) {
+__global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out) {
   const long long P = g.P;
   const double dtd = p.ctl->dt;
   if (!(dtd > 0.0)) return;  // a zero step changes nothing (end_step ignores it too)
@@ -948,149 +1151,88 @@ __global__ void k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T 
   // candidate (fixed grids: the next time step)
   double m0 = 0.0, m1 = 0.0, m2 = 0.0;
   double best = __longlong_as_double(0x7ff0000000000000LL);
-  FOR_LEAVES(p) {
-    long long k = p.leaves[_q];
-    int l, i, j;
-    node_of(g, k, l, i, j);
-    const T dxl = (T)g.dxl[l];
-    T w[9], zc[3];
+  const int nl = *p.nleaf;
+  if (Lanes<T>::per_leaf == 4) {
+    const int f = threadIdx.x & 3;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    // every lane runs the same number of iterations (shuffles need the warp)
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < 4LL * nl; base += nthreads) {
+      const long long q = (base + threadIdx.x) >> 2;
+      const bool valid = q < nl;
+      long long k = 0;
+      int l = 0, i = 0, j = 0;
+      T w[9], zc[3];
+      FaceOut<T> fo{};
+      if (valid) {
+        k = unpack_leaf(g, p.leaves[q], l, i, j);
 #pragma unroll
-    for (int m = 0; m < 9; m++) w[m] = p.F[m * P + k];
+        for (int m = 0; m < 9; m++) w[m] = p.F[m * P + k];
 #pragma unroll
-    for (int m = 0; m < 3; m++) zc[m] = p.Ze[m * P + k];
-    T Fh[4][3], hs[4], us[4], vs[4], zr[4];
-    double bout = 0.0;
+        for (int m = 0; m < 3; m++) zc[m] = p.Ze[m * P + k];
+        fo = face_flux(g, p, l, i, j, w, zc, f, tf);
+        bsum += fo.bout;
+      }
+      // every lane of the group gets the four interfaces; lanes 0, 1, 2
+      // then finish the variables h, qx, qy of the leaf
+      const int gbase = (threadIdx.x & 31) & ~3;
+      T Fv[4], hs[4], us[4], vs[4], zr[4];
 #pragma unroll
-    for (int f = 0; f < 4; f++) {
-      T own[4], nb[4];
-      own[0] = first_face(w[0], w[1], w[2], zc[0], f);
-      own[1] = face_value(w[3], w[4], w[5], f);
-      own[2] = face_value(w[6], w[7], w[8], f);
-      own[3] = face_value(zc[0], zc[1], zc[2], f);
-      bool inside = nbr_limit(g, p, l, i, j, f, nb);
-      if (!inside) {
-        // ghost: wall mirror, open copy, or critical-depth inflow
-        const int e = (f == 0) ? 1 : (f == 1) ? 0 : (f == 2) ? 3 : 2;
-        double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, tf);
-        nb[3] = own[3];
-        if (q > 0.0) {
-          T qt = (T)q;
-          T hc = tcbrt(qt * qt / gg);
-          T hown = Form<T>::eta ? own[0] - own[3] : own[0];
-          T hg = tmax(hown, hc);
-          nb[0] = Form<T>::eta ? hg + own[3] : hg;
-          T qn = (e == 0 || e == 2) ? qt : -qt;
-          if (e < 2) { nb[1] = qn; nb[2] = T(0); }
-          else { nb[1] = T(0); nb[2] = qn; }
-        } else if (g.bc[e] == MWDG_OPEN) {
-          nb[0] = own[0]; nb[1] = own[1]; nb[2] = own[2];
-        } else {
-          nb[0] = own[0];
-          if (e < 2) { nb[1] = -own[1]; nb[2] = own[2]; }
-          else { nb[1] = own[1]; nb[2] = -own[2]; }
-        }
+      for (int d = 0; d < 4; d++) {
+        T c0 = __shfl_sync(0xffffffffu, fo.F0, gbase + d);
+        T c1 = __shfl_sync(0xffffffffu, fo.F1, gbase + d);
+        T c2 = __shfl_sync(0xffffffffu, fo.F2, gbase + d);
+        Fv[d] = (f == 0) ? c0 : (f == 1) ? c1 : c2;
+        hs[d] = __shfl_sync(0xffffffffu, fo.hs, gbase + d);
+        us[d] = __shfl_sync(0xffffffffu, fo.us, gbase + d);
+        vs[d] = __shfl_sync(0xffffffffu, fo.vs, gbase + d);
+        zr[d] = __shfl_sync(0xffffffffu, fo.zr, gbase + d);
       }
-      const T zf = tmax(own[3], nb[3]);
-      Side<T> so, sn;
-      if (Form<T>::eta) {
-        so = revise_eta(own[0], own[1], own[2], own[3], zf, hd);
-        sn = revise_eta(nb[0], nb[1], nb[2], nb[3], zf, hd);
-      } else {
-        so = revise_h(own[0], own[1], own[2], own[3], zf, hd);
-        sn = revise_h(nb[0], nb[1], nb[2], nb[3], zf, hd);
+      T o0 = T(0), o1 = T(0), o2 = T(0);
+      if (valid && f < 3) finish_var<T, STAGE>(g, p, f, k, l, w, zc, Fv, hs, us, vs, zr, dt, Wst, Wcomb, o0, o1, o2);
+      // positivity clip (lane 0) and dry reset (all three)
+      const T h0n = __shfl_sync(0xffffffffu, o0, gbase);
+      if (valid && f < 3) {
+        post_var<T>(g, p, f, k, l, h0n, o0, o1, o2, ncl, csum, bad);
+        store_var(P, f, k, Out, o0, o1, o2);
       }
-      hs[f] = so.hs; us[f] = so.u; vs[f] = so.v; zr[f] = so.zr;
-      T F3[3];
-      if (f == 0) {
-        hll(so.hs, so.u, so.v, sn.hs, sn.u, sn.v, gg, hd, F3);
-        Fh[f][0] = F3[0]; Fh[f][1] = F3[1]; Fh[f][2] = F3[2];
-      } else if (f == 1) {
-        hll(sn.hs, sn.u, sn.v, so.hs, so.u, so.v, gg, hd, F3);
-        Fh[f][0] = F3[0]; Fh[f][1] = F3[1]; Fh[f][2] = F3[2];
-      } else if (f == 2) {
-        hll(so.hs, so.v, so.u, sn.hs, sn.v, sn.u, gg, hd, F3);
-        Fh[f][0] = F3[0]; Fh[f][1] = F3[2]; Fh[f][2] = F3[1];
-      } else {
-        hll(sn.hs, sn.v, sn.u, so.hs, so.v, so.u, gg, hd, F3);
-        Fh[f][0] = F3[0]; Fh[f][1] = F3[2]; Fh[f][2] = F3[1];
-      }
-      if (!inside) {
-        double outward = (f == 0 || f == 2) ? (double)Fh[f][0] : -(double)Fh[f][0];
-        bout += outward * (double)dxl;
+      if (STAGE == 2) {
+        const T qx0 = __shfl_sync(0xffffffffu, o0, gbase + 1);
+        const T qy0 = __shfl_sync(0xffffffffu, o0, gbase + 2);
+        if (valid && f == 0) next_step_reduce<T>(g, p, l, i, j, o0, qx0, qy0, tf, m0, m1, m2, best);
       }
     }
-    // physical fluxes of the own revised limits
-    T Fx[2][3], Gy[2][3];
+  } else {
+    // one thread per leaf: the four interfaces, then the three variables
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nl;
+         q += (long long)gridDim.x * blockDim.x) {
+      int l, i, j;
+      const long long k = unpack_leaf(g, p.leaves[q], l, i, j);
+      T w[9], zc[3];
 #pragma unroll
-    for (int a = 0; a < 2; a++) {
-      int f = a;
-      T q = hs[f] * us[f];
-      Fx[a][0] = q;
-      Fx[a][1] = q * us[f] + T(0.5) * gg * hs[f] * hs[f];
-      Fx[a][2] = q * vs[f];
-      f = 2 + a;
-      T r = hs[f] * vs[f];
-      Gy[a][0] = r;
-      Gy[a][1] = r * us[f];
-      Gy[a][2] = r * vs[f] + T(0.5) * gg * hs[f] * hs[f];
-    }
-    T Lo[9];
-    // slopes of the depth for the bed source: h1 and eta1 = h1 + z1
-    T h1x, h1y, e1x, e1y;
-    if (Form<T>::eta) {
-      e1x = w[1]; e1y = w[2];
-      h1x = w[1] - zc[1]; h1y = w[2] - zc[2];
-    } else {
-      h1x = w[1]; h1y = w[2];
-      e1x = w[1] + zc[1]; e1y = w[2] + zc[2];
-    }
+      for (int m = 0; m < 9; m++) w[m] = p.F[m * P + k];
 #pragma unroll
-    for (int v = 0; v < 3; v++) {
-      T L0 = -(Fh[0][v] - Fh[1][v]) / dxl - (Fh[2][v] - Fh[3][v]) / dxl;
-      if (v == 1) L0 = L0 + -gg * T(0.5) * (hs[0] + hs[1]) * (zr[0] - zr[1]) / dxl;
-      if (v == 2) L0 = L0 + -gg * T(0.5) * (hs[2] + hs[3]) * (zr[2] - zr[3]) / dxl;
-      T L1x = -(s3 / dxl) * (Fh[0][v] + Fh[1][v] - Fx[0][v] - Fx[1][v]);
-      T L1y = -(s3 / dxl) * (Fh[2][v] + Fh[3][v] - Gy[0][v] - Gy[1][v]);
-      if (v == 1) L1x = L1x + -(T(2) * s3 * gg / dxl) * h1x * e1x;
-      if (v == 2) L1y = L1y + -(T(2) * s3 * gg / dxl) * h1y * e1y;
-      Lo[3 * v + 0] = L0;
-      Lo[3 * v + 1] = L1x;
-      Lo[3 * v + 2] = L1y;
-    }
-    T o[9];
-    if (STAGE == 1) {
+      for (int m = 0; m < 3; m++) zc[m] = p.Ze[m * P + k];
+      T F[4][3], hs[4], us[4], vs[4], zr[4];
 #pragma unroll
-      for (int m = 0; m < 9; m++) o[m] = Wst[m * P + k] + dt * Lo[m];
-    } else {
-#pragma unroll
-      for (int m = 0; m < 9; m++) o[m] = T(0.5) * (Wcomb[m * P + k] + Wst[m * P + k] + dt * Lo[m]);
-    }
-    // positivity clip and dry reset
-    const double area = g.dxl[l] * g.dxl[l];
-    if (o[0] < T(0)) {
-      ncl++;
-      csum += -(double)o[0] * area;
-      o[0] = T(0);
-    }
-    if (!(o[0] > hd)) {  // dry: flat zero depth (free-surface slopes = bed slopes)
-      o[1] = Form<T>::eta ? p.Z[P + k] : T(0);
-      o[2] = Form<T>::eta ? p.Z[2 * P + k] : T(0);
-      for (int m = 3; m < 9; m++) o[m] = T(0);
-    }
-#pragma unroll
-    for (int m = 0; m < 9; m++) {
-      if (!isfinite(o[m])) bad = true;
-      Out[m * P + k] = o[m];
-    }
-    bsum += bout;
-    if (STAGE == 2) {
-      if (g.mode == MWDG_ADAPTIVE) {
-        m0 = fmax(m0, (double)tabs(o[0]));
-        m1 = fmax(m1, (double)tabs(o[3]));
-        m2 = fmax(m2, (double)tabs(o[6]));
-      } else {
-        best = fmin(best, leaf_dt_candidate(g, p, l, i, j, o[0], o[3], o[6], tf));
+      for (int d = 0; d < 4; d++) {
+        FaceOut<T> fo = face_flux(g, p, l, i, j, w, zc, d, tf);
+        bsum += fo.bout;
+        F[d][0] = fo.F0; F[d][1] = fo.F1; F[d][2] = fo.F2;
+        hs[d] = fo.hs; us[d] = fo.us; vs[d] = fo.vs; zr[d] = fo.zr;
       }
+      T o[3][3];
+#pragma unroll
+      for (int v = 0; v < 3; v++) {
+        T Fv[4] = {F[0][v], F[1][v], F[2][v], F[3][v]};
+        finish_var<T, STAGE>(g, p, v, k, l, w, zc, Fv, hs, us, vs, zr, dt, Wst, Wcomb, o[v][0], o[v][1], o[v][2]);
+      }
+      const T h0n = o[0][0];
+#pragma unroll
+      for (int v = 0; v < 3; v++) {
+        post_var<T>(g, p, v, k, l, h0n, o[v][0], o[v][1], o[v][2], ncl, csum, bad);
+        store_var(P, v, k, Out, o[v][0], o[v][1], o[v][2]);
+      }
+      if (STAGE == 2) next_step_reduce<T>(g, p, l, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
     }
   }
   if (bad) p.ctl->nonfinite = 1;
@@ -1180,9 +1322,8 @@ __global__ void k_read_active(Geo g, Ptrs<T> p, int32_t *lev, int32_t *ii, int32
   const int n = *p.nleaf;
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
-  long long k = p.leaves[q];
   int l, i, j;
-  node_of(g, k, l, i, j);
+  long long k = unpack_leaf(g, p.leaves[q], l, i, j);
   if (lev) lev[q] = l;
   if (ii) ii[q] = i;
   if (jj) jj[q] = j;
@@ -1203,9 +1344,8 @@ __global__ void k_volume_part(Geo g, Ptrs<T> p) {
   const int n = *p.nleaf;
   double acc = 0.0;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    long long k = p.leaves[q];
     int l, i, j;
-    node_of(g, k, l, i, j);
+    long long k = unpack_leaf(g, p.leaves[q], l, i, j);
     double h0 = (double)p.U[k];
     acc += h0 * (g.dxl[l] * g.dxl[l]);
   }
@@ -1325,7 +1465,7 @@ int Launch<T>::compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
   const int nb = (int)((g.P + CTILE - 1) / CTILE);
   k_compact_count<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk);
   k_compact_scan<<<1, 1024, 0, st>>>(nb, p.blk, p.nleaf);
-  k_compact_scatter<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk, p.leaves);
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves);
   return 3;
 }
 
@@ -1350,7 +1490,11 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
   }
   // bottom-up: encode + significance of level l, regularised flags of l+1
   const int lc = coarse_top(g);
-  for (int l = g.L - 1; l > lc; l--, n++) k_adapt_level<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+  for (int l = g.L - 1; l > lc; l--, n++) {
+    MARK(KC_ENCODE);
+    k_adapt_level<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+  }
+  MARK(KC_ENCODE);
   k_adapt_coarse<T><<<1, COARSE_TPB, 0, st>>>(g, p, lc);
   n++;
   if (encode_only) return n;
@@ -1361,7 +1505,8 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
   k_decode_count<T><<<nb, TPB, 0, st>>>(g, p);
   MARK(KC_COMPACT);
   k_compact_scan<<<1, 1024, 0, st>>>(nb, p.blk, p.nleaf);
-  k_compact_scatter<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk, p.leaves);
+  MARK(KC_COMPACT);
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves);
   return n + 3;
 }
 
@@ -1385,7 +1530,7 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
   const bool view = (g.mode == MWDG_ADAPTIVE);
   const int lc = coarse_top(g);
   MARK(KC_CONTROL);
-  k_begin_step<<<1, 1, 0, st>>>(g, p.ctl);
+  k_begin_step<<<1, 1, 0, st>>>(g, p.ctl, p.nleaf);
   n++;
   for (int stage = 1; stage <= 2; stage++) {
     MARK(KC_LIMIT);
@@ -1393,9 +1538,12 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
     else k_leaf_limit<T, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
     n++;
     if (view) {
-      MARK(KC_VIEW);
-      for (int l = g.L - 1; l > lc; l--, n++) k_encode_view<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+      for (int l = g.L - 1; l > lc; l--, n++) {
+        MARK(KC_VIEW);
+        k_encode_view<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+      }
       if (lc >= 0) {
+        MARK(KC_VIEW);
         k_encode_view_coarse<T><<<1, COARSE_TPB, 0, st>>>(g, p, lc);
         n++;
       }
