@@ -332,9 +332,9 @@ def kernel_bytes_per_leaf(name, ts):
     bytes plus the 8-byte active-list entry; neighbour reads served from L2
     are not counted).  MRA classes are per node, not per leaf: None."""
     vals = {
-        "dg2_update_stage1": 9 + 3 + 9 + 9,      # F, Ze, Wn read; Ui written
-        "dg2_update_stage2": 9 + 3 + 9 + 9 + 9,  # F, Ze, Wi, Wn read; U written
-        "limit": 9 + 3 + 9 + 9 + 3,              # X, Z read; Wst, F, Ze written
+        "dg2_update_stage1": 12 + 9 + 9,      # FZ record, Wn read; Ui written
+        "dg2_update_stage2": 12 + 9 + 9 + 9,  # FZ record, Wi, Wn read; U written
+        "limit": 9 + 3 + 9 + 12,              # X, Z read; Wst, FZ record written
     }
     if name not in vals:
         return None
@@ -343,7 +343,7 @@ def kernel_bytes_per_leaf(name, ts):
 
 # DRAM bytes (read + write) per launch measured by ncu for a kernel, when the
 # kernel has not changed since (see profiles/); None otherwise
-TRAFFIC = {"dg2_update_stage2": 55_167_744 + 2_086_912}  # profiles/k_leaf_update_valley1024_f32.md
+TRAFFIC = {}
 
 
 def main():

@@ -155,8 +155,8 @@ mwdg_status allocate_state(mwdg_ctx *c) {
   const size_t P = (size_t)c->g.P;
   mwdg_status s;
   if ((s = alloc(c, &p.U, 9 * P)) || (s = alloc(c, &p.Ui, 9 * P)) || (s = alloc(c, &p.Wn, 9 * P)) ||
-      (s = alloc(c, &p.Wi, 9 * P)) || (s = alloc(c, &p.F, 9 * P)) || (s = alloc(c, &p.Z, 3 * P)) ||
-      (s = alloc(c, &p.Ze, 3 * P)) || (s = alloc(c, &p.NM, P)) || (s = alloc(c, &p.DZ, P)) ||
+      (s = alloc(c, &p.Wi, 9 * P)) || (s = alloc(c, &p.FZ, 12 * P)) || (s = alloc(c, &p.Z, 3 * P)) ||
+      (s = alloc(c, &p.NM, P)) || (s = alloc(c, &p.DZ, P)) ||
       (s = alloc(c, &p.kind, P)) || (s = alloc(c, &p.kind_old, P)) || (s = alloc(c, &p.flag, P)) ||
       (s = alloc(c, &p.flag2, P)) || (s = alloc(c, &p.leaves, P)) || (s = alloc(c, &p.nleaf, 1)))
     return s;
@@ -166,9 +166,8 @@ mwdg_status allocate_state(mwdg_ctx *c) {
   CK(cudaMemsetAsync(p.Ui, 0, 9 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.Wn, 0, 9 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.Wi, 0, 9 * P * sizeof(T), c->st));
-  CK(cudaMemsetAsync(p.F, 0, 9 * P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.FZ, 0, 12 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.Z, 0, 3 * P * sizeof(T), c->st));
-  CK(cudaMemsetAsync(p.Ze, 0, 3 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.NM, 0, P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.DZ, 0, P * sizeof(double), c->st));
   CK(cudaMemsetAsync(p.flag, 0, P, c->st));

@@ -49,9 +49,9 @@ struct Ptrs {
   T *Ui;    // RK2 intermediate state (9)
   T *Wn;    // limited stage-1 input in the stored view (9)
   T *Wi;    // limited stage-2 input in the stored view (9)
-  T *F;     // limited stage input in the flux view (9); refined nodes: encoding
+  T *FZ;    // flux view, one record of 12 per node: the limited stage input
+            // (9) and its bed planes (3); refined nodes hold their encoding
   T *Z;     // static topography pyramid (3)
-  T *Ze;    // bed planes of the flux view (3)
   T *NM;    // Manning n per node (1)
   double *DZ;   // normalised topography detail per node
   uint8_t *kind, *kind_old, *flag, *flag2;

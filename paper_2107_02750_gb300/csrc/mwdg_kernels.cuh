@@ -60,6 +60,44 @@ __device__ __forceinline__ void node_of(const Geo &g, long long k, int &l, int &
 __device__ __forceinline__ long long nid(const Geo &g, int l, int i, int j) {
   return g.off[l] + (long long)j * g.nxl[l] + i;
 }
+// flux-view record of a node: 12 values (9 coefficients, 3 bed) read with
+// 16-byte vector loads
+template <typename T>
+__device__ __forceinline__ void load_rec(const T *FZ, long long k, T (&r)[12]);
+template <>
+__device__ __forceinline__ void load_rec<float>(const float *FZ, long long k, float (&r)[12]) {
+  const float4 *q = reinterpret_cast<const float4 *>(FZ + 12 * k);
+  float4 a = q[0], b = q[1], c = q[2];
+  r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+  r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+  r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
+}
+template <>
+__device__ __forceinline__ void load_rec<double>(const double *FZ, long long k, double (&r)[12]) {
+  const double2 *q = reinterpret_cast<const double2 *>(FZ + 12 * k);
+#pragma unroll
+  for (int m = 0; m < 6; m++) {
+    double2 a = q[m];
+    r[2 * m] = a.x;
+    r[2 * m + 1] = a.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void store_rec(T *FZ, long long k, const T (&r)[12]);
+template <>
+__device__ __forceinline__ void store_rec<float>(float *FZ, long long k, const float (&r)[12]) {
+  float4 *q = reinterpret_cast<float4 *>(FZ + 12 * k);
+  q[0] = make_float4(r[0], r[1], r[2], r[3]);
+  q[1] = make_float4(r[4], r[5], r[6], r[7]);
+  q[2] = make_float4(r[8], r[9], r[10], r[11]);
+}
+template <>
+__device__ __forceinline__ void store_rec<double>(double *FZ, long long k, const double (&r)[12]) {
+  double2 *q = reinterpret_cast<double2 *>(FZ + 12 * k);
+#pragma unroll
+  for (int m = 0; m < 6; m++) q[m] = make_double2(r[2 * m], r[2 * m + 1]);
+}
+
 // active-list entries carry the leaf's level and indices
 __device__ __forceinline__ long long pack_leaf(int l, int i, int j) {
   return ((long long)l << 56) | ((long long)j << 28) | (long long)i;
@@ -558,7 +596,7 @@ __global__ void k_adapt_level(Geo g, Ptrs<T> p, int l) {
 // levels lc..0 in one block (barrier between levels), then the regularised
 // flags of level 0
 template <typename T>
-__global__ void k_adapt_coarse(Geo g, Ptrs<T> p, int lc) {
+__global__ void __launch_bounds__(256) k_adapt_coarse(Geo g, Ptrs<T> p, int lc) {
   if (!ADAPT_LIVE(p)) return;
   for (int l = lc; l >= 0; l--) {
     long long n = (long long)g.nxl[l] * g.nyl[l];
@@ -802,12 +840,13 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
       for (int m = 0; m < 9; m++) wf[m] = ws[m];
     }
 #pragma unroll
-    for (int m = 0; m < 9; m++) {
-      Wst[m * P + k] = ws[m];
-      p.F[m * P + k] = wf[m];
-    }
+    for (int m = 0; m < 9; m++) Wst[m * P + k] = ws[m];
+    T rec[12];
 #pragma unroll
-    for (int m = 0; m < 3; m++) p.Ze[m * P + k] = ze[m];
+    for (int m = 0; m < 9; m++) rec[m] = wf[m];
+#pragma unroll
+    for (int m = 0; m < 3; m++) rec[9 + m] = ze[m];
+    store_rec(p.FZ, k, rec);
   }
 }
 
@@ -815,33 +854,34 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
 // (MWDG2 interfaces, Sect. 2.3)
 template <typename T>
 __device__ __forceinline__ void encode_view_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
-  const long long P = g.P, k = nid(g, l, i, j);
+  const long long k = nid(g, l, i, j);
   if (p.kind[k] != K_SIG) return;
-  long long kc[4];
+  T rc[4][12];
 #pragma unroll
-  for (int c = 0; c < 4; c++) kc[c] = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
-  T zc[4][3], zpar[3];
+  for (int c = 0; c < 4; c++) load_rec(p.FZ, nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1)), rc[c]);
+  T zc[4][3], zpar[3], rec[12];
 #pragma unroll
   for (int c = 0; c < 4; c++)
 #pragma unroll
-    for (int m = 0; m < 3; m++) zc[c][m] = p.Ze[m * P + kc[c]];
+    for (int m = 0; m < 3; m++) zc[c][m] = rc[c][9 + m];
   encode3(zc, zpar);
 #pragma unroll
-  for (int m = 0; m < 3; m++) p.Ze[m * P + k] = zpar[m];
+  for (int m = 0; m < 3; m++) rec[9 + m] = zpar[m];
+#pragma unroll
   for (int v = 0; v < 3; v++) {
-    T *X = p.F + 3 * v * P;
     T ch[4][3], sp[3];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
 #pragma unroll
-      for (int m = 0; m < 3; m++) ch[c][m] = X[m * P + kc[c]];
+      for (int m = 0; m < 3; m++) ch[c][m] = rc[c][3 * v + m];
       if (v == 0) slopes_to_h(ch[c][1], ch[c][2], zc[c][1], zc[c][2]);
     }
     encode3(ch, sp);
     if (v == 0) slopes_from_h(sp[1], sp[2], zpar[1], zpar[2]);
 #pragma unroll
-    for (int m = 0; m < 3; m++) X[m * P + k] = sp[m];
+    for (int m = 0; m < 3; m++) rec[3 * v + m] = sp[m];
   }
+  store_rec(p.FZ, k, rec);
 }
 
 template <typename T>
@@ -855,7 +895,7 @@ __global__ void k_encode_view(Geo g, Ptrs<T> p, int l) {
 
 // levels lc..0 in one block, barrier between levels
 template <typename T>
-__global__ void k_encode_view_coarse(Geo g, Ptrs<T> p, int lc) {
+__global__ void __launch_bounds__(256) k_encode_view_coarse(Geo g, Ptrs<T> p, int lc) {
   for (int l = lc; l >= 0; l--) {
     long long n = (long long)g.nxl[l] * g.nyl[l];
     for (long long r = threadIdx.x; r < n; r += blockDim.x) {
@@ -893,16 +933,14 @@ __device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, i
     else { c1 = 2; c2 = 3; }
     long long k1 = nid(g, l + 1, 2 * a + (c1 & 1), 2 * b + (c1 >> 1));
     long long k2 = nid(g, l + 1, 2 * a + (c2 & 1), 2 * b + (c2 >> 1));
-    const T *F = p.F;
-    out[0] = T(0.5) * (first_face(F[k1], F[P + k1], F[2 * P + k1], p.Ze[k1], fo) +
-                       first_face(F[k2], F[P + k2], F[2 * P + k2], p.Ze[k2], fo));
-    for (int v = 1; v < 3; v++) {
-      const T *X = p.F + 3 * v * P;
-      out[v] = T(0.5) * (face_value(X[k1], X[P + k1], X[2 * P + k1], fo) +
-                         face_value(X[k2], X[P + k2], X[2 * P + k2], fo));
-    }
-    out[3] = T(0.5) * (face_value(p.Ze[k1], p.Ze[P + k1], p.Ze[2 * P + k1], fo) +
-                       face_value(p.Ze[k2], p.Ze[P + k2], p.Ze[2 * P + k2], fo));
+    T r1[12], r2[12];
+    load_rec(p.FZ, k1, r1);
+    load_rec(p.FZ, k2, r2);
+    out[0] = T(0.5) * (first_face(r1[0], r1[1], r1[2], r1[9], fo) + first_face(r2[0], r2[1], r2[2], r2[9], fo));
+    for (int v = 1; v < 3; v++)
+      out[v] = T(0.5) * (face_value(r1[3 * v], r1[3 * v + 1], r1[3 * v + 2], fo) +
+                         face_value(r2[3 * v], r2[3 * v + 1], r2[3 * v + 2], fo));
+    out[3] = T(0.5) * (face_value(r1[9], r1[10], r1[11], fo) + face_value(r2[9], r2[10], r2[11], fo));
     return true;
   }
   if (kd == K_BELOW) {
@@ -918,27 +956,26 @@ __device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, i
       ka = nid(g, la, aa, bb);
     }
     // beds (v = 3) first, then the flow planes in depth form
-    T zb[3] = {p.Ze[ka], p.Ze[P + ka], p.Ze[2 * P + ka]};
+    T ra[12];
+    load_rec(p.FZ, ka, ra);
     for (int v = 3; v >= 0; v--) {
-      const T *X = (v < 3) ? p.F + 3 * v * P : p.Ze;
-      T s[3] = {X[ka], X[P + ka], X[2 * P + ka]};
-      if (v == 0) slopes_to_h(s[1], s[2], zb[1], zb[2]);
+      T sv[3] = {ra[3 * v], ra[3 * v + 1], ra[3 * v + 2]};
+      if (v == 0) slopes_to_h(sv[1], sv[2], ra[10], ra[11]);
       for (int q = d - 1; q >= 0; q--) {
         T o[3];
-        prolong3(s[0], s[1], s[2], path[q], o);
-        s[0] = o[0]; s[1] = o[1]; s[2] = o[2];
+        prolong3(sv[0], sv[1], sv[2], path[q], o);
+        sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
       }
-      out[v] = face_value(s[0], s[1], s[2], fo);
+      out[v] = face_value(sv[0], sv[1], sv[2], fo);
     }
     if (Form<T>::eta) out[0] = out[0] + out[3];  // depth + bed = free surface
     return true;
   }
-  out[0] = first_face(p.F[k], p.F[P + k], p.F[2 * P + k], p.Ze[k], fo);
-  for (int v = 1; v < 3; v++) {
-    const T *X = p.F + 3 * v * P;
-    out[v] = face_value(X[k], X[P + k], X[2 * P + k], fo);
-  }
-  out[3] = face_value(p.Ze[k], p.Ze[P + k], p.Ze[2 * P + k], fo);
+  T r[12];
+  load_rec(p.FZ, k, r);
+  out[0] = first_face(r[0], r[1], r[2], r[9], fo);
+  for (int v = 1; v < 3; v++) out[v] = face_value(r[3 * v], r[3 * v + 1], r[3 * v + 2], fo);
+  out[3] = face_value(r[9], r[10], r[11], fo);
   return true;
 }
 
@@ -1165,10 +1202,14 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
       FaceOut<T> fo{};
       if (valid) {
         k = unpack_leaf(g, p.leaves[q], l, i, j);
+        {
+          T r[12];
+          load_rec(p.FZ, k, r);
 #pragma unroll
-        for (int m = 0; m < 9; m++) w[m] = p.F[m * P + k];
+          for (int m = 0; m < 9; m++) w[m] = r[m];
 #pragma unroll
-        for (int m = 0; m < 3; m++) zc[m] = p.Ze[m * P + k];
+          for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
+        }
         fo = face_flux(g, p, l, i, j, w, zc, f, tf);
         bsum += fo.bout;
       }
@@ -1208,10 +1249,14 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
       int l, i, j;
       const long long k = unpack_leaf(g, p.leaves[q], l, i, j);
       T w[9], zc[3];
+      {
+        T r[12];
+        load_rec(p.FZ, k, r);
 #pragma unroll
-      for (int m = 0; m < 9; m++) w[m] = p.F[m * P + k];
+        for (int m = 0; m < 9; m++) w[m] = r[m];
 #pragma unroll
-      for (int m = 0; m < 3; m++) zc[m] = p.Ze[m * P + k];
+        for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
+      }
       T F[4][3], hs[4], us[4], vs[4], zr[4];
 #pragma unroll
       for (int d = 0; d < 4; d++) {
@@ -1471,7 +1516,7 @@ int Launch<T>::compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
 
 // coarsest levels handled by one block of the MRA kernels (levels with at
 // most g.coarse_nodes nodes)
-constexpr int COARSE_TPB = 1024;
+constexpr int COARSE_TPB = 256;
 inline int coarse_top(const Geo &g) {
   int lc = -1;
   while (lc + 1 < g.L && lvl(g, lc + 1) <= g.coarse_nodes) lc++;
