@@ -20,6 +20,9 @@ template <> __device__ __forceinline__ float s3v<float>() { return 1.7320508f; }
 
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return fmax(a, b); }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return fmin(a, b); }
+template <typename T> __device__ __forceinline__ T tinf();
+template <> __device__ __forceinline__ float tinf<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double tinf<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
 template <typename T> __device__ __forceinline__ T tsqrt(T a) { return sqrt(a); }
 template <typename T> __device__ __forceinline__ T tcbrt(T a) { return cbrt(a); }
 template <typename T> __device__ __forceinline__ T tabs(T a) { return fabs(a); }

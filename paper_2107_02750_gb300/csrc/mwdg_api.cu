@@ -157,7 +157,7 @@ mwdg_status allocate_state(mwdg_ctx *c) {
   if ((s = alloc(c, &p.U, 9 * P)) || (s = alloc(c, &p.Ui, 9 * P)) || (s = alloc(c, &p.Wn, 9 * P)) ||
       (s = alloc(c, &p.Wi, 9 * P)) || (s = alloc(c, &p.FZ, 12 * P)) || (s = alloc(c, &p.Z, 3 * P)) ||
       (s = alloc(c, &p.NM, P)) || (s = alloc(c, &p.DZ, P)) ||
-      (s = alloc(c, &p.kind, P)) || (s = alloc(c, &p.kind_old, P)) || (s = alloc(c, &p.flag, P)) ||
+      (s = alloc(c, &p.kind, P)) || (s = alloc(c, &p.kind_new, P)) || (s = alloc(c, &p.flag, P)) ||
       (s = alloc(c, &p.flag2, P)) || (s = alloc(c, &p.leaves, P)) || (s = alloc(c, &p.nleaf, 1)))
     return s;
   const size_t nb = (P + 2048 - 1) / 2048 + 1;
@@ -223,7 +223,7 @@ mwdg_status build_static_grid(mwdg_ctx *c, int is_eta_encoded) {
   }
   c->launches += dispatch(c, [&](auto &p, auto *) {
     using T = std::remove_pointer_t<decltype(p.U)>;
-    int n = Launch<T>::kinds(g, p, p.flag, 0, c->st) + Launch<T>::encode_dense_U(g, p, c->st);
+    int n = Launch<T>::kinds(g, p, p.flag, c->st) + Launch<T>::encode_dense_U(g, p, c->st);
     if (is_eta_encoded) n += Launch<T>::eta_rule_leaves(g, p, c->st);
     return n + Launch<T>::compact(g, p, c->st);
   });
@@ -407,7 +407,7 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
   }
   c->launches += dispatch(c, [&](auto &pp, auto *) {
     using T = std::remove_pointer_t<decltype(pp.U)>;
-    int n = (g.L == 0) ? Launch<T>::kinds(g, pp, pp.flag, 0, c->st) : Launch<T>::all_finest(g, pp, c->st);
+    int n = (g.L == 0) ? Launch<T>::kinds(g, pp, pp.flag, c->st) : Launch<T>::all_finest(g, pp, c->st);
     return n + Launch<T>::compact(g, pp, c->st);
   });
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->st) != cudaSuccess) {
@@ -520,7 +520,7 @@ mwdg_status mwdg_load_initial(mwdg_ctx *c, const double *h_vert, const double *q
   } else {
     c->launches += dispatch(c, [&](auto &p, auto *) {
       using T = std::remove_pointer_t<decltype(p.U)>;
-      int n = (g.L == 0) ? Launch<T>::kinds(g, p, p.flag, 0, c->st) : Launch<T>::all_finest(g, p, c->st);
+      int n = (g.L == 0) ? Launch<T>::kinds(g, p, p.flag, c->st) : Launch<T>::all_finest(g, p, c->st);
       return n + Launch<T>::compact(g, p, c->st);
     });
     CHECK_LAUNCH();

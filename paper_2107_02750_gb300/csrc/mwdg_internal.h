@@ -23,7 +23,7 @@ struct Ctl {
   int nonfinite;
   int changed;                 // grading sweep made a change
   unsigned int blocks_done;    // completion tickets of the last kernel of a step
-  int pad_;
+  unsigned int ticket;         // completion tickets of the multi-level MRA kernels (self-resetting)
 };
 
 // Geometry and parameters of the level hierarchy (passed by value).
@@ -54,7 +54,8 @@ struct Ptrs {
   T *Z;     // static topography pyramid (3)
   T *NM;    // Manning n per node (1)
   double *DZ;   // normalised topography detail per node
-  uint8_t *kind, *kind_old, *flag, *flag2;
+  uint8_t *kind, *flag, *flag2;
+  uint8_t *kind_new;  // kinds of the next active set while the old ones are still read
   long long *leaves;  // active leaves, packed (level << 56 | j << 28 | i)
   int *nleaf;
   int *blk;         // compaction scratch: per-block counts / offsets
@@ -77,8 +78,7 @@ template <typename T> struct Launch {
   static int static_flags(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
   static int closure(const Geo &g, uint8_t *flag, cudaStream_t st);
   static int grading_sweep(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
-  static int kinds(const Geo &g, const Ptrs<T> &p, const uint8_t *flag, int keep_old,
-                   cudaStream_t st);
+  static int kinds(const Geo &g, const Ptrs<T> &p, const uint8_t *flag, cudaStream_t st);
   static int all_finest(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
   static int compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
   static int adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_maxabs,

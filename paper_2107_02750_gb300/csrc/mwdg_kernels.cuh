@@ -53,9 +53,15 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double x) 
 __device__ __forceinline__ void node_of(const Geo &g, long long k, int &l, int &i, int &j) {
   l = 0;
   while (l < g.L && k >= g.off[l + 1]) l++;
-  long long r = k - g.off[l];
-  j = (int)(r / g.nxl[l]);
-  i = (int)(r - (long long)j * g.nxl[l]);
+  const long long r = k - g.off[l];
+  if (r < (1LL << 32)) {  // 32-bit division (levels of fewer than 2^32 nodes)
+    const unsigned r32 = (unsigned)r, n = (unsigned)g.nxl[l];
+    j = (int)(r32 / n);
+    i = (int)(r32 - (unsigned)j * n);
+  } else {
+    j = (int)(r / g.nxl[l]);
+    i = (int)(r - (long long)j * g.nxl[l]);
+  }
 }
 __device__ __forceinline__ long long nid(const Geo &g, int l, int i, int j) {
   return g.off[l] + (long long)j * g.nxl[l] + i;
@@ -296,15 +302,13 @@ __global__ void k_grading(Geo g, Ptrs<T> p, int l) {
 // node kinds from flags (flags already closed under parents): refined,
 // active leaf (parent refined or root, not refined itself) or below a leaf
 template <typename T>
-__global__ void k_kinds(Geo g, Ptrs<T> p, const uint8_t *flag, int keep_old) {
+__global__ void k_kinds(Geo g, Ptrs<T> p, const uint8_t *flag) {
   long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (keep_old && k == 0) p.ctl->dtmin = 0x7ff0000000000000ULL;  // the decode pass refills it
   if (k >= g.P) return;
   int l, i, j;
   node_of(g, k, l, i, j);
   int f = (l < g.L) ? flag[k] : 0;
   int parent = (l == 0) ? 1 : flag[nid(g, l - 1, i >> 1, j >> 1)];
-  if (keep_old) p.kind_old[k] = p.kind[k];
   p.kind[k] = f ? K_SIG : (parent ? K_LEAF : K_BELOW);
 }
 
@@ -339,15 +343,16 @@ static __global__ void k_compact_count(long long P, const uint8_t *kind, int *bl
   }
 }
 
-// exclusive scan of the block counts (one block) and the total
-static __global__ void k_compact_scan(int nb, int *blk, int *total) {
+// exclusive scan of the per-block leaf counts in place (read through L2)
+// and their total, by one block
+__device__ __forceinline__ void block_scan_counts(int nb, int *blk, int *total) {
   __shared__ int carry;
-  __shared__ int ws[1024 / 32];
+  __shared__ int ws[32];
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (int base = 0; base < nb; base += blockDim.x) {
     int idx = base + threadIdx.x;
-    int v = (idx < nb) ? blk[idx] : 0;
+    int v = (idx < nb) ? __ldcg(&blk[idx]) : 0;
     int x = v;
     for (int o = 1; o < 32; o <<= 1) {
       int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -374,13 +379,35 @@ static __global__ void k_compact_scan(int nb, int *blk, int *total) {
   if (threadIdx.x == 0) *total = carry;
 }
 
-static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *blk, long long *leaves) {
+static __global__ void k_compact_scan(int nb, int *blk, int *total) { block_scan_counts(nb, blk, total); }
+
+// order-preserving scatter of the active leaves (each thread owns CPT
+// consecutive nodes, read as one 8-byte word); with kind_out the kinds are
+// also copied there
+static_assert(CPT == 8, "one 8-byte word of kinds per thread");
+static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *blk, long long *leaves,
+                                         uint8_t *kind_out) {
   const long long P = g.P;
-  long long base = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
+  const long long base = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
+  const bool full = base + CPT <= P;
+  uint8_t kk[CPT];
+  uint2 w8 = make_uint2(0u, 0u);
+  if (full) {
+    w8 = *reinterpret_cast<const uint2 *>(kind + base);
+#pragma unroll
+    for (int q = 0; q < CPT; q++) kk[q] = (uint8_t)(((q < 4) ? (w8.x >> (8 * q)) : (w8.y >> (8 * (q - 4)))) & 0xffu);
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPT; q++) kk[q] = (base + q < P) ? kind[base + q] : (uint8_t)K_BELOW;
+  }
   int c = 0;
-  for (int q = 0; q < CPT; q++) {
-    long long k = base + q;
-    c += (k < P && kind[k] == K_LEAF);
+#pragma unroll
+  for (int q = 0; q < CPT; q++) c += (kk[q] == K_LEAF);
+  if (kind_out) {
+    if (full) *reinterpret_cast<uint2 *>(kind_out + base) = w8;
+    else
+      for (int q = 0; q < CPT; q++)
+        if (base + q < P) kind_out[base + q] = kk[q];
   }
   // block-wide exclusive scan of per-thread counts
   int x = c;
@@ -402,10 +429,9 @@ static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *
   __syncthreads();
   int pos = blk[blockIdx.x] + x - c + ((threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0);
   for (int q = 0; q < CPT; q++) {
-    long long k = base + q;
-    if (k < P && kind[k] == K_LEAF) {
+    if (kk[q] == K_LEAF) {
       int l, i, j;
-      node_of(g, k, l, i, j);
+      node_of(g, base + q, l, i, j);
       leaves[pos++] = pack_leaf(l, i, j);
     }
   }
@@ -476,15 +502,15 @@ __global__ void k_leaf_maxabs(Geo g, Ptrs<T> p) {
 // min over x and y of dx / (|u| + sqrt(g h)) when wet, and the inflow ghost
 // states at the critical depth on inflow faces; +inf when there is none
 template <typename T>
-__device__ __forceinline__ double leaf_dt_candidate(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
-                                                    T h0, T qx0, T qy0, double t) {
+__device__ __forceinline__ T leaf_dt_candidate(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
+                                               T h0, T qx0, T qy0, double t) {
   const T gg = (T)g.g, hd = (T)g.hd;
   const T dxl = (T)g.dxl[l];
-  double best = __longlong_as_double(0x7ff0000000000000LL);
+  T best = tinf<T>();
   if (h0 > hd) {
     T u = qx0 / h0, v = qy0 / h0;
     T c = tsqrt(gg * h0);
-    best = (double)tmin(dxl / (tabs(u) + c), dxl / (tabs(v) + c));
+    best = tmin(dxl / (tabs(u) + c), dxl / (tabs(v) + c));
   }
   if (g.inflow_edge >= 0) {
     for (int e = 0; e < 4; e++) {
@@ -495,16 +521,17 @@ __device__ __forceinline__ double leaf_dt_candidate(const Geo &g, const Ptrs<T> 
       if (q > 0.0) {
         T qt = (T)q;
         T hc = tcbrt(qt * qt / gg);
-        if (hc > hd) best = fmin(best, (double)(dxl / (qt / hc + tsqrt(gg * hc))));
+        if (hc > hd) best = tmin(best, dxl / (qt / hc + tsqrt(gg * hc)));
       }
     }
   }
   return best;
 }
 
-__device__ __forceinline__ void warp_min_to(unsigned long long *dst, double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0 && v < __longlong_as_double(0x7ff0000000000000LL)) atomic_min_pos(dst, v);
+template <typename T>
+__device__ __forceinline__ void warp_min_to(unsigned long long *dst, T v) {
+  for (int o = 16; o > 0; o >>= 1) v = tmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v < tinf<T>()) atomic_min_pos(dst, (double)v);
 }
 
 // CFL candidates over the leaves
@@ -512,150 +539,506 @@ template <typename T>
 __global__ void k_leaf_dt(Geo g, Ptrs<T> p) {
   const long long P = g.P;
   const double t = p.ctl->t;
-  double best = __longlong_as_double(0x7ff0000000000000LL);
+  T best = tinf<T>();
   FOR_LEAVES(p) {
     int l, i, j;
     long long k = unpack_leaf(g, p.leaves[_q], l, i, j);
-    best = fmin(best, leaf_dt_candidate(g, p, l, i, j, p.U[k], p.U[3 * P + k], p.U[6 * P + k], t));
+    best = tmin(best, leaf_dt_candidate(g, p, l, i, j, p.U[k], p.U[3 * P + k], p.U[6 * P + k], t));
   }
   warp_min_to(&p.ctl->dtmin, best);
+}
+
+// ---------------------------------------------------------------------------
+// Tiled multi-level MRA passes
+// ---------------------------------------------------------------------------
+// A block owns a 16 x 16 tile of nodes at a chunk's finest level ltop and
+// the nodes above them at up to four coarser levels (8 x 8, 4 x 4, 2 x 2,
+// 1).  It first stages in shared memory what each tile node brings from
+// global memory (its kind, and a leaf's own coefficients) while the
+// refined nodes of the finest tile level read their children, then runs
+// the coarser levels from shared memory with a block barrier between them:
+// a chunk of five levels is one launch with two memory round trips per
+// block.  The coarsest levels (at most g.coarse_nodes nodes each) are run by
+// the last block of the chunk below them to finish: each block takes a
+// completion ticket after its writes and the block that draws the last one
+// continues (no block waits on another).
+constexpr int MT = 16;         // tile side at a chunk's finest level (one node per thread)
+constexpr int MT_LEVELS = 5;   // levels per chunk: 16, 8, 4, 2, 1 nodes per side
+static_assert(MT * MT == TPB, "one thread per node of a tile's finest level");
+
+// first shared-memory slot of tile level s (levels stacked finest first)
+__host__ __device__ constexpr int tbase(int s) {
+  return s == 0 ? 0 : tbase(s - 1) + (MT >> (s - 1)) * (MT >> (s - 1));
+}
+constexpr int MT_NODES = tbase(MT_LEVELS);  // 341 nodes in a full tile
+static_assert(MT_NODES <= 2 * TPB, "two staged slots per thread");
+constexpr uint8_t K_OUT = 0xff;             // slot outside its level
+
+struct Tile { int ltop, nlev, bx, by; };
+
+__device__ __forceinline__ Tile tile_of_block(const Geo &g, int ltop, int nlev) {
+  const int tiles_x = (g.nxl[ltop] + MT - 1) / MT;
+  return Tile{ltop, nlev, (int)(blockIdx.x % tiles_x), (int)(blockIdx.x / tiles_x)};
+}
+
+// the coarsest levels fit one tile (run from shared memory by the last block)
+__device__ __forceinline__ bool tail_is_tile(const Geo &g, int tail) {
+  return tail + 1 <= MT_LEVELS && g.nxl[tail] <= MT && g.nyl[tail] <= MT;
+}
+
+// tile level s and index t within it of a slot
+__device__ __forceinline__ void slot_st(int slot, int &s, int &t) {
+  s = 0;
+  while (s + 1 < MT_LEVELS && slot >= tbase(s + 1)) s++;
+  t = slot - tbase(s);
+}
+
+// grid node (level ltop - s) of node t of tile level s; false outside the level
+__device__ __forceinline__ bool tile_coord(const Geo &g, const Tile &tl, int s, int t, int &i, int &j) {
+  const int side = MT >> s, l = tl.ltop - s;
+  i = tl.bx * side + t % side;
+  j = tl.by * side + t / side;
+  return i < g.nxl[l] && j < g.nyl[l];
+}
+
+// slot of child c (= cx + 2 cy) of node t of tile level s >= 1
+__device__ __forceinline__ int child_slot(int s, int t, int c) {
+  const int side = MT >> s;
+  const int a = 2 * (t % side) + (c & 1), b = 2 * (t / side) + (c >> 1);
+  return tbase(s - 1) + b * (2 * side) + a;
+}
+
+// the two slots a thread stages, with their grid node (-1: none)
+__device__ __forceinline__ void staged_slots(const Geo &g, const Tile &tl, int sl[2], long long kk[2]) {
+  const int n_slots = tbase(tl.nlev);
+#pragma unroll
+  for (int q = 0; q < 2; q++) {
+    sl[q] = (int)threadIdx.x + q * TPB;
+    kk[q] = -1;
+    if (sl[q] < n_slots) {
+      int s, t, i, j;
+      slot_st(sl[q], s, t);
+      if (tile_coord(g, tl, s, t, i, j)) kk[q] = nid(g, tl.ltop - s, i, j);
+    }
+  }
+}
+
+// true in exactly one block, the last to get here; every block's global
+// writes before this point are visible to that block's L2 reads afterwards
+__device__ __forceinline__ bool last_block(unsigned int *ticket) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int v = atomicAdd(ticket, 1u);
+    last = (v == gridDim.x - 1);
+    if (last) {
+      *ticket = 0u;  // ready for the next launch
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  return last != 0;
+}
+
+// load through L2 (CG: data written by other blocks of the same launch)
+template <bool CG, typename X>
+__device__ __forceinline__ X ldx(const X *a) {
+  if (CG) return __ldcg(a);
+  return *a;
 }
 
 // MWDG2 encode of one node of level l (Sect. 2.3): a refined node gets the
 // scale coefficients of its children (Eq. 9) and is flagged when its largest
 // normalised flow or topography detail reaches epsilon; other nodes carry no
-// flow details, so only their topography detail counts.
-template <typename T>
+// flow details, so only their topography detail counts.  SPEC: the
+// children's coefficients are read together with the node's kind (one
+// memory round trip; used on the small coarsest levels).
+template <bool SPEC, typename T>
 __device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
   const long long P = g.P, k = nid(g, l, i, j);
-  double dmax = p.DZ[k];
-  if (p.kind[k] == K_SIG) {
-    long long kc[4];
+  const uint8_t kd = p.kind[k];
+  T dmax = (T)p.DZ[k];
+  T ch[3][4][3], zc[4][2];
+  if (SPEC || kd == K_SIG) {
 #pragma unroll
-    for (int c = 0; c < 4; c++) kc[c] = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
-    for (int v = 0; v < 3; v++) {
-      T ch[4][3], sp[3];
+    for (int c = 0; c < 4; c++) {
+      const long long kc = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
 #pragma unroll
-      for (int c = 0; c < 4; c++) {
+      for (int v = 0; v < 3; v++)
 #pragma unroll
-        for (int m = 0; m < 3; m++) ch[c][m] = p.U[(3 * v + m) * P + kc[c]];
-        if (v == 0) slopes_to_h(ch[c][1], ch[c][2], p.Z[P + kc[c]], p.Z[2 * P + kc[c]]);
-      }
-      encode3(ch, sp);
-      if (v == 0) slopes_from_h(sp[1], sp[2], p.Z[P + k], p.Z[2 * P + k]);
-#pragma unroll
-      for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sp[m];
-      double dm = (double)detail_max3(ch);
-      double mx = __longlong_as_double((long long)p.ctl->vmax[v]);
-      dmax = fmax(dmax, dm / fmax(1.0, mx));
+        for (int m = 0; m < 3; m++) ch[v][c][m] = ldx<SPEC>(&p.U[(3 * v + m) * P + kc]);
+      zc[c][0] = p.Z[P + kc];
+      zc[c][1] = p.Z[2 * P + kc];
     }
   }
-  p.flag[k] = (uint8_t)(dmax >= g.eps);
+  if (kd == K_SIG) {
+    const T zp1 = p.Z[P + k], zp2 = p.Z[2 * P + k];
+#pragma unroll
+    for (int c = 0; c < 4; c++) slopes_to_h(ch[0][c][1], ch[0][c][2], zc[c][0], zc[c][1]);
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+      T sp[3];
+      encode3(ch[v], sp);
+      if (v == 0) slopes_from_h(sp[1], sp[2], zp1, zp2);
+#pragma unroll
+      for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sp[m];
+      const T mx = (T)__longlong_as_double((long long)p.ctl->vmax[v]);
+      dmax = tmax(dmax, detail_max3(ch[v]) / tmax(T(1), mx));
+    }
+  }
+  p.flag[k] = (uint8_t)(dmax >= (T)g.eps);
 }
 
 // regularised flag of node (m, a, b): prediction (the node or one of its
 // eight same-level neighbours is significant) or closure (a child is
-// refined; children's regularised flags are final by then)
-template <typename T>
+// refined; the children's regularised flags are final by then)
+template <bool CG, typename T>
 __device__ __forceinline__ uint8_t regular_flag(const Geo &g, const Ptrs<T> &p, int m, int a, int b) {
   uint8_t f = 0;
-  for (int bb = b - 1; bb <= b + 1; bb++)
-    for (int aa = a - 1; aa <= a + 1; aa++)
-      if (aa >= 0 && bb >= 0 && aa < g.nxl[m] && bb < g.nyl[m]) f |= p.flag[nid(g, m, aa, bb)];
+#pragma unroll
+  for (int bb = -1; bb <= 1; bb++)
+#pragma unroll
+    for (int aa = -1; aa <= 1; aa++) {
+      const int x = a + aa, y = b + bb;
+      if (x >= 0 && y >= 0 && x < g.nxl[m] && y < g.nyl[m]) f |= p.flag[nid(g, m, x, y)];
+    }
   if (m + 1 < g.L)
-    for (int c = 0; c < 4; c++) f |= p.flag2[nid(g, m + 1, 2 * a + (c & 1), 2 * b + (c >> 1))];
+#pragma unroll
+    for (int c = 0; c < 4; c++) f |= ldx<CG>(&p.flag2[nid(g, m + 1, 2 * a + (c & 1), 2 * b + (c >> 1))]);
   return f;
 }
 
-// one bottom-up pass at level l: the regularised flags of the children
-// (level l+1, whose significance flags are final) and the encode/flag of
-// the node itself
-template <typename T>
-__device__ __forceinline__ void adapt_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
-  if (l + 1 < g.L)
-    for (int c = 0; c < 4; c++) {
-      int a = 2 * i + (c & 1), b = 2 * j + (c >> 1);
-      p.flag2[nid(g, l + 1, a, b)] = regular_flag(g, p, l + 1, a, b);
-    }
-  encode_flag_node(g, p, l, i, j);
-}
-
 // adaptation runs only while there is time left to step (steps queued
-// beyond the end time are no-ops, as on the host side)
+// beyond the end time are no-ops, as on the host side); the condition is
+// the same in every block of a launch
 #define ADAPT_LIVE(p) ((p).ctl->t < (p).ctl->t_end)
 
+// Eq. 9 encode of a refined node from its children's stored coefficients
+// ch[v][c][m] and bed slopes zc[c]; the node's stored coefficients go to
+// out, the largest normalised flow detail is returned
 template <typename T>
-__global__ void k_adapt_level(Geo g, Ptrs<T> p, int l) {
-  long long n = (long long)g.nxl[l] * g.nyl[l];
-  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (r >= n || !ADAPT_LIVE(p)) return;
-  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
-  adapt_node(g, p, l, i, j);
+__device__ __forceinline__ T encode_sig(T (&ch)[3][4][3], const T (&zc)[4][2], T zp1, T zp2,
+                                        const T (&mx)[3], T (&out)[9]) {
+#pragma unroll
+  for (int c = 0; c < 4; c++) slopes_to_h(ch[0][c][1], ch[0][c][2], zc[c][0], zc[c][1]);
+  T dmax = T(0);
+#pragma unroll
+  for (int v = 0; v < 3; v++) {
+    T sp[3];
+    encode3(ch[v], sp);
+    if (v == 0) slopes_from_h(sp[1], sp[2], zp1, zp2);
+#pragma unroll
+    for (int m = 0; m < 3; m++) out[3 * v + m] = sp[m];
+    dmax = tmax(dmax, detail_max3(ch[v]) / tmax(T(1), mx[v]));
+  }
+  return dmax;
 }
 
-// levels lc..0 in one block (barrier between levels), then the regularised
-// flags of level 0
 template <typename T>
-__global__ void __launch_bounds__(256) k_adapt_coarse(Geo g, Ptrs<T> p, int lc) {
+struct SigStage {
+  T u[MT_NODES][9];     // stored coefficients (leaves: own; refined: encoded)
+  T z[MT_NODES][2];     // bed slopes (free-surface form)
+  T dz[MT_NODES];       // normalised topography detail
+  uint8_t kind[MT_NODES];
+};
+
+// encode + significance of one tile (CG: the children of its finest level
+// were written by other blocks of this launch)
+template <bool CG, typename T>
+__device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const Tile &tl, SigStage<T> &sh) {
+  const long long P = g.P;
+  T mx[3];
+#pragma unroll
+  for (int v = 0; v < 3; v++) mx[v] = (T)__longlong_as_double((long long)p.ctl->vmax[v]);
+  const T eps = (T)g.eps;
+  int sl[2];
+  long long kk[2];
+  staged_slots(g, tl, sl, kk);
+  uint8_t kd[2];
+  T dz[2];
+  T zs[2][2];
+#pragma unroll
+  for (int q = 0; q < 2; q++) {
+    kd[q] = K_OUT;
+    dz[q] = T(0);
+    zs[q][0] = zs[q][1] = T(0);
+    if (kk[q] >= 0) {
+      kd[q] = p.kind[kk[q]];
+      dz[q] = (T)p.DZ[kk[q]];
+      if (Form<T>::eta) {
+        zs[q][0] = p.Z[P + kk[q]];
+        zs[q][1] = p.Z[2 * P + kk[q]];
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; q++)
+    if (sl[q] < MT_NODES) {
+      sh.kind[sl[q]] = kd[q];
+      sh.dz[sl[q]] = dz[q];
+      sh.z[sl[q]][0] = zs[q][0];
+      sh.z[sl[q]][1] = zs[q][1];
+      if (kd[q] == K_LEAF)
+#pragma unroll
+        for (int m = 0; m < 9; m++) sh.u[sl[q]][m] = p.U[m * P + kk[q]];
+    }
+  // finest tile level: refined nodes read their children from global memory
+  if (kk[0] >= 0) {
+    T dmax = dz[0];
+    if (kd[0] == K_SIG) {
+      int s0, t0, i, j;
+      slot_st(sl[0], s0, t0);
+      tile_coord(g, tl, 0, t0, i, j);
+      T ch[3][4][3], zc[4][2], out[9];
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const long long kc = nid(g, tl.ltop + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
+#pragma unroll
+        for (int v = 0; v < 3; v++)
+#pragma unroll
+          for (int m = 0; m < 3; m++) ch[v][c][m] = ldx<CG>(&p.U[(3 * v + m) * P + kc]);
+        zc[c][0] = p.Z[P + kc];
+        zc[c][1] = p.Z[2 * P + kc];
+      }
+      dmax = tmax(dmax, encode_sig(ch, zc, zs[0][0], zs[0][1], mx, out));
+#pragma unroll
+      for (int m = 0; m < 9; m++) {
+        p.U[m * P + kk[0]] = out[m];
+        sh.u[sl[0]][m] = out[m];
+      }
+    }
+    p.flag[kk[0]] = (uint8_t)(dmax >= eps);
+  }
+  // coarser tile levels from shared memory
+  for (int s = 1; s < tl.nlev; s++) {
+    __syncthreads();
+    const int side = MT >> s, t = threadIdx.x;
+    if (t >= side * side) continue;
+    const int slot = tbase(s) + t;
+    const uint8_t k2 = sh.kind[slot];
+    if (k2 == K_OUT) continue;
+    int i, j;
+    tile_coord(g, tl, s, t, i, j);
+    const long long k = nid(g, tl.ltop - s, i, j);
+    T dmax = sh.dz[slot];
+    if (k2 == K_SIG) {
+      T ch[3][4][3], zc[4][2], out[9];
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const int cs = child_slot(s, t, c);
+#pragma unroll
+        for (int v = 0; v < 3; v++)
+#pragma unroll
+          for (int m = 0; m < 3; m++) ch[v][c][m] = sh.u[cs][3 * v + m];
+        zc[c][0] = sh.z[cs][0];
+        zc[c][1] = sh.z[cs][1];
+      }
+      dmax = tmax(dmax, encode_sig(ch, zc, sh.z[slot][0], sh.z[slot][1], mx, out));
+#pragma unroll
+      for (int m = 0; m < 9; m++) {
+        p.U[m * P + k] = out[m];
+        sh.u[slot][m] = out[m];
+      }
+    }
+    p.flag[k] = (uint8_t)(dmax >= eps);
+  }
+}
+
+// encode + significance flags: levels ltop..ltop-nlev+1 in tiles, then
+// (tail >= 0) levels tail..0 in the last block
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_mra_sig(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+  __shared__ SigStage<T> sh;
   if (!ADAPT_LIVE(p)) return;
-  for (int l = lc; l >= 0; l--) {
-    long long n = (long long)g.nxl[l] * g.nyl[l];
-    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
-      int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
-      adapt_node(g, p, l, i, j);
+  if (nlev > 0) sig_tile<false>(g, p, tile_of_block(g, ltop, nlev), sh);
+  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+  if (tail_is_tile(g, tail)) {
+    sig_tile<true>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
+    return;
+  }
+  for (int l = tail; l >= 0; l--) {
+    const int n = g.nxl[l] * g.nyl[l];
+    for (int r = threadIdx.x; r < n; r += blockDim.x) encode_flag_node<true>(g, p, l, r % g.nxl[l], r / g.nxl[l]);
+    __syncthreads();
+  }
+}
+
+struct RegStage {
+  uint8_t pred[MT_NODES];  // prediction: a node of the 3 x 3 same-level neighbourhood is significant
+  uint8_t f2[MT_NODES];    // regularised flag
+};
+
+// prediction flag of node (m, a, b)
+template <typename T>
+__device__ __forceinline__ uint8_t predicted(const Geo &g, const Ptrs<T> &p, int m, int a, int b) {
+  uint8_t f = 0;
+#pragma unroll
+  for (int bb = -1; bb <= 1; bb++)
+#pragma unroll
+    for (int aa = -1; aa <= 1; aa++) {
+      const int x = a + aa, y = b + bb;
+      if (x >= 0 && y >= 0 && x < g.nxl[m] && y < g.nyl[m]) f |= p.flag[nid(g, m, x, y)];
+    }
+  return f;
+}
+
+// regularised flags of one tile: prediction, then closure bottom-up
+template <bool CG, typename T>
+__device__ __forceinline__ void reg_tile(const Geo &g, const Ptrs<T> &p, const Tile &tl, RegStage &sh) {
+  int sl[2];
+  long long kk[2];
+  staged_slots(g, tl, sl, kk);
+  uint8_t pr[2] = {0, 0};
+#pragma unroll
+  for (int q = 0; q < 2; q++)
+    if (kk[q] >= 0) {
+      int s, t, i, j;
+      slot_st(sl[q], s, t);
+      tile_coord(g, tl, s, t, i, j);
+      pr[q] = predicted(g, p, tl.ltop - s, i, j);
+    }
+  uint8_t cl = 0;  // closure from the children of the finest tile level
+  if (kk[0] >= 0 && tl.ltop + 1 < g.L) {
+    int i, j;
+    tile_coord(g, tl, 0, threadIdx.x, i, j);
+#pragma unroll
+    for (int c = 0; c < 4; c++) cl |= ldx<CG>(&p.flag2[nid(g, tl.ltop + 1, 2 * i + (c & 1), 2 * j + (c >> 1))]);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; q++)
+    if (sl[q] < MT_NODES) sh.pred[sl[q]] = pr[q];
+  if (kk[0] >= 0) {
+    const uint8_t f = pr[0] | cl;
+    p.flag2[kk[0]] = f;
+    sh.f2[sl[0]] = f;
+  }
+  for (int s = 1; s < tl.nlev; s++) {
+    __syncthreads();
+    const int side = MT >> s, t = threadIdx.x;
+    if (t >= side * side) continue;
+    int i, j;
+    if (!tile_coord(g, tl, s, t, i, j)) continue;
+    const int slot = tbase(s) + t;
+    uint8_t f = sh.pred[slot];
+#pragma unroll
+    for (int c = 0; c < 4; c++) f |= sh.f2[child_slot(s, t, c)];
+    sh.f2[slot] = f;
+    p.flag2[nid(g, tl.ltop - s, i, j)] = f;
+  }
+}
+
+// regularised flags, same chunking; the CFL minimum is reset here for the
+// decode pass that follows
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_mra_regularise(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+  __shared__ RegStage sh;
+  if (ltop == g.L - 1 && blockIdx.x == 0 && threadIdx.x == 0) p.ctl->dtmin = 0x7ff0000000000000ULL;
+  if (!ADAPT_LIVE(p)) return;
+  if (nlev > 0) reg_tile<false>(g, p, tile_of_block(g, ltop, nlev), sh);
+  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+  if (tail_is_tile(g, tail)) {
+    reg_tile<true>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
+    return;
+  }
+  for (int l = tail; l >= 0; l--) {
+    const int n = g.nxl[l] * g.nyl[l];
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const int i = r % g.nxl[l], j = r / g.nxl[l];
+      p.flag2[nid(g, l, i, j)] = regular_flag<true>(g, p, l, i, j);
     }
     __syncthreads();
   }
-  long long n0 = (long long)g.nxl[0] * g.nyl[0];
-  for (long long r = threadIdx.x; r < n0; r += blockDim.x) {
-    int j = (int)(r / g.nxl[0]), i = (int)(r - (long long)j * g.nxl[0]);
-    p.flag2[nid(g, 0, i, j)] = regular_flag(g, p, 0, i, j);
-  }
 }
 
-// Eq. 10 for the new active set: every new leaf that was below an old leaf
-// takes the prolongation of that leaf's plane (one level at a time, flow in
-// depth form); each block counts its active leaves for the compaction, and
-// every leaf contributes its CFL candidate for the coming step
+// New kinds from the regularised flags (refined; active leaf: parent
+// refined or root, not refined itself; below a leaf), written to
+// kind_new while kind keeps the old ones.  Eq. 10 for the new active set:
+// every new leaf that was below an old leaf takes the prolongation of that
+// leaf's plane (one level at a time, flow in depth form).  Each block counts
+// its new leaves, every new leaf contributes its CFL candidate for the coming
+// step, and the last block turns the counts into scatter offsets.
 template <typename T>
-__global__ void k_decode_count(Geo g, Ptrs<T> p) {
+__global__ void __launch_bounds__(TPB) k_mra_decode(Geo g, Ptrs<T> p) {
   const long long P = g.P;
-  const long long base = (long long)blockIdx.x * CTILE;
+  const long long base = (long long)blockIdx.x * CTILE + threadIdx.x;
   const double t = p.ctl->t;
-  int cnt = 0;
-  double best = __longlong_as_double(0x7ff0000000000000LL);
+  // flags and old kinds of the thread's nodes, all loads issued together
+  uint8_t f[CPT], fp[CPT], ko[CPT];
+#pragma unroll
   for (int q = 0; q < CPT; q++) {
-    long long k = base + q * TPB + threadIdx.x;
-    if (k >= P || p.kind[k] != K_LEAF) continue;
-    cnt++;
+    const long long k = base + q * TPB;
+    f[q] = 0;
+    fp[q] = 1;
+    ko[q] = K_OUT;
+    if (k < P) {
+      int l, i, j;
+      node_of(g, k, l, i, j);
+      if (l < g.L) f[q] = p.flag2[k];
+      if (l > 0) fp[q] = p.flag2[nid(g, l - 1, i >> 1, j >> 1)];
+      ko[q] = p.kind[k];
+    }
+  }
+  int cnt = 0;
+  unsigned leaf_mask = 0u;
+#pragma unroll
+  for (int q = 0; q < CPT; q++) {
+    const long long k = base + q * TPB;
+    if (k >= P) continue;
+    const uint8_t nk = f[q] ? K_SIG : (fp[q] ? K_LEAF : K_BELOW);
+    p.kind_new[k] = nk;
+    if (nk == K_LEAF) {
+      cnt++;
+      leaf_mask |= 1u << q;
+    }
+  }
+  // prolongation into new leaves that were below an old leaf (rare)
+  for (int q = 0; q < CPT; q++) {
+    if (!((leaf_mask >> q) & 1u) || ko[q] != K_BELOW) continue;
+    const long long k = base + q * TPB;
     int l, i, j;
     node_of(g, k, l, i, j);
-    if (p.kind_old[k] == K_BELOW) {
-      int path[MWDG_LMAX + 1];
-      int d = 0, a = i, b = j, la = l;
-      long long ka = k;
-      while (la > 0 && p.kind_old[ka] == K_BELOW) {
-        path[d++] = (a & 1) + 2 * (b & 1);
-        a >>= 1;
-        b >>= 1;
-        la--;
-        ka = nid(g, la, a, b);
-      }
-      for (int v = 0; v < 3; v++) {
-        T sv[3];
-        for (int m = 0; m < 3; m++) sv[m] = p.U[(3 * v + m) * P + ka];
-        if (v == 0) slopes_to_h(sv[1], sv[2], p.Z[P + ka], p.Z[2 * P + ka]);
-        for (int qq = d - 1; qq >= 0; qq--) {
-          T o[3];
-          prolong3(sv[0], sv[1], sv[2], path[qq], o);
-          sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
-        }
-        if (v == 0) slopes_from_h(sv[1], sv[2], p.Z[P + k], p.Z[2 * P + k]);
-        for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sv[m];
-      }
+    int path[MWDG_LMAX + 1];
+    int d = 0, a = i, b = j, la = l;
+    long long ka = k;
+    while (la > 0 && p.kind[ka] == K_BELOW) {
+      path[d++] = (a & 1) + 2 * (b & 1);
+      a >>= 1;
+      b >>= 1;
+      la--;
+      ka = nid(g, la, a, b);
     }
-    best = fmin(best, leaf_dt_candidate(g, p, l, i, j, p.U[k], p.U[3 * P + k], p.U[6 * P + k], t));
+    for (int v = 0; v < 3; v++) {
+      T sv[3];
+      for (int m = 0; m < 3; m++) sv[m] = p.U[(3 * v + m) * P + ka];
+      if (v == 0) slopes_to_h(sv[1], sv[2], p.Z[P + ka], p.Z[2 * P + ka]);
+      for (int qq = d - 1; qq >= 0; qq--) {
+        T o[3];
+        prolong3(sv[0], sv[1], sv[2], path[qq], o);
+        sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
+      }
+      if (v == 0) slopes_from_h(sv[1], sv[2], p.Z[P + k], p.Z[2 * P + k]);
+      for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sv[m];
+    }
   }
+  // CFL candidates of the new leaves
+  T h[CPT], qx[CPT], qy[CPT];
+#pragma unroll
+  for (int q = 0; q < CPT; q++)
+    if ((leaf_mask >> q) & 1u) {
+      const long long k = base + q * TPB;
+      h[q] = p.U[k];
+      qx[q] = p.U[3 * P + k];
+      qy[q] = p.U[6 * P + k];
+    }
+  T best = tinf<T>();
+#pragma unroll
+  for (int q = 0; q < CPT; q++)
+    if ((leaf_mask >> q) & 1u) {
+      int l, i, j;
+      node_of(g, base + q * TPB, l, i, j);
+      best = tmin(best, leaf_dt_candidate(g, p, l, i, j, h[q], qx[q], qy[q], t));
+    }
   warp_min_to(&p.ctl->dtmin, best);
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   __shared__ int ws[TPB / 32];
@@ -666,6 +1049,7 @@ __global__ void k_decode_count(Geo g, Ptrs<T> p) {
     for (int w = 0; w < TPB / 32; w++) sum += ws[w];
     p.blk[blockIdx.x] = sum;
   }
+  if (last_block(&p.ctl->ticket)) block_scan_counts(gridDim.x, p.blk, p.nleaf);
 }
 
 // dt = min(C * min candidate, dt_max, t_end - t) and per-step resets
@@ -851,15 +1235,10 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
 }
 
 // local encoding (Eq. 9) of the flux view and its beds onto a refined node
-// (MWDG2 interfaces, Sect. 2.3)
+// (MWDG2 interfaces, Sect. 2.3) from its children's records rc[c]
 template <typename T>
-__device__ __forceinline__ void encode_view_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
-  const long long k = nid(g, l, i, j);
-  if (p.kind[k] != K_SIG) return;
-  T rc[4][12];
-#pragma unroll
-  for (int c = 0; c < 4; c++) load_rec(p.FZ, nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1)), rc[c]);
-  T zc[4][3], zpar[3], rec[12];
+__device__ __forceinline__ void encode_view_rec(const T (&rc)[4][12], T (&rec)[12]) {
+  T zc[4][3], zpar[3];
 #pragma unroll
   for (int c = 0; c < 4; c++)
 #pragma unroll
@@ -881,27 +1260,105 @@ __device__ __forceinline__ void encode_view_node(const Geo &g, const Ptrs<T> &p,
 #pragma unroll
     for (int m = 0; m < 3; m++) rec[3 * v + m] = sp[m];
   }
+}
+
+// one node, records read through L2 together with its kind (coarsest
+// levels that do not fit one tile)
+template <typename T>
+__device__ __forceinline__ void encode_view_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
+  const long long k = nid(g, l, i, j);
+  const uint8_t kd = p.kind[k];
+  T rc[4][12], rec[12];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    const long long kc = nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
+#pragma unroll
+    for (int m = 0; m < 12; m++) rc[c][m] = __ldcg(&p.FZ[12 * kc + m]);
+  }
+  if (kd != K_SIG) return;
+  encode_view_rec(rc, rec);
   store_rec(p.FZ, k, rec);
 }
 
 template <typename T>
-__global__ void k_encode_view(Geo g, Ptrs<T> p, int l) {
-  long long n = (long long)g.nxl[l] * g.nyl[l];
-  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
-  encode_view_node(g, p, l, i, j);
+struct ViewStage {
+  T r[MT_NODES][12];  // flux-view records (leaves: own; refined: encoded)
+  uint8_t kind[MT_NODES];
+};
+
+template <bool CG, typename T>
+__device__ __forceinline__ void view_tile(const Geo &g, const Ptrs<T> &p, const Tile &tl, ViewStage<T> &sh) {
+  int sl[2];
+  long long kk[2];
+  staged_slots(g, tl, sl, kk);
+  uint8_t kd[2];
+#pragma unroll
+  for (int q = 0; q < 2; q++) kd[q] = (kk[q] >= 0) ? p.kind[kk[q]] : K_OUT;
+#pragma unroll
+  for (int q = 0; q < 2; q++)
+    if (sl[q] < MT_NODES) {
+      sh.kind[sl[q]] = kd[q];
+      if (kd[q] == K_LEAF) {
+        T r[12];
+        load_rec(p.FZ, kk[q], r);
+#pragma unroll
+        for (int m = 0; m < 12; m++) sh.r[sl[q]][m] = r[m];
+      }
+    }
+  if (kd[0] == K_SIG) {
+    int i, j;
+    tile_coord(g, tl, 0, threadIdx.x, i, j);
+    T rc[4][12], rec[12];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const long long kc = nid(g, tl.ltop + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
+      if (CG) {
+#pragma unroll
+        for (int m = 0; m < 12; m++) rc[c][m] = __ldcg(&p.FZ[12 * kc + m]);
+      } else {
+        load_rec(p.FZ, kc, rc[c]);
+      }
+    }
+    encode_view_rec(rc, rec);
+    store_rec(p.FZ, kk[0], rec);
+#pragma unroll
+    for (int m = 0; m < 12; m++) sh.r[sl[0]][m] = rec[m];
+  }
+  for (int s = 1; s < tl.nlev; s++) {
+    __syncthreads();
+    const int side = MT >> s, t = threadIdx.x;
+    if (t >= side * side) continue;
+    const int slot = tbase(s) + t;
+    if (sh.kind[slot] != K_SIG) continue;
+    int i, j;
+    tile_coord(g, tl, s, t, i, j);
+    T rc[4][12], rec[12];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const int cs = child_slot(s, t, c);
+#pragma unroll
+      for (int m = 0; m < 12; m++) rc[c][m] = sh.r[cs][m];
+    }
+    encode_view_rec(rc, rec);
+    store_rec(p.FZ, nid(g, tl.ltop - s, i, j), rec);
+#pragma unroll
+    for (int m = 0; m < 12; m++) sh.r[slot][m] = rec[m];
+  }
 }
 
-// levels lc..0 in one block, barrier between levels
+// flux-view encode of the refined nodes, chunked as the MRA passes
 template <typename T>
-__global__ void __launch_bounds__(256) k_encode_view_coarse(Geo g, Ptrs<T> p, int lc) {
-  for (int l = lc; l >= 0; l--) {
-    long long n = (long long)g.nxl[l] * g.nyl[l];
-    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
-      int j = (int)(r / g.nxl[l]), i = (int)(r - (long long)j * g.nxl[l]);
-      encode_view_node(g, p, l, i, j);
-    }
+__global__ void __launch_bounds__(TPB) k_view_tiles(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+  __shared__ ViewStage<T> sh;
+  if (nlev > 0) view_tile<false>(g, p, tile_of_block(g, ltop, nlev), sh);
+  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+  if (tail_is_tile(g, tail)) {
+    view_tile<true>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
+    return;
+  }
+  for (int l = tail; l >= 0; l--) {
+    const int n = g.nxl[l] * g.nyl[l];
+    for (int r = threadIdx.x; r < n; r += blockDim.x) encode_view_node(g, p, l, r % g.nxl[l], r / g.nxl[l]);
     __syncthreads();
   }
 }
@@ -985,7 +1442,7 @@ template <typename T>
 struct FaceOut {
   T F0, F1, F2;       // numerical flux
   T hs, us, vs, zr;   // own revised limit
-  double bout;        // outward boundary mass flux (m^3/s), 0 inside
+  T bout;             // outward boundary mass flux (m^3/s), 0 inside
 };
 
 template <typename T>
@@ -1045,11 +1502,8 @@ __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, 
     hll(sn.hs, sn.v, sn.u, so.hs, so.v, so.u, gg, hd, F3);
     o.F0 = F3[0]; o.F1 = F3[2]; o.F2 = F3[1];
   }
-  o.bout = 0.0;
-  if (!inside) {
-    double outward = (f == 0 || f == 2) ? (double)o.F0 : -(double)o.F0;
-    o.bout = outward * g.dxl[l];
-  }
+  o.bout = T(0);
+  if (!inside) o.bout = ((f == 0 || f == 2) ? o.F0 : -o.F0) * (T)g.dxl[l];
   return o;
 }
 
@@ -1151,14 +1605,13 @@ __device__ __forceinline__ void store_var(long long P, int v, long long k, T *Ou
 // CFL candidate (fixed grids)
 template <typename T>
 __device__ __forceinline__ void next_step_reduce(const Geo &g, const Ptrs<T> &p, int l, int i, int j, T h0,
-                                                 T qx0, T qy0, double tf, double &m0, double &m1,
-                                                 double &m2, double &best) {
+                                                 T qx0, T qy0, double tf, T &m0, T &m1, T &m2, T &best) {
   if (g.mode == MWDG_ADAPTIVE) {
-    m0 = fmax(m0, (double)tabs(h0));
-    m1 = fmax(m1, (double)tabs(qx0));
-    m2 = fmax(m2, (double)tabs(qy0));
+    m0 = tmax(m0, tabs(h0));
+    m1 = tmax(m1, tabs(qx0));
+    m2 = tmax(m2, tabs(qy0));
   } else {
-    best = fmin(best, leaf_dt_candidate(g, p, l, i, j, h0, qx0, qy0, tf));
+    best = tmin(best, leaf_dt_candidate(g, p, l, i, j, h0, qx0, qy0, tf));
   }
 }
 
@@ -1180,14 +1633,15 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
   if (!(dtd > 0.0)) return;  // a zero step changes nothing (end_step ignores it too)
   const T dt = (T)dtd, gg = (T)g.g, hd = (T)g.hd, s3 = s3v<T>();
   const double tf = (STAGE == 1) ? p.ctl->t : p.ctl->t + dtd;
-  double bsum = 0.0, csum = 0.0;
+  T bsum = T(0);  // per-thread sum of a few boundary fluxes; FP64 from the warp sum on
+  double csum = 0.0;
   unsigned long long ncl = 0;
   bool bad = false;
   // stage 2 also reduces, over the new state, what the next step needs:
   // max |v0| (adaptive: the next encode's normalisation) or the CFL
   // candidate (fixed grids: the next time step)
-  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
-  double best = __longlong_as_double(0x7ff0000000000000LL);
+  T m0 = T(0), m1 = T(0), m2 = T(0);
+  T best = tinf<T>();
   const int nl = *p.nleaf;
   if (Lanes<T>::per_leaf == 4) {
     const int f = threadIdx.x & 3;
@@ -1281,13 +1735,14 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
     }
   }
   if (bad) p.ctl->nonfinite = 1;
+  double bw = (double)bsum;
   for (int o = 16; o > 0; o >>= 1) {
-    bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+    bw += __shfl_xor_sync(0xffffffffu, bw, o);
     csum += __shfl_xor_sync(0xffffffffu, csum, o);
     ncl += __shfl_xor_sync(0xffffffffu, ncl, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    if (bsum != 0.0) atomicAdd(&p.ctl->bnd[STAGE - 1], bsum);
+    if (bw != 0.0) atomicAdd(&p.ctl->bnd[STAGE - 1], bw);
     if (ncl) {
       atomicAdd(&p.ctl->n_clip, ncl);
       atomicAdd(&p.ctl->v_clip, csum);
@@ -1296,14 +1751,14 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
   if (STAGE == 2) {
     if (g.mode == MWDG_ADAPTIVE) {
       for (int o = 16; o > 0; o >>= 1) {
-        m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        m0 = tmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = tmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = tmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
       }
       if ((threadIdx.x & 31) == 0) {
-        atomic_max_pos(&p.ctl->vmax[0], m0);
-        atomic_max_pos(&p.ctl->vmax[1], m1);
-        atomic_max_pos(&p.ctl->vmax[2], m2);
+        atomic_max_pos(&p.ctl->vmax[0], (double)m0);
+        atomic_max_pos(&p.ctl->vmax[1], (double)m1);
+        atomic_max_pos(&p.ctl->vmax[2], (double)m2);
       }
     } else {
       warp_min_to(&p.ctl->dtmin, best);
@@ -1494,8 +1949,8 @@ int Launch<T>::grading_sweep(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
 }
 
 template <typename T>
-int Launch<T>::kinds(const Geo &g, const Ptrs<T> &p, const uint8_t *flag, int keep_old, cudaStream_t st) {
-  k_kinds<T><<<nblk(g.P), TPB, 0, st>>>(g, p, flag, keep_old);
+int Launch<T>::kinds(const Geo &g, const Ptrs<T> &p, const uint8_t *flag, cudaStream_t st) {
+  k_kinds<T><<<nblk(g.P), TPB, 0, st>>>(g, p, flag);
   return 1;
 }
 
@@ -1510,17 +1965,37 @@ int Launch<T>::compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
   const int nb = (int)((g.P + CTILE - 1) / CTILE);
   k_compact_count<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk);
   k_compact_scan<<<1, 1024, 0, st>>>(nb, p.blk, p.nleaf);
-  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves);
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves, nullptr);
   return 3;
 }
 
-// coarsest levels handled by one block of the MRA kernels (levels with at
-// most g.coarse_nodes nodes)
-constexpr int COARSE_TPB = 256;
+// levels 0..coarse_top run in one block (each has at most g.coarse_nodes
+// nodes; -1: none)
 inline int coarse_top(const Geo &g) {
   int lc = -1;
   while (lc + 1 < g.L && lvl(g, lc + 1) <= g.coarse_nodes) lc++;
-  return lc;  // levels 0..lc in one block (-1: none)
+  return lc;
+}
+
+// chunks of the tiled MRA passes, finest first: f(ltop, nlev, tail, blocks)
+template <class F>
+int for_chunks(const Geo &g, F &&f) {
+  if (g.L < 1) return 0;
+  const int lc = coarse_top(g);
+  int l = g.L - 1, n = 0;
+  if (l <= lc) {
+    f(l, 0, lc, 1);
+    return 1;
+  }
+  while (l > lc) {
+    const int nlev = std::min(MT_LEVELS, l - lc);
+    const int tail = (l - nlev == lc) ? lc : -1;
+    const int blocks = ((g.nxl[l] + MT - 1) / MT) * ((g.nyl[l] + MT - 1) / MT);
+    f(l, nlev, tail, blocks);
+    l -= nlev;
+    n++;
+  }
+  return n;
 }
 
 template <typename T>
@@ -1528,31 +2003,30 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
                      void (*mark)(void *, int), void *mark_arg) {
   int n = 0;
   const int grid = (int)std::min<long long>(nblk(g.P), 152 * 8);
-  MARK(KC_ENCODE);
   if (with_maxabs) {
+    MARK(KC_ENCODE);
     k_leaf_maxabs<T><<<grid, TPB, 0, st>>>(g, p);
     n++;
   }
-  // bottom-up: encode + significance of level l, regularised flags of l+1
-  const int lc = coarse_top(g);
-  for (int l = g.L - 1; l > lc; l--, n++) {
+  // bottom-up encode + significance
+  n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
     MARK(KC_ENCODE);
-    k_adapt_level<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
-  }
-  MARK(KC_ENCODE);
-  k_adapt_coarse<T><<<1, COARSE_TPB, 0, st>>>(g, p, lc);
-  n++;
+    k_mra_sig<T><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
+  });
   if (encode_only) return n;
-  MARK(KC_FLAGS);
-  n += kinds(g, p, p.flag2, 1, st);
+  // prediction + closure
+  n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
+    MARK(KC_FLAGS);
+    k_mra_regularise<T><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
+  });
+  // new kinds, decode, counts and offsets; then the scatter, which also
+  // makes the new kinds current
   MARK(KC_DECODE);
   const int nb = (int)((g.P + CTILE - 1) / CTILE);
-  k_decode_count<T><<<nb, TPB, 0, st>>>(g, p);
+  k_mra_decode<T><<<nb, TPB, 0, st>>>(g, p);
   MARK(KC_COMPACT);
-  k_compact_scan<<<1, 1024, 0, st>>>(nb, p.blk, p.nleaf);
-  MARK(KC_COMPACT);
-  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves);
-  return n + 3;
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind_new, p.blk, p.leaves, p.kind);
+  return n + 2;
 }
 
 template <typename T>
@@ -1573,7 +2047,6 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
                     void (*mark)(void *, int), void *mark_arg) {
   int n = 0;
   const bool view = (g.mode == MWDG_ADAPTIVE);
-  const int lc = coarse_top(g);
   MARK(KC_CONTROL);
   k_begin_step<<<1, 1, 0, st>>>(g, p.ctl, p.nleaf);
   n++;
@@ -1582,17 +2055,11 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
     if (stage == 1) k_leaf_limit<T, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
     else k_leaf_limit<T, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
     n++;
-    if (view) {
-      for (int l = g.L - 1; l > lc; l--, n++) {
+    if (view)
+      n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
         MARK(KC_VIEW);
-        k_encode_view<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
-      }
-      if (lc >= 0) {
-        MARK(KC_VIEW);
-        k_encode_view_coarse<T><<<1, COARSE_TPB, 0, st>>>(g, p, lc);
-        n++;
-      }
-    }
+        k_view_tiles<T><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
+      });
     if (stage == 1) {
       MARK(KC_UPDATE1);
       k_leaf_update<T, 1><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui);
