@@ -169,7 +169,7 @@ mwdg_status allocate_state(mwdg_ctx *c) {
   CK(cudaMemsetAsync(p.FZ, 0, 12 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.Z, 0, 3 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.NM, 0, P * sizeof(T), c->st));
-  CK(cudaMemsetAsync(p.DZ, 0, P * sizeof(double), c->st));
+  CK(cudaMemsetAsync(p.DZ, 0, P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.flag, 0, P, c->st));
   CK(cudaMemsetAsync(p.flag2, 0, P, c->st));
   p.ctl = c->ctl;
@@ -243,8 +243,9 @@ int launch_step(mwdg_ctx *c, int with_maxabs) {
   return dispatch(c, [&](auto &p, auto *) {
     using T = std::remove_pointer_t<decltype(p.U)>;
     int n = 0;
-    if (g.mode == MWDG_ADAPTIVE) n += Launch<T>::adapt(g, p, 0, with_maxabs, c->st, mark_cb, c);
-    n += Launch<T>::step(g, p, c->grid_leaves, c->st, mark_cb, c);
+    const int adaptive = (g.mode == MWDG_ADAPTIVE);
+    if (adaptive) n += Launch<T>::adapt(g, p, 0, with_maxabs, c->st, mark_cb, c, 1);
+    n += Launch<T>::step(g, p, c->grid_leaves, c->st, mark_cb, c, adaptive);
     return n;
   });
 }
@@ -378,6 +379,7 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
   g.dt_max = p->dt_max;
   g.eps = p->eps;
   g.area = (double)g.nxl[g.L] * g.dxl[g.L] * (double)g.nyl[g.L] * g.dxl[g.L];
+  sync_single(g);
   for (int e = 0; e < 4; e++) g.bc[e] = p->bc[e];
   g.inflow_edge = -1;
   g.inflow_c0 = 0;
@@ -595,6 +597,7 @@ mwdg_status mwdg_mra_adapt(mwdg_ctx *c, double eps, int64_t *n_active) {
   Geo &g = c->g;
   if (g.mode == MWDG_UNIFORM) return fail(c, MWDG_ERR_STATE, "uniform grids do not adapt");
   g.eps = eps;
+  sync_single(g);
   drop_graph(c);
   if (g.mode == MWDG_STATIC) {
     if (c->stepped) return fail(c, MWDG_ERR_STATE, "a static grid is fixed once stepping started");
@@ -785,11 +788,11 @@ struct StateHeader {
   int64_t P;
   Ctl ctl;
 };
-constexpr char kMagic[8] = {'M', 'W', 'D', 'G', 'S', 'T', '0', '1'};
+constexpr char kMagic[8] = {'M', 'W', 'D', 'G', 'S', 'T', '0', '2'};
 
 size_t state_bytes(const mwdg_ctx *c) {
   const size_t P = (size_t)c->g.P, ts = (c->g.prec == MWDG_F64) ? 8 : 4;
-  return sizeof(StateHeader) + P + 9 * P * ts + 3 * P * ts + P * ts + P * 8;
+  return sizeof(StateHeader) + P + 9 * P * ts + 3 * P * ts + P * ts + P * ts;
 }
 }  // namespace
 
@@ -807,7 +810,7 @@ mwdg_status mwdg_save_state(mwdg_ctx *c, void *buf, int64_t cap) {
   const Geo &g = c->g;
   StateHeader h{};
   memcpy(h.magic, kMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.prec = g.prec;
   h.L = g.L;
   h.M = g.M;
@@ -833,7 +836,7 @@ mwdg_status mwdg_save_state(mwdg_ctx *c, void *buf, int64_t cap) {
   b += 3 * P * ts;
   CK(cudaMemcpyAsync(b, NM, P * ts, cudaMemcpyDeviceToHost, c->st));
   b += P * ts;
-  CK(cudaMemcpyAsync(b, DZ, P * 8, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(b, DZ, P * ts, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   return MWDG_OK;
 }
@@ -844,7 +847,7 @@ mwdg_status mwdg_load_state(mwdg_ctx *c, const void *buf, int64_t size) {
   const Geo &g = c->g;
   StateHeader h;
   memcpy(&h, buf, sizeof h);
-  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return fail(c, MWDG_ERR_ARG, "not a state buffer");
+  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 2) return fail(c, MWDG_ERR_ARG, "not a state buffer");
   if (h.prec != g.prec || h.L != g.L || h.M != g.M || h.N != g.N || h.P != g.P || h.mode != g.mode)
     return fail(c, MWDG_ERR_DIMS, "state belongs to another grid or precision");
   if (size < (int64_t)state_bytes(c)) return fail(c, MWDG_ERR_ARG, "state buffer truncated");
@@ -863,7 +866,7 @@ mwdg_status mwdg_load_state(mwdg_ctx *c, const void *buf, int64_t size) {
   b += 3 * P * ts;
   CK(cudaMemcpyAsync(NM, b, P * ts, cudaMemcpyHostToDevice, c->st));
   b += P * ts;
-  CK(cudaMemcpyAsync(DZ, b, P * 8, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(DZ, b, P * ts, cudaMemcpyHostToDevice, c->st));
   Ctl ctl = h.ctl;
   ctl.t_end = 1e300;
   ctl.blocks_done = 0u;

@@ -38,7 +38,19 @@ struct Geo {
   int inflow_edge, inflow_c0, inflow_c1, nknots;
   double rain_rate, rain_t_end;
   long long coarse_nodes;      // MRA levels up to this size run in one block
+  // single-precision copies of g, h_dry, eps and the element sizes, so that
+  // FP32 kernels convert nothing from FP64 on the device
+  float gf, hdf, epsf;
+  float dxlf[MWDG_LMAX + 1];
 };
+
+// refresh the single-precision copies after any change of g, hd, eps or dxl
+inline void sync_single(Geo &g) {
+  g.gf = (float)g.g;
+  g.hdf = (float)g.hd;
+  g.epsf = (float)g.eps;
+  for (int l = 0; l <= MWDG_LMAX; l++) g.dxlf[l] = (float)g.dxl[l];
+}
 
 // Device arrays.  Coefficient arrays are component-major with stride P:
 // component m of node k is at [m * P + k]; node (l, i, j) is
@@ -53,7 +65,7 @@ struct Ptrs {
             // (9) and its bed planes (3); refined nodes hold their encoding
   T *Z;     // static topography pyramid (3)
   T *NM;    // Manning n per node (1)
-  double *DZ;   // normalised topography detail per node
+  T *DZ;        // normalised topography detail per node
   uint8_t *kind, *flag, *flag2;
   uint8_t *kind_new;  // kinds of the next active set while the old ones are still read
   long long *leaves;  // active leaves, packed (level << 56 | j << 28 | i)
@@ -81,10 +93,12 @@ template <typename T> struct Launch {
   static int kinds(const Geo &g, const Ptrs<T> &p, const uint8_t *flag, cudaStream_t st);
   static int all_finest(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
   static int compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
+  // begin: the adaptation's last kernel also starts the step that follows
   static int adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_maxabs,
-                   cudaStream_t st, void (*mark)(void *, int), void *mark_arg);
+                   cudaStream_t st, void (*mark)(void *, int), void *mark_arg, int begin = 0);
+  // begun: the step was started by the adaptation
   static int step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st,
-                  void (*mark)(void *, int), void *mark_arg);
+                  void (*mark)(void *, int), void *mark_arg, int begun = 0);
   // max |v0| and the CFL candidate over the current leaves (after a load,
   // a checkpoint restore or a stand-alone adaptation)
   static int prime(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st);

@@ -41,6 +41,20 @@ __device__ __forceinline__ void slopes_from_h(T &s1, T &s2, T z1, T z2) {
   }
 }
 
+// Geo constants in the coefficient type (FP32: the single-precision copies)
+template <typename T> __device__ __forceinline__ T geo_g(const Geo &g);
+template <> __device__ __forceinline__ float geo_g<float>(const Geo &g) { return g.gf; }
+template <> __device__ __forceinline__ double geo_g<double>(const Geo &g) { return g.g; }
+template <typename T> __device__ __forceinline__ T geo_hd(const Geo &g);
+template <> __device__ __forceinline__ float geo_hd<float>(const Geo &g) { return g.hdf; }
+template <> __device__ __forceinline__ double geo_hd<double>(const Geo &g) { return g.hd; }
+template <typename T> __device__ __forceinline__ T geo_eps(const Geo &g);
+template <> __device__ __forceinline__ float geo_eps<float>(const Geo &g) { return g.epsf; }
+template <> __device__ __forceinline__ double geo_eps<double>(const Geo &g) { return g.eps; }
+template <typename T> __device__ __forceinline__ T geo_dx(const Geo &g, int l);
+template <> __device__ __forceinline__ float geo_dx<float>(const Geo &g, int l) { return g.dxlf[l]; }
+template <> __device__ __forceinline__ double geo_dx<double>(const Geo &g, int l) { return g.dxl[l]; }
+
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 __device__ __forceinline__ void atomic_min_pos(unsigned long long *a, double x) {
@@ -169,7 +183,7 @@ __global__ void k_encode_z(Geo g, Ptrs<T> p, int l) {
 #pragma unroll
   for (int m = 0; m < 3; m++) p.Z[m * P + k] = sp[m];
   double norm = fmax(1.0, __longlong_as_double((long long)p.ctl->vmax[0]));
-  p.DZ[k] = (double)detail_max3(ch) / norm;
+  p.DZ[k] = (T)((double)detail_max3(ch) / norm);
 }
 
 // Manning n: coarser nodes hold the mean of their children
@@ -265,7 +279,7 @@ template <typename T>
 __global__ void k_static_flags(Geo g, Ptrs<T> p) {
   long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k >= g.P) return;
-  p.flag[k] = (k < g.off[g.L]) ? (uint8_t)(p.DZ[k] >= g.eps) : (uint8_t)0;
+  p.flag[k] = (k < g.off[g.L]) ? (uint8_t)((double)p.DZ[k] >= g.eps) : (uint8_t)0;
 }
 
 // parent closure from level l to l-1: a flagged child flags its parent
@@ -381,12 +395,49 @@ __device__ __forceinline__ void block_scan_counts(int nb, int *blk, int *total) 
 
 static __global__ void k_compact_scan(int nb, int *blk, int *total) { block_scan_counts(nb, blk, total); }
 
+// true in exactly one block, the last to get here; every block's global
+// writes before this point are visible to that block's L2 reads afterwards
+__device__ __forceinline__ bool last_block(unsigned int *ticket) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int v = atomicAdd(ticket, 1u);
+    last = (v == gridDim.x - 1);
+    if (last) {
+      *ticket = 0u;  // ready for the next launch
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  return last != 0;
+}
+
+// dt = min(C * min candidate, dt_max, t_end - t) and per-step resets (one thread)
+__device__ __forceinline__ void begin_step(const Geo &g, Ctl *c, const int *nleaf) {
+  double best = __longlong_as_double((long long)c->dtmin);
+  double dt = g.dt_max;
+  if (best < __longlong_as_double(0x7ff0000000000000LL)) dt = fmin(dt, g.cfl * best);
+  dt = fmin(dt, c->t_end - c->t);
+  c->dt = dt > 0.0 ? dt : 0.0;
+  c->bnd[0] = 0.0;
+  c->bnd[1] = 0.0;
+  c->blocks_done = 0u;
+  // the reductions that the last kernel of this step accumulates for the
+  // next; a zero step changes nothing, so the current ones stay valid
+  if (c->dt > 0.0) {
+    c->updates += *nleaf;
+    c->dtmin = 0x7ff0000000000000ULL;
+    c->vmax[0] = c->vmax[1] = c->vmax[2] = 0ULL;
+  }
+}
+
 // order-preserving scatter of the active leaves (each thread owns CPT
 // consecutive nodes, read as one 8-byte word); with kind_out the kinds are
 // also copied there
 static_assert(CPT == 8, "one 8-byte word of kinds per thread");
 static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *blk, long long *leaves,
-                                         uint8_t *kind_out) {
+                                         uint8_t *kind_out, Ctl *begin_ctl, const int *nleaf) {
   const long long P = g.P;
   const long long base = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
   const bool full = base + CPT <= P;
@@ -435,6 +486,8 @@ static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *
       leaves[pos++] = pack_leaf(l, i, j);
     }
   }
+  // with begin_ctl, the last block also starts the step on the new leaves
+  if (begin_ctl && last_block(&begin_ctl->ticket) && threadIdx.x == 0) begin_step(g, begin_ctl, nleaf);
 }
 
 // ---------------------------------------------------------------------------
@@ -504,8 +557,8 @@ __global__ void k_leaf_maxabs(Geo g, Ptrs<T> p) {
 template <typename T>
 __device__ __forceinline__ T leaf_dt_candidate(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
                                                T h0, T qx0, T qy0, double t) {
-  const T gg = (T)g.g, hd = (T)g.hd;
-  const T dxl = (T)g.dxl[l];
+  const T gg = geo_g<T>(g), hd = geo_hd<T>(g);
+  const T dxl = geo_dx<T>(g, l);
   T best = tinf<T>();
   if (h0 > hd) {
     T u = qx0 / h0, v = qy0 / h0;
@@ -576,6 +629,10 @@ constexpr uint8_t K_OUT = 0xff;             // slot outside its level
 
 struct Tile { int ltop, nlev, bx, by; };
 
+// resident blocks per SM asked of the latency-bound MRA kernels (FP32: at
+// most 64 registers a thread; FP64 keeps its registers)
+template <typename T> struct MraOcc { static constexpr int blocks = std::is_same<T, float>::value ? 4 : 1; };
+
 __device__ __forceinline__ Tile tile_of_block(const Geo &g, int ltop, int nlev) {
   const int tiles_x = (g.nxl[ltop] + MT - 1) / MT;
   return Tile{ltop, nlev, (int)(blockIdx.x % tiles_x), (int)(blockIdx.x / tiles_x)};
@@ -623,24 +680,6 @@ __device__ __forceinline__ void staged_slots(const Geo &g, const Tile &tl, int s
   }
 }
 
-// true in exactly one block, the last to get here; every block's global
-// writes before this point are visible to that block's L2 reads afterwards
-__device__ __forceinline__ bool last_block(unsigned int *ticket) {
-  __shared__ int last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int v = atomicAdd(ticket, 1u);
-    last = (v == gridDim.x - 1);
-    if (last) {
-      *ticket = 0u;  // ready for the next launch
-      __threadfence();
-    }
-  }
-  __syncthreads();
-  return last != 0;
-}
-
 // load through L2 (CG: data written by other blocks of the same launch)
 template <bool CG, typename X>
 __device__ __forceinline__ X ldx(const X *a) {
@@ -658,7 +697,7 @@ template <bool SPEC, typename T>
 __device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
   const long long P = g.P, k = nid(g, l, i, j);
   const uint8_t kd = p.kind[k];
-  T dmax = (T)p.DZ[k];
+  T dmax = p.DZ[k];
   T ch[3][4][3], zc[4][2];
   if (SPEC || kd == K_SIG) {
 #pragma unroll
@@ -687,7 +726,7 @@ __device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p,
       dmax = tmax(dmax, detail_max3(ch[v]) / tmax(T(1), mx));
     }
   }
-  p.flag[k] = (uint8_t)(dmax >= (T)g.eps);
+  p.flag[k] = (uint8_t)(dmax >= geo_eps<T>(g));
 }
 
 // regularised flag of node (m, a, b): prediction (the node or one of its
@@ -741,6 +780,7 @@ struct SigStage {
   T z[MT_NODES][2];     // bed slopes (free-surface form)
   T dz[MT_NODES];       // normalised topography detail
   uint8_t kind[MT_NODES];
+  T mx[3];              // max |v0| of h, qx, qy (normalisation of the flow details)
 };
 
 // encode + significance of one tile (CG: the children of its finest level
@@ -748,10 +788,8 @@ struct SigStage {
 template <bool CG, typename T>
 __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const Tile &tl, SigStage<T> &sh) {
   const long long P = g.P;
-  T mx[3];
-#pragma unroll
-  for (int v = 0; v < 3; v++) mx[v] = (T)__longlong_as_double((long long)p.ctl->vmax[v]);
-  const T eps = (T)g.eps;
+  if (threadIdx.x < 3) sh.mx[threadIdx.x] = (T)__longlong_as_double((long long)p.ctl->vmax[threadIdx.x]);
+  const T eps = geo_eps<T>(g);
   int sl[2];
   long long kk[2];
   staged_slots(g, tl, sl, kk);
@@ -765,7 +803,7 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
     zs[q][0] = zs[q][1] = T(0);
     if (kk[q] >= 0) {
       kd[q] = p.kind[kk[q]];
-      dz[q] = (T)p.DZ[kk[q]];
+      dz[q] = p.DZ[kk[q]];
       if (Form<T>::eta) {
         zs[q][0] = p.Z[P + kk[q]];
         zs[q][1] = p.Z[2 * P + kk[q]];
@@ -783,6 +821,10 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
 #pragma unroll
         for (int m = 0; m < 9; m++) sh.u[sl[q]][m] = p.U[m * P + kk[q]];
     }
+  __syncthreads();
+  T mx[3];
+#pragma unroll
+  for (int v = 0; v < 3; v++) mx[v] = sh.mx[v];
   // finest tile level: refined nodes read their children from global memory
   if (kk[0] >= 0) {
     T dmax = dz[0];
@@ -848,7 +890,7 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
 // encode + significance flags: levels ltop..ltop-nlev+1 in tiles, then
 // (tail >= 0) levels tail..0 in the last block
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_mra_sig(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_sig(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
   __shared__ SigStage<T> sh;
   if (!ADAPT_LIVE(p)) return;
   if (nlev > 0) sig_tile<false>(g, p, tile_of_block(g, ltop, nlev), sh);
@@ -958,87 +1000,120 @@ __global__ void __launch_bounds__(TPB) k_mra_regularise(Geo g, Ptrs<T> p, int lt
 // leaf's plane (one level at a time, flow in depth form).  Each block counts
 // its new leaves, every new leaf contributes its CFL candidate for the coming
 // step, and the last block turns the counts into scatter offsets.
+// prolongation (Eq. 10) into new leaf k (level l, i, j) from the old leaf
+// above it (flow in depth form, one level at a time)
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_mra_decode(Geo g, Ptrs<T> p) {
+__device__ __noinline__ void prolong_from_old_leaf(const Geo &g, const Ptrs<T> &p, long long k, int l, int i,
+                                                   int j) {
   const long long P = g.P;
-  const long long base = (long long)blockIdx.x * CTILE + threadIdx.x;
+  int path[MWDG_LMAX + 1];
+  int d = 0, a = i, b = j, la = l;
+  long long ka = k;
+  while (la > 0 && p.kind[ka] == K_BELOW) {
+    path[d++] = (a & 1) + 2 * (b & 1);
+    a >>= 1;
+    b >>= 1;
+    la--;
+    ka = nid(g, la, a, b);
+  }
+  for (int v = 0; v < 3; v++) {
+    T sv[3];
+    for (int m = 0; m < 3; m++) sv[m] = p.U[(3 * v + m) * P + ka];
+    if (v == 0) slopes_to_h(sv[1], sv[2], p.Z[P + ka], p.Z[2 * P + ka]);
+    for (int qq = d - 1; qq >= 0; qq--) {
+      T o[3];
+      prolong3(sv[0], sv[1], sv[2], path[qq], o);
+      sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
+    }
+    if (v == 0) slopes_from_h(sv[1], sv[2], p.Z[P + k], p.Z[2 * P + k]);
+    for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sv[m];
+  }
+}
+
+// bytes q of an 8-byte word
+__device__ __forceinline__ uint8_t byte_of(uint2 w, int q) {
+  return (uint8_t)(((q < 4) ? (w.x >> (8 * q)) : (w.y >> (8 * (q - 4)))) & 0xffu);
+}
+
+// Each thread takes CPT consecutive nodes (the scatter's layout); when they
+// lie in one row of one level (the common case) their flags and kinds are
+// read as 8-byte words and their parents follow from the first node.
+template <typename T>
+__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_decode(Geo g, Ptrs<T> p) {
+  const long long P = g.P;
+  const long long k0 = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
   const double t = p.ctl->t;
-  // flags and old kinds of the thread's nodes, all loads issued together
-  uint8_t f[CPT], fp[CPT], ko[CPT];
-#pragma unroll
-  for (int q = 0; q < CPT; q++) {
-    const long long k = base + q * TPB;
-    f[q] = 0;
-    fp[q] = 1;
-    ko[q] = K_OUT;
-    if (k < P) {
-      int l, i, j;
-      node_of(g, k, l, i, j);
-      if (l < g.L) f[q] = p.flag2[k];
-      if (l > 0) fp[q] = p.flag2[nid(g, l - 1, i >> 1, j >> 1)];
-      ko[q] = p.kind[k];
-    }
-  }
   int cnt = 0;
-  unsigned leaf_mask = 0u;
-#pragma unroll
-  for (int q = 0; q < CPT; q++) {
-    const long long k = base + q * TPB;
-    if (k >= P) continue;
-    const uint8_t nk = f[q] ? K_SIG : (fp[q] ? K_LEAF : K_BELOW);
-    p.kind_new[k] = nk;
-    if (nk == K_LEAF) {
-      cnt++;
-      leaf_mask |= 1u << q;
-    }
-  }
-  // prolongation into new leaves that were below an old leaf (rare)
-  for (int q = 0; q < CPT; q++) {
-    if (!((leaf_mask >> q) & 1u) || ko[q] != K_BELOW) continue;
-    const long long k = base + q * TPB;
-    int l, i, j;
-    node_of(g, k, l, i, j);
-    int path[MWDG_LMAX + 1];
-    int d = 0, a = i, b = j, la = l;
-    long long ka = k;
-    while (la > 0 && p.kind[ka] == K_BELOW) {
-      path[d++] = (a & 1) + 2 * (b & 1);
-      a >>= 1;
-      b >>= 1;
-      la--;
-      ka = nid(g, la, a, b);
-    }
-    for (int v = 0; v < 3; v++) {
-      T sv[3];
-      for (int m = 0; m < 3; m++) sv[m] = p.U[(3 * v + m) * P + ka];
-      if (v == 0) slopes_to_h(sv[1], sv[2], p.Z[P + ka], p.Z[2 * P + ka]);
-      for (int qq = d - 1; qq >= 0; qq--) {
-        T o[3];
-        prolong3(sv[0], sv[1], sv[2], path[qq], o);
-        sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
-      }
-      if (v == 0) slopes_from_h(sv[1], sv[2], p.Z[P + k], p.Z[2 * P + k]);
-      for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sv[m];
-    }
-  }
-  // CFL candidates of the new leaves
-  T h[CPT], qx[CPT], qy[CPT];
-#pragma unroll
-  for (int q = 0; q < CPT; q++)
-    if ((leaf_mask >> q) & 1u) {
-      const long long k = base + q * TPB;
-      h[q] = p.U[k];
-      qx[q] = p.U[3 * P + k];
-      qy[q] = p.U[6 * P + k];
-    }
   T best = tinf<T>();
+  if (k0 < P) {
+    int l, i0, j0;
+    node_of(g, k0, l, i0, j0);
+    uint8_t nk[CPT];
+    unsigned leaf_mask = 0u, below_mask = 0u;
+    const bool row = (k0 + CPT <= P) && (i0 + CPT <= g.nxl[l]);
+    if (row) {
+      const uint2 ko8 = *reinterpret_cast<const uint2 *>(p.kind + k0);
+      const uint2 f8 = (l < g.L) ? *reinterpret_cast<const uint2 *>(p.flag2 + k0) : make_uint2(0u, 0u);
+      // parents' flags, byte m for parent (i0 >> 1) + m (five when i0 is odd)
+      unsigned long long fpw = 0x0101010101ULL;
+      if (l > 0) {
+        const long long kp = nid(g, l - 1, i0 >> 1, j0 >> 1);
+        fpw = 0ULL;
 #pragma unroll
-  for (int q = 0; q < CPT; q++)
-    if ((leaf_mask >> q) & 1u) {
-      int l, i, j;
-      node_of(g, base + q * TPB, l, i, j);
-      best = tmin(best, leaf_dt_candidate(g, p, l, i, j, h[q], qx[q], qy[q], t));
+        for (int m = 0; m <= CPT / 2; m++)
+          if (m < CPT / 2 || (i0 & 1)) fpw |= (unsigned long long)p.flag2[kp + m] << (8 * m);
+      }
+#pragma unroll
+      for (int q = 0; q < CPT; q++) {
+        const uint8_t f = byte_of(f8, q);
+        const uint8_t par = (uint8_t)((fpw >> (8 * ((q + (i0 & 1)) >> 1))) & 0xffULL);
+        nk[q] = f ? K_SIG : (par ? K_LEAF : K_BELOW);
+        if (nk[q] == K_LEAF) {
+          leaf_mask |= 1u << q;
+          if (byte_of(ko8, q) == K_BELOW) below_mask |= 1u << q;
+        }
+      }
+      uint2 w = make_uint2(0u, 0u);
+#pragma unroll
+      for (int q = 0; q < CPT; q++) {
+        if (q < 4) w.x |= (unsigned)nk[q] << (8 * q);
+        else w.y |= (unsigned)nk[q] << (8 * (q - 4));
+      }
+      *reinterpret_cast<uint2 *>(p.kind_new + k0) = w;
+      // prolongation into new leaves that were below an old leaf (rare)
+      for (int q = 0; q < CPT; q++)
+        if ((below_mask >> q) & 1u) prolong_from_old_leaf(g, p, k0 + q, l, i0 + q, j0);
+      // CFL candidates of the new leaves
+      T h[CPT], qx[CPT], qy[CPT];
+#pragma unroll
+      for (int q = 0; q < CPT; q++)
+        if ((leaf_mask >> q) & 1u) {
+          h[q] = p.U[k0 + q];
+          qx[q] = p.U[3 * P + k0 + q];
+          qy[q] = p.U[6 * P + k0 + q];
+        }
+#pragma unroll
+      for (int q = 0; q < CPT; q++)
+        if ((leaf_mask >> q) & 1u) best = tmin(best, leaf_dt_candidate(g, p, l, i0 + q, j0, h[q], qx[q], qy[q], t));
+      cnt = __popc(leaf_mask);
+    } else {
+      // nodes across a row or level boundary, or the end of the pyramid
+      for (int q = 0; q < CPT; q++) {
+        const long long k = k0 + q;
+        if (k >= P) break;
+        int lq, i, j;
+        node_of(g, k, lq, i, j);
+        const int f = (lq < g.L) ? p.flag2[k] : 0;
+        const int par = (lq == 0) ? 1 : p.flag2[nid(g, lq - 1, i >> 1, j >> 1)];
+        const uint8_t n = f ? K_SIG : (par ? K_LEAF : K_BELOW);
+        p.kind_new[k] = n;
+        if (n != K_LEAF) continue;
+        cnt++;
+        if (p.kind[k] == K_BELOW) prolong_from_old_leaf(g, p, k, lq, i, j);
+        best = tmin(best, leaf_dt_candidate(g, p, lq, i, j, p.U[k], p.U[3 * P + k], p.U[6 * P + k], t));
+      }
     }
+  }
   warp_min_to(&p.ctl->dtmin, best);
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   __shared__ int ws[TPB / 32];
@@ -1052,24 +1127,7 @@ __global__ void __launch_bounds__(TPB) k_mra_decode(Geo g, Ptrs<T> p) {
   if (last_block(&p.ctl->ticket)) block_scan_counts(gridDim.x, p.blk, p.nleaf);
 }
 
-// dt = min(C * min candidate, dt_max, t_end - t) and per-step resets
-static __global__ void k_begin_step(Geo g, Ctl *c, const int *nleaf) {
-  double best = __longlong_as_double((long long)c->dtmin);
-  double dt = g.dt_max;
-  if (best < __longlong_as_double(0x7ff0000000000000LL)) dt = fmin(dt, g.cfl * best);
-  dt = fmin(dt, c->t_end - c->t);
-  c->dt = dt > 0.0 ? dt : 0.0;
-  c->bnd[0] = 0.0;
-  c->bnd[1] = 0.0;
-  c->blocks_done = 0u;
-  // the reductions that the last kernel of this step accumulates for the
-  // next; a zero step changes nothing, so the current ones stay valid
-  if (c->dt > 0.0) {
-    c->updates += *nleaf;
-    c->dtmin = 0x7ff0000000000000ULL;
-    c->vmax[0] = c->vmax[1] = c->vmax[2] = 0ULL;
-  }
-}
+static __global__ void k_begin_step(Geo g, Ctl *c, const int *nleaf) { begin_step(g, c, nleaf); }
 
 // end of a step: mass budget, time and step count (run once, by the last
 // block of the stage-2 update to finish)
@@ -1113,7 +1171,7 @@ __device__ __forceinline__ T friction_factor(T h0, T qx0, T qy0, T nm, T dt, T g
 template <typename T, bool FRIC>
 __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   const long long P = g.P;
-  const T hd = (T)g.hd, s3 = s3v<T>(), gg = (T)g.g;
+  const T hd = geo_hd<T>(g), s3 = s3v<T>(), gg = geo_g<T>(g);
   const double dtd = p.ctl->dt;
   const T dt = (T)dtd;
   const bool rain = FRIC && p.ctl->t < g.rain_t_end && g.rain_rate > 0.0;
@@ -1448,7 +1506,7 @@ struct FaceOut {
 template <typename T>
 __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
                                                 const T (&w)[9], const T (&zc)[3], int f, double tf) {
-  const T gg = (T)g.g, hd = (T)g.hd;
+  const T gg = geo_g<T>(g), hd = geo_hd<T>(g);
   T own[4], nb[4];
   own[0] = first_face(w[0], w[1], w[2], zc[0], f);
   own[1] = face_value(w[3], w[4], w[5], f);
@@ -1503,7 +1561,7 @@ __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, 
     o.F0 = F3[0]; o.F1 = F3[2]; o.F2 = F3[1];
   }
   o.bout = T(0);
-  if (!inside) o.bout = ((f == 0 || f == 2) ? o.F0 : -o.F0) * (T)g.dxl[l];
+  if (!inside) o.bout = ((f == 0 || f == 2) ? o.F0 : -o.F0) * geo_dx<T>(g, l);
   return o;
 }
 
@@ -1520,8 +1578,8 @@ __device__ __forceinline__ void finish_var(const Geo &g, const Ptrs<T> &p, int v
                                            const T (&zr)[4], T dt, const T *Wst, const T *Wcomb,
                                            T &o0, T &o1, T &o2) {
   const long long P = g.P;
-  const T gg = (T)g.g, s3 = s3v<T>();
-  const T dxl = (T)g.dxl[l];
+  const T gg = geo_g<T>(g), s3 = s3v<T>();
+  const T dxl = geo_dx<T>(g, l);
   // physical fluxes of the own revised limits, component v
   T Fx0, Fx1, Gy0, Gy1;
   {
@@ -1576,7 +1634,7 @@ __device__ __forceinline__ void post_var(const Geo &g, const Ptrs<T> &p, int v, 
                                          bool &bad) {
   const long long P = g.P;
   const T h0c = (h0n < T(0)) ? T(0) : h0n;
-  const bool dry = !(h0c > (T)g.hd);
+  const bool dry = !(h0c > geo_hd<T>(g));
   if (v == 0) {
     if (h0n < T(0)) {
       ncl++;
@@ -1631,7 +1689,7 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
   const long long P = g.P;
   const double dtd = p.ctl->dt;
   if (!(dtd > 0.0)) return;  // a zero step changes nothing (end_step ignores it too)
-  const T dt = (T)dtd, gg = (T)g.g, hd = (T)g.hd, s3 = s3v<T>();
+  const T dt = (T)dtd, gg = geo_g<T>(g), hd = geo_hd<T>(g), s3 = s3v<T>();
   const double tf = (STAGE == 1) ? p.ctl->t : p.ctl->t + dtd;
   T bsum = T(0);  // per-thread sum of a few boundary fluxes; FP64 from the warp sum on
   double csum = 0.0;
@@ -1965,7 +2023,7 @@ int Launch<T>::compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
   const int nb = (int)((g.P + CTILE - 1) / CTILE);
   k_compact_count<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk);
   k_compact_scan<<<1, 1024, 0, st>>>(nb, p.blk, p.nleaf);
-  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves, nullptr);
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves, nullptr, nullptr, nullptr);
   return 3;
 }
 
@@ -2000,7 +2058,7 @@ int for_chunks(const Geo &g, F &&f) {
 
 template <typename T>
 int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_maxabs, cudaStream_t st,
-                     void (*mark)(void *, int), void *mark_arg) {
+                     void (*mark)(void *, int), void *mark_arg, int begin) {
   int n = 0;
   const int grid = (int)std::min<long long>(nblk(g.P), 152 * 8);
   if (with_maxabs) {
@@ -2025,7 +2083,8 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
   const int nb = (int)((g.P + CTILE - 1) / CTILE);
   k_mra_decode<T><<<nb, TPB, 0, st>>>(g, p);
   MARK(KC_COMPACT);
-  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind_new, p.blk, p.leaves, p.kind);
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind_new, p.blk, p.leaves, p.kind, begin ? p.ctl : nullptr,
+                                        p.nleaf);
   return n + 2;
 }
 
@@ -2044,12 +2103,14 @@ int Launch<T>::dt_only(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStre
 
 template <typename T>
 int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st,
-                    void (*mark)(void *, int), void *mark_arg) {
+                    void (*mark)(void *, int), void *mark_arg, int begun) {
   int n = 0;
   const bool view = (g.mode == MWDG_ADAPTIVE);
-  MARK(KC_CONTROL);
-  k_begin_step<<<1, 1, 0, st>>>(g, p.ctl, p.nleaf);
-  n++;
+  if (!begun) {
+    MARK(KC_CONTROL);
+    k_begin_step<<<1, 1, 0, st>>>(g, p.ctl, p.nleaf);
+    n++;
+  }
   for (int stage = 1; stage <= 2; stage++) {
     MARK(KC_LIMIT);
     if (stage == 1) k_leaf_limit<T, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
