@@ -60,6 +60,13 @@ enum { MWDG_UNIFORM = 0, MWDG_STATIC = 1, MWDG_ADAPTIVE = 2 };
 enum { MWDG_F64 = 0, MWDG_F32 = 1 };
 enum { MWDG_WALL = 0, MWDG_OPEN = 1 };
 enum { MWDG_WEST = 0, MWDG_EAST = 1, MWDG_SOUTH = 2, MWDG_NORTH = 3 };
+/* flux through a face between a leaf and a finer (refined) neighbour on a
+ * static grid: PAPER, each side from its own same-level view (Sect. 2.2.1;
+ * exactly well-balanced, mass moves at round-off only on homogeneous
+ * faces); REFLUX, the coarse side takes the mean of the two fine leaves'
+ * fluxes through their halves of the face (mass conserved to round-off,
+ * lake at rest no longer exact at those faces).  Adaptive grids use PAPER. */
+enum { MWDG_IFACE_PAPER = 0, MWDG_IFACE_REFLUX = 1 };
 #define MWDG_LMAX 15
 
 typedef struct {
@@ -68,6 +75,7 @@ typedef struct {
   int32_t precision;   /* MWDG_F64 / MWDG_F32                               */
   int32_t limiter;     /* 0 off, 1 minmod slope limiter                     */
   int32_t bc[4];       /* per edge (west, east, south, north): wall / open  */
+  int32_t iface_rule;  /* static grids: MWDG_IFACE_PAPER or MWDG_IFACE_REFLUX */
   double dx;           /* finest resolution R (m)                           */
   double eps;          /* MRA threshold (Sect. 2.2; 1e-3 recommended)      */
   double cfl;          /* Courant number (0.33 for DG2, Sect. 2.1.1)        */
@@ -77,8 +85,9 @@ typedef struct {
   void *cuda_stream;   /* cudaStream_t for all device work                  */
 } mwdg_params;
 
-/* Fills defaults: M=N=1, L=0, uniform, FP64, minmod, walls, dx=1, eps=1e-3,
- * cfl=0.33, g=9.80665, h_dry=1e-3, dt_max=1, default stream. */
+/* Fills defaults: M=N=1, L=0, uniform, FP64, minmod, walls, PAPER interface
+ * rule, dx=1, eps=1e-3, cfl=0.33, g=9.80665, h_dry=1e-3, dt_max=1, default
+ * stream. */
 MWDG_API mwdg_status mwdg_params_default(mwdg_params *p);
 
 /* Creates a context and allocates its device memory (dense per-level
@@ -157,6 +166,15 @@ MWDG_API mwdg_status mwdg_run_to_time(mwdg_ctx *ctx, double t_end, int64_t *step
 MWDG_API mwdg_status mwdg_read_fields(mwdg_ctx *ctx, double *h, double *u, double *v);
 /* Same into device buffers (FP64, ny*nx each, any may be NULL). */
 MWDG_API mwdg_status mwdg_read_fields_dev(mwdg_ctx *ctx, double *h, double *u, double *v);
+
+/* Gauge time series (Sect. 3, depth and velocity at gauge points): h, u, v
+ * (host, n each, any may be NULL) at n finest cells given as (i, j) pairs in
+ * ij (host, 2n int32, i west->east, j south->north), with the same values as
+ * mwdg_read_fields at those cells.  MWDG_ERR_ARG if a cell is outside the
+ * grid.  Device scratch grows to the largest n seen and is kept until
+ * mwdg_destroy. */
+MWDG_API mwdg_status mwdg_read_gauges(mwdg_ctx *ctx, const int32_t *ij, int32_t n, double *h, double *u,
+                                      double *v);
 
 /* Active leaves ordered by level, then row-major: level, i, j (any may be
  * NULL) and their nine coefficients (h0 h1x h1y qx0 qx1x qx1y qy0 qy1x qy1y,

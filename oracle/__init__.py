@@ -71,6 +71,7 @@ class Params(C.Structure):
         ("limiter", C.c_int32), ("bc", C.c_int32 * 4),
         ("inflow_edge", C.c_int32), ("inflow_c0", C.c_int32), ("inflow_c1", C.c_int32),
         ("rain_rate", C.c_double), ("rain_t_end", C.c_double),
+        ("iface_rule", C.c_int32),
     ]
 
 
@@ -176,7 +177,8 @@ class Sim:
 
     def __init__(self, *, M, N, L, R, mode=UNIFORM, eps=1e-3, cfl=0.33, g=9.80665,
                  h_dry=1e-3, dt_max=1.0, limiter=1, bc=(WALL, WALL, WALL, WALL),
-                 inflow_edge=-1, inflow_c0=0, inflow_c1=-1, rain_rate=0.0, rain_t_end=0.0):
+                 inflow_edge=-1, inflow_c0=0, inflow_c1=-1, rain_rate=0.0, rain_t_end=0.0,
+                 iface_rule=0):
         p = Params()
         p.M, p.N, p.L, p.mode = M, N, L, mode
         p.R, p.eps, p.cfl, p.g, p.h_dry, p.dt_max = R, eps, cfl, g, h_dry, dt_max
@@ -185,6 +187,7 @@ class Sim:
             p.bc[k] = bc[k]
         p.inflow_edge, p.inflow_c0, p.inflow_c1 = inflow_edge, inflow_c0, inflow_c1
         p.rain_rate, p.rain_t_end = rain_rate, rain_t_end
+        p.iface_rule = iface_rule
         self.p = p
         self.nx, self.ny = M << L, N << L
         self._h = lib().orc_create(C.byref(p))

@@ -54,6 +54,8 @@ typedef struct {
   int32_t inflow_c0, inflow_c1; /* finest cell range along the edge, incl.   */
   double rain_rate;       /* m/s                                             */
   double rain_t_end;      /* s                                               */
+  int32_t iface_rule;     /* static grids: 0 each side from its own view,    */
+                          /* 1 coarse side takes the mean fine flux (reflux) */
 } orc_params;
 
 typedef struct {
@@ -81,6 +83,26 @@ typedef struct {
   double v_clip, v_in, v_out, v_rain;
   double last_dt;
 } orc_sim;
+
+/* Cube root by Newton's method on y^3 = x, seeded by dividing the exponent
+ * field of x by three (W. Kahan, "Computing a real cube root", 1991): the
+ * seed is within a few per cent, six iterations of
+ * y <- y - (y^3 - x) / (3 y^2) reach the rounding level.  Used for the
+ * friction depth power h^(4/3) and the critical depth; written out with
+ * basic operations only, so the result does not depend on a math library. */
+static double cube_root(double x) {
+  if (x == 0.0 || x != x) return x;
+  double sgn = 1.0, scale = 1.0;
+  if (x < 0.0) { x = -x; sgn = -1.0; }
+  if (x < 1e-290) { x = x * 0x1p300; scale = 0x1p-100; }
+  uint64_t b;
+  memcpy(&b, &x, sizeof b);
+  b = b / 3u + ((uint64_t)682 << 52);
+  double y;
+  memcpy(&y, &b, sizeof y);
+  for (int it = 0; it < 6; it++) y = y - (y * y * y - x) / (3.0 * y * y);
+  return sgn * scale * y;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Basis and filters                                                         */
@@ -740,7 +762,7 @@ static void hll(double hL, double unL, double utL, double hR, double unR, double
 }
 
 /* critical depth of a unit discharge q */
-static double crit_depth(double q, double g) { return cbrt(q * q / g); }
+static double crit_depth(double q, double g) { return cube_root(q * q / g); }
 
 /* inflow unit discharge through the boundary face of a leaf (level l, index
  * k along the edge): the hydrograph Q(t) spread over the inflow cells, times
@@ -825,7 +847,7 @@ static void friction(double *w, double nman, double dt, double g, double hd) {
   if (h0 > hd) {
     double u = w[3] / h0, v = w[6] / h0;
     double sp = sqrt(u * u + v * v);
-    double den = 1.0 + dt * g * nman * nman * sp / (h0 * cbrt(h0));
+    double den = 1.0 + dt * g * nman * nman * sp / (h0 * cube_root(h0));
     double f = 1.0 / den;
     for (int m = 3; m < 9; m++) w[m] = w[m] * f;
   } else {
@@ -1065,6 +1087,72 @@ static void ghost_limit(const orc_sim *s, int l, int i, int j, int f, const doub
   else { out[1] = own[1]; out[2] = -own[2]; }
 }
 
+/* Numerical flux through face f of leaf (l, i, j) with flux-view
+ * coefficients w and beds zc: own interface limit and the neighbour's (same-
+ * level view or boundary ghost), both revised, HLL in (h, qx, qy) order,
+ * oriented along +x (E, W) or +y (N, S).  The own revised limit goes to
+ * hs, us, vs, zr; returns 1 inside the domain, 0 on the boundary. */
+static int face_flux(const orc_sim *s, int l, int i, int j, const double *w, const double *zc, int f,
+                     double t, double F[3], double *hs, double *us, double *vs, double *zr) {
+  double g = s->p.g, hd = s->p.h_dry;
+  double own[4];
+  own[0] = face_lim(w + 0, f);
+  own[1] = face_lim(w + 3, f);
+  own[2] = face_lim(w + 6, f);
+  own[3] = face_lim(zc, f);
+  double nb[4];
+  int inside = nbr_limit(s, l, i, j, f, nb);
+  if (!inside) ghost_limit(s, l, i, j, f, own, t, nb);
+  double zf = fmax(own[3], nb[3]);
+  double hn, un, vn, zn;
+  revise(own[0], own[1], own[2], own[3], zf, hd, hs, us, vs, zr);
+  revise(nb[0], nb[1], nb[2], nb[3], zf, hd, &hn, &un, &vn, &zn);
+  double H[3];
+  if (f == 0) { /* east: own on the left */
+    hll(*hs, *us, *vs, hn, un, vn, g, hd, H);
+    F[0] = H[0]; F[1] = H[1]; F[2] = H[2];
+  } else if (f == 1) {
+    hll(hn, un, vn, *hs, *us, *vs, g, hd, H);
+    F[0] = H[0]; F[1] = H[1]; F[2] = H[2];
+  } else if (f == 2) { /* north: own below */
+    hll(*hs, *vs, *us, hn, vn, un, g, hd, H);
+    F[0] = H[0]; F[1] = H[2]; F[2] = H[1];
+  } else {
+    hll(hn, vn, un, *hs, *vs, *us, g, hd, H);
+    F[0] = H[0]; F[1] = H[2]; F[2] = H[1];
+  }
+  return inside;
+}
+
+/* Reflux rule on static grids (the coarse side of a face whose neighbour
+ * is refined): the flux is the mean of the two fine leaves' own fluxes
+ * through their halves of the face, computed as they compute them, so the
+ * mass leaving one side enters the other. */
+static int reflux_face(const orc_sim *s, int l, int i, int j, int f, double t, double F[3]) {
+  static const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+  if (s->p.mode != ORC_STATIC || s->p.iface_rule != 1) return 0;
+  int a = i + di[f], b = j + dj[f];
+  if (!in_dom(s, l, a, b) || s->kind[l][id(s, l, a, b)] != K_SIG) return 0;
+  int c1, c2;
+  if (f == 0) { c1 = 0; c2 = 2; }
+  else if (f == 1) { c1 = 1; c2 = 3; }
+  else if (f == 2) { c1 = 0; c2 = 1; }
+  else { c1 = 2; c2 = 3; }
+  int cs[2] = {c1, c2};
+  double Fc[2][3];
+  size_t nf = nn(s, l + 1);
+  for (int q = 0; q < 2; q++) {
+    int ic = 2 * a + (cs[q] & 1), jc = 2 * b + (cs[q] >> 1);
+    size_t kc = id(s, l + 1, ic, jc);
+    double wc[9], zcc[3], hs, us, vs, zr;
+    get9(s->F, s, l + 1, kc, wc);
+    for (int m = 0; m < 3; m++) zcc[m] = s->Ze[l + 1][m * nf + kc];
+    face_flux(s, l + 1, ic, jc, wc, zcc, f ^ 1, t, Fc[q], &hs, &us, &vs, &zr);
+  }
+  for (int v = 0; v < 3; v++) F[v] = 0.5 * (Fc[0][v] + Fc[1][v]);
+  return 1;
+}
+
 /* DG2 spatial operator L = [L0, L1x, L1y] of one leaf (Eq. 4, Sect. 2.1.1),
  * evaluated on limited coefficients w and the same-level neighbour view.
  * Average: flux difference over the four faces plus the bed source with the
@@ -1075,38 +1163,16 @@ static void ghost_limit(const orc_sim *s, int l, int i, int j, int f, const doub
  * flux (m^3/s) in *bnd_out. */
 static void leaf_operator(const orc_sim *s, int l, int i, int j, const double *w, const double *zc,
                           double t, double *Lo, double *bnd_out) {
-  double g = s->p.g, hd = s->p.h_dry, s3 = S3();
+  double g = s->p.g, s3 = S3();
   double dxl = s->dx[l];
   double Fh[4][3];                 /* numerical flux per face in (h,qx,qy) */
   double hs[4], us[4], vs[4], zr[4]; /* own revised limits */
   double bout = 0.0;
   for (int f = 0; f < 4; f++) {
-    double own[4];
-    own[0] = face_lim(w + 0, f);
-    own[1] = face_lim(w + 3, f);
-    own[2] = face_lim(w + 6, f);
-    own[3] = face_lim(zc, f);
-    double nb[4];
-    int inside = nbr_limit(s, l, i, j, f, nb);
-    if (!inside) ghost_limit(s, l, i, j, f, own, t, nb);
-    double zf = fmax(own[3], nb[3]);
-    double hn, un, vn, zn;
-    revise(own[0], own[1], own[2], own[3], zf, hd, &hs[f], &us[f], &vs[f], &zr[f]);
-    revise(nb[0], nb[1], nb[2], nb[3], zf, hd, &hn, &un, &vn, &zn);
-    double F[3];
-    if (f == 0) { /* east: own on the left */
-      hll(hs[f], us[f], vs[f], hn, un, vn, g, hd, F);
-      Fh[f][0] = F[0]; Fh[f][1] = F[1]; Fh[f][2] = F[2];
-    } else if (f == 1) {
-      hll(hn, un, vn, hs[f], us[f], vs[f], g, hd, F);
-      Fh[f][0] = F[0]; Fh[f][1] = F[1]; Fh[f][2] = F[2];
-    } else if (f == 2) { /* north: own below */
-      hll(hs[f], vs[f], us[f], hn, vn, un, g, hd, F);
-      Fh[f][0] = F[0]; Fh[f][1] = F[2]; Fh[f][2] = F[1];
-    } else {
-      hll(hn, vn, un, hs[f], vs[f], us[f], g, hd, F);
-      Fh[f][0] = F[0]; Fh[f][1] = F[2]; Fh[f][2] = F[1];
-    }
+    int inside = face_flux(s, l, i, j, w, zc, f, t, Fh[f], &hs[f], &us[f], &vs[f], &zr[f]);
+    double Fr[3];
+    if (inside && reflux_face(s, l, i, j, f, t, Fr))
+      for (int v = 0; v < 3; v++) Fh[f][v] = Fr[v];
     if (!inside) {
       double outward = (f == 0 || f == 2) ? Fh[f][0] : -Fh[f][0];
       bout += outward * dxl;

@@ -21,7 +21,7 @@ EXPORTS = (
     "mwdg_read_fields", "mwdg_read_fields_dev", "mwdg_read_active", "mwdg_get_time",
     "mwdg_get_volume", "mwdg_profile", "mwdg_kernel_times", "mwdg_launch_count",
     "mwdg_last_error", "mwdg_status_string", "mwdg_state_bytes", "mwdg_save_state",
-    "mwdg_load_state", "mwdg_volume_noalloc", "mwdg_get_counters",
+    "mwdg_load_state", "mwdg_volume_noalloc", "mwdg_get_counters", "mwdg_read_gauges",
 )
 
 
@@ -29,7 +29,7 @@ class Params(C.Structure):
     _fields_ = [
         ("M", C.c_int32), ("N", C.c_int32), ("L", C.c_int32), ("mode", C.c_int32),
         ("precision", C.c_int32), ("limiter", C.c_int32), ("bc", C.c_int32 * 4),
-        ("dx", C.c_double), ("eps", C.c_double), ("cfl", C.c_double), ("g", C.c_double),
+        ("iface_rule", C.c_int32), ("dx", C.c_double), ("eps", C.c_double), ("cfl", C.c_double), ("g", C.c_double),
         ("h_dry", C.c_double), ("dt_max", C.c_double), ("cuda_stream", C.c_void_p),
     ]
 
@@ -72,6 +72,7 @@ def lib(build: bool = True):
         "mwdg_run_to_time": [vp, C.c_double, lp],
         "mwdg_read_fields": [vp, dp, dp, dp],
         "mwdg_read_fields_dev": [vp, vp, vp, vp],
+        "mwdg_read_gauges": [vp, ip, C.c_int32, dp, dp, dp],
         "mwdg_read_active": [vp, ip, ip, ip, dp, C.c_int64, lp],
         "mwdg_get_time": [vp, dp, lp],
         "mwdg_get_counters": [vp, lp, lp],
@@ -114,11 +115,12 @@ class Solver:
     """One simulation context (mwdg_ctx) on the current CUDA device."""
 
     def __init__(self, *, M, N, L, dx, mode=UNIFORM, precision=F64, eps=1e-3, cfl=0.33,
-                 g=9.80665, h_dry=1e-3, dt_max=1.0, limiter=1, bc=(WALL,) * 4, stream=None):
+                 g=9.80665, h_dry=1e-3, dt_max=1.0, limiter=1, bc=(WALL,) * 4, iface_rule=0, stream=None):
         self._lib = lib()
         p = Params()
         self._lib.mwdg_params_default(C.byref(p))
         p.M, p.N, p.L, p.mode, p.precision, p.limiter = M, N, L, mode, precision, limiter
+        p.iface_rule = iface_rule
         for k in range(4):
             p.bc[k] = bc[k]
         p.dx, p.eps, p.cfl, p.g, p.h_dry, p.dt_max = dx, eps, cfl, g, h_dry, dt_max
@@ -128,6 +130,8 @@ class Solver:
         p.cuda_stream = stream
         self.p = p
         self.nx, self.ny = M << L, N << L
+        # finest level of the reported active leaves (a uniform grid is one level)
+        self.levels = 0 if mode == UNIFORM else L
         h = C.c_void_p()
         st = self._lib.mwdg_create(C.byref(p), C.byref(h))
         if st != 0:
@@ -211,6 +215,14 @@ class Solver:
         ptr = lambda x: None if x is None else C.c_void_p(x.data_ptr())
         self._ck(self._lib.mwdg_read_fields_dev(self._h, ptr(h), ptr(u), ptr(v)), "mwdg_read_fields_dev")
 
+    def read_gauges(self, cells):
+        """h, u, v at finest cells given as an (n, 2) array of (i, j)"""
+        ij = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 2))
+        n = ij.shape[0]
+        h, u, v = (np.empty(n) for _ in range(3))
+        self._ck(self._lib.mwdg_read_gauges(self._h, _ip(ij), n, _dp(h), _dp(u), _dp(v)), "mwdg_read_gauges")
+        return h, u, v
+
     def read_active(self):
         n = C.c_int64()
         self._ck(self._lib.mwdg_read_active(self._h, None, None, None, None, 0, C.byref(n)),
@@ -292,7 +304,7 @@ class Solver:
 def solver_from_problem(p, precision=F64, stream=None, **over) -> Solver:
     """A Solver loaded with a synthetic problem (paper_2107_02750_gb300.synth)."""
     kw = dict(M=p.M, N=p.N, L=p.L, dx=p.dx, mode=p.mode, precision=precision, eps=p.eps,
-              limiter=p.limiter, bc=p.bc, dt_max=p.dt_max, stream=stream)
+              limiter=p.limiter, bc=p.bc, dt_max=p.dt_max, iface_rule=p.iface_rule, stream=stream)
     kw.update(over)
     s = Solver(**kw)
     s.load_dem(p.z_vert)

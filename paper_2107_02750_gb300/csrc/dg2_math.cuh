@@ -24,7 +24,25 @@ template <typename T> __device__ __forceinline__ T tinf();
 template <> __device__ __forceinline__ float tinf<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double tinf<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
 template <typename T> __device__ __forceinline__ T tsqrt(T a) { return sqrt(a); }
-template <typename T> __device__ __forceinline__ T tcbrt(T a) { return cbrt(a); }
+// Cube root.  FP32: the library's.  FP64: Newton's method on y^3 = x seeded
+// by dividing the exponent field by three (W. Kahan, "Computing a real cube
+// root", 1991), six iterations of y <- y - (y^3 - x) / (3 y^2) with basic
+// IEEE operations only, so the result is the same on any IEEE machine.
+__device__ __forceinline__ double newton_cbrt(double x) {
+  if (x == 0.0 || x != x) return x;
+  double sgn = 1.0, scale = 1.0;
+  if (x < 0.0) { x = -x; sgn = -1.0; }
+  if (x < 1e-290) { x = x * 0x1p300; scale = 0x1p-100; }
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  b = b / 3ull + (682ull << 52);
+  double y = __longlong_as_double((long long)b);
+#pragma unroll
+  for (int it = 0; it < 6; it++) y = y - (y * y * y - x) / (3.0 * y * y);
+  return sgn * scale * y;
+}
+template <typename T> __device__ __forceinline__ T tcbrt(T a);
+template <> __device__ __forceinline__ float tcbrt<float>(float a) { return cbrtf(a); }
+template <> __device__ __forceinline__ double tcbrt<double>(double a) { return newton_cbrt(a); }
 template <typename T> __device__ __forceinline__ T tabs(T a) { return fabs(a); }
 
 // Limit of a plane (Eq. 2-3) at the interface centre of face f:

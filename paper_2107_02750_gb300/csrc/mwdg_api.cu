@@ -41,6 +41,9 @@ struct mwdg_ctx {
   double *d_fields = nullptr;    // 3 finest rasters for read-back
   int32_t *d_active = nullptr;   // level, i, j for read-back
   double *d_coef = nullptr;      // coefficients for read-back
+  int32_t *d_gauge_ij = nullptr; // gauge cells and their values for read-back
+  double *d_gauge_out = nullptr;
+  int gauge_cap = 0;
   int grid_leaves = 0;
   bool dem = false, initial = false, stepped = false, failed = false, encoded = false;
   bool vmax_fresh = false;   // max |v0| on the device is that of the current leaves
@@ -169,7 +172,7 @@ mwdg_status allocate_state(mwdg_ctx *c) {
   CK(cudaMemsetAsync(p.FZ, 0, 12 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.Z, 0, 3 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.NM, 0, P * sizeof(T), c->st));
-  CK(cudaMemsetAsync(p.DZ, 0, P * sizeof(T), c->st));
+  CK(cudaMemsetAsync(p.DZ, 0, P * sizeof(double), c->st));
   CK(cudaMemsetAsync(p.flag, 0, P, c->st));
   CK(cudaMemsetAsync(p.flag2, 0, P, c->st));
   p.ctl = c->ctl;
@@ -346,7 +349,9 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
   if ((int64_t)p->M << p->L > (1 << 20) || (int64_t)p->N << p->L > (1 << 20)) return MWDG_ERR_DIMS;
   if (p->mode < MWDG_UNIFORM || p->mode > MWDG_ADAPTIVE || p->precision < MWDG_F64 ||
       p->precision > MWDG_F32 || !(p->cfl > 0.0) || !(p->g > 0.0) || !(p->h_dry >= 0.0) ||
-      !(p->dt_max > 0.0) || !std::isfinite(p->eps) || p->eps < 0.0)
+      !(p->dt_max > 0.0) || !std::isfinite(p->eps) || p->eps < 0.0 ||
+      (p->iface_rule != MWDG_IFACE_PAPER && p->iface_rule != MWDG_IFACE_REFLUX) ||
+      (p->iface_rule == MWDG_IFACE_REFLUX && p->mode == MWDG_ADAPTIVE))
     return MWDG_ERR_ARG;
   mwdg_ctx *c = new mwdg_ctx();
   c->p = *p;
@@ -356,6 +361,7 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
   g.mode = p->mode;
   g.prec = p->precision;
   g.limiter = p->limiter;
+  g.iface = p->iface_rule;
   if (p->mode == MWDG_UNIFORM) {  // a uniform grid is the single level of an L = 0 hierarchy
     g.L = 0;
     g.M = p->M << p->L;
@@ -706,6 +712,36 @@ mwdg_status mwdg_read_fields(mwdg_ctx *c, double *h, double *u, double *v) {
   return MWDG_OK;
 }
 
+mwdg_status mwdg_read_gauges(mwdg_ctx *c, const int32_t *ij, int32_t n, double *h, double *u, double *v) {
+  LIVE(c);
+  if (n < 0 || (n > 0 && !ij)) return fail(c, MWDG_ERR_ARG, "invalid gauge list");
+  const Geo &g = c->g;
+  for (int32_t q = 0; q < n; q++)
+    if (ij[2 * q] < 0 || ij[2 * q] >= g.nxl[g.L] || ij[2 * q + 1] < 0 || ij[2 * q + 1] >= g.nyl[g.L])
+      return fail(c, MWDG_ERR_ARG, "gauge %d (%d, %d) outside the grid", q, ij[2 * q], ij[2 * q + 1]);
+  if (n == 0) return MWDG_OK;
+  if (n > c->gauge_cap) {
+    int cap = 256;
+    while (cap < n) cap *= 2;
+    mwdg_status s;
+    if ((s = alloc(c, &c->d_gauge_ij, 2 * (size_t)cap)) || (s = alloc(c, &c->d_gauge_out, 3 * (size_t)cap))) return s;
+    c->gauge_cap = cap;
+  }
+  CK(cudaMemcpyAsync(c->d_gauge_ij, ij, 2 * (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, c->st));
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::gauges(g, p, c->d_gauge_ij, n, c->d_gauge_out, c->st);
+  });
+  CHECK_LAUNCH();
+  double *dst[3] = {h, u, v};
+  for (int q = 0; q < 3; q++)
+    if (dst[q])
+      CK(cudaMemcpyAsync(dst[q], c->d_gauge_out + (size_t)q * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
+                         c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return MWDG_OK;
+}
+
 mwdg_status mwdg_read_active(mwdg_ctx *c, int32_t *level, int32_t *i, int32_t *j, double *coeffs,
                              int64_t cap, int64_t *n) {
   LIVE(c);
@@ -788,11 +824,11 @@ struct StateHeader {
   int64_t P;
   Ctl ctl;
 };
-constexpr char kMagic[8] = {'M', 'W', 'D', 'G', 'S', 'T', '0', '2'};
+constexpr char kMagic[8] = {'M', 'W', 'D', 'G', 'S', 'T', '0', '1'};
 
 size_t state_bytes(const mwdg_ctx *c) {
   const size_t P = (size_t)c->g.P, ts = (c->g.prec == MWDG_F64) ? 8 : 4;
-  return sizeof(StateHeader) + P + 9 * P * ts + 3 * P * ts + P * ts + P * ts;
+  return sizeof(StateHeader) + P + 9 * P * ts + 3 * P * ts + P * ts + P * 8;
 }
 }  // namespace
 
@@ -810,7 +846,7 @@ mwdg_status mwdg_save_state(mwdg_ctx *c, void *buf, int64_t cap) {
   const Geo &g = c->g;
   StateHeader h{};
   memcpy(h.magic, kMagic, 8);
-  h.version = 2;
+  h.version = 1;
   h.prec = g.prec;
   h.L = g.L;
   h.M = g.M;
@@ -836,7 +872,7 @@ mwdg_status mwdg_save_state(mwdg_ctx *c, void *buf, int64_t cap) {
   b += 3 * P * ts;
   CK(cudaMemcpyAsync(b, NM, P * ts, cudaMemcpyDeviceToHost, c->st));
   b += P * ts;
-  CK(cudaMemcpyAsync(b, DZ, P * ts, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(b, DZ, P * 8, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   return MWDG_OK;
 }
@@ -847,7 +883,7 @@ mwdg_status mwdg_load_state(mwdg_ctx *c, const void *buf, int64_t size) {
   const Geo &g = c->g;
   StateHeader h;
   memcpy(&h, buf, sizeof h);
-  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 2) return fail(c, MWDG_ERR_ARG, "not a state buffer");
+  if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return fail(c, MWDG_ERR_ARG, "not a state buffer");
   if (h.prec != g.prec || h.L != g.L || h.M != g.M || h.N != g.N || h.P != g.P || h.mode != g.mode)
     return fail(c, MWDG_ERR_DIMS, "state belongs to another grid or precision");
   if (size < (int64_t)state_bytes(c)) return fail(c, MWDG_ERR_ARG, "state buffer truncated");
@@ -866,7 +902,7 @@ mwdg_status mwdg_load_state(mwdg_ctx *c, const void *buf, int64_t size) {
   b += 3 * P * ts;
   CK(cudaMemcpyAsync(NM, b, P * ts, cudaMemcpyHostToDevice, c->st));
   b += P * ts;
-  CK(cudaMemcpyAsync(DZ, b, P * ts, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(DZ, b, P * 8, cudaMemcpyHostToDevice, c->st));
   Ctl ctl = h.ctl;
   ctl.t_end = 1e300;
   ctl.blocks_done = 0u;

@@ -28,7 +28,7 @@ struct Ctl {
 
 // Geometry and parameters of the level hierarchy (passed by value).
 struct Geo {
-  int L, M, N, mode, limiter, prec;
+  int L, M, N, mode, limiter, prec, iface;
   int nxl[MWDG_LMAX + 1], nyl[MWDG_LMAX + 1];
   long long off[MWDG_LMAX + 2];
   long long P;                 // nodes over all levels
@@ -38,17 +38,16 @@ struct Geo {
   int inflow_edge, inflow_c0, inflow_c1, nknots;
   double rain_rate, rain_t_end;
   long long coarse_nodes;      // MRA levels up to this size run in one block
-  // single-precision copies of g, h_dry, eps and the element sizes, so that
+  // single-precision copies of g, h_dry and the element sizes, so that
   // FP32 kernels convert nothing from FP64 on the device
-  float gf, hdf, epsf;
+  float gf, hdf;
   float dxlf[MWDG_LMAX + 1];
 };
 
-// refresh the single-precision copies after any change of g, hd, eps or dxl
+// refresh the single-precision copies after any change of g, hd or dxl
 inline void sync_single(Geo &g) {
   g.gf = (float)g.g;
   g.hdf = (float)g.hd;
-  g.epsf = (float)g.eps;
   for (int l = 0; l <= MWDG_LMAX; l++) g.dxlf[l] = (float)g.dxl[l];
 }
 
@@ -65,7 +64,7 @@ struct Ptrs {
             // (9) and its bed planes (3); refined nodes hold their encoding
   T *Z;     // static topography pyramid (3)
   T *NM;    // Manning n per node (1)
-  T *DZ;        // normalised topography detail per node
+  double *DZ;   // normalised topography detail per node (compared with eps in FP64)
   uint8_t *kind, *flag, *flag2;
   uint8_t *kind_new;  // kinds of the next active set while the old ones are still read
   long long *leaves;  // active leaves, packed (level << 56 | j << 28 | i)
@@ -104,6 +103,7 @@ template <typename T> struct Launch {
   static int prime(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st);
   static int fields(const Geo &g, const Ptrs<T> &p, double *h, double *u, double *v,
                     cudaStream_t st);
+  static int gauges(const Geo &g, const Ptrs<T> &p, const int32_t *ij, int n, double *out, cudaStream_t st);
   static int read_active(const Geo &g, const Ptrs<T> &p, int32_t *lev, int32_t *i, int32_t *j,
                          double *coef, cudaStream_t st);
   static int volume(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st);

@@ -48,9 +48,6 @@ template <> __device__ __forceinline__ double geo_g<double>(const Geo &g) { retu
 template <typename T> __device__ __forceinline__ T geo_hd(const Geo &g);
 template <> __device__ __forceinline__ float geo_hd<float>(const Geo &g) { return g.hdf; }
 template <> __device__ __forceinline__ double geo_hd<double>(const Geo &g) { return g.hd; }
-template <typename T> __device__ __forceinline__ T geo_eps(const Geo &g);
-template <> __device__ __forceinline__ float geo_eps<float>(const Geo &g) { return g.epsf; }
-template <> __device__ __forceinline__ double geo_eps<double>(const Geo &g) { return g.eps; }
 template <typename T> __device__ __forceinline__ T geo_dx(const Geo &g, int l);
 template <> __device__ __forceinline__ float geo_dx<float>(const Geo &g, int l) { return g.dxlf[l]; }
 template <> __device__ __forceinline__ double geo_dx<double>(const Geo &g, int l) { return g.dxl[l]; }
@@ -183,7 +180,7 @@ __global__ void k_encode_z(Geo g, Ptrs<T> p, int l) {
 #pragma unroll
   for (int m = 0; m < 3; m++) p.Z[m * P + k] = sp[m];
   double norm = fmax(1.0, __longlong_as_double((long long)p.ctl->vmax[0]));
-  p.DZ[k] = (T)((double)detail_max3(ch) / norm);
+  p.DZ[k] = (double)detail_max3(ch) / norm;
 }
 
 // Manning n: coarser nodes hold the mean of their children
@@ -279,7 +276,7 @@ template <typename T>
 __global__ void k_static_flags(Geo g, Ptrs<T> p) {
   long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k >= g.P) return;
-  p.flag[k] = (k < g.off[g.L]) ? (uint8_t)((double)p.DZ[k] >= g.eps) : (uint8_t)0;
+  p.flag[k] = (k < g.off[g.L]) ? (uint8_t)(p.DZ[k] >= g.eps) : (uint8_t)0;
 }
 
 // parent closure from level l to l-1: a flagged child flags its parent
@@ -687,6 +684,21 @@ __device__ __forceinline__ X ldx(const X *a) {
   return *a;
 }
 
+// Significance of a flow detail: max |d| / max(1, max |v0|) >= eps, compared
+// in FP64 in both precisions.  FP64: in that form (the oracle's order);
+// FP32: as max |d| >= thr with thr = eps * max(1, max |v0|) formed in FP64
+// once per block (a float detail converts exactly).
+template <typename T>
+__device__ __forceinline__ bool detail_significant(T dm, double mx, double thr, double eps);
+template <>
+__device__ __forceinline__ bool detail_significant<double>(double dm, double mx, double thr, double eps) {
+  return dm / fmax(1.0, mx) >= eps;
+}
+template <>
+__device__ __forceinline__ bool detail_significant<float>(float dm, double, double thr, double) {
+  return (double)dm >= thr;
+}
+
 // MWDG2 encode of one node of level l (Sect. 2.3): a refined node gets the
 // scale coefficients of its children (Eq. 9) and is flagged when its largest
 // normalised flow or topography detail reaches epsilon; other nodes carry no
@@ -697,7 +709,7 @@ template <bool SPEC, typename T>
 __device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
   const long long P = g.P, k = nid(g, l, i, j);
   const uint8_t kd = p.kind[k];
-  T dmax = p.DZ[k];
+  bool sig = p.DZ[k] >= g.eps;
   T ch[3][4][3], zc[4][2];
   if (SPEC || kd == K_SIG) {
 #pragma unroll
@@ -722,11 +734,11 @@ __device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p,
       if (v == 0) slopes_from_h(sp[1], sp[2], zp1, zp2);
 #pragma unroll
       for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sp[m];
-      const T mx = (T)__longlong_as_double((long long)p.ctl->vmax[v]);
-      dmax = tmax(dmax, detail_max3(ch[v]) / tmax(T(1), mx));
+      const double mx = __longlong_as_double((long long)p.ctl->vmax[v]);
+      sig = detail_significant<T>(detail_max3(ch[v]), mx, g.eps * fmax(1.0, mx), g.eps) || sig;
     }
   }
-  p.flag[k] = (uint8_t)(dmax >= geo_eps<T>(g));
+  p.flag[k] = (uint8_t)sig;
 }
 
 // regularised flag of node (m, a, b): prediction (the node or one of its
@@ -755,13 +767,14 @@ __device__ __forceinline__ uint8_t regular_flag(const Geo &g, const Ptrs<T> &p, 
 
 // Eq. 9 encode of a refined node from its children's stored coefficients
 // ch[v][c][m] and bed slopes zc[c]; the node's stored coefficients go to
-// out, the largest normalised flow detail is returned
+// out; true when a normalised flow detail is significant
 template <typename T>
-__device__ __forceinline__ T encode_sig(T (&ch)[3][4][3], const T (&zc)[4][2], T zp1, T zp2,
-                                        const T (&mx)[3], T (&out)[9]) {
+__device__ __forceinline__ bool encode_sig(T (&ch)[3][4][3], const T (&zc)[4][2], T zp1, T zp2,
+                                           const double (&mx)[3], const double (&thr)[3], double eps,
+                                           T (&out)[9]) {
 #pragma unroll
   for (int c = 0; c < 4; c++) slopes_to_h(ch[0][c][1], ch[0][c][2], zc[c][0], zc[c][1]);
-  T dmax = T(0);
+  bool sig = false;
 #pragma unroll
   for (int v = 0; v < 3; v++) {
     T sp[3];
@@ -769,18 +782,19 @@ __device__ __forceinline__ T encode_sig(T (&ch)[3][4][3], const T (&zc)[4][2], T
     if (v == 0) slopes_from_h(sp[1], sp[2], zp1, zp2);
 #pragma unroll
     for (int m = 0; m < 3; m++) out[3 * v + m] = sp[m];
-    dmax = tmax(dmax, detail_max3(ch[v]) / tmax(T(1), mx[v]));
+    sig = sig | detail_significant<T>(detail_max3(ch[v]), mx[v], thr[v], eps);
   }
-  return dmax;
+  return sig;
 }
 
 template <typename T>
 struct SigStage {
   T u[MT_NODES][9];     // stored coefficients (leaves: own; refined: encoded)
   T z[MT_NODES][2];     // bed slopes (free-surface form)
-  T dz[MT_NODES];       // normalised topography detail
   uint8_t kind[MT_NODES];
-  T mx[3];              // max |v0| of h, qx, qy (normalisation of the flow details)
+  uint8_t topo[MT_NODES];  // topography detail significant
+  double mx[3];            // max |v0| of h, qx, qy (normalisation of the flow details)
+  double thr[3];           // eps * max(1, mx)
 };
 
 // encode + significance of one tile (CG: the children of its finest level
@@ -788,22 +802,25 @@ struct SigStage {
 template <bool CG, typename T>
 __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const Tile &tl, SigStage<T> &sh) {
   const long long P = g.P;
-  if (threadIdx.x < 3) sh.mx[threadIdx.x] = (T)__longlong_as_double((long long)p.ctl->vmax[threadIdx.x]);
-  const T eps = geo_eps<T>(g);
+  if (threadIdx.x < 3) {
+    const double m = __longlong_as_double((long long)p.ctl->vmax[threadIdx.x]);
+    sh.mx[threadIdx.x] = m;
+    sh.thr[threadIdx.x] = g.eps * fmax(1.0, m);
+  }
   int sl[2];
   long long kk[2];
   staged_slots(g, tl, sl, kk);
   uint8_t kd[2];
-  T dz[2];
+  bool tp[2];
   T zs[2][2];
 #pragma unroll
   for (int q = 0; q < 2; q++) {
     kd[q] = K_OUT;
-    dz[q] = T(0);
+    tp[q] = false;
     zs[q][0] = zs[q][1] = T(0);
     if (kk[q] >= 0) {
       kd[q] = p.kind[kk[q]];
-      dz[q] = p.DZ[kk[q]];
+      tp[q] = p.DZ[kk[q]] >= g.eps;
       if (Form<T>::eta) {
         zs[q][0] = p.Z[P + kk[q]];
         zs[q][1] = p.Z[2 * P + kk[q]];
@@ -814,7 +831,7 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
   for (int q = 0; q < 2; q++)
     if (sl[q] < MT_NODES) {
       sh.kind[sl[q]] = kd[q];
-      sh.dz[sl[q]] = dz[q];
+      sh.topo[sl[q]] = tp[q];
       sh.z[sl[q]][0] = zs[q][0];
       sh.z[sl[q]][1] = zs[q][1];
       if (kd[q] == K_LEAF)
@@ -822,12 +839,15 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
         for (int m = 0; m < 9; m++) sh.u[sl[q]][m] = p.U[m * P + kk[q]];
     }
   __syncthreads();
-  T mx[3];
+  double mx[3], thr[3];
 #pragma unroll
-  for (int v = 0; v < 3; v++) mx[v] = sh.mx[v];
+  for (int v = 0; v < 3; v++) {
+    mx[v] = sh.mx[v];
+    thr[v] = sh.thr[v];
+  }
   // finest tile level: refined nodes read their children from global memory
   if (kk[0] >= 0) {
-    T dmax = dz[0];
+    bool sig = tp[0];
     if (kd[0] == K_SIG) {
       int s0, t0, i, j;
       slot_st(sl[0], s0, t0);
@@ -843,14 +863,14 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
         zc[c][0] = p.Z[P + kc];
         zc[c][1] = p.Z[2 * P + kc];
       }
-      dmax = tmax(dmax, encode_sig(ch, zc, zs[0][0], zs[0][1], mx, out));
+      sig = encode_sig(ch, zc, zs[0][0], zs[0][1], mx, thr, g.eps, out) || sig;
 #pragma unroll
       for (int m = 0; m < 9; m++) {
         p.U[m * P + kk[0]] = out[m];
         sh.u[sl[0]][m] = out[m];
       }
     }
-    p.flag[kk[0]] = (uint8_t)(dmax >= eps);
+    p.flag[kk[0]] = (uint8_t)sig;
   }
   // coarser tile levels from shared memory
   for (int s = 1; s < tl.nlev; s++) {
@@ -863,7 +883,7 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
     int i, j;
     tile_coord(g, tl, s, t, i, j);
     const long long k = nid(g, tl.ltop - s, i, j);
-    T dmax = sh.dz[slot];
+    bool sig = sh.topo[slot] != 0;
     if (k2 == K_SIG) {
       T ch[3][4][3], zc[4][2], out[9];
 #pragma unroll
@@ -876,14 +896,14 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
         zc[c][0] = sh.z[cs][0];
         zc[c][1] = sh.z[cs][1];
       }
-      dmax = tmax(dmax, encode_sig(ch, zc, sh.z[slot][0], sh.z[slot][1], mx, out));
+      sig = encode_sig(ch, zc, sh.z[slot][0], sh.z[slot][1], mx, thr, g.eps, out) || sig;
 #pragma unroll
       for (int m = 0; m < 9; m++) {
         p.U[m * P + k] = out[m];
         sh.u[slot][m] = out[m];
       }
     }
-    p.flag[k] = (uint8_t)(dmax >= eps);
+    p.flag[k] = (uint8_t)sig;
   }
 }
 
@@ -1565,6 +1585,37 @@ __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, 
   return o;
 }
 
+// Reflux rule on static grids (MWDG_IFACE_REFLUX): on the coarse side of a
+// face whose neighbour is refined, the flux is the mean of the two fine
+// leaves' own fluxes through their halves of the face, computed by the same
+// code as theirs, so the mass leaving one side enters the other.
+template <typename T>
+__device__ __noinline__ bool reflux_face(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, double tf,
+                                         T &F0, T &F1, T &F2) {
+  const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
+  if (a < 0 || b < 0 || a >= g.nxl[l] || b >= g.nyl[l] || p.kind[nid(g, l, a, b)] != K_SIG) return false;
+  int c1, c2;
+  if (f == 0) { c1 = 0; c2 = 2; }
+  else if (f == 1) { c1 = 1; c2 = 3; }
+  else if (f == 2) { c1 = 0; c2 = 1; }
+  else { c1 = 2; c2 = 3; }
+  T G[2][3];
+  for (int q = 0; q < 2; q++) {
+    const int cq = q ? c2 : c1;
+    const int ic = 2 * a + (cq & 1), jc = 2 * b + (cq >> 1);
+    T r[12], w[9], zc[3];
+    load_rec(p.FZ, nid(g, l + 1, ic, jc), r);
+    for (int m = 0; m < 9; m++) w[m] = r[m];
+    for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
+    const FaceOut<T> o = face_flux(g, p, l + 1, ic, jc, w, zc, f ^ 1, tf);
+    G[q][0] = o.F0; G[q][1] = o.F1; G[q][2] = o.F2;
+  }
+  F0 = T(0.5) * (G[0][0] + G[1][0]);
+  F1 = T(0.5) * (G[0][1] + G[1][1]);
+  F2 = T(0.5) * (G[0][2] + G[1][2]);
+  return true;
+}
+
 // The operator and update of variable v (0 h, 1 qx, 2 qy) of one leaf from
 // its four interfaces (flux component v, own revised limits): L0 from the
 // flux difference and the bed source with the revised interface beds, the
@@ -1684,7 +1735,8 @@ __device__ __forceinline__ void next_step_reduce(const Geo &g, const Ptrs<T> &p,
 // arithmetic units are few on this GPU): one thread per leaf.
 template <typename T> struct Lanes { static constexpr int per_leaf = std::is_same<T, float>::value ? 4 : 1; };
 
-template <typename T, int STAGE>
+// REFLUX: compiled with the reflux interface rule (static grids only)
+template <typename T, int STAGE, bool REFLUX>
 __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out) {
   const long long P = g.P;
   const double dtd = p.ctl->dt;
@@ -1723,6 +1775,7 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
           for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
         }
         fo = face_flux(g, p, l, i, j, w, zc, f, tf);
+        if (REFLUX) reflux_face(g, p, l, i, j, f, tf, fo.F0, fo.F1, fo.F2);
         bsum += fo.bout;
       }
       // every lane of the group gets the four interfaces; lanes 0, 1, 2
@@ -1773,6 +1826,7 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
 #pragma unroll
       for (int d = 0; d < 4; d++) {
         FaceOut<T> fo = face_flux(g, p, l, i, j, w, zc, d, tf);
+        if (REFLUX) reflux_face(g, p, l, i, j, d, tf, fo.F0, fo.F1, fo.F2);
         bsum += fo.bout;
         F[d][0] = fo.F0; F[d][1] = fo.F1; F[d][2] = fo.F2;
         hs[d] = fo.hs; us[d] = fo.us; vs[d] = fo.vs; zr[d] = fo.zr;
@@ -1838,13 +1892,11 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
 // ---------------------------------------------------------------------------
 // Read-back
 // ---------------------------------------------------------------------------
+// h, u, v of finest cell (I, J): the plane of the active leaf covering it
+// evaluated at the cell centre (FP64); velocities q/h where h > h_dry, else 0
 template <typename T>
-__global__ void k_fields(Geo g, Ptrs<T> p, double *h, double *u, double *v) {
+__device__ __forceinline__ void finest_values(const Geo &g, const Ptrs<T> &p, int I, int J, double (&out)[3]) {
   const int L = g.L;
-  long long n = (long long)g.nxl[L] * g.nyl[L];
-  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  int J = (int)(r / g.nxl[L]), I = (int)(r - (long long)J * g.nxl[L]);
   int l = L, a = I, b = J;
   long long k = nid(g, l, a, b);
   while (l > 0 && p.kind[k] != K_LEAF) {
@@ -1865,14 +1917,38 @@ __global__ void k_fields(Geo g, Ptrs<T> p, double *h, double *u, double *v) {
     }
     val[q] = c0 + 2.0 * s3 * xi * c1 + 2.0 * s3 * et * c2;
   }
-  if (h) h[r] = val[0];
-  double uu = 0.0, vv = 0.0;
+  out[0] = val[0];
+  out[1] = out[2] = 0.0;
   if (val[0] > g.hd) {
-    uu = val[1] / val[0];
-    vv = val[2] / val[0];
+    out[1] = val[1] / val[0];
+    out[2] = val[2] / val[0];
   }
-  if (u) u[r] = uu;
-  if (v) v[r] = vv;
+}
+
+template <typename T>
+__global__ void k_fields(Geo g, Ptrs<T> p, double *h, double *u, double *v) {
+  const int L = g.L;
+  long long n = (long long)g.nxl[L] * g.nyl[L];
+  long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int J = (int)(r / g.nxl[L]), I = (int)(r - (long long)J * g.nxl[L]);
+  double o[3];
+  finest_values(g, p, I, J, o);
+  if (h) h[r] = o[0];
+  if (u) u[r] = o[1];
+  if (v) v[r] = o[2];
+}
+
+// the same at n gauge cells (ij: i, j pairs) into out (h, u, v blocks of n)
+template <typename T>
+__global__ void k_gauges(Geo g, Ptrs<T> p, const int32_t *ij, int n, double *out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  double o[3];
+  finest_values(g, p, ij[2 * q], ij[2 * q + 1], o);
+  out[q] = o[0];
+  out[n + q] = o[1];
+  out[2 * n + q] = o[2];
 }
 
 template <typename T>
@@ -2121,12 +2197,15 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
         MARK(KC_VIEW);
         k_view_tiles<T><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
       });
+    const bool reflux = (g.mode == MWDG_STATIC && g.iface == MWDG_IFACE_REFLUX);
     if (stage == 1) {
       MARK(KC_UPDATE1);
-      k_leaf_update<T, 1><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui);
+      if (reflux) k_leaf_update<T, 1, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui);
+      else k_leaf_update<T, 1, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui);
     } else {
       MARK(KC_UPDATE2);
-      k_leaf_update<T, 2><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U);
+      if (reflux) k_leaf_update<T, 2, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U);
+      else k_leaf_update<T, 2, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U);
     }
     n++;
   }
@@ -2137,6 +2216,13 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
 template <typename T>
 int Launch<T>::fields(const Geo &g, const Ptrs<T> &p, double *h, double *u, double *v, cudaStream_t st) {
   k_fields<T><<<nblk(lvl(g, g.L)), TPB, 0, st>>>(g, p, h, u, v);
+  return 1;
+}
+
+template <typename T>
+int Launch<T>::gauges(const Geo &g, const Ptrs<T> &p, const int32_t *ij, int n, double *out, cudaStream_t st) {
+  if (n <= 0) return 0;
+  k_gauges<T><<<(n + TPB - 1) / TPB, TPB, 0, st>>>(g, p, ij, n, out);
   return 1;
 }
 

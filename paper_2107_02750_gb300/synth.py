@@ -61,6 +61,7 @@ class Problem:
     t_end: float = 1.0
     limiter: int = 1
     dt_max: float = 1.0
+    iface_rule: int = 0                 # static grids: 0 paper rule, 1 reflux
 
     @property
     def nx(self) -> int:

@@ -9,7 +9,7 @@ def oracle_sim(p, **over):
     kw = dict(M=p.M, N=p.N, L=p.L, R=p.dx, mode=p.mode, eps=p.eps, bc=p.bc,
               inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1,
               rain_rate=p.rain_rate, rain_t_end=p.rain_t_end, limiter=p.limiter,
-              dt_max=p.dt_max)
+              dt_max=p.dt_max, iface_rule=p.iface_rule)
     kw.update(over)
     s = O.Sim(**kw)
     s.load_dem(p.z_vert)
@@ -19,6 +19,21 @@ def oracle_sim(p, **over):
         s.set_inflow(p.inflow_t, p.inflow_Q)
     s.init_grid()
     return s
+
+
+def average_raster(sim):
+    """Finest-resolution raster of the active leaves' average depths (each
+    finest cell takes the average of the leaf covering it)."""
+    lev, ii, jj, co = sim.read_active()
+    L = sim.levels
+    nx, ny = sim.nx, sim.ny
+    out = np.zeros((ny, nx))
+    for l in np.unique(lev):
+        m = lev == l
+        w = 1 << (L - l)
+        for a, b, h in zip(ii[m], jj[m], co[m, 0]):
+            out[b * w:(b + 1) * w, a * w:(a + 1) * w] = h
+    return out
 
 
 def ritter_depth(x, t, x0, hL, g):
