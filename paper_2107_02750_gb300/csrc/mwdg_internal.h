@@ -24,6 +24,12 @@ struct Ctl {
   int changed;                 // grading sweep made a change
   unsigned int blocks_done;    // completion tickets of the last kernel of a step
   unsigned int ticket;         // completion tickets of the multi-level MRA kernels (self-resetting)
+  // set with dt at the start of a step, so that the FP32 kernels read them
+  // without FP64 arithmetic: dt in FP32, and the rain depth of the step
+  float dt_f, rain_inc_f;
+  int rain_on;
+  int pad_;
+  double rain_inc;
 };
 
 // Geometry and parameters of the level hierarchy (passed by value).

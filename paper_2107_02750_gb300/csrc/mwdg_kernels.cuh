@@ -417,6 +417,10 @@ __device__ __forceinline__ void begin_step(const Geo &g, Ctl *c, const int *nlea
   if (best < __longlong_as_double(0x7ff0000000000000LL)) dt = fmin(dt, g.cfl * best);
   dt = fmin(dt, c->t_end - c->t);
   c->dt = dt > 0.0 ? dt : 0.0;
+  c->dt_f = (float)c->dt;
+  c->rain_on = (c->t < g.rain_t_end && g.rain_rate > 0.0) ? 1 : 0;
+  c->rain_inc = c->rain_on ? g.rain_rate * c->dt : 0.0;
+  c->rain_inc_f = (float)c->rain_inc;
   c->bnd[0] = 0.0;
   c->bnd[1] = 0.0;
   c->blocks_done = 0u;
@@ -548,12 +552,30 @@ __global__ void k_leaf_maxabs(Geo g, Ptrs<T> p) {
   }
 }
 
+// forcing time of the inflow hydrograph, read only where a boundary face
+// needs it: t (stage 1 and the CFL pass) or t + dt (stage 2)
+struct ForceTime {
+  const Ctl *c;
+  bool plus_dt;
+  __device__ __forceinline__ double operator()() const { return plus_dt ? c->t + c->dt : c->t; }
+};
+
+// dt and the rain depth of the step in the coefficient type
+template <typename T> __device__ __forceinline__ T ctl_dt(const Ctl *c);
+template <> __device__ __forceinline__ float ctl_dt<float>(const Ctl *c) { return c->dt_f; }
+template <> __device__ __forceinline__ double ctl_dt<double>(const Ctl *c) { return c->dt; }
+template <typename T> __device__ __forceinline__ T ctl_rain(const Ctl *c);
+template <> __device__ __forceinline__ float ctl_rain<float>(const Ctl *c) { return c->rain_inc_f; }
+template <> __device__ __forceinline__ double ctl_rain<double>(const Ctl *c) { return c->rain_inc; }
+// dt > 0 without FP64 arithmetic (a non-negative double orders as its bits)
+__device__ __forceinline__ bool ctl_stepping(const Ctl *c) { return __double_as_longlong(c->dt) > 0; }
+
 // CFL candidate of one leaf (Courant number applied in k_begin_step):
 // min over x and y of dx / (|u| + sqrt(g h)) when wet, and the inflow ghost
 // states at the critical depth on inflow faces; +inf when there is none
 template <typename T>
 __device__ __forceinline__ T leaf_dt_candidate(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
-                                               T h0, T qx0, T qy0, double t) {
+                                               T h0, T qx0, T qy0, ForceTime t) {
   const T gg = geo_g<T>(g), hd = geo_hd<T>(g);
   const T dxl = geo_dx<T>(g, l);
   T best = tinf<T>();
@@ -567,7 +589,7 @@ __device__ __forceinline__ T leaf_dt_candidate(const Geo &g, const Ptrs<T> &p, i
       bool on = (e == 0 && i == 0) || (e == 1 && i == g.nxl[l] - 1) || (e == 2 && j == 0) ||
                 (e == 3 && j == g.nyl[l] - 1);
       if (!on) continue;
-      double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, t);
+      double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, t());
       if (q > 0.0) {
         T qt = (T)q;
         T hc = tcbrt(qt * qt / gg);
@@ -588,7 +610,7 @@ __device__ __forceinline__ void warp_min_to(unsigned long long *dst, T v) {
 template <typename T>
 __global__ void k_leaf_dt(Geo g, Ptrs<T> p) {
   const long long P = g.P;
-  const double t = p.ctl->t;
+  const ForceTime t{p.ctl, false};
   T best = tinf<T>();
   FOR_LEAVES(p) {
     int l, i, j;
@@ -684,19 +706,30 @@ __device__ __forceinline__ X ldx(const X *a) {
   return *a;
 }
 
-// Significance of a flow detail: max |d| / max(1, max |v0|) >= eps, compared
-// in FP64 in both precisions.  FP64: in that form (the oracle's order);
-// FP32: as max |d| >= thr with thr = eps * max(1, max |v0|) formed in FP64
-// once per block (a float detail converts exactly).
+// Significance of a flow detail: max |d| / max(1, max |v0|) >= eps, decided
+// as an FP64 comparison in both precisions.  FP64: in that form (the
+// oracle's order).  FP32: as (double) max |d| >= thr with thr = eps *
+// max(1, max |v0|) formed in FP64 once per block; for a non-negative float
+// that equals max |d| >= thr_f, thr_f the smallest float not below thr, so
+// the comparison itself needs no FP64 unit.
 template <typename T>
-__device__ __forceinline__ bool detail_significant(T dm, double mx, double thr, double eps);
+__device__ __forceinline__ bool detail_significant(T dm, double mx, float thr_f, double eps);
 template <>
-__device__ __forceinline__ bool detail_significant<double>(double dm, double mx, double thr, double eps) {
+__device__ __forceinline__ bool detail_significant<double>(double dm, double mx, float, double eps) {
   return dm / fmax(1.0, mx) >= eps;
 }
 template <>
-__device__ __forceinline__ bool detail_significant<float>(float dm, double, double thr, double) {
-  return (double)dm >= thr;
+__device__ __forceinline__ bool detail_significant<float>(float dm, double, float thr_f, double) {
+  return dm >= thr_f;
+}
+__device__ __forceinline__ float float_at_or_above(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = nextafterf(f, __int_as_float(0x7f800000));
+  return f;
+}
+// a >= b for non-negative doubles, on their bits (integer unit)
+__device__ __forceinline__ bool ge_nonneg(double a, double b) {
+  return __double_as_longlong(a) >= __double_as_longlong(b);
 }
 
 // MWDG2 encode of one node of level l (Sect. 2.3): a refined node gets the
@@ -709,7 +742,7 @@ template <bool SPEC, typename T>
 __device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
   const long long P = g.P, k = nid(g, l, i, j);
   const uint8_t kd = p.kind[k];
-  bool sig = p.DZ[k] >= g.eps;
+  bool sig = ge_nonneg(p.DZ[k], g.eps);
   T ch[3][4][3], zc[4][2];
   if (SPEC || kd == K_SIG) {
 #pragma unroll
@@ -735,7 +768,7 @@ __device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p,
 #pragma unroll
       for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sp[m];
       const double mx = __longlong_as_double((long long)p.ctl->vmax[v]);
-      sig = detail_significant<T>(detail_max3(ch[v]), mx, g.eps * fmax(1.0, mx), g.eps) || sig;
+      sig = detail_significant<T>(detail_max3(ch[v]), mx, float_at_or_above(g.eps * fmax(1.0, mx)), g.eps) || sig;
     }
   }
   p.flag[k] = (uint8_t)sig;
@@ -763,14 +796,14 @@ __device__ __forceinline__ uint8_t regular_flag(const Geo &g, const Ptrs<T> &p, 
 // adaptation runs only while there is time left to step (steps queued
 // beyond the end time are no-ops, as on the host side); the condition is
 // the same in every block of a launch
-#define ADAPT_LIVE(p) ((p).ctl->t < (p).ctl->t_end)
+#define ADAPT_LIVE(p) (!ge_nonneg((p).ctl->t, (p).ctl->t_end))
 
 // Eq. 9 encode of a refined node from its children's stored coefficients
 // ch[v][c][m] and bed slopes zc[c]; the node's stored coefficients go to
 // out; true when a normalised flow detail is significant
 template <typename T>
 __device__ __forceinline__ bool encode_sig(T (&ch)[3][4][3], const T (&zc)[4][2], T zp1, T zp2,
-                                           const double (&mx)[3], const double (&thr)[3], double eps,
+                                           const double (&mx)[3], const float (&thr)[3], double eps,
                                            T (&out)[9]) {
 #pragma unroll
   for (int c = 0; c < 4; c++) slopes_to_h(ch[0][c][1], ch[0][c][2], zc[c][0], zc[c][1]);
@@ -794,7 +827,7 @@ struct SigStage {
   uint8_t kind[MT_NODES];
   uint8_t topo[MT_NODES];  // topography detail significant
   double mx[3];            // max |v0| of h, qx, qy (normalisation of the flow details)
-  double thr[3];           // eps * max(1, mx)
+  float thr[3];            // eps * max(1, mx), rounded up to a float
 };
 
 // encode + significance of one tile (CG: the children of its finest level
@@ -805,7 +838,7 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
   if (threadIdx.x < 3) {
     const double m = __longlong_as_double((long long)p.ctl->vmax[threadIdx.x]);
     sh.mx[threadIdx.x] = m;
-    sh.thr[threadIdx.x] = g.eps * fmax(1.0, m);
+    sh.thr[threadIdx.x] = float_at_or_above(g.eps * fmax(1.0, m));
   }
   int sl[2];
   long long kk[2];
@@ -820,7 +853,7 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
     zs[q][0] = zs[q][1] = T(0);
     if (kk[q] >= 0) {
       kd[q] = p.kind[kk[q]];
-      tp[q] = p.DZ[kk[q]] >= g.eps;
+      tp[q] = ge_nonneg(p.DZ[kk[q]], g.eps);
       if (Form<T>::eta) {
         zs[q][0] = p.Z[P + kk[q]];
         zs[q][1] = p.Z[2 * P + kk[q]];
@@ -839,7 +872,8 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
         for (int m = 0; m < 9; m++) sh.u[sl[q]][m] = p.U[m * P + kk[q]];
     }
   __syncthreads();
-  double mx[3], thr[3];
+  double mx[3];
+  float thr[3];
 #pragma unroll
   for (int v = 0; v < 3; v++) {
     mx[v] = sh.mx[v];
@@ -1062,7 +1096,7 @@ template <typename T>
 __global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_decode(Geo g, Ptrs<T> p) {
   const long long P = g.P;
   const long long k0 = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
-  const double t = p.ctl->t;
+  const ForceTime t{p.ctl, false};
   int cnt = 0;
   T best = tinf<T>();
   if (k0 < P) {
@@ -1134,15 +1168,26 @@ __global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_decode(Geo g, Pt
       }
     }
   }
-  warp_min_to(&p.ctl->dtmin, best);
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    best = tmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  }
   __shared__ int ws[TPB / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = cnt;
+  __shared__ T wb[TPB / 32];
+  if ((threadIdx.x & 31) == 0) {
+    ws[threadIdx.x >> 5] = cnt;
+    wb[threadIdx.x >> 5] = best;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     int sum = 0;
-    for (int w = 0; w < TPB / 32; w++) sum += ws[w];
+    T b = wb[0];
+    for (int w = 0; w < TPB / 32; w++) {
+      sum += ws[w];
+      b = tmin(b, wb[w]);
+    }
     p.blk[blockIdx.x] = sum;
+    if (b < tinf<T>()) atomic_min_pos(&p.ctl->dtmin, (double)b);  // one FP64 conversion per block
   }
   if (last_block(&p.ctl->ticket)) block_scan_counts(gridDim.x, p.blk, p.nleaf);
 }
@@ -1192,10 +1237,9 @@ template <typename T, bool FRIC>
 __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   const long long P = g.P;
   const T hd = geo_hd<T>(g), s3 = s3v<T>(), gg = geo_g<T>(g);
-  const double dtd = p.ctl->dt;
-  const T dt = (T)dtd;
-  const bool rain = FRIC && p.ctl->t < g.rain_t_end && g.rain_rate > 0.0;
-  const T rinc = Form<T>::eta ? (T)(g.rain_rate * dtd) : (T)(g.rain_rate) * dt;
+  const T dt = ctl_dt<T>(p.ctl);
+  const bool rain = FRIC && p.ctl->rain_on;
+  const T rinc = ctl_rain<T>(p.ctl);
   FOR_LEAVES(p) {
     int l, i, j;
     long long k = unpack_leaf(g, p.leaves[_q], l, i, j);
@@ -1525,7 +1569,7 @@ struct FaceOut {
 
 template <typename T>
 __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
-                                                const T (&w)[9], const T (&zc)[3], int f, double tf) {
+                                                const T (&w)[9], const T (&zc)[3], int f, ForceTime tf) {
   const T gg = geo_g<T>(g), hd = geo_hd<T>(g);
   T own[4], nb[4];
   own[0] = first_face(w[0], w[1], w[2], zc[0], f);
@@ -1536,7 +1580,7 @@ __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, 
   if (!inside) {
     // ghost: wall mirror, open copy, or critical-depth inflow
     const int e = (f == 0) ? 1 : (f == 1) ? 0 : (f == 2) ? 3 : 2;
-    double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, tf);
+    double q = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, tf());
     nb[3] = own[3];
     if (q > 0.0) {
       T qt = (T)q;
@@ -1590,7 +1634,7 @@ __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, 
 // leaves' own fluxes through their halves of the face, computed by the same
 // code as theirs, so the mass leaving one side enters the other.
 template <typename T>
-__device__ __noinline__ bool reflux_face(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, double tf,
+__device__ __noinline__ bool reflux_face(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, ForceTime tf,
                                          T &F0, T &F1, T &F2) {
   const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
   if (a < 0 || b < 0 || a >= g.nxl[l] || b >= g.nyl[l] || p.kind[nid(g, l, a, b)] != K_SIG) return false;
@@ -1714,7 +1758,7 @@ __device__ __forceinline__ void store_var(long long P, int v, long long k, T *Ou
 // CFL candidate (fixed grids)
 template <typename T>
 __device__ __forceinline__ void next_step_reduce(const Geo &g, const Ptrs<T> &p, int l, int i, int j, T h0,
-                                                 T qx0, T qy0, double tf, T &m0, T &m1, T &m2, T &best) {
+                                                 T qx0, T qy0, ForceTime tf, T &m0, T &m1, T &m2, T &best) {
   if (g.mode == MWDG_ADAPTIVE) {
     m0 = tmax(m0, tabs(h0));
     m1 = tmax(m1, tabs(qx0));
@@ -1739,11 +1783,10 @@ template <typename T> struct Lanes { static constexpr int per_leaf = std::is_sam
 template <typename T, int STAGE, bool REFLUX>
 __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out) {
   const long long P = g.P;
-  const double dtd = p.ctl->dt;
-  if (!(dtd > 0.0)) return;  // a zero step changes nothing (end_step ignores it too)
-  const T dt = (T)dtd, gg = geo_g<T>(g), hd = geo_hd<T>(g), s3 = s3v<T>();
-  const double tf = (STAGE == 1) ? p.ctl->t : p.ctl->t + dtd;
-  T bsum = T(0);  // per-thread sum of a few boundary fluxes; FP64 from the warp sum on
+  if (!ctl_stepping(p.ctl)) return;  // a zero step changes nothing (end_step ignores it too)
+  const T dt = ctl_dt<T>(p.ctl), gg = geo_g<T>(g), hd = geo_hd<T>(g), s3 = s3v<T>();
+  const ForceTime tf{p.ctl, STAGE == 2};
+  T bsum = T(0);  // per-thread sum of a few boundary fluxes; FP64 from the block sum on
   double csum = 0.0;
   unsigned long long ncl = 0;
   bool bad = false;
@@ -1847,37 +1890,61 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
     }
   }
   if (bad) p.ctl->nonfinite = 1;
-  double bw = (double)bsum;
+  // block sums in the coefficient type, one FP64 conversion and atomic per
+  // block; clip volumes (rare) in FP64 where they occur
   for (int o = 16; o > 0; o >>= 1) {
-    bw += __shfl_xor_sync(0xffffffffu, bw, o);
-    csum += __shfl_xor_sync(0xffffffffu, csum, o);
+    bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
     ncl += __shfl_xor_sync(0xffffffffu, ncl, o);
   }
-  if ((threadIdx.x & 31) == 0) {
-    if (bw != 0.0) atomicAdd(&p.ctl->bnd[STAGE - 1], bw);
-    if (ncl) {
+  if (__any_sync(0xffffffffu, ncl != 0ULL)) {
+    for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
+    if ((threadIdx.x & 31) == 0 && ncl) {
       atomicAdd(&p.ctl->n_clip, ncl);
       atomicAdd(&p.ctl->v_clip, csum);
     }
   }
-  if (STAGE == 2) {
-    if (g.mode == MWDG_ADAPTIVE) {
-      for (int o = 16; o > 0; o >>= 1) {
-        m0 = tmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        m1 = tmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-        m2 = tmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-      }
-      if ((threadIdx.x & 31) == 0) {
-        atomic_max_pos(&p.ctl->vmax[0], (double)m0);
-        atomic_max_pos(&p.ctl->vmax[1], (double)m1);
-        atomic_max_pos(&p.ctl->vmax[2], (double)m2);
-      }
-    } else {
-      warp_min_to(&p.ctl->dtmin, best);
+  if (STAGE == 2 && g.mode == MWDG_ADAPTIVE)
+    for (int o = 16; o > 0; o >>= 1) {
+      m0 = tmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+      m1 = tmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+      m2 = tmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
     }
+  if (STAGE == 2 && g.mode != MWDG_ADAPTIVE)
+    for (int o = 16; o > 0; o >>= 1) best = tmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ T red[5][TPB / 32];
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][wid] = bsum;
+    red[1][wid] = m0;
+    red[2][wid] = m1;
+    red[3][wid] = m2;
+    red[4][wid] = best;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T b = red[0][0], r0 = red[1][0], r1 = red[2][0], r2 = red[3][0], r3 = red[4][0];
+    for (int w = 1; w < TPB / 32; w++) {
+      b += red[0][w];
+      r0 = tmax(r0, red[1][w]);
+      r1 = tmax(r1, red[2][w]);
+      r2 = tmax(r2, red[3][w]);
+      r3 = tmin(r3, red[4][w]);
+    }
+    if (b != T(0)) atomicAdd(&p.ctl->bnd[STAGE - 1], (double)b);
+    if (STAGE == 2) {
+      if (g.mode == MWDG_ADAPTIVE) {
+        atomic_max_pos(&p.ctl->vmax[0], (double)r0);
+        atomic_max_pos(&p.ctl->vmax[1], (double)r1);
+        atomic_max_pos(&p.ctl->vmax[2], (double)r2);
+      } else if (r3 < tinf<T>()) {
+        atomic_min_pos(&p.ctl->dtmin, (double)r3);
+      }
+    }
+  }
+  if (STAGE == 2) {
     // the last block to finish closes the step (no waiting: each block takes
     // a ticket after its own atomics are visible)
-    if ((threadIdx.x & 31) == 0) __threadfence();
+    if (threadIdx.x == 0) __threadfence();
     __syncthreads();
     __shared__ bool last;
     if (threadIdx.x == 0) last = (atomicAdd(&p.ctl->blocks_done, 1u) == gridDim.x - 1);
