@@ -355,16 +355,24 @@ static __global__ void k_compact_count(long long P, const uint8_t *kind, int *bl
 }
 
 // exclusive scan of the per-block leaf counts in place (read through L2)
-// and their total, by one block
+// and their total, by one block: each thread reads its run of up to SCAN_RUN
+// consecutive counts at once, then one block-wide scan of the run sums
+constexpr int SCAN_RUN = 16;
 __device__ __forceinline__ void block_scan_counts(int nb, int *blk, int *total) {
   __shared__ int carry;
   __shared__ int ws[32];
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int base = 0; base < nb; base += blockDim.x) {
-    int idx = base + threadIdx.x;
-    int v = (idx < nb) ? __ldcg(&blk[idx]) : 0;
-    int x = v;
+  const int span = blockDim.x * SCAN_RUN;
+  for (int base = 0; base < nb; base += span) {
+    const int b0 = base + threadIdx.x * SCAN_RUN;
+    int v[SCAN_RUN];
+#pragma unroll
+    for (int q = 0; q < SCAN_RUN; q++) v[q] = (b0 + q < nb) ? __ldcg(&blk[b0 + q]) : 0;
+    int run = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_RUN; q++) run += v[q];
+    int x = run;
     for (int o = 1; o < 32; o <<= 1) {
       int y = __shfl_up_sync(0xffffffffu, x, o);
       if ((threadIdx.x & 31) >= o) x += y;
@@ -380,9 +388,15 @@ __device__ __forceinline__ void block_scan_counts(int nb, int *blk, int *total) 
       ws[threadIdx.x] = w;
     }
     __syncthreads();
-    int warp_off = (threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0;
-    int incl = x + warp_off + carry;
-    if (idx < nb) blk[idx] = incl - v;
+    const int warp_off = (threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0;
+    const int incl = x + warp_off + carry;
+    int e = incl - run;  // exclusive prefix of this run
+#pragma unroll
+    for (int q = 0; q < SCAN_RUN; q++)
+      if (b0 + q < nb) {
+        blk[b0 + q] = e;
+        e += v[q];
+      }
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1) carry = incl;
     __syncthreads();
@@ -1492,16 +1506,25 @@ __device__ __forceinline__ T first_face(T c0, T c1, T c2, T ze0, int f) {
   return Form<T>::eta ? face_value(c0 + ze0, c1, c2, f) : face_value(c0, c1, c2, f);
 }
 
-// limit (first variable, qx, qy, z) of the same-level view of the neighbour
-// across face f of leaf (l, i, j); false on the domain boundary
+// neighbour node k across face f of leaf (l, i, j) and its kind; false on
+// the domain boundary
 template <typename T>
-__device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, T out[4]) {
+__device__ __forceinline__ bool nbr_locate(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f,
+                                           long long &k, uint8_t &kd) {
   const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
   if (a < 0 || b < 0 || a >= g.nxl[l] || b >= g.nyl[l]) return false;
+  k = nid(g, l, a, b);
+  kd = p.kind[k];
+  return true;
+}
+
+// limit (first variable, qx, qy, z) of the same-level view of neighbour k
+// (kind kd) across face f of leaf (l, i, j)
+template <typename T>
+__device__ void nbr_view(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, long long k, uint8_t kd,
+                         T out[4]) {
+  const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
   const int fo = f ^ 1;
-  const long long P = g.P;
-  long long k = nid(g, l, a, b);
-  const uint8_t kd = p.kind[k];
   if (kd == K_SIG && g.mode == MWDG_STATIC) {
     // Sect. 2.2.1: the coarse side interpolates the limit from the two finer
     // interface centres (graded grid: both are level l+1 leaves)
@@ -1520,7 +1543,7 @@ __device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, i
       out[v] = T(0.5) * (face_value(r1[3 * v], r1[3 * v + 1], r1[3 * v + 2], fo) +
                          face_value(r2[3 * v], r2[3 * v + 1], r2[3 * v + 2], fo));
     out[3] = T(0.5) * (face_value(r1[9], r1[10], r1[11], fo) + face_value(r2[9], r2[10], r2[11], fo));
-    return true;
+    return;
   }
   if (kd == K_BELOW) {
     // prolongation of the covering coarser leaf's plane down to this node
@@ -1548,13 +1571,22 @@ __device__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, i
       out[v] = face_value(sv[0], sv[1], sv[2], fo);
     }
     if (Form<T>::eta) out[0] = out[0] + out[3];  // depth + bed = free surface
-    return true;
+    return;
   }
   T r[12];
   load_rec(p.FZ, k, r);
   out[0] = first_face(r[0], r[1], r[2], r[9], fo);
   for (int v = 1; v < 3; v++) out[v] = face_value(r[3 * v], r[3 * v + 1], r[3 * v + 2], fo);
   out[3] = face_value(r[9], r[10], r[11], fo);
+}
+
+// both: the neighbour's view limit across face f; false on the boundary
+template <typename T>
+__device__ __forceinline__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, T out[4]) {
+  long long k;
+  uint8_t kd;
+  if (!nbr_locate(g, p, l, i, j, f, k, kd)) return false;
+  nbr_view(g, p, l, i, j, f, k, kd, out);
   return true;
 }
 
@@ -1567,16 +1599,17 @@ struct FaceOut {
   T bout;             // outward boundary mass flux (m^3/s), 0 inside
 };
 
+// given the neighbour's view limit nb (inside) or a boundary (ghost)
 template <typename T>
-__device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
-                                                const T (&w)[9], const T (&zc)[3], int f, ForceTime tf) {
+__device__ __forceinline__ FaceOut<T> face_flux_nb(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
+                                                   const T (&w)[9], const T (&zc)[3], int f, ForceTime tf,
+                                                   bool inside, T (&nb)[4]) {
   const T gg = geo_g<T>(g), hd = geo_hd<T>(g);
-  T own[4], nb[4];
+  T own[4];
   own[0] = first_face(w[0], w[1], w[2], zc[0], f);
   own[1] = face_value(w[3], w[4], w[5], f);
   own[2] = face_value(w[6], w[7], w[8], f);
   own[3] = face_value(zc[0], zc[1], zc[2], f);
-  const bool inside = nbr_limit(g, p, l, i, j, f, nb);
   if (!inside) {
     // ghost: wall mirror, open copy, or critical-depth inflow
     const int e = (f == 0) ? 1 : (f == 1) ? 0 : (f == 2) ? 3 : 2;
@@ -1627,6 +1660,14 @@ __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, 
   o.bout = T(0);
   if (!inside) o.bout = ((f == 0 || f == 2) ? o.F0 : -o.F0) * geo_dx<T>(g, l);
   return o;
+}
+
+template <typename T>
+__device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
+                                                const T (&w)[9], const T (&zc)[3], int f, ForceTime tf) {
+  T nb[4];
+  const bool inside = nbr_limit(g, p, l, i, j, f, nb);
+  return face_flux_nb(g, p, l, i, j, w, zc, f, tf, inside, nb);
 }
 
 // Reflux rule on static grids (MWDG_IFACE_REFLUX): on the coarse side of a
@@ -1774,14 +1815,16 @@ __device__ __forceinline__ void next_step_reduce(const Geo &g, const Ptrs<T> &p,
 // two-point interface rule for the slope volume integrals with the bed
 // source S1 = -(2 sqrt3 g / dx) h1 (h1 + z1) that cancels its hydrostatic
 // error at rest), then the update, the positivity clip and the dry reset.
-// FP32: four lanes share a leaf, one per interface (E, W, N, S), and lanes
-// 0-2 then finish h, qx, qy after a warp-shuffle exchange.  FP64 (whose
-// arithmetic units are few on this GPU): one thread per leaf.
-template <typename T> struct Lanes { static constexpr int per_leaf = std::is_same<T, float>::value ? 4 : 1; };
+// One thread per leaf: the four neighbours' kinds are read together, then
+// their views, then the four interfaces and the three variables.
+//
+// resident blocks per SM asked of the update (FP32: at most 64 registers a
+// thread, four blocks; FP64 keeps its registers)
+template <typename T> struct UpdOcc { static constexpr int blocks = std::is_same<T, float>::value ? 4 : 1; };
 
 // REFLUX: compiled with the reflux interface rule (static grids only)
 template <typename T, int STAGE, bool REFLUX>
-__global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out) {
+__global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out) {
   const long long P = g.P;
   if (!ctl_stepping(p.ctl)) return;  // a zero step changes nothing (end_step ignores it too)
   const T dt = ctl_dt<T>(p.ctl), gg = geo_g<T>(g), hd = geo_hd<T>(g), s3 = s3v<T>();
@@ -1796,98 +1839,57 @@ __global__ void __launch_bounds__(TPB) k_leaf_update(Geo g, Ptrs<T> p, const T *
   T m0 = T(0), m1 = T(0), m2 = T(0);
   T best = tinf<T>();
   const int nl = *p.nleaf;
-  if (Lanes<T>::per_leaf == 4) {
-    const int f = threadIdx.x & 3;
-    const long long nthreads = (long long)gridDim.x * blockDim.x;
-    // every lane runs the same number of iterations (shuffles need the warp)
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < 4LL * nl; base += nthreads) {
-      const long long q = (base + threadIdx.x) >> 2;
-      const bool valid = q < nl;
-      long long k = 0;
-      int l = 0, i = 0, j = 0;
-      T w[9], zc[3];
-      FaceOut<T> fo{};
-      if (valid) {
-        k = unpack_leaf(g, p.leaves[q], l, i, j);
-        {
-          T r[12];
-          load_rec(p.FZ, k, r);
+  // one thread per leaf: the four interfaces, then the three variables
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nl;
+       q += (long long)gridDim.x * blockDim.x) {
+    int l, i, j;
+    const long long k = unpack_leaf(g, p.leaves[q], l, i, j);
+    T w[9], zc[3];
+    {
+      T r[12];
+      load_rec(p.FZ, k, r);
 #pragma unroll
-          for (int m = 0; m < 9; m++) w[m] = r[m];
+      for (int m = 0; m < 9; m++) w[m] = r[m];
 #pragma unroll
-          for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
-        }
-        fo = face_flux(g, p, l, i, j, w, zc, f, tf);
-        if (REFLUX) reflux_face(g, p, l, i, j, f, tf, fo.F0, fo.F1, fo.F2);
-        bsum += fo.bout;
-      }
-      // every lane of the group gets the four interfaces; lanes 0, 1, 2
-      // then finish the variables h, qx, qy of the leaf
-      const int gbase = (threadIdx.x & 31) & ~3;
-      T Fv[4], hs[4], us[4], vs[4], zr[4];
-#pragma unroll
-      for (int d = 0; d < 4; d++) {
-        T c0 = __shfl_sync(0xffffffffu, fo.F0, gbase + d);
-        T c1 = __shfl_sync(0xffffffffu, fo.F1, gbase + d);
-        T c2 = __shfl_sync(0xffffffffu, fo.F2, gbase + d);
-        Fv[d] = (f == 0) ? c0 : (f == 1) ? c1 : c2;
-        hs[d] = __shfl_sync(0xffffffffu, fo.hs, gbase + d);
-        us[d] = __shfl_sync(0xffffffffu, fo.us, gbase + d);
-        vs[d] = __shfl_sync(0xffffffffu, fo.vs, gbase + d);
-        zr[d] = __shfl_sync(0xffffffffu, fo.zr, gbase + d);
-      }
-      T o0 = T(0), o1 = T(0), o2 = T(0);
-      if (valid && f < 3) finish_var<T, STAGE>(g, p, f, k, l, w, zc, Fv, hs, us, vs, zr, dt, Wst, Wcomb, o0, o1, o2);
-      // positivity clip (lane 0) and dry reset (all three)
-      const T h0n = __shfl_sync(0xffffffffu, o0, gbase);
-      if (valid && f < 3) {
-        post_var<T>(g, p, f, k, l, h0n, o0, o1, o2, ncl, csum, bad);
-        store_var(P, f, k, Out, o0, o1, o2);
-      }
-      if (STAGE == 2) {
-        const T qx0 = __shfl_sync(0xffffffffu, o0, gbase + 1);
-        const T qy0 = __shfl_sync(0xffffffffu, o0, gbase + 2);
-        if (valid && f == 0) next_step_reduce<T>(g, p, l, i, j, o0, qx0, qy0, tf, m0, m1, m2, best);
-      }
+      for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
     }
-  } else {
-    // one thread per leaf: the four interfaces, then the three variables
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nl;
-         q += (long long)gridDim.x * blockDim.x) {
-      int l, i, j;
-      const long long k = unpack_leaf(g, p.leaves[q], l, i, j);
-      T w[9], zc[3];
-      {
-        T r[12];
-        load_rec(p.FZ, k, r);
+    // the four neighbours' kinds, then their views, with every load of a
+    // phase in flight together
+    long long kn[4];
+    uint8_t kd[4];
+    bool in[4];
 #pragma unroll
-        for (int m = 0; m < 9; m++) w[m] = r[m];
-#pragma unroll
-        for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
-      }
-      T F[4][3], hs[4], us[4], vs[4], zr[4];
-#pragma unroll
-      for (int d = 0; d < 4; d++) {
-        FaceOut<T> fo = face_flux(g, p, l, i, j, w, zc, d, tf);
-        if (REFLUX) reflux_face(g, p, l, i, j, d, tf, fo.F0, fo.F1, fo.F2);
-        bsum += fo.bout;
-        F[d][0] = fo.F0; F[d][1] = fo.F1; F[d][2] = fo.F2;
-        hs[d] = fo.hs; us[d] = fo.us; vs[d] = fo.vs; zr[d] = fo.zr;
-      }
-      T o[3][3];
-#pragma unroll
-      for (int v = 0; v < 3; v++) {
-        T Fv[4] = {F[0][v], F[1][v], F[2][v], F[3][v]};
-        finish_var<T, STAGE>(g, p, v, k, l, w, zc, Fv, hs, us, vs, zr, dt, Wst, Wcomb, o[v][0], o[v][1], o[v][2]);
-      }
-      const T h0n = o[0][0];
-#pragma unroll
-      for (int v = 0; v < 3; v++) {
-        post_var<T>(g, p, v, k, l, h0n, o[v][0], o[v][1], o[v][2], ncl, csum, bad);
-        store_var(P, v, k, Out, o[v][0], o[v][1], o[v][2]);
-      }
-      if (STAGE == 2) next_step_reduce<T>(g, p, l, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
+    for (int d = 0; d < 4; d++) {
+      kn[d] = 0;
+      kd[d] = K_BELOW;
+      in[d] = nbr_locate(g, p, l, i, j, d, kn[d], kd[d]);
     }
+    T nb[4][4];
+#pragma unroll
+    for (int d = 0; d < 4; d++)
+      if (in[d]) nbr_view(g, p, l, i, j, d, kn[d], kd[d], nb[d]);
+    T F[4][3], hs[4], us[4], vs[4], zr[4];
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+      FaceOut<T> fo = face_flux_nb(g, p, l, i, j, w, zc, d, tf, in[d], nb[d]);
+      if (REFLUX) reflux_face(g, p, l, i, j, d, tf, fo.F0, fo.F1, fo.F2);
+      bsum += fo.bout;
+      F[d][0] = fo.F0; F[d][1] = fo.F1; F[d][2] = fo.F2;
+      hs[d] = fo.hs; us[d] = fo.us; vs[d] = fo.vs; zr[d] = fo.zr;
+    }
+    T o[3][3];
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+      T Fv[4] = {F[0][v], F[1][v], F[2][v], F[3][v]};
+      finish_var<T, STAGE>(g, p, v, k, l, w, zc, Fv, hs, us, vs, zr, dt, Wst, Wcomb, o[v][0], o[v][1], o[v][2]);
+    }
+    const T h0n = o[0][0];
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+      post_var<T>(g, p, v, k, l, h0n, o[v][0], o[v][1], o[v][2], ncl, csum, bad);
+      store_var(P, v, k, Out, o[v][0], o[v][1], o[v][2]);
+    }
+    if (STAGE == 2) next_step_reduce<T>(g, p, l, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
   }
   if (bad) p.ctl->nonfinite = 1;
   // block sums in the coefficient type, one FP64 conversion and atomic per
