@@ -375,7 +375,7 @@ def kernel_bytes_per_leaf(name, ts):
 
 # DRAM bytes (read + write) per launch measured by ncu for a kernel, when the
 # kernel has not changed since (see profiles/); None otherwise
-TRAFFIC = {}
+TRAFFIC = {"dg2_update_stage2": 51_160_320 + 3_683_328}  # ncu: dram read + write, one launch at this workload
 
 
 def main():
