@@ -161,7 +161,8 @@ mwdg_status allocate_state(mwdg_ctx *c) {
       (s = alloc(c, &p.Wi, 9 * P)) || (s = alloc(c, &p.FZ, 12 * P)) || (s = alloc(c, &p.Z, 3 * P)) ||
       (s = alloc(c, &p.NM, P)) || (s = alloc(c, &p.DZ, P)) ||
       (s = alloc(c, &p.kind, P)) || (s = alloc(c, &p.kind_new, P)) || (s = alloc(c, &p.flag, P)) ||
-      (s = alloc(c, &p.flag2, P)) || (s = alloc(c, &p.leaves, P)) || (s = alloc(c, &p.nleaf, 1)))
+      (s = alloc(c, &p.flag2, P)) || (s = alloc(c, &p.leaves, P)) || (s = alloc(c, &p.nbr, 4 * P)) ||
+      (s = alloc(c, &p.nleaf, 1)))
     return s;
   const size_t nb = (P + 2048 - 1) / 2048 + 1;
   if ((s = alloc(c, &p.blk, nb)) || (s = alloc(c, &p.part, (size_t)c->grid_leaves))) return s;

@@ -74,6 +74,7 @@ struct Ptrs {
   uint8_t *kind, *flag, *flag2;
   uint8_t *kind_new;  // kinds of the next active set while the old ones are still read
   long long *leaves;  // active leaves, packed (level << 56 | j << 28 | i)
+  long long *nbr;     // per active leaf, its four face-neighbour codes (E, W, N, S)
   int *nleaf;
   int *blk;         // compaction scratch: per-block counts / offsets
   double *part;     // volume partial sums

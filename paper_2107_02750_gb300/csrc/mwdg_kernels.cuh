@@ -447,6 +447,61 @@ __device__ __forceinline__ void begin_step(const Geo &g, Ctl *c, const int *nlea
   }
 }
 
+// Face-neighbour code of a leaf, fixed for a step (the grid does not change
+// between the stages): what the same-level view of the neighbour across the
+// face is made from, and which node holds it.
+//   NB_EDGE     domain boundary
+//   NB_LEAF     a leaf at the same level (its record)
+//   NB_REFINED  a refined node at the same level (MWDG2: its encoded record;
+//               static grid: its two finer leaves)
+//   NB_COARSER  below a coarser leaf: that leaf and the level difference
+enum : int { NB_EDGE = 0, NB_LEAF = 1, NB_REFINED = 2, NB_COARSER = 3 };
+__device__ __forceinline__ long long nb_code(int type, int d, long long k) {
+  return ((long long)type << 62) | ((long long)d << 56) | k;
+}
+__device__ __forceinline__ int nb_type(long long c) { return (int)((unsigned long long)c >> 62); }
+__device__ __forceinline__ int nb_depth(long long c) { return (int)((c >> 56) & 0xF); }
+__device__ __forceinline__ long long nb_node(long long c) { return c & 0xFFFFFFFFFFFFFFLL; }
+
+// the four codes of leaf (l, i, j) under the kinds `kind`; the first kinds
+// are read together, then the walks up (coarser neighbours) follow
+__device__ __forceinline__ void leaf_nb_codes(const Geo &g, const uint8_t *kind, int l, int i, int j,
+                                              long long (&out)[4]) {
+  long long kn[4];
+  uint8_t kd[4];
+  bool in[4];
+#pragma unroll
+  for (int f = 0; f < 4; f++) {
+    const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
+    in[f] = !(a < 0 || b < 0 || a >= g.nxl[l] || b >= g.nyl[l]);
+    kn[f] = in[f] ? nid(g, l, a, b) : 0;
+    kd[f] = in[f] ? kind[kn[f]] : (uint8_t)K_BELOW;
+  }
+#pragma unroll
+  for (int f = 0; f < 4; f++) {
+    if (!in[f]) { out[f] = nb_code(NB_EDGE, 0, 0); continue; }
+    if (kd[f] == K_LEAF) { out[f] = nb_code(NB_LEAF, 0, kn[f]); continue; }
+    if (kd[f] == K_SIG) { out[f] = nb_code(NB_REFINED, 0, kn[f]); continue; }
+    int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3), la = l, d = 0;
+    long long ka = kn[f];
+    while (la > 0 && kind[ka] == K_BELOW) {
+      a >>= 1;
+      b >>= 1;
+      la--;
+      d++;
+      ka = nid(g, la, a, b);
+    }
+    out[f] = nb_code(NB_COARSER, d, ka);
+  }
+}
+
+// a leaf's four neighbour codes (E, W, N, S) from the per-step table
+__device__ __forceinline__ void load_nb_codes(const long long *nbr, long long q, long long (&c)[4]) {
+  const longlong2 *src = reinterpret_cast<const longlong2 *>(nbr + 4 * q);
+  const longlong2 a = src[0], b = src[1];
+  c[0] = a.x; c[1] = a.y; c[2] = b.x; c[3] = b.y;
+}
+
 // order-preserving scatter of the active leaves (each thread owns CPT
 // consecutive nodes, read as one 8-byte word); with kind_out the kinds are
 // also copied there
@@ -503,6 +558,21 @@ static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *
   }
   // with begin_ctl, the last block also starts the step on the new leaves
   if (begin_ctl && last_block(&begin_ctl->ticket) && threadIdx.x == 0) begin_step(g, begin_ctl, nleaf);
+}
+
+// the four face-neighbour codes of every active leaf (one thread per leaf)
+static __global__ void k_leaf_codes(Geo g, const uint8_t *kind, const long long *leaves, const int *nleaf,
+                                    long long *nbr) {
+  const int n = *nleaf;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    int l, i, j;
+    unpack_leaf(g, leaves[q], l, i, j);
+    long long c4[4];
+    leaf_nb_codes(g, kind, l, i, j, c4);
+    longlong2 *dst = reinterpret_cast<longlong2 *>(nbr + 4LL * q);
+    dst[0] = make_longlong2(c4[0], c4[1]);
+    dst[1] = make_longlong2(c4[2], c4[3]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1304,12 +1374,14 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
       for (int m = 0; m < 9; m++) ws[m] = w[m];
       ze[0] = zp[0]; ze[1] = zp[1]; ze[2] = zp[2];
       if (g.limiter) {
+        // same-level leaf neighbours from the step's neighbour codes
+        long long code[4];
+        load_nb_codes(p.nbr, _q, code);
         for (int dir = 0; dir < 2; dir++) {
-          const int ia = i + (dir == 0), ja = j + (dir == 1), ib = i - (dir == 0), jb = j - (dir == 1);
-          const bool hasA = ia < g.nxl[l] && ja < g.nyl[l] && p.kind[nid(g, l, ia, ja)] == K_LEAF;
-          const bool hasB = ib >= 0 && jb >= 0 && p.kind[nid(g, l, ib, jb)] == K_LEAF;
+          const long long cA = code[2 * dir], cB = code[2 * dir + 1];  // E/W, then N/S
+          const bool hasA = nb_type(cA) == NB_LEAF, hasB = nb_type(cB) == NB_LEAF;
           if (!hasA && !hasB) continue;
-          const long long ka = hasA ? nid(g, l, ia, ja) : k, kb = hasB ? nid(g, l, ib, jb) : k;
+          const long long ka = hasA ? nb_node(cA) : k, kb = hasB ? nb_node(cB) : k;
           T hC = h0;
           T hA = X[ka];
           T hB = X[kb];
@@ -1575,6 +1647,56 @@ __device__ void nbr_view(const Geo &g, const Ptrs<T> &p, int l, int i, int j, in
   }
   T r[12];
   load_rec(p.FZ, k, r);
+  out[0] = first_face(r[0], r[1], r[2], r[9], fo);
+  for (int v = 1; v < 3; v++) out[v] = face_value(r[3 * v], r[3 * v + 1], r[3 * v + 2], fo);
+  out[3] = face_value(r[9], r[10], r[11], fo);
+}
+
+// the same from the leaf's neighbour code (no kind reads, no walk)
+template <typename T>
+__device__ void nbr_view_code(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, long long code,
+                              T out[4]) {
+  const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
+  const int fo = f ^ 1;
+  const int type = nb_type(code);
+  const long long k = nb_node(code);
+  if (type == NB_REFINED && g.mode == MWDG_STATIC) {
+    int c1, c2;
+    if (f == 0) { c1 = 0; c2 = 2; }
+    else if (f == 1) { c1 = 1; c2 = 3; }
+    else if (f == 2) { c1 = 0; c2 = 1; }
+    else { c1 = 2; c2 = 3; }
+    long long k1 = nid(g, l + 1, 2 * a + (c1 & 1), 2 * b + (c1 >> 1));
+    long long k2 = nid(g, l + 1, 2 * a + (c2 & 1), 2 * b + (c2 >> 1));
+    T r1[12], r2[12];
+    load_rec(p.FZ, k1, r1);
+    load_rec(p.FZ, k2, r2);
+    out[0] = T(0.5) * (first_face(r1[0], r1[1], r1[2], r1[9], fo) + first_face(r2[0], r2[1], r2[2], r2[9], fo));
+    for (int v = 1; v < 3; v++)
+      out[v] = T(0.5) * (face_value(r1[3 * v], r1[3 * v + 1], r1[3 * v + 2], fo) +
+                         face_value(r2[3 * v], r2[3 * v + 1], r2[3 * v + 2], fo));
+    out[3] = T(0.5) * (face_value(r1[9], r1[10], r1[11], fo) + face_value(r2[9], r2[10], r2[11], fo));
+    return;
+  }
+  T r[12];
+  load_rec(p.FZ, k, r);
+  if (type == NB_COARSER) {
+    // prolongation of the coarser leaf's plane down to the neighbour node,
+    // one level at a time (child of level l - q: bits q of a and b)
+    const int d = nb_depth(code);
+    for (int v = 3; v >= 0; v--) {
+      T sv[3] = {r[3 * v], r[3 * v + 1], r[3 * v + 2]};
+      if (v == 0) slopes_to_h(sv[1], sv[2], r[10], r[11]);
+      for (int q = d - 1; q >= 0; q--) {
+        T o[3];
+        prolong3(sv[0], sv[1], sv[2], ((a >> q) & 1) + 2 * ((b >> q) & 1), o);
+        sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
+      }
+      out[v] = face_value(sv[0], sv[1], sv[2], fo);
+    }
+    if (Form<T>::eta) out[0] = out[0] + out[3];  // depth + bed = free surface
+    return;
+  }
   out[0] = first_face(r[0], r[1], r[2], r[9], fo);
   for (int v = 1; v < 3; v++) out[v] = face_value(r[3 * v], r[3 * v + 1], r[3 * v + 2], fo);
   out[3] = face_value(r[9], r[10], r[11], fo);
@@ -1853,21 +1975,17 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
 #pragma unroll
       for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
     }
-    // the four neighbours' kinds, then their views, with every load of a
-    // phase in flight together
-    long long kn[4];
-    uint8_t kd[4];
+    // the four neighbours' views from the step's neighbour codes, all
+    // loads in flight together
+    long long code[4];
+    load_nb_codes(p.nbr, q, code);
     bool in[4];
-#pragma unroll
-    for (int d = 0; d < 4; d++) {
-      kn[d] = 0;
-      kd[d] = K_BELOW;
-      in[d] = nbr_locate(g, p, l, i, j, d, kn[d], kd[d]);
-    }
     T nb[4][4];
 #pragma unroll
-    for (int d = 0; d < 4; d++)
-      if (in[d]) nbr_view(g, p, l, i, j, d, kn[d], kd[d], nb[d]);
+    for (int d = 0; d < 4; d++) {
+      in[d] = nb_type(code[d]) != NB_EDGE;
+      if (in[d]) nbr_view_code(g, p, l, i, j, d, code[d], nb[d]);
+    }
     T F[4][3], hs[4], us[4], vs[4], zr[4];
 #pragma unroll
     for (int d = 0; d < 4; d++) {
@@ -2169,7 +2287,8 @@ int Launch<T>::compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
   k_compact_count<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk);
   k_compact_scan<<<1, 1024, 0, st>>>(nb, p.blk, p.nleaf);
   k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves, nullptr, nullptr, nullptr);
-  return 3;
+  k_leaf_codes<<<(int)std::min<long long>(nblk(g.P), 152 * 8), TPB, 0, st>>>(g, p.kind, p.leaves, p.nleaf, p.nbr);
+  return 4;
 }
 
 // levels 0..coarse_top run in one block (each has at most g.coarse_nodes
@@ -2230,7 +2349,10 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
   MARK(KC_COMPACT);
   k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind_new, p.blk, p.leaves, p.kind, begin ? p.ctl : nullptr,
                                         p.nleaf);
-  return n + 2;
+  MARK(KC_COMPACT);
+  k_leaf_codes<<<(int)std::min<long long>(nblk(g.P), 152 * 8), TPB, 0, st>>>(g, p.kind_new, p.leaves, p.nleaf,
+                                                                             p.nbr);
+  return n + 3;
 }
 
 template <typename T>
