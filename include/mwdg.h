@@ -239,6 +239,51 @@ MWDG_API mwdg_status mwdg_launch_count(mwdg_ctx *ctx, int64_t *n);
 MWDG_API mwdg_status mwdg_volume_noalloc(const double *h0, const int32_t *level, int64_t n, double dx,
                                          int32_t L, double *volume, void *cuda_stream);
 
+/* Launch shape of a context's step kernels: the number of blocks of the
+ * leaf kernels (grid_leaves, 1..65535) and the size of the coarsest MRA
+ * levels run by one block (coarse_nodes >= 1: levels with at most that many
+ * nodes).  Neither changes the arithmetic of a leaf or node; both change
+ * only how the work is spread.  Either argument <= 0 keeps the current
+ * value.  mwdg_get_launch_shape reads them (any pointer may be NULL). */
+MWDG_API mwdg_status mwdg_set_launch_shape(mwdg_ctx *ctx, int32_t grid_leaves, int64_t coarse_nodes);
+MWDG_API mwdg_status mwdg_get_launch_shape(mwdg_ctx *ctx, int32_t *grid_leaves, int64_t *coarse_nodes);
+
+/* Ensembles (batched scenarios of uneven sizes).  An ensemble steps n
+ * independent contexts together: one CUDA graph per ensemble step holds
+ * every member's step as a parallel branch, so small members share the GPU
+ * instead of each leaving most of it idle.  Members are created and loaded
+ * as usual (any mode, precision and size, same device); the ensemble
+ * borrows them (the caller keeps ownership and must not destroy a member
+ * while the ensemble exists).  Each member keeps its own time step; in
+ * mwdg_ensemble_run_to_time every member stops at t_end.  A member's own
+ * calls may be interleaved with ensemble calls: ensemble work is ordered
+ * after the member's earlier work on its stream and before its later work.
+ * The graph is rebuilt when a member's parameters changed.  Results equal
+ * those of the members stepped one by one.  cuda_stream orders the
+ * ensemble's work (NULL: the ensemble creates a stream of its own; a
+ * stream passed in must be capturable, i.e. not the legacy default
+ * stream).  Errors: MWDG_ERR_ARG (NULL, n < 1, a member listed twice),
+ * MWDG_ERR_STATE (a member without an initial state, in an error state or
+ * with per-kernel timing on), MWDG_ERR_NONFINITE, MWDG_ERR_CUDA. */
+typedef struct mwdg_ensemble mwdg_ensemble;
+MWDG_API mwdg_status mwdg_ensemble_create(mwdg_ctx *const *members, int32_t n, void *cuda_stream,
+                                          mwdg_ensemble **out);
+MWDG_API void mwdg_ensemble_destroy(mwdg_ensemble *ens);
+/* n ensemble steps (each member one step, queued, no host synchronisation) */
+MWDG_API mwdg_status mwdg_ensemble_step(mwdg_ensemble *ens, int64_t n);
+/* until every member's time reaches t_end (last steps shortened to land on
+ * it); *graph_launches_out (may be NULL) receives the ensemble steps queued */
+MWDG_API mwdg_status mwdg_ensemble_run_to_time(mwdg_ensemble *ens, double t_end, int64_t *graph_launches_out);
+/* Autotuner: for each member, times `steps` steps of every candidate launch
+ * shape (grid_leaves in {1, 2, 4, 8} x 152 blocks, coarse_nodes in {64,
+ * 256, 1024}) from a saved state, restores the state, and keeps the fastest.
+ * chosen (may be NULL) receives grid_leaves and coarse_nodes per member
+ * (2n int64).  Members end with the state they had.  The results of later
+ * steps are unchanged up to the FP32 contraction order of the coarsest MRA
+ * levels (FP64: identical). */
+MWDG_API mwdg_status mwdg_ensemble_tune(mwdg_ensemble *ens, int32_t steps, int64_t *chosen);
+MWDG_API const char *mwdg_ensemble_last_error(const mwdg_ensemble *ens);
+
 MWDG_API const char *mwdg_last_error(const mwdg_ctx *ctx);
 MWDG_API const char *mwdg_status_string(mwdg_status s);
 

@@ -22,6 +22,8 @@ EXPORTS = (
     "mwdg_get_volume", "mwdg_profile", "mwdg_kernel_times", "mwdg_launch_count",
     "mwdg_last_error", "mwdg_status_string", "mwdg_state_bytes", "mwdg_save_state",
     "mwdg_load_state", "mwdg_volume_noalloc", "mwdg_get_counters", "mwdg_read_gauges",
+    "mwdg_set_launch_shape", "mwdg_get_launch_shape", "mwdg_ensemble_create", "mwdg_ensemble_destroy",
+    "mwdg_ensemble_step", "mwdg_ensemble_run_to_time", "mwdg_ensemble_tune", "mwdg_ensemble_last_error",
 )
 
 
@@ -73,6 +75,12 @@ def lib(build: bool = True):
         "mwdg_read_fields": [vp, dp, dp, dp],
         "mwdg_read_fields_dev": [vp, vp, vp, vp],
         "mwdg_read_gauges": [vp, ip, C.c_int32, dp, dp, dp],
+        "mwdg_set_launch_shape": [vp, C.c_int32, C.c_int64],
+        "mwdg_get_launch_shape": [vp, ip, lp],
+        "mwdg_ensemble_create": [C.POINTER(C.c_void_p), C.c_int32, vp, C.POINTER(C.c_void_p)],
+        "mwdg_ensemble_step": [vp, C.c_int64],
+        "mwdg_ensemble_run_to_time": [vp, C.c_double, lp],
+        "mwdg_ensemble_tune": [vp, C.c_int32, lp],
         "mwdg_read_active": [vp, ip, ip, ip, dp, C.c_int64, lp],
         "mwdg_get_time": [vp, dp, lp],
         "mwdg_get_counters": [vp, lp, lp],
@@ -91,6 +99,10 @@ def lib(build: bool = True):
         f.restype = C.c_int
     L.mwdg_destroy.argtypes = [vp]
     L.mwdg_destroy.restype = None
+    L.mwdg_ensemble_destroy.argtypes = [vp]
+    L.mwdg_ensemble_destroy.restype = None
+    L.mwdg_ensemble_last_error.argtypes = [vp]
+    L.mwdg_ensemble_last_error.restype = C.c_char_p
     L.mwdg_last_error.argtypes = [vp]
     L.mwdg_last_error.restype = C.c_char_p
     L.mwdg_status_string.argtypes = [C.c_int]
@@ -299,6 +311,62 @@ class Solver:
         n = C.c_int64()
         self._ck(self._lib.mwdg_launch_count(self._h, C.byref(n)), "mwdg_launch_count")
         return n.value
+
+    def set_launch_shape(self, grid_leaves=0, coarse_nodes=0):
+        self._ck(self._lib.mwdg_set_launch_shape(self._h, int(grid_leaves), int(coarse_nodes)),
+                 "mwdg_set_launch_shape")
+
+    def launch_shape(self):
+        g, c = C.c_int32(), C.c_int64()
+        self._ck(self._lib.mwdg_get_launch_shape(self._h, C.byref(g), C.byref(c)), "mwdg_get_launch_shape")
+        return g.value, c.value
+
+
+class Ensemble:
+    """Members (Solver objects on one device) stepped together: one CUDA graph
+    per ensemble step with every member's step as a parallel branch."""
+
+    def __init__(self, members, stream=None):
+        self._lib = lib()
+        self.members = list(members)  # keeps them alive
+        n = len(self.members)
+        arr = (C.c_void_p * n)(*[m._h.value for m in self.members])
+        h = C.c_void_p()
+        st = self._lib.mwdg_ensemble_create(arr, n, None if stream is None else C.c_void_p(stream), C.byref(h))
+        if st != 0:
+            raise MwdgError(st, "mwdg_ensemble_create", self._lib.mwdg_status_string(st).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mwdg_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st, where):
+        if st != 0:
+            raise MwdgError(st, where, self._lib.mwdg_ensemble_last_error(self._h).decode())
+
+    def step(self, n=1):
+        self._ck(self._lib.mwdg_ensemble_step(self._h, int(n)), "mwdg_ensemble_step")
+
+    def run_to_time(self, t_end) -> int:
+        n = C.c_int64()
+        self._ck(self._lib.mwdg_ensemble_run_to_time(self._h, float(t_end), C.byref(n)),
+                 "mwdg_ensemble_run_to_time")
+        return n.value
+
+    def tune(self, steps=8):
+        """autotune every member's launch shape; returns (n, 2) (grid_leaves, coarse_nodes)"""
+        out = np.zeros(2 * len(self.members), np.int64)
+        self._ck(self._lib.mwdg_ensemble_tune(self._h, int(steps), out.ctypes.data_as(C.POINTER(C.c_int64))),
+                 "mwdg_ensemble_tune")
+        return out.reshape(-1, 2)
 
 
 def solver_from_problem(p, precision=F64, stream=None, **over) -> Solver:

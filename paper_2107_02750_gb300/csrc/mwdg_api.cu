@@ -52,6 +52,7 @@ struct mwdg_ctx {
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
   int graph_launches = 0;
+  int64_t generation = 0;   // bumped whenever the captured step becomes stale
   int static_eta = 0;   // static run with a free-surface initial state
   int64_t launches = 0;
   std::string err;
@@ -238,6 +239,7 @@ mwdg_status build_static_grid(mwdg_ctx *c, int is_eta_encoded) {
 void drop_graph(mwdg_ctx *c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
+  c->generation++;
 }
 
 // the kernels of one step: [adaptive: encode, flags, decode, compaction],
@@ -962,3 +964,305 @@ mwdg_status mwdg_launch_count(mwdg_ctx *c, int64_t *n) {
 const char *mwdg_last_error(const mwdg_ctx *c) { return c ? c->err.c_str() : "no context"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Launch shape and ensembles
+// ---------------------------------------------------------------------------
+mwdg_status mwdg_set_launch_shape(mwdg_ctx *c, int32_t grid_leaves, int64_t coarse_nodes) {
+  LIVE(c);
+  if (grid_leaves > 65535) return fail(c, MWDG_ERR_ARG, "grid_leaves above 65535");
+  if (grid_leaves > 0) c->grid_leaves = grid_leaves;
+  if (coarse_nodes > 0) c->g.coarse_nodes = coarse_nodes;
+  drop_graph(c);
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_get_launch_shape(mwdg_ctx *c, int32_t *grid_leaves, int64_t *coarse_nodes) {
+  LIVE(c);
+  if (grid_leaves) *grid_leaves = c->grid_leaves;
+  if (coarse_nodes) *coarse_nodes = c->g.coarse_nodes;
+  return MWDG_OK;
+}
+
+struct mwdg_ensemble {
+  std::vector<mwdg_ctx *> m;
+  cudaStream_t st = nullptr;          // the caller's stream: ensemble work is ordered on it
+  std::vector<cudaStream_t> br;       // one branch stream per member (used while capturing)
+  std::vector<cudaEvent_t> ev;        // per member: ordering and join events
+  cudaEvent_t fork = nullptr, done = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<int64_t> gen;           // member generations the graph was built from
+  std::vector<int> nk;                // kernels per member in one ensemble step
+  bool own_st = false;                // st created here (no caller stream)
+  std::string err;
+};
+
+namespace {
+
+mwdg_status efail(mwdg_ensemble *e, mwdg_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (e) e->err = buf;
+  return s;
+}
+
+#define ECK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return efail(e, MWDG_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                   __FILE__, __LINE__);                                                   \
+  } while (0)
+
+void ens_drop_graph(mwdg_ensemble *e) {
+  if (e->graph) cudaGraphExecDestroy(e->graph);
+  e->graph = nullptr;
+}
+
+// members ready to step (reductions of their current leaves), and ensemble
+// work ordered after each member's earlier work
+mwdg_status ens_begin(mwdg_ensemble *e) {
+  for (size_t k = 0; k < e->m.size(); k++) {
+    mwdg_ctx *c = e->m[k];
+    if (!c || c->failed) return efail(e, MWDG_ERR_STATE, "member %zu is in an error state", k);
+    if (!c->initial) return efail(e, MWDG_ERR_STATE, "member %zu has no initial state", k);
+    if (c->prof) return efail(e, MWDG_ERR_STATE, "member %zu has per-kernel timing on", k);
+    if (c->g.mode == MWDG_ADAPTIVE && !c->vmax_fresh) {
+      mwdg_status s = prime(c);
+      if (s) return efail(e, s, "member %zu: %s", k, c->err.c_str());
+    }
+    ECK(cudaEventRecord(e->ev[k], c->st));
+    ECK(cudaStreamWaitEvent(e->st, e->ev[k], 0));
+  }
+  return MWDG_OK;
+}
+
+// members' later work ordered after the ensemble work; step bookkeeping
+mwdg_status ens_end(mwdg_ensemble *e, int64_t graph_launches) {
+  ECK(cudaEventRecord(e->done, e->st));
+  for (mwdg_ctx *c : e->m) {
+    ECK(cudaStreamWaitEvent(c->st, e->done, 0));
+    if (graph_launches > 0) {
+      c->stepped = true;
+      c->encoded = false;
+      c->vmax_fresh = true;
+    }
+  }
+  return MWDG_OK;
+}
+
+// one ensemble step as a graph: fork, every member's step on its own branch
+// stream, join
+mwdg_status ens_graph(mwdg_ensemble *e) {
+  bool stale = !e->graph;
+  for (size_t k = 0; k < e->m.size() && !stale; k++) stale = e->gen[k] != e->m[k]->generation;
+  if (!stale) return MWDG_OK;
+  ens_drop_graph(e);
+  cudaGraph_t gr = nullptr;
+  ECK(cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaEventRecord(e->fork, e->st);
+  for (size_t k = 0; k < e->m.size() && err == cudaSuccess; k++) {
+    mwdg_ctx *c = e->m[k];
+    err = cudaStreamWaitEvent(e->br[k], e->fork, 0);
+    if (err != cudaSuccess) break;
+    cudaStream_t own = c->st;
+    c->st = e->br[k];
+    e->nk[k] = launch_step(c, 0);
+    c->st = own;
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaEventRecord(e->ev[k], e->br[k]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(e->st, e->ev[k], 0);
+  }
+  cudaError_t e1 = cudaStreamEndCapture(e->st, &gr);
+  if (err != cudaSuccess || e1 != cudaSuccess || !gr) {
+    if (gr) cudaGraphDestroy(gr);
+    return efail(e, MWDG_ERR_CUDA, "ensemble capture: %s",
+                 cudaGetErrorString(err != cudaSuccess ? err : e1));
+  }
+  cudaError_t e2 = cudaGraphInstantiate(&e->graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e2 != cudaSuccess) return efail(e, MWDG_ERR_CUDA, "ensemble graph: %s", cudaGetErrorString(e2));
+  for (size_t k = 0; k < e->m.size(); k++) e->gen[k] = e->m[k]->generation;
+  return MWDG_OK;
+}
+
+mwdg_status ens_launch(mwdg_ensemble *e, int64_t n) {
+  for (int64_t q = 0; q < n; q++) ECK(cudaGraphLaunch(e->graph, e->st));
+  for (size_t k = 0; k < e->m.size(); k++) e->m[k]->launches += (int64_t)e->nk[k] * n;
+  return MWDG_OK;
+}
+
+}  // namespace
+
+mwdg_status mwdg_ensemble_create(mwdg_ctx *const *members, int32_t n, void *cuda_stream, mwdg_ensemble **out) {
+  if (!members || !out || n < 1) return MWDG_ERR_ARG;
+  *out = nullptr;
+  for (int32_t a = 0; a < n; a++) {
+    if (!members[a]) return MWDG_ERR_ARG;
+    if (members[a]->failed || !members[a]->initial) return MWDG_ERR_STATE;
+    for (int32_t b = 0; b < a; b++)
+      if (members[a] == members[b]) return MWDG_ERR_ARG;
+  }
+  mwdg_ensemble *e = new mwdg_ensemble();
+  e->m.assign(members, members + n);
+  e->st = (cudaStream_t)cuda_stream;
+  e->gen.assign(n, -1);
+  e->nk.assign(n, 0);
+  bool ok = true;
+  if (!e->st) {  // a capturable stream of its own
+    ok = cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking) == cudaSuccess;
+    e->own_st = ok;
+  }
+  ok = ok && cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&e->done, cudaEventDisableTiming) == cudaSuccess;
+  for (int32_t k = 0; k < n && ok; k++) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    if (s) e->br.push_back(s);
+    if (ev) e->ev.push_back(ev);
+  }
+  if (!ok) {
+    mwdg_ensemble_destroy(e);
+    return MWDG_ERR_CUDA;
+  }
+  *out = e;
+  return MWDG_OK;
+}
+
+void mwdg_ensemble_destroy(mwdg_ensemble *e) {
+  if (!e) return;
+  if (e->st) cudaStreamSynchronize(e->st);
+  ens_drop_graph(e);
+  for (cudaStream_t s : e->br) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (cudaEvent_t ev : e->ev) cudaEventDestroy(ev);
+  if (e->fork) cudaEventDestroy(e->fork);
+  if (e->done) cudaEventDestroy(e->done);
+  if (e->own_st && e->st) cudaStreamDestroy(e->st);
+  delete e;
+}
+
+mwdg_status mwdg_ensemble_step(mwdg_ensemble *e, int64_t n) {
+  if (!e) return MWDG_ERR_ARG;
+  if (n < 0) return efail(e, MWDG_ERR_ARG, "negative step count");
+  mwdg_status s;
+  if ((s = ens_begin(e)) || (s = ens_graph(e)) || (s = ens_launch(e, n))) return s;
+  return ens_end(e, n);
+}
+
+mwdg_status mwdg_ensemble_run_to_time(mwdg_ensemble *e, double t_end, int64_t *graph_launches_out) {
+  if (!e) return MWDG_ERR_ARG;
+  if (std::isnan(t_end)) return efail(e, MWDG_ERR_ARG, "t_end is NaN");
+  mwdg_status s;
+  if ((s = ens_begin(e)) || (s = ens_graph(e))) return s;
+  const size_t nm = e->m.size();
+  for (mwdg_ctx *c : e->m) k_set_tend<<<1, 1, 0, e->st>>>(c->ctl, t_end);
+  ECK(cudaGetLastError());
+  std::vector<Ctl> h(nm);
+  auto read_all = [&]() -> mwdg_status {
+    for (size_t k = 0; k < nm; k++)
+      ECK(cudaMemcpyAsync(&h[k], e->m[k]->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, e->st));
+    ECK(cudaStreamSynchronize(e->st));
+    for (size_t k = 0; k < nm; k++)
+      if (h[k].nonfinite) {
+        e->m[k]->failed = true;
+        e->m[k]->err = "non-finite value in the solution";
+        return efail(e, MWDG_ERR_NONFINITE, "member %zu: non-finite value in the solution", k);
+      }
+    return MWDG_OK;
+  };
+  if ((s = read_all())) return s;
+  int64_t launched = 0;
+  int batch = 8;
+  for (;;) {
+    bool open = false;
+    long long before = 0;
+    for (size_t k = 0; k < nm; k++) {
+      open = open || h[k].t < t_end;
+      before += h[k].steps;
+    }
+    if (!open) break;
+    if ((s = ens_launch(e, batch))) return s;
+    launched += batch;
+    if ((s = read_all())) return s;
+    long long after = 0;
+    double left = 1.0;
+    for (size_t k = 0; k < nm; k++) {
+      after += h[k].steps;
+      if (h[k].t < t_end && h[k].dt > 0.0) left = std::max(left, (t_end - h[k].t) / h[k].dt);
+    }
+    if (after == before) break;  // every open member's dt reached zero
+    batch = (int)std::max(1.0, std::min(256.0, std::ceil(left * 1.05) + 1.0));
+  }
+  for (mwdg_ctx *c : e->m) k_set_tend<<<1, 1, 0, e->st>>>(c->ctl, 1e300);
+  ECK(cudaGetLastError());
+  if (graph_launches_out) *graph_launches_out = launched;
+  return ens_end(e, launched);
+}
+
+mwdg_status mwdg_ensemble_tune(mwdg_ensemble *e, int32_t steps, int64_t *chosen) {
+  if (!e) return MWDG_ERR_ARG;
+  if (steps < 1) return efail(e, MWDG_ERR_ARG, "steps must be positive");
+  static const int grids[] = {152, 304, 608, 1216};
+  static const long long coarse[] = {64, 256, 1024};
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  ECK(cudaEventCreate(&t0));
+  ECK(cudaEventCreate(&t1));
+  mwdg_status s = MWDG_OK;
+  for (size_t k = 0; k < e->m.size() && s == MWDG_OK; k++) {
+    mwdg_ctx *c = e->m[k];
+    std::vector<char> saved(state_bytes(c));
+    if ((s = mwdg_save_state(c, saved.data(), (int64_t)saved.size()))) break;
+    const int grid0 = c->grid_leaves;
+    const long long coarse0 = c->g.coarse_nodes;
+    const int grid_max = (int)std::max<long long>(1, std::min<long long>((c->g.P + 255) / 256, 152 * 8));
+    float best = 1e30f;
+    int bg = grid0;
+    long long bc = coarse0;
+    for (int gi : grids) {
+      const int gsz = std::min(gi, grid_max);
+      for (long long cn : coarse) {
+        if ((s = mwdg_set_launch_shape(c, gsz, cn))) break;
+        if ((s = queue_step(c))) break;  // warm-up (captures the step)
+        cudaEventRecord(t0, c->st);
+        for (int q = 0; q < steps && s == MWDG_OK; q++) s = queue_step(c);
+        cudaEventRecord(t1, c->st);
+        if (s || cudaEventSynchronize(t1) != cudaSuccess) {
+          if (!s) s = MWDG_ERR_CUDA;
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (ms < best) {
+          best = ms;
+          bg = gsz;
+          bc = cn;
+        }
+        if ((s = mwdg_load_state(c, saved.data(), (int64_t)saved.size()))) break;
+      }
+      if (s) break;
+    }
+    if (s) {
+      efail(e, s, "tuning member %zu: %s", k, c->err.c_str());
+      break;
+    }
+    if ((s = mwdg_set_launch_shape(c, bg, bc))) break;
+    if (chosen) {
+      chosen[2 * k] = bg;
+      chosen[2 * k + 1] = bc;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  ens_drop_graph(e);
+  return s;
+}
+
+const char *mwdg_ensemble_last_error(const mwdg_ensemble *e) { return e ? e->err.c_str() : "null ensemble"; }

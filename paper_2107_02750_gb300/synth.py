@@ -146,6 +146,25 @@ def valley(n: int = 1024, dx: float = 10.0, seed: int = 1, L: int = 10, relief: 
                    inflow_Q=np.array([0.0, peak_Q, 0.0, 0.0]), eps=eps, mode=mode, t_end=t_end)
 
 
+def ensemble(count: int = 64, seed: int = 4, base_seed: int = 1000, sides=(256, 512, 768, 1024),
+             n_range=(0.02, 0.06), q_scale=(0.5, 2.0), eps: float = 1e-3, dx: float = 10.0) -> list:
+    """Batched scenarios of uneven sizes: fractal valleys (as `valley`) with
+    sides drawn from `sides` (each M 2^L with M in {1, 3}), member k seeded
+    base_seed + k, Manning n ~ U(n_range) and the inflow peak scaled by
+    U(q_scale)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(count):
+        side = int(rng.choice(sides))
+        M = 3 if side % 3 == 0 else 1
+        L = int(np.log2(side // M))
+        nm = float(rng.uniform(*n_range))
+        qs = float(rng.uniform(*q_scale))
+        out.append(valley(n=side, dx=dx, seed=base_seed + k, L=L, n_manning=nm, peak_Q=400.0 * qs,
+                          eps=eps))
+    return out
+
+
 def urban(n: int = 2048, dx: float = 2.0, seed: int = 2, L: int = 11, relief: float = 1.0,
           block_min: float = 10.0, block_max: float = 40.0, block_height: float = 8.0,
           cover: float = 0.25, road_spacing: float = 100.0, road_width: float = 12.0,

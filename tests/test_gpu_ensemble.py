@@ -1,0 +1,100 @@
+"""Ensembles (batched scenarios of uneven sizes, one CUDA graph per ensemble
+step): every member ends exactly where it ends when stepped alone, through
+step counts, run_to_time, interleaved member calls and the launch-shape
+autotuner."""
+import numpy as np
+import pytest
+
+from paper_2107_02750_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _members(precisions, eps=1e-2, sides=(64, 96, 128, 192), count=4, seed=4):
+    import paper_2107_02750_gb300 as M
+    probs = S.ensemble(count=count, seed=seed, sides=sides, eps=eps)
+    return probs, [M.solver_from_problem(p, precision=precisions[k % len(precisions)])
+                   for k, p in enumerate(probs)]
+
+
+def _same(a, b, what):
+    la, ia, ja, ca = a.read_active()
+    lb, ib, jb, cb = b.read_active()
+    assert len(la) == len(lb), what
+    np.testing.assert_array_equal(la, lb)
+    np.testing.assert_array_equal(ia, ib)
+    np.testing.assert_array_equal(ja, jb)
+    np.testing.assert_array_equal(ca, cb, err_msg=what)
+    assert a.get_time() == b.get_time(), what
+
+
+def test_ensemble_run_to_time_equals_members_alone():
+    """Uneven sizes (64..192 cells a side, M in {1, 3}), both precisions,
+    adaptive grids: run to 40 s as one ensemble and one by one."""
+    import paper_2107_02750_gb300 as M
+    probs, ens_members = _members([M.F32, M.F64])
+    _, alone = _members([M.F32, M.F64])
+    e = M.Ensemble(ens_members)
+    launches = e.run_to_time(40.0)
+    assert launches > 0
+    for k, s in enumerate(alone):
+        s.run_to_time(40.0)
+        _same(ens_members[k], s, f"member {k}")
+        assert abs(ens_members[k].get_time()[0] - 40.0) < 1e-12
+    # a second leg continues from there
+    e.run_to_time(55.0)
+    for k, s in enumerate(alone):
+        s.run_to_time(55.0)
+        _same(ens_members[k], s, f"member {k}, second leg")
+
+
+def test_ensemble_steps_interleaved_with_member_calls():
+    import paper_2107_02750_gb300 as M
+    probs, ens_members = _members([M.F64], count=3)
+    _, alone = _members([M.F64], count=3)
+    e = M.Ensemble(ens_members)
+    e.step(5)
+    ens_members[1].run_steps(3)  # a member's own call between ensemble calls
+    e.step(2)
+    for k, s in enumerate(alone):
+        s.run_steps(5 + (3 if k == 1 else 0) + 2)
+        _same(ens_members[k], s, f"member {k}")
+    # a parameter change on a member rebuilds the ensemble graph
+    ens_members[0].set_rain(1e-4, 1e9)
+    alone[0].set_rain(1e-4, 1e9)
+    e.step(4)
+    for k, s in enumerate(alone):
+        s.run_steps(4)
+        _same(ens_members[k], s, f"member {k} after set_rain")
+
+
+def test_autotuner_keeps_results_and_state():
+    """The tuner times candidate launch shapes from a saved state, restores
+    it, and keeps the fastest; FP64 results are unchanged by the shape."""
+    import paper_2107_02750_gb300 as M
+    probs, ens_members = _members([M.F64], count=3)
+    _, alone = _members([M.F64], count=3)
+    for s in ens_members + alone:
+        s.run_steps(3)
+    e = M.Ensemble(ens_members)
+    chosen = e.tune(steps=3)
+    assert chosen.shape == (3, 2)
+    for k, s in enumerate(ens_members):
+        assert tuple(chosen[k]) == s.launch_shape()
+        assert 1 <= chosen[k, 0] <= 1216  # 152 x {1, 2, 4, 8}, capped by the member's size
+        assert chosen[k, 1] in (64, 256, 1024)
+        _same(s, alone[k], f"member {k} state after tuning")
+    e.run_to_time(30.0)
+    for k, s in enumerate(alone):
+        s.run_to_time(30.0)
+        _same(ens_members[k], s, f"member {k} after tuned run")
+
+
+def test_ensemble_rejects_bad_members():
+    import paper_2107_02750_gb300 as M
+    _, ms = _members([M.F64], count=2)
+    with pytest.raises(M.MwdgError):
+        M.Ensemble([ms[0], ms[0]])
+    fresh = M.Solver(M=1, N=1, L=4, dx=1.0, mode=M.ADAPTIVE)  # no initial state
+    with pytest.raises(M.MwdgError):
+        M.Ensemble([ms[1], fresh])
