@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="instead: the batched ensemble of this many seeded valleys (sides 256-1024)")
+    ap.add_argument("--no-tune", action="store_true", help="ensemble: keep the default launch shapes")
     return ap.parse_args()
 
 
@@ -378,8 +381,64 @@ def kernel_bytes_per_leaf(name, ts):
 TRAFFIC = {"dg2_update_stage2": 51_160_320 + 3_683_328}  # ncu: dram read + write, one launch at this workload
 
 
+def run_ensemble(args):
+    """Batched ensemble: seeded valleys of sides 256, 512, 768, 1024 (M 2^L,
+    M in {1, 3}), per-member Manning n and inflow scale, FP32 MWDG2 at
+    eps = 1e-3.  All members run to the spin-up time, the launch shapes are
+    autotuned (unless --no-tune), then K ensemble steps (one graph launch
+    each) are timed with CUDA events, bracketed by an L2 flush.  The same K
+    steps with the members queued one after another (each its own graph)
+    are timed for comparison."""
+    import torch
+    import paper_2107_02750_gb300 as M
+    from paper_2107_02750_gb300 import synth as S
+    probs = S.ensemble(count=args.ensemble)
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    members = [make_solver(p, M.F32, sptr) for p in probs]
+    ens = M.Ensemble(members, stream=sptr)
+    ens.run_to_time(args.spinup)
+    chosen = None if args.no_tune else ens.tune(steps=8).tolist()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        ens.step(args.warmup)
+        torch.cuda.synchronize()
+        u0 = sum(m.get_counters()[1] for m in members)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        flush.fill_(1.0)
+        ev[0][0].record(stream)
+        ens.step(args.steps)
+        ev[0][1].record(stream)
+        torch.cuda.synchronize()
+        u1 = sum(m.get_counters()[1] for m in members)
+        flush.fill_(2.0)
+        ev[1][0].record(stream)
+        for _ in range(args.steps):
+            for m in members:
+                m.run_steps(1)
+        ev[1][1].record(stream)
+        torch.cuda.synchronize()
+        u2 = sum(m.get_counters()[1] for m in members)
+    ms_ens = ev[0][0].elapsed_time(ev[0][1])
+    ms_seq = ev[1][0].elapsed_time(ev[1][1])
+    sides = [p.nx for p in probs]
+    return {"metric": "MWDG2 ensemble active-cell updates/s (batched scenarios, one graph per step)",
+            "value": (u1 - u0) / (ms_ens * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_ens / args.steps, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{len(probs)} seeded fractal valleys, sides {sorted(set(sides))} "
+                                   f"(total {sum(x * x for x in sides)} finest cells), eps=1e-3",
+                       "spinup_s": args.spinup, "tuned_shapes": chosen},
+            "sequential": {"value": (u2 - u1) / (ms_seq * 1e-3), "unit": UNIT,
+                           "ms_per_step": ms_seq / args.steps,
+                           "what": "the same steps with members queued one after another"}}
+
+
 def main():
     args = parse()
+    if args.ensemble > 0:
+        print(json.dumps(run_ensemble(args)))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
