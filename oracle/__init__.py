@@ -71,7 +71,7 @@ class Params(C.Structure):
         ("limiter", C.c_int32), ("bc", C.c_int32 * 4),
         ("inflow_edge", C.c_int32), ("inflow_c0", C.c_int32), ("inflow_c1", C.c_int32),
         ("rain_rate", C.c_double), ("rain_t_end", C.c_double),
-        ("iface_rule", C.c_int32),
+        ("iface_rule", C.c_int32), ("scheme", C.c_int32),
     ]
 
 
@@ -116,6 +116,8 @@ def lib():
         L.orc_filters.argtypes = [dp, dp]
         L.orc_encode_node.argtypes = [dp, dp, dp]
         L.orc_decode_node.argtypes = [dp, dp, dp]
+        L.orc_haar_encode.argtypes = [dp, dp, dp]
+        L.orc_haar_decode.argtypes = [C.c_double, dp, dp]
         _lib = L
     return _lib
 
@@ -160,6 +162,21 @@ def encode_node(children: np.ndarray):
     return sp, d
 
 
+def haar_encode(children: np.ndarray):
+    """Haar wavelets (HWFV1): four child averages -> (parent average, 3 details)."""
+    sc = _f64(children).reshape(4)
+    p, d = np.empty(1), np.empty(3)
+    lib().orc_haar_encode(_dp(sc), _dp(p), _dp(d))
+    return float(p[0]), d
+
+
+def haar_decode(parent: float, details: np.ndarray):
+    d = _f64(details)
+    out = np.empty(4)
+    lib().orc_haar_decode(float(parent), _dp(d), _dp(out))
+    return out
+
+
 def decode_node(parent: np.ndarray, details: np.ndarray):
     """Eq. 10 for one variable: -> children (4, 3)."""
     sp, d = _f64(parent), _f64(details)
@@ -178,7 +195,7 @@ class Sim:
     def __init__(self, *, M, N, L, R, mode=UNIFORM, eps=1e-3, cfl=0.33, g=9.80665,
                  h_dry=1e-3, dt_max=1.0, limiter=1, bc=(WALL, WALL, WALL, WALL),
                  inflow_edge=-1, inflow_c0=0, inflow_c1=-1, rain_rate=0.0, rain_t_end=0.0,
-                 iface_rule=0):
+                 iface_rule=0, scheme=0):
         p = Params()
         p.M, p.N, p.L, p.mode = M, N, L, mode
         p.R, p.eps, p.cfl, p.g, p.h_dry, p.dt_max = R, eps, cfl, g, h_dry, dt_max
@@ -188,6 +205,7 @@ class Sim:
         p.inflow_edge, p.inflow_c0, p.inflow_c1 = inflow_edge, inflow_c0, inflow_c1
         p.rain_rate, p.rain_t_end = rain_rate, rain_t_end
         p.iface_rule = iface_rule
+        p.scheme = scheme
         self.p = p
         self.nx, self.ny = M << L, N << L
         self._h = lib().orc_create(C.byref(p))

@@ -56,6 +56,8 @@ typedef struct {
   double rain_t_end;      /* s                                               */
   int32_t iface_rule;     /* static grids: 0 each side from its own view,    */
                           /* 1 coarse side takes the mean fine flux (reflux) */
+  int32_t scheme;         /* 0 DG2 (Sect. 2.1.1), 1 FV1 (Sect. 2.1.2); with  */
+                          /* the adaptive mode FV1 is HWFV1 (Sect. 2.3)     */
 } orc_params;
 
 typedef struct {
@@ -283,6 +285,25 @@ void orc_decode_node(const double *sp /*3*/, const double *d /*9 or NULL*/, doub
 /* The printed four-vertex form of Eq. 8a has a factor 1/2; the E/W and N/S  */
 /* forms on the same line require 1/4, which is used.                        */
 /* ------------------------------------------------------------------------ */
+/* Haar wavelets (HWFV1, Sect. 2.3): piecewise-constant children s_c (c =
+ * ix + 2 iy) -> parent average p = 1/4 sum s_c and three details from the
+ * orthonormal Haar transform (rows 1/2 (+-1, ...)): d_x (west-east),
+ * d_y (south-north), d_xy; decode s_c = p + 1/2 (sx d_x + sy d_y + sx sy d_xy)
+ * with sx, sy = -1 / +1 on the west / east and south / north children. */
+void orc_haar_encode(const double *sc /*4*/, double *p, double *d /*3*/) {
+  *p = 0.25 * (sc[0] + sc[1] + sc[2] + sc[3]);
+  d[0] = 0.5 * (-sc[0] + sc[1] - sc[2] + sc[3]);
+  d[1] = 0.5 * (-sc[0] - sc[1] + sc[2] + sc[3]);
+  d[2] = 0.5 * (sc[0] - sc[1] - sc[2] + sc[3]);
+}
+
+void orc_haar_decode(double p, const double *d /*3*/, double *sc /*4*/) {
+  for (int c = 0; c < 4; c++) {
+    double sx = (c & 1) ? 1.0 : -1.0, sy = (c & 2) ? 1.0 : -1.0;
+    sc[c] = p + 0.5 * (sx * d[0] + sy * d[1] + sx * sy * d[2]);
+  }
+}
+
 void orc_project(const double *vert, int nx, int ny, double *c0, double *c1x, double *c1y) {
   double s3 = S3();
   for (int j = 0; j < ny; j++)
@@ -381,6 +402,26 @@ void orc_load_dem(orc_sim *s, const double *vert) {
         s->dz[l][k] = dm / norm;
       }
   }
+  if (s->p.scheme == 1) {
+    /* FV1 sees the bed as one level per element (Eq. 6): the pyramid keeps
+     * the averages (the multiwavelet average is the children's mean) and
+     * drops the slopes.  The static grid keeps the multiwavelet details of
+     * the planar topography (Sect. 2.2); HWFV1 thresholds Haar details of
+     * the piecewise-constant bed (Sect. 2.3). */
+    if (s->p.mode == ORC_ADAPTIVE)
+      for (int l = L - 1; l >= 0; l--)
+        for (int j = 0; j < s->ny[l]; j++)
+          for (int i = 0; i < s->nx[l]; i++) {
+            double a[4], pa, d[3];
+            for (int c = 0; c < 4; c++) a[c] = s->z[l + 1][id(s, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1))];
+            orc_haar_encode(a, &pa, d);
+            s->dz[l][id(s, l, i, j)] = fmax(fabs(d[0]), fmax(fabs(d[1]), fabs(d[2]))) / norm;
+          }
+    for (int l = 0; l <= L; l++) {
+      size_t nl = nn(s, l);
+      for (size_t k = 0; k < nl; k++) s->z[l][nl + k] = s->z[l][2 * nl + k] = 0.0;
+    }
+  }
 }
 
 /* Manning n on the finest cells; coarser nodes hold the mean of their
@@ -418,6 +459,33 @@ static double inflow_Q(const orc_sim *s, double t) {
   return Qk + (Qk1 - Qk) * (t - tk) / (tk1 - tk);
 }
 
+/* encode/decode of one variable's node from its children (4 x 3 coefficients):
+ * DG2 multiwavelets (Eq. 9, 10), or for FV1 Haar wavelets on the averages
+ * (slopes stay zero; the details beyond the three Haar ones are zero) */
+static void encode_node_scheme(const orc_sim *s, const double *ch /*4x3*/, double *sp /*3*/, double *d /*9*/) {
+  if (s->p.scheme != 1) {
+    orc_encode_node(ch, sp, d);
+    return;
+  }
+  double a[4] = {ch[0], ch[3], ch[6], ch[9]};
+  for (int q = 0; q < 9; q++) d[q] = 0.0;
+  orc_haar_encode(a, &sp[0], d);
+  sp[1] = sp[2] = 0.0;
+}
+
+static void decode_node_scheme(const orc_sim *s, const double *sp, const double *d, double *ch /*4x3*/) {
+  if (s->p.scheme != 1) {
+    orc_decode_node(sp, d, ch);
+    return;
+  }
+  double a[4];
+  orc_haar_decode(sp[0], d, a);
+  for (int c = 0; c < 4; c++) {
+    ch[3 * c] = a[c];
+    ch[3 * c + 1] = ch[3 * c + 2] = 0.0;
+  }
+}
+
 /* full encode of the 9 flow coefficients from level `from` down to 0, all
  * nodes; details of every node are stored when D != NULL */
 static void encode_flow_all(orc_sim *s, double **X, int from, int store_details) {
@@ -432,7 +500,7 @@ static void encode_flow_all(orc_sim *s, double **X, int from, int store_details)
             size_t kc = id(s, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
             for (int m = 0; m < 3; m++) ch[3 * c + m] = X[l + 1][(3 * v + m) * nf + kc];
           }
-          orc_encode_node(ch, sp, d);
+          encode_node_scheme(s, ch, sp, d);
           for (int m = 0; m < 3; m++) X[l][(3 * v + m) * nl + k] = sp[m];
           if (store_details)
             for (int q = 0; q < 9; q++) s->D[l][(9 * v + q) * nl + k] = d[q];
@@ -468,6 +536,9 @@ void orc_load_initial(orc_sim *s, const double *hv, const double *qxv, const dou
       }
     }
   }
+  if (s->p.scheme == 1)  /* FV1: averages only (Eq. 5) */
+    for (size_t k = 0; k < n; k++)
+      for (int v = 0; v < 3; v++) U[(3 * v + 1) * n + k] = U[(3 * v + 2) * n + k] = 0.0;
   s->t = 0.0;
   s->steps = 0;
   s->n_clip = 0;
@@ -564,7 +635,7 @@ void orc_init_grid(orc_sim *s) {
             size_t kc = id(s, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
             for (int m = 0; m < 3; m++) ch[3 * c + m] = s->V[l + 1][m * nf + kc];
           }
-          orc_encode_node(ch, sp, d);
+          encode_node_scheme(s, ch, sp, d);
           for (int m = 0; m < 3; m++) s->V[l][m * nl + id(s, l, i, j)] = sp[m];
         }
     }
@@ -575,6 +646,7 @@ void orc_init_grid(orc_sim *s) {
         double *U = s->U[l];
         if (s->V[l][k] > s->z[l][k]) {
           for (int m = 0; m < 3; m++) U[m * n + k] = s->V[l][m * n + k] - s->z[l][m * n + k];
+          if (s->p.scheme == 1) U[n + k] = U[2 * n + k] = 0.0;
         } else {
           for (int m = 0; m < 9; m++) U[m * n + k] = 0.0;
         }
@@ -670,7 +742,7 @@ void orc_adapt(orc_sim *s) {
           double sp[3], d[9], ch[12];
           for (int m = 0; m < 3; m++) sp[m] = s->U[l][(3 * v + m) * n + k];
           for (int q = 0; q < 9; q++) d[q] = s->D[l][(9 * v + q) * n + k];
-          orc_decode_node(sp, d, ch);
+          decode_node_scheme(s, sp, d, ch);
           for (int c = 0; c < 4; c++) {
             size_t kc = id(s, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
             for (int m = 0; m < 3; m++) s->U[l + 1][(3 * v + m) * nf + kc] = ch[3 * c + m];
@@ -900,6 +972,10 @@ static void limit_leaf(const orc_sim *s, double *const *X, int l, int i, int j, 
   double hd = s->p.h_dry;
   for (int m = 0; m < 9; m++) w_st[m] = w_in[m];
   for (int m = 0; m < 3; m++) ze[m] = s->z[l][m * n + kc];
+  if (s->p.scheme == 1) {  /* FV1: first order, nothing to limit */
+    for (int m = 0; m < 9; m++) w_fx[m] = w_in[m];
+    return;
+  }
   double h0 = w_in[0];
   double eta0 = h0 + ze[0];
   int reduced = !(h0 > hd);
@@ -982,7 +1058,7 @@ static void build_view(orc_sim *s, double **X, double **Z) {
             size_t kc = id(s, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
             for (int m = 0; m < 3; m++) ch[3 * c + m] = s->V[l + 1][(3 * v + m) * nf + kc];
           }
-          orc_encode_node(ch, sp, d);
+          encode_node_scheme(s, ch, sp, d);
           for (int m = 0; m < 3; m++) s->V[l][(3 * v + m) * n + k] = sp[m];
         }
         double ch[12], sp[3], d[9];
@@ -990,7 +1066,7 @@ static void build_view(orc_sim *s, double **X, double **Z) {
           size_t kc = id(s, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
           for (int m = 0; m < 3; m++) ch[3 * c + m] = s->Vz[l + 1][m * nf + kc];
         }
-        orc_encode_node(ch, sp, d);
+        encode_node_scheme(s, ch, sp, d);
         for (int m = 0; m < 3; m++) s->Vz[l][m * n + k] = sp[m];
       }
   }
@@ -1200,6 +1276,7 @@ static void leaf_operator(const orc_sim *s, int l, int i, int j, const double *w
     double L1y = -(s3 / dxl) * (Fh[2][v] + Fh[3][v] - Gy[0][v] - Gy[1][v]);
     if (v == 1) L1x = L1x + -(2.0 * s3 * g / dxl) * w[1] * (w[1] + zc[1]);
     if (v == 2) L1y = L1y + -(2.0 * s3 * g / dxl) * w[2] * (w[2] + zc[2]);
+    if (s->p.scheme == 1) L1x = L1y = 0.0;  /* FV1: L0 only (Sect. 2.1.2) */
     Lo[3 * v + 0] = L0;
     Lo[3 * v + 1] = L1x;
     Lo[3 * v + 2] = L1y;
@@ -1273,9 +1350,16 @@ double orc_step(orc_sim *s, double t_end) {
       put9(s->U, s, l, k, w);
     }
   }
-  double b1 = rk_stage(s, s->U, s->Wn, NULL, s->Ui, dt, s->t);
-  double b2 = rk_stage(s, s->Ui, s->Wi, s->Wn, s->U, dt, s->t + dt);
-  double net_out = 0.5 * dt * (b1 + b2);
+  double net_out;
+  if (s->p.scheme == 1) {
+    /* FV1: forward Euler, Eq. 7 */
+    double b1 = rk_stage(s, s->U, s->Wn, NULL, s->U, dt, s->t);
+    net_out = dt * b1;
+  } else {
+    double b1 = rk_stage(s, s->U, s->Wn, NULL, s->Ui, dt, s->t);
+    double b2 = rk_stage(s, s->Ui, s->Wi, s->Wn, s->U, dt, s->t + dt);
+    net_out = 0.5 * dt * (b1 + b2);
+  }
   if (net_out >= 0.0) s->v_out += net_out;
   else s->v_in += -net_out;
   s->t = s->t + dt;

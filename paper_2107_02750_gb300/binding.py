@@ -11,6 +11,7 @@ from . import build as _build
 
 UNIFORM, STATIC, ADAPTIVE = 0, 1, 2
 F64, F32 = 0, 1
+DG2, FV1 = 0, 1
 WALL, OPEN = 0, 1
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 
@@ -31,7 +32,7 @@ class Params(C.Structure):
     _fields_ = [
         ("M", C.c_int32), ("N", C.c_int32), ("L", C.c_int32), ("mode", C.c_int32),
         ("precision", C.c_int32), ("limiter", C.c_int32), ("bc", C.c_int32 * 4),
-        ("iface_rule", C.c_int32), ("dx", C.c_double), ("eps", C.c_double), ("cfl", C.c_double), ("g", C.c_double),
+        ("iface_rule", C.c_int32), ("scheme", C.c_int32), ("dx", C.c_double), ("eps", C.c_double), ("cfl", C.c_double), ("g", C.c_double),
         ("h_dry", C.c_double), ("dt_max", C.c_double), ("cuda_stream", C.c_void_p),
     ]
 
@@ -127,12 +128,14 @@ class Solver:
     """One simulation context (mwdg_ctx) on the current CUDA device."""
 
     def __init__(self, *, M, N, L, dx, mode=UNIFORM, precision=F64, eps=1e-3, cfl=0.33,
-                 g=9.80665, h_dry=1e-3, dt_max=1.0, limiter=1, bc=(WALL,) * 4, iface_rule=0, stream=None):
+                 g=9.80665, h_dry=1e-3, dt_max=1.0, limiter=1, bc=(WALL,) * 4, iface_rule=0, scheme=0,
+                 stream=None):
         self._lib = lib()
         p = Params()
         self._lib.mwdg_params_default(C.byref(p))
         p.M, p.N, p.L, p.mode, p.precision, p.limiter = M, N, L, mode, precision, limiter
         p.iface_rule = iface_rule
+        p.scheme = scheme
         for k in range(4):
             p.bc[k] = bc[k]
         p.dx, p.eps, p.cfl, p.g, p.h_dry, p.dt_max = dx, eps, cfl, g, h_dry, dt_max
@@ -372,7 +375,8 @@ class Ensemble:
 def solver_from_problem(p, precision=F64, stream=None, **over) -> Solver:
     """A Solver loaded with a synthetic problem (paper_2107_02750_gb300.synth)."""
     kw = dict(M=p.M, N=p.N, L=p.L, dx=p.dx, mode=p.mode, precision=precision, eps=p.eps,
-              limiter=p.limiter, bc=p.bc, dt_max=p.dt_max, iface_rule=p.iface_rule, stream=stream)
+              limiter=p.limiter, bc=p.bc, dt_max=p.dt_max, iface_rule=p.iface_rule, scheme=p.scheme,
+              cfl=p.cfl, stream=stream)
     kw.update(over)
     s = Solver(**kw)
     s.load_dem(p.z_vert)

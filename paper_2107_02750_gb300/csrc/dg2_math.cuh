@@ -180,6 +180,21 @@ __device__ __forceinline__ T minmod3(T a, T b, T c) {
 //   d_V = sum_c (sx/4 s0 - sqrt3/4 s1x, sx/2 s1x, sx/2 s1y)
 //   d_D = sum_c (sx sy/2 s0, sx sy/2 s1x, sx sy/2 s1y)
 // ---------------------------------------------------------------------------
+// Haar wavelets (HWFV1): the parent average and the largest of the three
+// orthonormal Haar details (west-east, south-north, diagonal) of four child
+// averages (child c = ix + 2 iy)
+template <typename T>
+__device__ __forceinline__ T haar_avg(T s0, T s1, T s2, T s3) {
+  return T(0.25) * (((s0 + s1) + s2) + s3);
+}
+template <typename T>
+__device__ __forceinline__ T haar_detail_max(T s0, T s1, T s2, T s3) {
+  const T dx = T(0.5) * (((-s0 + s1) - s2) + s3);
+  const T dy = T(0.5) * (((-s0 - s1) + s2) + s3);
+  const T dd = T(0.5) * (((s0 - s1) - s2) + s3);
+  return tmax(tabs(dx), tmax(tabs(dy), tabs(dd)));
+}
+
 template <typename T>
 __device__ __forceinline__ void encode3(const T (&ch)[4][3], T sp[3]) {
   const T hs3 = T(0.5) * s3v<T>();

@@ -354,7 +354,8 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
       p->precision > MWDG_F32 || !(p->cfl > 0.0) || !(p->g > 0.0) || !(p->h_dry >= 0.0) ||
       !(p->dt_max > 0.0) || !std::isfinite(p->eps) || p->eps < 0.0 ||
       (p->iface_rule != MWDG_IFACE_PAPER && p->iface_rule != MWDG_IFACE_REFLUX) ||
-      (p->iface_rule == MWDG_IFACE_REFLUX && p->mode == MWDG_ADAPTIVE))
+      (p->iface_rule == MWDG_IFACE_REFLUX && p->mode == MWDG_ADAPTIVE) ||
+      (p->scheme != MWDG_DG2 && p->scheme != MWDG_FV1))
     return MWDG_ERR_ARG;
   mwdg_ctx *c = new mwdg_ctx();
   c->p = *p;
@@ -365,6 +366,7 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
   g.prec = p->precision;
   g.limiter = p->limiter;
   g.iface = p->iface_rule;
+  g.scheme = p->scheme;
   if (p->mode == MWDG_UNIFORM) {  // a uniform grid is the single level of an L = 0 hierarchy
     g.L = 0;
     g.M = p->M << p->L;

@@ -34,7 +34,7 @@ struct Ctl {
 
 // Geometry and parameters of the level hierarchy (passed by value).
 struct Geo {
-  int L, M, N, mode, limiter, prec, iface;
+  int L, M, N, mode, limiter, prec, iface, scheme;
   int nxl[MWDG_LMAX + 1], nyl[MWDG_LMAX + 1];
   long long off[MWDG_LMAX + 2];
   long long P;                 // nodes over all levels

@@ -199,6 +199,28 @@ __global__ void k_nm_level(Geo g, Ptrs<T> p, int l) {
 // projected depth (is_eta = 0) or free surface (is_eta = 1).  With is_eta,
 // wet elements (average free surface above the average bed) get h = eta - z,
 // others are dry.  The free-surface form stores free-surface slopes.
+// FV1 sees the bed as one level per element (Eq. 6): the pyramid keeps the
+// averages (the multiwavelet average is the children's mean) and drops the
+// slopes; HWFV1 (adaptive) thresholds Haar details of the piecewise-constant
+// bed (Sect. 2.3) instead of the multiwavelet ones
+template <typename T>
+__global__ void k_fv1_bed(Geo g, Ptrs<T> p) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= g.P) return;
+  const long long P = g.P;
+  int l, i, j;
+  node_of(g, k, l, i, j);
+  if (g.mode == MWDG_ADAPTIVE && l < g.L) {
+    T a[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) a[c] = p.Z[nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1))];
+    const double norm = fmax(1.0, __longlong_as_double((long long)p.ctl->vmax[0]));
+    p.DZ[k] = (double)haar_detail_max(a[0], a[1], a[2], a[3]) / norm;
+  }
+  p.Z[P + k] = T(0);
+  p.Z[2 * P + k] = T(0);
+}
+
 template <typename T>
 __global__ void k_initial_finest(Geo g, Ptrs<T> p, int is_eta) {
   const int L = g.L;
@@ -224,6 +246,8 @@ __global__ void k_initial_finest(Geo g, Ptrs<T> p, int is_eta) {
       for (int m = 0; m < 9; m++) U[m * P + k] = T(0);
     }
   }
+  if (g.scheme == MWDG_FV1)  // averages only (Eq. 5); the bed slopes are zero
+    for (int v = 0; v < 3; v++) U[(3 * v + 1) * P + k] = U[(3 * v + 2) * P + k] = T(0);
 }
 
 // dense Eq. 9 of `ncomp` components of X from level l+1 to level l; with a
@@ -245,8 +269,13 @@ __global__ void k_encode_dense(Geo g, T *X, int ncomp, int l, const T *Zb) {
       for (int m = 0; m < 3; m++) ch[c][m] = X[(3 * v + m) * P + kc];
       if (Zb && v == 0) slopes_to_h(ch[c][1], ch[c][2], Zb[P + kc], Zb[2 * P + kc]);
     }
-    encode3(ch, sp);
-    if (Zb && v == 0) slopes_from_h(sp[1], sp[2], Zb[P + k], Zb[2 * P + k]);
+    if (g.scheme == MWDG_FV1) {  // Haar: the average, no slopes
+      sp[0] = haar_avg(ch[0][0], ch[1][0], ch[2][0], ch[3][0]);
+      sp[1] = sp[2] = T(0);
+    } else {
+      encode3(ch, sp);
+      if (Zb && v == 0) slopes_from_h(sp[1], sp[2], Zb[P + k], Zb[2 * P + k]);
+    }
 #pragma unroll
     for (int m = 0; m < 3; m++) X[(3 * v + m) * P + k] = sp[m];
   }
@@ -816,13 +845,45 @@ __device__ __forceinline__ bool ge_nonneg(double a, double b) {
   return __double_as_longlong(a) >= __double_as_longlong(b);
 }
 
+// Eq. 9 encode of a refined node from its children's stored coefficients
+// ch[v][c][m] and bed slopes zc[c]; the node's stored coefficients go to
+// out; true when a normalised flow detail is significant
+template <typename T>
+__device__ __forceinline__ bool encode_sig(T (&ch)[3][4][3], const T (&zc)[4][2], T zp1, T zp2,
+                                           const double (&mx)[3], const float (&thr)[3], double eps,
+                                           bool fv1, T (&out)[9]) {
+  bool sig = false;
+  if (fv1) {  // HWFV1: Haar average and details of the child averages
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+      out[3 * v] = haar_avg(ch[v][0][0], ch[v][1][0], ch[v][2][0], ch[v][3][0]);
+      out[3 * v + 1] = out[3 * v + 2] = T(0);
+      sig = sig | detail_significant<T>(haar_detail_max(ch[v][0][0], ch[v][1][0], ch[v][2][0], ch[v][3][0]),
+                                         mx[v], thr[v], eps);
+    }
+    return sig;
+  }
+#pragma unroll
+  for (int c = 0; c < 4; c++) slopes_to_h(ch[0][c][1], ch[0][c][2], zc[c][0], zc[c][1]);
+#pragma unroll
+  for (int v = 0; v < 3; v++) {
+    T sp[3];
+    encode3(ch[v], sp);
+    if (v == 0) slopes_from_h(sp[1], sp[2], zp1, zp2);
+#pragma unroll
+    for (int m = 0; m < 3; m++) out[3 * v + m] = sp[m];
+    sig = sig | detail_significant<T>(detail_max3(ch[v]), mx[v], thr[v], eps);
+  }
+  return sig;
+}
+
 // MWDG2 encode of one node of level l (Sect. 2.3): a refined node gets the
 // scale coefficients of its children (Eq. 9) and is flagged when its largest
 // normalised flow or topography detail reaches epsilon; other nodes carry no
 // flow details, so only their topography detail counts.  SPEC: the
 // children's coefficients are read together with the node's kind (one
 // memory round trip; used on the small coarsest levels).
-template <bool SPEC, typename T>
+template <bool SPEC, bool FV1, typename T>
 __device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
   const long long P = g.P, k = nid(g, l, i, j);
   const uint8_t kd = p.kind[k];
@@ -841,19 +902,17 @@ __device__ __forceinline__ void encode_flag_node(const Geo &g, const Ptrs<T> &p,
     }
   }
   if (kd == K_SIG) {
-    const T zp1 = p.Z[P + k], zp2 = p.Z[2 * P + k];
-#pragma unroll
-    for (int c = 0; c < 4; c++) slopes_to_h(ch[0][c][1], ch[0][c][2], zc[c][0], zc[c][1]);
+    double mx[3];
+    float thr[3];
 #pragma unroll
     for (int v = 0; v < 3; v++) {
-      T sp[3];
-      encode3(ch[v], sp);
-      if (v == 0) slopes_from_h(sp[1], sp[2], zp1, zp2);
-#pragma unroll
-      for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sp[m];
-      const double mx = __longlong_as_double((long long)p.ctl->vmax[v]);
-      sig = detail_significant<T>(detail_max3(ch[v]), mx, float_at_or_above(g.eps * fmax(1.0, mx)), g.eps) || sig;
+      mx[v] = __longlong_as_double((long long)p.ctl->vmax[v]);
+      thr[v] = float_at_or_above(g.eps * fmax(1.0, mx[v]));
     }
+    T out[9];
+    sig = encode_sig(ch, zc, p.Z[P + k], p.Z[2 * P + k], mx, thr, g.eps, FV1, out) || sig;
+#pragma unroll
+    for (int m = 0; m < 9; m++) p.U[m * P + k] = out[m];
   }
   p.flag[k] = (uint8_t)sig;
 }
@@ -882,28 +941,6 @@ __device__ __forceinline__ uint8_t regular_flag(const Geo &g, const Ptrs<T> &p, 
 // the same in every block of a launch
 #define ADAPT_LIVE(p) (!ge_nonneg((p).ctl->t, (p).ctl->t_end))
 
-// Eq. 9 encode of a refined node from its children's stored coefficients
-// ch[v][c][m] and bed slopes zc[c]; the node's stored coefficients go to
-// out; true when a normalised flow detail is significant
-template <typename T>
-__device__ __forceinline__ bool encode_sig(T (&ch)[3][4][3], const T (&zc)[4][2], T zp1, T zp2,
-                                           const double (&mx)[3], const float (&thr)[3], double eps,
-                                           T (&out)[9]) {
-#pragma unroll
-  for (int c = 0; c < 4; c++) slopes_to_h(ch[0][c][1], ch[0][c][2], zc[c][0], zc[c][1]);
-  bool sig = false;
-#pragma unroll
-  for (int v = 0; v < 3; v++) {
-    T sp[3];
-    encode3(ch[v], sp);
-    if (v == 0) slopes_from_h(sp[1], sp[2], zp1, zp2);
-#pragma unroll
-    for (int m = 0; m < 3; m++) out[3 * v + m] = sp[m];
-    sig = sig | detail_significant<T>(detail_max3(ch[v]), mx[v], thr[v], eps);
-  }
-  return sig;
-}
-
 template <typename T>
 struct SigStage {
   T u[MT_NODES][9];     // stored coefficients (leaves: own; refined: encoded)
@@ -916,7 +953,7 @@ struct SigStage {
 
 // encode + significance of one tile (CG: the children of its finest level
 // were written by other blocks of this launch)
-template <bool CG, typename T>
+template <bool CG, bool FV1, typename T>
 __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const Tile &tl, SigStage<T> &sh) {
   const long long P = g.P;
   if (threadIdx.x < 3) {
@@ -981,7 +1018,7 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
         zc[c][0] = p.Z[P + kc];
         zc[c][1] = p.Z[2 * P + kc];
       }
-      sig = encode_sig(ch, zc, zs[0][0], zs[0][1], mx, thr, g.eps, out) || sig;
+      sig = encode_sig(ch, zc, zs[0][0], zs[0][1], mx, thr, g.eps, FV1, out) || sig;
 #pragma unroll
       for (int m = 0; m < 9; m++) {
         p.U[m * P + kk[0]] = out[m];
@@ -1014,7 +1051,7 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
         zc[c][0] = sh.z[cs][0];
         zc[c][1] = sh.z[cs][1];
       }
-      sig = encode_sig(ch, zc, sh.z[slot][0], sh.z[slot][1], mx, thr, g.eps, out) || sig;
+      sig = encode_sig(ch, zc, sh.z[slot][0], sh.z[slot][1], mx, thr, g.eps, FV1, out) || sig;
 #pragma unroll
       for (int m = 0; m < 9; m++) {
         p.U[m * P + k] = out[m];
@@ -1027,19 +1064,19 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
 
 // encode + significance flags: levels ltop..ltop-nlev+1 in tiles, then
 // (tail >= 0) levels tail..0 in the last block
-template <typename T>
+template <typename T, bool FV1>
 __global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_sig(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
   __shared__ SigStage<T> sh;
   if (!ADAPT_LIVE(p)) return;
-  if (nlev > 0) sig_tile<false>(g, p, tile_of_block(g, ltop, nlev), sh);
+  if (nlev > 0) sig_tile<false, FV1>(g, p, tile_of_block(g, ltop, nlev), sh);
   if (tail < 0 || !last_block(&p.ctl->ticket)) return;
   if (tail_is_tile(g, tail)) {
-    sig_tile<true>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
+    sig_tile<true, FV1>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
     return;
   }
   for (int l = tail; l >= 0; l--) {
     const int n = g.nxl[l] * g.nyl[l];
-    for (int r = threadIdx.x; r < n; r += blockDim.x) encode_flag_node<true>(g, p, l, r % g.nxl[l], r / g.nxl[l]);
+    for (int r = threadIdx.x; r < n; r += blockDim.x) encode_flag_node<true, FV1>(g, p, l, r % g.nxl[l], r / g.nxl[l]);
     __syncthreads();
   }
 }
@@ -1280,11 +1317,12 @@ static __global__ void k_begin_step(Geo g, Ctl *c, const int *nleaf) { begin_ste
 
 // end of a step: mass budget, time and step count (run once, by the last
 // block of the stage-2 update to finish)
-__device__ __forceinline__ void end_step(const Geo &g, Ctl *c) {
+// (euler: one stage, Eq. 7, whose boundary fluxes are in bnd[0])
+__device__ __forceinline__ void end_step(const Geo &g, Ctl *c, bool euler) {
   double dt = c->dt;
   if (!(dt > 0.0)) return;
   double b0 = atomicAdd(&c->bnd[0], 0.0), b1 = atomicAdd(&c->bnd[1], 0.0);
-  double net = 0.5 * dt * (b0 + b1);
+  double net = euler ? dt * b0 : 0.5 * dt * (b0 + b1);
   if (net >= 0.0) c->v_out += net;
   else c->v_in += -net;
   if (c->t < g.rain_t_end && g.rain_rate > 0.0) c->v_rain += g.rain_rate * dt * g.area;
@@ -1317,7 +1355,7 @@ __device__ __forceinline__ T friction_factor(T h0, T qx0, T qy0, T nm, T dt, T g
 // With FRIC (stage 1), the stage input is U after rain and friction, which
 // are applied here to the leaf and, for the limiter, to its neighbours'
 // averages (both are pointwise, so every leaf sees the same values).
-template <typename T, bool FRIC>
+template <typename T, bool FRIC, bool FV1>
 __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   const long long P = g.P;
   const T hd = geo_hd<T>(g), s3 = s3v<T>(), gg = geo_g<T>(g);
@@ -1342,6 +1380,18 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
 #pragma unroll
         for (int m = 3; m < 9; m++) w[m] = T(0);
       }
+    }
+    if (FV1) {  // first order: nothing to limit
+      T rec[12];
+#pragma unroll
+      for (int m = 0; m < 9; m++) {
+        Wst[m * P + k] = w[m];
+        rec[m] = w[m];
+      }
+#pragma unroll
+      for (int m = 0; m < 3; m++) rec[9 + m] = zp[m];
+      store_rec(p.FZ, k, rec);
+      continue;
     }
     const T h0 = w[0];
     const T eta0 = h0 + zp[0];
@@ -1445,7 +1495,15 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
 // local encoding (Eq. 9) of the flux view and its beds onto a refined node
 // (MWDG2 interfaces, Sect. 2.3) from its children's records rc[c]
 template <typename T>
-__device__ __forceinline__ void encode_view_rec(const T (&rc)[4][12], T (&rec)[12]) {
+__device__ __forceinline__ void encode_view_rec(const T (&rc)[4][12], T (&rec)[12], bool fv1) {
+  if (fv1) {  // HWFV1: averages of the children (Haar), no slopes
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      rec[3 * q] = haar_avg(rc[0][3 * q], rc[1][3 * q], rc[2][3 * q], rc[3][3 * q]);
+      rec[3 * q + 1] = rec[3 * q + 2] = T(0);
+    }
+    return;
+  }
   T zc[4][3], zpar[3];
 #pragma unroll
   for (int c = 0; c < 4; c++)
@@ -1472,7 +1530,7 @@ __device__ __forceinline__ void encode_view_rec(const T (&rc)[4][12], T (&rec)[1
 
 // one node, records read through L2 together with its kind (coarsest
 // levels that do not fit one tile)
-template <typename T>
+template <bool FV1, typename T>
 __device__ __forceinline__ void encode_view_node(const Geo &g, const Ptrs<T> &p, int l, int i, int j) {
   const long long k = nid(g, l, i, j);
   const uint8_t kd = p.kind[k];
@@ -1484,7 +1542,7 @@ __device__ __forceinline__ void encode_view_node(const Geo &g, const Ptrs<T> &p,
     for (int m = 0; m < 12; m++) rc[c][m] = __ldcg(&p.FZ[12 * kc + m]);
   }
   if (kd != K_SIG) return;
-  encode_view_rec(rc, rec);
+  encode_view_rec(rc, rec, FV1);
   store_rec(p.FZ, k, rec);
 }
 
@@ -1494,7 +1552,7 @@ struct ViewStage {
   uint8_t kind[MT_NODES];
 };
 
-template <bool CG, typename T>
+template <bool CG, bool FV1, typename T>
 __device__ __forceinline__ void view_tile(const Geo &g, const Ptrs<T> &p, const Tile &tl, ViewStage<T> &sh) {
   int sl[2];
   long long kk[2];
@@ -1527,7 +1585,7 @@ __device__ __forceinline__ void view_tile(const Geo &g, const Ptrs<T> &p, const 
         load_rec(p.FZ, kc, rc[c]);
       }
     }
-    encode_view_rec(rc, rec);
+    encode_view_rec(rc, rec, FV1);
     store_rec(p.FZ, kk[0], rec);
 #pragma unroll
     for (int m = 0; m < 12; m++) sh.r[sl[0]][m] = rec[m];
@@ -1547,7 +1605,7 @@ __device__ __forceinline__ void view_tile(const Geo &g, const Ptrs<T> &p, const 
 #pragma unroll
       for (int m = 0; m < 12; m++) rc[c][m] = sh.r[cs][m];
     }
-    encode_view_rec(rc, rec);
+    encode_view_rec(rc, rec, FV1);
     store_rec(p.FZ, nid(g, tl.ltop - s, i, j), rec);
 #pragma unroll
     for (int m = 0; m < 12; m++) sh.r[slot][m] = rec[m];
@@ -1555,18 +1613,18 @@ __device__ __forceinline__ void view_tile(const Geo &g, const Ptrs<T> &p, const 
 }
 
 // flux-view encode of the refined nodes, chunked as the MRA passes
-template <typename T>
+template <typename T, bool FV1>
 __global__ void __launch_bounds__(TPB) k_view_tiles(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
   __shared__ ViewStage<T> sh;
-  if (nlev > 0) view_tile<false>(g, p, tile_of_block(g, ltop, nlev), sh);
+  if (nlev > 0) view_tile<false, FV1>(g, p, tile_of_block(g, ltop, nlev), sh);
   if (tail < 0 || !last_block(&p.ctl->ticket)) return;
   if (tail_is_tile(g, tail)) {
-    view_tile<true>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
+    view_tile<true, FV1>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
     return;
   }
   for (int l = tail; l >= 0; l--) {
     const int n = g.nxl[l] * g.nyl[l];
-    for (int r = threadIdx.x; r < n; r += blockDim.x) encode_view_node(g, p, l, r % g.nxl[l], r / g.nxl[l]);
+    for (int r = threadIdx.x; r < n; r += blockDim.x) encode_view_node<FV1>(g, p, l, r % g.nxl[l], r / g.nxl[l]);
     __syncthreads();
   }
 }
@@ -1872,8 +1930,9 @@ __device__ __forceinline__ void finish_var(const Geo &g, const Ptrs<T> &p, int v
   T L1y = -(s3 / dxl) * (Fv[2] + Fv[3] - Gy0 - Gy1);
   if (v == 1) L1x = L1x + -(T(2) * s3 * gg / dxl) * h1x * e1x;
   if (v == 2) L1y = L1y + -(T(2) * s3 * gg / dxl) * h1y * e1y;
+  if (STAGE == 3) L1x = L1y = T(0);  // FV1 (its only stage): L0 only (Sect. 2.1.2)
   const long long b0 = (long long)(3 * v) * P + k;
-  if (STAGE == 1) {
+  if (STAGE == 1 || STAGE == 3) {
     o0 = Wst[b0] + dt * L0;
     o1 = Wst[b0 + P] + dt * L1x;
     o2 = Wst[b0 + 2 * P] + dt * L1y;
@@ -1931,7 +1990,8 @@ __device__ __forceinline__ void next_step_reduce(const Geo &g, const Ptrs<T> &p,
   }
 }
 
-// One RK2 stage on every leaf (Eq. 4a for STAGE 1, Eq. 4b for STAGE 2):
+// One RK2 stage on every leaf (Eq. 4a for STAGE 1, Eq. 4b for STAGE 2; STAGE
+// 3 is FV1's single forward-Euler stage, Eq. 7, which also ends the step):
 // the DG2 operator L = [L0, L1x, L1y] from the flux view (interface fluxes
 // of the revised limits by HLL, bed source with the revised interface beds,
 // two-point interface rule for the slope volume integrals with the bed
@@ -2007,7 +2067,7 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
       post_var<T>(g, p, v, k, l, h0n, o[v][0], o[v][1], o[v][2], ncl, csum, bad);
       store_var(P, v, k, Out, o[v][0], o[v][1], o[v][2]);
     }
-    if (STAGE == 2) next_step_reduce<T>(g, p, l, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
+    if (STAGE >= 2) next_step_reduce<T>(g, p, l, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
   }
   if (bad) p.ctl->nonfinite = 1;
   // block sums in the coefficient type, one FP64 conversion and atomic per
@@ -2023,13 +2083,13 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
       atomicAdd(&p.ctl->v_clip, csum);
     }
   }
-  if (STAGE == 2 && g.mode == MWDG_ADAPTIVE)
+  if (STAGE >= 2 && g.mode == MWDG_ADAPTIVE)
     for (int o = 16; o > 0; o >>= 1) {
       m0 = tmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
       m1 = tmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
       m2 = tmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
     }
-  if (STAGE == 2 && g.mode != MWDG_ADAPTIVE)
+  if (STAGE >= 2 && g.mode != MWDG_ADAPTIVE)
     for (int o = 16; o > 0; o >>= 1) best = tmin(best, __shfl_xor_sync(0xffffffffu, best, o));
   __shared__ T red[5][TPB / 32];
   const int wid = threadIdx.x >> 5;
@@ -2050,8 +2110,8 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
       r2 = tmax(r2, red[3][w]);
       r3 = tmin(r3, red[4][w]);
     }
-    if (b != T(0)) atomicAdd(&p.ctl->bnd[STAGE - 1], (double)b);
-    if (STAGE == 2) {
+    if (b != T(0)) atomicAdd(&p.ctl->bnd[STAGE == 2 ? 1 : 0], (double)b);
+    if (STAGE >= 2) {
       if (g.mode == MWDG_ADAPTIVE) {
         atomic_max_pos(&p.ctl->vmax[0], (double)r0);
         atomic_max_pos(&p.ctl->vmax[1], (double)r1);
@@ -2061,7 +2121,7 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
       }
     }
   }
-  if (STAGE == 2) {
+  if (STAGE >= 2) {
     // the last block to finish closes the step (no waiting: each block takes
     // a ticket after its own atomics are visible)
     if (threadIdx.x == 0) __threadfence();
@@ -2071,7 +2131,7 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
     __syncthreads();
     if (last && threadIdx.x == 0) {
       __threadfence();
-      end_step(g, p.ctl);
+      end_step(g, p.ctl, STAGE == 3);
     }
   }
 }
@@ -2218,6 +2278,10 @@ int Launch<T>::load_dem_pyramid(const Geo &g, const Ptrs<T> &p, cudaStream_t st)
   k_zmax<T><<<152 * 4, TPB, 0, st>>>(g, p);
   n++;
   for (int l = g.L - 1; l >= 0; l--, n++) k_encode_z<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
+  if (g.scheme == MWDG_FV1) {
+    k_fv1_bed<T><<<nblk(g.P), TPB, 0, st>>>(g, p);
+    n++;
+  }
   return n;
 }
 
@@ -2333,7 +2397,8 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
   // bottom-up encode + significance
   n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
     MARK(KC_ENCODE);
-    k_mra_sig<T><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
+    if (g.scheme == MWDG_FV1) k_mra_sig<T, true><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
+    else k_mra_sig<T, false><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
   });
   if (encode_only) return n;
   // prediction + closure
@@ -2378,18 +2443,25 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
     k_begin_step<<<1, 1, 0, st>>>(g, p.ctl, p.nleaf);
     n++;
   }
-  for (int stage = 1; stage <= 2; stage++) {
+  const int stages = (g.scheme == MWDG_FV1) ? 1 : 2;  // FV1: forward Euler (Eq. 7)
+  for (int stage = 1; stage <= stages; stage++) {
     MARK(KC_LIMIT);
-    if (stage == 1) k_leaf_limit<T, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
-    else k_leaf_limit<T, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
+    if (stages == 1) k_leaf_limit<T, true, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+    else if (stage == 1) k_leaf_limit<T, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+    else k_leaf_limit<T, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
     n++;
     if (view)
       n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
         MARK(KC_VIEW);
-        k_view_tiles<T><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
+        if (g.scheme == MWDG_FV1) k_view_tiles<T, true><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
+        else k_view_tiles<T, false><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
       });
     const bool reflux = (g.mode == MWDG_STATIC && g.iface == MWDG_IFACE_REFLUX);
-    if (stage == 1) {
+    if (stages == 1) {
+      MARK(KC_UPDATE2);
+      if (reflux) k_leaf_update<T, 3, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U);
+      else k_leaf_update<T, 3, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U);
+    } else if (stage == 1) {
       MARK(KC_UPDATE1);
       if (reflux) k_leaf_update<T, 1, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui);
       else k_leaf_update<T, 1, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui);

@@ -62,6 +62,8 @@ class Problem:
     limiter: int = 1
     dt_max: float = 1.0
     iface_rule: int = 0                 # static grids: 0 paper rule, 1 reflux
+    scheme: int = 0                     # 0 DG2, 1 FV1 (adaptive: HWFV1)
+    cfl: float = 0.33                   # Courant number (DG2 0.33, FV1 0.5)
 
     @property
     def nx(self) -> int:
@@ -257,6 +259,12 @@ def dam_break_strip(nx: int = 256, ny: int = 4, dx: float = 0.5, h_left: float =
     M, N = nx >> L, ny >> L
     return Problem("dam_break_strip", M, N, L, dx, zeros.copy(), h, zeros.copy(), zeros.copy(),
                    n_manning=0.0, limiter=1)
+
+
+def fv1(p: Problem) -> Problem:
+    """The same problem solved by FV1 (Sect. 2.1.2; adaptive: HWFV1), at its
+    Courant number 0.5."""
+    return replace(p, scheme=1, cfl=0.5)
 
 
 def crop(p: Problem, i0: int, j0: int, nx: int, ny: int, L: int) -> Problem:

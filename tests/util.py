@@ -9,7 +9,7 @@ def oracle_sim(p, **over):
     kw = dict(M=p.M, N=p.N, L=p.L, R=p.dx, mode=p.mode, eps=p.eps, bc=p.bc,
               inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1,
               rain_rate=p.rain_rate, rain_t_end=p.rain_t_end, limiter=p.limiter,
-              dt_max=p.dt_max, iface_rule=p.iface_rule)
+              dt_max=p.dt_max, iface_rule=p.iface_rule, scheme=p.scheme, cfl=p.cfl)
     kw.update(over)
     s = O.Sim(**kw)
     s.load_dem(p.z_vert)
