@@ -71,8 +71,12 @@ enum { MWDG_IFACE_PAPER = 0, MWDG_IFACE_REFLUX = 1 };
  * constant, forward Euler, Eq. 5-7, Sect. 2.1.2; Courant number 0.5).  On an
  * adaptive grid FV1 is HWFV1: the MRA uses Haar wavelets on the averages
  * (Sect. 2.3); a static FV1 grid comes from the multiwavelet MRA of the
- * planar topography like DG2's (Sect. 2.2). */
-enum { MWDG_DG2 = 0, MWDG_FV1 = 1 };
+ * planar topography like DG2's (Sect. 2.2).  ACC is the local inertial
+ * solver (Sect. 2.1.3; Courant number 0.7) on uniform and static graded
+ * grids: depth per element, a discharge per interface with semi-implicit
+ * Manning resistance, the finer half-face discharges summed on a coarser
+ * element (Sect. 2.2.1); open edges carry the discharge through. */
+enum { MWDG_DG2 = 0, MWDG_FV1 = 1, MWDG_ACC = 2 };
 #define MWDG_LMAX 15
 
 typedef struct {
@@ -82,7 +86,7 @@ typedef struct {
   int32_t limiter;     /* 0 off, 1 minmod slope limiter                     */
   int32_t bc[4];       /* per edge (west, east, south, north): wall / open  */
   int32_t iface_rule;  /* static grids: MWDG_IFACE_PAPER or MWDG_IFACE_REFLUX */
-  int32_t scheme;      /* MWDG_DG2 or MWDG_FV1 (cfl: 0.33 and 0.5)          */
+  int32_t scheme;      /* MWDG_DG2, MWDG_FV1, MWDG_ACC (cfl 0.33, 0.5, 0.7) */
   double dx;           /* finest resolution R (m)                           */
   double eps;          /* MRA threshold (Sect. 2.2; 1e-3 recommended)      */
   double cfl;          /* Courant number (0.33 for DG2, Sect. 2.1.1)        */

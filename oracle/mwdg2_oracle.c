@@ -56,8 +56,9 @@ typedef struct {
   double rain_t_end;      /* s                                               */
   int32_t iface_rule;     /* static grids: 0 each side from its own view,    */
                           /* 1 coarse side takes the mean fine flux (reflux) */
-  int32_t scheme;         /* 0 DG2 (Sect. 2.1.1), 1 FV1 (Sect. 2.1.2); with  */
-                          /* the adaptive mode FV1 is HWFV1 (Sect. 2.3)     */
+  int32_t scheme;         /* 0 DG2 (Sect. 2.1.1), 1 FV1 (Sect. 2.1.2; with   */
+                          /* the adaptive mode HWFV1, Sect. 2.3), 2 ACC      */
+                          /* (Sect. 2.1.3; uniform and static grids)         */
 } orc_params;
 
 typedef struct {
@@ -402,13 +403,13 @@ void orc_load_dem(orc_sim *s, const double *vert) {
         s->dz[l][k] = dm / norm;
       }
   }
-  if (s->p.scheme == 1) {
-    /* FV1 sees the bed as one level per element (Eq. 6): the pyramid keeps
+  if (s->p.scheme == 1 || s->p.scheme == 2) {
+    /* FV1 and ACC see the bed as one level per element (Eq. 6): the pyramid keeps
      * the averages (the multiwavelet average is the children's mean) and
      * drops the slopes.  The static grid keeps the multiwavelet details of
      * the planar topography (Sect. 2.2); HWFV1 thresholds Haar details of
      * the piecewise-constant bed (Sect. 2.3). */
-    if (s->p.mode == ORC_ADAPTIVE)
+    if (s->p.mode == ORC_ADAPTIVE && s->p.scheme == 1)
       for (int l = L - 1; l >= 0; l--)
         for (int j = 0; j < s->ny[l]; j++)
           for (int i = 0; i < s->nx[l]; i++) {
@@ -536,9 +537,11 @@ void orc_load_initial(orc_sim *s, const double *hv, const double *qxv, const dou
       }
     }
   }
-  if (s->p.scheme == 1)  /* FV1: averages only (Eq. 5) */
+  if (s->p.scheme == 1 || s->p.scheme == 2)  /* FV1, ACC: averages only (Eq. 5) */
     for (size_t k = 0; k < n; k++)
       for (int v = 0; v < 3; v++) U[(3 * v + 1) * n + k] = U[(3 * v + 2) * n + k] = 0.0;
+  if (s->p.scheme == 2)  /* ACC: face discharges start at zero */
+    for (int l = 0; l <= L; l++) memset(s->Wi[l], 0, 4 * nn(s, l) * sizeof(double));
   s->t = 0.0;
   s->steps = 0;
   s->n_clip = 0;
@@ -646,7 +649,7 @@ void orc_init_grid(orc_sim *s) {
         double *U = s->U[l];
         if (s->V[l][k] > s->z[l][k]) {
           for (int m = 0; m < 3; m++) U[m * n + k] = s->V[l][m * n + k] - s->z[l][m * n + k];
-          if (s->p.scheme == 1) U[n + k] = U[2 * n + k] = 0.0;
+          if (s->p.scheme != 0) U[n + k] = U[2 * n + k] = 0.0;
         } else {
           for (int m = 0; m < 9; m++) U[m * n + k] = 0.0;
         }
@@ -888,6 +891,10 @@ static double compute_dt(orc_sim *s, double t_end) {
         if (s->kind[l][k] != K_LEAF) continue;
         double h0 = s->U[l][k];
         double dxl = s->dx[l];
+        if (s->p.scheme == 2) {  /* ACC: gravity-wave celerity only (Bates et al. 2010) */
+          if (h0 > hd) best = fmin(best, dxl / sqrt(g * h0));
+          continue;
+        }
         if (h0 > hd) {
           double u = s->U[l][3 * n + k] / h0, v = s->U[l][6 * n + k] / h0;
           double c = sqrt(g * h0);
@@ -1328,12 +1335,149 @@ static double rk_stage(orc_sim *s, double **Xin, double **Wout, double **Wcomb, 
   return bnd;
 }
 
+/* ------------------------------------------------------------------------ */
+/* ACC: the local inertial solver (Sect. 2.1.3)                              */
+/* ------------------------------------------------------------------------ */
+/* The paper describes ACC by reference (Bates et al. 2010, De Almeida et al.
+ * 2012): piecewise-constant depth and bed, a discharge per interface from
+ * the momentum equation without convective acceleration coupled to the
+ * Manning resistance, continuity from the four interface discharges,
+ * Courant number 0.7.  Reading used here: the explicit scheme of Bates et
+ * al. with the resistance taken semi-implicitly in the discharge,
+ *   q^{n+1} = (q^n - g h_f dt (eta_b - eta_a) / d)
+ *             / (1 + g dt n_f^2 |q^n| / h_f^{7/3}),
+ * h_f = max(eta_a, eta_b) - max(z_a, z_b) (no flow where h_f <= h_dry),
+ * n_f the mean of the two cells' Manning n, d the distance between the cell
+ * centres; rain enters continuity.  On graded static grids each finer
+ * element computes the discharge of its half of a face with the coarser
+ * element, and the coarser element sums them (Sect. 2.2.1, "aggregated").
+ * Face discharges (m^2/s, positive towards +x / +y) are held per leaf and
+ * face (E, W, N, S) in s->Wi; a face between two leaves of one level is
+ * computed by both with the same operands, so both hold the same value.
+ * Discharges start at zero.  Boundaries: walls carry none, inflow faces the
+ * hydrograph's unit discharge, and an open face carries the discharge of
+ * the element's opposite face (zero gradient of the discharge; a zero
+ * surface gradient would let friction stop the outflow). */
+static double acc_face_q(double q0, double ha, double za, double hb, double zb, double d, double nf,
+                         double dt, double g, double hd) {
+  double ea = ha + za, eb = hb + zb;
+  double hf = fmax(ea, eb) - fmax(za, zb);
+  if (!(hf > hd)) return 0.0;
+  double num = q0 - g * hf * dt * (eb - ea) / d;
+  double den = 1.0 + g * dt * nf * nf * fabs(q0) / (hf * hf * cube_root(hf));
+  return num / den;
+}
+
+/* the leaf covering node (l, a, b) at that level or above: its level */
+static int acc_cover(const orc_sim *s, int l, int a, int b, int *la, int *ia, int *ja) {
+  while (l > 0 && s->kind[l][id(s, l, a, b)] == K_BELOW) {
+    a /= 2;
+    b /= 2;
+    l--;
+  }
+  *la = l; *ia = a; *ja = b;
+  return s->kind[l][id(s, l, a, b)];
+}
+
+/* one ACC step of length dt; returns the outward boundary mass flux */
+static double acc_step(orc_sim *s, double dt) {
+  static const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+  const double g = s->p.g, hd = s->p.h_dry;
+  const int L = s->L;
+  /* discharges of every leaf's faces, from the old state, into s->Ui */
+  for (int l = 0; l <= L; l++) {
+    size_t n = nn(s, l);
+    for (int j = 0; j < s->ny[l]; j++)
+      for (int i = 0; i < s->nx[l]; i++) {
+        size_t k = id(s, l, i, j);
+        if (s->kind[l][k] != K_LEAF) continue;
+        double h = s->U[l][k], z = s->z[l][k], nm = s->nm[l][k];
+        for (int f = 0; f < 4; f++) {
+          double q0 = s->Wi[l][f * n + k], qn = 0.0;
+          int a = i + di[f], b = j + dj[f];
+          if (!in_dom(s, l, a, b)) {
+            int e = (f == 0) ? 1 : (f == 1) ? 0 : (f == 2) ? 3 : 2;
+            double qin = inflow_q(s, e, l, (e < 2) ? j : i, s->t);
+            if (qin > 0.0) qn = (e == 0 || e == 2) ? qin : -qin;
+            else if (s->p.bc[e] == ORC_OPEN) qn = s->Wi[l][(f ^ 1) * n + k];  /* discharge carried through */
+          } else {
+            int la, ia, ja;
+            int kd = acc_cover(s, l, a, b, &la, &ia, &ja);
+            if (kd == K_SIG) {
+              qn = 0.0; /* finer neighbour: its elements hold the half-face discharges */
+            } else {
+              size_t kb = id(s, la, ia, ja);
+              double hb = s->U[la][kb], zb = s->z[la][kb], nb = s->nm[la][kb];
+              double d = 0.5 * (s->dx[l] + s->dx[la]), nf = 0.5 * (nm + nb);
+              if (f == 0 || f == 2) qn = acc_face_q(q0, h, z, hb, zb, d, nf, dt, g, hd);
+              else qn = acc_face_q(q0, hb, zb, h, z, d, 0.5 * (nb + nm), dt, g, hd);
+            }
+          }
+          s->Ui[l][f * n + k] = qn;
+        }
+      }
+  }
+  for (int l = 0; l <= L; l++) memcpy(s->Wi[l], s->Ui[l], 4 * nn(s, l) * sizeof(double));
+  /* continuity */
+  double bnd = 0.0;
+  double rain = (s->t < s->p.rain_t_end) ? s->p.rain_rate : 0.0;
+  for (int l = 0; l <= L; l++) {
+    size_t n = nn(s, l);
+    double dxl = s->dx[l];
+    for (int j = 0; j < s->ny[l]; j++)
+      for (int i = 0; i < s->nx[l]; i++) {
+        size_t k = id(s, l, i, j);
+        if (s->kind[l][k] != K_LEAF) continue;
+        double F[4];
+        for (int f = 0; f < 4; f++) {
+          int a = i + di[f], b = j + dj[f];
+          F[f] = s->Wi[l][f * n + k] * dxl;
+          if (in_dom(s, l, a, b) && s->kind[l][id(s, l, a, b)] == K_SIG) {
+            int c1, c2;
+            if (f == 0) { c1 = 0; c2 = 2; }
+            else if (f == 1) { c1 = 1; c2 = 3; }
+            else if (f == 2) { c1 = 0; c2 = 1; }
+            else { c1 = 2; c2 = 3; }
+            size_t nf = nn(s, l + 1);
+            size_t k1 = id(s, l + 1, 2 * a + (c1 & 1), 2 * b + (c1 >> 1));
+            size_t k2 = id(s, l + 1, 2 * a + (c2 & 1), 2 * b + (c2 >> 1));
+            double q1 = s->Wi[l + 1][(f ^ 1) * nf + k1], q2 = s->Wi[l + 1][(f ^ 1) * nf + k2];
+            F[f] = q1 * s->dx[l + 1] + q2 * s->dx[l + 1];
+            s->Wi[l][f * n + k] = 0.5 * (q1 + q2);  /* the face's mean, for the read-out */
+          }
+          if (!in_dom(s, l, a, b)) bnd += (f == 0 || f == 2) ? F[f] : -F[f];
+        }
+        double h = s->U[l][k] + rain * dt;
+        if (rain > 0.0) s->v_rain += rain * dt * dxl * dxl;
+        h = h + dt * ((F[1] - F[0]) + (F[3] - F[2])) / (dxl * dxl);
+        if (h < 0.0) {
+          s->n_clip++;
+          s->v_clip += -h * dxl * dxl;
+          h = 0.0;
+        }
+        s->U[l][k] = h;
+        s->U[l][3 * n + k] = 0.5 * (s->Wi[l][0 * n + k] + s->Wi[l][1 * n + k]);
+        s->U[l][6 * n + k] = 0.5 * (s->Wi[l][2 * n + k] + s->Wi[l][3 * n + k]);
+      }
+  }
+  return bnd;
+}
+
 /* One time step (Sect. 2.1.1 and 2.3): adapt (MWDG2), dt, rain, friction,
  * stage 1 (Eq. 4a), stage 2 (Eq. 4b).  Returns dt. */
 double orc_step(orc_sim *s, double t_end) {
   orc_adapt(s);
   double dt = compute_dt(s, t_end);
   if (!(dt > 0.0)) return 0.0;
+  if (s->p.scheme == 2) {
+    double net_out = dt * acc_step(s, dt);
+    if (net_out >= 0.0) s->v_out += net_out;
+    else s->v_in += -net_out;
+    s->t = s->t + dt;
+    s->steps++;
+    s->last_dt = dt;
+    return dt;
+  }
   int L = s->L;
   double rain = (s->t < s->p.rain_t_end) ? s->p.rain_rate : 0.0;
   for (int l = 0; l <= L; l++) {

@@ -11,7 +11,7 @@ All computation runs in the CUDA library ``libmwdg`` (``csrc/``, C ABI in
 fallback: without the built library and a GPU the calls raise.
 """
 from .binding import (Solver, Ensemble, MwdgError, lib, solver_from_problem, UNIFORM, STATIC, ADAPTIVE,
-                      F64, F32, DG2, FV1, WALL, OPEN, WEST, EAST, SOUTH, NORTH)
+                      F64, F32, DG2, FV1, ACC, WALL, OPEN, WEST, EAST, SOUTH, NORTH)
 
 __all__ = ["Solver", "Ensemble", "MwdgError", "lib", "solver_from_problem", "UNIFORM", "STATIC", "ADAPTIVE",
-           "F64", "F32", "DG2", "FV1", "WALL", "OPEN", "WEST", "EAST", "SOUTH", "NORTH"]
+           "F64", "F32", "DG2", "FV1", "ACC", "WALL", "OPEN", "WEST", "EAST", "SOUTH", "NORTH"]

@@ -11,7 +11,7 @@ from . import build as _build
 
 UNIFORM, STATIC, ADAPTIVE = 0, 1, 2
 F64, F32 = 0, 1
-DG2, FV1 = 0, 1
+DG2, FV1, ACC = 0, 1, 2
 WALL, OPEN = 0, 1
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 

@@ -355,7 +355,8 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
       !(p->dt_max > 0.0) || !std::isfinite(p->eps) || p->eps < 0.0 ||
       (p->iface_rule != MWDG_IFACE_PAPER && p->iface_rule != MWDG_IFACE_REFLUX) ||
       (p->iface_rule == MWDG_IFACE_REFLUX && p->mode == MWDG_ADAPTIVE) ||
-      (p->scheme != MWDG_DG2 && p->scheme != MWDG_FV1))
+      (p->scheme != MWDG_DG2 && p->scheme != MWDG_FV1 && p->scheme != MWDG_ACC) ||
+      (p->scheme == MWDG_ACC && p->mode == MWDG_ADAPTIVE))
     return MWDG_ERR_ARG;
   mwdg_ctx *c = new mwdg_ctx();
   c->p = *p;
@@ -523,6 +524,8 @@ mwdg_status mwdg_load_initial(mwdg_ctx *c, const double *h_vert, const double *q
   }
   c->launches += dispatch(c, [&](auto &p, auto *) {
     using T = std::remove_pointer_t<decltype(p.U)>;
+    // ACC: face discharges (held in the second stage view) start at zero
+    if (g.scheme == MWDG_ACC) cudaMemsetAsync(p.Wi, 0, 4 * (size_t)g.P * sizeof(T), c->st);
     return Launch<T>::initial_finest(g, p, is_eta ? 1 : 0, c->st);
   });
   CHECK_LAUNCH();
@@ -833,7 +836,8 @@ constexpr char kMagic[8] = {'M', 'W', 'D', 'G', 'S', 'T', '0', '1'};
 
 size_t state_bytes(const mwdg_ctx *c) {
   const size_t P = (size_t)c->g.P, ts = (c->g.prec == MWDG_F64) ? 8 : 4;
-  return sizeof(StateHeader) + P + 9 * P * ts + 3 * P * ts + P * ts + P * 8;
+  const size_t acc = (c->g.scheme == MWDG_ACC) ? 4 * P * ts : 0;  // ACC face discharges
+  return sizeof(StateHeader) + P + 9 * P * ts + 3 * P * ts + P * ts + P * 8 + acc;
 }
 }  // namespace
 
@@ -878,6 +882,11 @@ mwdg_status mwdg_save_state(mwdg_ctx *c, void *buf, int64_t cap) {
   CK(cudaMemcpyAsync(b, NM, P * ts, cudaMemcpyDeviceToHost, c->st));
   b += P * ts;
   CK(cudaMemcpyAsync(b, DZ, P * 8, cudaMemcpyDeviceToHost, c->st));
+  b += P * 8;
+  if (g.scheme == MWDG_ACC) {
+    const void *Wi = (g.prec == MWDG_F64) ? (void *)c->pd.Wi : (void *)c->pf.Wi;
+    CK(cudaMemcpyAsync(b, Wi, 4 * P * ts, cudaMemcpyDeviceToHost, c->st));
+  }
   CK(cudaStreamSynchronize(c->st));
   return MWDG_OK;
 }
@@ -908,6 +917,11 @@ mwdg_status mwdg_load_state(mwdg_ctx *c, const void *buf, int64_t size) {
   CK(cudaMemcpyAsync(NM, b, P * ts, cudaMemcpyHostToDevice, c->st));
   b += P * ts;
   CK(cudaMemcpyAsync(DZ, b, P * 8, cudaMemcpyHostToDevice, c->st));
+  b += P * 8;
+  if (g.scheme == MWDG_ACC) {
+    void *Wi = (g.prec == MWDG_F64) ? (void *)c->pd.Wi : (void *)c->pf.Wi;
+    CK(cudaMemcpyAsync(Wi, b, 4 * P * ts, cudaMemcpyHostToDevice, c->st));
+  }
   Ctl ctl = h.ctl;
   ctl.t_end = 1e300;
   ctl.blocks_done = 0u;

@@ -210,7 +210,7 @@ __global__ void k_fv1_bed(Geo g, Ptrs<T> p) {
   const long long P = g.P;
   int l, i, j;
   node_of(g, k, l, i, j);
-  if (g.mode == MWDG_ADAPTIVE && l < g.L) {
+  if (g.scheme == MWDG_FV1 && g.mode == MWDG_ADAPTIVE && l < g.L) {
     T a[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) a[c] = p.Z[nid(g, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1))];
@@ -246,7 +246,7 @@ __global__ void k_initial_finest(Geo g, Ptrs<T> p, int is_eta) {
       for (int m = 0; m < 9; m++) U[m * P + k] = T(0);
     }
   }
-  if (g.scheme == MWDG_FV1)  // averages only (Eq. 5); the bed slopes are zero
+  if (g.scheme != MWDG_DG2)  // FV1, ACC: averages only (Eq. 5); the bed slopes are zero
     for (int v = 0; v < 3; v++) U[(3 * v + 1) * P + k] = U[(3 * v + 2) * P + k] = T(0);
 }
 
@@ -692,6 +692,7 @@ __device__ __forceinline__ T leaf_dt_candidate(const Geo &g, const Ptrs<T> &p, i
   const T gg = geo_g<T>(g), hd = geo_hd<T>(g);
   const T dxl = geo_dx<T>(g, l);
   T best = tinf<T>();
+  if (g.scheme == MWDG_ACC) return (h0 > hd) ? dxl / tsqrt(gg * h0) : best;  // gravity waves only
   if (h0 > hd) {
     T u = qx0 / h0, v = qy0 / h0;
     T c = tsqrt(gg * h0);
@@ -2137,6 +2138,163 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
 }
 
 // ---------------------------------------------------------------------------
+// ACC: the local inertial solver (Sect. 2.1.3)
+// ---------------------------------------------------------------------------
+// Depth and bed piecewise constant; a discharge per interface from the
+// momentum equation without convective acceleration with the Manning
+// resistance taken semi-implicitly (the scheme of Bates et al. 2010, which
+// the paper cites):
+//   q' = (q - g h_f dt (eta_b - eta_a) / d) / (1 + g dt n_f^2 |q| / h_f^{7/3}),
+// h_f = max(eta_a, eta_b) - max(z_a, z_b) (no flow where h_f <= h_dry), n_f the
+// mean Manning n, d the distance between the cell centres.  Each leaf holds
+// the discharges of its four faces (E, W, N, S; m^2/s towards +x / +y): a
+// face between two leaves of one level is computed by both with the same
+// operands; on graded static grids each finer leaf computes its half of a
+// face with the coarser leaf, and the coarser leaf sums the halves
+// (Sect. 2.2.1).  Old discharges are read from Wi, new ones written to Ui;
+// the continuity pass copies them back.  Open faces carry the discharge of
+// the leaf's opposite face, inflow faces the hydrograph.
+template <typename T>
+__device__ __forceinline__ T acc_face_q(T q0, T ha, T za, T hb, T zb, T d, T nf, T dt, T gg, T hd) {
+  const T ea = ha + za, eb = hb + zb;
+  const T hf = tmax(ea, eb) - tmax(za, zb);
+  if (!(hf > hd)) return T(0);
+  const T num = q0 - gg * hf * dt * (eb - ea) / d;
+  const T den = T(1) + gg * dt * nf * nf * tabs(q0) / (hf * hf * tcbrt(hf));
+  return num / den;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_acc_q(Geo g, Ptrs<T> p) {
+  if (!ctl_stepping(p.ctl)) return;
+  const long long P = g.P;
+  const T dt = ctl_dt<T>(p.ctl), gg = geo_g<T>(g), hd = geo_hd<T>(g);
+  const ForceTime tf{p.ctl, false};
+  FOR_LEAVES(p) {
+    int l, i, j;
+    const long long k = unpack_leaf(g, p.leaves[_q], l, i, j);
+    long long code[4];
+    load_nb_codes(p.nbr, _q, code);
+    const T h = p.U[k], z = p.Z[k], nm = p.NM[k], dxl = geo_dx<T>(g, l);
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+      const T q0 = p.Wi[f * P + k];
+      T qn = T(0);
+      const int type = nb_type(code[f]);
+      if (type == NB_EDGE) {
+        const int e = (f == 0) ? 1 : (f == 1) ? 0 : (f == 2) ? 3 : 2;
+        const double qin = inflow_q(g, p.knot_t, p.knot_Q, e, l, (e < 2) ? j : i, tf());
+        if (qin > 0.0) qn = (e == 0 || e == 2) ? (T)qin : -(T)qin;
+        else if (g.bc[e] == MWDG_OPEN) qn = p.Wi[(f ^ 1) * P + k];
+      } else if (type != NB_REFINED) {
+        const long long kb = nb_node(code[f]);
+        const int lb = l - nb_depth(code[f]);
+        const T hb = p.U[kb], zb = p.Z[kb], nb = p.NM[kb];
+        const T d = T(0.5) * (dxl + geo_dx<T>(g, lb));
+        if (f == 0 || f == 2) qn = acc_face_q(q0, h, z, hb, zb, d, T(0.5) * (nm + nb), dt, gg, hd);
+        else qn = acc_face_q(q0, hb, zb, h, z, d, T(0.5) * (nb + nm), dt, gg, hd);
+      }
+      p.Ui[f * P + k] = qn;
+    }
+  }
+}
+
+// continuity (rain as a source, clip of negative depth), read-out discharges,
+// the next CFL candidate, and the end of the step in the last block
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_acc_h(Geo g, Ptrs<T> p) {
+  if (!ctl_stepping(p.ctl)) return;
+  const long long P = g.P;
+  const T dt = ctl_dt<T>(p.ctl), gg = geo_g<T>(g), hd = geo_hd<T>(g);
+  const bool rain = p.ctl->rain_on;
+  const T rinc = ctl_rain<T>(p.ctl);
+  T bsum = T(0), best = tinf<T>();
+  double csum = 0.0;
+  unsigned long long ncl = 0;
+  bool bad = false;
+  FOR_LEAVES(p) {
+    int l, i, j;
+    const long long k = unpack_leaf(g, p.leaves[_q], l, i, j);
+    long long code[4];
+    load_nb_codes(p.nbr, _q, code);
+    const T dxl = geo_dx<T>(g, l);
+    T F[4], qs[4];
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+      qs[f] = p.Ui[f * P + k];
+      F[f] = qs[f] * dxl;
+      const int type = nb_type(code[f]);
+      if (type == NB_REFINED) {
+        const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
+        int c1, c2;
+        if (f == 0) { c1 = 0; c2 = 2; }
+        else if (f == 1) { c1 = 1; c2 = 3; }
+        else if (f == 2) { c1 = 0; c2 = 1; }
+        else { c1 = 2; c2 = 3; }
+        const T q1 = p.Ui[(f ^ 1) * P + nid(g, l + 1, 2 * a + (c1 & 1), 2 * b + (c1 >> 1))];
+        const T q2 = p.Ui[(f ^ 1) * P + nid(g, l + 1, 2 * a + (c2 & 1), 2 * b + (c2 >> 1))];
+        const T dxf = geo_dx<T>(g, l + 1);
+        F[f] = q1 * dxf + q2 * dxf;
+        qs[f] = T(0.5) * (q1 + q2);
+      }
+      if (type == NB_EDGE) bsum += (f == 0 || f == 2) ? F[f] : -F[f];
+    }
+    T h = p.U[k];
+    if (rain) h = h + rinc;
+    h = h + dt * ((F[1] - F[0]) + (F[3] - F[2])) / (dxl * dxl);
+    if (h < T(0)) {
+      ncl++;
+      csum += -(double)h * (g.dxl[l] * g.dxl[l]);
+      h = T(0);
+    }
+    if (!isfinite(h)) bad = true;
+    p.U[k] = h;
+    p.U[3 * P + k] = T(0.5) * (qs[0] + qs[1]);
+    p.U[6 * P + k] = T(0.5) * (qs[2] + qs[3]);
+#pragma unroll
+    for (int f = 0; f < 4; f++) p.Wi[f * P + k] = qs[f];
+    if (h > hd) best = tmin(best, dxl / tsqrt(gg * h));
+  }
+  if (bad) p.ctl->nonfinite = 1;
+  for (int o = 16; o > 0; o >>= 1) {
+    bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+    best = tmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+    ncl += __shfl_xor_sync(0xffffffffu, ncl, o);
+  }
+  if (__any_sync(0xffffffffu, ncl != 0ULL)) {
+    for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
+    if ((threadIdx.x & 31) == 0 && ncl) {
+      atomicAdd(&p.ctl->n_clip, ncl);
+      atomicAdd(&p.ctl->v_clip, csum);
+    }
+  }
+  __shared__ T red[2][TPB / 32];
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = bsum;
+    red[1][threadIdx.x >> 5] = best;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T b = red[0][0], m = red[1][0];
+    for (int w = 1; w < TPB / 32; w++) {
+      b += red[0][w];
+      m = tmin(m, red[1][w]);
+    }
+    if (b != T(0)) atomicAdd(&p.ctl->bnd[0], (double)b);
+    if (m < tinf<T>()) atomic_min_pos(&p.ctl->dtmin, (double)m);
+    __threadfence();
+  }
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) last = (atomicAdd(&p.ctl->blocks_done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    end_step(g, p.ctl, true);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Read-back
 // ---------------------------------------------------------------------------
 // h, u, v of finest cell (I, J): the plane of the active leaf covering it
@@ -2278,7 +2436,7 @@ int Launch<T>::load_dem_pyramid(const Geo &g, const Ptrs<T> &p, cudaStream_t st)
   k_zmax<T><<<152 * 4, TPB, 0, st>>>(g, p);
   n++;
   for (int l = g.L - 1; l >= 0; l--, n++) k_encode_z<T><<<nblk(lvl(g, l)), TPB, 0, st>>>(g, p, l);
-  if (g.scheme == MWDG_FV1) {
+  if (g.scheme != MWDG_DG2) {
     k_fv1_bed<T><<<nblk(g.P), TPB, 0, st>>>(g, p);
     n++;
   }
@@ -2442,6 +2600,14 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
     MARK(KC_CONTROL);
     k_begin_step<<<1, 1, 0, st>>>(g, p.ctl, p.nleaf);
     n++;
+  }
+  if (g.scheme == MWDG_ACC) {  // local inertial: discharges, then continuity
+    MARK(KC_UPDATE1);
+    k_acc_q<T><<<grid_leaves, TPB, 0, st>>>(g, p);
+    MARK(KC_UPDATE2);
+    k_acc_h<T><<<grid_leaves, TPB, 0, st>>>(g, p);
+    MARK(-1);
+    return n + 2;
   }
   const int stages = (g.scheme == MWDG_FV1) ? 1 : 2;  // FV1: forward Euler (Eq. 7)
   for (int stage = 1; stage <= stages; stage++) {

@@ -267,6 +267,25 @@ def fv1(p: Problem) -> Problem:
     return replace(p, scheme=1, cfl=0.5)
 
 
+def acc(p: Problem) -> Problem:
+    """The same problem solved by ACC (Sect. 2.1.3), at its Courant number 0.7."""
+    return replace(p, scheme=2, cfl=0.7)
+
+
+def sloped_channel(nx: int = 256, ny: int = 4, dx: float = 10.0, slope: float = 1e-3, q_in: float = 2.0,
+                   n_manning: float = 0.03) -> Problem:
+    """A y-invariant strip with a uniform bed slope falling eastward, unit
+    inflow q_in (m^2/s) through the whole west edge and an open east edge."""
+    X, Y = _vertex_xy(nx, ny, dx)
+    z = slope * (nx * dx - X)
+    zeros = np.zeros_like(z)
+    Lx = nx * dx
+    return Problem("sloped_channel", nx, ny, 0, dx, z, zeros.copy(), zeros.copy(), zeros.copy(),
+                   n_manning=n_manning, bc=(WALL, OPEN, WALL, WALL), inflow_edge=WEST, inflow_c0=0,
+                   inflow_c1=ny - 1, inflow_t=np.array([0.0, 1e9]), inflow_Q=np.array([q_in * ny * dx] * 2),
+                   mode=UNIFORM, t_end=1e9)
+
+
 def crop(p: Problem, i0: int, j0: int, nx: int, ny: int, L: int) -> Problem:
     """A window of a problem (finest cells [i0, i0+nx) x [j0, j0+ny)) as its own
     problem with maximum level L; the inflow segment is clipped to it."""

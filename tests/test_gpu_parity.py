@@ -390,3 +390,47 @@ def test_fv1_dam_break_and_lake_f64_f32():
         s.run_steps(200)
         _, _, _, c = s.read_active()
         assert np.abs(c[:, 3:]).max() <= tol, prec
+
+
+# ---------------------------------------------------------------------------
+# ACC (local inertial, Sect. 2.1.3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [S.UNIFORM, S.STATIC])
+def test_acc_valley_f64(mode):
+    """ACC on the valley with inflow and rain, uniform and static graded grid
+    (half-face discharges aggregated): lockstep parity with the oracle and the
+    mass budget."""
+    p = S.acc(S.valley(n=128, L=7, mode=mode, eps=1e-2, peak_Q=200.0, t_peak=100.0))
+    p.rain_rate, p.rain_t_end = 1e-4, 1e9
+    v0 = gpu_sim(p).get_volume()["volume"]
+    g, o = run_parity(p, 150, check_every=25)
+    lev, _, _, c = g.read_active()
+    assert (c[:, 0] > 1e-3).sum() > 20
+    if mode == S.STATIC:
+        assert len(np.unique(lev)) >= 3
+    v, vo = g.get_volume(), o.diag()
+    for key in ("volume", "v_in", "v_out", "v_rain", "v_clip"):
+        assert abs(v[key] - vo[key]) <= 1e-9 * max(1.0, abs(vo[key])), key
+    budget = v0 + v["v_in"] - v["v_out"] + v["v_rain"] + v["v_clip"]
+    assert abs(v["volume"] - budget) <= 1e-12 * v["volume"]
+
+
+def test_acc_channel_and_lake_f64_f32():
+    """ACC sloped channel (open outlet) in lockstep with the oracle; FP32
+    against FP64; lake at rest with islands exact in both precisions."""
+    p = S.acc(S.sloped_channel(nx=128, ny=4, dx=10.0, slope=1e-3, q_in=2.0, n_manning=0.03))
+    p.dt_max = 5.0
+    g, o = run_parity(p, 200, check_every=50)
+    f = gpu_sim(p, precision=1)
+    f.run_to_time(g.get_time()[0])
+    h32, _, _ = f.read_fields()
+    h64, _, _ = g.read_fields()
+    assert np.abs(h32 - h64).max() <= TOL32_H
+    q = S.acc(S.lake_at_rest(n=48, islands=True))
+    for prec in (0, 1):
+        s = gpu_sim(q, precision=prec)
+        _, _, _, c0 = s.read_active()
+        s.run_steps(200)
+        _, _, _, c = s.read_active()
+        assert np.abs(c[:, 3:]).max() == 0.0, prec
+        np.testing.assert_array_equal(c[:, 0], c0[:, 0])
