@@ -778,24 +778,24 @@ __device__ __forceinline__ bool tail_is_tile(const Geo &g, int tail) {
 
 // tile level s and index t within it of a slot
 __device__ __forceinline__ void slot_st(int slot, int &s, int &t) {
-  s = 0;
-  while (s + 1 < MT_LEVELS && slot >= tbase(s + 1)) s++;
-  t = slot - tbase(s);
+  s = (slot >= tbase(1)) + (slot >= tbase(2)) + (slot >= tbase(3)) + (slot >= tbase(4));
+  t = slot - ((s == 0) ? 0 : (s == 1) ? tbase(1) : (s == 2) ? tbase(2) : (s == 3) ? tbase(3) : tbase(4));
 }
 
 // grid node (level ltop - s) of node t of tile level s; false outside the level
 __device__ __forceinline__ bool tile_coord(const Geo &g, const Tile &tl, int s, int t, int &i, int &j) {
-  const int side = MT >> s, l = tl.ltop - s;
-  i = tl.bx * side + t % side;
-  j = tl.by * side + t / side;
+  const int lg = 4 - s, l = tl.ltop - s;  // side = MT >> s = 2^lg
+  static_assert(MT == 16, "tile side 2^4");
+  i = (tl.bx << lg) + (t & ((1 << lg) - 1));
+  j = (tl.by << lg) + (t >> lg);
   return i < g.nxl[l] && j < g.nyl[l];
 }
 
 // slot of child c (= cx + 2 cy) of node t of tile level s >= 1
 __device__ __forceinline__ int child_slot(int s, int t, int c) {
-  const int side = MT >> s;
-  const int a = 2 * (t % side) + (c & 1), b = 2 * (t / side) + (c >> 1);
-  return tbase(s - 1) + b * (2 * side) + a;
+  const int lg = 4 - s;  // side = 2^lg
+  const int a = 2 * (t & ((1 << lg) - 1)) + (c & 1), b = 2 * (t >> lg) + (c >> 1);
+  return tbase(s - 1) + (b << (lg + 1)) + a;
 }
 
 // the two slots a thread stages, with their grid node (-1: none)
@@ -1090,14 +1090,24 @@ struct RegStage {
 // prediction flag of node (m, a, b)
 template <typename T>
 __device__ __forceinline__ uint8_t predicted(const Geo &g, const Ptrs<T> &p, int m, int a, int b) {
-  uint8_t f = 0;
-#pragma unroll
-  for (int bb = -1; bb <= 1; bb++)
-#pragma unroll
-    for (int aa = -1; aa <= 1; aa++) {
-      const int x = a + aa, y = b + bb;
-      if (x >= 0 && y >= 0 && x < g.nxl[m] && y < g.nyl[m]) f |= p.flag[nid(g, m, x, y)];
-    }
+  const int nx = g.nxl[m], ny = g.nyl[m];
+  const uint8_t *row = p.flag + nid(g, m, a, b);
+  const bool w = a > 0, e = a + 1 < nx, s_ = b > 0, n_ = b + 1 < ny;
+  uint8_t f = row[0];
+  if (w) f |= row[-1];
+  if (e) f |= row[1];
+  if (s_) {
+    const uint8_t *r = row - nx;
+    f |= r[0];
+    if (w) f |= r[-1];
+    if (e) f |= r[1];
+  }
+  if (n_) {
+    const uint8_t *r = row + nx;
+    f |= r[0];
+    if (w) f |= r[-1];
+    if (e) f |= r[1];
+  }
   return f;
 }
 
