@@ -1366,7 +1366,9 @@ __device__ __forceinline__ T friction_factor(T h0, T qx0, T qy0, T nm, T dt, T g
 // With FRIC (stage 1), the stage input is U after rain and friction, which
 // are applied here to the leaf and, for the limiter, to its neighbours'
 // averages (both are pointwise, so every leaf sees the same values).
-template <typename T, bool FRIC, bool FV1>
+// CODES (the first kernel after an adaptation): the leaf's four neighbour
+// codes are computed here from the kinds and stored for the later kernels
+template <typename T, bool FRIC, bool FV1, bool CODES>
 __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   const long long P = g.P;
   const T hd = geo_hd<T>(g), s3 = s3v<T>(), gg = geo_g<T>(g);
@@ -1376,6 +1378,13 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   FOR_LEAVES(p) {
     int l, i, j;
     long long k = unpack_leaf(g, p.leaves[_q], l, i, j);
+    long long code[4];
+    if (CODES) {
+      leaf_nb_codes(g, p.kind, l, i, j, code);
+      longlong2 *dst = reinterpret_cast<longlong2 *>(p.nbr + 4LL * _q);
+      dst[0] = make_longlong2(code[0], code[1]);
+      dst[1] = make_longlong2(code[2], code[3]);
+    }
     T w[9], zp[3];
 #pragma unroll
     for (int m = 0; m < 9; m++) w[m] = X[m * P + k];
@@ -1436,8 +1445,7 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
       ze[0] = zp[0]; ze[1] = zp[1]; ze[2] = zp[2];
       if (g.limiter) {
         // same-level leaf neighbours from the step's neighbour codes
-        long long code[4];
-        load_nb_codes(p.nbr, _q, code);
+        if (!CODES) load_nb_codes(p.nbr, _q, code);
         for (int dir = 0; dir < 2; dir++) {
           const long long cA = code[2 * dir], cB = code[2 * dir + 1];  // E/W, then N/S
           const bool hasA = nb_type(cA) == NB_LEAF, hasB = nb_type(cB) == NB_LEAF;
@@ -2582,10 +2590,15 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
   MARK(KC_COMPACT);
   k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind_new, p.blk, p.leaves, p.kind, begin ? p.ctl : nullptr,
                                         p.nleaf);
-  MARK(KC_COMPACT);
-  k_leaf_codes<<<(int)std::min<long long>(nblk(g.P), 152 * 8), TPB, 0, st>>>(g, p.kind_new, p.leaves, p.nleaf,
-                                                                             p.nbr);
-  return n + 3;
+  // (the neighbour codes of the new leaves: the stage-1 limiter of the step,
+  // or a pass of their own when the adaptation is not followed by a step)
+  if (!begin) {
+    MARK(KC_COMPACT);
+    k_leaf_codes<<<(int)std::min<long long>(nblk(g.P), 152 * 8), TPB, 0, st>>>(g, p.kind_new, p.leaves,
+                                                                               p.nleaf, p.nbr);
+    n++;
+  }
+  return n + 2;
 }
 
 template <typename T>
@@ -2622,9 +2635,16 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
   const int stages = (g.scheme == MWDG_FV1) ? 1 : 2;  // FV1: forward Euler (Eq. 7)
   for (int stage = 1; stage <= stages; stage++) {
     MARK(KC_LIMIT);
-    if (stages == 1) k_leaf_limit<T, true, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
-    else if (stage == 1) k_leaf_limit<T, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
-    else k_leaf_limit<T, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
+    const bool codes = (stage == 1 && begun);  // the step follows an adaptation
+    if (stages == 1) {
+      if (codes) k_leaf_limit<T, true, true, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+      else k_leaf_limit<T, true, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+    } else if (stage == 1) {
+      if (codes) k_leaf_limit<T, true, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+      else k_leaf_limit<T, true, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+    } else {
+      k_leaf_limit<T, false, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
+    }
     n++;
     if (view)
       n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
