@@ -1192,28 +1192,38 @@ template <typename T>
 __device__ __noinline__ void prolong_from_old_leaf(const Geo &g, const Ptrs<T> &p, long long k, int l, int i,
                                                    int j) {
   const long long P = g.P;
-  int path[MWDG_LMAX + 1];
-  int d = 0, a = i, b = j, la = l;
-  long long ka = k;
-  while (la > 0 && p.kind[ka] == K_BELOW) {
-    path[d++] = (a & 1) + 2 * (b & 1);
-    a >>= 1;
-    b >>= 1;
-    la--;
-    ka = nid(g, la, a, b);
+  // the old leaf above: the node itself was below a leaf, so start at its
+  // parent; the next three ancestors' kinds are read together
+  int d = 1;
+  for (;;) {
+    uint8_t kd[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) kd[q] = (l - d - q >= 0) ? p.kind[nid(g, l - d - q, i >> (d + q), j >> (d + q))]
+                                                         : (uint8_t)K_LEAF;
+    if (kd[0] != K_BELOW || l - d == 0) break;
+    if (kd[1] != K_BELOW || l - d - 1 == 0) { d += 1; break; }
+    if (kd[2] != K_BELOW || l - d - 2 == 0) { d += 2; break; }
+    d += 3;
   }
+  const long long ka = nid(g, l - d, i >> d, j >> d);
+  T u[9];
+#pragma unroll
+  for (int m = 0; m < 9; m++) u[m] = p.U[m * P + ka];
+  const T za1 = p.Z[P + ka], za2 = p.Z[2 * P + ka], zk1 = p.Z[P + k], zk2 = p.Z[2 * P + k];
+  T out[9];
   for (int v = 0; v < 3; v++) {
-    T sv[3];
-    for (int m = 0; m < 3; m++) sv[m] = p.U[(3 * v + m) * P + ka];
-    if (v == 0) slopes_to_h(sv[1], sv[2], p.Z[P + ka], p.Z[2 * P + ka]);
-    for (int qq = d - 1; qq >= 0; qq--) {
+    T sv[3] = {u[3 * v], u[3 * v + 1], u[3 * v + 2]};
+    if (v == 0) slopes_to_h(sv[1], sv[2], za1, za2);
+    for (int qq = d - 1; qq >= 0; qq--) {  // child at level l - qq: bits qq of i and j
       T o[3];
-      prolong3(sv[0], sv[1], sv[2], path[qq], o);
+      prolong3(sv[0], sv[1], sv[2], ((i >> qq) & 1) + 2 * ((j >> qq) & 1), o);
       sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
     }
-    if (v == 0) slopes_from_h(sv[1], sv[2], p.Z[P + k], p.Z[2 * P + k]);
-    for (int m = 0; m < 3; m++) p.U[(3 * v + m) * P + k] = sv[m];
+    if (v == 0) slopes_from_h(sv[1], sv[2], zk1, zk2);
+    out[3 * v] = sv[0]; out[3 * v + 1] = sv[1]; out[3 * v + 2] = sv[2];
   }
+#pragma unroll
+  for (int m = 0; m < 9; m++) p.U[m * P + k] = out[m];
 }
 
 // bytes q of an 8-byte word
