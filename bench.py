@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="instead: the batched ensemble of this many seeded valleys (sides 256-1024)")
     ap.add_argument("--no-tune", action="store_true", help="ensemble: keep the default launch shapes")
+    ap.add_argument("--scheme", default="dg2", choices=["dg2", "fv1", "acc"],
+                    help="solver: DG2 (MWDG2, the headline), FV1 (HWFV1 on the adaptive grid) or ACC "
+                         "(static graded grid from the same MRA of the topography)")
     return ap.parse_args()
 
 
@@ -212,6 +215,11 @@ def run_gpu(args, rank, world):
     torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
     p = S.valley(n=args.n, L=args.n.bit_length() - 1)
+    if args.scheme == "fv1":
+        p = S.fv1(p)  # HWFV1 on the adaptive grid
+    elif args.scheme == "acc":
+        from dataclasses import replace
+        p = S.acc(replace(p, mode=S.STATIC))  # static graded grid from the MRA of the topography
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # FP32 free-surface path (headline)
@@ -240,7 +248,7 @@ def run_gpu(args, rank, world):
     dom_name = max(per_launch, key=per_launch.get)
     dom_ms, dom_n = kt[dom_name]
     mean_leaves = kupd / len(kms)
-    bpl = kernel_bytes_per_leaf(dom_name, 4)
+    bpl = kernel_bytes_per_leaf(dom_name, 4, args.scheme)
     achieved = (bpl * mean_leaves) / (dom_ms / dom_n * 1e-3) / 1e9 if bpl else None
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs,
                 "unit": "GB/s", "frac": (achieved / peak_gbs) if achieved else None,
@@ -362,23 +370,31 @@ def reference_arm(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def kernel_bytes_per_leaf(name, ts):
-    """Algorithmic HBM bytes per active leaf of a kernel class (values of ts
-    bytes plus the 8-byte active-list entry; neighbour reads served from L2
-    are not counted).  MRA classes are per node, not per leaf: None."""
-    vals = {
-        "dg2_update_stage1": 12 + 9 + 9,      # FZ record, Wn read; Ui written
-        "dg2_update_stage2": 12 + 9 + 9 + 9,  # FZ record, Wi, Wn read; U written
-        "limit": 9 + 3 + 9 + 12,              # X, Z read; Wst, FZ record written
-    }
+def kernel_bytes_per_leaf(name, ts, scheme="dg2"):
+    """Algorithmic HBM bytes per active leaf of a kernel class: values of ts
+    bytes, the 8-byte active-list entry and the leaf's 32-byte neighbour
+    codes where the kernel reads them; neighbour values served from L2 are
+    not counted.  MRA classes are per node, not per leaf: None."""
+    if scheme == "acc":  # discharges, then continuity (values, entry, codes)
+        vals = {"dg2_update_stage1": (3 + 4 + 4, 40),   # h, z, n, old q read; new q written
+                "dg2_update_stage2": (4 + 1 + 4 + 3, 40)}  # new q, h read; h, qx, qy, q written
+    elif scheme == "fv1":  # one forward-Euler stage (labelled stage 2)
+        vals = {"dg2_update_stage2": (12 + 9 + 9, 40), "limit": (9 + 3 + 9 + 12, 40)}
+    else:
+        vals = {
+            "dg2_update_stage1": (12 + 9 + 9, 40),      # FZ record, Wn read; Ui written
+            "dg2_update_stage2": (12 + 9 + 9 + 9, 40),  # FZ record, Wi, Wn read; U written
+            "limit": (9 + 3 + 9 + 12, 40),              # X, Z read; Wst, FZ record written
+        }
     if name not in vals:
         return None
-    return vals[name] * ts + 8
+    n, extra = vals[name]
+    return n * ts + extra
 
 
 # DRAM bytes (read + write) per launch measured by ncu for a kernel, when the
 # kernel has not changed since (see profiles/); None otherwise
-TRAFFIC = {"dg2_update_stage2": 51_160_320 + 3_683_328}  # ncu: dram read + write, one launch at this workload
+TRAFFIC = {"dg2_update_stage2": 58_135_808 + 5_134_336}  # ncu: dram read + write, one launch at this workload
 
 
 def run_ensemble(args):
@@ -436,6 +452,9 @@ def run_ensemble(args):
 
 def main():
     args = parse()
+    if args.scheme != "dg2":  # the other solvers: throughput line only
+        args.no_fp64 = True
+        args.no_cpu = True
     if args.ensemble > 0:
         print(json.dumps(run_ensemble(args)))
         return
@@ -455,7 +474,9 @@ def main():
         line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "L": args.n.bit_length() - 1,
+                "config": {"workload": WORKLOAD if args.scheme == "dg2" else
+                           {"fv1": "HWFV1", "acc": "static-grid ACC"}[args.scheme] + WORKLOAD[5:],
+                           "nx": args.n, "ny": args.n, "L": args.n.bit_length() - 1,
                            "eps": 1e-3, "spinup_s": out["t_spinup"], "mean_active_leaves": out["mean_active"],
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
