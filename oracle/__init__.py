@@ -25,6 +25,10 @@ tests):
                                   volume conservation, D4 symmetry
   friction, limiter, non-homogeneous interface rule:
                                   parity unpinned beyond the invariants above
+  discrete adjoint of the uniform DG2 step (dg2_adjoint.py, PyTorch CPU
+  autograd over a restatement of the step):
+                                  pinned: bit-for-bit forward against the C
+                                  step, central differences of the C step
 """
 from __future__ import annotations
 
@@ -98,6 +102,8 @@ def lib():
         L.orc_adapt.argtypes = [C.c_void_p]
         L.orc_step.restype = C.c_double
         L.orc_step.argtypes = [C.c_void_p, C.c_double]
+        L.orc_step_dt.restype = C.c_double
+        L.orc_step_dt.argtypes = [C.c_void_p, C.c_double]
         L.orc_run_to.restype = C.c_int64
         L.orc_run_to.argtypes = [C.c_void_p, C.c_double, C.c_int64]
         L.orc_time.restype = C.c_double
@@ -246,6 +252,10 @@ class Sim:
 
     def step(self, t_end=float("inf")) -> float:
         return lib().orc_step(self._h, t_end)
+
+    def step_dt(self, dt) -> float:
+        """one step with the given dt (the CFL condition is not applied)"""
+        return lib().orc_step_dt(self._h, dt)
 
     def run_to(self, t_end, max_steps=1 << 40) -> int:
         return lib().orc_run_to(self._h, t_end, max_steps)

@@ -1465,9 +1465,13 @@ static double acc_step(orc_sim *s, double dt) {
 
 /* One time step (Sect. 2.1.1 and 2.3): adapt (MWDG2), dt, rain, friction,
  * stage 1 (Eq. 4a), stage 2 (Eq. 4b).  Returns dt. */
-double orc_step(orc_sim *s, double t_end) {
+/* One step with a time step given by the caller (dt_given > 0) or chosen by
+ * the CFL condition (dt_given <= 0).  A given dt serves the discrete adjoint:
+ * the step map differentiated there is the one with the recorded dt held
+ * fixed, and its central differences must be taken on that same map. */
+static double step_with(orc_sim *s, double t_end, double dt_given) {
   orc_adapt(s);
-  double dt = compute_dt(s, t_end);
+  double dt = dt_given > 0.0 ? dt_given : compute_dt(s, t_end);
   if (!(dt > 0.0)) return 0.0;
   if (s->p.scheme == 2) {
     double net_out = dt * acc_step(s, dt);
@@ -1511,6 +1515,10 @@ double orc_step(orc_sim *s, double t_end) {
   s->last_dt = dt;
   return dt;
 }
+
+double orc_step(orc_sim *s, double t_end) { return step_with(s, t_end, 0.0); }
+
+double orc_step_dt(orc_sim *s, double dt) { return step_with(s, INFINITY, dt); }
 
 int64_t orc_run_to(orc_sim *s, double t_end, int64_t max_steps) {
   int64_t k = 0;

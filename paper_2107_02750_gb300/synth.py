@@ -22,6 +22,9 @@ Workloads:
                        optional emerging islands (well-balancing checks)
   dam_break_strip      y-invariant 1D dam break (Ritter dry bed, Stoker wet
                        bed)
+  adjoint_reach        uniform crop of the valley terrain with water in the
+                       channel, a 60-knot hydrograph over 1 h, spatially
+                       varying Manning n and 16 gauge cells (gradient checks)
 """
 from __future__ import annotations
 
@@ -314,3 +317,39 @@ def crop(p: Problem, i0: int, j0: int, nx: int, ny: int, L: int) -> Problem:
                    qx_vert=np.ascontiguousarray(p.qx_vert[sl]),
                    qy_vert=np.ascontiguousarray(p.qy_vert[sl]),
                    n_manning=nm, inflow_edge=edge, inflow_c0=c0, inflow_c1=c1)
+
+
+def adjoint_reach(n: int = 64, dx: float = 10.0, seed: int = 5, knots: int = 60, t_span: float = 3600.0,
+                  n_gauges: int = 16, depth0: float = 1.0, relief: float = 10.0, q_unit: float = 1.0,
+                  n_mean: float = 0.035) -> tuple:
+    """Gradient workload: an n x n uniform grid of the valley terrain (seeded)
+    with a 4-cell channel holding about depth0 metres of flowing water over
+    each column's lowest point, an open east edge, a piecewise-linear inflow hydrograph of
+    `knots` seeded positive knots over t_span seconds (unit discharge around
+    q_unit) and a spatially varying Manning n (n_mean +- 30 %).  Returns
+    (problem, gauges), gauges an (n_gauges, 2) array of (j, i) cells drawn
+    from the initially wet ones."""
+    p = valley(n=n, dx=dx, seed=seed, L=0, relief=relief, channel_width=4.0 * dx, channel_depth=2.0,
+               mode=UNIFORM, t_end=t_span)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = p.z_vert
+    # a flowing start: a rippled free surface over the channel and a seeded
+    # discharge field (a derivative needs a state away from rest, where the
+    # limiter's differences are all zero)
+    ripple = fractal_surface(n + 1, seed + 2, 4.0)
+    eta = z.min(axis=0, keepdims=True) + depth0 + 0.1 * ripple / np.abs(ripple).max()
+    h = np.maximum(0.0, eta - z)
+    swirl = fractal_surface(n + 1, seed + 3, 4.0)
+    qx = h * (0.5 + 0.2 * swirl / np.abs(swirl).max())
+    qy = h * (0.2 * ripple / np.abs(ripple).max())
+    nin = p.inflow_c1 - p.inflow_c0 + 1
+    t = np.linspace(0.0, t_span, knots)
+    Q = q_unit * nin * dx * (0.6 + 0.8 * rng.random(knots))
+    rough = fractal_surface(n + 1, seed + 1, 3.0)[:n, :n]
+    nm = np.clip(n_mean * (1.0 + 0.3 * rough / max(1e-12, np.abs(rough).max())), 0.5 * n_mean, 1.5 * n_mean)
+    q = replace(p, name="adjoint_reach", h_vert=h, qx_vert=qx, qy_vert=qy, n_manning=np.ascontiguousarray(nm),
+                bc=(WALL, OPEN, WALL, WALL), inflow_t=t, inflow_Q=Q)
+    hc = 0.25 * (h[:-1, :-1] + h[1:, :-1] + h[:-1, 1:] + h[1:, 1:])
+    wet = np.argwhere(hc > 0.25 * depth0)
+    pick = rng.choice(len(wet), size=min(n_gauges, len(wet)), replace=False)
+    return q, np.ascontiguousarray(wet[np.sort(pick)].astype(np.int64))
