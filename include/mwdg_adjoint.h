@@ -1,0 +1,114 @@
+/*
+ * mwdg_adjoint.h -- C ABI of the discrete adjoint of the uniform-grid DG2
+ * step (GB300, sm_103a, FP64).
+ *
+ * The step is the DG2 shallow-water step of Sharifian & Kesserwani, arXiv
+ * 2107.02750, Sect. 2.1.1 (Eq. 1-4) on a uniform grid of nx x ny cells:
+ * rain depth and split implicit Manning friction at the start of the step,
+ * stage-input limiting (partial-wet reduction, minmod), hydrostatic face
+ * revision and HLL fluxes, two RK2 stages with the positivity clip, the
+ * time step from the CFL condition (Courant number cfl).  The same step as
+ * mwdg.h's uniform mode in FP64, rounded the same way.
+ *
+ * The adjoint is the derivative of a run of K such steps,
+ *   U_K = S_{dt_K} o ... o S_{dt_1}(U_0; z, n, Q),
+ * with the time steps held at the values recorded by the forward run (a
+ * perturbation of the parameters does not move dt), and every branch (wet
+ * or dry, reduced, minmod selection, HLL region, clip) as the forward run
+ * took it.  At an interface whose two bed limits agree to within
+ * 1e-10 max(1, |z_L|, |z_R|) the derivative of max(z_L, z_R) is split in
+ * halves between the sides (the mean of the one-sided derivatives).  Where
+ * the step is not differentiable (still water, where the limiter's
+ * differences vanish) the derivative is that of the branch taken.
+ *
+ * Layout (device memory, FP64, caller-owned):
+ *   U   9 x n, component-major: component m of cell k = j nx + i at
+ *       U[m n + k]; components (h0, h1x, h1y, qx0, qx1x, qx1y, qy0, qy1x,
+ *       qy1y), the average and the two scaled-Legendre slope coefficients
+ *       of depth and unit discharges (Eq. 2-3);
+ *   z   3 x n, the bed planes (z0, z1x, z1y) in the same layout;
+ *   n   n Manning coefficients;
+ *   knot_t, knot_Q  the inflow hydrograph, piecewise linear, constant
+ *       outside its knots (nknots >= 1 when an inflow edge is set);
+ *   dts K time steps; vertex rasters (ny+1) x (nx+1), row j south to north.
+ * Rows run south to north, columns west to east; edges 0 W, 1 E, 2 S, 3 N.
+ *
+ * Work is queued on the given CUDA stream (NULL: the legacy default stream);
+ * no call synchronises it, except mwdg_adj_create and mwdg_adj_destroy.  A
+ * context holds a tape of max_steps + 1 states (9 n doubles each) and about
+ * 130 n doubles of work arrays; one host thread uses it at a time, and its
+ * calls on one stream run in order.  Statuses are those of mwdg.h.
+ */
+#ifndef MWDG_ADJOINT_H
+#define MWDG_ADJOINT_H
+
+#include <stdint.h>
+
+#include "mwdg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mwdg_adj mwdg_adj;
+
+typedef struct {
+  int32_t nx, ny;          /* cells                                          */
+  double dx;               /* cell size (m)                                  */
+  double g, h_dry;         /* gravity, dry-depth tolerance                   */
+  double cfl, dt_max;      /* Courant number (0.33 for DG2), dt bound        */
+  int32_t limiter;         /* 0 off, 1 minmod                                */
+  int32_t bc[4];           /* MWDG_WALL / MWDG_OPEN per edge W, E, S, N      */
+  int32_t inflow_edge;     /* -1 none, else the edge carrying the hydrograph */
+  int32_t inflow_c0, inflow_c1; /* cells along that edge, inclusive          */
+  double rain_rate, rain_t_end; /* m/s while t < rain_t_end                  */
+  int32_t max_steps;       /* tape capacity: steps per forward/backward call */
+} mwdg_adj_params;
+
+/* Defaults: g = 9.80665, h_dry = 1e-3, cfl = 0.33, dt_max = 1, limiter on,
+ * walls, no inflow, no rain, max_steps = 200; nx, ny, dx must be set. */
+MWDG_API mwdg_status mwdg_adj_params_default(mwdg_adj_params *p);
+
+/* Allocates the context on the current device.  MWDG_ERR_DIMS when nx or ny
+ * < 1, nx ny > 2^28, dx <= 0 or max_steps < 1; MWDG_ERR_ARG on a bad edge,
+ * inflow range or parameter; MWDG_ERR_CUDA when the allocation fails. */
+MWDG_API mwdg_status mwdg_adj_create(const mwdg_adj_params *p, mwdg_adj **out);
+MWDG_API void mwdg_adj_destroy(mwdg_adj *a);
+
+/* Eq. 8: vertex raster (ny+1) x (nx+1) -> planes out (3 x n), on the device. */
+MWDG_API mwdg_status mwdg_adj_project(mwdg_adj *a, const double *vert, double *out, void *cuda_stream);
+
+/* Forward run of `steps` steps from U0 at time t0 (all device pointers).
+ * fixed_dt = 0: each dt from the CFL condition, written to dts[0..steps);
+ * fixed_dt = 1: the steps dts[0..steps) are read.  U_out receives U_K (it
+ * may alias U0).  MWDG_ERR_CAPACITY when steps > max_steps; MWDG_ERR_ARG on
+ * NULL pointers, steps < 0, or nknots < 1 with an inflow edge. */
+MWDG_API mwdg_status mwdg_adj_forward(mwdg_adj *a, const double *U0, const double *z, const double *n,
+                                      int32_t nknots, const double *knot_t, const double *knot_Q, double t0,
+                                      int32_t steps, int32_t fixed_dt, double *dts, double *U_out,
+                                      void *cuda_stream);
+
+/* Vector-Jacobian product of the run over the time steps dts[0..steps) from
+ * U0 at t0: given gU_K (9 x n), the cotangent of U_K, writes gU0 (9 x n)
+ * and ADDS to gz (3 x n), gn (n) and gQ (nknots), so that gradients of
+ * several segments accumulate.  The run's states are recomputed from U0
+ * into the tape (the segment's checkpoint is U0 itself).  gU0 may alias
+ * gU_K.  Errors as mwdg_adj_forward. */
+MWDG_API mwdg_status mwdg_adj_backward(mwdg_adj *a, const double *U0, const double *z, const double *n,
+                                       int32_t nknots, const double *knot_t, const double *knot_Q, double t0,
+                                       int32_t steps, const double *dts, const double *gU_K, double *gU0,
+                                       double *gz, double *gn, double *gQ, void *cuda_stream);
+
+/* Transpose of Eq. 8: plane cotangents (3 x n) -> vertex cotangents
+ * ((ny+1) x (nx+1)), overwritten. */
+MWDG_API mwdg_status mwdg_adj_project_transpose(mwdg_adj *a, const double *g_planes, double *g_vert,
+                                                void *cuda_stream);
+
+/* Description of the context's most recent failure ("" if none). */
+MWDG_API const char *mwdg_adj_last_error(const mwdg_adj *a);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MWDG_ADJOINT_H */

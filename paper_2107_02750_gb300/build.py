@@ -1,7 +1,7 @@
 """In-tree build of the CUDA library libmwdg (sm_103a) with nvcc.
 
-The translation units compile in parallel; the FP64 kernels are built
-without FMA contraction (-fmad=false) so that their arithmetic rounds as
+The translation units compile in parallel; the FP64 kernels (the solver's
+and the adjoint's) are built without FMA contraction (-fmad=false) so that their arithmetic rounds as
 written, the FP32 kernels with fast division and square root.  Output: paper_2107_02750_gb300/_build/libmwdg_<machine>.so.
 """
 from __future__ import annotations
@@ -25,6 +25,7 @@ UNITS = {
     "mwdg_f64.cu": ["-fmad=false"],
     "mwdg_f32.cu": ["--use_fast_math"],
     "mwdg_noalloc.cu": [],
+    "mwdg_adjoint.cu": ["-fmad=false"],
 }
 
 
@@ -40,7 +41,7 @@ def lib_path() -> Path:
 
 
 def _sources():
-    return sorted(CSRC.glob("*.cu")) + sorted(CSRC.glob("*.cuh")) + sorted(CSRC.glob("*.h")) + [INCLUDE / "mwdg.h"]
+    return sorted(CSRC.glob("*.cu")) + sorted(CSRC.glob("*.cuh")) + sorted(CSRC.glob("*.h")) + sorted(INCLUDE.glob("*.h"))
 
 
 def up_to_date() -> bool:

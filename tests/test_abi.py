@@ -1,15 +1,15 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry
-point that include/mwdg.h declares (no compute calls: no GPU needed)."""
+point that include/*.h declares (no compute calls: no GPU needed)."""
 import re
 from pathlib import Path
 
-from paper_2107_02750_gb300 import binding, build
+from paper_2107_02750_gb300 import adjoint, binding, build
 
-HEADER = Path(__file__).resolve().parents[1] / "include" / "mwdg.h"
+INCLUDE = Path(__file__).resolve().parents[1] / "include"
 
 
 def declared():
-    text = HEADER.read_text()
+    text = "".join(h.read_text() for h in sorted(INCLUDE.glob("*.h")))
     return sorted(set(re.findall(r"MWDG_API[^;(]*?\b(mwdg_\w+)\s*\(", text, flags=re.S)))
 
 
@@ -17,7 +17,8 @@ def test_header_declares_the_boundary():
     names = declared()
     for must in ("mwdg_create", "mwdg_load_dem", "mwdg_load_roughness", "mwdg_set_inflow",
                  "mwdg_mra_encode", "mwdg_mra_adapt", "mwdg_dg2_step", "mwdg_run_to_time",
-                 "mwdg_read_fields", "mwdg_read_active", "mwdg_get_volume"):
+                 "mwdg_read_fields", "mwdg_read_active", "mwdg_get_volume", "mwdg_adj_forward",
+                 "mwdg_adj_backward"):
         assert must in names
 
 
@@ -27,6 +28,7 @@ def test_library_exports_every_declared_symbol():
     for name in declared():
         assert hasattr(L, name), name
     assert set(binding.EXPORTS) <= set(declared())
+    assert set(adjoint.ADJ_EXPORTS) <= set(declared())
 
 
 def test_status_strings_and_defaults_without_device():

@@ -1,0 +1,197 @@
+"""Discrete adjoint of the uniform DG2 step on the GPU (include/mwdg_adjoint.h)
+against the FP64 oracle (oracle/dg2_adjoint.py, pinned on the CPU).
+
+  * the adjoint's forward sweep is the C oracle's step bit for bit (states
+    and CFL time steps), through wet/dry fronts, inflow, an open edge, rain;
+  * its gradients with respect to U0, the bed planes, Manning n and the
+    hydrograph knots agree with the oracle's to 1e-9 of each array's largest
+    entry (same branches, different rounding order in the reverse sweep);
+  * the bed's vertex gradient (transpose of Eq. 8) agrees likewise;
+  * two checkpointed segments chained by autograd give the one-segment
+    gradients;
+  * central differences of the GPU forward (time steps held), with steps
+    shrinking to 1e-8, converge to the GPU gradients (1e-4 relative).
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from oracle import dg2_adjoint as A
+from paper_2107_02750_gb300 import synth as S
+
+from util import oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+def grid_of(p):
+    return A.Grid(nx=p.nx, ny=p.ny, dx=p.dx, limiter=p.limiter, bc=tuple(p.bc), inflow_edge=p.inflow_edge,
+                  inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, rain_rate=p.rain_rate,
+                  rain_t_end=p.rain_t_end, knot_t=list(map(float, p.inflow_t)))
+
+
+def state(sim, p):
+    _, _, _, co = sim.leaves()
+    return co.T.reshape(9, p.ny, p.nx).copy()
+
+
+def context(p, max_steps):
+    from paper_2107_02750_gb300.adjoint import Dg2Adjoint
+    return Dg2Adjoint(p.nx, p.ny, p.dx, cfl=p.cfl, dt_max=p.dt_max, limiter=p.limiter, bc=tuple(p.bc),
+                      inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1,
+                      rain_rate=p.rain_rate, rain_t_end=p.rain_t_end, max_steps=max_steps)
+
+
+def device_inputs(adj, p):
+    """the GPU's own projection of the seeded vertex rasters (Eq. 8)"""
+    import torch
+    U0 = torch.cat([adj.project(p.h_vert), adj.project(p.qx_vert), adj.project(p.qy_vert)])
+    z = adj.project(p.z_vert)
+    n = torch.tensor(p.n_cell(), dtype=torch.float64, device=adj.device)
+    if p.inflow_edge >= 0:
+        kt = torch.tensor(p.inflow_t, dtype=torch.float64, device=adj.device)
+        kQ = torch.tensor(p.inflow_Q, dtype=torch.float64, device=adj.device)
+    else:
+        kt = kQ = None
+    return U0, z, n, kt, kQ
+
+
+def _cases():
+    reach, gauges = S.adjoint_reach(n=32)
+    rain = replace(reach, rain_rate=5e-3, rain_t_end=8.0)
+    dam = S.dam_break_circular(n=32, L=0, radius=6.0, h_out=0.0)
+    return [("reach", reach, 40), ("reach_rain", rain, 30), ("dam_dry", dam, 40)]
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name,p,K", CASES, ids=[c[0] for c in CASES])
+def test_forward_sweep_is_the_c_oracle_bit_for_bit(name, p, K):
+    s = oracle_sim(p)
+    U0o = state(s, p)
+    zo = s.z_level(0)[0].reshape(3, p.ny, p.nx)
+    dts = np.array([s.step() for _ in range(K)])
+    want = state(s, p)
+    adj = context(p, K)
+    U0, z, n, kt, kQ = device_inputs(adj, p)
+    assert np.array_equal(U0.cpu().numpy(), U0o) and np.array_equal(z.cpu().numpy(), zo)
+    UK, d = adj.forward(U0, z, n, kt, kQ, 0.0, K)
+    assert np.array_equal(d.cpu().numpy(), dts)
+    got = UK.cpu().numpy()
+    assert np.array_equal(got, want), np.abs(got - want).max()
+    # the same run with the steps given
+    UK2, _ = adj.forward(U0, z, n, kt, kQ, 0.0, K, dts=d)
+    assert np.array_equal(UK2.cpu().numpy(), want)
+
+
+def _close(got, want, what):
+    scale = max(np.abs(want).max(), 1e-300)
+    err = np.abs(got - want).max()
+    assert err <= TOL * scale, (what, err, scale)
+
+
+@pytest.mark.parametrize("name,p,K", CASES, ids=[c[0] for c in CASES])
+def test_gradients_match_the_oracle(name, p, K):
+    import torch
+    s = oracle_sim(p)
+    U0o = state(s, p)
+    zo = s.z_level(0)[0].reshape(3, p.ny, p.nx)
+    dts = [s.step() for _ in range(K)]
+    rng = np.random.default_rng(11)
+    seed = rng.standard_normal((9, p.ny, p.nx))
+    Q = p.inflow_Q if p.inflow_edge >= 0 else np.zeros(1)
+    G = A.gradients(U0o, zo, p.n_cell(), Q, dts, 0.0, grid_of(p), seed, z_vert=p.z_vert)
+    adj = context(p, K)
+    U0, z, n, kt, kQ = device_inputs(adj, p)
+    d = torch.tensor(dts, dtype=torch.float64, device=adj.device)
+    gU0, gz, gn, gQ = adj.backward(U0, z, n, kt, kQ, 0.0, d, torch.tensor(seed, device=adj.device))
+    _close(gU0.cpu().numpy(), G["gU0"], "U0")
+    _close(gz.cpu().numpy(), G["gz"], "z")
+    _close(gn.cpu().numpy(), G["gn"], "n")
+    if p.inflow_edge >= 0:
+        _close(gQ.cpu().numpy(), G["gQ"], "Q")
+    _close(adj.project_transpose(gz).cpu().numpy(), G["gzv"], "z vertices")
+
+
+def test_checkpointed_segments_chain_to_the_one_segment_gradient():
+    """Gauge objective after 40 steps: one segment of 40, or four of 10
+    chained by autograd (each backward recomputes its segment from its input
+    state)."""
+    import torch
+    from paper_2107_02750_gb300.adjoint import dg2_run
+    p, gauges = S.adjoint_reach(n=32)
+    adj = context(p, 40)
+    U0, z, n, kt, kQ = device_inputs(adj, p)
+
+    def grads(seg):
+        leaves = [x.clone().requires_grad_(True) for x in (U0, z, n, kQ)]
+        U, t = leaves[0], 0.0
+        for _ in range(40 // seg):
+            U, _, t = dg2_run(adj, U, leaves[1], leaves[2], leaves[3], kt, t, seg)
+        J = sum(U[0, j, i] for j, i in gauges)
+        J.backward()
+        return [x.grad.cpu().numpy() for x in leaves], U.detach().cpu().numpy()
+
+    (g1, U1), (g4, U4) = grads(40), grads(10)
+    assert np.array_equal(U1, U4)
+    for a, b, what in zip(g1, g4, ("U0", "z", "n", "Q")):
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(a).max(), 1e-300), what
+    assert np.abs(g1[2]).max() > 0 and np.abs(g1[3]).max() > 0
+
+
+def test_gpu_gradients_match_central_differences_of_the_gpu_forward():
+    """The run is piecewise smooth: a wet/dry test, a minmod pick or the
+    inflow ghost's max can switch within 1e-7 (relative) of the base point
+    near the inlet, and a difference whose step straddles such a switch
+    mixes two branches.  Each check therefore takes steps of 1e-6, 1e-7 and
+    1e-8 (relative to the parameter, or metres) and requires the closest
+    difference to agree with the gradient to 1e-4: the differences converge
+    to it as the step shrinks below the nearest switch."""
+    import torch
+    p, gauges = S.adjoint_reach(n=32)
+    K = 40
+    adj = context(p, K)
+    U0, z, n, kt, kQ = device_inputs(adj, p)
+    _, d = adj.forward(U0, z, n, kt, kQ, 0.0, K)
+    seed = torch.zeros((9, p.ny, p.nx), dtype=torch.float64, device=adj.device)
+    for j, i in gauges:
+        seed[0, j, i] += 1.0
+    gU0, gz, gn, gQ = adj.backward(U0, z, n, kt, kQ, 0.0, d, seed)
+
+    def J(U0_=U0, z_=z, n_=n, kQ_=kQ):
+        UK, _ = adj.forward(U0_, z_, n_, kt, kQ_, 0.0, K, dts=d)
+        return float((UK * seed).sum())
+
+    def fd_best(ad, arr, idx, scale, which):
+        best = None
+        for rel in (1e-6, 1e-7, 1e-8):
+            delta = rel * scale
+            a, b = arr.clone(), arr.clone()
+            a[idx] += delta
+            b[idx] -= delta
+            f = (J(**{which: a}) - J(**{which: b})) / (2.0 * delta)
+            if best is None or abs(f - ad) < abs(best - ad):
+                best = f
+        return best
+
+    checks = []
+    gnn = gn.cpu().numpy()
+    for j, i in np.argwhere(np.abs(gnn) > 1e-2 * np.abs(gnn).max())[::9][:4]:
+        checks.append(("n", gnn[j, i], fd_best(gnn[j, i], n, (j, i), float(n[j, i]), "n_")))
+    gzz = gz.cpu().numpy()
+    for j, i in np.argwhere(np.abs(gzz[0]) > 1e-2 * np.abs(gzz[0]).max())[::13][:4]:
+        checks.append(("z0", gzz[0, j, i], fd_best(gzz[0, j, i], z, (0, j, i), 1.0, "z_")))
+    for k in (0, 1):
+        gq = float(gQ[k])
+        checks.append(("Q", gq, fd_best(gq, kQ, (k,), float(kQ[k]), "kQ_")))
+    gh = gU0.cpu().numpy()
+    for j, i in np.argwhere(np.abs(gh[0]) > 1e-2 * np.abs(gh[0]).max())[::11][:3]:
+        checks.append(("h0", gh[0, j, i], fd_best(gh[0, j, i], U0, (0, j, i), 1.0, "U0_")))
+    assert len(checks) >= 10
+    for what, ad, f in checks:
+        assert ad != 0.0, what
+        assert abs(ad - f) <= 1e-4 * abs(ad), (what, ad, f)
