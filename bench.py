@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="instead: the batched ensemble of this many seeded valleys (sides 256-1024)")
     ap.add_argument("--no-tune", action="store_true", help="ensemble: keep the default launch shapes")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the FP64 DG2 adjoint: one checkpoint segment forward and backward")
+    ap.add_argument("--adjoint-steps", type=int, default=200, help="adjoint: steps per checkpoint segment")
     ap.add_argument("--scheme", default="dg2", choices=["dg2", "fv1", "acc"],
                     help="solver: DG2 (MWDG2, the headline), FV1 (HWFV1 on the adaptive grid) or ACC "
                          "(static graded grid from the same MRA of the topography)")
@@ -450,8 +453,104 @@ def run_ensemble(args):
                            "what": "the same steps with members queued one after another"}}
 
 
+def run_adjoint(args):
+    """Differentiable DG2 (FP64 discrete adjoint, uniform grid): the squared
+    depth misfit at 16 seeded gauge cells after one checkpoint segment of
+    --adjoint-steps steps on the n x n valley (seed 1, with a flowing start and
+    a 60-knot hydrograph), differentiated with respect to Manning n, the bed
+    planes, the knots and the initial state.  Timed with CUDA events on the
+    library's stream: the segment's forward sweep (CFL steps recorded) and its
+    backward sweep (recomputation from the checkpoint, then the reverse
+    kernels).  One unit = one cell carried through one step forward and back."""
+    import torch
+    from paper_2107_02750_gb300 import synth as S
+    from paper_2107_02750_gb300.adjoint import Dg2Adjoint, dg2_run
+    K = args.adjoint_steps
+    p, gauges = S.adjoint_reach(n=args.n, crop_of=args.n)
+    adj = Dg2Adjoint(p.nx, p.ny, p.dx, cfl=p.cfl, dt_max=p.dt_max, limiter=p.limiter, bc=tuple(p.bc),
+                     inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, max_steps=K)
+    dev = adj.device
+    f64 = dict(dtype=torch.float64, device=dev)
+    U0 = torch.cat([adj.project(p.h_vert), adj.project(p.qx_vert), adj.project(p.qy_vert)])
+    z = adj.project(p.z_vert)
+    n = torch.tensor(p.n_cell(), **f64)
+    kt, kQ = torch.tensor(p.inflow_t, **f64), torch.tensor(p.inflow_Q, **f64)
+    gj = torch.tensor(gauges[:, 0], device=dev)
+    gi = torch.tensor(gauges[:, 1], device=dev)
+    h_obs = U0[0, gj, gi] + 0.05   # synthetic observations
+
+    def segment(steps):
+        leaves = [x.clone().requires_grad_(True) for x in (U0, z, n, kQ)]
+        UK, d, t = dg2_run(adj, leaves[0], leaves[1], leaves[2], leaves[3], kt, 0.0, steps)
+        return leaves, ((UK[0, gj, gi] - h_obs) ** 2).sum(), t
+
+    for _ in range(max(3, args.warmup)):
+        leaves, J, _ = segment(min(K, 20))
+        J.backward()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with Clocks(dev.index) as clk:
+        ev[0].record()
+        leaves, J, t_seg = segment(K)
+        ev[1].record()
+        J.backward()
+        ev[2].record()
+        torch.cuda.synchronize()
+    ms_f, ms_b = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    cells = p.nx * p.ny
+    grads = {k: float(x.grad.abs().max()) for k, x in zip(("U0", "z", "n", "Q"), leaves)}
+    cb = None
+    if not args.no_cpu:
+        cb = adjoint_cpu_baseline(args.n)
+    return {"metric": "DG2 adjoint cell-steps/s (forward + reverse sweep of one checkpoint segment, FP64)",
+            "value": cells * K / ((ms_f + ms_b) * 1e-3), "unit": "cell-steps/s", "n_gpus": 1, "steps": K,
+            "warmup": max(3, args.warmup), "ms_per_step": (ms_f + ms_b) / K, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"DG2 adjoint, {p.nx}x{p.ny} uniform valley (seed 1), dx=10 m, flowing start, "
+                                   f"60-knot hydrograph, 16 gauges, squared depth misfit, segment {K} steps",
+                       "inputs": "tape and state arrays far larger than L2"},
+            "forward_ms": ms_f, "backward_ms": ms_b, "simulated_s": t_seg,
+            "max_abs_grad": grads, "gpu_launches": 29 * K + 3, "clocks": clk.summary(), "cpu_baseline": cb}
+
+
+def adjoint_cpu_baseline(n_full, budget_s=10.0):
+    """The adjoint oracle (PyTorch CPU autograd over the restated step) on a
+    64 x 64 crop of the same valley, as many steps as fit the budget."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import torch
+    import oracle as O
+    from oracle import dg2_adjoint as A
+    from paper_2107_02750_gb300 import synth as S
+    from util import oracle_sim
+    p, gauges = S.adjoint_reach(n=64, crop_of=n_full)
+    s = oracle_sim(p)
+    _, _, _, co = s.leaves()
+    U0 = co.T.reshape(9, p.ny, p.nx).copy()
+    z = s.z_level(0)[0].reshape(3, p.ny, p.nx)
+    P = A.Grid(nx=p.nx, ny=p.ny, dx=p.dx, limiter=p.limiter, bc=tuple(p.bc), inflow_edge=p.inflow_edge,
+               inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, knot_t=list(map(float, p.inflow_t)))
+    seed = np.zeros((9, p.ny, p.nx))
+    for j, i in gauges:
+        seed[0, j, i] = 1.0
+    K, spent = 5, 0.0
+    while True:
+        dts = [s.step() for _ in range(K)]
+        t0 = time.perf_counter()
+        A.gradients(U0, z, p.n_cell(), p.inflow_Q, dts, 0.0, P, seed)
+        spent = time.perf_counter() - t0
+        if spent > budget_s / 4 or K >= 80:
+            break
+        s = oracle_sim(p)
+        K *= 2
+    return {"value": p.nx * p.ny * K / spent, "unit": "cell-steps/s", "cores": torch.get_num_threads(),
+            "kind": "oracle", "sample": f"64x64 crop, {K} steps, forward + autograd reverse"}
+
+
 def main():
     args = parse()
+    if args.adjoint:
+        print(json.dumps(run_adjoint(args)))
+        return
     if args.scheme != "dg2":  # the other solvers: throughput line only
         args.no_fp64 = True
         args.no_cpu = True

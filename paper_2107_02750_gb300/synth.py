@@ -321,16 +321,24 @@ def crop(p: Problem, i0: int, j0: int, nx: int, ny: int, L: int) -> Problem:
 
 def adjoint_reach(n: int = 64, dx: float = 10.0, seed: int = 5, knots: int = 60, t_span: float = 3600.0,
                   n_gauges: int = 16, depth0: float = 1.0, relief: float = 10.0, q_unit: float = 1.0,
-                  n_mean: float = 0.035) -> tuple:
-    """Gradient workload: an n x n uniform grid of the valley terrain (seeded)
-    with a 4-cell channel holding about depth0 metres of flowing water over
-    each column's lowest point, an open east edge, a piecewise-linear inflow hydrograph of
-    `knots` seeded positive knots over t_span seconds (unit discharge around
-    q_unit) and a spatially varying Manning n (n_mean +- 30 %).  Returns
-    (problem, gauges), gauges an (n_gauges, 2) array of (j, i) cells drawn
-    from the initially wet ones."""
-    p = valley(n=n, dx=dx, seed=seed, L=0, relief=relief, channel_width=4.0 * dx, channel_depth=2.0,
-               mode=UNIFORM, t_end=t_span)
+                  n_mean: float = 0.035, crop_of: int = 0) -> tuple:
+    """Gradient workload: an n x n uniform grid of valley terrain with a channel
+    holding about depth0 metres of flowing water over each column's lowest
+    point, an open east edge, a piecewise-linear inflow hydrograph of `knots`
+    seeded positive knots over t_span seconds (unit discharge around q_unit)
+    and a spatially varying Manning n (n_mean +- 30 %).  The terrain is a small
+    valley of its own (seed `seed`, `relief` metres, 4-cell channel), or with
+    crop_of = N the n x n window at the inlet of the N x N valley (seed 1,
+    30 m relief, 40 m channel).  Returns (problem, gauges), gauges an
+    (n_gauges, 2) array of (j, i) cells drawn from the initially wet ones."""
+    if crop_of:
+        big = valley(n=crop_of, dx=dx, seed=1, L=0, mode=UNIFORM, t_end=t_span)
+        mid = (big.inflow_c0 + big.inflow_c1) // 2
+        j0 = int(min(max(mid - n // 2, 0), crop_of - n))
+        p = crop(big, 0, j0, n, n, 0)
+    else:
+        p = valley(n=n, dx=dx, seed=seed, L=0, relief=relief, channel_width=4.0 * dx, channel_depth=2.0,
+                   mode=UNIFORM, t_end=t_span)
     rng = np.random.Generator(np.random.PCG64(seed))
     z = p.z_vert
     # a flowing start: a rippled free surface over the channel and a seeded
