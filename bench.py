@@ -454,63 +454,75 @@ def run_ensemble(args):
 
 
 def run_adjoint(args):
-    """Differentiable DG2 (FP64 discrete adjoint, uniform grid): the squared
-    depth misfit at 16 seeded gauge cells after one checkpoint segment of
+    """Differentiable DG2 (discrete adjoint, uniform grid): the squared depth
+    misfit at 16 seeded gauge cells after one checkpoint segment of
     --adjoint-steps steps on the n x n valley (seed 1, with a flowing start and
     a 60-knot hydrograph), differentiated with respect to Manning n, the bed
-    planes, the knots and the initial state.  Timed with CUDA events on the
-    library's stream: the segment's forward sweep (CFL steps recorded) and its
-    backward sweep (recomputation from the checkpoint, then the reverse
-    kernels).  One unit = one cell carried through one step forward and back."""
+    planes, the knots and the initial state, in FP32 (the line's value) and in
+    FP64 (the bit-exact reference path, reported beside it).  Timed with CUDA
+    events on the library's stream: the segment's forward sweep (CFL steps
+    recorded) and its backward sweep (recomputation from the checkpoint, then
+    the reverse kernels).  One unit = one cell carried through one step forward
+    and back."""
     import torch
+    import paper_2107_02750_gb300 as M
     from paper_2107_02750_gb300 import synth as S
     from paper_2107_02750_gb300.adjoint import Dg2Adjoint, dg2_run
     K = args.adjoint_steps
     p, gauges = S.adjoint_reach(n=args.n, crop_of=args.n)
-    adj = Dg2Adjoint(p.nx, p.ny, p.dx, cfl=p.cfl, dt_max=p.dt_max, limiter=p.limiter, bc=tuple(p.bc),
-                     inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, max_steps=K)
-    dev = adj.device
-    f64 = dict(dtype=torch.float64, device=dev)
-    U0 = torch.cat([adj.project(p.h_vert), adj.project(p.qx_vert), adj.project(p.qy_vert)])
-    z = adj.project(p.z_vert)
-    n = torch.tensor(p.n_cell(), **f64)
-    kt, kQ = torch.tensor(p.inflow_t, **f64), torch.tensor(p.inflow_Q, **f64)
-    gj = torch.tensor(gauges[:, 0], device=dev)
-    gi = torch.tensor(gauges[:, 1], device=dev)
-    h_obs = U0[0, gj, gi] + 0.05   # synthetic observations
-
-    def segment(steps):
-        leaves = [x.clone().requires_grad_(True) for x in (U0, z, n, kQ)]
-        UK, d, t = dg2_run(adj, leaves[0], leaves[1], leaves[2], leaves[3], kt, 0.0, steps)
-        return leaves, ((UK[0, gj, gi] - h_obs) ** 2).sum(), t
-
-    for _ in range(max(3, args.warmup)):
-        leaves, J, _ = segment(min(K, 20))
-        J.backward()
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    with Clocks(dev.index) as clk:
-        ev[0].record()
-        leaves, J, t_seg = segment(K)
-        ev[1].record()
-        J.backward()
-        ev[2].record()
-        torch.cuda.synchronize()
-    ms_f, ms_b = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     cells = p.nx * p.ny
-    grads = {k: float(x.grad.abs().max()) for k, x in zip(("U0", "z", "n", "Q"), leaves)}
-    cb = None
-    if not args.no_cpu:
-        cb = adjoint_cpu_baseline(args.n)
-    return {"metric": "DG2 adjoint cell-steps/s (forward + reverse sweep of one checkpoint segment, FP64)",
-            "value": cells * K / ((ms_f + ms_b) * 1e-3), "unit": "cell-steps/s", "n_gpus": 1, "steps": K,
-            "warmup": max(3, args.warmup), "ms_per_step": (ms_f + ms_b) / K, "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic",
+
+    def measure(precision):
+        adj = Dg2Adjoint(p.nx, p.ny, p.dx, cfl=p.cfl, dt_max=p.dt_max, limiter=p.limiter, bc=tuple(p.bc),
+                         inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, max_steps=K,
+                         precision=precision)
+        dev = adj.device
+        U0 = torch.cat([adj.project(p.h_vert), adj.project(p.qx_vert), adj.project(p.qy_vert)])
+        z = adj.project(p.z_vert)
+        n = torch.tensor(p.n_cell(), dtype=adj.dtype, device=dev)
+        kt = torch.tensor(p.inflow_t, dtype=torch.float64, device=dev)
+        kQ = torch.tensor(p.inflow_Q, dtype=torch.float64, device=dev)
+        gj = torch.tensor(gauges[:, 0], device=dev)
+        gi = torch.tensor(gauges[:, 1], device=dev)
+        h_obs = U0[0, gj, gi] + 0.05   # synthetic observations
+
+        def segment(steps):
+            leaves = [x.clone().requires_grad_(True) for x in (U0, z, n, kQ)]
+            UK, d, t = dg2_run(adj, leaves[0], leaves[1], leaves[2], leaves[3], kt, 0.0, steps)
+            return leaves, ((UK[0, gj, gi] - h_obs) ** 2).sum(), t
+
+        for _ in range(max(3, args.warmup)):
+            leaves, J, _ = segment(min(K, 20))
+            J.backward()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with Clocks(dev.index) as clk:
+            ev[0].record()
+            leaves, J, t_seg = segment(K)
+            ev[1].record()
+            J.backward()
+            ev[2].record()
+            torch.cuda.synchronize()
+        ms_f, ms_b = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        grads = {k: float(x.grad.abs().max()) for k, x in zip(("U0", "z", "n", "Q"), leaves)}
+        return {"value": cells * K / ((ms_f + ms_b) * 1e-3), "ms_per_step": (ms_f + ms_b) / K,
+                "forward_ms": ms_f, "backward_ms": ms_b, "simulated_s": t_seg, "max_abs_grad": grads,
+                "clocks": clk.summary()}
+
+    r32 = measure(M.F32)
+    r64 = None if args.no_fp64 else measure(M.F64)
+    cb = None if args.no_cpu else adjoint_cpu_baseline(args.n)
+    line = {"metric": "DG2 adjoint cell-steps/s (forward + reverse sweep of one checkpoint segment)",
+            "value": r32["value"], "unit": "cell-steps/s", "n_gpus": 1, "steps": K,
+            "warmup": max(3, args.warmup), "ms_per_step": r32["ms_per_step"], "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"DG2 adjoint, {p.nx}x{p.ny} uniform valley (seed 1), dx=10 m, flowing start, "
                                    f"60-knot hydrograph, 16 gauges, squared depth misfit, segment {K} steps",
                        "inputs": "tape and state arrays far larger than L2"},
-            "forward_ms": ms_f, "backward_ms": ms_b, "simulated_s": t_seg,
-            "max_abs_grad": grads, "gpu_launches": 29 * K + 3, "clocks": clk.summary(), "cpu_baseline": cb}
+            "forward_ms": r32["forward_ms"], "backward_ms": r32["backward_ms"], "simulated_s": r32["simulated_s"],
+            "max_abs_grad": r32["max_abs_grad"], "gpu_launches": 29 * K + 3, "clocks": r32["clocks"],
+            "fp64": r64, "cpu_baseline": cb}
+    return line
 
 
 def adjoint_cpu_baseline(n_full, budget_s=10.0):

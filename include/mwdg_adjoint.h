@@ -1,6 +1,6 @@
 /*
  * mwdg_adjoint.h -- C ABI of the discrete adjoint of the uniform-grid DG2
- * step (GB300, sm_103a, FP64).
+ * step (GB300, sm_103a; FP64 and FP32).
  *
  * The step is the DG2 shallow-water step of Sharifian & Kesserwani, arXiv
  * 2107.02750, Sect. 2.1.1 (Eq. 1-4) on a uniform grid of nx x ny cells:
@@ -21,9 +21,15 @@
  * the step is not differentiable (still water, where the limiter's
  * differences vanish) the derivative is that of the branch taken.
  *
- * Layout (device memory, FP64, caller-owned):
- *   U   9 x n, component-major: component m of cell k = j nx + i at
- *       U[m n + k]; components (h0, h1x, h1y, qx0, qx1x, qx1y, qy0, qy1x,
+ * Precision (mwdg_adj_params.precision): MWDG_F64 runs every cell in FP64
+ * and reproduces the solver's FP64 step bit for bit; MWDG_F32 runs the cells
+ * in FP32 (depth form) with time, time steps, the hydrograph and its
+ * gradient in FP64.  "Coefficient arrays" below are double for MWDG_F64 and
+ * float for MWDG_F32; time steps, knots and gQ are double in both.
+ *
+ * Layout (device memory, caller-owned):
+ *   U   9 x n coefficient array, component-major: component m of cell
+ *       k = j nx + i at U[m n + k]; components (h0, h1x, h1y, qx0, qx1x, qx1y, qy0, qy1x,
  *       qy1y), the average and the two scaled-Legendre slope coefficients
  *       of depth and unit discharges (Eq. 2-3);
  *   z   3 x n, the bed planes (z0, z1x, z1y) in the same layout;
@@ -35,9 +41,9 @@
  *
  * Work is queued on the given CUDA stream (NULL: the legacy default stream);
  * no call synchronises it, except mwdg_adj_create and mwdg_adj_destroy.  A
- * context holds a tape of max_steps + 1 states (9 n doubles each) and about
- * 130 n doubles of work arrays; one host thread uses it at a time, and its
- * calls on one stream run in order.  Statuses are those of mwdg.h.
+ * context holds a tape of max_steps + 1 states (9 n coefficients each) and
+ * about 130 n coefficients of work arrays; one host thread uses it at a
+ * time, and its calls on one stream run in order.  Statuses are those of mwdg.h.
  */
 #ifndef MWDG_ADJOINT_H
 #define MWDG_ADJOINT_H
@@ -63,10 +69,11 @@ typedef struct {
   int32_t inflow_c0, inflow_c1; /* cells along that edge, inclusive          */
   double rain_rate, rain_t_end; /* m/s while t < rain_t_end                  */
   int32_t max_steps;       /* tape capacity: steps per forward/backward call */
+  int32_t precision;       /* MWDG_F64 or MWDG_F32                           */
 } mwdg_adj_params;
 
 /* Defaults: g = 9.80665, h_dry = 1e-3, cfl = 0.33, dt_max = 1, limiter on,
- * walls, no inflow, no rain, max_steps = 200; nx, ny, dx must be set. */
+ * walls, no inflow, no rain, max_steps = 200, FP64; nx, ny, dx must be set. */
 MWDG_API mwdg_status mwdg_adj_params_default(mwdg_adj_params *p);
 
 /* Allocates the context on the current device.  MWDG_ERR_DIMS when nx or ny
@@ -75,17 +82,18 @@ MWDG_API mwdg_status mwdg_adj_params_default(mwdg_adj_params *p);
 MWDG_API mwdg_status mwdg_adj_create(const mwdg_adj_params *p, mwdg_adj **out);
 MWDG_API void mwdg_adj_destroy(mwdg_adj *a);
 
-/* Eq. 8: vertex raster (ny+1) x (nx+1) -> planes out (3 x n), on the device. */
-MWDG_API mwdg_status mwdg_adj_project(mwdg_adj *a, const double *vert, double *out, void *cuda_stream);
+/* Eq. 8: vertex raster (ny+1) x (nx+1), double -> planes out (3 x n
+ * coefficient array), on the device; computed in FP64. */
+MWDG_API mwdg_status mwdg_adj_project(mwdg_adj *a, const double *vert, void *out, void *cuda_stream);
 
 /* Forward run of `steps` steps from U0 at time t0 (all device pointers).
  * fixed_dt = 0: each dt from the CFL condition, written to dts[0..steps);
  * fixed_dt = 1: the steps dts[0..steps) are read.  U_out receives U_K (it
  * may alias U0).  MWDG_ERR_CAPACITY when steps > max_steps; MWDG_ERR_ARG on
  * NULL pointers, steps < 0, or nknots < 1 with an inflow edge. */
-MWDG_API mwdg_status mwdg_adj_forward(mwdg_adj *a, const double *U0, const double *z, const double *n,
+MWDG_API mwdg_status mwdg_adj_forward(mwdg_adj *a, const void *U0, const void *z, const void *n,
                                       int32_t nknots, const double *knot_t, const double *knot_Q, double t0,
-                                      int32_t steps, int32_t fixed_dt, double *dts, double *U_out,
+                                      int32_t steps, int32_t fixed_dt, double *dts, void *U_out,
                                       void *cuda_stream);
 
 /* Vector-Jacobian product of the run over the time steps dts[0..steps) from
@@ -94,14 +102,14 @@ MWDG_API mwdg_status mwdg_adj_forward(mwdg_adj *a, const double *U0, const doubl
  * several segments accumulate.  The run's states are recomputed from U0
  * into the tape (the segment's checkpoint is U0 itself).  gU0 may alias
  * gU_K.  Errors as mwdg_adj_forward. */
-MWDG_API mwdg_status mwdg_adj_backward(mwdg_adj *a, const double *U0, const double *z, const double *n,
+MWDG_API mwdg_status mwdg_adj_backward(mwdg_adj *a, const void *U0, const void *z, const void *n,
                                        int32_t nknots, const double *knot_t, const double *knot_Q, double t0,
-                                       int32_t steps, const double *dts, const double *gU_K, double *gU0,
-                                       double *gz, double *gn, double *gQ, void *cuda_stream);
+                                       int32_t steps, const double *dts, const void *gU_K, void *gU0,
+                                       void *gz, void *gn, double *gQ, void *cuda_stream);
 
 /* Transpose of Eq. 8: plane cotangents (3 x n) -> vertex cotangents
- * ((ny+1) x (nx+1)), overwritten. */
-MWDG_API mwdg_status mwdg_adj_project_transpose(mwdg_adj *a, const double *g_planes, double *g_vert,
+ * ((ny+1) x (nx+1)), both coefficient arrays, overwritten. */
+MWDG_API mwdg_status mwdg_adj_project_transpose(mwdg_adj *a, const void *g_planes, void *g_vert,
                                                 void *cuda_stream);
 
 /* Description of the context's most recent failure ("" if none). */

@@ -1,7 +1,8 @@
 """Binding of the DG2 adjoint (include/mwdg_adjoint.h) and its autograd form.
 
 Argument marshalling only: the forward and reverse sweeps run in the
-library's CUDA kernels.  Tensors are FP64 on the CUDA device, contiguous:
+library's CUDA kernels.  Tensors are on the CUDA device, contiguous, FP64 for
+an F64 context and FP32 for an F32 one (time steps and knots FP64 in both):
 U (9, ny, nx) in the component order (h0, h1x, h1y, qx0, qx1x, qx1y, qy0,
 qy1x, qy1y), bed planes z (3, ny, nx), Manning n (ny, nx), hydrograph knots
 (k,).  Work is queued on torch's current CUDA stream.
@@ -16,7 +17,7 @@ from __future__ import annotations
 
 import ctypes as C
 
-from .binding import MwdgError, lib as _lib, WALL
+from .binding import MwdgError, lib as _lib, WALL, F64, F32
 
 ADJ_EXPORTS = (
     "mwdg_adj_params_default", "mwdg_adj_create", "mwdg_adj_destroy", "mwdg_adj_project",
@@ -30,6 +31,7 @@ class AdjParams(C.Structure):
         ("cfl", C.c_double), ("dt_max", C.c_double), ("limiter", C.c_int32), ("bc", C.c_int32 * 4),
         ("inflow_edge", C.c_int32), ("inflow_c0", C.c_int32), ("inflow_c1", C.c_int32),
         ("rain_rate", C.c_double), ("rain_t_end", C.c_double), ("max_steps", C.c_int32),
+        ("precision", C.c_int32),
     ]
 
 
@@ -68,7 +70,7 @@ class Dg2Adjoint:
 
     def __init__(self, nx, ny, dx, *, g=9.80665, h_dry=1e-3, cfl=0.33, dt_max=1.0, limiter=1,
                  bc=(WALL, WALL, WALL, WALL), inflow_edge=-1, inflow_c0=0, inflow_c1=-1, rain_rate=0.0,
-                 rain_t_end=0.0, max_steps=200):
+                 rain_t_end=0.0, max_steps=200, precision=F64):
         import torch
         if not torch.cuda.is_available():
             raise MwdgError(-3, "Dg2Adjoint", "no CUDA device")
@@ -80,6 +82,7 @@ class Dg2Adjoint:
             p.bc[e] = bc[e]
         p.inflow_edge, p.inflow_c0, p.inflow_c1 = inflow_edge, inflow_c0, inflow_c1
         p.rain_rate, p.rain_t_end, p.max_steps = rain_rate, rain_t_end, max_steps
+        p.precision = precision
         h = C.c_void_p()
         st = L.mwdg_adj_create(C.byref(p), C.byref(h))
         if st != 0:
@@ -88,6 +91,7 @@ class Dg2Adjoint:
         self.p = p
         self.nx, self.ny, self.dx, self.max_steps = nx, ny, dx, max_steps
         self.device = torch.device("cuda", torch.cuda.current_device())
+        self.dtype = torch.float32 if precision == F32 else torch.float64
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -99,9 +103,9 @@ class Dg2Adjoint:
         if st != 0:
             raise MwdgError(st, where, lib().mwdg_adj_last_error(self._h).decode())
 
-    def _t(self, a, shape=None):
+    def _t(self, a, shape=None, dtype=None):
         import torch
-        t = torch.as_tensor(a, dtype=torch.float64, device=self.device).contiguous()
+        t = torch.as_tensor(a, dtype=dtype or self.dtype, device=self.device).contiguous()
         if shape is not None and tuple(t.shape) != tuple(shape):
             raise MwdgError(-1, "Dg2Adjoint", f"shape {tuple(t.shape)}, expected {tuple(shape)}")
         return t
@@ -109,8 +113,8 @@ class Dg2Adjoint:
     def project(self, vert):
         """Eq. 8: (ny+1, nx+1) vertex raster -> planes (3, ny, nx)."""
         import torch
-        v = self._t(vert, (self.ny + 1, self.nx + 1))
-        out = torch.empty((3, self.ny, self.nx), dtype=torch.float64, device=self.device)
+        v = self._t(vert, (self.ny + 1, self.nx + 1), torch.float64)
+        out = torch.empty((3, self.ny, self.nx), dtype=self.dtype, device=self.device)
         self._check(lib().mwdg_adj_project(self._h, _ptr(v), _ptr(out), _stream()), "mwdg_adj_project")
         return out
 
@@ -118,17 +122,18 @@ class Dg2Adjoint:
         """cotangents of the planes (3, ny, nx) -> of the vertex raster"""
         import torch
         gp = self._t(g_planes, (3, self.ny, self.nx))
-        out = torch.empty((self.ny + 1, self.nx + 1), dtype=torch.float64, device=self.device)
+        out = torch.empty((self.ny + 1, self.nx + 1), dtype=self.dtype, device=self.device)
         self._check(lib().mwdg_adj_project_transpose(self._h, _ptr(gp), _ptr(out), _stream()),
                     "mwdg_adj_project_transpose")
         return out
 
     def _common(self, U0, z, n, knot_t, knot_Q):
+        import torch
         U0 = self._t(U0, (9, self.ny, self.nx))
         z = self._t(z, (3, self.ny, self.nx))
         n = self._t(n, (self.ny, self.nx))
-        kt = self._t(knot_t) if knot_t is not None else None
-        kQ = self._t(knot_Q) if knot_Q is not None else None
+        kt = self._t(knot_t, dtype=torch.float64) if knot_t is not None else None
+        kQ = self._t(knot_Q, dtype=torch.float64) if knot_Q is not None else None
         nk = 0 if kt is None else int(kt.numel())
         if kQ is not None and int(kQ.numel()) != nk:
             raise MwdgError(-1, "Dg2Adjoint", "knot_t and knot_Q differ in length")
@@ -140,8 +145,8 @@ class Dg2Adjoint:
         import torch
         U0, z, n, kt, kQ, nk = self._common(U0, z, n, knot_t, knot_Q)
         fixed = dts is not None
-        d = self._t(dts, (steps,)) if fixed else torch.empty(max(1, steps), dtype=torch.float64,
-                                                              device=self.device)
+        d = self._t(dts, (steps,), torch.float64) if fixed else torch.empty(max(1, steps), dtype=torch.float64,
+                                                                             device=self.device)
         out = torch.empty_like(U0)
         st = lib().mwdg_adj_forward(self._h, _ptr(U0), _ptr(z), _ptr(n), nk, _ptr(kt), _ptr(kQ), float(t0),
                                     int(steps), int(fixed), _ptr(d), _ptr(out), _stream())
@@ -153,7 +158,7 @@ class Dg2Adjoint:
         that of U_K, over the steps dts from U0 at t0."""
         import torch
         U0, z, n, kt, kQ, nk = self._common(U0, z, n, knot_t, knot_Q)
-        d = self._t(dts)
+        d = self._t(dts, dtype=torch.float64)
         g = self._t(gUK, (9, self.ny, self.nx))
         gU0 = torch.empty_like(U0)
         gz = torch.zeros_like(z)

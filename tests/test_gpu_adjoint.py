@@ -10,7 +10,11 @@ against the FP64 oracle (oracle/dg2_adjoint.py, pinned on the CPU).
   * two checkpointed segments chained by autograd give the one-segment
     gradients;
   * central differences of the GPU forward (time steps held), with steps
-    shrinking to 1e-8, converge to the GPU gradients (1e-4 relative).
+    shrinking to 1e-8, converge to the GPU gradients (1e-4 relative);
+  * the FP32 adjoint tracks the FP64 oracle: time steps to 1e-5, depths to
+    1e-4 m, gradients correlated above 0.999 with 99 % of entries within 2 %
+    of the array's largest and none beyond 5 % (wet/dry tests that FP32
+    rounding flips move single cells).
 """
 from dataclasses import replace
 
@@ -38,11 +42,11 @@ def state(sim, p):
     return co.T.reshape(9, p.ny, p.nx).copy()
 
 
-def context(p, max_steps):
+def context(p, max_steps, precision=0):
     from paper_2107_02750_gb300.adjoint import Dg2Adjoint
     return Dg2Adjoint(p.nx, p.ny, p.dx, cfl=p.cfl, dt_max=p.dt_max, limiter=p.limiter, bc=tuple(p.bc),
                       inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1,
-                      rain_rate=p.rain_rate, rain_t_end=p.rain_t_end, max_steps=max_steps)
+                      rain_rate=p.rain_rate, rain_t_end=p.rain_t_end, max_steps=max_steps, precision=precision)
 
 
 def device_inputs(adj, p):
@@ -50,7 +54,7 @@ def device_inputs(adj, p):
     import torch
     U0 = torch.cat([adj.project(p.h_vert), adj.project(p.qx_vert), adj.project(p.qy_vert)])
     z = adj.project(p.z_vert)
-    n = torch.tensor(p.n_cell(), dtype=torch.float64, device=adj.device)
+    n = torch.tensor(p.n_cell(), dtype=adj.dtype, device=adj.device)
     if p.inflow_edge >= 0:
         kt = torch.tensor(p.inflow_t, dtype=torch.float64, device=adj.device)
         kQ = torch.tensor(p.inflow_Q, dtype=torch.float64, device=adj.device)
@@ -229,3 +233,38 @@ def test_gauge_misfit_gradient_descends():
     step = 1e-3 * float(n.abs().max()) / float(g.abs().max())
     J1, _ = run(n - step * g)
     assert float(J1) < float(J0), (float(J1), float(J0))
+
+
+@pytest.mark.parametrize("name,p,K", CASES, ids=[c[0] for c in CASES])
+def test_f32_adjoint_tracks_the_fp64_oracle(name, p, K):
+    import torch
+    s = oracle_sim(p)
+    U0o = state(s, p)
+    zo = s.z_level(0)[0].reshape(3, p.ny, p.nx)
+    dts = [s.step() for _ in range(K)]
+    want = state(s, p)
+    seed = np.random.default_rng(11).standard_normal((9, p.ny, p.nx))
+    Q = p.inflow_Q if p.inflow_edge >= 0 else np.zeros(1)
+    G = A.gradients(U0o, zo, p.n_cell(), Q, dts, 0.0, grid_of(p), seed)
+    adj = context(p, K, precision=1)
+    U0, z, n, kt, kQ = device_inputs(adj, p)
+    assert U0.dtype == torch.float32
+    UK, d = adj.forward(U0, z, n, kt, kQ, 0.0, K)
+    assert np.abs(d.cpu().numpy() - np.array(dts)).max() <= 1e-5 * max(dts)
+    assert np.abs(UK[0].double().cpu().numpy() - want[0]).max() <= 1e-4
+    d64 = torch.tensor(dts, dtype=torch.float64, device=adj.device)
+    gU0, gz, gn, gQ = adj.backward(U0, z, n, kt, kQ, 0.0, d64, torch.tensor(seed, dtype=torch.float32,
+                                                                            device=adj.device))
+    pairs = [("U0", gU0, G["gU0"]), ("z", gz, G["gz"]), ("n", gn, G["gn"])]
+    if p.inflow_edge >= 0:
+        pairs.append(("Q", gQ, G["gQ"]))
+    for what, got, ref in pairs:
+        a = got.double().cpu().numpy()
+        scale = np.abs(ref).max()
+        if scale == 0.0:
+            assert np.abs(a).max() == 0.0, what
+            continue
+        err = np.abs(a - ref) / scale
+        assert err.max() <= 5e-2, (what, err.max())
+        assert np.quantile(err, 0.99) <= 2e-2, (what, np.quantile(err, 0.99))
+        assert np.corrcoef(a.ravel(), ref.ravel())[0, 1] >= 0.999, what
