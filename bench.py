@@ -472,7 +472,7 @@ def run_adjoint(args):
     p, gauges = S.adjoint_reach(n=args.n, crop_of=args.n)
     cells = p.nx * p.ny
 
-    def measure(precision):
+    def measure(precision, prof=False):
         adj = Dg2Adjoint(p.nx, p.ny, p.dx, cfl=p.cfl, dt_max=p.dt_max, limiter=p.limiter, bc=tuple(p.bc),
                          inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, max_steps=K,
                          precision=precision)
@@ -504,13 +504,25 @@ def run_adjoint(args):
             ev[2].record()
             torch.cuda.synchronize()
         ms_f, ms_b = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        times = None
+        if prof:
+            # the same segment again with a CUDA event pair around every
+            # launch group, for the per-kernel roofline (the events cost
+            # about 10 % of the segment, so the line's value is the run above)
+            adj.profile(40 * K + 64)
+            _, J2, _ = segment(K)
+            J2.backward()
+            torch.cuda.synchronize()
+            times = adj.kernel_times()
+            adj.profile(0)
         grads = {k: float(x.grad.abs().max()) for k, x in zip(("U0", "z", "n", "Q"), leaves)}
         return {"value": cells * K / ((ms_f + ms_b) * 1e-3), "ms_per_step": (ms_f + ms_b) / K,
                 "forward_ms": ms_f, "backward_ms": ms_b, "simulated_s": t_seg, "max_abs_grad": grads,
-                "clocks": clk.summary()}
+                "clocks": clk.summary(), "kernel_ms": times}
 
-    r32 = measure(M.F32)
+    r32 = measure(M.F32, prof=True)
     r64 = None if args.no_fp64 else measure(M.F64)
+    roof = adjoint_roofline(r32.pop("kernel_ms"), cells, 4)
     cb = None if args.no_cpu else adjoint_cpu_baseline(args.n)
     line = {"metric": "DG2 adjoint cell-steps/s (forward + reverse sweep of one checkpoint segment)",
             "value": r32["value"], "unit": "cell-steps/s", "n_gpus": 1, "steps": K,
@@ -521,8 +533,37 @@ def run_adjoint(args):
                        "inputs": "tape and state arrays far larger than L2"},
             "forward_ms": r32["forward_ms"], "backward_ms": r32["backward_ms"], "simulated_s": r32["simulated_s"],
             "max_abs_grad": r32["max_abs_grad"], "gpu_launches": 29 * K + 3, "clocks": r32["clocks"],
-            "fp64": r64, "cpu_baseline": cb}
+            "roofline": roof, "fp64": r64, "cpu_baseline": cb}
+    if r64 is not None:
+        r64.pop("kernel_ms", None)
     return line
+
+
+# algorithmic coefficients moved per cell by one launch of each adjoint kernel
+# class (reads + writes of unique data, neighbour re-reads not counted; the
+# two stages averaged where they differ; the interface class per cell covers
+# its two faces), and the bytes of the clip flags
+ADJ_VALUES_PER_CELL = {"friction": 19, "limit": 33, "update": 34.5, "cfl": 3, "rev_cell": 72, "rev_face": 56,
+                       "rev_limit": 68, "rev_gather": 32, "rev_friction": 30}
+ADJ_FLAG_BYTES = {"update": 1, "rev_cell": 1}
+# DRAM bytes (read + write) per launch measured by ncu for the FP32 adjoint
+# kernels at this workload, while the kernel is unchanged (see profiles/)
+ADJ_TRAFFIC = {"update": 89_190_000 + 11_490_000}  # ncu: one stage launch, dram read + write
+
+
+def adjoint_roofline(times, cells, elem):
+    """roofline of the adjoint kernel class with the largest time in the timed
+    segment: algorithmic bytes per launch / its mean event-timed duration"""
+    peak, src = peaks()
+    cls = max((c for c in times if c in ADJ_VALUES_PER_CELL), key=lambda c: times[c][0])
+    ms, cnt = times[cls]
+    per_launch = cells * (ADJ_VALUES_PER_CELL[cls] * elem + ADJ_FLAG_BYTES.get(cls, 0))
+    achieved = per_launch / (ms / cnt * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": cls, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": src, "traffic": ADJ_TRAFFIC.get(cls),
+            "bytes_per_launch": per_launch, "launches": cnt, "mean_ms": ms / cnt,
+            "share_of_segment": ms / sum(v[0] for v in times.values()),
+            "step_ms_by_class": {c: v[0] for c, v in times.items() if v[1]}}
 
 
 def adjoint_cpu_baseline(n_full, budget_s=10.0):

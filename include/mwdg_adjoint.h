@@ -112,6 +112,28 @@ MWDG_API mwdg_status mwdg_adj_backward(mwdg_adj *a, const void *U0, const void *
 MWDG_API mwdg_status mwdg_adj_project_transpose(mwdg_adj *a, const void *g_planes, void *g_vert,
                                                 void *cuda_stream);
 
+/* Per-kernel timing.  mwdg_adj_profile(a, L) with L > 0 records a pair of
+ * CUDA events around each of the next L launch groups (a group is one
+ * kernel, or the two interface kernels of a stage); L = 0 stops recording.
+ * It synchronises the device.  mwdg_adj_kernel_times waits for the recorded
+ * events, writes per class the summed milliseconds and the number of
+ * groups, and starts a new recording.  Classes, in order: */
+enum {
+  MWDG_ADJ_KC_CFL = 0,      /* CFL reduction and dt                         */
+  MWDG_ADJ_KC_FRICTION,     /* rain and friction                            */
+  MWDG_ADJ_KC_LIMIT,        /* stage-input limiting                         */
+  MWDG_ADJ_KC_UPDATE,       /* RK2 stage update                             */
+  MWDG_ADJ_KC_REV_CELL,     /* reverse: per-cell operator terms             */
+  MWDG_ADJ_KC_REV_FACE,     /* reverse: x and y interfaces                  */
+  MWDG_ADJ_KC_REV_KNOTS,    /* reverse: hydrograph knots                    */
+  MWDG_ADJ_KC_REV_LIMIT,    /* reverse: limiter                             */
+  MWDG_ADJ_KC_REV_GATHER,   /* reverse: limiter's neighbour terms           */
+  MWDG_ADJ_KC_REV_FRICTION, /* reverse: friction                            */
+  MWDG_ADJ_KC_COUNT
+};
+MWDG_API mwdg_status mwdg_adj_profile(mwdg_adj *a, int32_t max_launches);
+MWDG_API mwdg_status mwdg_adj_kernel_times(mwdg_adj *a, double *ms, int64_t *count);
+
 /* Description of the context's most recent failure ("" if none). */
 MWDG_API const char *mwdg_adj_last_error(const mwdg_adj *a);
 

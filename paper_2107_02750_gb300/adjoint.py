@@ -22,7 +22,11 @@ from .binding import MwdgError, lib as _lib, WALL, F64, F32
 ADJ_EXPORTS = (
     "mwdg_adj_params_default", "mwdg_adj_create", "mwdg_adj_destroy", "mwdg_adj_project",
     "mwdg_adj_project_transpose", "mwdg_adj_forward", "mwdg_adj_backward", "mwdg_adj_last_error",
+    "mwdg_adj_profile", "mwdg_adj_kernel_times",
 )
+# kernel classes of mwdg_adj_kernel_times, in order
+ADJ_CLASSES = ("cfl", "friction", "limit", "update", "rev_cell", "rev_face", "rev_knots", "rev_limit",
+               "rev_gather", "rev_friction")
 
 
 class AdjParams(C.Structure):
@@ -49,8 +53,11 @@ def lib():
         L.mwdg_adj_backward.argtypes = [vp, vp, vp, vp, i32, vp, vp, dp, i32, vp, vp, vp, vp, vp, vp, vp]
         L.mwdg_adj_last_error.argtypes = [vp]
         L.mwdg_adj_last_error.restype = C.c_char_p
+        L.mwdg_adj_profile.argtypes = [vp, i32]
+        L.mwdg_adj_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in ("mwdg_adj_params_default", "mwdg_adj_create", "mwdg_adj_project",
-                     "mwdg_adj_project_transpose", "mwdg_adj_forward", "mwdg_adj_backward"):
+                     "mwdg_adj_project_transpose", "mwdg_adj_forward", "mwdg_adj_backward",
+                     "mwdg_adj_profile", "mwdg_adj_kernel_times"):
             getattr(L, name).restype = C.c_int
         L._adj_ready = True
     return L
@@ -109,6 +116,18 @@ class Dg2Adjoint:
         if shape is not None and tuple(t.shape) != tuple(shape):
             raise MwdgError(-1, "Dg2Adjoint", f"shape {tuple(t.shape)}, expected {tuple(shape)}")
         return t
+
+    def profile(self, max_launches: int):
+        """time the next `max_launches` launch groups with CUDA events (0: stop)"""
+        self._check(lib().mwdg_adj_profile(self._h, int(max_launches)), "mwdg_adj_profile")
+
+    def kernel_times(self):
+        """{class: (milliseconds, launch groups)} since the last call"""
+        n = len(ADJ_CLASSES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        self._check(lib().mwdg_adj_kernel_times(self._h, ms, cnt), "mwdg_adj_kernel_times")
+        return {c: (ms[k], cnt[k]) for k, c in enumerate(ADJ_CLASSES)}
 
     def project(self, vert):
         """Eq. 8: (ny+1, nx+1) vertex raster -> planes (3, ny, nx)."""

@@ -37,6 +37,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -1088,6 +1089,10 @@ using namespace mwdg::adj;
 
 struct mwdg_adj {
   mwdg_adj_params p{};
+  // per-kernel timing: a pool of event pairs recorded around each launch
+  std::vector<cudaEvent_t> evs;
+  std::vector<int> ev_class;
+  size_t ev_used = 0;
   long long n = 0;
   size_t elem = 8;             // bytes per coefficient (8 FP64, 4 FP32)
   void *tape = nullptr;        // (max_steps + 1) x 9n: the state at the start of each step
@@ -1105,7 +1110,36 @@ struct mwdg_adj {
 
 namespace {
 
+void free_events(mwdg_adj *a) {
+  for (cudaEvent_t e : a->evs) cudaEventDestroy(e);
+  a->evs.clear();
+  a->ev_class.clear();
+  a->ev_used = 0;
+}
+
+// records an event pair around the launches of one scope when the profiler
+// is on and its pool has room
+struct Timed {
+  mwdg_adj *a;
+  cudaStream_t st;
+  size_t slot;
+  bool on;
+  Timed(mwdg_adj *a_, int cls, cudaStream_t st_) : a(a_), st(st_), slot(0), on(false) {
+    if (a->ev_used + 2 <= a->evs.size()) {
+      slot = a->ev_used;
+      a->ev_used += 2;
+      a->ev_class[slot / 2] = cls;
+      cudaEventRecord(a->evs[slot], st);
+      on = true;
+    }
+  }
+  ~Timed() {
+    if (on) cudaEventRecord(a->evs[slot + 1], st);
+  }
+};
+
 void free_all(mwdg_adj *a) {
+  free_events(a);
   void *ptrs[] = {a->tape, a->clip, a->tt, a->dtbuf, a->best, a->Un, a->Ui, a->W1, a->F1, a->Z1, a->W2,
                   a->F2, a->Z2, a->lU, a->lX, a->lWs, a->lW1, a->cF, a->cR, a->cD, a->limx, a->limy,
                   a->lXo, a->lnb, a->lq};
@@ -1152,26 +1186,48 @@ Par<T> make_par(const mwdg_adj *a, int nknots, const double *kt, const double *k
 
 template <typename T> T *ptr(void *p) { return static_cast<T *>(p); }
 
+// friction, limit, stage 1 and limit of step s: the two stage inputs (Un, Ui)
+// and their stored and flux views
+template <typename T>
+void recompute_stages(mwdg_adj *a, const Par<T> &P, const T *U, const T *z, const T *nman, int s, const double *dts,
+                      uint8_t *clip, cudaStream_t st) {
+  const unsigned nb = blocks(a->n);
+  T *Un = ptr<T>(a->Un), *Ui = ptr<T>(a->Ui), *W1 = ptr<T>(a->W1), *F1 = ptr<T>(a->F1), *Z1 = ptr<T>(a->Z1);
+  T *W2 = ptr<T>(a->W2), *F2 = ptr<T>(a->F2), *Z2 = ptr<T>(a->Z2);
+  {
+    Timed tm(a, MWDG_ADJ_KC_FRICTION, st);
+    k_friction<T><<<nb, TPB, 0, st>>>(P, U, nman, dts, a->tt, s, Un);
+  }
+  {
+    Timed tm(a, MWDG_ADJ_KC_LIMIT, st);
+    k_limit<T><<<nb, TPB, 0, st>>>(P, Un, z, W1, F1, Z1);
+  }
+  {
+    Timed tm(a, MWDG_ADJ_KC_UPDATE, st);
+    k_update<T><<<nb, TPB, 0, st>>>(P, 1, F1, Z1, W1, nullptr, dts, a->tt, s, Ui, clip);
+  }
+  Timed tm(a, MWDG_ADJ_KC_LIMIT, st);
+  k_limit<T><<<nb, TPB, 0, st>>>(P, Ui, z, W2, F2, Z2);
+}
+
 // the forward sweep of one step s from tape slot s into slot s + 1
 template <typename T>
-void launch_step(const mwdg_adj *a, const Par<T> &P, const T *z, const T *nman, int s, bool cfl, double *dts,
+void launch_step(mwdg_adj *a, const Par<T> &P, const T *z, const T *nman, int s, bool cfl, double *dts,
                  cudaStream_t st) {
   const long long n = a->n;
   const T *U = ptr<T>(a->tape) + (long long)s * 9 * n;
   T *Unext = ptr<T>(a->tape) + (long long)(s + 1) * 9 * n;
   uint8_t *clip = a->clip + (long long)s * n;
   const unsigned nb = blocks(n);
-  T *Un = ptr<T>(a->Un), *Ui = ptr<T>(a->Ui), *W1 = ptr<T>(a->W1), *F1 = ptr<T>(a->F1), *Z1 = ptr<T>(a->Z1);
-  T *W2 = ptr<T>(a->W2), *F2 = ptr<T>(a->F2), *Z2 = ptr<T>(a->Z2);
   if (cfl) {
+    Timed tm(a, MWDG_ADJ_KC_CFL, st);
     k_cfl<T><<<nb, TPB, 0, st>>>(P, U, a->tt, s, a->best);
     k_dt<<<1, 1, 0, st>>>(P.cfl, P.dt_max, a->best, dts, a->tt, s);
   }
-  k_friction<T><<<nb, TPB, 0, st>>>(P, U, nman, dts, a->tt, s, Un);
-  k_limit<T><<<nb, TPB, 0, st>>>(P, Un, z, W1, F1, Z1);
-  k_update<T><<<nb, TPB, 0, st>>>(P, 1, F1, Z1, W1, nullptr, dts, a->tt, s, Ui, clip);
-  k_limit<T><<<nb, TPB, 0, st>>>(P, Ui, z, W2, F2, Z2);
-  k_update<T><<<nb, TPB, 0, st>>>(P, 2, F2, Z2, W2, W1, dts, a->tt, s, Unext, clip);
+  recompute_stages<T>(a, P, U, z, nman, s, dts, clip, st);
+  Timed tm(a, MWDG_ADJ_KC_UPDATE, st);
+  k_update<T><<<nb, TPB, 0, st>>>(P, 2, ptr<T>(a->F2), ptr<T>(a->Z2), ptr<T>(a->W2), ptr<T>(a->W1), dts, a->tt, s,
+                                  Unext, clip);
 }
 
 mwdg_status check_run(mwdg_adj *a, const void *U0, const void *z, const void *n, int32_t nknots, const double *kt,
@@ -1210,8 +1266,8 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
   const size_t bytes = (size_t)9 * n * sizeof(T);
   const unsigned nb = blocks(n);
   const long long nfx = (long long)a->p.ny * (a->p.nx + 1), nfy = (long long)(a->p.ny + 1) * a->p.nx;
-  T *Un = ptr<T>(a->Un), *Ui = ptr<T>(a->Ui), *W1 = ptr<T>(a->W1), *F1 = ptr<T>(a->F1), *Z1 = ptr<T>(a->Z1);
-  T *W2 = ptr<T>(a->W2), *F2 = ptr<T>(a->F2), *Z2 = ptr<T>(a->Z2);
+  T *Un = ptr<T>(a->Un), *Ui = ptr<T>(a->Ui), *F1 = ptr<T>(a->F1), *Z1 = ptr<T>(a->Z1);
+  T *F2 = ptr<T>(a->F2), *Z2 = ptr<T>(a->Z2);
   T *lU = ptr<T>(a->lU), *lX = ptr<T>(a->lX), *lWs = ptr<T>(a->lWs), *lW1 = ptr<T>(a->lW1);
   T *cF = ptr<T>(a->cF), *cR = ptr<T>(a->cR), *cD = ptr<T>(a->cD), *limx = ptr<T>(a->limx),
     *limy = ptr<T>(a->limy), *lXo = ptr<T>(a->lXo), *lnb = ptr<T>(a->lnb);
@@ -1233,23 +1289,34 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
     uint8_t *clip = a->clip + (long long)k * n;
     // recompute the stage inputs of step k (stage 1 rewrites its clip bit
     // with the same value and keeps stage 2's from the tape run)
-    k_friction<T><<<nb, TPB, 0, st>>>(P, U, nman, dts, a->tt, k, Un);
-    k_limit<T><<<nb, TPB, 0, st>>>(P, Un, z, W1, F1, Z1);
-    k_update<T><<<nb, TPB, 0, st>>>(P, 1, F1, Z1, W1, nullptr, dts, a->tt, k, Ui, clip);
-    k_limit<T><<<nb, TPB, 0, st>>>(P, Ui, z, W2, F2, Z2);
+    recompute_stages<T>(a, P, U, z, nman, k, dts, clip, st);
     for (int stage = 2; stage >= 1; stage--) {
       const T *X = stage == 2 ? Ui : Un;
       const T *Y = stage == 2 ? Y2 : Ui;
       const T *Wf = stage == 2 ? F2 : F1;
       const T *Zf = stage == 2 ? Z2 : Z1;
       const T *lY = stage == 2 ? lU : lX;
-      k_rev_cell<T><<<nb, TPB, 0, st>>>(P, stage, lY, Y, clip, dts, a->tt, k, Wf, Zf, lWs, lW1, cF, cR, cD);
-      k_rev_face<T, true><<<blocks(nfx), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, cF, cR, limx, a->lq);
-      k_rev_face<T, false><<<blocks(nfy), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, cF, cR, limy, a->lq);
-      if (P.nknots > 0) k_rev_knots<T><<<1, TPB, 0, st>>>(P, stage, dts, a->tt, k, a->lq, gQ);
-      k_rev_limit<T><<<nb, TPB, 0, st>>>(P, X, z, lWs, limx, limy, cD, lXo, lnb, gz);
+      {
+        Timed tm(a, MWDG_ADJ_KC_REV_CELL, st);
+        k_rev_cell<T><<<nb, TPB, 0, st>>>(P, stage, lY, Y, clip, dts, a->tt, k, Wf, Zf, lWs, lW1, cF, cR, cD);
+      }
+      {
+        Timed tm(a, MWDG_ADJ_KC_REV_FACE, st);
+        k_rev_face<T, true><<<blocks(nfx), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, cF, cR, limx, a->lq);
+        k_rev_face<T, false><<<blocks(nfy), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, cF, cR, limy, a->lq);
+      }
+      if (P.nknots > 0) {
+        Timed tm(a, MWDG_ADJ_KC_REV_KNOTS, st);
+        k_rev_knots<T><<<1, TPB, 0, st>>>(P, stage, dts, a->tt, k, a->lq, gQ);
+      }
+      {
+        Timed tm(a, MWDG_ADJ_KC_REV_LIMIT, st);
+        k_rev_limit<T><<<nb, TPB, 0, st>>>(P, X, z, lWs, limx, limy, cD, lXo, lnb, gz);
+      }
+      Timed tm(a, MWDG_ADJ_KC_REV_GATHER, st);
       k_rev_gather<T><<<nb, TPB, 0, st>>>(P, lXo, lnb, lX, gz);
     }
+    Timed tm(a, MWDG_ADJ_KC_REV_FRICTION, st);
     k_rev_friction<T><<<nb, TPB, 0, st>>>(P, U, nman, dts, a->tt, k, lX, lU, gn);
   }
   if (cudaMemcpyAsync(gU0, lU, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
@@ -1345,6 +1412,40 @@ void mwdg_adj_destroy(mwdg_adj *a) {
 }
 
 const char *mwdg_adj_last_error(const mwdg_adj *a) { return a ? a->err.c_str() : ""; }
+
+mwdg_status mwdg_adj_profile(mwdg_adj *a, int32_t max_launches) {
+  if (!a || max_launches < 0) return MWDG_ERR_ARG;
+  cudaDeviceSynchronize();
+  free_events(a);
+  if (max_launches == 0) return MWDG_OK;
+  a->evs.resize((size_t)2 * max_launches, nullptr);
+  a->ev_class.assign((size_t)max_launches, 0);
+  for (auto &e : a->evs)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      e = nullptr;
+      free_events(a);
+      return cuda_check(a, "mwdg_adj_profile");
+    }
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_adj_kernel_times(mwdg_adj *a, double *ms, int64_t *count) {
+  if (!a || !ms || !count) return MWDG_ERR_ARG;
+  for (int c = 0; c < MWDG_ADJ_KC_COUNT; c++) {
+    ms[c] = 0.0;
+    count[c] = 0;
+  }
+  for (size_t q = 0; q + 1 < a->ev_used; q += 2) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(a->evs[q + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, a->evs[q], a->evs[q + 1]) != cudaSuccess)
+      return cuda_check(a, "mwdg_adj_kernel_times");
+    ms[a->ev_class[q / 2]] += t;
+    count[a->ev_class[q / 2]] += 1;
+  }
+  a->ev_used = 0;
+  return MWDG_OK;
+}
 
 mwdg_status mwdg_adj_project(mwdg_adj *a, const double *vert, void *out, void *stream) {
   if (!a) return MWDG_ERR_ARG;
