@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="instead: the batched ensemble of this many seeded valleys (sides 256-1024)")
     ap.add_argument("--no-tune", action="store_true", help="ensemble: keep the default launch shapes")
+    ap.add_argument("--grid", default="adaptive", choices=["adaptive", "uniform", "static"],
+                    help="DG2 grid: adaptive MWDG2 (the headline), the uniform finest grid, or the static graded grid")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the FP64 DG2 adjoint: one checkpoint segment forward and backward")
     ap.add_argument("--adjoint-steps", type=int, default=200, help="adjoint: steps per checkpoint segment")
@@ -218,6 +220,9 @@ def run_gpu(args, rank, world):
     torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
     p = S.valley(n=args.n, L=args.n.bit_length() - 1)
+    if args.grid != "adaptive":
+        from dataclasses import replace
+        p = replace(p, mode=S.UNIFORM if args.grid == "uniform" else S.STATIC)
     if args.scheme == "fv1":
         p = S.fv1(p)  # HWFV1 on the adaptive grid
     elif args.scheme == "acc":
@@ -255,7 +260,8 @@ def run_gpu(args, rank, world):
     achieved = (bpl * mean_leaves) / (dom_ms / dom_n * 1e-3) / 1e9 if bpl else None
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs,
                 "unit": "GB/s", "frac": (achieved / peak_gbs) if achieved else None,
-                "traffic": TRAFFIC.get(dom_name), "peak_kind": peak_kind,
+                "traffic": TRAFFIC.get(dom_name) if (args.grid, args.scheme) == ("adaptive", "dg2") else None,
+                "peak_kind": peak_kind,
                 "algorithmic_bytes_per_leaf": bpl, "launches": dom_n,
                 "share_of_step": dom_ms / max(sum(v[0] for v in kt.values()), 1e-9),
                 "step_ms_by_class": {k: round(v[0] / len(kms), 5) for k, v in kt.items() if v[1]},
@@ -395,8 +401,9 @@ def kernel_bytes_per_leaf(name, ts, scheme="dg2"):
     return n * ts + extra
 
 
-# DRAM bytes (read + write) per launch measured by ncu for a kernel, when the
-# kernel has not changed since (see profiles/); None otherwise
+# DRAM bytes (read + write) per launch measured by ncu for a kernel of the
+# headline workload (FP32 MWDG2), when the kernel has not changed since (see
+# profiles/); None otherwise
 TRAFFIC = {"dg2_update_stage2": 58_135_808 + 5_134_336}  # ncu: dram read + write, one launch at this workload
 
 
@@ -626,7 +633,9 @@ def main():
         line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD if args.scheme == "dg2" else
+                "config": {"workload": (WORKLOAD if args.grid == "adaptive" else
+                                        {"uniform": "uniform DG2", "static": "static DG2"}[args.grid] + WORKLOAD[5:])
+                           if args.scheme == "dg2" else
                            {"fv1": "HWFV1", "acc": "static-grid ACC"}[args.scheme] + WORKLOAD[5:],
                            "nx": args.n, "ny": args.n, "L": args.n.bit_length() - 1,
                            "eps": 1e-3, "spinup_s": out["t_spinup"], "mean_active_leaves": out["mean_active"],

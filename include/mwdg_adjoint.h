@@ -99,13 +99,17 @@ MWDG_API mwdg_status mwdg_adj_forward(mwdg_adj *a, const void *U0, const void *z
 /* Vector-Jacobian product of the run over the time steps dts[0..steps) from
  * U0 at t0: given gU_K (9 x n), the cotangent of U_K, writes gU0 (9 x n)
  * and ADDS to gz (3 x n), gn (n) and gQ (nknots), so that gradients of
- * several segments accumulate.  The run's states are recomputed from U0
- * into the tape (the segment's checkpoint is U0 itself).  gU0 may alias
- * gU_K.  Errors as mwdg_adj_forward. */
+ * several segments accumulate.  With reuse_tape = 0 the run's states are
+ * recomputed from U0 into the tape (the segment's checkpoint is U0 itself).
+ * reuse_tape = 1 states that the tape still holds this run: the last
+ * forward call on the context ran these steps from the same U0, z, n,
+ * knots, t0 and time steps, none of which changed since (no check is made
+ * beyond the number of steps: MWDG_ERR_STATE when it differs).  gU0 may
+ * alias gU_K.  Other errors as mwdg_adj_forward. */
 MWDG_API mwdg_status mwdg_adj_backward(mwdg_adj *a, const void *U0, const void *z, const void *n,
                                        int32_t nknots, const double *knot_t, const double *knot_Q, double t0,
                                        int32_t steps, const double *dts, const void *gU_K, void *gU0,
-                                       void *gz, void *gn, double *gQ, void *cuda_stream);
+                                       void *gz, void *gn, double *gQ, int32_t reuse_tape, void *cuda_stream);
 
 /* Transpose of Eq. 8: plane cotangents (3 x n) -> vertex cotangents
  * ((ny+1) x (nx+1)), both coefficient arrays, overwritten. */

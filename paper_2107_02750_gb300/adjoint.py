@@ -50,7 +50,7 @@ def lib():
         L.mwdg_adj_project.argtypes = [vp, vp, vp, vp]
         L.mwdg_adj_project_transpose.argtypes = [vp, vp, vp, vp]
         L.mwdg_adj_forward.argtypes = [vp, vp, vp, vp, i32, vp, vp, dp, i32, i32, vp, vp, vp]
-        L.mwdg_adj_backward.argtypes = [vp, vp, vp, vp, i32, vp, vp, dp, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.mwdg_adj_backward.argtypes = [vp, vp, vp, vp, i32, vp, vp, dp, i32, vp, vp, vp, vp, vp, vp, i32, vp]
         L.mwdg_adj_last_error.argtypes = [vp]
         L.mwdg_adj_last_error.restype = C.c_char_p
         L.mwdg_adj_profile.argtypes = [vp, i32]
@@ -162,6 +162,7 @@ class Dg2Adjoint:
         """U_K after `steps` steps from U0 at t0, and the time steps (the CFL
         ones, or `dts` when given)."""
         import torch
+        self._tape_token = None
         U0, z, n, kt, kQ, nk = self._common(U0, z, n, knot_t, knot_Q)
         fixed = dts is not None
         d = self._t(dts, (steps,), torch.float64) if fixed else torch.empty(max(1, steps), dtype=torch.float64,
@@ -172,10 +173,12 @@ class Dg2Adjoint:
         self._check(st, "mwdg_adj_forward")
         return out, d[:steps]
 
-    def backward(self, U0, z, n, knot_t, knot_Q, t0, dts, gUK):
+    def backward(self, U0, z, n, knot_t, knot_Q, t0, dts, gUK, reuse_tape=False):
         """(gU0, gz, gn, gQ): the cotangents of U0, z, n and the knots, given
-        that of U_K, over the steps dts from U0 at t0."""
+        that of U_K, over the steps dts from U0 at t0.  reuse_tape: the last
+        forward call ran exactly this segment and nothing changed since."""
         import torch
+        self._tape_token = None
         U0, z, n, kt, kQ, nk = self._common(U0, z, n, knot_t, knot_Q)
         d = self._t(dts, dtype=torch.float64)
         g = self._t(gUK, (9, self.ny, self.nx))
@@ -185,7 +188,7 @@ class Dg2Adjoint:
         gQ = torch.zeros(max(1, nk), dtype=torch.float64, device=self.device)
         st = lib().mwdg_adj_backward(self._h, _ptr(U0), _ptr(z), _ptr(n), nk, _ptr(kt), _ptr(kQ), float(t0),
                                      int(d.numel()), _ptr(d), _ptr(g), _ptr(gU0), _ptr(gz), _ptr(gn), _ptr(gQ),
-                                     _stream())
+                                     int(bool(reuse_tape)), _stream())
         self._check(st, "mwdg_adj_backward")
         return gU0, gz, gn, gQ[:nk]
 
@@ -201,13 +204,20 @@ def _autograd_function():
             UK, d = adj.forward(U0, z, n, knot_t, Q, t0, steps, dts)
             ctx.save_for_backward(U0, z, n, Q, d)
             ctx.adj, ctx.knot_t, ctx.t0 = adj, knot_t, t0
+            # the context's tape holds this segment until another call
+            # writes it; saved tensors cannot change (autograd's version
+            # check), so the tape is valid while this token is the last
+            adj._tape_token = ctx.token = object()
             ctx.mark_non_differentiable(d)
             return UK, d
 
         @staticmethod
         def backward(ctx, gUK, _gd):
             U0, z, n, Q, d = ctx.saved_tensors
-            gU0, gz, gn, gQ = ctx.adj.backward(U0, z, n, ctx.knot_t, Q, ctx.t0, d, gUK.contiguous())
+            reuse = getattr(ctx.adj, "_tape_token", None) is ctx.token
+            gU0, gz, gn, gQ = ctx.adj.backward(U0, z, n, ctx.knot_t, Q, ctx.t0, d, gUK.contiguous(),
+                                               reuse_tape=reuse)
+            ctx.adj._tape_token = ctx.token   # the tape holds this segment's run either way
             return gU0, gz, gn, (gQ if Q is not None and Q.numel() else None), None, None, None, None, None
 
     return Dg2Run

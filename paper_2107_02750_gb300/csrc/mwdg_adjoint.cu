@@ -7,7 +7,8 @@
 // kernel, with every branch replayed from the recomputed forward values:
 //
 //   forward per step   friction -> limit(Un) -> update stage 1 -> limit(Ui)
-//                      -> update stage 2 (+ the CFL dt when not given)
+//                      -> update stage 2 (+ the CFL dt when not given); the
+//                      update computes each interface once per 16 x 16 tile
 //   reverse per step   recompute friction, limit, stage 1, limit; then for
 //                      stage 2 and stage 1 in turn:
 //                        rev_cell   post-stage clip/dry masks, RK2 weights,
@@ -389,28 +390,77 @@ __global__ void __launch_bounds__(TPB) k_limit(Par<T> P, const T *X, const T *Z,
   for (int m = 0; m < 3; m++) Zfx[m * n + k] = ze[m];
 }
 
-// One RK2 stage (Eq. 4a for stage 1, Eq. 4b for stage 2): the DG2 operator
-// of the cell from its four face fluxes, the stage combination and the
-// positivity clip; the clip is recorded in bit (stage - 1) of clip[k].
+// One RK2 stage (Eq. 4a for stage 1, Eq. 4b for stage 2) on a tile of
+// UT x UT cells: every interface of the tile (its own and the ones on its
+// edge) is computed once into shared memory -- the flux and both sides'
+// revised limits -- then each cell takes its four faces, forms the DG2
+// operator, the stage combination and the positivity clip.  The clip is
+// recorded in bit (stage - 1) of clip[k].  A face's values are the ones
+// either cell would compute for it (the interface bed is the max of the two
+// limits, HLL takes the west/south side first), so the result equals a
+// per-cell evaluation bit for bit.
+constexpr int UT = 16;
+constexpr int UFX = (UT + 1) * UT, UFY = UT * (UT + 1);
+
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_update(Par<T> P, int stage, const T *Wfx, const T *Zfx, const T *Wst,
-                                                const T *W1, const double *dts, const double *tt, int step, T *Out,
-                                                uint8_t *clip) {
-  long long k;
-  int i, j;
-  if (!cell_of(P, k, i, j)) return;
+__global__ void __launch_bounds__(UT * UT) k_update(Par<T> P, int stage, const T *Wfx, const T *Zfx, const T *Wst,
+                                                    const T *W1, const double *dts, const double *tt, int step,
+                                                    T *Out, uint8_t *clip) {
+  __shared__ T sF[UFX + UFY][3];
+  __shared__ T sR[UFX + UFY][8];  // low side (hs, u, v, zr), high side (hs, u, v, zr)
+  const int i0 = blockIdx.x * UT, j0 = blockIdx.y * UT;
   const long long n = P.n;
-  const T dt = (T)dts[step];
   const double t = stage == 1 ? tt[step] : tt[step] + dts[step];
+  for (int q = threadIdx.x; q < UFX + UFY; q += UT * UT) {
+    const bool xf = q < UFX;
+    int fi, fj;
+    if (xf) { fj = q / (UT + 1); fi = q - fj * (UT + 1); }
+    else { fj = (q - UFX) / UT; fi = (q - UFX) - fj * UT; }
+    const int gi = i0 + fi, gj = j0 + fj;   // the face's high-side cell
+    if (xf ? (gj >= P.ny || gi > P.nx) : (gi >= P.nx || gj > P.ny)) continue;
+    const bool hasLo = xf ? gi > 0 : gj > 0;
+    const bool hasHi = xf ? gi < P.nx : gj < P.ny;
+    const int along = xf ? gj : gi;
+    const long long kHi = (long long)gj * P.nx + gi;
+    const long long kLo = xf ? kHi - 1 : kHi - P.nx;
+    Lim<T> lo, hi;
+    if (hasLo) lo = cell_lim(Wfx, Zfx, n, kLo, xf ? 0 : 2);
+    if (hasHi) hi = cell_lim(Wfx, Zfx, n, kHi, xf ? 1 : 3);
+    if (!hasLo) lo = ghost(P, xf ? 0 : 2, along, hi, t);
+    if (!hasHi) hi = ghost(P, xf ? 1 : 3, along, lo, t);
+    const T zf = tmax(lo.z, hi.z);
+    const Side<T> sl = revise_h(lo.h, lo.qx, lo.qy, lo.z, zf, P.hd);
+    const Side<T> sh = revise_h(hi.h, hi.qx, hi.qy, hi.z, zf, P.hd);
+    T H[3];
+    if (xf) {
+      hll(sl.hs, sl.u, sl.v, sh.hs, sh.u, sh.v, P.g, P.hd, H);
+      sF[q][0] = H[0]; sF[q][1] = H[1]; sF[q][2] = H[2];
+    } else {
+      hll(sl.hs, sl.v, sl.u, sh.hs, sh.v, sh.u, P.g, P.hd, H);
+      sF[q][0] = H[0]; sF[q][1] = H[2]; sF[q][2] = H[1];
+    }
+    sR[q][0] = sl.hs; sR[q][1] = sl.u; sR[q][2] = sl.v; sR[q][3] = sl.zr;
+    sR[q][4] = sh.hs; sR[q][5] = sh.u; sR[q][6] = sh.v; sR[q][7] = sh.zr;
+  }
+  __syncthreads();
+  const int ci = threadIdx.x % UT, cj = threadIdx.x / UT;
+  const int i = i0 + ci, j = j0 + cj;
+  if (i >= P.nx || j >= P.ny) return;
+  const long long k = (long long)j * P.nx + i;
+  const T dt = (T)dts[step];
   const T g = P.g, s3 = s3v<T>(), dxl = P.dx;
+  // faces E, W (x faces (ci+1, cj), (ci, cj)) and N, S (y faces (ci, cj+1),
+  // (ci, cj)); the cell is the low side of E and N, the high side of W and S
+  const int qf[4] = {cj * (UT + 1) + ci + 1, cj * (UT + 1) + ci, UFX + (cj + 1) * UT + ci, UFX + cj * UT + ci};
+  const int side[4] = {0, 4, 0, 4};
   T Fh[4][3], hs[4], us[4], vs[4], zr[4];
 #pragma unroll
   for (int f = 0; f < 4; f++) {
-    const Lim<T> o = cell_lim(Wfx, Zfx, n, k, f);
-    const Lim<T> b = other_side(P, Wfx, Zfx, i, j, f, o, t);
-    Side<T> so;
-    face_flux(P, o, b, f, Fh[f], so);
-    hs[f] = so.hs; us[f] = so.u; vs[f] = so.v; zr[f] = so.zr;
+    Fh[f][0] = sF[qf[f]][0]; Fh[f][1] = sF[qf[f]][1]; Fh[f][2] = sF[qf[f]][2];
+    hs[f] = sR[qf[f]][side[f]];
+    us[f] = sR[qf[f]][side[f] + 1];
+    vs[f] = sR[qf[f]][side[f] + 2];
+    zr[f] = sR[qf[f]][side[f] + 3];
   }
   T Fx[2][3], Gy[2][3];
 #pragma unroll
@@ -1093,6 +1143,7 @@ struct mwdg_adj {
   std::vector<cudaEvent_t> evs;
   std::vector<int> ev_class;
   size_t ev_used = 0;
+  int tape_steps = -1;         // steps of the run the tape holds (-1: none)
   long long n = 0;
   size_t elem = 8;             // bytes per coefficient (8 FP64, 4 FP32)
   void *tape = nullptr;        // (max_steps + 1) x 9n: the state at the start of each step
@@ -1202,9 +1253,10 @@ void recompute_stages(mwdg_adj *a, const Par<T> &P, const T *U, const T *z, cons
     Timed tm(a, MWDG_ADJ_KC_LIMIT, st);
     k_limit<T><<<nb, TPB, 0, st>>>(P, Un, z, W1, F1, Z1);
   }
+  const dim3 tiles((P.nx + UT - 1) / UT, (P.ny + UT - 1) / UT);
   {
     Timed tm(a, MWDG_ADJ_KC_UPDATE, st);
-    k_update<T><<<nb, TPB, 0, st>>>(P, 1, F1, Z1, W1, nullptr, dts, a->tt, s, Ui, clip);
+    k_update<T><<<tiles, UT * UT, 0, st>>>(P, 1, F1, Z1, W1, nullptr, dts, a->tt, s, Ui, clip);
   }
   Timed tm(a, MWDG_ADJ_KC_LIMIT, st);
   k_limit<T><<<nb, TPB, 0, st>>>(P, Ui, z, W2, F2, Z2);
@@ -1225,9 +1277,10 @@ void launch_step(mwdg_adj *a, const Par<T> &P, const T *z, const T *nman, int s,
     k_dt<<<1, 1, 0, st>>>(P.cfl, P.dt_max, a->best, dts, a->tt, s);
   }
   recompute_stages<T>(a, P, U, z, nman, s, dts, clip, st);
+  const dim3 tiles((P.nx + UT - 1) / UT, (P.ny + UT - 1) / UT);
   Timed tm(a, MWDG_ADJ_KC_UPDATE, st);
-  k_update<T><<<nb, TPB, 0, st>>>(P, 2, ptr<T>(a->F2), ptr<T>(a->Z2), ptr<T>(a->W2), ptr<T>(a->W1), dts, a->tt, s,
-                                  Unext, clip);
+  k_update<T><<<tiles, UT * UT, 0, st>>>(P, 2, ptr<T>(a->F2), ptr<T>(a->Z2), ptr<T>(a->W2), ptr<T>(a->W1), dts, a->tt,
+                                         s, Unext, clip);
 }
 
 mwdg_status check_run(mwdg_adj *a, const void *U0, const void *z, const void *n, int32_t nknots, const double *kt,
@@ -1260,7 +1313,7 @@ mwdg_status forward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int32
 template <typename T>
 mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int32_t nknots, const double *kt,
                        const double *kQ, double t0, int32_t steps, const double *dts_in, const T *gUK, T *gU0, T *gz,
-                       T *gn, double *gQ, cudaStream_t st) {
+                       T *gn, double *gQ, bool reuse, cudaStream_t st) {
   const Par<T> P = make_par<T>(a, nknots, kt, kQ);
   const long long n = a->n;
   const size_t bytes = (size_t)9 * n * sizeof(T);
@@ -1271,15 +1324,18 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
   T *lU = ptr<T>(a->lU), *lX = ptr<T>(a->lX), *lWs = ptr<T>(a->lWs), *lW1 = ptr<T>(a->lW1);
   T *cF = ptr<T>(a->cF), *cR = ptr<T>(a->cR), *cD = ptr<T>(a->cD), *limx = ptr<T>(a->limx),
     *limy = ptr<T>(a->limy), *lXo = ptr<T>(a->lXo), *lnb = ptr<T>(a->lnb);
-  // the tape: the run recomputed from its checkpoint U0 over the given steps
+  // the tape: the run recomputed from its checkpoint U0 over the given steps,
+  // unless the caller states that the last forward call left it in place
   if (steps > 0 && cudaMemcpyAsync(a->dtbuf, dts_in, (size_t)steps * sizeof(double), cudaMemcpyDeviceToDevice,
                                    st) != cudaSuccess)
     return cuda_check(a, "mwdg_adj_backward dts");
-  if (cudaMemcpyAsync(a->tape, U0, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-    return cuda_check(a, "mwdg_adj_backward copy-in");
-  k_set_t0<<<1, 1, 0, st>>>(a->tt, t0);
-  k_times<<<1, 1, 0, st>>>(a->dtbuf, steps, a->tt);
-  for (int k = 0; k < steps; k++) launch_step<T>(a, P, z, nman, k, false, a->dtbuf, st);
+  if (!reuse) {
+    if (cudaMemcpyAsync(a->tape, U0, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return cuda_check(a, "mwdg_adj_backward copy-in");
+    k_set_t0<<<1, 1, 0, st>>>(a->tt, t0);
+    k_times<<<1, 1, 0, st>>>(a->dtbuf, steps, a->tt);
+    for (int k = 0; k < steps; k++) launch_step<T>(a, P, z, nman, k, false, a->dtbuf, st);
+  }
   if (cudaMemcpyAsync(lU, gUK, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return cuda_check(a, "mwdg_adj_backward seed");
   const double *dts = a->dtbuf;
@@ -1480,6 +1536,7 @@ mwdg_status mwdg_adj_forward(mwdg_adj *a, const void *U0, const void *z, const v
   if (s != MWDG_OK) return s;
   if (!U_out) return fail(a, MWDG_ERR_ARG, "NULL pointer");
   cudaStream_t st = (cudaStream_t)stream;
+  a->tape_steps = steps;
   if (a->p.precision == MWDG_F32)
     return forward_t<float>(a, static_cast<const float *>(U0), static_cast<const float *>(z),
                             static_cast<const float *>(nman), nknots, kt, kQ, t0, steps, fixed_dt, dts,
@@ -1491,20 +1548,24 @@ mwdg_status mwdg_adj_forward(mwdg_adj *a, const void *U0, const void *z, const v
 
 mwdg_status mwdg_adj_backward(mwdg_adj *a, const void *U0, const void *z, const void *nman, int32_t nknots,
                               const double *kt, const double *kQ, double t0, int32_t steps, const double *dts_in,
-                              const void *gUK, void *gU0, void *gz, void *gn, double *gQ, void *stream) {
+                              const void *gUK, void *gU0, void *gz, void *gn, double *gQ, int32_t reuse_tape,
+                              void *stream) {
   mwdg_status s = check_run(a, U0, z, nman, nknots, kt, kQ, steps, dts_in);
   if (s != MWDG_OK) return s;
+  const bool reuse = reuse_tape != 0;
+  if (reuse && steps != a->tape_steps) return fail(a, MWDG_ERR_STATE, "the tape holds another number of steps");
+  a->tape_steps = steps;
   if (!gUK || !gU0 || !gz || !gn || (a->p.inflow_edge >= 0 && !gQ)) return fail(a, MWDG_ERR_ARG, "NULL pointer");
   cudaStream_t st = (cudaStream_t)stream;
   if (a->p.precision == MWDG_F32)
     return backward_t<float>(a, static_cast<const float *>(U0), static_cast<const float *>(z),
                              static_cast<const float *>(nman), nknots, kt, kQ, t0, steps, dts_in,
                              static_cast<const float *>(gUK), ptr<float>(gU0), ptr<float>(gz), ptr<float>(gn), gQ,
-                             st);
+                             reuse, st);
   return backward_t<double>(a, static_cast<const double *>(U0), static_cast<const double *>(z),
                             static_cast<const double *>(nman), nknots, kt, kQ, t0, steps, dts_in,
                             static_cast<const double *>(gUK), ptr<double>(gU0), ptr<double>(gz), ptr<double>(gn), gQ,
-                            st);
+                            reuse, st);
 }
 
 }  // extern "C"

@@ -268,3 +268,26 @@ def test_f32_adjoint_tracks_the_fp64_oracle(name, p, K):
         assert err.max() <= 5e-2, (what, err.max())
         assert np.quantile(err, 0.99) <= 2e-2, (what, np.quantile(err, 0.99))
         assert np.corrcoef(a.ravel(), ref.ravel())[0, 1] >= 0.999, what
+
+
+def test_tape_reuse_gives_the_recomputed_gradients():
+    """The backward may reuse the tape the forward left (reuse_tape); the
+    gradients equal those of a backward that recomputes the segment from its
+    checkpoint, bit for bit, in both precisions.  A tape of another length is
+    refused."""
+    import torch
+    import paper_2107_02750_gb300 as M
+    p, _ = S.adjoint_reach(n=32)
+    for precision in (M.F64, M.F32):
+        adj = context(p, 20, precision=precision)
+        U0, z, n, kt, kQ = device_inputs(adj, p)
+        seed = torch.randn((9, p.ny, p.nx), generator=torch.Generator().manual_seed(3)).to(U0)
+        _, d = adj.forward(U0, z, n, kt, kQ, 0.0, 20)
+        a = adj.backward(U0, z, n, kt, kQ, 0.0, d, seed, reuse_tape=False)
+        adj.forward(U0, z, n, kt, kQ, 0.0, 20, dts=d)
+        b = adj.backward(U0, z, n, kt, kQ, 0.0, d, seed, reuse_tape=True)
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+        adj.forward(U0, z, n, kt, kQ, 0.0, 10, dts=d[:10])
+        with pytest.raises(M.MwdgError):
+            adj.backward(U0, z, n, kt, kQ, 0.0, d, seed, reuse_tape=True)
