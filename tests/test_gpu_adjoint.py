@@ -291,3 +291,60 @@ def test_tape_reuse_gives_the_recomputed_gradients():
         adj.forward(U0, z, n, kt, kQ, 0.0, 10, dts=d[:10])
         with pytest.raises(M.MwdgError):
             adj.backward(U0, z, n, kt, kQ, 0.0, d, seed, reuse_tape=True)
+
+
+def test_full_size_gradients():
+    """The bench's workload, 1024 x 1024 valley with a flowing start, one
+    20-step segment, gauge misfit seed.  The oracle cannot run this size, so
+    properties that hold at any size stand in: central differences of the
+    FP64 forward (steps held, 1e-6 to 1e-8) converge to the FP64 gradients
+    at sampled Manning n, bed and depth entries of wet cells (a dry cell at
+    h0 = 0 sits on the positivity clip's kink: a negative perturbation is
+    clipped, a positive one is not, and a central difference takes half the
+    one-sided slope); the FP32 gradients track the FP64 ones (correlation
+    >= 0.999 over all cells)."""
+    import torch
+    import paper_2107_02750_gb300 as M
+    p, gauges = S.adjoint_reach(n=1024, crop_of=1024)
+    K = 20
+    out = {}
+    for precision in (M.F64, M.F32):
+        adj = context(p, K, precision=precision)
+        U0, z, n, kt, kQ = device_inputs(adj, p)
+        if precision == M.F64:
+            _, d = adj.forward(U0, z, n, kt, kQ, 0.0, K)
+        seed = torch.zeros((9, p.ny, p.nx), dtype=adj.dtype, device=adj.device)
+        seed[0] = torch.randn((p.ny, p.nx), generator=torch.Generator().manual_seed(9)).to(seed)
+        out[precision] = (adj, U0, z, n, kt, kQ, seed, adj.backward(U0, z, n, kt, kQ, 0.0, d, seed))
+    adj, U0, z, n, kt, kQ, seed, (gU0, gz, gn, gQ) = out[M.F64]
+
+    def J(U0_=U0, z_=z, n_=n):
+        UK, _ = adj.forward(U0_, z_, n_, kt, kQ, 0.0, K, dts=d)
+        return float((UK * seed).sum())
+
+    def best(ad, arr, idx, scale, which):
+        fs = []
+        for rel in (1e-6, 1e-7, 1e-8):
+            a, b = arr.clone(), arr.clone()
+            a[idx] += rel * scale
+            b[idx] -= rel * scale
+            fs.append((J(**{which: a}) - J(**{which: b})) / (2.0 * rel * scale))
+        return min(fs, key=lambda f: abs(f - ad))
+
+    rng = np.random.default_rng(21)
+    gnn, gzz, ghh = gn.cpu().numpy(), gz.cpu().numpy(), gU0.cpu().numpy()
+    checks = []
+    wet = U0[0].cpu().numpy() > 0.05   # a dry cell at h0 = 0 sits on the clip's kink
+    for arr, g, which, scale_of in ((n, gnn, "n_", lambda v: v), (z, gzz[0], "z_", lambda v: 1.0),
+                                    (U0, ghh[0], "U0_", lambda v: 1.0)):
+        idx = np.argwhere((np.abs(g) > 1e-2 * np.abs(g).max()) & wet)
+        for j, i in idx[rng.choice(len(idx), 2, replace=False)]:
+            full = (j, i) if which == "n_" else (0, j, i)
+            ad = float(g[j, i])
+            checks.append((which, ad, best(ad, arr, full, scale_of(float(arr[full])), which)))
+    for what, ad, f in checks:
+        assert abs(ad - f) <= 1e-4 * abs(ad), (what, ad, f)
+    g32 = out[M.F32][-1]
+    for a, b, what in zip(g32[:3], (gU0, gz, gn), ("U0", "z", "n")):
+        x, y = a.double().cpu().numpy().ravel(), b.cpu().numpy().ravel()
+        assert np.corrcoef(x, y)[0, 1] >= 0.999, what
