@@ -963,8 +963,8 @@ static void post_stage(orc_sim *s, double *w, double area) {
  *     its interface depths are its average and a shoreline leaf at rest
  *     stays at rest.  The paper delegates its wet/dry treatment to cited works;
  *     this is the reading used here.
- * (2) Otherwise, the slope limiter (the paper names none; the benchmark spec asks
- *     for one): minmod on the face-limit offsets sqrt3*v1 of eta, qx and qy
+ * (2) Otherwise, the slope limiter (the paper names none; the DG2 step it
+ *     cites limits its slopes): minmod on the face-limit offsets sqrt3*v1 of eta, qx and qy
  *     against the differences of the averages of the same-level leaf
  *     neighbours, per direction (two-argument minmod against the one
  *     difference where only one such neighbour exists: domain edges and
