@@ -550,12 +550,12 @@ def run_adjoint(args):
 # class (reads + writes of unique data, neighbour re-reads not counted; the
 # two stages averaged where they differ; the interface class per cell covers
 # its two faces), and the bytes of the clip flags
-ADJ_VALUES_PER_CELL = {"friction": 19, "limit": 33, "update": 34.5, "cfl": 3, "rev_cell": 72, "rev_face": 56,
-                       "rev_limit": 68, "rev_gather": 32, "rev_friction": 30}
-ADJ_FLAG_BYTES = {"update": 1, "rev_cell": 1}
+ADJ_VALUES_PER_CELL = {"friction": 19, "limit": 33, "update": 34.5, "cfl": 3, "rev_face": 49, "rev_limit": 67,
+                       "rev_gather": 32, "rev_friction": 30}
+ADJ_FLAG_BYTES = {"update": 1, "rev_face": 1, "rev_limit": 1}
 # DRAM bytes (read + write) per launch measured by ncu for the FP32 adjoint
 # kernels at this workload, while the kernel is unchanged (see profiles/)
-ADJ_TRAFFIC = {"update": 89_190_000 + 11_490_000}  # ncu: one stage launch, dram read + write
+ADJ_TRAFFIC = {}
 
 
 def adjoint_roofline(times, cells, elem):

@@ -42,7 +42,7 @@
  * Work is queued on the given CUDA stream (NULL: the legacy default stream);
  * no call synchronises it, except mwdg_adj_create and mwdg_adj_destroy.  A
  * context holds a tape of max_steps + 1 states (9 n coefficients each) and
- * about 130 n coefficients of work arrays; one host thread uses it at a
+ * about 100 n coefficients of work arrays; one host thread uses it at a
  * time, and its calls on one stream run in order.  Statuses are those of mwdg.h.
  */
 #ifndef MWDG_ADJOINT_H
@@ -127,7 +127,6 @@ enum {
   MWDG_ADJ_KC_FRICTION,     /* rain and friction                            */
   MWDG_ADJ_KC_LIMIT,        /* stage-input limiting                         */
   MWDG_ADJ_KC_UPDATE,       /* RK2 stage update                             */
-  MWDG_ADJ_KC_REV_CELL,     /* reverse: per-cell operator terms             */
   MWDG_ADJ_KC_REV_FACE,     /* reverse: x and y interfaces                  */
   MWDG_ADJ_KC_REV_KNOTS,    /* reverse: hydrograph knots                    */
   MWDG_ADJ_KC_REV_LIMIT,    /* reverse: limiter                             */

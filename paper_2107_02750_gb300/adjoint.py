@@ -25,8 +25,8 @@ ADJ_EXPORTS = (
     "mwdg_adj_profile", "mwdg_adj_kernel_times",
 )
 # kernel classes of mwdg_adj_kernel_times, in order
-ADJ_CLASSES = ("cfl", "friction", "limit", "update", "rev_cell", "rev_face", "rev_knots", "rev_limit",
-               "rev_gather", "rev_friction")
+ADJ_CLASSES = ("cfl", "friction", "limit", "update", "rev_face", "rev_knots", "rev_limit", "rev_gather",
+               "rev_friction")
 
 
 class AdjParams(C.Structure):

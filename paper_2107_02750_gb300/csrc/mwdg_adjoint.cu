@@ -11,15 +11,17 @@
 //                      update computes each interface once per 16 x 16 tile
 //   reverse per step   recompute friction, limit, stage 1, limit; then for
 //                      stage 2 and stage 1 in turn:
-//                        rev_cell   post-stage clip/dry masks, RK2 weights,
-//                                   operator terms local to a cell (flux
-//                                   weights, physical fluxes of the own
-//                                   revised limits, bed-slope sources)
-//                        rev_face   per interface: HLL and the two
-//                                   revisions, the interface bed max,
-//                                   boundary ghosts (and the hydrograph)
-//                        rev_limit  face-limit transpose and the limiter
-//                                   (partial-wet reduction, minmod picks)
+//                        rev_face   per interface: both cells' operator
+//                                   terms for it (post-stage masks, RK2
+//                                   weights, flux weights, physical fluxes
+//                                   and bed sources of the own revised
+//                                   limits), then HLL and the two revisions,
+//                                   the interface bed max, boundary ghosts
+//                                   (and the hydrograph)
+//                        rev_limit  the stored view's and the slope sources'
+//                                   terms, the face-limit transpose and the
+//                                   limiter (partial-wet reduction, minmod
+//                                   picks)
 //                        rev_gather neighbour terms of the limiter
 //                      then friction.
 //
@@ -555,112 +557,84 @@ __global__ void __launch_bounds__(TPB) k_project_t(Par<T> P, const T *gp, T *gv)
 // ---------------------------------------------------------------------------
 // reverse sweep
 // ---------------------------------------------------------------------------
-// Cotangents of the own revised limits and fluxes of one cell's operator.
-// Buffers: cF (4 faces x 3) the flux cotangent this cell contributes to
-// each face, cR (4 x 4) the cotangents of its own revised (hs, u, v, zr) per
-// face, cD (4) direct cotangents of (w1x of h, w1y of h, z1x, z1y) of the
-// flux view from the bed-slope sources.  lWs receives the cotangent of the
-// stage's stored view; lW1 carries stage 2's share of the stage-1 view.
+// The cotangents a stage's output cotangent lY gives the cell's operator:
+// lo = lY through the positivity clip and the dry reset (the clip recorded
+// in bit stage - 1, the dry reset read off the stage's output Y), and
+// lL = lo times the RK2 weight of the operator (dt, or dt / 2 in stage 2).
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_rev_cell(Par<T> P, int stage, const T *lY, const T *Y,
-                                                  const uint8_t *clip, const double *dts, const double *tt, int step,
-                                                  const T *Wfx, const T *Zfx, T *lWs, T *lW1, T *cF, T *cR, T *cD) {
-  long long k;
-  int i, j;
-  if (!cell_of(P, k, i, j)) return;
+__device__ __forceinline__ void stage_cot(const Par<T> &P, int stage, T dt, const T *lY, const T *Y,
+                                          const uint8_t *clip, long long k, T lo[9], T lL[9]) {
   const long long n = P.n;
-  const T dt = (T)dts[step];
-  const double t = stage == 1 ? tt[step] : tt[step] + dts[step];
-  const T g = P.g, s3 = s3v<T>(), rdx = T(1) / P.dx;
   const bool clipped = (clip[k] >> (stage - 1)) & 1u;
   const bool dry = !(Y[k] > P.hd);
-  T lL[9];
+  const T wL = stage == 2 ? T(0.5) * dt : dt;
 #pragma unroll
   for (int m = 0; m < 9; m++) {
-    T lo = lY[m * n + k];
-    if ((m == 0 && clipped) || (m > 0 && dry)) lo = T(0);
-    if (stage == 2) {
-      lWs[m * n + k] = T(0.5) * lo;
-      lW1[m * n + k] = T(0.5) * lo;
-      lL[m] = T(0.5) * dt * lo;
-    } else {
-      lWs[m * n + k] = lo + lW1[m * n + k];
-      lL[m] = dt * lo;
-    }
+    T l = lY[m * n + k];
+    if ((m == 0 && clipped) || (m > 0 && dry)) l = T(0);
+    lo[m] = l;
+    lL[m] = wL * l;
   }
-  // forward values of the own revised limits
-  T hs[4], us[4], vs[4], zr[4];
-#pragma unroll
-  for (int f = 0; f < 4; f++) {
-    const Lim<T> o = cell_lim(Wfx, Zfx, n, k, f);
-    const Lim<T> b = other_side(P, Wfx, Zfx, i, j, f, o, t);
-    const T zf = tmax(o.z, b.z);
-    const Side<T> so = revise_h(o.h, o.qx, o.qy, o.z, zf, P.hd);
-    hs[f] = so.hs; us[f] = so.u; vs[f] = so.v; zr[f] = so.zr;
+}
+
+// the cell's own revised limits at its face f (the other side's bed limit,
+// or its own on the boundary, sets the interface bed)
+template <typename T>
+__device__ __forceinline__ Side<T> own_revised(const Par<T> &P, const T *W, const T *Z, int i, int j, int f) {
+  const long long k = (long long)j * P.nx + i;
+  const Lim<T> o = cell_lim(W, Z, P.n, k, f);
+  const int di = f == 0 ? 1 : f == 1 ? -1 : 0, dj = f == 2 ? 1 : f == 3 ? -1 : 0;
+  const int a = i + di, b = j + dj;
+  T zb = o.z;
+  if (a >= 0 && b >= 0 && a < P.nx && b < P.ny) {
+    const long long kb = (long long)b * P.nx + a;
+    zb = face_value(Z[kb], Z[P.n + kb], Z[2 * P.n + kb], f ^ 1);
   }
-  T lF[4][3] = {}, lH[4] = {}, lU[4] = {}, lV[4] = {}, lZ[4] = {}, lFx[2][3] = {}, lGy[2][3] = {};
-  T lD[4] = {};
-  const T kx = -(s3 * rdx);
-  const T c = -g * T(0.5) * rdx, c2 = -(T(2) * s3 * g * rdx);
-  const T w1 = Wfx[n + k], w2 = Wfx[2 * n + k], zc1 = Zfx[n + k], zc2 = Zfx[2 * n + k];
+  return revise_h(o.h, o.qx, o.qy, o.z, tmax(o.z, zb), P.hd);
+}
+
+// What one cell's operator (Eq. 4, with lL its cotangent) gives its face f:
+// the cotangent of the face flux (lF) and of the cell's own revised limits
+// there (lr: hs, u, v, zr).  sf are those revised limits, so the ones at the
+// opposite face (the bed source couples the two faces of a direction).
+template <typename T>
+__device__ __forceinline__ void cell_face_cot(const Par<T> &P, int f, const T lL[9], const Side<T> &sf,
+                                              const Side<T> &so, T lF[3], T lr[4]) {
+  const T g = P.g, rdx = T(1) / P.dx;
+  const T kx = -(s3v<T>() * rdx);
+  const T c = -g * T(0.5) * rdx;
+  const bool xf = f < 2, plus = (f == 0 || f == 2);
+  T lP[3];
 #pragma unroll
   for (int v = 0; v < 3; v++) {
-    const T l0 = lL[3 * v], lx = lL[3 * v + 1], ly = lL[3 * v + 2];
-    lF[0][v] += -l0 * rdx + kx * lx;
-    lF[1][v] += l0 * rdx + kx * lx;
-    lF[2][v] += -l0 * rdx + kx * ly;
-    lF[3][v] += l0 * rdx + kx * ly;
-    lFx[0][v] -= kx * lx;
-    lFx[1][v] -= kx * lx;
-    lGy[0][v] -= kx * ly;
-    lGy[1][v] -= kx * ly;
-    if (v == 1) {
-      lH[0] += l0 * c * (zr[0] - zr[1]);
-      lH[1] += l0 * c * (zr[0] - zr[1]);
-      lZ[0] += l0 * c * (hs[0] + hs[1]);
-      lZ[1] -= l0 * c * (hs[0] + hs[1]);
-      lD[0] += lx * c2 * (T(2) * w1 + zc1);
-      lD[2] += lx * c2 * w1;
-    }
-    if (v == 2) {
-      lH[2] += l0 * c * (zr[2] - zr[3]);
-      lH[3] += l0 * c * (zr[2] - zr[3]);
-      lZ[2] += l0 * c * (hs[2] + hs[3]);
-      lZ[3] -= l0 * c * (hs[2] + hs[3]);
-      lD[1] += ly * c2 * (T(2) * w2 + zc2);
-      lD[3] += ly * c2 * w2;
-    }
+    const T l0 = lL[3 * v], ls = xf ? lL[3 * v + 1] : lL[3 * v + 2];
+    lF[v] = (plus ? -l0 : l0) * rdx + kx * ls;   // L0 = -(F0 - F1)/dx - (F2 - F3)/dx; L1 = kx (F+ + F-)
+    lP[v] = -kx * ls;                            // the physical flux of the own revised limits
   }
-#pragma unroll
-  for (int a = 0; a < 2; a++) {
-    int f = a;
-    const T q = hs[f] * us[f];
-    const T lq = lFx[a][0] + lFx[a][1] * us[f] + lFx[a][2] * vs[f];
-    lU[f] += lFx[a][1] * q;
-    lV[f] += lFx[a][2] * q;
-    lH[f] += lFx[a][1] * g * hs[f];
-    lH[f] += lq * us[f];
-    lU[f] += lq * hs[f];
-    f = 2 + a;
-    const T r = hs[f] * vs[f];
-    const T lr = lGy[a][0] + lGy[a][1] * us[f] + lGy[a][2] * vs[f];
-    lU[f] += lGy[a][1] * r;
-    lV[f] += lGy[a][2] * r;
-    lH[f] += lGy[a][2] * g * hs[f];
-    lH[f] += lr * vs[f];
-    lV[f] += lr * hs[f];
+  lr[0] = lr[1] = lr[2] = lr[3] = T(0);
+  if (xf) {
+    const T q = sf.hs * sf.u;
+    const T lq = lP[0] + lP[1] * sf.u + lP[2] * sf.v;
+    lr[1] += lP[1] * q;
+    lr[2] += lP[2] * q;
+    lr[0] += lP[1] * g * sf.hs;
+    lr[0] += lq * sf.u;
+    lr[1] += lq * sf.hs;
+  } else {
+    const T r = sf.hs * sf.v;
+    const T lq = lP[0] + lP[1] * sf.u + lP[2] * sf.v;
+    lr[1] += lP[1] * r;
+    lr[2] += lP[2] * r;
+    lr[0] += lP[2] * g * sf.hs;
+    lr[0] += lq * sf.v;
+    lr[2] += lq * sf.hs;
   }
-#pragma unroll
-  for (int f = 0; f < 4; f++) {
-#pragma unroll
-    for (int v = 0; v < 3; v++) cF[(f * 3 + v) * n + k] = lF[f][v];
-    cR[(f * 4 + 0) * n + k] = lH[f];
-    cR[(f * 4 + 1) * n + k] = lU[f];
-    cR[(f * 4 + 2) * n + k] = lV[f];
-    cR[(f * 4 + 3) * n + k] = lZ[f];
-  }
-#pragma unroll
-  for (int q = 0; q < 4; q++) cD[q * n + k] = lD[q];
+  // bed source of L0 in this direction: c (hs+ + hs-)(zr+ - zr-)
+  const T l0s = xf ? lL[3] : lL[6];
+  const T hsA = plus ? sf.hs : so.hs, hsB = plus ? so.hs : sf.hs;
+  const T zrA = plus ? sf.zr : so.zr, zrB = plus ? so.zr : sf.zr;
+  lr[0] += l0s * c * (zrA - zrB);
+  lr[3] += (plus ? T(1) : T(-1)) * l0s * c * (hsA + hsB);
 }
 
 // reverse of hll(): cotangents of (hL, unL, utL, hR, unR, utR) from those of F
@@ -841,8 +815,8 @@ __device__ double ghost_rev(const Par<T> &P, int e, int along, const Lim<T> &o, 
 // boundary cell of the inflow edge, the cotangent of Q(t).
 template <typename T, bool XF>
 __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const double *dts, const double *tt, int step,
-                                                  const T *Wfx, const T *Zfx, const T *cF, const T *cR, T *lim,
-                                                  double *lq) {
+                                                  const T *Wfx, const T *Zfx, const T *lY, const T *Y,
+                                                  const uint8_t *clip, T *lim, double *lq) {
   const long long nf = XF ? (long long)P.ny * (P.nx + 1) : (long long)(P.ny + 1) * P.nx;
   const long long fi = (long long)blockIdx.x * TPB + threadIdx.x;
   if (fi >= nf) return;
@@ -866,11 +840,23 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
   const T zf = tmax(lo.z, hi.z);
   const Side<T> sLo = revise_h(lo.h, lo.qx, lo.qy, lo.z, zf, P.hd);
   const Side<T> sHi = revise_h(hi.h, hi.qx, hi.qy, hi.z, zf, P.hd);
-  T lF[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int v = 0; v < 3; v++) {
-    if (hasLo) lF[v] += cF[(fLo * 3 + v) * n + kLo];
-    if (hasHi) lF[v] += cF[(fHi * 3 + v) * n + kHi];
+  // each adjacent cell's operator: its share of the flux cotangent and the
+  // cotangents of its own revised limits at this face
+  const T dt = (T)dts[step];
+  T lF[3] = {T(0), T(0), T(0)}, cLo[4] = {T(0), T(0), T(0), T(0)}, cHi[4] = {T(0), T(0), T(0), T(0)};
+  if (hasLo) {
+    T lo_[9], lL[9], f3[3];
+    stage_cot(P, stage, dt, lY, Y, clip, kLo, lo_, lL);
+    const Side<T> opp = own_revised(P, Wfx, Zfx, XF ? i - 1 : i, XF ? j : j - 1, fLo ^ 1);
+    cell_face_cot(P, fLo, lL, sLo, opp, f3, cLo);
+    lF[0] += f3[0]; lF[1] += f3[1]; lF[2] += f3[2];
+  }
+  if (hasHi) {
+    T lo_[9], lL[9], f3[3];
+    stage_cot(P, stage, dt, lY, Y, clip, kHi, lo_, lL);
+    const Side<T> opp = own_revised(P, Wfx, Zfx, i, j, fHi ^ 1);
+    cell_face_cot(P, fHi, lL, sHi, opp, f3, cHi);
+    lF[0] += f3[0]; lF[1] += f3[1]; lF[2] += f3[2];
   }
   T l6[6];
   if (XF) {
@@ -887,10 +873,11 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
   else { rLo[2] = l6[1]; rLo[1] = l6[2]; rHi[2] = l6[4]; rHi[1] = l6[5]; }
   rLo[3] = T(0);
   rHi[3] = T(0);
-  if (hasLo)
-    for (int q = 0; q < 4; q++) rLo[q] += cR[(fLo * 4 + q) * n + kLo];
-  if (hasHi)
-    for (int q = 0; q < 4; q++) rHi[q] += cR[(fHi * 4 + q) * n + kHi];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    rLo[q] += cLo[q];
+    rHi[q] += cHi[q];
+  }
   T gLo[4], gHi[4], lzf = T(0);
   revise_rev(lo, zf, P.hd, rLo[0], rLo[1], rLo[2], rLo[3], gLo, lzf);
   revise_rev(hi, zf, P.hd, rHi[0], rHi[1], rHi[2], rHi[3], gHi, lzf);
@@ -950,8 +937,9 @@ __global__ void k_rev_knots(Par<T> P, int stage, const double *dts, const double
 // neighbours' averages (lnb: direction, side A/B, variable), the bed's own
 // cotangents added to gz.
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, const T *X, const T *Z, const T *lWs, const T *limx,
-                                                   const T *limy, const T *cD, T *lXo, T *lnb, T *gz) {
+__global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, int stage, const double *dts, int step, const T *X,
+                                                   const T *Z, const T *lY, const T *Y, const uint8_t *clip, T *lW1,
+                                                   const T *limx, const T *limy, T *lXo, T *lnb, T *gz) {
   long long k;
   int i, j;
   if (!cell_of(P, k, i, j)) return;
@@ -983,14 +971,28 @@ __global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, const T *X, const T
     if (v < 3) { lw[3 * v] = a; lw[3 * v + 1] = bx; lw[3 * v + 2] = by; }
     else { lz[0] = a; lz[1] = bx; lz[2] = by; }
   }
-  lw[1] += cD[k];
-  lw[2] += cD[n + k];
-  lz[1] += cD[2 * n + k];
-  lz[2] += cD[3 * n + k];
-  T lX[9], gzz[3] = {T(0), T(0), T(0)}, nb[2][2][3] = {};
-  T lsw[9];
+  // the stage's output cotangent: the stored view's share (stage 2 also
+  // passes half to the stage-1 view) and the slope bed sources
+  // S1 = c2 h1 (h1 + z1) of the flux view
+  T lo_[9], lL[9], lsw[9];
+  stage_cot(P, stage, (T)dts[step], lY, Y, clip, k, lo_, lL);
 #pragma unroll
-  for (int m = 0; m < 9; m++) lsw[m] = lWs[m * n + k];
+  for (int m = 0; m < 9; m++) {
+    if (stage == 2) {
+      lsw[m] = T(0.5) * lo_[m];
+      lW1[m * n + k] = T(0.5) * lo_[m];
+    } else {
+      lsw[m] = lo_[m] + lW1[m * n + k];
+    }
+  }
+  {
+    const T c2 = -(T(2) * s3 * P.g / P.dx);
+    lw[1] += lL[4] * c2 * (T(2) * wf[1] + ze[1]);
+    lw[2] += lL[8] * c2 * (T(2) * wf[2] + ze[2]);
+    lz[1] += lL[4] * c2 * wf[1];
+    lz[2] += lL[8] * c2 * wf[2];
+  }
+  T lX[9], gzz[3] = {T(0), T(0), T(0)}, nb[2][2][3] = {};
   if (r.red) {
 #pragma unroll
     for (int m = 0; m < 9; m++) lX[m] = T(0);
@@ -1153,8 +1155,8 @@ struct mwdg_adj {
   unsigned long long *best = nullptr;
   void *Un = nullptr, *Ui = nullptr, *W1 = nullptr, *F1 = nullptr, *Z1 = nullptr;
   void *W2 = nullptr, *F2 = nullptr, *Z2 = nullptr;
-  void *lU = nullptr, *lX = nullptr, *lWs = nullptr, *lW1 = nullptr, *cF = nullptr, *cR = nullptr,
-       *cD = nullptr, *limx = nullptr, *limy = nullptr, *lXo = nullptr, *lnb = nullptr;
+  void *lU = nullptr, *lX = nullptr, *lW1 = nullptr, *limx = nullptr, *limy = nullptr, *lXo = nullptr,
+       *lnb = nullptr;
   double *lq = nullptr;
   std::string err;
 };
@@ -1192,8 +1194,7 @@ struct Timed {
 void free_all(mwdg_adj *a) {
   free_events(a);
   void *ptrs[] = {a->tape, a->clip, a->tt, a->dtbuf, a->best, a->Un, a->Ui, a->W1, a->F1, a->Z1, a->W2,
-                  a->F2, a->Z2, a->lU, a->lX, a->lWs, a->lW1, a->cF, a->cR, a->cD, a->limx, a->limy,
-                  a->lXo, a->lnb, a->lq};
+                  a->F2, a->Z2, a->lU, a->lX, a->lW1, a->limx, a->limy, a->lXo, a->lnb, a->lq};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -1321,9 +1322,8 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
   const long long nfx = (long long)a->p.ny * (a->p.nx + 1), nfy = (long long)(a->p.ny + 1) * a->p.nx;
   T *Un = ptr<T>(a->Un), *Ui = ptr<T>(a->Ui), *F1 = ptr<T>(a->F1), *Z1 = ptr<T>(a->Z1);
   T *F2 = ptr<T>(a->F2), *Z2 = ptr<T>(a->Z2);
-  T *lU = ptr<T>(a->lU), *lX = ptr<T>(a->lX), *lWs = ptr<T>(a->lWs), *lW1 = ptr<T>(a->lW1);
-  T *cF = ptr<T>(a->cF), *cR = ptr<T>(a->cR), *cD = ptr<T>(a->cD), *limx = ptr<T>(a->limx),
-    *limy = ptr<T>(a->limy), *lXo = ptr<T>(a->lXo), *lnb = ptr<T>(a->lnb);
+  T *lU = ptr<T>(a->lU), *lX = ptr<T>(a->lX), *lW1 = ptr<T>(a->lW1);
+  T *limx = ptr<T>(a->limx), *limy = ptr<T>(a->limy), *lXo = ptr<T>(a->lXo), *lnb = ptr<T>(a->lnb);
   // the tape: the run recomputed from its checkpoint U0 over the given steps,
   // unless the caller states that the last forward call left it in place
   if (steps > 0 && cudaMemcpyAsync(a->dtbuf, dts_in, (size_t)steps * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1353,13 +1353,10 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
       const T *Zf = stage == 2 ? Z2 : Z1;
       const T *lY = stage == 2 ? lU : lX;
       {
-        Timed tm(a, MWDG_ADJ_KC_REV_CELL, st);
-        k_rev_cell<T><<<nb, TPB, 0, st>>>(P, stage, lY, Y, clip, dts, a->tt, k, Wf, Zf, lWs, lW1, cF, cR, cD);
-      }
-      {
         Timed tm(a, MWDG_ADJ_KC_REV_FACE, st);
-        k_rev_face<T, true><<<blocks(nfx), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, cF, cR, limx, a->lq);
-        k_rev_face<T, false><<<blocks(nfy), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, cF, cR, limy, a->lq);
+        k_rev_face<T, true><<<blocks(nfx), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, lY, Y, clip, limx, a->lq);
+        k_rev_face<T, false><<<blocks(nfy), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, lY, Y, clip, limy,
+                                                          a->lq);
       }
       if (P.nknots > 0) {
         Timed tm(a, MWDG_ADJ_KC_REV_KNOTS, st);
@@ -1367,7 +1364,7 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
       }
       {
         Timed tm(a, MWDG_ADJ_KC_REV_LIMIT, st);
-        k_rev_limit<T><<<nb, TPB, 0, st>>>(P, X, z, lWs, limx, limy, cD, lXo, lnb, gz);
+        k_rev_limit<T><<<nb, TPB, 0, st>>>(P, stage, dts, k, X, z, lY, Y, clip, lW1, limx, limy, lXo, lnb, gz);
       }
       Timed tm(a, MWDG_ADJ_KC_REV_GATHER, st);
       k_rev_gather<T><<<nb, TPB, 0, st>>>(P, lXo, lnb, lX, gz);
@@ -1433,13 +1430,10 @@ mwdg_status mwdg_adj_create(const mwdg_adj_params *p, mwdg_adj **out) {
   alloc((void **)&a->tt, S + 1, sizeof(double));
   alloc((void **)&a->dtbuf, S, sizeof(double));
   alloc((void **)&a->best, 1, sizeof(unsigned long long));
-  for (void **w : {&a->Un, &a->Ui, &a->W1, &a->F1, &a->W2, &a->F2, &a->lU, &a->lX, &a->lWs, &a->lW1, &a->lXo})
+  for (void **w : {&a->Un, &a->Ui, &a->W1, &a->F1, &a->W2, &a->F2, &a->lU, &a->lX, &a->lW1, &a->lXo})
     alloc(w, 9 * n, E);
   alloc(&a->Z1, 3 * n, E);
   alloc(&a->Z2, 3 * n, E);
-  alloc(&a->cF, 12 * n, E);
-  alloc(&a->cR, 16 * n, E);
-  alloc(&a->cD, 4 * n, E);
   alloc(&a->lnb, 12 * n, E);
   alloc(&a->limx, 8 * nfx, E);
   alloc(&a->limy, 8 * nfy, E);
