@@ -555,7 +555,7 @@ ADJ_VALUES_PER_CELL = {"friction": 19, "limit": 33, "update": 34.5, "cfl": 3, "r
 ADJ_FLAG_BYTES = {"update": 1, "rev_face": 1, "rev_limit": 1}
 # DRAM bytes (read + write) per launch measured by ncu for the FP32 adjoint
 # kernels at this workload, while the kernel is unchanged (see profiles/)
-ADJ_TRAFFIC = {}
+ADJ_TRAFFIC = {"update": 108_080_000 + 33_630_000}  # ncu: mean of 6 stage launches, dram read + write
 
 
 def adjoint_roofline(times, cells, elem):
