@@ -302,12 +302,22 @@ def run_gpu(args, rank, world):
                        "ms_per_step": sum(ms64) / len(ms64), "dtype": "f64"}
         tcmp = max(s64.get_time()[0], s32.get_time()[0]) + 1.0
         a32, a64 = make_solver(p, M.F32, sptr), make_solver(p, M.F64, sptr)
-        acc = []
+        # the method's own sensitivity: a second FP64 run whose only
+        # difference is one extra stop (one shortened step) at 150.5 s
+        b64 = make_solver(p, M.F64, sptr)
+        acc, self64 = [], []
         for t in (60.0, 300.0, 900.0, tcmp):
             a32.run_to_time(t)
             a64.run_to_time(t)
             acc.append(compare_depths(a32, a64, t))
+            if t == 60.0:
+                b64.run_to_time(60.0)
+                b64.run_to_time(150.5)
+            elif t in (300.0, 900.0):
+                b64.run_to_time(t)
+                self64.append(compare_depths(b64, a64, t))
         out["accuracy_f32_vs_f64"] = acc
+        out["fp64_vs_fp64_one_extra_stop"] = self64
     return out
 
 
@@ -340,8 +350,6 @@ def compare_depths(s32, s64, t):
     h32, _, _ = s32.read_fields()
     h64, _, _ = s64.read_fields()
     return {"t": t, "planes": scores(h32, h64), "averages": scores(average_raster(s32), average_raster(s64))}
-
-    return out
 
 
 def reference_arm(args):
@@ -643,7 +651,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": out["roofline"], "cpu_baseline": cb, "e2e": out["e2e"], "clocks": out["clocks"],
                 "gpu_launches": out["gpu_launches"]}
-        for k in ("fp64", "accuracy_f32_vs_f64"):
+        for k in ("fp64", "accuracy_f32_vs_f64", "fp64_vs_fp64_one_extra_stop"):
             if k in out:
                 line[k] = out[k]
         print(json.dumps(line))
