@@ -335,3 +335,25 @@ def test_grading_is_minimal_on_tiny_grid():
                     added += 1
                 assert ok, (l, ii, jj)
     assert added > 0
+
+
+def test_projection_matches_the_printed_eq8_examples():
+    """tests/golden/eq8_projection.txt: one element per line, its four
+    vertex heights and the planes evaluated by hand from Eq. 8a-c."""
+    import math
+    from pathlib import Path
+    import numpy as np
+    import oracle as O
+    rows = []
+    for line in (Path(__file__).parent / "golden" / "eq8_projection.txt").read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        verts, z0, nums = (part.split() for part in line.split("|"))
+        rows.append(([float(v) for v in verts], float(z0[0]), [float(x) for x in nums]))
+    assert len(rows) >= 5
+    for (sw, se, nw, ne), z0, (nx_, ny_) in rows:
+        vert = np.array([[sw, se], [nw, ne]])      # row j = 0 south, j = 1 north
+        c0, c1x, c1y = O.project(vert)
+        assert abs(c0[0, 0] - z0) <= 1e-15 * max(1.0, abs(z0))
+        assert abs(c1x[0, 0] - nx_ / (4.0 * math.sqrt(3.0))) <= 1e-15
+        assert abs(c1y[0, 0] - ny_ / (4.0 * math.sqrt(3.0))) <= 1e-15
