@@ -48,7 +48,8 @@ def _cases():
     dam = S.dam_break_circular(n=32, L=0, radius=6.0, h_out=0.0)
     lake = S.lake_at_rest(n=24, L=0, islands=True)
     rain = replace(lake, rain_rate=2e-3, rain_t_end=5.0, n_manning=0.03)
-    return [("reach", reach, 30), ("dam_dry", dam, 30), ("rain_islands", rain, 20)]
+    rect = S.crop(S.adjoint_reach(n=64)[0], 0, 18, 40, 28, 0)
+    return [("reach", reach, 30), ("dam_dry", dam, 30), ("rain_islands", rain, 20), ("rect_40x28", rect, 20)]
 
 
 @pytest.mark.parametrize("name,p,K", _cases(), ids=[c[0] for c in _cases()])
