@@ -23,8 +23,10 @@ tests):
   DG2 step (Eq. 4, HLL, revisions) pinned: lake at rest (wet and with
                                   islands), Ritter and Stoker dam breaks,
                                   volume conservation, D4 symmetry
-  friction, limiter, non-homogeneous interface rule:
-                                  parity unpinned beyond the invariants above
+  friction                        pinned: exact decay of a uniform flow
+  limiter                         pinned: hand-evaluated minmod cases (through
+                                  the bit-exact restatement in dg2_adjoint.py)
+  non-homogeneous interface rule  parity unpinned beyond the invariants above
   discrete adjoint of the uniform DG2 step (dg2_adjoint.py, PyTorch CPU
   autograd over a restatement of the step):
                                   pinned: bit-for-bit forward against the C

@@ -12,6 +12,7 @@ here against things outside itself:
   * still water: no sensitivity to Manning n or to a hydrograph that does not
     flow.
 """
+import math
 from dataclasses import replace
 
 import numpy as np
@@ -198,3 +199,42 @@ def test_valley_crop_gradients_converge_to_central_differences():
     for name, ad, fd in checks:
         assert ad != 0.0, name
         assert abs(ad - fd) <= 1e-4 * abs(ad), (name, ad, fd)
+
+
+def test_limiter_hand_examples():
+    """Stage-input limiting on a 3 x 1 strip, evaluated by hand (minmod on the
+    interface offsets sqrt3 v1 against the neighbour differences of the
+    averages; the restated limiter is the C oracle's, bit for bit, through
+    the forward-step test above):
+      cell 1: a = 0.75, forward 0.5, backward 0.25 -> 0.25 (smallest, same sign)
+      cell 0: a = 0.125, forward 0.25 (one neighbour) -> kept
+      cell 2: a = -0.1, backward 0.5 (opposite signs) -> 0
+    (dyadic averages, so the differences are exact)
+    and a cell with h0 below h_dry is reduced to a flat free surface over
+    its planar bed: h1 = -z1, discharge slopes zero, the flux view flat."""
+    s3 = math.sqrt(3.0)
+    P = A.Grid(nx=3, ny=1, dx=1.0)
+    X = np.zeros((9, 1, 3))
+    X[0, 0] = [1.0, 1.25, 1.75]
+    X[1, 0] = [0.125 / s3, 0.75 / s3, -0.1 / s3]
+    X[3, 0] = [0.1, 0.1, 0.1]
+    X[4, 0] = [0.0, 0.02 / s3, 0.0]       # qx slope, differences 0 and 0: limited to 0
+    z = np.zeros((3, 1, 3))
+    w_st, w_fx, ze = A.limit([torch.tensor(x) for x in X], [torch.tensor(x) for x in z], P)
+    slope = w_st[1].numpy()[0]
+    assert slope[1] == 0.25 / s3
+    assert slope[0] == 0.125 / s3
+    assert slope[2] == 0.0
+    assert w_st[4].numpy()[0, 1] == 0.0
+    # partial-wet reduction
+    X2 = np.zeros((9, 1, 3))
+    X2[0, 0] = [1.0, 0.0005, 1.0]
+    X2[1, 0] = [0.0, 0.3, 0.0]
+    X2[3, 0] = [0.0, 0.001, 0.0]
+    X2[4, 0] = [0.0, 0.2, 0.0]
+    z2 = np.zeros((3, 1, 3))
+    z2[1, 0] = [0.0, 0.25, 0.0]
+    w_st, w_fx, ze = A.limit([torch.tensor(x) for x in X2], [torch.tensor(x) for x in z2], P)
+    assert w_st[1].numpy()[0, 1] == -0.25 and w_st[4].numpy()[0, 1] == 0.0
+    assert w_st[3].numpy()[0, 1] == 0.001
+    assert w_fx[1].numpy()[0, 1] == 0.0 and ze[1].numpy()[0, 1] == 0.0
