@@ -23,9 +23,10 @@
  *                           finer elements at non-homogeneous interfaces)
  * The paper delegates the DG2 operator details (HLL, wet/dry revisions,
  * friction, limiter, filter entries) to cited works; the readings used here
- * are listed beside each function.  Parts with no closed form to pin them
- * (friction, limiter, non-homogeneous interface rule) are "parity unpinned"
- * beyond invariants.
+ * are listed beside each function.  Friction is pinned by the exact decay
+ * of a uniform flow and the limiter by hand-evaluated minmod cases; the
+ * non-homogeneous interface rule has no closed form to pin it and is
+ * "parity unpinned" beyond invariants.
  */
 #include <math.h>
 #include <stdint.h>
