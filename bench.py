@@ -490,7 +490,7 @@ def run_adjoint(args):
     def measure(precision, prof=False):
         adj = Dg2Adjoint(p.nx, p.ny, p.dx, cfl=p.cfl, dt_max=p.dt_max, limiter=p.limiter, bc=tuple(p.bc),
                          inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, max_steps=K,
-                         precision=precision)
+                         precision=precision, tape_views=True)
         dev = adj.device
         U0 = torch.cat([adj.project(p.h_vert), adj.project(p.qx_vert), adj.project(p.qy_vert)])
         z = adj.project(p.z_vert)
@@ -545,9 +545,10 @@ def run_adjoint(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"DG2 adjoint, {p.nx}x{p.ny} uniform valley (seed 1), dx=10 m, flowing start, "
                                    f"60-knot hydrograph, 16 gauges, squared depth misfit, segment {K} steps",
-                       "inputs": "tape and state arrays far larger than L2"},
+                       "inputs": "tape and state arrays far larger than L2",
+                       "tape": "each step's state, stage inputs and flux views (51 coefficients per cell)"},
             "forward_ms": r32["forward_ms"], "backward_ms": r32["backward_ms"], "simulated_s": r32["simulated_s"],
-            "max_abs_grad": r32["max_abs_grad"], "gpu_launches": 29 * K + 3, "clocks": r32["clocks"],
+            "max_abs_grad": r32["max_abs_grad"], "gpu_launches": 18 * K + 1, "clocks": r32["clocks"],
             "roofline": roof, "fp64": r64, "cpu_baseline": cb}
     if r64 is not None:
         r64.pop("kernel_ms", None)
@@ -563,7 +564,8 @@ ADJ_VALUES_PER_CELL = {"friction": 19, "limit": 33, "update": 34.5, "cfl": 3, "r
 ADJ_FLAG_BYTES = {"update": 1, "rev_face": 1, "rev_limit": 1}
 # DRAM bytes (read + write) per launch measured by ncu for the FP32 adjoint
 # kernels at this workload, while the kernel is unchanged (see profiles/)
-ADJ_TRAFFIC = {"update": 108_080_000 + 33_630_000}  # ncu: mean of 6 stage launches, dram read + write
+ADJ_TRAFFIC = {"update": 108_080_000 + 33_630_000,     # ncu: mean of 6 stage launches, dram read + write
+               "rev_face": 64_010_000 * 2 + 4_800_000 + 3_190_000}  # ncu: the x and y kernels of a stage
 
 
 def adjoint_roofline(times, cells, elem):

@@ -41,9 +41,10 @@
  *
  * Work is queued on the given CUDA stream (NULL: the legacy default stream);
  * no call synchronises it, except mwdg_adj_create and mwdg_adj_destroy.  A
- * context holds a tape of max_steps + 1 states (9 n coefficients each) and
- * about 100 n coefficients of work arrays; one host thread uses it at a
- * time, and its calls on one stream run in order.  Statuses are those of mwdg.h.
+ * context holds a tape of max_steps + 1 states (9 n coefficients each), with
+ * tape_views 42 n more per step, and about 100 n coefficients of work
+ * arrays; one host thread uses it at a time, and its calls on one stream run
+ * in order.  Statuses are those of mwdg.h.
  */
 #ifndef MWDG_ADJOINT_H
 #define MWDG_ADJOINT_H
@@ -70,10 +71,15 @@ typedef struct {
   double rain_rate, rain_t_end; /* m/s while t < rain_t_end                  */
   int32_t max_steps;       /* tape capacity: steps per forward/backward call */
   int32_t precision;       /* MWDG_F64 or MWDG_F32                           */
+  int32_t tape_views;      /* 1: the tape also keeps each step's two stage   */
+                           /* inputs and flux views (42 n coefficients per   */
+                           /* step more), so the reverse sweep recomputes    */
+                           /* nothing; 0: it recomputes them step by step    */
 } mwdg_adj_params;
 
 /* Defaults: g = 9.80665, h_dry = 1e-3, cfl = 0.33, dt_max = 1, limiter on,
- * walls, no inflow, no rain, max_steps = 200, FP64; nx, ny, dx must be set. */
+ * walls, no inflow, no rain, max_steps = 200, FP64, tape of states only;
+ * nx, ny, dx must be set. */
 MWDG_API mwdg_status mwdg_adj_params_default(mwdg_adj_params *p);
 
 /* Allocates the context on the current device.  MWDG_ERR_DIMS when nx or ny

@@ -35,7 +35,7 @@ class AdjParams(C.Structure):
         ("cfl", C.c_double), ("dt_max", C.c_double), ("limiter", C.c_int32), ("bc", C.c_int32 * 4),
         ("inflow_edge", C.c_int32), ("inflow_c0", C.c_int32), ("inflow_c1", C.c_int32),
         ("rain_rate", C.c_double), ("rain_t_end", C.c_double), ("max_steps", C.c_int32),
-        ("precision", C.c_int32),
+        ("precision", C.c_int32), ("tape_views", C.c_int32),
     ]
 
 
@@ -77,7 +77,7 @@ class Dg2Adjoint:
 
     def __init__(self, nx, ny, dx, *, g=9.80665, h_dry=1e-3, cfl=0.33, dt_max=1.0, limiter=1,
                  bc=(WALL, WALL, WALL, WALL), inflow_edge=-1, inflow_c0=0, inflow_c1=-1, rain_rate=0.0,
-                 rain_t_end=0.0, max_steps=200, precision=F64):
+                 rain_t_end=0.0, max_steps=200, precision=F64, tape_views=False):
         import torch
         if not torch.cuda.is_available():
             raise MwdgError(-3, "Dg2Adjoint", "no CUDA device")
@@ -90,6 +90,7 @@ class Dg2Adjoint:
         p.inflow_edge, p.inflow_c0, p.inflow_c1 = inflow_edge, inflow_c0, inflow_c1
         p.rain_rate, p.rain_t_end, p.max_steps = rain_rate, rain_t_end, max_steps
         p.precision = precision
+        p.tape_views = int(bool(tape_views))
         h = C.c_void_p()
         st = L.mwdg_adj_create(C.byref(p), C.byref(h))
         if st != 0:

@@ -1146,6 +1146,7 @@ struct mwdg_adj {
   std::vector<int> ev_class;
   size_t ev_used = 0;
   int tape_steps = -1;         // steps of the run the tape holds (-1: none)
+  bool views = false;          // the tape also keeps each step's stage inputs and flux views
   long long n = 0;
   size_t elem = 8;             // bytes per coefficient (8 FP64, 4 FP32)
   void *tape = nullptr;        // (max_steps + 1) x 9n: the state at the start of each step
@@ -1238,14 +1239,30 @@ Par<T> make_par(const mwdg_adj *a, int nknots, const double *kt, const double *k
 
 template <typename T> T *ptr(void *p) { return static_cast<T *>(p); }
 
+// where step s keeps its two stage inputs (Un, Ui) and their flux views
+// (F1, Z1, F2, Z2): per-step slots of the tape when it keeps them, else one
+// set of work arrays that the reverse sweep refills step by step
+template <typename T>
+struct StageArrays {
+  T *Un, *Ui, *F1, *Z1, *F2, *Z2;
+};
+
+template <typename T>
+StageArrays<T> stage_arrays(const mwdg_adj *a, int s) {
+  const long long n = a->n, o9 = a->views ? (long long)s * 9 * n : 0, o3 = a->views ? (long long)s * 3 * n : 0;
+  return StageArrays<T>{ptr<T>(a->Un) + o9, ptr<T>(a->Ui) + o9, ptr<T>(a->F1) + o9,
+                        ptr<T>(a->Z1) + o3, ptr<T>(a->F2) + o9, ptr<T>(a->Z2) + o3};
+}
+
 // friction, limit, stage 1 and limit of step s: the two stage inputs (Un, Ui)
 // and their stored and flux views
 template <typename T>
 void recompute_stages(mwdg_adj *a, const Par<T> &P, const T *U, const T *z, const T *nman, int s, const double *dts,
                       uint8_t *clip, cudaStream_t st) {
   const unsigned nb = blocks(a->n);
-  T *Un = ptr<T>(a->Un), *Ui = ptr<T>(a->Ui), *W1 = ptr<T>(a->W1), *F1 = ptr<T>(a->F1), *Z1 = ptr<T>(a->Z1);
-  T *W2 = ptr<T>(a->W2), *F2 = ptr<T>(a->F2), *Z2 = ptr<T>(a->Z2);
+  const StageArrays<T> v = stage_arrays<T>(a, s);
+  T *Un = v.Un, *Ui = v.Ui, *W1 = ptr<T>(a->W1), *F1 = v.F1, *Z1 = v.Z1;
+  T *W2 = ptr<T>(a->W2), *F2 = v.F2, *Z2 = v.Z2;
   {
     Timed tm(a, MWDG_ADJ_KC_FRICTION, st);
     k_friction<T><<<nb, TPB, 0, st>>>(P, U, nman, dts, a->tt, s, Un);
@@ -1278,10 +1295,10 @@ void launch_step(mwdg_adj *a, const Par<T> &P, const T *z, const T *nman, int s,
     k_dt<<<1, 1, 0, st>>>(P.cfl, P.dt_max, a->best, dts, a->tt, s);
   }
   recompute_stages<T>(a, P, U, z, nman, s, dts, clip, st);
+  const StageArrays<T> v = stage_arrays<T>(a, s);
   const dim3 tiles((P.nx + UT - 1) / UT, (P.ny + UT - 1) / UT);
   Timed tm(a, MWDG_ADJ_KC_UPDATE, st);
-  k_update<T><<<tiles, UT * UT, 0, st>>>(P, 2, ptr<T>(a->F2), ptr<T>(a->Z2), ptr<T>(a->W2), ptr<T>(a->W1), dts, a->tt,
-                                         s, Unext, clip);
+  k_update<T><<<tiles, UT * UT, 0, st>>>(P, 2, v.F2, v.Z2, ptr<T>(a->W2), ptr<T>(a->W1), dts, a->tt, s, Unext, clip);
 }
 
 mwdg_status check_run(mwdg_adj *a, const void *U0, const void *z, const void *n, int32_t nknots, const double *kt,
@@ -1320,8 +1337,6 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
   const size_t bytes = (size_t)9 * n * sizeof(T);
   const unsigned nb = blocks(n);
   const long long nfx = (long long)a->p.ny * (a->p.nx + 1), nfy = (long long)(a->p.ny + 1) * a->p.nx;
-  T *Un = ptr<T>(a->Un), *Ui = ptr<T>(a->Ui), *F1 = ptr<T>(a->F1), *Z1 = ptr<T>(a->Z1);
-  T *F2 = ptr<T>(a->F2), *Z2 = ptr<T>(a->Z2);
   T *lU = ptr<T>(a->lU), *lX = ptr<T>(a->lX), *lW1 = ptr<T>(a->lW1);
   T *limx = ptr<T>(a->limx), *limy = ptr<T>(a->limy), *lXo = ptr<T>(a->lXo), *lnb = ptr<T>(a->lnb);
   // the tape: the run recomputed from its checkpoint U0 over the given steps,
@@ -1343,9 +1358,12 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
     const T *U = ptr<T>(a->tape) + (long long)k * 9 * n;
     const T *Y2 = ptr<T>(a->tape) + (long long)(k + 1) * 9 * n;
     uint8_t *clip = a->clip + (long long)k * n;
-    // recompute the stage inputs of step k (stage 1 rewrites its clip bit
-    // with the same value and keeps stage 2's from the tape run)
-    recompute_stages<T>(a, P, U, z, nman, k, dts, clip, st);
+    // the stage inputs of step k and their flux views: kept on the tape, or
+    // recomputed (stage 1 then rewrites its clip bit with the same value and
+    // keeps stage 2's from the tape run)
+    if (!a->views) recompute_stages<T>(a, P, U, z, nman, k, dts, clip, st);
+    const StageArrays<T> v = stage_arrays<T>(a, k);
+    const T *Un = v.Un, *Ui = v.Ui, *F1 = v.F1, *Z1 = v.Z1, *F2 = v.F2, *Z2 = v.Z2;
     for (int stage = 2; stage >= 1; stage--) {
       const T *X = stage == 2 ? Ui : Un;
       const T *Y = stage == 2 ? Y2 : Ui;
@@ -1394,6 +1412,7 @@ mwdg_status mwdg_adj_params_default(mwdg_adj_params *p) {
   p->inflow_c1 = -1;
   p->max_steps = 200;
   p->precision = MWDG_F64;
+  p->tape_views = 0;
   return MWDG_OK;
 }
 
@@ -1430,10 +1449,12 @@ mwdg_status mwdg_adj_create(const mwdg_adj_params *p, mwdg_adj **out) {
   alloc((void **)&a->tt, S + 1, sizeof(double));
   alloc((void **)&a->dtbuf, S, sizeof(double));
   alloc((void **)&a->best, 1, sizeof(unsigned long long));
-  for (void **w : {&a->Un, &a->Ui, &a->W1, &a->F1, &a->W2, &a->F2, &a->lU, &a->lX, &a->lW1, &a->lXo})
-    alloc(w, 9 * n, E);
-  alloc(&a->Z1, 3 * n, E);
-  alloc(&a->Z2, 3 * n, E);
+  a->views = p->tape_views != 0;
+  const long long SV = a->views ? S : 1;   // copies of the stage arrays
+  for (void **w : {&a->Un, &a->Ui, &a->F1, &a->F2}) alloc(w, SV * 9 * n, E);
+  alloc(&a->Z1, SV * 3 * n, E);
+  alloc(&a->Z2, SV * 3 * n, E);
+  for (void **w : {&a->W1, &a->W2, &a->lU, &a->lX, &a->lW1, &a->lXo}) alloc(w, 9 * n, E);
   alloc(&a->lnb, 12 * n, E);
   alloc(&a->limx, 8 * nfx, E);
   alloc(&a->limy, 8 * nfy, E);

@@ -42,11 +42,12 @@ def state(sim, p):
     return co.T.reshape(9, p.ny, p.nx).copy()
 
 
-def context(p, max_steps, precision=0):
+def context(p, max_steps, precision=0, tape_views=False):
     from paper_2107_02750_gb300.adjoint import Dg2Adjoint
     return Dg2Adjoint(p.nx, p.ny, p.dx, cfl=p.cfl, dt_max=p.dt_max, limiter=p.limiter, bc=tuple(p.bc),
                       inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1,
-                      rain_rate=p.rain_rate, rain_t_end=p.rain_t_end, max_steps=max_steps, precision=precision)
+                      rain_rate=p.rain_rate, rain_t_end=p.rain_t_end, max_steps=max_steps, precision=precision,
+                      tape_views=tape_views)
 
 
 def device_inputs(adj, p):
@@ -275,15 +276,17 @@ def test_f32_adjoint_tracks_the_fp64_oracle(name, p, K):
 
 
 def test_tape_reuse_gives_the_recomputed_gradients():
-    """The backward may reuse the tape the forward left (reuse_tape); the
-    gradients equal those of a backward that recomputes the segment from its
+    """The backward may reuse the tape the forward left (reuse_tape), and the
+    tape may keep each step's stage inputs and flux views (tape_views); the
+    gradients equal those of a backward that recomputes everything from the
     checkpoint, bit for bit, in both precisions.  A tape of another length is
     refused."""
     import torch
     import paper_2107_02750_gb300 as M
     p, _ = S.adjoint_reach(n=32)
-    for precision in (M.F64, M.F32):
-        adj = context(p, 20, precision=precision)
+    ref = {}
+    for precision, views in ((M.F64, False), (M.F32, False), (M.F64, True), (M.F32, True)):
+        adj = context(p, 20, precision=precision, tape_views=views)
         U0, z, n, kt, kQ = device_inputs(adj, p)
         seed = torch.randn((9, p.ny, p.nx), generator=torch.Generator().manual_seed(3)).to(U0)
         _, d = adj.forward(U0, z, n, kt, kQ, 0.0, 20)
@@ -292,6 +295,10 @@ def test_tape_reuse_gives_the_recomputed_gradients():
         b = adj.backward(U0, z, n, kt, kQ, 0.0, d, seed, reuse_tape=True)
         for x, y in zip(a, b):
             assert torch.equal(x, y)
+        if precision in ref:
+            for x, y in zip(ref[precision], a):
+                assert torch.equal(x, y)
+        ref[precision] = a
         adj.forward(U0, z, n, kt, kQ, 0.0, 10, dts=d[:10])
         with pytest.raises(M.MwdgError):
             adj.backward(U0, z, n, kt, kQ, 0.0, d, seed, reuse_tape=True)
