@@ -1910,40 +1910,54 @@ __device__ __noinline__ bool reflux_face(const Geo &g, const Ptrs<T> &p, int l, 
   return true;
 }
 
-// The operator and update of variable v (0 h, 1 qx, 2 qy) of one leaf from
-// its four interfaces (flux component v, own revised limits): L0 from the
-// flux difference and the bed source with the revised interface beds, the
-// slopes from the two-point interface rule with the bed source
-// S1 = -(2 sqrt3 g / dx) h1 (h1 + z1) that cancels its hydrostatic error at
-// rest, then Eq. 4a (STAGE 1) or Eq. 4b (STAGE 2).
+// The operator and update of variable v (0 h, 1 qx, 2 qy) of one leaf:
+// L0 from the flux difference and the bed source with the revised
+// interface beds, the slopes from the two-point interface rule with the bed
+// source S1 = -(2 sqrt3 g / dx) h1 (h1 + z1) that cancels its hydrostatic
+// error at rest, then Eq. 4a (STAGE 1) or Eq. 4b (STAGE 2).  Each
+// direction's share is formed as soon as its two interfaces are known.
+// physical flux component v of a revised limit (hs, us, vs): across an x
+// face (F) or a y face (G)
+template <typename T>
+__device__ __forceinline__ T phys_flux(bool xdir, int v, T hs, T us, T vs, T gg) {
+  if (xdir) {
+    const T q = hs * us;
+    return v == 0 ? q : (v == 1 ? q * us + T(0.5) * gg * hs * hs : q * vs);
+  }
+  const T r = hs * vs;
+  return v == 0 ? r : (v == 1 ? r * us : r * vs + T(0.5) * gg * hs * hs);
+}
+
+// One direction's share of the operator, formed as soon as its two faces are
+// known (so the four faces' fluxes and revised limits need not stay live):
+// per variable the flux difference (F+ - F-) and the slope sum
+// ((F+ + F-) - P+) - P- with P the physical flux of the own revised limits;
+// and the bed-source factors (hs+ + hs-), (zr+ - zr-).
+template <typename T>
+struct DirTerms {
+  T d[3], s[3], hsum, zdif;
+};
+
+template <typename T>
+__device__ __forceinline__ void dir_terms(bool xdir, const FaceOut<T> &a, const FaceOut<T> &b, T gg, DirTerms<T> &o) {
+  const T Fa[3] = {a.F0, a.F1, a.F2}, Fb[3] = {b.F0, b.F1, b.F2};
+#pragma unroll
+  for (int v = 0; v < 3; v++) {
+    o.d[v] = Fa[v] - Fb[v];
+    o.s[v] = Fa[v] + Fb[v] - phys_flux(xdir, v, a.hs, a.us, a.vs, gg) - phys_flux(xdir, v, b.hs, b.us, b.vs, gg);
+  }
+  o.hsum = a.hs + b.hs;
+  o.zdif = a.zr - b.zr;
+}
+
+// the update of variable v from the two directions' terms
 template <typename T, int STAGE>
-__device__ __forceinline__ void finish_var(const Geo &g, const Ptrs<T> &p, int v, long long k, int l,
-                                           const T (&w)[9], const T (&zc)[3], const T (&Fv)[4],
-                                           const T (&hs)[4], const T (&us)[4], const T (&vs)[4],
-                                           const T (&zr)[4], T dt, const T *Wst, const T *Wcomb,
-                                           T &o0, T &o1, T &o2) {
+__device__ __forceinline__ void finish_var_dir(const Geo &g, int v, long long k, int l, const T (&w)[9],
+                                               const T (&zc)[3], const DirTerms<T> &X, const DirTerms<T> &Y, T dt,
+                                               const T *Wst, const T *Wcomb, T &o0, T &o1, T &o2) {
   const long long P = g.P;
   const T gg = geo_g<T>(g), s3 = s3v<T>();
   const T dxl = geo_dx<T>(g, l);
-  // physical fluxes of the own revised limits, component v
-  T Fx0, Fx1, Gy0, Gy1;
-  {
-    T q0 = hs[0] * us[0], q1 = hs[1] * us[1], r2 = hs[2] * vs[2], r3 = hs[3] * vs[3];
-    if (v == 0) {
-      Fx0 = q0; Fx1 = q1; Gy0 = r2; Gy1 = r3;
-    } else if (v == 1) {
-      Fx0 = q0 * us[0] + T(0.5) * gg * hs[0] * hs[0];
-      Fx1 = q1 * us[1] + T(0.5) * gg * hs[1] * hs[1];
-      Gy0 = r2 * us[2];
-      Gy1 = r3 * us[3];
-    } else {
-      Fx0 = q0 * vs[0];
-      Fx1 = q1 * vs[1];
-      Gy0 = r2 * vs[2] + T(0.5) * gg * hs[2] * hs[2];
-      Gy1 = r3 * vs[3] + T(0.5) * gg * hs[3] * hs[3];
-    }
-  }
-  // slopes of the depth for the bed source: h1 and eta1 = h1 + z1
   T h1x, h1y, e1x, e1y;
   if (Form<T>::eta) {
     e1x = w[1]; e1y = w[2];
@@ -1952,11 +1966,11 @@ __device__ __forceinline__ void finish_var(const Geo &g, const Ptrs<T> &p, int v
     h1x = w[1]; h1y = w[2];
     e1x = w[1] + zc[1]; e1y = w[2] + zc[2];
   }
-  T L0 = -(Fv[0] - Fv[1]) / dxl - (Fv[2] - Fv[3]) / dxl;
-  if (v == 1) L0 = L0 + -gg * T(0.5) * (hs[0] + hs[1]) * (zr[0] - zr[1]) / dxl;
-  if (v == 2) L0 = L0 + -gg * T(0.5) * (hs[2] + hs[3]) * (zr[2] - zr[3]) / dxl;
-  T L1x = -(s3 / dxl) * (Fv[0] + Fv[1] - Fx0 - Fx1);
-  T L1y = -(s3 / dxl) * (Fv[2] + Fv[3] - Gy0 - Gy1);
+  T L0 = -(X.d[v]) / dxl - (Y.d[v]) / dxl;
+  if (v == 1) L0 = L0 + -gg * T(0.5) * X.hsum * X.zdif / dxl;
+  if (v == 2) L0 = L0 + -gg * T(0.5) * Y.hsum * Y.zdif / dxl;
+  T L1x = -(s3 / dxl) * X.s[v];
+  T L1y = -(s3 / dxl) * Y.s[v];
   if (v == 1) L1x = L1x + -(T(2) * s3 * gg / dxl) * h1x * e1x;
   if (v == 2) L1y = L1y + -(T(2) * s3 * gg / dxl) * h1y * e1y;
   if (STAGE == 3) L1x = L1y = T(0);  // FV1 (its only stage): L0 only (Sect. 2.1.2)
@@ -2075,21 +2089,23 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
       in[d] = nb_type(code[d]) != NB_EDGE;
       if (in[d]) nbr_view_code(g, p, l, i, j, d, code[d], nb[d]);
     }
-    T F[4][3], hs[4], us[4], vs[4], zr[4];
+    // the interfaces in the order E, W, N, S; each direction's terms are
+    // formed as soon as its two faces are known
+    DirTerms<T> dx_, dy_;
 #pragma unroll
-    for (int d = 0; d < 4; d++) {
-      FaceOut<T> fo = face_flux_nb(g, p, l, i, j, w, zc, d, tf, in[d], nb[d]);
-      if (REFLUX) reflux_face(g, p, l, i, j, d, tf, fo.F0, fo.F1, fo.F2);
-      bsum += fo.bout;
-      F[d][0] = fo.F0; F[d][1] = fo.F1; F[d][2] = fo.F2;
-      hs[d] = fo.hs; us[d] = fo.us; vs[d] = fo.vs; zr[d] = fo.zr;
+    for (int dir = 0; dir < 2; dir++) {
+      FaceOut<T> fa = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir, tf, in[2 * dir], nb[2 * dir]);
+      if (REFLUX) reflux_face(g, p, l, i, j, 2 * dir, tf, fa.F0, fa.F1, fa.F2);
+      bsum += fa.bout;
+      FaceOut<T> fb = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir + 1, tf, in[2 * dir + 1], nb[2 * dir + 1]);
+      if (REFLUX) reflux_face(g, p, l, i, j, 2 * dir + 1, tf, fb.F0, fb.F1, fb.F2);
+      bsum += fb.bout;
+      dir_terms(dir == 0, fa, fb, gg, dir == 0 ? dx_ : dy_);
     }
     T o[3][3];
 #pragma unroll
-    for (int v = 0; v < 3; v++) {
-      T Fv[4] = {F[0][v], F[1][v], F[2][v], F[3][v]};
-      finish_var<T, STAGE>(g, p, v, k, l, w, zc, Fv, hs, us, vs, zr, dt, Wst, Wcomb, o[v][0], o[v][1], o[v][2]);
-    }
+    for (int v = 0; v < 3; v++)
+      finish_var_dir<T, STAGE>(g, v, k, l, w, zc, dx_, dy_, dt, Wst, Wcomb, o[v][0], o[v][1], o[v][2]);
     const T h0n = o[0][0];
 #pragma unroll
     for (int v = 0; v < 3; v++) {
