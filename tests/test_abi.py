@@ -48,3 +48,33 @@ def test_status_strings_and_defaults_without_device():
     bad.L, bad.M = 0, 0
     assert L.mwdg_create(C.byref(bad), C.byref(h)) == -2
     assert L.mwdg_create(None, C.byref(h)) == -1
+
+
+def test_adjoint_parameters_are_validated_without_device():
+    """mwdg_adj_create rejects bad sizes and parameters before any device
+    work (no GPU needed for these answers)."""
+    import ctypes as C
+    L = adjoint.lib()
+    h = C.c_void_p()
+    assert L.mwdg_adj_create(None, C.byref(h)) == -1
+
+    def create(**kw):
+        p = adjoint.AdjParams()
+        assert L.mwdg_adj_params_default(C.byref(p)) == 0
+        p.nx, p.ny, p.dx = 8, 8, 1.0
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return L.mwdg_adj_create(C.byref(p), C.byref(h))
+
+    p = adjoint.AdjParams()
+    L.mwdg_adj_params_default(C.byref(p))
+    assert (p.max_steps, p.precision, p.tape_views, p.inflow_edge, p.limiter) == (200, 0, 0, -1, 1)
+    assert abs(p.cfl - 0.33) < 1e-15 and abs(p.g - 9.80665) < 1e-15
+    assert create(nx=0) == -2
+    assert create(dx=0.0) == -2
+    assert create(max_steps=0) == -2
+    assert create(precision=7) == -1
+    assert create(cfl=-1.0) == -1
+    assert create(inflow_edge=4) == -1
+    assert create(inflow_edge=0, inflow_c0=3, inflow_c1=2) == -1
+    assert create(inflow_edge=0, inflow_c0=0, inflow_c1=8) == -1     # beyond the 8 cells of the edge
