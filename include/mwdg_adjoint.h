@@ -96,7 +96,8 @@ MWDG_API mwdg_status mwdg_adj_project(mwdg_adj *a, const double *vert, void *out
  * fixed_dt = 0: each dt from the CFL condition, written to dts[0..steps);
  * fixed_dt = 1: the steps dts[0..steps) are read.  U_out receives U_K (it
  * may alias U0).  MWDG_ERR_CAPACITY when steps > max_steps; MWDG_ERR_ARG on
- * NULL pointers, steps < 0, or nknots < 1 with an inflow edge. */
+ * NULL pointers (dts may be NULL when steps = 0), steps < 0, or nknots < 1
+ * with an inflow edge. */
 MWDG_API mwdg_status mwdg_adj_forward(mwdg_adj *a, const void *U0, const void *z, const void *n,
                                       int32_t nknots, const double *knot_t, const double *knot_Q, double t0,
                                       int32_t steps, int32_t fixed_dt, double *dts, void *U_out,

@@ -1304,7 +1304,7 @@ void launch_step(mwdg_adj *a, const Par<T> &P, const T *z, const T *nman, int s,
 mwdg_status check_run(mwdg_adj *a, const void *U0, const void *z, const void *n, int32_t nknots, const double *kt,
                       const double *kQ, int32_t steps, const double *dts) {
   if (!a) return MWDG_ERR_ARG;
-  if (!U0 || !z || !n || !dts || steps < 0) return fail(a, MWDG_ERR_ARG, "NULL pointer or steps < 0");
+  if (!U0 || !z || !n || (!dts && steps > 0) || steps < 0) return fail(a, MWDG_ERR_ARG, "NULL pointer or steps < 0");
   if (steps > a->p.max_steps) return fail(a, MWDG_ERR_CAPACITY, "steps > max_steps");
   if (a->p.inflow_edge >= 0 && (nknots < 1 || !kt || !kQ))
     return fail(a, MWDG_ERR_ARG, "an inflow edge needs nknots >= 1 knots");

@@ -359,3 +359,69 @@ def test_full_size_gradients():
     for a, b, what in zip(g32[:3], (gU0, gz, gn), ("U0", "z", "n")):
         x, y = a.double().cpu().numpy().ravel(), b.cpu().numpy().ravel()
         assert np.corrcoef(x, y)[0, 1] >= 0.999, what
+
+
+def _strip(along_x):
+    """a one-cell-wide dam break on a sloping, rough bed, along x or along y"""
+    p = S.dam_break_strip(nx=64, ny=1, dx=0.5, h_left=1.0, h_right=0.1)
+    z = np.tile(np.linspace(0.4, 0.0, 65), (2, 1))
+    p = replace(p, z_vert=z, n_manning=0.03)
+    if along_x:
+        return p
+    return replace(p, M=1, N=64, z_vert=np.ascontiguousarray(p.z_vert.T),
+                   h_vert=np.ascontiguousarray(p.h_vert.T), qx_vert=np.ascontiguousarray(p.qy_vert.T),
+                   qy_vert=np.ascontiguousarray(p.qx_vert.T))
+
+
+@pytest.mark.parametrize("along_x", [True, False], ids=["strip_x", "strip_y"])
+def test_one_cell_wide_strips(along_x):
+    """64 x 1 and 1 x 64: one-sided limiting, a single row of update tiles;
+    the forward sweep is the C oracle's bit for bit and the gradients are
+    the oracle's (1e-9)."""
+    import torch
+    p = _strip(along_x)
+    K = 30
+    s = oracle_sim(p)
+    U0o = state(s, p)
+    zo = s.z_level(0)[0].reshape(3, p.ny, p.nx)
+    dts = [s.step() for _ in range(K)]
+    want = state(s, p)
+    seed = np.random.default_rng(2).standard_normal((9, p.ny, p.nx))
+    G = A.gradients(U0o, zo, p.n_cell(), np.zeros(1), dts, 0.0, grid_of(p), seed)
+    adj = context(p, K)
+    U0, z, n, kt, kQ = device_inputs(adj, p)
+    UK, d = adj.forward(U0, z, n, kt, kQ, 0.0, K)
+    assert np.array_equal(d.cpu().numpy(), np.array(dts))
+    assert np.array_equal(UK.cpu().numpy(), want)
+    gU0, gz, gn, _ = adj.backward(U0, z, n, kt, kQ, 0.0, d, torch.tensor(seed, device=adj.device))
+    _close(gU0.cpu().numpy(), G["gU0"], "U0")
+    _close(gz.cpu().numpy(), G["gz"], "z")
+    _close(gn.cpu().numpy(), G["gn"], "n")
+
+
+def test_degenerate_runs():
+    """Zero steps: U_K = U0 and the cotangent passes through unchanged, with
+    no bed, roughness or knot sensitivity.  An all-dry domain: nothing moves,
+    the depth average's cotangent passes through (a dry cell keeps its
+    average), everything else is zero."""
+    import torch
+    p, _ = S.adjoint_reach(n=32)
+    adj = context(p, 10)
+    U0, z, n, kt, kQ = device_inputs(adj, p)
+    seed = torch.randn((9, p.ny, p.nx), generator=torch.Generator().manual_seed(4)).to(U0)
+    UK, d = adj.forward(U0, z, n, kt, kQ, 0.0, 0)
+    assert torch.equal(UK, U0) and d.numel() == 0
+    gU0, gz, gn, gQ = adj.backward(U0, z, n, kt, kQ, 0.0, d, seed)
+    assert torch.equal(gU0, seed)
+    assert float(gz.abs().max()) == 0.0 and float(gn.abs().max()) == 0.0 and float(gQ.abs().max()) == 0.0
+    dry = replace(p, h_vert=np.zeros_like(p.h_vert), qx_vert=np.zeros_like(p.h_vert),
+                  qy_vert=np.zeros_like(p.h_vert), inflow_edge=-1)
+    adj = context(dry, 10)
+    U0, z, n, kt, kQ = device_inputs(adj, dry)
+    UK, d = adj.forward(U0, z, n, kt, kQ, 0.0, 10)
+    assert float(UK.abs().max()) == 0.0
+    assert np.all(d.cpu().numpy() == dry.dt_max)
+    gU0, gz, gn, _ = adj.backward(U0, z, n, kt, kQ, 0.0, d, seed)
+    assert torch.equal(gU0[0], seed[0])
+    assert float(gU0[1:].abs().max()) == 0.0
+    assert float(gz.abs().max()) == 0.0 and float(gn.abs().max()) == 0.0
