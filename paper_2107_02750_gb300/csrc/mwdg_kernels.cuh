@@ -535,11 +535,22 @@ __device__ __forceinline__ void load_nb_codes(const long long *nbr, long long q,
 // consecutive nodes, read as one 8-byte word); with kind_out the kinds are
 // also copied there
 static_assert(CPT == 8, "one 8-byte word of kinds per thread");
+// ctl == nullptr: blk holds each block's exclusive offset (k_compact_scan
+// wrote it and the total).  ctl != nullptr: blk holds each block's raw leaf
+// count (the decode's); every block sums the counts before its own, the
+// block with the highest index writes the total to *nleaf before it takes
+// its completion ticket, and with begin the last block to finish starts the
+// step on the new leaves.
 static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *blk, long long *leaves,
-                                         uint8_t *kind_out, Ctl *begin_ctl, const int *nleaf) {
+                                         uint8_t *kind_out, Ctl *ctl, int *nleaf, int begin) {
   const long long P = g.P;
   const long long base = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
   const bool full = base + CPT <= P;
+  // the counts of the blocks before this one (their loads in flight with
+  // the kinds')
+  int before = 0;
+  if (ctl)
+    for (int r = threadIdx.x; r < (int)blockIdx.x; r += TPB) before += blk[r];
   uint8_t kk[CPT];
   uint2 w8 = make_uint2(0u, 0u);
   if (full) {
@@ -577,7 +588,20 @@ static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *
     if (threadIdx.x < TPB / 32) ws[threadIdx.x] = w;
   }
   __syncthreads();
-  int pos = blk[blockIdx.x] + x - c + ((threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0);
+  int off;
+  if (ctl) {
+    __shared__ int wb[TPB / 32];
+    for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+    if ((threadIdx.x & 31) == 0) wb[threadIdx.x >> 5] = before;
+    __syncthreads();
+    off = 0;
+#pragma unroll
+    for (int w = 0; w < TPB / 32; w++) off += wb[w];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == TPB - 1) *nleaf = off + ws[TPB / 32 - 1];
+  } else {
+    off = blk[blockIdx.x];
+  }
+  int pos = off + x - c + ((threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0);
   for (int q = 0; q < CPT; q++) {
     if (kk[q] == K_LEAF) {
       int l, i, j;
@@ -585,8 +609,8 @@ static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *
       leaves[pos++] = pack_leaf(l, i, j);
     }
   }
-  // with begin_ctl, the last block also starts the step on the new leaves
-  if (begin_ctl && last_block(&begin_ctl->ticket) && threadIdx.x == 0) begin_step(g, begin_ctl, nleaf);
+  // the last block to finish sees the total and starts the step
+  if (ctl && last_block(&ctl->ticket) && begin && threadIdx.x == 0) begin_step(g, ctl, nleaf);
 }
 
 // the four face-neighbour codes of every active leaf (one thread per leaf)
@@ -1063,14 +1087,10 @@ __device__ __forceinline__ void sig_tile(const Geo &g, const Ptrs<T> &p, const T
   }
 }
 
-// encode + significance flags: levels ltop..ltop-nlev+1 in tiles, then
-// (tail >= 0) levels tail..0 in the last block
-template <typename T, bool FV1>
-__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_sig(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
-  __shared__ SigStage<T> sh;
-  if (!ADAPT_LIVE(p)) return;
-  if (nlev > 0) sig_tile<false, FV1>(g, p, tile_of_block(g, ltop, nlev), sh);
-  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+// encode + significance of the coarsest levels tail..0 by one block (the
+// levels below are final)
+template <bool FV1, typename T>
+__device__ __forceinline__ void sig_tail(const Geo &g, const Ptrs<T> &p, int tail, SigStage<T> &sh) {
   if (tail_is_tile(g, tail)) {
     sig_tile<true, FV1>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
     return;
@@ -1080,6 +1100,17 @@ __global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_sig(Geo g, Ptrs<
     for (int r = threadIdx.x; r < n; r += blockDim.x) encode_flag_node<true, FV1>(g, p, l, r % g.nxl[l], r / g.nxl[l]);
     __syncthreads();
   }
+}
+
+// encode + significance flags: levels ltop..ltop-nlev+1 in tiles, then
+// (tail >= 0) levels tail..0 in the last block
+template <typename T, bool FV1>
+__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_sig(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+  __shared__ SigStage<T> sh;
+  if (!ADAPT_LIVE(p)) return;
+  if (nlev > 0) sig_tile<false, FV1>(g, p, tile_of_block(g, ltop, nlev), sh);
+  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+  sig_tail<FV1>(g, p, tail, sh);
 }
 
 struct RegStage {
@@ -1156,15 +1187,9 @@ __device__ __forceinline__ void reg_tile(const Geo &g, const Ptrs<T> &p, const T
   }
 }
 
-// regularised flags, same chunking; the CFL minimum is reset here for the
-// decode pass that follows
+// regularised flags of the coarsest levels tail..0 by one block
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_mra_regularise(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
-  __shared__ RegStage sh;
-  if (ltop == g.L - 1 && blockIdx.x == 0 && threadIdx.x == 0) p.ctl->dtmin = 0x7ff0000000000000ULL;
-  if (!ADAPT_LIVE(p)) return;
-  if (nlev > 0) reg_tile<false>(g, p, tile_of_block(g, ltop, nlev), sh);
-  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+__device__ __forceinline__ void reg_tail(const Geo &g, const Ptrs<T> &p, int tail, RegStage &sh) {
   if (tail_is_tile(g, tail)) {
     reg_tile<true>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
     return;
@@ -1179,13 +1204,41 @@ __global__ void __launch_bounds__(TPB) k_mra_regularise(Geo g, Ptrs<T> p, int lt
   }
 }
 
+// regularised flags, same chunking; the CFL minimum is reset here for the
+// decode pass that follows
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_mra_regularise(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+  __shared__ RegStage sh;
+  if (ltop == g.L - 1 && blockIdx.x == 0 && threadIdx.x == 0) p.ctl->dtmin = 0x7ff0000000000000ULL;
+  if (!ADAPT_LIVE(p)) return;
+  if (nlev > 0) reg_tile<false>(g, p, tile_of_block(g, ltop, nlev), sh);
+  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+  reg_tail(g, p, tail, sh);
+}
+
+// The regularisation's coarsest levels tail..0, run by the first block of
+// the decode when the regularise pass leaves them out.  Only nodes of levels
+// up to tail + 1 read these flags (a node's kind depends on its own flag and
+// its parent's), and the host defers only when all of them belong to that
+// first block, which runs this before them; so the other blocks need nothing
+// from here and the coarsest levels leave the critical path.  (The encode
+// and significance tail stays in the last block of its own pass: run here,
+// beside three decode blocks on one SM, its chain of five dependent levels
+// took longer than the decode itself.)
+template <typename T>
+__device__ __noinline__ void coarse_flags(const Geo &g, const Ptrs<T> &p, int tail) {
+  __shared__ RegStage sh;
+  reg_tail(g, p, tail, sh);
+  __syncthreads();
+}
+
 // New kinds from the regularised flags (refined; active leaf: parent
 // refined or root, not refined itself; below a leaf), written to
 // kind_new while kind keeps the old ones.  Eq. 10 for the new active set:
 // every new leaf that was below an old leaf takes the prolongation of that
 // leaf's plane (one level at a time, flow in depth form).  Each block counts
-// its new leaves, every new leaf contributes its CFL candidate for the coming
-// step, and the last block turns the counts into scatter offsets.
+// its new leaves (the scatter turns the counts into offsets), and every new
+// leaf contributes its CFL candidate for the coming step.
 // prolongation (Eq. 10) into new leaf k (level l, i, j) from the old leaf
 // above it (flow in depth form, one level at a time)
 template <typename T>
@@ -1234,9 +1287,12 @@ __device__ __forceinline__ uint8_t byte_of(uint2 w, int q) {
 // Each thread takes CPT consecutive nodes (the scatter's layout); when they
 // lie in one row of one level (the common case) their flags and kinds are
 // read as 8-byte words and their parents follow from the first node.
+// ftail >= 0: the first block first runs the coarsest levels ftail..0 of
+// the regularisation (coarse_flags).
 template <typename T>
-__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_decode(Geo g, Ptrs<T> p) {
+__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_decode(Geo g, Ptrs<T> p, int ftail) {
   const long long P = g.P;
+  if (ftail >= 0 && blockIdx.x == 0 && ADAPT_LIVE(p)) coarse_flags<T>(g, p, ftail);
   const long long k0 = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
   const ForceTime t{p.ctl, false};
   int cnt = 0;
@@ -1331,7 +1387,6 @@ __global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_decode(Geo g, Pt
     p.blk[blockIdx.x] = sum;
     if (b < tinf<T>()) atomic_min_pos(&p.ctl->dtmin, (double)b);  // one FP64 conversion per block
   }
-  if (last_block(&p.ctl->ticket)) block_scan_counts(gridDim.x, p.blk, p.nleaf);
 }
 
 static __global__ void k_begin_step(Geo g, Ctl *c, const int *nleaf) { begin_step(g, c, nleaf); }
@@ -1654,6 +1709,26 @@ __global__ void __launch_bounds__(TPB) k_view_tiles(Geo g, Ptrs<T> p, int ltop, 
   for (int l = tail; l >= 0; l--) {
     const int n = g.nxl[l] * g.nyl[l];
     for (int r = threadIdx.x; r < n; r += blockDim.x) encode_view_node<FV1>(g, p, l, r % g.nxl[l], r / g.nxl[l]);
+    __syncthreads();
+  }
+}
+
+// Flux-view encode of the coarsest levels tail..0, run by the first block of
+// a stage update when the view pass leaves them out.  A leaf reads encoded
+// views of its own level only; the leaves of levels up to tail come first
+// in the leaf list (node order, coarsest level first) and are at most as
+// many as the nodes of level tail, which the host defers only when they fit
+// the first block's first pass over the list.  So they are updated by that
+// block, after this, and no other block reads what it writes.
+template <typename T>
+__device__ __noinline__ void coarse_views(const Geo &g, const Ptrs<T> &p, int tail) {
+  const bool fv1 = g.scheme == MWDG_FV1;
+  for (int l = tail; l >= 0; l--) {
+    const int n = g.nxl[l] * g.nyl[l];
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      if (fv1) encode_view_node<true>(g, p, l, r % g.nxl[l], r / g.nxl[l]);
+      else encode_view_node<false>(g, p, l, r % g.nxl[l], r / g.nxl[l]);
+    }
     __syncthreads();
   }
 }
@@ -2047,11 +2122,15 @@ __device__ __forceinline__ void next_step_reduce(const Geo &g, const Ptrs<T> &p,
 // thread, four blocks; FP64 keeps its registers)
 template <typename T> struct UpdOcc { static constexpr int blocks = std::is_same<T, float>::value ? 4 : 1; };
 
-// REFLUX: compiled with the reflux interface rule (static grids only)
+// REFLUX: compiled with the reflux interface rule (static grids only).
+// vtail >= 0: the first block first encodes the coarsest levels vtail..0 of
+// the flux views (coarse_views).
 template <typename T, int STAGE, bool REFLUX>
-__global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out) {
+__global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out,
+                                                                      int vtail) {
   const long long P = g.P;
   if (!ctl_stepping(p.ctl)) return;  // a zero step changes nothing (end_step ignores it too)
+  if (vtail >= 0 && blockIdx.x == 0) coarse_views<T>(g, p, vtail);
   const T dt = ctl_dt<T>(p.ctl), gg = geo_g<T>(g), hd = geo_hd<T>(g), s3 = s3v<T>();
   const ForceTime tf{p.ctl, STAGE == 2};
   T bsum = T(0);  // per-thread sum of a few boundary fluxes; FP64 from the block sum on
@@ -2552,7 +2631,7 @@ int Launch<T>::compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st) {
   const int nb = (int)((g.P + CTILE - 1) / CTILE);
   k_compact_count<<<nb, TPB, 0, st>>>(g.P, p.kind, p.blk);
   k_compact_scan<<<1, 1024, 0, st>>>(nb, p.blk, p.nleaf);
-  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves, nullptr, nullptr, nullptr);
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind, p.blk, p.leaves, nullptr, nullptr, nullptr, 0);
   k_leaf_codes<<<(int)std::min<long long>(nblk(g.P), 152 * 8), TPB, 0, st>>>(g, p.kind, p.leaves, p.nleaf, p.nbr);
   return 4;
 }
@@ -2596,6 +2675,10 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
     k_leaf_maxabs<T><<<grid, TPB, 0, st>>>(g, p);
     n++;
   }
+  // the coarsest levels of the regularisation move to the decode's first
+  // block when every node that reads them (levels up to lc + 1) is its own
+  const int lc = coarse_top(g);
+  const bool defer = !encode_only && lc >= 0 && lc < g.L - 1 && g.off[lc + 2] <= CTILE;
   // bottom-up encode + significance
   n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
     MARK(KC_ENCODE);
@@ -2606,16 +2689,16 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
   // prediction + closure
   n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
     MARK(KC_FLAGS);
+    if (defer) tail = -1;
     k_mra_regularise<T><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
   });
   // new kinds, decode, counts and offsets; then the scatter, which also
   // makes the new kinds current
   MARK(KC_DECODE);
   const int nb = (int)((g.P + CTILE - 1) / CTILE);
-  k_mra_decode<T><<<nb, TPB, 0, st>>>(g, p);
+  k_mra_decode<T><<<nb, TPB, 0, st>>>(g, p, defer ? lc : -1);
   MARK(KC_COMPACT);
-  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind_new, p.blk, p.leaves, p.kind, begin ? p.ctl : nullptr,
-                                        p.nleaf);
+  k_compact_scatter<<<nb, TPB, 0, st>>>(g, p.kind_new, p.blk, p.leaves, p.kind, p.ctl, p.nleaf, begin);
   // (the neighbour codes of the new leaves: the stage-1 limiter of the step,
   // or a pass of their own when the adaptation is not followed by a step)
   if (!begin) {
@@ -2659,6 +2742,10 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
     return n + 2;
   }
   const int stages = (g.scheme == MWDG_FV1) ? 1 : 2;  // FV1: forward Euler (Eq. 7)
+  // the coarsest levels of the flux views move to the update's first block
+  // when the coarse leaves fit its first pass (at most lvl(lc) of them)
+  const int lc = coarse_top(g);
+  const int vtail = (view && lc >= 0 && lc < g.L - 1 && lvl(g, lc) <= TPB) ? lc : -1;
   for (int stage = 1; stage <= stages; stage++) {
     MARK(KC_LIMIT);
     const bool codes = (stage == 1 && begun);  // the step follows an adaptation
@@ -2675,22 +2762,23 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
     if (view)
       n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
         MARK(KC_VIEW);
+        if (vtail >= 0) tail = -1;
         if (g.scheme == MWDG_FV1) k_view_tiles<T, true><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
         else k_view_tiles<T, false><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
       });
     const bool reflux = (g.mode == MWDG_STATIC && g.iface == MWDG_IFACE_REFLUX);
     if (stages == 1) {
       MARK(KC_UPDATE2);
-      if (reflux) k_leaf_update<T, 3, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U);
-      else k_leaf_update<T, 3, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U);
+      if (reflux) k_leaf_update<T, 3, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, vtail);
+      else k_leaf_update<T, 3, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, vtail);
     } else if (stage == 1) {
       MARK(KC_UPDATE1);
-      if (reflux) k_leaf_update<T, 1, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui);
-      else k_leaf_update<T, 1, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui);
+      if (reflux) k_leaf_update<T, 1, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, vtail);
+      else k_leaf_update<T, 1, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, vtail);
     } else {
       MARK(KC_UPDATE2);
-      if (reflux) k_leaf_update<T, 2, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U);
-      else k_leaf_update<T, 2, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U);
+      if (reflux) k_leaf_update<T, 2, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, vtail);
+      else k_leaf_update<T, 2, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, vtail);
     }
     n++;
   }
