@@ -412,7 +412,7 @@ def kernel_bytes_per_leaf(name, ts, scheme="dg2"):
 # DRAM bytes (read + write) per launch measured by ncu for a kernel of the
 # headline workload (FP32 MWDG2), when the kernel has not changed since (see
 # profiles/); None otherwise
-TRAFFIC = {"dg2_update_stage2": 58_103_040 + 3_647_488}  # ncu: dram read + write, one launch at this workload
+TRAFFIC = {"dg2_update_stage2": 58_196_224 + 2_093_312}  # ncu: dram read + write, one launch at this workload
 
 
 def run_ensemble(args):

@@ -1696,9 +1696,12 @@ __device__ __forceinline__ void view_tile(const Geo &g, const Ptrs<T> &p, const 
   }
 }
 
-// flux-view encode of the refined nodes, chunked as the MRA passes
+// flux-view encode of the refined nodes, chunked as the MRA passes (FP32:
+// seven resident blocks per SM, 32 registers a thread, so that the 1024
+// tiles of a 512 x 512 level run in one wave; FP64 keeps its registers)
+template <typename T> struct ViewOcc { static constexpr int blocks = std::is_same<T, float>::value ? 7 : 1; };
 template <typename T, bool FV1>
-__global__ void __launch_bounds__(TPB) k_view_tiles(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+__global__ void __launch_bounds__(TPB, ViewOcc<T>::blocks) k_view_tiles(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
   __shared__ ViewStage<T> sh;
   if (nlev > 0) view_tile<false, FV1>(g, p, tile_of_block(g, ltop, nlev), sh);
   if (tail < 0 || !last_block(&p.ctl->ticket)) return;
