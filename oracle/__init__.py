@@ -26,7 +26,11 @@ tests):
   friction                        pinned: exact decay of a uniform flow
   limiter                         pinned: hand-evaluated minmod cases (through
                                   the bit-exact restatement in dg2_adjoint.py)
-  non-homogeneous interface rule  parity unpinned beyond the invariants above
+  non-homogeneous interface rule  pinned on planar data: one stage on a
+                                  non-uniform grid equals, leaf by leaf, the
+                                  stage on the uniform grid of each leaf's
+                                  level (static and adaptive); elsewhere by
+                                  the invariants above
   discrete adjoint of the uniform DG2 step (dg2_adjoint.py, PyTorch CPU
   autograd over a restatement of the step):
                                   pinned: bit-for-bit forward against the C
@@ -104,6 +108,7 @@ def lib():
         L.orc_adapt.argtypes = [C.c_void_p]
         L.orc_step.restype = C.c_double
         L.orc_step.argtypes = [C.c_void_p, C.c_double]
+        L.orc_stage.argtypes = [C.c_void_p, C.c_double]
         L.orc_step_dt.restype = C.c_double
         L.orc_step_dt.argtypes = [C.c_void_p, C.c_double]
         L.orc_run_to.restype = C.c_int64
@@ -258,6 +263,11 @@ class Sim:
     def step_dt(self, dt) -> float:
         """one step with the given dt (the CFL condition is not applied)"""
         return lib().orc_step_dt(self._h, dt)
+
+    def stage(self, dt):
+        """one forward-Euler stage of Eq. 4a on the current leaves (no
+        adaptation, rain, friction or clock advance)"""
+        lib().orc_stage(self._h, dt)
 
     def run_to(self, t_end, max_steps=1 << 40) -> int:
         return lib().orc_run_to(self._h, t_end, max_steps)

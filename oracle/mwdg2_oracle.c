@@ -24,9 +24,12 @@
  * The paper delegates the DG2 operator details (HLL, wet/dry revisions,
  * friction, limiter, filter entries) to cited works; the readings used here
  * are listed beside each function.  Friction is pinned by the exact decay
- * of a uniform flow and the limiter by hand-evaluated minmod cases; the
- * non-homogeneous interface rule has no closed form to pin it and is
- * "parity unpinned" beyond invariants.
+ * of a uniform flow and the limiter by hand-evaluated minmod cases.  The
+ * non-homogeneous interface rule is pinned on planar data, where each
+ * leaf's stage equals the uniform grid's of the leaf's level (views of a
+ * plane are exact); with a plane's details zero, that fixes which views and
+ * faces the rule uses but not its arithmetic on non-planar data beyond the
+ * invariants (lake at rest, mass budget).
  */
 #include <math.h>
 #include <stdint.h>
@@ -1518,6 +1521,12 @@ static double step_with(orc_sim *s, double t_end, double dt_given) {
 }
 
 double orc_step(orc_sim *s, double t_end) { return step_with(s, t_end, 0.0); }
+
+/* One forward-Euler stage of Eq. 4a on the current active leaves, with no
+ * adaptation, rain or friction and the clock left where it is: the stage
+ * operator of Sect. 2.1.1 applied once, so that tests can compare it
+ * between grids (the interface rule of Sect. 2.3). */
+void orc_stage(orc_sim *s, double dt) { (void)rk_stage(s, s->U, s->Wn, NULL, s->U, dt, s->t); }
 
 double orc_step_dt(orc_sim *s, double dt) { return step_with(s, INFINITY, dt); }
 

@@ -187,3 +187,103 @@ def test_metrics():
     r = np.array([[1, 1], [0, 1]], float)
     H, F, C = O.extent_scores(h, r)
     assert (H, F, C) == (2 / 3, 1 / 3, 2 / 4)
+
+
+def _planar_case(Lf=4, M=4, R=1.0):
+    """A planar bed with one compactly supported bump, a planar free surface
+    and planar discharges; returns the vertex fields of a grid of cell size
+    `dx` and the bump's zone (the box, one finest cell wider than the bump's
+    support, outside which bed, depth and discharges are exactly planar)."""
+    xb, yb, rb = 21.5, 22.5, 1.5
+
+    def fields(dx, n):
+        x = np.arange(n + 1) * dx
+        X, Y = np.meshgrid(x, x)
+        r2 = ((X - xb) ** 2 + (Y - yb) ** 2) / rb ** 2
+        z = 0.02 * X + 0.01 * Y + 0.8 * np.maximum(0.0, 1.0 - r2) ** 2
+        eta = 3.0 + 0.01 * X - 0.005 * Y
+        qx = 0.4 + 0.01 * Y - 0.005 * X
+        qy = -0.3 + 0.008 * X + 0.002 * Y
+        return z, eta - z, qx, qy
+
+    zone = (xb - rb - R, xb + rb + R, yb - rb - R, yb + rb + R)
+    return fields, zone
+
+
+@pytest.mark.parametrize("mode", [S.STATIC, S.ADAPTIVE])
+def test_interface_rule_on_planar_data_equals_the_uniform_grid_of_each_level(mode):
+    """Pin of the interface rule on non-homogeneous faces (Sect. 2.3): each
+    leaf evaluates its faces from its neighbours' views at its own level
+    (the encoding of finer neighbours, the prolongation of a coarser one;
+    on static grids the coarse side averages the two finer interface
+    values).  Encoding and prolongation reproduce a plane exactly, and
+    minmod keeps a plane's slopes, so on globally planar data one stage of
+    Eq. 4a on the non-uniform grid must equal, leaf by leaf, the same stage
+    on the uniform grid of the leaf's own level.  Only leaves whose stencil
+    (the leaf and its four face neighbours at its level) stays clear of the
+    bump that makes the grid non-uniform are compared; the test requires
+    many of them to border a leaf of another level."""
+    Lf, M, R, dt = 4, 4, 1.0, 0.05
+    fields, (x0, x1, y0, y1) = _planar_case(Lf, M, R)
+    n = M << Lf
+    z, h, qx, qy = fields(R, n)
+    s = O.Sim(M=M, N=M, L=Lf, R=R, mode=mode, eps=1e-3)
+    s.load_dem(z)
+    s.load_roughness(np.zeros((n, n)))
+    s.load_initial(h, qx, qy)
+    s.init_grid()
+    if mode == S.ADAPTIVE:
+        s.adapt()
+    lev, ii, jj, before = s.leaves()
+    s.stage(dt)
+    lev2, ii2, jj2, after = s.leaves()
+    assert np.array_equal(lev, lev2) and np.array_equal(ii, ii2) and np.array_equal(jj, jj2)
+    assert len(np.unique(lev)) >= 3
+    Lop = (after - before) / dt
+
+    # the uniform grid of each level present
+    ref = {}
+    for l in np.unique(lev):
+        dxl = R * (1 << (Lf - l))
+        nl = M << l
+        zl, hl, qxl, qyl = fields(dxl, nl)
+        u = O.Sim(M=M, N=M, L=int(l), R=dxl, mode=S.UNIFORM)
+        u.load_dem(zl)
+        u.load_roughness(np.zeros((nl, nl)))
+        u.load_initial(hl, qxl, qyl)
+        u.init_grid()
+        _, ui, uj, ub = u.leaves()
+        u.stage(dt)
+        _, _, _, ua = u.leaves()
+        ref[int(l)] = {(int(a), int(b)): (ub[k], (ua[k] - ub[k]) / dt) for k, (a, b) in enumerate(zip(ui, uj))}
+
+    # level of the leaf covering each finest cell, to find mixed-level faces
+    cover = np.full((n, n), -1)
+    for l, a, b in zip(lev, ii, jj):
+        f = 1 << (Lf - l)
+        cover[b * f:(b + 1) * f, a * f:(a + 1) * f] = l
+    compared = mixed = coarse_side = 0
+    for k, (l, a, b) in enumerate(zip(lev, ii, jj)):
+        dxl = R * (1 << (Lf - l))
+        bx0, bx1, by0, by1 = (a - 1) * dxl, (a + 2) * dxl, (b - 1) * dxl, (b + 2) * dxl
+        if bx0 < x1 and bx1 > x0 and by0 < y1 and by1 > y0:
+            continue  # the stencil reaches the bump
+        ub, uL = ref[int(l)][(int(a), int(b))]
+        np.testing.assert_allclose(before[k], ub, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(Lop[k], uL, rtol=0, atol=1e-9 * max(1.0, np.abs(uL).max()))
+        compared += 1
+        f = 1 << (Lf - l)
+        ring = []
+        if a > 0:
+            ring.append(cover[b * f:(b + 1) * f, a * f - 1])
+        if (a + 1) * f < n:
+            ring.append(cover[b * f:(b + 1) * f, (a + 1) * f])
+        if b > 0:
+            ring.append(cover[b * f - 1, a * f:(a + 1) * f])
+        if (b + 1) * f < n:
+            ring.append(cover[(b + 1) * f, a * f:(a + 1) * f])
+        if any(np.any(r != l) for r in ring):
+            mixed += 1
+        if any(np.any(r > l) for r in ring):
+            coarse_side += 1
+    assert compared >= 20 and mixed >= 8 and coarse_side >= 4, (compared, mixed, coarse_side)
