@@ -2126,14 +2126,15 @@ __device__ __forceinline__ void next_step_reduce(const Geo &g, const Ptrs<T> &p,
 template <typename T> struct UpdOcc { static constexpr int blocks = std::is_same<T, float>::value ? 4 : 1; };
 
 // REFLUX: compiled with the reflux interface rule (static grids only).
-// vtail >= 0: the first block first encodes the coarsest levels vtail..0 of
-// the flux views (coarse_views).
-template <typename T, int STAGE, bool REFLUX>
+// VIEWS (adaptive grids): with vtail >= 0 the first block first encodes the
+// coarsest levels vtail..0 of the flux views (coarse_views); the other
+// instantiations do not contain the call.
+template <typename T, int STAGE, bool REFLUX, bool VIEWS>
 __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out,
                                                                       int vtail) {
   const long long P = g.P;
   if (!ctl_stepping(p.ctl)) return;  // a zero step changes nothing (end_step ignores it too)
-  if (vtail >= 0 && blockIdx.x == 0) coarse_views<T>(g, p, vtail);
+  if (VIEWS && vtail >= 0 && blockIdx.x == 0) coarse_views<T>(g, p, vtail);
   const T dt = ctl_dt<T>(p.ctl), gg = geo_g<T>(g), hd = geo_hd<T>(g), s3 = s3v<T>();
   const ForceTime tf{p.ctl, STAGE == 2};
   T bsum = T(0);  // per-thread sum of a few boundary fluxes; FP64 from the block sum on
@@ -2772,16 +2773,19 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
     const bool reflux = (g.mode == MWDG_STATIC && g.iface == MWDG_IFACE_REFLUX);
     if (stages == 1) {
       MARK(KC_UPDATE2);
-      if (reflux) k_leaf_update<T, 3, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, vtail);
-      else k_leaf_update<T, 3, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, vtail);
+      if (reflux) k_leaf_update<T, 3, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, -1);
+      else if (view) k_leaf_update<T, 3, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, vtail);
+      else k_leaf_update<T, 3, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, -1);
     } else if (stage == 1) {
       MARK(KC_UPDATE1);
-      if (reflux) k_leaf_update<T, 1, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, vtail);
-      else k_leaf_update<T, 1, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, vtail);
+      if (reflux) k_leaf_update<T, 1, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, -1);
+      else if (view) k_leaf_update<T, 1, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, vtail);
+      else k_leaf_update<T, 1, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, -1);
     } else {
       MARK(KC_UPDATE2);
-      if (reflux) k_leaf_update<T, 2, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, vtail);
-      else k_leaf_update<T, 2, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, vtail);
+      if (reflux) k_leaf_update<T, 2, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, -1);
+      else if (view) k_leaf_update<T, 2, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, vtail);
+      else k_leaf_update<T, 2, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, -1);
     }
     n++;
   }
