@@ -434,3 +434,24 @@ def test_acc_channel_and_lake_f64_f32():
         _, _, _, c = s.read_active()
         assert np.abs(c[:, 3:]).max() == 0.0, prec
         np.testing.assert_array_equal(c[:, 0], c0[:, 0])
+
+
+@pytest.mark.parametrize("coarse_nodes", [64, 1024])
+def test_adaptive_coarse_level_schedules_f64(coarse_nodes):
+    """The coarsest MRA levels (those of at most `coarse_nodes` nodes) run in
+    one block: with 256 (the default) and 64 the flux views' coarse levels
+    are encoded by the first block of each stage update and the
+    regularisation's by the first block of the decode; with 1024 on this
+    pyramid (levels of 1024 nodes, more than one pass of a block) every pass
+    keeps them in its last block, as loops over the levels.  Each schedule
+    gives the oracle's steps."""
+    p = S.valley(n=128, L=7, mode=S.ADAPTIVE, eps=1e-2, peak_Q=200.0, t_peak=100.0)
+    g, o = gpu_sim(p), oracle_sim(p)
+    g.set_launch_shape(coarse_nodes=coarse_nodes)
+    assert g.launch_shape()[1] == coarse_nodes
+    for k in range(60):
+        dg = g.dg2_step()
+        do = o.step()
+        assert abs(dg - do) <= 1e-9 * do, (k, dg, do)
+        if (k + 1) % 20 == 0:
+            assert_same_leaves(g, o, what=f"coarse_nodes {coarse_nodes}, step {k + 1}")
