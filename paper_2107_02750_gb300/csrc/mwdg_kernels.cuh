@@ -1433,8 +1433,10 @@ __device__ __forceinline__ T friction_factor(T h0, T qx0, T qy0, T nm, T dt, T g
 // averages (both are pointwise, so every leaf sees the same values).
 // CODES (the first kernel after an adaptation): the leaf's four neighbour
 // codes are computed here from the kinds and stored for the later kernels
+// FP32: at most 64 registers a thread (four resident blocks per SM)
+template <typename T> struct LimOcc { static constexpr int blocks = std::is_same<T, float>::value ? 4 : 1; };
 template <typename T, bool FRIC, bool FV1, bool CODES>
-__global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
+__global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   const long long P = g.P;
   const T hd = geo_hd<T>(g), s3 = s3v<T>(), gg = geo_g<T>(g);
   const T dt = ctl_dt<T>(p.ctl);
@@ -1509,16 +1511,30 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
       for (int m = 0; m < 9; m++) ws[m] = w[m];
       ze[0] = zp[0]; ze[1] = zp[1]; ze[2] = zp[2];
       if (g.limiter) {
-        // same-level leaf neighbours from the step's neighbour codes
+        // same-level leaf neighbours from the step's neighbour codes: the
+        // averages (and Manning n) of all four read together (a missing
+        // neighbour reads the leaf's own, unused)
         if (!CODES) load_nb_codes(p.nbr, _q, code);
+        bool has[4];
+        T nh[4], nq[4][2], nzb[4], nmn[4];
+#pragma unroll
+        for (int d = 0; d < 4; d++) {
+          has[d] = nb_type(code[d]) == NB_LEAF;
+          const long long kn = has[d] ? nb_node(code[d]) : k;
+          nh[d] = X[kn];
+          nq[d][0] = X[3 * P + kn];
+          nq[d][1] = X[6 * P + kn];
+          nzb[d] = p.Z[kn];
+          nmn[d] = FRIC ? p.NM[kn] : T(0);
+        }
+#pragma unroll
         for (int dir = 0; dir < 2; dir++) {
-          const long long cA = code[2 * dir], cB = code[2 * dir + 1];  // E/W, then N/S
-          const bool hasA = nb_type(cA) == NB_LEAF, hasB = nb_type(cB) == NB_LEAF;
+          const int dA = 2 * dir, dB = 2 * dir + 1;  // E/W, then N/S
+          const bool hasA = has[dA], hasB = has[dB];
           if (!hasA && !hasB) continue;
-          const long long ka = hasA ? nb_node(cA) : k, kb = hasB ? nb_node(cB) : k;
           T hC = h0;
-          T hA = X[ka];
-          T hB = X[kb];
+          T hA = nh[dA];
+          T hB = nh[dB];
           if (rain) {
             hA = hA + rinc;
             hB = hB + rinc;
@@ -1526,24 +1542,25 @@ __global__ void k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
           // neighbours' friction factors (stage 1), for their discharge averages
           T fA = T(1), fB = T(1);
           if (FRIC) {
-            fA = (hA > hd) ? friction_factor(hA, X[3 * P + ka], X[6 * P + ka], p.NM[ka], dt, gg) : T(0);
-            fB = (hB > hd) ? friction_factor(hB, X[3 * P + kb], X[6 * P + kb], p.NM[kb], dt, gg) : T(0);
+            fA = (hA > hd) ? friction_factor(hA, nq[dA][0], nq[dA][1], nmn[dA], dt, gg) : T(0);
+            fB = (hB > hd) ? friction_factor(hB, nq[dB][0], nq[dB][1], nmn[dB], dt, gg) : T(0);
           }
           const bool wet = (hC > hd) && (!hasA || hA > hd) && (!hasB || hB > hd);
           const int cs = 1 + dir;
+#pragma unroll
           for (int v = 0; v < 3; v++) {
             if (v == 0 && !wet) continue;
             T a0, aC, aB, slope;
             const T zs = zp[cs];
             if (v == 0) {
               aC = hC + zp[0];
-              a0 = hA + p.Z[ka];
-              aB = hB + p.Z[kb];
+              a0 = hA + nzb[dA];
+              aB = hB + nzb[dB];
               slope = Form<T>::eta ? w[cs] : w[cs] + zs;
             } else {
               aC = w[3 * v];
-              a0 = X[3 * v * P + ka];
-              aB = X[3 * v * P + kb];
+              a0 = nq[dA][v - 1];
+              aB = nq[dB][v - 1];
               if (FRIC) {
                 a0 = (hA > hd) ? a0 * fA : T(0);
                 aB = (hB > hd) ? aB * fB : T(0);
