@@ -256,7 +256,7 @@ def run_gpu(args, rank, world):
     dom_name = max(per_launch, key=per_launch.get)
     dom_ms, dom_n = kt[dom_name]
     mean_leaves = kupd / len(kms)
-    bpl = kernel_bytes_per_leaf(dom_name, 4, args.scheme)
+    bpl = kernel_bytes_per_leaf(dom_name, 4, args.scheme, args.grid)
     achieved = (bpl * mean_leaves) / (dom_ms / dom_n * 1e-3) / 1e9 if bpl else None
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs,
                 "unit": "GB/s", "frac": (achieved / peak_gbs) if achieved else None,
@@ -387,10 +387,11 @@ def reference_arm(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def kernel_bytes_per_leaf(name, ts, scheme="dg2"):
+def kernel_bytes_per_leaf(name, ts, scheme="dg2", grid="adaptive"):
     """Algorithmic HBM bytes per active leaf of a kernel class: values of ts
     bytes, the 8-byte active-list entry and the leaf's 32-byte neighbour
-    codes where the kernel reads them; neighbour values served from L2 are
+    codes where the kernel reads them (not on uniform grids, whose kernels
+    form both from the thread index); neighbour values served from L2 are
     not counted.  MRA classes are per node, not per leaf: None."""
     if scheme == "acc":  # discharges, then continuity (values, entry, codes)
         vals = {"dg2_update_stage1": (3 + 4 + 4, 40),   # h, z, n, old q read; new q written
@@ -406,6 +407,8 @@ def kernel_bytes_per_leaf(name, ts, scheme="dg2"):
     if name not in vals:
         return None
     n, extra = vals[name]
+    if grid == "uniform" and scheme != "acc":
+        extra = 0
     return n * ts + extra
 
 

@@ -531,6 +531,23 @@ __device__ __forceinline__ void load_nb_codes(const long long *nbr, long long q,
   c[0] = a.x; c[1] = a.y; c[2] = b.x; c[3] = b.y;
 }
 
+// Active leaf q of a uniform grid (the one level of an L = 0 hierarchy,
+// every node a leaf, the active list in node order): its node, indices and
+// four neighbour codes, the ones the list and the code pass hold for it,
+// formed from q without reading them.
+__device__ __forceinline__ long long uniform_leaf(const Geo &g, long long q, int &l, int &i, int &j,
+                                                  long long (&c)[4]) {
+  const int nx = g.nxl[0], ny = g.nyl[0];
+  l = 0;
+  j = (int)(q / nx);
+  i = (int)(q - (long long)j * nx);
+  c[0] = (i + 1 < nx) ? nb_code(NB_LEAF, 0, q + 1) : nb_code(NB_EDGE, 0, 0);
+  c[1] = (i > 0) ? nb_code(NB_LEAF, 0, q - 1) : nb_code(NB_EDGE, 0, 0);
+  c[2] = (j + 1 < ny) ? nb_code(NB_LEAF, 0, q + nx) : nb_code(NB_EDGE, 0, 0);
+  c[3] = (j > 0) ? nb_code(NB_LEAF, 0, q - nx) : nb_code(NB_EDGE, 0, 0);
+  return q;
+}
+
 // order-preserving scatter of the active leaves (each thread owns CPT
 // consecutive nodes, read as one 8-byte word); with kind_out the kinds are
 // also copied there
@@ -1435,7 +1452,8 @@ __device__ __forceinline__ T friction_factor(T h0, T qx0, T qy0, T nm, T dt, T g
 // codes are computed here from the kinds and stored for the later kernels
 // FP32: at most 64 registers a thread (four resident blocks per SM)
 template <typename T> struct LimOcc { static constexpr int blocks = std::is_same<T, float>::value ? 4 : 1; };
-template <typename T, bool FRIC, bool FV1, bool CODES>
+// UNI: a uniform grid (uniform_leaf instead of the active list and codes)
+template <typename T, bool FRIC, bool FV1, bool CODES, bool UNI>
 __global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
   const long long P = g.P;
   const T hd = geo_hd<T>(g), s3 = s3v<T>(), gg = geo_g<T>(g);
@@ -1444,8 +1462,8 @@ __global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) k_leaf_limit(Geo g, Pt
   const T rinc = ctl_rain<T>(p.ctl);
   FOR_LEAVES(p) {
     int l, i, j;
-    long long k = unpack_leaf(g, p.leaves[_q], l, i, j);
     long long code[4];
+    const long long k = UNI ? uniform_leaf(g, _q, l, i, j, code) : unpack_leaf(g, p.leaves[_q], l, i, j);
     if (CODES) {
       leaf_nb_codes(g, p.kind, l, i, j, code);
       longlong2 *dst = reinterpret_cast<longlong2 *>(p.nbr + 4LL * _q);
@@ -1514,7 +1532,7 @@ __global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) k_leaf_limit(Geo g, Pt
         // same-level leaf neighbours from the step's neighbour codes: the
         // averages (and Manning n) of all four read together (a missing
         // neighbour reads the leaf's own, unused)
-        if (!CODES) load_nb_codes(p.nbr, _q, code);
+        if (!CODES && !UNI) load_nb_codes(p.nbr, _q, code);
         bool has[4];
         T nh[4], nq[4][2], nzb[4], nmn[4];
 #pragma unroll
@@ -2146,7 +2164,8 @@ template <typename T> struct UpdOcc { static constexpr int blocks = std::is_same
 // VIEWS (adaptive grids): with vtail >= 0 the first block first encodes the
 // coarsest levels vtail..0 of the flux views (coarse_views); the other
 // instantiations do not contain the call.
-template <typename T, int STAGE, bool REFLUX, bool VIEWS>
+// UNI: a uniform grid (uniform_leaf instead of the active list and codes)
+template <typename T, int STAGE, bool REFLUX, bool VIEWS, bool UNI>
 __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out,
                                                                       int vtail) {
   const long long P = g.P;
@@ -2168,7 +2187,8 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nl;
        q += (long long)gridDim.x * blockDim.x) {
     int l, i, j;
-    const long long k = unpack_leaf(g, p.leaves[q], l, i, j);
+    long long code[4];
+    const long long k = UNI ? uniform_leaf(g, q, l, i, j, code) : unpack_leaf(g, p.leaves[q], l, i, j);
     T w[9], zc[3];
     {
       T r[12];
@@ -2180,8 +2200,7 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
     }
     // the four neighbours' views from the step's neighbour codes, all
     // loads in flight together
-    long long code[4];
-    load_nb_codes(p.nbr, q, code);
+    if (!UNI) load_nb_codes(p.nbr, q, code);
     bool in[4];
     T nb[4][4];
 #pragma unroll
@@ -2767,17 +2786,23 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
   // when the coarse leaves fit its first pass (at most lvl(lc) of them)
   const int lc = coarse_top(g);
   const int vtail = (view && lc >= 0 && lc < g.L - 1 && lvl(g, lc) <= TPB) ? lc : -1;
+  // uniform grids: leaf and neighbours from the thread index (no list or
+  // code reads)
+  const bool uni = (g.mode == MWDG_UNIFORM);
   for (int stage = 1; stage <= stages; stage++) {
     MARK(KC_LIMIT);
     const bool codes = (stage == 1 && begun);  // the step follows an adaptation
     if (stages == 1) {
-      if (codes) k_leaf_limit<T, true, true, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
-      else k_leaf_limit<T, true, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+      if (codes) k_leaf_limit<T, true, true, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+      else if (uni) k_leaf_limit<T, true, true, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+      else k_leaf_limit<T, true, true, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
     } else if (stage == 1) {
-      if (codes) k_leaf_limit<T, true, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
-      else k_leaf_limit<T, true, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+      if (codes) k_leaf_limit<T, true, false, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+      else if (uni) k_leaf_limit<T, true, false, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
+      else k_leaf_limit<T, true, false, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.U, p.Wn);
     } else {
-      k_leaf_limit<T, false, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
+      if (uni) k_leaf_limit<T, false, false, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
+      else k_leaf_limit<T, false, false, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Ui, p.Wi);
     }
     n++;
     if (view)
@@ -2790,19 +2815,22 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
     const bool reflux = (g.mode == MWDG_STATIC && g.iface == MWDG_IFACE_REFLUX);
     if (stages == 1) {
       MARK(KC_UPDATE2);
-      if (reflux) k_leaf_update<T, 3, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, -1);
-      else if (view) k_leaf_update<T, 3, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, vtail);
-      else k_leaf_update<T, 3, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, -1);
+      if (reflux) k_leaf_update<T, 3, true, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, -1);
+      else if (view) k_leaf_update<T, 3, false, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, vtail);
+      else if (uni) k_leaf_update<T, 3, false, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, -1);
+      else k_leaf_update<T, 3, false, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.U, -1);
     } else if (stage == 1) {
       MARK(KC_UPDATE1);
-      if (reflux) k_leaf_update<T, 1, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, -1);
-      else if (view) k_leaf_update<T, 1, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, vtail);
-      else k_leaf_update<T, 1, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, -1);
+      if (reflux) k_leaf_update<T, 1, true, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, -1);
+      else if (view) k_leaf_update<T, 1, false, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, vtail);
+      else if (uni) k_leaf_update<T, 1, false, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, -1);
+      else k_leaf_update<T, 1, false, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wn, nullptr, p.Ui, -1);
     } else {
       MARK(KC_UPDATE2);
-      if (reflux) k_leaf_update<T, 2, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, -1);
-      else if (view) k_leaf_update<T, 2, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, vtail);
-      else k_leaf_update<T, 2, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, -1);
+      if (reflux) k_leaf_update<T, 2, true, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, -1);
+      else if (view) k_leaf_update<T, 2, false, true, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, vtail);
+      else if (uni) k_leaf_update<T, 2, false, false, true><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, -1);
+      else k_leaf_update<T, 2, false, false, false><<<grid_leaves, TPB, 0, st>>>(g, p, p.Wi, p.Wn, p.U, -1);
     }
     n++;
   }
