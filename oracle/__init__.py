@@ -23,7 +23,8 @@ tests):
   DG2 step (Eq. 4, HLL, revisions) pinned: lake at rest (wet and with
                                   islands), Ritter and Stoker dam breaks,
                                   volume conservation, D4 symmetry
-  friction                        pinned: exact decay of a uniform flow
+  friction                        pinned: exact decay of a uniform flow; the
+                                  Manning normal depth of a sloped channel
   limiter                         pinned: hand-evaluated minmod cases (through
                                   the bit-exact restatement in dg2_adjoint.py)
   non-homogeneous interface rule  pinned on planar data: one stage on a

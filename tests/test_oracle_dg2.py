@@ -287,3 +287,31 @@ def test_interface_rule_on_planar_data_equals_the_uniform_grid_of_each_level(mod
         if any(np.any(r > l) for r in ring):
             coarse_side += 1
     assert compared >= 20 and mixed >= 8 and coarse_side >= 4, (compared, mixed, coarse_side)
+
+
+def test_dg2_relaxes_to_manning_normal_depth():
+    """Steady uniform flow down a constant slope S with Manning friction:
+    the bed-slope force g h S balances the resistance g n^2 u |u| / h^(1/3),
+    so the unit discharge is q = h^(5/3) S^(1/2) / n and the depth away
+    from the ends is h_n = (q n / S^(1/2))^(3/5) (Manning's formula).  The
+    split implicit friction reaches it up to an O(dt) error of the split.
+    Started 20 % too deep, the DG2 step (bed source, revisions, friction,
+    inflow ghost, open outlet) must drain to h_n and carry the inflow
+    through.  The discharge is read after the two stages and before the
+    next friction step, so it sits half a step's bed-slope increment
+    (dt g h S / 2, 0.2 % of q here) above the face flux that mass
+    conservation ties to the inflow."""
+    q_in, S_, n_m = 2.0, 1e-3, 0.03
+    hn = (q_in * n_m / np.sqrt(S_)) ** 0.6
+    p = S.sloped_channel(nx=200, ny=4, dx=10.0, slope=S_, q_in=q_in, n_manning=n_m)
+    p.h_vert = np.full_like(p.z_vert, 1.2 * hn)
+    p.qx_vert = np.full_like(p.z_vert, q_in)
+    s = oracle_sim(p)
+    h0, _, _ = s.fields()
+    s.run_to(3600.0)
+    h, u, v = s.fields()
+    reach = slice(40, 160)
+    assert np.abs(h0[:, reach] / hn - 1.2).max() < 1e-12
+    assert np.abs(h[:, reach] / hn - 1.0).max() < 0.01, (h[:, reach].min(), h[:, reach].max(), hn)
+    assert np.abs(h[:, reach] * u[:, reach] / q_in - 1.0).max() < 5e-3
+    assert np.abs(v).max() < 1e-9
