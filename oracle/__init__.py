@@ -19,7 +19,9 @@ tests):
   encode / decode (Eq. 9-10)      pinned: lossless round trip, planar fields
                                   give zero details
   threshold / closure / grading   pinned: brute force from quadrature details
-                                  on tiny grids, tiling and 2:1 invariants
+                                  on tiny grids, tiling and 2:1 invariants;
+                                  MWDG2 regridding (normalisation, prediction,
+                                  closure) by brute force on a tiny grid
   DG2 step (Eq. 4, HLL, revisions) pinned: lake at rest (wet and with
                                   islands), Ritter and Stoker dam breaks,
                                   volume conservation, D4 symmetry

@@ -357,3 +357,61 @@ def test_projection_matches_the_printed_eq8_examples():
         assert abs(c0[0, 0] - z0) <= 1e-15 * max(1.0, abs(z0))
         assert abs(c1x[0, 0] - nx_ / (4.0 * math.sqrt(3.0))) <= 1e-15
         assert abs(c1y[0, 0] - ny_ / (4.0 * math.sqrt(3.0))) <= 1e-15
+
+
+@pytest.mark.parametrize("eps", [1e-2, 3e-2, 1e-1])
+def test_mwdg2_adaptation_brute_force_tiny_grid(eps):
+    """MWDG2 regridding (Sect. 2.3, Eq. 9 and the normalised details of
+    Sect. 2.2) from all-finest leaves, by brute force: each node's measure
+    is the largest of its topography detail and its flow details (h, qx,
+    qy), each divided by max(1, max |v0|) over the current leaves, with the
+    details from a direct quadrature of the finest planes (independent of
+    the filter code); a node is significant when the measure reaches eps,
+    its eight same-level neighbours are flagged too (prediction), parents of
+    flagged nodes are flagged (closure), and the leaves are the unflagged
+    children of flagged nodes (or the root).  The oracle's leaves after one
+    adaptation must be exactly these."""
+    L, n = 4, 16
+    rng = np.random.default_rng(17)
+    y, x = np.mgrid[0:n + 1, 0:n + 1].astype(float)
+    z = 0.05 * x + 0.8 * np.exp(-((x - 4) ** 2 + (y - 12) ** 2) / 5.0) + 1e-5 * rng.normal(size=x.shape)
+    h = 1.0 + 0.6 * np.exp(-((x - 11) ** 2 + (y - 5) ** 2) / 3.0) + 1e-5 * rng.normal(size=x.shape)
+    qx = 0.3 * np.tanh((x - 8) / 1.5) + 1e-5 * rng.normal(size=x.shape)
+    qy = 0.2 * np.exp(-((x - 12) ** 2 + (y - 12) ** 2) / 4.0)
+    measure = {l: np.zeros((1 << l, 1 << l)) for l in range(L)}
+    for v in (z, h, qx, qy):
+        c = bilinear_projection(v)
+        d = quadrature_details(c[0], (c[1], c[2]), L)
+        for l in range(L):
+            measure[l] = np.maximum(measure[l], d[l])
+    gap = min(np.abs(measure[l] - eps).min() for l in range(L))
+    assert gap > 1e-9, gap  # no decision within rounding of eps
+    flag = {}
+    for l in range(L):
+        f0 = measure[l] >= eps
+        f = f0.copy()
+        nl = 1 << l
+        for jj, ii in zip(*np.nonzero(f0)):
+            f[max(jj - 1, 0):min(jj + 2, nl), max(ii - 1, 0):min(ii + 2, nl)] = True
+        flag[l] = f
+    for l in range(L - 1, 0, -1):
+        f = flag[l]
+        flag[l - 1] = flag[l - 1] | f.reshape(f.shape[0] // 2, 2, f.shape[1] // 2, 2).any(axis=(1, 3))
+    want = set()
+    for l in range(L + 1):
+        for jj in range(1 << l):
+            for ii in range(1 << l):
+                f = flag[l][jj, ii] if l < L else False
+                parent = True if l == 0 else flag[l - 1][jj // 2, ii // 2]
+                if parent and not f:
+                    want.add((l, ii, jj))
+    s = O.Sim(M=1, N=1, L=L, R=1.0, mode=S.ADAPTIVE, eps=eps)
+    s.load_dem(z)
+    s.load_roughness(np.zeros((n, n)))
+    s.load_initial(h, qx, qy)
+    s.init_grid()
+    s.adapt()
+    lev, ii, jj, _ = s.leaves()
+    got = set(zip(lev.tolist(), ii.tolist(), jj.tolist()))
+    assert got == want, (sorted(got - want)[:5], sorted(want - got)[:5])
+    assert 2 <= len(np.unique(lev)) and len(got) < n * n
