@@ -38,6 +38,9 @@ tests):
   autograd over a restatement of the step):
                                   pinned: bit-for-bit forward against the C
                                   step, central differences of the C step
+  the same on static graded grids (dg2_adjoint_static.py):
+                                  pinned the same way, on graded grids of
+                                  three and five levels
 """
 from __future__ import annotations
 

@@ -223,8 +223,10 @@ def _shift(a, axis, step):
     return out
 
 
-def limit(X, z, P: Grid):
-    """Stage-input limiting: (stored view w_st, flux view w_fx, flux-view bed ze)."""
+def limit(X, z, P: Grid, nbmask=None):
+    """Stage-input limiting: (stored view w_st, flux view w_fx, flux-view bed ze).
+    nbmask (non-uniform grids): which cells of the level are leaves; only
+    those count as neighbours (same-level leaf neighbours, Sect. 2.2.1)."""
     hd = P.hd
     ny, nx = X[0].shape
     h0 = X[0]
@@ -243,6 +245,9 @@ def limit(X, z, P: Grid):
                 hasA, hasB = ii < nx - 1, ii > 0
             else:
                 hasA, hasB = jj < ny - 1, jj > 0
+            if nbmask is not None:
+                hasA = hasA & _shift(nbmask, axis, 1)
+                hasB = hasB & _shift(nbmask, axis, -1)
             cs = 1 + d
             hC, hA, hB = X[0], _shift(X[0], axis, 1), _shift(X[0], axis, -1)
             wet = (hC > hd) & (~hasA | (hA > hd)) & (~hasB | (hB > hd))

@@ -1,0 +1,357 @@
+"""FP64 oracle of the discrete adjoint of the DG2 step on a static graded grid.
+
+TEST INFRASTRUCTURE ONLY.  Like the rest of ``oracle/``, this module is the
+plain, slow reference that the CUDA library is checked against; only the tests
+may import it, and the product package never imports or falls back to it.
+
+What it computes.  The DG2 step of Sect. 2.1.1 (Eq. 1-4) on the static
+non-uniform grid of Sect. 2.2.1 (the MRA of the topography run once, graded
+2:1), with the paper's rule on non-homogeneous interfaces: every leaf
+evaluates its four faces from its own limits and its neighbour's view at the
+leaf's own level.  That view is the neighbour leaf's limits; for a refined
+neighbour (whose two children on the face are leaves, the grid being graded)
+the mean of those children's interface-centre limits; for a neighbour below
+a coarser leaf (one level up, graded) the prolongation of that leaf's planes
+(Eq. 10 with zero details).  Friction, limiting (same-level leaf neighbours
+only), revision, HLL, the RK2 stages and the positivity clip are those of the
+uniform restatement in ``dg2_adjoint.py``, applied level by level.  The inputs
+are the ones the C oracle takes: the DEM vertices (projected by Eq. 8 and
+encoded up the levels by Eq. 9), the finest Manning raster (each coarser node
+the mean of its children), the initial vertex rasters and the hydrograph
+knots.  Each level is a dense array; positions that are not leaves carry
+still water and are reset to it after every stage, so they never reach a
+leaf.  The discrete adjoint is the derivative of this map by PyTorch's
+reverse-mode automatic differentiation, with the readings of
+``dg2_adjoint.py`` (time steps held at the recorded values, branches as
+taken, the interface bed max split at ties, zero derivative of the Manning
+speed at rest).  The reflux rule is not restated (the paper rule only).
+
+Pinned by the tests against: the C oracle's static-grid steps over a
+recorded time-step sequence; central differences of the C oracle's fixed-dt
+steps with respect to DEM vertices, the Manning raster, hydrograph knots and
+initial depth vertices.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from .dg2_adjoint import (F64, S3, WALL, OPEN, _Cbrt, _TieMax, _safe, _shift, _w, face_lim, friction,
+                          hll, inflow_Q, limit, post, project, revise)
+
+HALF_S3 = 0.5 * S3
+
+
+@dataclass
+class StaticGrid:
+    """A frozen graded grid: M x N roots, L levels below them, finest cell
+    size R; `leaf[l]` marks the active leaves of level l (row j south to
+    north, column i west to east).  Physical parameters as in Grid."""
+    M: int
+    N: int
+    L: int
+    R: float
+    leaf: list
+    g: float = 9.80665
+    hd: float = 1e-3
+    limiter: int = 1
+    bc: tuple = (WALL, WALL, WALL, WALL)
+    inflow_edge: int = -1
+    inflow_c0: int = 0
+    inflow_c1: int = -1
+    rain_rate: float = 0.0
+    rain_t_end: float = 0.0
+    knot_t: list = field(default_factory=list)
+
+    def __post_init__(self):
+        L = self.L
+        self.leaf = [torch.as_tensor(np.asarray(a, dtype=bool)) for a in self.leaf]
+        # refined: an ancestor of a leaf; below: covered by a coarser leaf
+        sig = [None] * (L + 1)
+        sig[L] = torch.zeros_like(self.leaf[L])
+        for l in range(L - 1, -1, -1):
+            d = self.leaf[l + 1] | sig[l + 1]
+            ny, nx = d.shape
+            sig[l] = d.reshape(ny // 2, 2, nx // 2, 2).any(dim=3).any(dim=1)
+        self.sig = sig
+        self.below = [~(self.leaf[l] | sig[l]) for l in range(L + 1)]
+
+    def nx(self, l):
+        return self.M << l
+
+    def ny(self, l):
+        return self.N << l
+
+    def dx(self, l):
+        return self.R * float(1 << (self.L - l))
+
+
+def grid_from_leaves(M, N, L, R, lev, ii, jj, **kw) -> StaticGrid:
+    leaf = [np.zeros((N << l, M << l), dtype=bool) for l in range(L + 1)]
+    for l, a, b in zip(lev, ii, jj):
+        leaf[int(l)][int(b), int(a)] = True
+    return StaticGrid(M, N, L, R, leaf, **kw)
+
+
+# ---------------------------------------------------------------------------
+# the pyramid: Eq. 9 encode, the mean of the Manning raster, Eq. 10 prolongation
+# ---------------------------------------------------------------------------
+def _lowpass(c):
+    """A_c as the C oracle forms it (rows k, columns m)"""
+    sx = 1.0 if c & 1 else -1.0
+    sy = 1.0 if c & 2 else -1.0
+    return [[1.0, 0.0, 0.0], [HALF_S3 * sx, 0.5, 0.0], [HALF_S3 * sy, 0.0, 0.5]]
+
+
+_A = [_lowpass(c) for c in range(4)]
+
+
+def _children(a):
+    """the four children (c = cx + 2 cy) of every node of the coarser level"""
+    return [a[(c >> 1)::2, (c & 1)::2] for c in range(4)]
+
+
+def encode_planes(p):
+    """Eq. 9 (scale coefficients only) of one variable's planes p = (c0, c1x,
+    c1y) one level up, summed in the C oracle's order"""
+    ch = [_children(q) for q in p]
+    out = []
+    for k in range(3):
+        acc = None
+        for c in range(4):
+            for m in range(3):
+                term = _A[c][k][m] * ch[m][c]
+                acc = term if acc is None else acc + term
+        out.append(0.25 * acc)
+    return out
+
+
+def pyramid(finest, L):
+    """planes of one variable at every level, finest (level L) first given"""
+    levels = [None] * (L + 1)
+    levels[L] = list(finest)
+    for l in range(L - 1, -1, -1):
+        levels[l] = encode_planes(levels[l + 1])
+    return levels
+
+
+def manning_levels(n_finest, L):
+    levels = [None] * (L + 1)
+    levels[L] = n_finest
+    for l in range(L - 1, -1, -1):
+        ch = _children(levels[l + 1])
+        levels[l] = 0.25 * (((ch[0] + ch[1]) + ch[2]) + ch[3])
+    return levels
+
+
+def _upsample(a):
+    return a.repeat_interleave(2, dim=0).repeat_interleave(2, dim=1)
+
+
+def prolong_planes(p, ny, nx):
+    """Eq. 10 with zero details: every node of a level from its parent's
+    planes p (one level up), in the C oracle's order"""
+    sp = [_upsample(q) for q in p]
+    jj = torch.arange(ny).view(ny, 1).expand(ny, nx)
+    ii = torch.arange(nx).view(1, nx).expand(ny, nx)
+    sx = torch.where((ii & 1) == 1, 1.0, -1.0).to(F64)
+    sy = torch.where((jj & 1) == 1, 1.0, -1.0).to(F64)
+    c0 = (sp[0] + (HALF_S3 * sx) * sp[1]) + (HALF_S3 * sy) * sp[2]
+    return [c0, 0.5 * sp[1], 0.5 * sp[2]]
+
+
+# ---------------------------------------------------------------------------
+# the operator on a graded grid
+# ---------------------------------------------------------------------------
+_PAIR = {0: (0, 2), 1: (1, 3), 2: (0, 1), 3: (2, 3)}   # the neighbour's children on face f
+_EDGE = {0: 1, 1: 0, 2: 3, 3: 2}                        # the domain edge of face f
+_STEP = {0: (1, 1), 1: (1, -1), 2: (0, 1), 3: (0, -1)}  # (axis, step) to the neighbour
+
+
+def _inside(G, l, f):
+    ny, nx = G.ny(l), G.nx(l)
+    jj = torch.arange(ny).view(ny, 1).expand(ny, nx)
+    ii = torch.arange(nx).view(1, nx).expand(ny, nx)
+    return {0: ii < nx - 1, 1: ii > 0, 2: jj < ny - 1, 3: jj > 0}[f]
+
+
+def _limits(w, ze, f):
+    """interface-centre limits (h, qx, qy, z) of flux-view planes on face f"""
+    return [face_lim(w[3 * v], w[3 * v + 1], w[3 * v + 2], f) for v in range(3)] + \
+        [face_lim(ze[0], ze[1], ze[2], f)]
+
+
+def _ghost(own, f, l, Q, t, G):
+    """boundary ghost of face f (wall mirror, open copy, or the inflow at
+    critical depth with the unit discharge of the leaf's overlap with the
+    inflow cells), over the whole level"""
+    h, qx, qy, zz = own
+    e = _EDGE[f]
+    out_h, out_x, out_y = h, qx, qy
+    if G.bc[e] == WALL:
+        if e < 2:
+            out_x = -qx
+        else:
+            out_y = -qy
+    if G.inflow_edge == e and len(G.knot_t) > 0:
+        ny, nx = h.shape
+        sh = G.L - l
+        nk = ny if e < 2 else nx
+        k = torch.arange(nk)
+        lo = torch.clamp(k << sh, min=G.inflow_c0)
+        hi = torch.clamp((k + 1) << sh, max=G.inflow_c1 + 1)
+        ov = (hi - lo).clamp(min=0).to(F64)
+        nin = float(G.inflow_c1 - G.inflow_c0 + 1)
+        q1 = inflow_Q(Q, t, G.knot_t) * ov / (nin * G.dx(l))
+        q = q1.view(ny, 1).expand(ny, nx) if e < 2 else q1.view(1, nx).expand(ny, nx)
+        has = (ov > 0).view(-1, 1).expand(ny, nx) if e < 2 else (ov > 0).view(1, -1).expand(ny, nx)
+        has = has & (q > 0.0)
+        qs = _safe(has, q)
+        hc = _Cbrt.apply(qs * qs / G.g)
+        qn = qs if e in (0, 2) else -qs
+        zero = torch.zeros_like(h)
+        out_h = _w(has, _w(h >= hc, h, hc), out_h)
+        if e < 2:
+            out_x = _w(has, qn, out_x)
+            out_y = _w(has, zero, out_y)
+        else:
+            out_x = _w(has, zero, out_x)
+            out_y = _w(has, qn, out_y)
+    return [out_h, out_x, out_y, zz]
+
+
+def operator(Wf, Zf, t, Q, G: StaticGrid):
+    """DG2 operator of every leaf (Eq. 4) from the flux views Wf[l] (9) and
+    beds Zf[l] (3) of every level; returns the nine components per level."""
+    g, hd = G.g, G.hd
+    Lout = [None] * (G.L + 1)
+    for l in range(G.L + 1):
+        if not bool(G.leaf[l].any()):
+            continue
+        ny, nx, dxl = G.ny(l), G.nx(l), G.dx(l)
+        own = [_limits(Wf[l], Zf[l], f) for f in range(4)]
+        Fh, hs, us, vs, zr = [None] * 4, [None] * 4, [None] * 4, [None] * 4, [None] * 4
+        for f in range(4):
+            fo = f ^ 1
+            axis, step = _STEP[f]
+            # the view of every node of this level across its face fo
+            view = own[fo]
+            if l + 1 <= G.L and bool(G.leaf[l + 1].any()):
+                c1, c2 = _PAIR[f]
+                fine = _limits(Wf[l + 1], Zf[l + 1], fo)
+                avg = [0.5 * (_children(q)[c1] + _children(q)[c2]) for q in fine]
+                view = [_w(G.sig[l], avg[q], view[q]) for q in range(4)]
+            if l >= 1 and bool(G.leaf[l - 1].any()):
+                par = [prolong_planes(Wf[l - 1][3 * v:3 * v + 3], ny, nx) for v in range(3)]
+                parz = prolong_planes(Zf[l - 1], ny, nx)
+                pro = [face_lim(p[0], p[1], p[2], fo) for p in par] + [face_lim(parz[0], parz[1], parz[2], fo)]
+                view = [_w(G.below[l], pro[q], view[q]) for q in range(4)]
+            nb = [_shift(q, axis, step) for q in view]
+            gh = _ghost(own[f], f, l, Q, t, G)
+            ins = _inside(G, l, f)
+            nb = [_w(ins, nb[q], gh[q]) for q in range(4)]
+            zf = _TieMax.apply(own[f][3], nb[3])
+            ro = revise(own[f][0], own[f][1], own[f][2], own[f][3], zf, hd)
+            rn = revise(nb[0], nb[1], nb[2], nb[3], zf, hd)
+            if f == 0:
+                Fh[f] = hll(ro[0], ro[1], ro[2], rn[0], rn[1], rn[2], g, hd)
+            elif f == 1:
+                Fh[f] = hll(rn[0], rn[1], rn[2], ro[0], ro[1], ro[2], g, hd)
+            elif f == 2:
+                H = hll(ro[0], ro[2], ro[1], rn[0], rn[2], rn[1], g, hd)
+                Fh[f] = [H[0], H[2], H[1]]
+            else:
+                H = hll(rn[0], rn[2], rn[1], ro[0], ro[2], ro[1], g, hd)
+                Fh[f] = [H[0], H[2], H[1]]
+            hs[f], us[f], vs[f], zr[f] = ro
+        Fxp, Gyp = [], []
+        for a in range(2):
+            f = a
+            q = hs[f] * us[f]
+            Fxp.append([q, q * us[f] + 0.5 * g * hs[f] * hs[f], q * vs[f]])
+            f = 2 + a
+            r = hs[f] * vs[f]
+            Gyp.append([r, r * us[f], r * vs[f] + 0.5 * g * hs[f] * hs[f]])
+        w, ze = Wf[l], Zf[l]
+        Lo = [None] * 9
+        for v in range(3):
+            L0 = -(Fh[0][v] - Fh[1][v]) / dxl - (Fh[2][v] - Fh[3][v]) / dxl
+            if v == 1:
+                L0 = L0 + -g * 0.5 * (hs[0] + hs[1]) * (zr[0] - zr[1]) / dxl
+            if v == 2:
+                L0 = L0 + -g * 0.5 * (hs[2] + hs[3]) * (zr[2] - zr[3]) / dxl
+            L1x = -(S3 / dxl) * (Fh[0][v] + Fh[1][v] - Fxp[0][v] - Fxp[1][v])
+            L1y = -(S3 / dxl) * (Fh[2][v] + Fh[3][v] - Gyp[0][v] - Gyp[1][v])
+            if v == 1:
+                L1x = L1x + -(2.0 * S3 * g / dxl) * w[1] * (w[1] + ze[1])
+            if v == 2:
+                L1y = L1y + -(2.0 * S3 * g / dxl) * w[2] * (w[2] + ze[2])
+            Lo[3 * v], Lo[3 * v + 1], Lo[3 * v + 2] = L0, L1x, L1y
+        Lout[l] = Lo
+    return Lout
+
+
+# ---------------------------------------------------------------------------
+# step and run
+# ---------------------------------------------------------------------------
+def _still(ref):
+    one, zero = torch.ones_like(ref), torch.zeros_like(ref)
+    return [one] + [zero] * 8
+
+
+def _mask(U, G):
+    """non-leaf positions back to still water (they never reach a leaf)"""
+    out = []
+    for l in range(G.L + 1):
+        still = _still(U[l][0])
+        out.append([_w(G.leaf[l], U[l][m], still[m]) for m in range(9)])
+    return out
+
+
+def step(U, z, nman, Q, dt, t, G: StaticGrid):
+    """One DG2 step of size dt from time t on the static grid (Eq. 4a, 4b)."""
+    rain = G.rain_rate if t < G.rain_t_end else 0.0
+    levels = range(G.L + 1)
+    Un = [friction(U[l], nman[l], dt, rain, G) for l in levels]
+    s1 = [limit(Un[l], z[l], G, nbmask=G.leaf[l]) for l in levels]
+    L1 = operator([s[1] for s in s1], [s[2] for s in s1], t, Q, G)
+    Ui = _mask([post([s1[l][0][m] + dt * L1[l][m] for m in range(9)], G.hd) if L1[l] is not None
+                else s1[l][0] for l in levels], G)
+    s2 = [limit(Ui[l], z[l], G, nbmask=G.leaf[l]) for l in levels]
+    L2 = operator([s[1] for s in s2], [s[2] for s in s2], t + dt, Q, G)
+    return _mask([post([0.5 * (s1[l][0][m] + s2[l][0][m] + dt * L2[l][m]) for m in range(9)], G.hd)
+                  if L2[l] is not None else s1[l][0] for l in levels], G)
+
+
+def inputs(z_vert, n_finest, h_vert, qx_vert, qy_vert, G: StaticGrid):
+    """per-level beds, Manning n and initial state from the C oracle's inputs
+    (vertex rasters and the finest Manning raster), as the C oracle forms them"""
+    zc = pyramid(project(z_vert), G.L)
+    nm = manning_levels(n_finest, G.L)
+    flow = [pyramid(project(v), G.L) for v in (h_vert, qx_vert, qy_vert)]
+    U = [[flow[v][l][m] for v in range(3) for m in range(3)] for l in range(G.L + 1)]
+    return _mask(U, G), zc, nm
+
+
+def leaves_of(U, G: StaticGrid):
+    """(n_leaves, 9) coefficients in the C oracle's leaf order (level, then
+    row-major)"""
+    rows = []
+    for l in range(G.L + 1):
+        idx = torch.nonzero(G.leaf[l], as_tuple=False)
+        if idx.numel() == 0:
+            continue
+        jj, ii = idx[:, 0], idx[:, 1]
+        rows.append(torch.stack([U[l][m][jj, ii] for m in range(9)], dim=1))
+    return torch.cat(rows, dim=0)
+
+
+def run(z_vert, n_finest, h_vert, qx_vert, qy_vert, Q, dts, t0, G: StaticGrid):
+    U, zc, nm = inputs(z_vert, n_finest, h_vert, qx_vert, qy_vert, G)
+    t = t0
+    for dt in dts:
+        U = step(U, zc, nm, Q, float(dt), t, G)
+        t = t + float(dt)
+    return leaves_of(U, G)

@@ -1,0 +1,118 @@
+"""Pins of the static-grid adjoint oracle (oracle/dg2_adjoint_static.py): its
+forward is the C oracle's static-grid DG2 step bit for bit (graded grids of
+three and five levels, with leaves next to refined nodes and to nodes below
+coarser leaves), and its reverse-mode gradients equal central differences of
+the C oracle's fixed-dt steps with respect to DEM vertices, the Manning
+raster, initial depth vertices and hydrograph knots."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dg2_adjoint_static as AS
+from paper_2107_02750_gb300 import synth as S
+from util import oracle_sim
+
+
+def static_reach(n, Ls, eps):
+    """the flowing reach of the uniform adjoint tests on a static graded grid
+    built from its own DEM (Sect. 2.2.1)"""
+    p, _ = S.adjoint_reach(n=n)
+    return replace(p, mode=S.STATIC, L=Ls, M=n >> Ls, N=n >> Ls, eps=eps)
+
+
+def grid_of(p, lev, ii, jj):
+    return AS.grid_from_leaves(p.M, p.N, p.L, p.dx, lev, ii, jj, bc=p.bc, inflow_edge=p.inflow_edge,
+                               inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, rain_rate=p.rain_rate,
+                               rain_t_end=p.rain_t_end, knot_t=list(p.inflow_t))
+
+
+def t64(a, grad=False):
+    return torch.tensor(np.array(a, dtype=np.float64)).requires_grad_(grad)
+
+
+def mixed_faces(lev, ii, jj, L, n):
+    """leaf faces whose neighbour is finer (the two-children mean) and
+    coarser (the prolongation)"""
+    cover = np.full((n, n), -1)
+    for l, a, b in zip(lev, ii, jj):
+        w = 1 << (L - l)
+        cover[b * w:(b + 1) * w, a * w:(a + 1) * w] = l
+    finer = coarser = 0
+    for l, a, b in zip(lev, ii, jj):
+        w = 1 << (L - l)
+        ring = []
+        if a > 0:
+            ring.append(cover[b * w:(b + 1) * w, a * w - 1])
+        if (a + 1) * w < n:
+            ring.append(cover[b * w:(b + 1) * w, (a + 1) * w])
+        if b > 0:
+            ring.append(cover[b * w - 1, a * w:(a + 1) * w])
+        if (b + 1) * w < n:
+            ring.append(cover[(b + 1) * w, a * w:(a + 1) * w])
+        finer += sum(int(np.any(r > l)) for r in ring)
+        coarser += sum(int(np.any(r < l)) for r in ring)
+    return finer, coarser
+
+
+@pytest.mark.parametrize("n,Ls,eps", [(32, 3, 5e-2), (64, 5, 1e-1)])
+def test_static_forward_is_the_c_oracle_bit_for_bit(n, Ls, eps):
+    p = static_reach(n, Ls, eps)
+    s = oracle_sim(p)
+    lev, ii, jj, c0 = s.leaves()
+    assert len(np.unique(lev)) >= 3
+    finer, coarser = mixed_faces(lev, ii, jj, Ls, n)
+    assert finer >= 10 and coarser >= 10, (finer, coarser)
+    dts = [s.step() for _ in range(8)]
+    _, _, _, cK = s.leaves()
+    G = grid_of(p, lev, ii, jj)
+    U, _, _ = AS.inputs(t64(p.z_vert), t64(p.n_cell()), t64(p.h_vert), t64(p.qx_vert), t64(p.qy_vert), G)
+    assert np.array_equal(AS.leaves_of(U, G).numpy(), c0)
+    out = AS.run(t64(p.z_vert), t64(p.n_cell()), t64(p.h_vert), t64(p.qx_vert), t64(p.qy_vert),
+                 t64(p.inflow_Q), dts, 0.0, G).detach().numpy()
+    assert np.array_equal(out, cK), np.abs(out - cK).max()
+    assert (cK[:, 3] != c0[:, 3]).any()  # the state has moved
+
+
+def test_static_gradients_match_central_differences_of_the_c_oracle():
+    p = static_reach(32, 3, 5e-2)
+    s = oracle_sim(p)
+    lev, ii, jj, _ = s.leaves()
+    dts = [s.step() for _ in range(6)]
+    G = grid_of(p, lev, ii, jj)
+    W = np.random.default_rng(7).normal(size=(len(lev), 9))
+    zv, nf, hv, Q = t64(p.z_vert, True), t64(p.n_cell(), True), t64(p.h_vert, True), t64(p.inflow_Q, True)
+    out = AS.run(zv, nf, hv, t64(p.qx_vert), t64(p.qy_vert), Q, dts, 0.0, G)
+    (out * torch.as_tensor(W)).sum().backward()
+
+    def c_loss(pp):
+        o = oracle_sim(pp)
+        l2, i2, j2, _ = o.leaves()
+        assert np.array_equal(l2, lev) and np.array_equal(i2, ii) and np.array_equal(j2, jj)
+        for dt in dts:
+            o.step_dt(dt)
+        return float((o.leaves()[3] * W).sum())
+
+    def central(field, idx, ad):
+        best = None
+        for h in (1e-5, 1e-6, 1e-7):  # the best of three steps dodges branch kinks
+            a = np.array(getattr(p, field), dtype=np.float64)
+            b = a.copy()
+            a[idx] += h
+            b[idx] -= h
+            d = (c_loss(replace(p, **{field: a})) - c_loss(replace(p, **{field: b}))) / (2 * h)
+            if best is None or abs(d - ad) < abs(best - ad):
+                best = d
+        return best
+
+    checked = 0
+    for field, tens in (("z_vert", zv), ("n_manning", nf), ("h_vert", hv), ("inflow_Q", Q)):
+        g = tens.grad.numpy()
+        assert np.abs(g).max() > 0, field
+        for f in np.argsort(-np.abs(g).ravel())[:3]:
+            idx = np.unravel_index(f, g.shape)
+            d = central(field, idx, g[idx])
+            assert abs(d - g[idx]) <= 1e-4 * abs(g[idx]) + 1e-9, (field, idx, g[idx], d)
+            checked += 1
+    assert checked == 12
