@@ -38,9 +38,9 @@ tests):
   autograd over a restatement of the step):
                                   pinned: bit-for-bit forward against the C
                                   step, central differences of the C step
-  the same on static graded grids (dg2_adjoint_static.py):
-                                  pinned the same way, on graded grids of
-                                  three and five levels
+  the same on frozen non-uniform grids (dg2_adjoint_nonuniform.py, static
+  graded and MWDG2 grids held over a segment):
+                                  pinned the same way
 """
 from __future__ import annotations
 
@@ -115,6 +115,8 @@ def lib():
         L.orc_step.restype = C.c_double
         L.orc_step.argtypes = [C.c_void_p, C.c_double]
         L.orc_stage.argtypes = [C.c_void_p, C.c_double]
+        L.orc_step_frozen.restype = C.c_double
+        L.orc_step_frozen.argtypes = [C.c_void_p, C.c_double]
         L.orc_step_dt.restype = C.c_double
         L.orc_step_dt.argtypes = [C.c_void_p, C.c_double]
         L.orc_run_to.restype = C.c_int64
@@ -269,6 +271,11 @@ class Sim:
     def step_dt(self, dt) -> float:
         """one step with the given dt (the CFL condition is not applied)"""
         return lib().orc_step_dt(self._h, dt)
+
+    def step_frozen(self, dt) -> float:
+        """one step with the given dt on the current active set (no MWDG2
+        regridding at its start)"""
+        return lib().orc_step_frozen(self._h, dt)
 
     def stage(self, dt):
         """one forward-Euler stage of Eq. 4a on the current leaves (no

@@ -1,35 +1,41 @@
-"""FP64 oracle of the discrete adjoint of the DG2 step on a static graded grid.
+"""FP64 oracle of the discrete adjoint of the DG2 step on a frozen
+non-uniform grid: a static graded grid, or an adaptive (MWDG2) grid held
+fixed over a checkpoint segment.
 
 TEST INFRASTRUCTURE ONLY.  Like the rest of ``oracle/``, this module is the
 plain, slow reference that the CUDA library is checked against; only the tests
 may import it, and the product package never imports or falls back to it.
 
-What it computes.  The DG2 step of Sect. 2.1.1 (Eq. 1-4) on the static
-non-uniform grid of Sect. 2.2.1 (the MRA of the topography run once, graded
-2:1), with the paper's rule on non-homogeneous interfaces: every leaf
-evaluates its four faces from its own limits and its neighbour's view at the
-leaf's own level.  That view is the neighbour leaf's limits; for a refined
-neighbour (whose two children on the face are leaves, the grid being graded)
-the mean of those children's interface-centre limits; for a neighbour below
-a coarser leaf (one level up, graded) the prolongation of that leaf's planes
-(Eq. 10 with zero details).  Friction, limiting (same-level leaf neighbours
-only), revision, HLL, the RK2 stages and the positivity clip are those of the
-uniform restatement in ``dg2_adjoint.py``, applied level by level.  The inputs
-are the ones the C oracle takes: the DEM vertices (projected by Eq. 8 and
-encoded up the levels by Eq. 9), the finest Manning raster (each coarser node
-the mean of its children), the initial vertex rasters and the hydrograph
-knots.  Each level is a dense array; positions that are not leaves carry
+What it computes.  The DG2 step of Sect. 2.1.1 (Eq. 1-4) on the active leaves
+of a non-uniform grid, with the paper's rule on non-homogeneous interfaces:
+every leaf evaluates its four faces from its own limits and its neighbour's
+view at the leaf's own level.  That view is the neighbour leaf's limits; for
+a neighbour below a coarser leaf, the prolongation of that leaf's planes down
+to it (Eq. 10 with zero details); for a refined neighbour, on static grids
+(Sect. 2.2.1, graded) the mean of the interface-centre limits of its two
+children on the face, and on MWDG2 grids (Sect. 2.3) the local encoding of
+its finer leaves' views (Eq. 9).  Friction, limiting (same-level leaf
+neighbours only), revision, HLL, the RK2 stages and the positivity clip are
+those of the uniform restatement in ``dg2_adjoint.py``, applied level by
+level, in the C oracle's operation order, so that a run over given time
+steps reproduces the C oracle bit for bit (its `orc_step_dt` on static grids,
+`orc_step_frozen` on a frozen MWDG2 grid).  The bed pyramid, the Manning
+means and (static grids) the initial state come from the inputs the C oracle
+takes: DEM vertices (Eq. 8, then Eq. 9 up the levels), the finest Manning
+raster (each coarser node the mean of its children), the initial vertex
+rasters.  Each level is a dense array; positions that are not leaves carry
 still water and are reset to it after every stage, so they never reach a
 leaf.  The discrete adjoint is the derivative of this map by PyTorch's
 reverse-mode automatic differentiation, with the readings of
 ``dg2_adjoint.py`` (time steps held at the recorded values, branches as
 taken, the interface bed max split at ties, zero derivative of the Manning
-speed at rest).  The reflux rule is not restated (the paper rule only).
+speed at rest).  The static reflux rule is not restated (the paper rule
+only).
 
-Pinned by the tests against: the C oracle's static-grid steps over a
-recorded time-step sequence; central differences of the C oracle's fixed-dt
-steps with respect to DEM vertices, the Manning raster, hydrograph knots and
-initial depth vertices.
+Pinned by the tests against: the C oracle's steps over recorded time steps,
+bit for bit; central differences of the C oracle's fixed-dt steps with
+respect to DEM vertices, the Manning raster, initial depth vertices (static)
+and hydrograph knots.
 """
 from __future__ import annotations
 
@@ -45,15 +51,18 @@ HALF_S3 = 0.5 * S3
 
 
 @dataclass
-class StaticGrid:
-    """A frozen graded grid: M x N roots, L levels below them, finest cell
-    size R; `leaf[l]` marks the active leaves of level l (row j south to
-    north, column i west to east).  Physical parameters as in Grid."""
+class LeafGrid:
+    """A frozen non-uniform grid: M x N roots, L levels below them, finest
+    cell size R; `leaf[l]` marks the active leaves of level l (row j south to
+    north, column i west to east); mode "static" (graded, the static
+    interface rule) or "adaptive" (MWDG2 views).  Physical parameters as in
+    Grid."""
     M: int
     N: int
     L: int
     R: float
     leaf: list
+    mode: str = "static"
     g: float = 9.80665
     hd: float = 1e-3
     limiter: int = 1
@@ -88,11 +97,11 @@ class StaticGrid:
         return self.R * float(1 << (self.L - l))
 
 
-def grid_from_leaves(M, N, L, R, lev, ii, jj, **kw) -> StaticGrid:
+def grid_from_leaves(M, N, L, R, lev, ii, jj, **kw) -> LeafGrid:
     leaf = [np.zeros((N << l, M << l), dtype=bool) for l in range(L + 1)]
     for l, a, b in zip(lev, ii, jj):
         leaf[int(l)][int(b), int(a)] = True
-    return StaticGrid(M, N, L, R, leaf, **kw)
+    return LeafGrid(M, N, L, R, leaf, **kw)
 
 
 # ---------------------------------------------------------------------------
@@ -222,10 +231,37 @@ def _ghost(own, f, l, Q, t, G):
     return [out_h, out_x, out_y, zz]
 
 
-def operator(Wf, Zf, t, Q, G: StaticGrid):
+def build_views(Wf, Zf, G: LeafGrid):
+    """the same-level view (9 flow and 3 bed coefficients) of every node of
+    every level, as the C oracle builds it: leaves their flux views, refined
+    nodes the encoding of their children's views (Eq. 9, bottom-up), nodes
+    below a coarser leaf the prolongation of their parent's view (Eq. 10 with
+    zero details, top-down)"""
+    L = G.L
+    VS = [None] * (L + 1)
+    for l in range(L, -1, -1):
+        own = list(Wf[l]) + list(Zf[l])
+        if l < L:
+            enc = []
+            for g0 in range(0, 12, 3):
+                enc += encode_planes(VS[l + 1][g0:g0 + 3])
+            own = [_w(G.sig[l], enc[m], own[m]) for m in range(12)]
+        VS[l] = own
+    V = [None] * (L + 1)
+    V[0] = VS[0]
+    for l in range(1, L + 1):
+        pro = []
+        for g0 in range(0, 12, 3):
+            pro += prolong_planes(V[l - 1][g0:g0 + 3], G.ny(l), G.nx(l))
+        V[l] = [_w(G.below[l], pro[m], VS[l][m]) for m in range(12)]
+    return V
+
+
+def operator(Wf, Zf, t, Q, G: LeafGrid):
     """DG2 operator of every leaf (Eq. 4) from the flux views Wf[l] (9) and
     beds Zf[l] (3) of every level; returns the nine components per level."""
     g, hd = G.g, G.hd
+    V = build_views(Wf, Zf, G)
     Lout = [None] * (G.L + 1)
     for l in range(G.L + 1):
         if not bool(G.leaf[l].any()):
@@ -236,18 +272,16 @@ def operator(Wf, Zf, t, Q, G: StaticGrid):
         for f in range(4):
             fo = f ^ 1
             axis, step = _STEP[f]
-            # the view of every node of this level across its face fo
-            view = own[fo]
-            if l + 1 <= G.L and bool(G.leaf[l + 1].any()):
+            # the same-level view of every node of this level across its face
+            # fo: leaves, encodings of refined nodes, prolongations below
+            # coarser leaves; on static grids a refined node's is the mean of
+            # its two children on the face
+            view = _limits(V[l][:9], V[l][9:], fo)
+            if G.mode == "static" and l + 1 <= G.L:
                 c1, c2 = _PAIR[f]
-                fine = _limits(Wf[l + 1], Zf[l + 1], fo)
+                fine = _limits(V[l + 1][:9], V[l + 1][9:], fo)
                 avg = [0.5 * (_children(q)[c1] + _children(q)[c2]) for q in fine]
                 view = [_w(G.sig[l], avg[q], view[q]) for q in range(4)]
-            if l >= 1 and bool(G.leaf[l - 1].any()):
-                par = [prolong_planes(Wf[l - 1][3 * v:3 * v + 3], ny, nx) for v in range(3)]
-                parz = prolong_planes(Zf[l - 1], ny, nx)
-                pro = [face_lim(p[0], p[1], p[2], fo) for p in par] + [face_lim(parz[0], parz[1], parz[2], fo)]
-                view = [_w(G.below[l], pro[q], view[q]) for q in range(4)]
             nb = [_shift(q, axis, step) for q in view]
             gh = _ghost(own[f], f, l, Q, t, G)
             ins = _inside(G, l, f)
@@ -310,8 +344,8 @@ def _mask(U, G):
     return out
 
 
-def step(U, z, nman, Q, dt, t, G: StaticGrid):
-    """One DG2 step of size dt from time t on the static grid (Eq. 4a, 4b)."""
+def step(U, z, nman, Q, dt, t, G: LeafGrid):
+    """One DG2 step of size dt from time t on the frozen grid (Eq. 4a, 4b)."""
     rain = G.rain_rate if t < G.rain_t_end else 0.0
     levels = range(G.L + 1)
     Un = [friction(U[l], nman[l], dt, rain, G) for l in levels]
@@ -325,7 +359,7 @@ def step(U, z, nman, Q, dt, t, G: StaticGrid):
                   if L2[l] is not None else s1[l][0] for l in levels], G)
 
 
-def inputs(z_vert, n_finest, h_vert, qx_vert, qy_vert, G: StaticGrid):
+def inputs(z_vert, n_finest, h_vert, qx_vert, qy_vert, G: LeafGrid):
     """per-level beds, Manning n and initial state from the C oracle's inputs
     (vertex rasters and the finest Manning raster), as the C oracle forms them"""
     zc = pyramid(project(z_vert), G.L)
@@ -335,7 +369,7 @@ def inputs(z_vert, n_finest, h_vert, qx_vert, qy_vert, G: StaticGrid):
     return _mask(U, G), zc, nm
 
 
-def leaves_of(U, G: StaticGrid):
+def leaves_of(U, G: LeafGrid):
     """(n_leaves, 9) coefficients in the C oracle's leaf order (level, then
     row-major)"""
     rows = []
@@ -348,7 +382,40 @@ def leaves_of(U, G: StaticGrid):
     return torch.cat(rows, dim=0)
 
 
-def run(z_vert, n_finest, h_vert, qx_vert, qy_vert, Q, dts, t0, G: StaticGrid):
+def dense_from_leaves(coef, G: LeafGrid):
+    """per-level state from (n_leaves, 9) coefficients in the C oracle's
+    leaf order (non-leaf positions still water)"""
+    U = []
+    k0 = 0
+    for l in range(G.L + 1):
+        idx = torch.nonzero(G.leaf[l], as_tuple=False)
+        still = _still(torch.zeros(G.ny(l), G.nx(l), dtype=F64))
+        n = idx.shape[0]
+        lvl = []
+        for m in range(9):
+            a = still[m].clone()
+            if n:
+                a = a.index_put((idx[:, 0], idx[:, 1]), coef[k0:k0 + n, m])
+            lvl.append(a)
+        U.append(lvl)
+        k0 += n
+    return U
+
+
+def run_from(coef0, z_vert, n_finest, Q, dts, t0, G: LeafGrid):
+    """the run from given leaf coefficients (an MWDG2 grid frozen after its
+    adaptation, whose leaves hold the decoded state)"""
+    U = dense_from_leaves(coef0, G)
+    zc = pyramid(project(z_vert), G.L)
+    nm = manning_levels(n_finest, G.L)
+    t = t0
+    for dt in dts:
+        U = step(U, zc, nm, Q, float(dt), t, G)
+        t = t + float(dt)
+    return leaves_of(U, G)
+
+
+def run(z_vert, n_finest, h_vert, qx_vert, qy_vert, Q, dts, t0, G: LeafGrid):
     U, zc, nm = inputs(z_vert, n_finest, h_vert, qx_vert, qy_vert, G)
     t = t0
     for dt in dts:

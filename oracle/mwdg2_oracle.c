@@ -1473,8 +1473,8 @@ static double acc_step(orc_sim *s, double dt) {
  * the CFL condition (dt_given <= 0).  A given dt serves the discrete adjoint:
  * the step map differentiated there is the one with the recorded dt held
  * fixed, and its central differences must be taken on that same map. */
-static double step_with(orc_sim *s, double t_end, double dt_given) {
-  orc_adapt(s);
+static double step_with(orc_sim *s, double t_end, double dt_given, int adapt) {
+  if (adapt) orc_adapt(s);
   double dt = dt_given > 0.0 ? dt_given : compute_dt(s, t_end);
   if (!(dt > 0.0)) return 0.0;
   if (s->p.scheme == 2) {
@@ -1520,7 +1520,7 @@ static double step_with(orc_sim *s, double t_end, double dt_given) {
   return dt;
 }
 
-double orc_step(orc_sim *s, double t_end) { return step_with(s, t_end, 0.0); }
+double orc_step(orc_sim *s, double t_end) { return step_with(s, t_end, 0.0, 1); }
 
 /* One forward-Euler stage of Eq. 4a on the current active leaves, with no
  * adaptation, rain or friction and the clock left where it is: the stage
@@ -1528,7 +1528,13 @@ double orc_step(orc_sim *s, double t_end) { return step_with(s, t_end, 0.0); }
  * between grids (the interface rule of Sect. 2.3). */
 void orc_stage(orc_sim *s, double dt) { (void)rk_stage(s, s->U, s->Wn, NULL, s->U, dt, s->t); }
 
-double orc_step_dt(orc_sim *s, double dt) { return step_with(s, INFINITY, dt); }
+double orc_step_dt(orc_sim *s, double dt) { return step_with(s, INFINITY, dt, 1); }
+
+/* A step of the given dt on the current active set, without the MWDG2
+ * regridding at its start: the map that an adjoint differentiates when it
+ * freezes the adaptive grid over a checkpoint segment (test entry point; on
+ * uniform and static grids it equals orc_step_dt). */
+double orc_step_frozen(orc_sim *s, double dt) { return step_with(s, INFINITY, dt, 0); }
 
 int64_t orc_run_to(orc_sim *s, double t_end, int64_t max_steps) {
   int64_t k = 0;

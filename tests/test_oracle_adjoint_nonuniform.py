@@ -1,16 +1,17 @@
-"""Pins of the static-grid adjoint oracle (oracle/dg2_adjoint_static.py): its
-forward is the C oracle's static-grid DG2 step bit for bit (graded grids of
-three and five levels, with leaves next to refined nodes and to nodes below
-coarser leaves), and its reverse-mode gradients equal central differences of
-the C oracle's fixed-dt steps with respect to DEM vertices, the Manning
-raster, initial depth vertices and hydrograph knots."""
+"""Pins of the non-uniform-grid adjoint oracle
+(oracle/dg2_adjoint_nonuniform.py): its forward is the C oracle's DG2 step
+bit for bit on static graded grids (three and five levels) and on MWDG2
+grids frozen after a regridding, with leaves next to refined nodes and to
+nodes below coarser leaves; its reverse-mode gradients equal central
+differences of the C oracle's fixed-dt steps with respect to DEM vertices,
+the Manning raster, initial depth vertices (static) and hydrograph knots."""
 from dataclasses import replace
 
 import numpy as np
 import pytest
 import torch
 
-from oracle import dg2_adjoint_static as AS
+from oracle import dg2_adjoint_nonuniform as AS
 from paper_2107_02750_gb300 import synth as S
 from util import oracle_sim
 
@@ -22,8 +23,8 @@ def static_reach(n, Ls, eps):
     return replace(p, mode=S.STATIC, L=Ls, M=n >> Ls, N=n >> Ls, eps=eps)
 
 
-def grid_of(p, lev, ii, jj):
-    return AS.grid_from_leaves(p.M, p.N, p.L, p.dx, lev, ii, jj, bc=p.bc, inflow_edge=p.inflow_edge,
+def grid_of(p, lev, ii, jj, mode="static"):
+    return AS.grid_from_leaves(p.M, p.N, p.L, p.dx, lev, ii, jj, mode=mode, bc=p.bc, inflow_edge=p.inflow_edge,
                                inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, rain_rate=p.rain_rate,
                                rain_t_end=p.rain_t_end, knot_t=list(p.inflow_t))
 
@@ -116,3 +117,82 @@ def test_static_gradients_match_central_differences_of_the_c_oracle():
             assert abs(d - g[idx]) <= 1e-4 * abs(g[idx]) + 1e-9, (field, idx, g[idx], d)
             checked += 1
     assert checked == 12
+
+
+def adaptive_reach(n, Ls, eps):
+    p, _ = S.adjoint_reach(n=n)
+    return replace(p, mode=S.ADAPTIVE, L=Ls, M=n >> Ls, N=n >> Ls, eps=eps)
+
+
+def frozen_start(p):
+    """the C oracle after one MWDG2 regridding, and a time step of 0.8 times
+    the CFL choice on that state"""
+    s = oracle_sim(p)
+    s.adapt()
+    probe = oracle_sim(p)
+    dt = 0.8 * probe.step()
+    return s, dt
+
+
+@pytest.mark.parametrize("n,Ls,eps", [(32, 3, 5e-2), (64, 4, 2e-2)])
+def test_frozen_mwdg2_forward_is_the_c_oracle_bit_for_bit(n, Ls, eps):
+    """On an MWDG2 grid frozen after its regridding, refined neighbours are
+    seen through the encoding of their leaves' views and nodes below coarser
+    leaves through prolongation (Sect. 2.3); the restatement started from
+    the C oracle's leaves equals its frozen steps bit for bit."""
+    p = adaptive_reach(n, Ls, eps)
+    s, dt = frozen_start(p)
+    lev, ii, jj, c0 = s.leaves()
+    assert len(np.unique(lev)) >= 2
+    finer, coarser = mixed_faces(lev, ii, jj, Ls, n)
+    assert finer >= 10 and coarser >= 10, (finer, coarser)
+    dts = [dt] * 8
+    for d in dts:
+        s.step_frozen(d)
+    l2, _, _, cK = s.leaves()
+    assert np.array_equal(l2, lev)
+    G = grid_of(p, lev, ii, jj, mode="adaptive")
+    out = AS.run_from(t64(c0), t64(p.z_vert), t64(p.n_cell()), t64(p.inflow_Q), dts, 0.0, G).detach().numpy()
+    assert np.array_equal(out, cK), np.abs(out - cK).max()
+    assert (cK[:, 3] != c0[:, 3]).any()
+
+
+def test_frozen_mwdg2_gradients_match_central_differences_of_the_c_oracle():
+    p = adaptive_reach(32, 3, 5e-2)
+    s, dt = frozen_start(p)
+    lev, ii, jj, c0 = s.leaves()
+    dts = [dt] * 6
+    G = grid_of(p, lev, ii, jj, mode="adaptive")
+    W = np.random.default_rng(9).normal(size=(len(lev), 9))
+    zv, nf, Q = t64(p.z_vert, True), t64(p.n_cell(), True), t64(p.inflow_Q, True)
+    out = AS.run_from(t64(c0), zv, nf, Q, dts, 0.0, G)
+    (out * torch.as_tensor(W)).sum().backward()
+
+    def c_loss(pp):
+        o = oracle_sim(pp)
+        o.adapt()
+        l2, i2, j2, u0 = o.leaves()
+        assert np.array_equal(l2, lev) and np.array_equal(i2, ii) and np.array_equal(j2, jj)
+        assert np.array_equal(u0, c0)
+        for d in dts:
+            o.step_frozen(d)
+        return float((o.leaves()[3] * W).sum())
+
+    checked = 0
+    for field, tens in (("z_vert", zv), ("n_manning", nf), ("inflow_Q", Q)):
+        g = tens.grad.numpy()
+        assert np.abs(g).max() > 0, field
+        for f in np.argsort(-np.abs(g).ravel())[:3]:
+            idx = np.unravel_index(f, g.shape)
+            best = None
+            for h in (1e-5, 1e-6, 1e-7):
+                a = np.array(getattr(p, field), dtype=np.float64)
+                b = a.copy()
+                a[idx] += h
+                b[idx] -= h
+                d = (c_loss(replace(p, **{field: a})) - c_loss(replace(p, **{field: b}))) / (2 * h)
+                if best is None or abs(d - g[idx]) < abs(best - g[idx]):
+                    best = d
+            assert abs(best - g[idx]) <= 1e-4 * abs(g[idx]) + 1e-9, (field, idx, g[idx], best)
+            checked += 1
+    assert checked == 9
