@@ -3,6 +3,8 @@ point that include/*.h declares (no compute calls: no GPU needed)."""
 import re
 from pathlib import Path
 
+import pytest
+
 from paper_2107_02750_gb300 import adjoint, binding, build
 
 INCLUDE = Path(__file__).resolve().parents[1] / "include"
@@ -78,3 +80,51 @@ def test_adjoint_parameters_are_validated_without_device():
     assert create(inflow_edge=4) == -1
     assert create(inflow_edge=0, inflow_c0=3, inflow_c1=2) == -1
     assert create(inflow_edge=0, inflow_c0=0, inflow_c1=8) == -1     # beyond the 8 cells of the edge
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("L", -1, -2), ("M", 0, -2), ("N", -3, -2), ("dx", 0.0, -2), ("dx", float("nan"), -2),
+    ("mode", 3, -1), ("mode", -1, -1), ("precision", 2, -1), ("cfl", 0.0, -1), ("cfl", float("nan"), -1),
+    ("g", -9.8, -1), ("h_dry", -1e-3, -1), ("dt_max", 0.0, -1), ("eps", -1e-3, -1),
+    ("eps", float("inf"), -1), ("eps", float("nan"), -1), ("iface_rule", 2, -1), ("scheme", 3, -1),
+])
+def test_create_rejects_each_bad_parameter_without_device(field, value, status):
+    """mwdg_create answers every invalid parameter with its status before any
+    device work (MWDG_ERR_DIMS for sizes, MWDG_ERR_ARG otherwise), and
+    leaves the handle NULL."""
+    import ctypes as C
+    L = binding.lib()
+    p = binding.Params()
+    assert L.mwdg_params_default(C.byref(p)) == 0
+    p.M = p.N = 4
+    p.L = 3
+    setattr(p, field, value)
+    h = C.c_void_p(12345)
+    assert L.mwdg_create(C.byref(p), C.byref(h)) == status
+    assert not h.value
+
+
+@pytest.mark.parametrize("combo", ["reflux_adaptive", "acc_adaptive", "too_wide", "too_tall"])
+def test_create_rejects_bad_combinations_without_device(combo):
+    """the reflux rule and the ACC solver are static-grid options (not on
+    adaptive grids), and a finest level wider or taller than 2^20 cells is
+    refused"""
+    import ctypes as C
+    L = binding.lib()
+    p = binding.Params()
+    L.mwdg_params_default(C.byref(p))
+    if combo == "reflux_adaptive":
+        p.L, p.mode, p.iface_rule = 3, 2, 1
+        want = -1
+    elif combo == "acc_adaptive":
+        p.L, p.mode, p.scheme = 3, 2, 2
+        want = -1
+    elif combo == "too_wide":
+        p.M, p.L = 3, 19  # 3 * 2^19 > 2^20
+        want = -2
+    else:
+        p.N, p.L = 2049, 10
+        want = -2
+    h = C.c_void_p(1)
+    assert L.mwdg_create(C.byref(p), C.byref(h)) == want
+    assert not h.value
