@@ -315,3 +315,49 @@ def test_dg2_relaxes_to_manning_normal_depth():
     assert np.abs(h[:, reach] / hn - 1.0).max() < 0.01, (h[:, reach].min(), h[:, reach].max(), hn)
     assert np.abs(h[:, reach] * u[:, reach] / q_in - 1.0).max() < 5e-3
     assert np.abs(v).max() < 1e-9
+
+
+def test_cfl_time_step_closed_forms():
+    """The time step (Sect. 2.1.1, Courant number 0.33 for DG2): C times the
+    minimum over wet leaves of dx / (|u| + sqrt(g h)) in both directions,
+    with the inflow ghost at critical depth (dx / (q / h_c + sqrt(g h_c)),
+    h_c = (q^2 / g)^(1/3)) as one more candidate, at most dt_max and never
+    past the end time."""
+    g, C = 9.80665, 0.33
+    n = 8
+    ones = np.ones((n + 1, n + 1))
+    # uniform flow: the faster of the two directions decides
+    p = S.Problem("cfl", n, n, 0, 5.0, 0.0 * ones, 2.0 * ones, 3.0 * ones, -1.0 * ones, bc=(S.WALL,) * 4)
+    s = oracle_sim(p, dt_max=10.0)
+    want = C * min(5.0 / (1.5 + np.sqrt(g * 2.0)), 5.0 / (0.5 + np.sqrt(g * 2.0)))
+    assert abs(s.step() - want) <= 1e-15 * want
+    # dt_max and the end time clamp it
+    s = oracle_sim(p, dt_max=0.1)
+    assert s.step() == 0.1
+    s = oracle_sim(p, dt_max=10.0)
+    assert abs(s.step(0.05) - 0.05) <= 1e-17
+    # a static graded grid: brute force over its leaves (dx per level)
+    q = S.valley(n=64, L=6, mode=S.STATIC, eps=1e-2, peak_Q=0.0)
+    x = np.linspace(0.0, 1.0, 65)
+    X, Y = np.meshgrid(x, x)
+    q.h_vert = 1.0 + 0.5 * X
+    q.qx_vert = 0.8 * np.sin(3.0 * Y)
+    q.qy_vert = 0.3 + 0.2 * X * Y
+    q.inflow_edge = -1
+    s = oracle_sim(q, dt_max=100.0)
+    lev, _, _, c = s.leaves()
+    assert len(np.unique(lev)) > 1
+    dx = q.dx * 2.0 ** (q.L - lev)
+    h = c[:, 0]
+    cel = np.sqrt(g * h)
+    want = C * np.min(np.minimum(dx / (np.abs(c[:, 3] / h) + cel), dx / (np.abs(c[:, 6] / h) + cel)))
+    assert abs(s.step() - want) <= 1e-14 * want
+    # a dry domain: only the inflow ghost's critical-depth speed counts
+    d = S.Problem("dry_inflow", n, n, 0, 2.0, 0.0 * ones, 0.0 * ones, 0.0 * ones, 0.0 * ones,
+                  bc=(S.WALL,) * 4, inflow_edge=S.WEST, inflow_c0=2, inflow_c1=5,
+                  inflow_t=np.array([0.0, 100.0]), inflow_Q=np.array([4.0, 4.0]))
+    s = oracle_sim(d, dt_max=100.0)
+    qu = 4.0 / (4 * 2.0)  # unit discharge over the four inflow cells
+    hc = (qu * qu / g) ** (1.0 / 3.0)
+    want = C * 2.0 / (qu / hc + np.sqrt(g * hc))
+    assert abs(s.step() - want) <= 1e-12 * want
