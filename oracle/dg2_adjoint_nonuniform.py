@@ -422,3 +422,68 @@ def run(z_vert, n_finest, h_vert, qx_vert, qy_vert, Q, dts, t0, G: LeafGrid):
         U = step(U, zc, nm, Q, float(dt), t, G)
         t = t + float(dt)
     return leaves_of(U, G)
+
+
+# ---------------------------------------------------------------------------
+# the reverse of the views: who reads each leaf's flux-view planes
+# ---------------------------------------------------------------------------
+def _face_row(f):
+    """face_lim on face f as a row vector on (c0, c1x, c1y)"""
+    return {0: np.array([1.0, S3, 0.0]), 1: np.array([1.0, -S3, 0.0]), 2: np.array([1.0, 0.0, S3]),
+            3: np.array([1.0, 0.0, -S3])}[f]
+
+
+def view_reverse_table(G: LeafGrid):
+    """The neighbour-side limits of every leaf face, written as a linear
+    function of the owner leaves' flux-view planes: entries (reader leaf,
+    face f, owner leaf, w) with nb_q(reader, f) = sum over its entries of
+    w . planes_q(owner), the same 3-vector w for each variable q (h, qx, qy,
+    bed).  Leaves are numbered in the C oracle's order (level, then
+    row-major); domain-edge faces (ghosts) have no entries.  Same-level leaf:
+    w = the face-limit row of face f^1.  Static refined neighbour: half of it
+    on each of the two children on the face.  MWDG2 refined neighbour: the
+    transpose of the encode down its subtree (1/4 row A_c per level).  Below
+    a coarser leaf: the transpose of the prolongation up to that leaf (row
+    A_c^T per level).  The reverse of the views is then g_owner += w
+    cot(reader, f, q), which is what reverse kernels gather by owner."""
+    L = G.L
+    index = {}
+    for l in range(L + 1):
+        for j, i in torch.nonzero(G.leaf[l], as_tuple=False).tolist():
+            index[(l, i, j)] = len(index)
+
+    def kind(l, i, j):
+        return 'leaf' if bool(G.leaf[l][j, i]) else ('sig' if bool(G.sig[l][j, i]) else 'below')
+
+    def down(l, a, b, row):
+        out = []
+        for c in range(4):
+            ca, cb = 2 * a + (c & 1), 2 * b + (c >> 1)
+            r = 0.25 * row @ np.array(_A[c])
+            out += [(index[(l + 1, ca, cb)], r)] if kind(l + 1, ca, cb) == 'leaf' else down(l + 1, ca, cb, r)
+        return out
+
+    def up(l, a, b, row):
+        r = row @ np.array(_A[(a & 1) + 2 * (b & 1)]).T
+        pa, pb = a >> 1, b >> 1
+        return [(index[(l - 1, pa, pb)], r)] if kind(l - 1, pa, pb) == 'leaf' else up(l - 1, pa, pb, r)
+
+    table = []
+    for (l, i, j), k in index.items():
+        for f in range(4):
+            a = i + (f == 0) - (f == 1)
+            b = j + (f == 2) - (f == 3)
+            if not (0 <= a < G.nx(l) and 0 <= b < G.ny(l)):
+                continue
+            row = _face_row(f ^ 1)
+            kd = kind(l, a, b)
+            if kd == 'leaf':
+                ents = [(index[(l, a, b)], row)]
+            elif kd == 'sig' and G.mode == 'static':
+                ents = [(index[(l + 1, 2 * a + (c & 1), 2 * b + (c >> 1))], 0.5 * row) for c in _PAIR[f]]
+            elif kd == 'sig':
+                ents = down(l, a, b, row)
+            else:
+                ents = up(l, a, b, row)
+            table += [(k, f, owner, w) for owner, w in ents]
+    return table

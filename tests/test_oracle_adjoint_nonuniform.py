@@ -196,3 +196,54 @@ def test_frozen_mwdg2_gradients_match_central_differences_of_the_c_oracle():
             assert abs(best - g[idx]) <= 1e-4 * abs(g[idx]) + 1e-9, (field, idx, g[idx], best)
             checked += 1
     assert checked == 9
+
+
+@pytest.mark.parametrize("mode", ["static", "adaptive"])
+def test_view_reverse_table_is_the_transpose_of_the_views(mode):
+    """The reverse table of the views (what the non-uniform reverse kernels
+    gather by owner) applied to random face cotangents equals autograd of
+    the oracle's view construction: leaves, static two-children means,
+    MWDG2 encodes of refined subtrees, prolongations below coarser leaves."""
+    n, Ls, eps = 32, 3, 5e-2
+    p = static_reach(n, Ls, eps) if mode == "static" else adaptive_reach(n, Ls, eps)
+    s = oracle_sim(p)
+    if mode == "adaptive":
+        s.adapt()
+    lev, ii, jj, _ = s.leaves()
+    G = grid_of(p, lev, ii, jj, mode=mode)
+    nl = len(lev)
+    rng = np.random.default_rng(3)
+    planes = torch.tensor(rng.normal(size=(nl, 12)), requires_grad=True)
+    dense = AS.dense_from_leaves(planes[:, :9], G)
+    beds = AS.dense_from_leaves(torch.cat([planes[:, 9:], torch.zeros(nl, 6, dtype=torch.float64)], 1), G)
+    V = AS.build_views(dense, [b[:3] for b in beds], G)
+    cot = rng.normal(size=(nl, 4, 4))
+    index = {(int(l), int(a), int(b)): k for k, (l, a, b) in enumerate(zip(lev, ii, jj))}
+    loss = torch.zeros((), dtype=torch.float64)
+    for l in range(Ls + 1):
+        if not bool(G.leaf[l].any()):
+            continue
+        for f in range(4):
+            fo = f ^ 1
+            axis, step = AS._STEP[f]
+            view = AS._limits(V[l][:9], V[l][9:], fo)
+            if mode == "static" and l + 1 <= Ls:
+                c1, c2 = AS._PAIR[f]
+                fine = AS._limits(V[l + 1][:9], V[l + 1][9:], fo)
+                avg = [0.5 * (AS._children(q)[c1] + AS._children(q)[c2]) for q in fine]
+                view = [AS._w(G.sig[l], avg[q], view[q]) for q in range(4)]
+            nb = [AS._shift(q, axis, step) for q in view]
+            ins = AS._inside(G, l, f)
+            for (ll, a, b), k in index.items():
+                if ll == l and bool(ins[b, a]):
+                    for q in range(4):
+                        loss = loss + float(cot[k, f, q]) * nb[q][b, a]
+    loss.backward()
+    ref = planes.grad.numpy()
+    got = np.zeros((nl, 12))
+    table = AS.view_reverse_table(G)
+    for k, f, owner, w in table:
+        for q in range(4):
+            got[owner, 3 * q:3 * q + 3] += w * cot[k, f, q]
+    assert len(table) > 4 * nl // 2
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
