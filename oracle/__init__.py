@@ -25,6 +25,12 @@ tests):
   DG2 step (Eq. 4, HLL, revisions) pinned: lake at rest (wet and with
                                   islands), Ritter and Stoker dam breaks,
                                   volume conservation, D4 symmetry
+  outflow limit (non-negative      pinned: no clipped depth and the mass budget
+  depths at wet/dry fronts)       closed without clipped volume on the valley
+                                  window through the inflow and on a dam
+                                  break over a steep dry slope; a mound drained
+                                  in one stage ends at zero; a scratch copy
+                                  without the limit fails each of these
   friction                        pinned: exact decay of a uniform flow; the
                                   Manning normal depth of a sloped channel
   limiter                         pinned: hand-evaluated minmod cases (through
@@ -94,52 +100,56 @@ class Params(C.Structure):
 _lib = None
 
 
+def load(path) -> C.CDLL:
+    """The oracle's entry points from a compiled copy at path, typed."""
+    L = C.CDLL(str(path))
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int32)
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.POINTER(Params)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_levels.restype = C.c_int
+    L.orc_levels.argtypes = [C.c_void_p]
+    for name in ("orc_load_dem", "orc_load_roughness"):
+        getattr(L, name).argtypes = [C.c_void_p, dp]
+    L.orc_load_initial.argtypes = [C.c_void_p, dp, dp, dp, C.c_int]
+    L.orc_set_inflow.argtypes = [C.c_void_p, C.c_int, dp, dp]
+    L.orc_init_grid.argtypes = [C.c_void_p]
+    L.orc_adapt.argtypes = [C.c_void_p]
+    L.orc_step.restype = C.c_double
+    L.orc_step.argtypes = [C.c_void_p, C.c_double]
+    L.orc_stage.argtypes = [C.c_void_p, C.c_double]
+    L.orc_step_frozen.restype = C.c_double
+    L.orc_step_frozen.argtypes = [C.c_void_p, C.c_double]
+    L.orc_step_dt.restype = C.c_double
+    L.orc_step_dt.argtypes = [C.c_void_p, C.c_double]
+    L.orc_run_to.restype = C.c_int64
+    L.orc_run_to.argtypes = [C.c_void_p, C.c_double, C.c_int64]
+    L.orc_time.restype = C.c_double
+    L.orc_time.argtypes = [C.c_void_p]
+    L.orc_steps.restype = C.c_int64
+    L.orc_steps.argtypes = [C.c_void_p]
+    L.orc_last_dt.restype = C.c_double
+    L.orc_last_dt.argtypes = [C.c_void_p]
+    L.orc_diag.argtypes = [C.c_void_p, dp]
+    L.orc_n_leaves.restype = C.c_int64
+    L.orc_n_leaves.argtypes = [C.c_void_p]
+    L.orc_get_leaves.argtypes = [C.c_void_p, ip, ip, ip, dp]
+    L.orc_read_fields.argtypes = [C.c_void_p, dp, dp, dp]
+    L.orc_get_z.argtypes = [C.c_void_p, C.c_int, dp, dp]
+    L.orc_project.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp]
+    L.orc_filters.argtypes = [dp, dp]
+    L.orc_encode_node.argtypes = [dp, dp, dp]
+    L.orc_decode_node.argtypes = [dp, dp, dp]
+    L.orc_haar_encode.argtypes = [dp, dp, dp]
+    L.orc_haar_decode.argtypes = [C.c_double, dp, dp]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = build()
-        L = C.CDLL(str(path))
-        dp = C.POINTER(C.c_double)
-        ip = C.POINTER(C.c_int32)
-        L.orc_create.restype = C.c_void_p
-        L.orc_create.argtypes = [C.POINTER(Params)]
-        L.orc_destroy.argtypes = [C.c_void_p]
-        L.orc_levels.restype = C.c_int
-        L.orc_levels.argtypes = [C.c_void_p]
-        for name in ("orc_load_dem", "orc_load_roughness"):
-            getattr(L, name).argtypes = [C.c_void_p, dp]
-        L.orc_load_initial.argtypes = [C.c_void_p, dp, dp, dp, C.c_int]
-        L.orc_set_inflow.argtypes = [C.c_void_p, C.c_int, dp, dp]
-        L.orc_init_grid.argtypes = [C.c_void_p]
-        L.orc_adapt.argtypes = [C.c_void_p]
-        L.orc_step.restype = C.c_double
-        L.orc_step.argtypes = [C.c_void_p, C.c_double]
-        L.orc_stage.argtypes = [C.c_void_p, C.c_double]
-        L.orc_step_frozen.restype = C.c_double
-        L.orc_step_frozen.argtypes = [C.c_void_p, C.c_double]
-        L.orc_step_dt.restype = C.c_double
-        L.orc_step_dt.argtypes = [C.c_void_p, C.c_double]
-        L.orc_run_to.restype = C.c_int64
-        L.orc_run_to.argtypes = [C.c_void_p, C.c_double, C.c_int64]
-        L.orc_time.restype = C.c_double
-        L.orc_time.argtypes = [C.c_void_p]
-        L.orc_steps.restype = C.c_int64
-        L.orc_steps.argtypes = [C.c_void_p]
-        L.orc_last_dt.restype = C.c_double
-        L.orc_last_dt.argtypes = [C.c_void_p]
-        L.orc_diag.argtypes = [C.c_void_p, dp]
-        L.orc_n_leaves.restype = C.c_int64
-        L.orc_n_leaves.argtypes = [C.c_void_p]
-        L.orc_get_leaves.argtypes = [C.c_void_p, ip, ip, ip, dp]
-        L.orc_read_fields.argtypes = [C.c_void_p, dp, dp, dp]
-        L.orc_get_z.argtypes = [C.c_void_p, C.c_int, dp, dp]
-        L.orc_project.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp]
-        L.orc_filters.argtypes = [dp, dp]
-        L.orc_encode_node.argtypes = [dp, dp, dp]
-        L.orc_decode_node.argtypes = [dp, dp, dp]
-        L.orc_haar_encode.argtypes = [dp, dp, dp]
-        L.orc_haar_decode.argtypes = [C.c_double, dp, dp]
-        _lib = L
+        _lib = load(build())
     return _lib
 
 
@@ -216,7 +226,8 @@ class Sim:
     def __init__(self, *, M, N, L, R, mode=UNIFORM, eps=1e-3, cfl=0.33, g=9.80665,
                  h_dry=1e-3, dt_max=1.0, limiter=1, bc=(WALL, WALL, WALL, WALL),
                  inflow_edge=-1, inflow_c0=0, inflow_c1=-1, rain_rate=0.0, rain_t_end=0.0,
-                 iface_rule=0, scheme=0):
+                 iface_rule=0, scheme=0, library=None):
+        self._L = library if library is not None else lib()
         p = Params()
         p.M, p.N, p.L, p.mode = M, N, L, mode
         p.R, p.eps, p.cfl, p.g, p.h_dry, p.dt_max = R, eps, cfl, g, h_dry, dt_max
@@ -229,23 +240,23 @@ class Sim:
         p.scheme = scheme
         self.p = p
         self.nx, self.ny = M << L, N << L
-        self._h = lib().orc_create(C.byref(p))
+        self._h = self._L.orc_create(C.byref(p))
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self._h = None
 
     def load_dem(self, z_vert):
         z = _f64(z_vert)
         assert z.shape == (self.ny + 1, self.nx + 1)
-        lib().orc_load_dem(self._h, _dp(z))
+        self._L.orc_load_dem(self._h, _dp(z))
 
     def load_roughness(self, n):
         a = np.broadcast_to(np.asarray(n, dtype=np.float64), (self.ny, self.nx))
         a = _f64(a)
-        lib().orc_load_roughness(self._h, _dp(a))
+        self._L.orc_load_roughness(self._h, _dp(a))
 
     def load_initial(self, h_vert, qx_vert=None, qy_vert=None, is_eta=False):
         shape = (self.ny + 1, self.nx + 1)
@@ -253,79 +264,79 @@ class Sim:
         qx = _f64(np.zeros(shape) if qx_vert is None else qx_vert)
         qy = _f64(np.zeros(shape) if qy_vert is None else qy_vert)
         assert h.shape == shape and qx.shape == shape and qy.shape == shape
-        lib().orc_load_initial(self._h, _dp(h), _dp(qx), _dp(qy), int(is_eta))
+        self._L.orc_load_initial(self._h, _dp(h), _dp(qx), _dp(qy), int(is_eta))
 
     def set_inflow(self, t, Q):
         t, Q = _f64(t), _f64(Q)
-        lib().orc_set_inflow(self._h, len(t), _dp(t), _dp(Q))
+        self._L.orc_set_inflow(self._h, len(t), _dp(t), _dp(Q))
 
     def init_grid(self):
-        lib().orc_init_grid(self._h)
+        self._L.orc_init_grid(self._h)
 
     def adapt(self):
-        lib().orc_adapt(self._h)
+        self._L.orc_adapt(self._h)
 
     def step(self, t_end=float("inf")) -> float:
-        return lib().orc_step(self._h, t_end)
+        return self._L.orc_step(self._h, t_end)
 
     def step_dt(self, dt) -> float:
         """one step with the given dt (the CFL condition is not applied)"""
-        return lib().orc_step_dt(self._h, dt)
+        return self._L.orc_step_dt(self._h, dt)
 
     def step_frozen(self, dt) -> float:
         """one step with the given dt on the current active set (no MWDG2
         regridding at its start)"""
-        return lib().orc_step_frozen(self._h, dt)
+        return self._L.orc_step_frozen(self._h, dt)
 
     def stage(self, dt):
         """one forward-Euler stage of Eq. 4a on the current leaves (no
         adaptation, rain, friction or clock advance)"""
-        lib().orc_stage(self._h, dt)
+        self._L.orc_stage(self._h, dt)
 
     def run_to(self, t_end, max_steps=1 << 40) -> int:
-        return lib().orc_run_to(self._h, t_end, max_steps)
+        return self._L.orc_run_to(self._h, t_end, max_steps)
 
     @property
     def t(self) -> float:
-        return lib().orc_time(self._h)
+        return self._L.orc_time(self._h)
 
     @property
     def steps(self) -> int:
-        return lib().orc_steps(self._h)
+        return self._L.orc_steps(self._h)
 
     @property
     def last_dt(self) -> float:
-        return lib().orc_last_dt(self._h)
+        return self._L.orc_last_dt(self._h)
 
     def diag(self) -> dict:
         out = np.empty(6)
-        lib().orc_diag(self._h, _dp(out))
+        self._L.orc_diag(self._h, _dp(out))
         return dict(volume=out[0], v_in=out[1], v_out=out[2], v_rain=out[3], v_clip=out[4],
                     n_clip=int(out[5]))
 
     def leaves(self):
         """(level, i, j, coeffs (n, 9)) ordered by level then row-major."""
-        n = lib().orc_n_leaves(self._h)
+        n = self._L.orc_n_leaves(self._h)
         lev = np.empty(n, np.int32)
         ii = np.empty(n, np.int32)
         jj = np.empty(n, np.int32)
         co = np.empty((n, 9))
-        lib().orc_get_leaves(self._h, _ip(lev), _ip(ii), _ip(jj), _dp(co))
+        self._L.orc_get_leaves(self._h, _ip(lev), _ip(ii), _ip(jj), _dp(co))
         return lev, ii, jj, co
 
     def fields(self):
         """finest-resolution (h, u, v), each (ny, nx)."""
         h, u, v = (np.empty((self.ny, self.nx)) for _ in range(3))
-        lib().orc_read_fields(self._h, _dp(h), _dp(u), _dp(v))
+        self._L.orc_read_fields(self._h, _dp(h), _dp(u), _dp(v))
         return h, u, v
 
     def z_level(self, level):
         """static topography pyramid at a stored level: (coeffs (3, n), dz (n,))."""
-        Ls = lib().orc_levels(self._h)
+        Ls = self._L.orc_levels(self._h)
         nl = (self.p.M << level) * (self.p.N << level) if Ls > 0 else self.nx * self.ny
         z = np.empty(3 * nl)
         dz = np.empty(nl)
-        lib().orc_get_z(self._h, level, _dp(z), _dp(dz))
+        self._L.orc_get_z(self._h, level, _dp(z), _dp(dz))
         return z.reshape(3, nl), dz
 
 

@@ -394,9 +394,41 @@ def hll(hL, unL, utL, hR, unR, utR, g, hd):
     return F
 
 
-def operator(w, ze, t, Q, P: Grid):
+def drain_limit(F, don, act, dt, dx, g, hd):
+    """Outflow limited by content (the C oracle's drain_limit): where act (the
+    donor, the side the mass leaves, is a leaf and F[0] != 0) the mass flux is
+    limited to |F[0]| dt <= s_f h0 dx with the donor's share
+    s_f = e_f / (e_E + e_W + e_N + e_S), e_f = max(0, outward average
+    velocity) + sqrt(g h0), and the momentum components are scaled by the
+    same factor; a donor without content passes nothing.  F in (h, qx, qy)
+    order along +x or +y; don = the donor's flux-view averages (h0, q_n0,
+    q_t0)."""
+    h0 = don[0]
+    zero = torch.zeros_like(h0)
+    pos = h0 > 0.0
+    wet = h0 > hd
+    hh = _safe(wet, h0)
+    un = _w(wet, don[1] / hh, zero)
+    ut = _w(wet, don[2] / hh, zero)
+    c = _Sqrt.apply(g * _safe(pos, h0))
+    out = _w(F[0] > 0.0, un, -un)
+    e = _w(out > 0.0, out, zero) + c
+    S = (un.abs() + ut.abs()) + 4.0 * c
+    cap = (h0 * dx / dt) * (e / S)
+    a = F[0].abs()
+    kill = act & ~pos
+    bite = act & pos & (a > cap)
+    th = cap / _safe(bite, a)
+    F0 = _w(bite, _w(F[0] > 0.0, cap, -cap), F[0])
+    out_F = [F0, _w(bite, F[1] * th, F[1]), _w(bite, F[2] * th, F[2])]
+    return [_w(kill, zero, q) for q in out_F]
+
+
+def operator(w, ze, t, Q, P: Grid, dt=0.0):
     """DG2 spatial operator of every cell (Eq. 4) from the flux view w (9) and
-    its beds ze (3); returns the nine operator components."""
+    its beds ze (3); returns the nine operator components.  With dt > 0 the
+    interface fluxes carry the outflow limit of a forward-Euler stage of that
+    length."""
     g, hd, dx = P.g, P.hd, P.dx
     lim = [[face_lim(w[3 * v], w[3 * v + 1], w[3 * v + 2], f) for v in range(3)] +
            [face_lim(ze[0], ze[1], ze[2], f)] for f in range(4)]
@@ -420,6 +452,32 @@ def operator(w, ze, t, Q, P: Grid):
     H = hll(rB[0], rB[2], rB[1], rT[0], rT[2], rT[1], g, hd)
     Fy = [H[0], H[2], H[1]]
 
+    if dt > 0.0:
+        # x interfaces (ny, nx + 1): left cell i - 1, right cell i; y
+        # interfaces (ny + 1, nx): below j - 1, above j; boundary ghosts are
+        # never limited donors
+        ny, nx = w[0].shape
+        col = torch.arange(nx + 1).view(1, nx + 1).expand(ny, nx + 1)
+        row = torch.arange(ny + 1).view(ny + 1, 1).expand(ny + 1, nx)
+        for xdir in (True, False):
+            Fi = Fx if xdir else Fy
+            mn, mt = (3, 6) if xdir else (6, 3)
+            if xdir:
+                lo = [torch.cat([w[m][:, :1], w[m]], dim=1) for m in (0, mn, mt)]
+                hi = [torch.cat([w[m], w[m][:, -1:]], dim=1) for m in (0, mn, mt)]
+                lo_ok, hi_ok = col >= 1, col <= nx - 1
+            else:
+                lo = [torch.cat([w[m][:1, :], w[m]], dim=0) for m in (0, mn, mt)]
+                hi = [torch.cat([w[m], w[m][-1:, :]], dim=0) for m in (0, mn, mt)]
+                lo_ok, hi_ok = row >= 1, row <= ny - 1
+            fwd = Fi[0] > 0.0
+            don = [_w(fwd, lo[q], hi[q]) for q in range(3)]
+            act = (Fi[0] != 0.0) & torch.where(fwd, lo_ok, hi_ok)
+            Fl = drain_limit(Fi, don, act, dt, dx, g, hd)
+            if xdir:
+                Fx = Fl
+            else:
+                Fy = Fl
     Fh = [[Fx[v][:, 1:] for v in range(3)], [Fx[v][:, :-1] for v in range(3)],
           [Fy[v][1:, :] for v in range(3)], [Fy[v][:-1, :] for v in range(3)]]
     own = [[r[:, 1:] for r in rL], [r[:, :-1] for r in rR], [r[1:, :] for r in rB], [r[:-1, :] for r in rT]]
@@ -467,10 +525,10 @@ def step(U, z, nman, Q, dt, t, P: Grid):
     rain = P.rain_rate if t < P.rain_t_end else 0.0
     Un = friction(U, nman, dt, rain, P)
     w1, f1, z1 = limit(Un, z, P)
-    L1 = operator(f1, z1, t, Q, P)
+    L1 = operator(f1, z1, t, Q, P, dt)
     Ui = post([w1[m] + dt * L1[m] for m in range(9)], P.hd)
     w2, f2, z2 = limit(Ui, z, P)
-    L2 = operator(f2, z2, t + dt, Q, P)
+    L2 = operator(f2, z2, t + dt, Q, P, dt)
     return post([0.5 * (w1[m] + w2[m] + dt * L2[m]) for m in range(9)], P.hd)
 
 

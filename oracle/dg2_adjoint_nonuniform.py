@@ -44,7 +44,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from .dg2_adjoint import (F64, S3, WALL, OPEN, _Cbrt, _TieMax, _safe, _shift, _w, face_lim, friction,
+from .dg2_adjoint import (F64, S3, WALL, OPEN, _Cbrt, _TieMax, _safe, _shift, _w, drain_limit, face_lim, friction,
                           hll, inflow_Q, limit, post, project, revise)
 
 HALF_S3 = 0.5 * S3
@@ -257,9 +257,13 @@ def build_views(Wf, Zf, G: LeafGrid):
     return V
 
 
-def operator(Wf, Zf, t, Q, G: LeafGrid):
+def operator(Wf, Zf, t, Q, G: LeafGrid, dt=0.0):
     """DG2 operator of every leaf (Eq. 4) from the flux views Wf[l] (9) and
-    beds Zf[l] (3) of every level; returns the nine components per level."""
+    beds Zf[l] (3) of every level; returns the nine components per level.
+    With dt > 0 each side's interface flux carries the outflow limit of a
+    forward-Euler stage of that length (the donor is the own leaf or the
+    neighbour's view, whose averages are those of the view's planes or, on a
+    static grid's coarse side, the mean of the two finer leaves')."""
     g, hd = G.g, G.hd
     V = build_views(Wf, Zf, G)
     Lout = [None] * (G.L + 1)
@@ -277,12 +281,17 @@ def operator(Wf, Zf, t, Q, G: LeafGrid):
             # coarser leaves; on static grids a refined node's is the mean of
             # its two children on the face
             view = _limits(V[l][:9], V[l][9:], fo)
+            vavg = [V[l][3 * v] for v in range(3)]
             if G.mode == "static" and l + 1 <= G.L:
                 c1, c2 = _PAIR[f]
                 fine = _limits(V[l + 1][:9], V[l + 1][9:], fo)
                 avg = [0.5 * (_children(q)[c1] + _children(q)[c2]) for q in fine]
                 view = [_w(G.sig[l], avg[q], view[q]) for q in range(4)]
+                favg = [0.5 * (_children(V[l + 1][3 * v])[c1] + _children(V[l + 1][3 * v])[c2])
+                        for v in range(3)]
+                vavg = [_w(G.sig[l], favg[v], vavg[v]) for v in range(3)]
             nb = [_shift(q, axis, step) for q in view]
+            nbavg = [_shift(q, axis, step) for q in vavg]
             gh = _ghost(own[f], f, l, Q, t, G)
             ins = _inside(G, l, f)
             nb = [_w(ins, nb[q], gh[q]) for q in range(4)]
@@ -299,6 +308,15 @@ def operator(Wf, Zf, t, Q, G: LeafGrid):
             else:
                 H = hll(rn[0], rn[2], rn[1], ro[0], ro[2], ro[1], g, hd)
                 Fh[f] = [H[0], H[2], H[1]]
+            if dt > 0.0:
+                own_first = f in (0, 2)
+                from_own = (Fh[f][0] > 0.0) if own_first else (Fh[f][0] < 0.0)
+                mn, mt = (3, 6) if f < 2 else (6, 3)
+                d_own = [Wf[l][0], Wf[l][mn], Wf[l][mt]]
+                d_nb = [nbavg[0], nbavg[mn // 3], nbavg[mt // 3]]
+                don = [_w(from_own, d_own[q], d_nb[q]) for q in range(3)]
+                act = (Fh[f][0] != 0.0) & (from_own | ins)
+                Fh[f] = drain_limit(Fh[f], don, act, dt, dxl, g, hd)
             hs[f], us[f], vs[f], zr[f] = ro
         Fxp, Gyp = [], []
         for a in range(2):
@@ -350,11 +368,11 @@ def step(U, z, nman, Q, dt, t, G: LeafGrid):
     levels = range(G.L + 1)
     Un = [friction(U[l], nman[l], dt, rain, G) for l in levels]
     s1 = [limit(Un[l], z[l], G, nbmask=G.leaf[l]) for l in levels]
-    L1 = operator([s[1] for s in s1], [s[2] for s in s1], t, Q, G)
+    L1 = operator([s[1] for s in s1], [s[2] for s in s1], t, Q, G, dt)
     Ui = _mask([post([s1[l][0][m] + dt * L1[l][m] for m in range(9)], G.hd) if L1[l] is not None
                 else s1[l][0] for l in levels], G)
     s2 = [limit(Ui[l], z[l], G, nbmask=G.leaf[l]) for l in levels]
-    L2 = operator([s[1] for s in s2], [s[2] for s in s2], t + dt, Q, G)
+    L2 = operator([s[1] for s in s2], [s[2] for s in s2], t + dt, Q, G, dt)
     return _mask([post([0.5 * (s1[l][0][m] + s2[l][0][m] + dt * L2[l][m]) for m in range(9)], G.hd)
                   if L2[l] is not None else s1[l][0] for l in levels], G)
 

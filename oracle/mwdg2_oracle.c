@@ -23,7 +23,11 @@
  *                           finer elements at non-homogeneous interfaces)
  * The paper delegates the DG2 operator details (HLL, wet/dry revisions,
  * friction, limiter, filter entries) to cited works; the readings used here
- * are listed beside each function.  Friction is pinned by the exact decay
+ * are listed beside each function.  The wet/dry treatment keeps depths
+ * non-negative, as Sect. 2.1.1 states it does, by limiting each interface's
+ * outflow to the donor leaf's share of its content (drain_limit); pinned by
+ * non-negative depths and a closed mass budget on the rapid-flow valley and
+ * a dam break over a steep dry slope, and by a mound drained in one stage.  Friction is pinned by the exact decay
  * of a uniform flow and the limiter by hand-evaluated minmod cases.  The
  * non-homogeneous interface rule is pinned on planar data, where each
  * leaf's stage equals the uniform grid's of the leaf's level (views of a
@@ -1102,9 +1106,11 @@ static void build_view(orc_sim *s, double **X, double **Z) {
   }
 }
 
-/* neighbour limit (h, qx, qy, z) across face f of leaf (l,i,j); returns 0
- * when the face is on the domain boundary */
-static int nbr_limit(const orc_sim *s, int l, int i, int j, int f, double out[4]) {
+/* neighbour limit (h, qx, qy, z) across face f of leaf (l,i,j) and the
+ * averages (h0, qx0, qy0) of the view it comes from (the mean of the two
+ * finer leaves' averages on the coarse side of a static grid's face);
+ * returns 0 when the face is on the domain boundary */
+static int nbr_limit(const orc_sim *s, int l, int i, int j, int f, double out[4], double avg[3]) {
   static const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
   int a = i + di[f], b = j + dj[f];
   if (!in_dom(s, l, a, b)) return 0;
@@ -1129,6 +1135,7 @@ static int nbr_limit(const orc_sim *s, int l, int i, int j, int f, double out[4]
         p2[m] = s->V[l + 1][(3 * v + m) * nf + k2];
       }
       out[v] = 0.5 * (face_lim(p1, fo) + face_lim(p2, fo));
+      avg[v] = 0.5 * (p1[0] + p2[0]);
     }
     double z1[3], z2[3];
     for (int m = 0; m < 3; m++) {
@@ -1142,6 +1149,7 @@ static int nbr_limit(const orc_sim *s, int l, int i, int j, int f, double out[4]
     double p[3];
     for (int m = 0; m < 3; m++) p[m] = s->V[l][(3 * v + m) * n + k];
     out[v] = face_lim(p, f ^ 1);
+    avg[v] = p[0];
   }
   double zp[3];
   for (int m = 0; m < 3; m++) zp[m] = s->Vz[l][m * n + k];
@@ -1174,21 +1182,67 @@ static void ghost_limit(const orc_sim *s, int l, int i, int j, int f, const doub
   else { out[1] = own[1]; out[2] = -own[2]; }
 }
 
+/* Outflow limited by content (Sect. 2.1.1 states that the wet/dry treatment
+ * keeps depths non-negative; the revisions alone do not where a thin leaf's
+ * interface limits carry large velocities).  Reading: a leaf's content
+ * h0 dx^2 is split among its four interfaces, and the volume that leaves
+ * through interface f during a forward-Euler stage is limited to its share
+ * s_f h0 dx^2, so that the average stays non-negative whatever the other
+ * interfaces do (the draining time step of Bollermann, Chen, Kurganov &
+ * Noelle 2013, with the donor's content divided among its interfaces so
+ * that each interface is limited on its own).  The shares follow the
+ * donor's average flow: s_f = e_f / (e_E + e_W + e_N + e_S) with
+ * e_f = max(0, outward average velocity through f) + sqrt(g h0), so a
+ * leaf's content goes mostly to the interfaces it flows towards and a leaf
+ * at rest splits it evenly.  The mass flux F[0] (per unit length, along +x
+ * or +y) is limited to |F[0]| dt <= s_f h0 dx, and the momentum components
+ * are scaled by the same factor.  don = the donor's (the side the mass
+ * leaves) flux-view averages (h0, q_n0 normal to the interface along +x or
+ * +y, q_t0); F[0] > 0 means the donor is the west or south side.  Both sides
+ * of an interface between two leaves of one level evaluate it from the same
+ * operands, so the flux stays conservative there. */
+static void drain_limit(double F[3], const double don[3], double g, double hd, double dx, double dt) {
+  double h0 = don[0];
+  if (!(h0 > 0.0)) {
+    F[0] = F[1] = F[2] = 0.0;
+    return;
+  }
+  double un = 0.0, ut = 0.0;
+  if (h0 > hd) {
+    un = don[1] / h0;
+    ut = don[2] / h0;
+  }
+  double c = sqrt(g * h0);
+  double out = F[0] > 0.0 ? un : -un;
+  double e = fmax(out, 0.0) + c;
+  double S = (fabs(un) + fabs(ut)) + 4.0 * c;
+  double cap = (h0 * dx / dt) * (e / S);
+  double a = fabs(F[0]);
+  if (a > cap) {
+    double th = cap / a;
+    F[0] = F[0] > 0.0 ? cap : -cap;
+    F[1] = F[1] * th;
+    F[2] = F[2] * th;
+  }
+}
+
 /* Numerical flux through face f of leaf (l, i, j) with flux-view
  * coefficients w and beds zc: own interface limit and the neighbour's (same-
  * level view or boundary ghost), both revised, HLL in (h, qx, qy) order,
- * oriented along +x (E, W) or +y (N, S).  The own revised limit goes to
- * hs, us, vs, zr; returns 1 inside the domain, 0 on the boundary. */
+ * oriented along +x (E, W) or +y (N, S), then (DG2, stage step dt > 0) the
+ * outflow limit of the donor side; a boundary ghost is never a donor that is
+ * limited.  The own revised limit goes to hs, us, vs, zr; returns 1 inside
+ * the domain, 0 on the boundary. */
 static int face_flux(const orc_sim *s, int l, int i, int j, const double *w, const double *zc, int f,
-                     double t, double F[3], double *hs, double *us, double *vs, double *zr) {
+                     double t, double dt, double F[3], double *hs, double *us, double *vs, double *zr) {
   double g = s->p.g, hd = s->p.h_dry;
   double own[4];
   own[0] = face_lim(w + 0, f);
   own[1] = face_lim(w + 3, f);
   own[2] = face_lim(w + 6, f);
   own[3] = face_lim(zc, f);
-  double nb[4];
-  int inside = nbr_limit(s, l, i, j, f, nb);
+  double nb[4], nbavg[3];
+  int inside = nbr_limit(s, l, i, j, f, nb, nbavg);
   if (!inside) ghost_limit(s, l, i, j, f, own, t, nb);
   double zf = fmax(own[3], nb[3]);
   double hn, un, vn, zn;
@@ -1208,6 +1262,22 @@ static int face_flux(const orc_sim *s, int l, int i, int j, const double *w, con
     hll(hn, vn, un, *hs, *vs, *us, g, hd, H);
     F[0] = H[0]; F[1] = H[2]; F[2] = H[1];
   }
+  if (dt > 0.0 && F[0] != 0.0) {
+    /* the donor: own side when the mass leaves it (own is the west side of
+     * an E face and the south side of an N face); a boundary ghost is never
+     * limited */
+    int own_first = (f == 0 || f == 2);
+    int from_own = own_first ? (F[0] > 0.0) : (F[0] < 0.0);
+    int xf = f < 2;
+    double don[3];
+    if (from_own) {
+      don[0] = w[0]; don[1] = xf ? w[3] : w[6]; don[2] = xf ? w[6] : w[3];
+      drain_limit(F, don, g, hd, s->dx[l], dt);
+    } else if (inside) {
+      don[0] = nbavg[0]; don[1] = xf ? nbavg[1] : nbavg[2]; don[2] = xf ? nbavg[2] : nbavg[1];
+      drain_limit(F, don, g, hd, s->dx[l], dt);
+    }
+  }
   return inside;
 }
 
@@ -1215,7 +1285,7 @@ static int face_flux(const orc_sim *s, int l, int i, int j, const double *w, con
  * is refined): the flux is the mean of the two fine leaves' own fluxes
  * through their halves of the face, computed as they compute them, so the
  * mass leaving one side enters the other. */
-static int reflux_face(const orc_sim *s, int l, int i, int j, int f, double t, double F[3]) {
+static int reflux_face(const orc_sim *s, int l, int i, int j, int f, double t, double dt, double F[3]) {
   static const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
   if (s->p.mode != ORC_STATIC || s->p.iface_rule != 1) return 0;
   int a = i + di[f], b = j + dj[f];
@@ -1234,7 +1304,7 @@ static int reflux_face(const orc_sim *s, int l, int i, int j, int f, double t, d
     double wc[9], zcc[3], hs, us, vs, zr;
     get9(s->F, s, l + 1, kc, wc);
     for (int m = 0; m < 3; m++) zcc[m] = s->Ze[l + 1][m * nf + kc];
-    face_flux(s, l + 1, ic, jc, wc, zcc, f ^ 1, t, Fc[q], &hs, &us, &vs, &zr);
+    face_flux(s, l + 1, ic, jc, wc, zcc, f ^ 1, t, dt, Fc[q], &hs, &us, &vs, &zr);
   }
   for (int v = 0; v < 3; v++) F[v] = 0.5 * (Fc[0][v] + Fc[1][v]);
   return 1;
@@ -1249,16 +1319,16 @@ static int reflux_face(const orc_sim *s, int l, int i, int j, int f, double t, d
  * S1 = -(2 sqrt3 g / dx) h1 (h1 + z1).  Returns the outward boundary mass
  * flux (m^3/s) in *bnd_out. */
 static void leaf_operator(const orc_sim *s, int l, int i, int j, const double *w, const double *zc,
-                          double t, double *Lo, double *bnd_out) {
+                          double t, double dt, double *Lo, double *bnd_out) {
   double g = s->p.g, s3 = S3();
   double dxl = s->dx[l];
   double Fh[4][3];                 /* numerical flux per face in (h,qx,qy) */
   double hs[4], us[4], vs[4], zr[4]; /* own revised limits */
   double bout = 0.0;
   for (int f = 0; f < 4; f++) {
-    int inside = face_flux(s, l, i, j, w, zc, f, t, Fh[f], &hs[f], &us[f], &vs[f], &zr[f]);
+    int inside = face_flux(s, l, i, j, w, zc, f, t, dt, Fh[f], &hs[f], &us[f], &vs[f], &zr[f]);
     double Fr[3];
-    if (inside && reflux_face(s, l, i, j, f, t, Fr))
+    if (inside && reflux_face(s, l, i, j, f, t, dt, Fr))
       for (int v = 0; v < 3; v++) Fh[f][v] = Fr[v];
     if (!inside) {
       double outward = (f == 0 || f == 2) ? Fh[f][0] : -Fh[f][0];
@@ -1324,7 +1394,7 @@ static double rk_stage(orc_sim *s, double **Xin, double **Wout, double **Wcomb, 
         get9(Wout, s, l, k, w);
         get9(s->F, s, l, k, wf);
         for (int m = 0; m < 3; m++) zc[m] = s->Ze[l][m * nn(s, l) + k];
-        leaf_operator(s, l, i, j, wf, zc, t_force, Lo, &b);
+        leaf_operator(s, l, i, j, wf, zc, t_force, dt, Lo, &b);
         bnd += b;
         if (!Wcomb) {
           for (int m = 0; m < 9; m++) o[m] = w[m] + dt * Lo[m];

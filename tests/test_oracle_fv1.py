@@ -81,7 +81,8 @@ def test_fv1_volume_and_mass_budget():
     v0 = s.diag()["volume"]
     s.run_to(120.0)
     d = s.diag()
-    budget = v0 + d["v_in"] - d["v_out"] + d["v_rain"] + d["v_clip"]
+    assert d["n_clip"] == 0 and d["v_clip"] == 0.0
+    budget = v0 + d["v_in"] - d["v_out"] + d["v_rain"]
     assert abs(d["volume"] - budget) <= 1e-12 * max(1.0, d["volume"])
     assert d["v_in"] > 0 and d["v_rain"] > 0
 

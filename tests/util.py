@@ -63,3 +63,21 @@ def stoker_depth(x, t, x0, hL, hR, g):
     h = np.where(xi <= -cL, hL, (2.0 * cL - xi) ** 2 / (9.0 * g))
     h = np.where(xi >= 2.0 * cL - 3.0 * cm, hm, h)
     return np.where(xi >= S, hR, h)
+
+
+def oracle_variant(tmp_path, edits):
+    """A scratch copy of the oracle with text edits applied (a planted change
+    whose effect a test checks), compiled like the oracle and typed by
+    ``oracle.load``; every edit must match the source exactly once or more."""
+    import subprocess
+    from pathlib import Path
+    src = (Path(O.__file__).resolve().parent / "mwdg2_oracle.c").read_text()
+    for old, new in edits:
+        assert old in src, old
+        src = src.replace(old, new)
+    c = tmp_path / "variant.c"
+    c.write_text(src)
+    so = tmp_path / "libvariant.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-shared", "-fPIC",
+                    str(c), "-o", str(so), "-lm"], check=True)
+    return O.load(so)
