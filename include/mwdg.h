@@ -164,6 +164,14 @@ MWDG_API mwdg_status mwdg_mra_adapt(mwdg_ctx *ctx, double eps, int64_t *n_active
  * the step's dt. */
 MWDG_API mwdg_status mwdg_dg2_step(mwdg_ctx *ctx, double *dt_out);
 
+/* One time step of the prescribed length dt (> 0, finite) instead of the
+ * CFL step: otherwise exactly mwdg_dg2_step (Sect. 2.1.1, Eq. 4).  The paper
+ * steps at the Courant number; a prescribed step serves comparisons of two
+ * runs on one step sequence (the FP32 path on the FP64 path's steps) and
+ * coupling to a caller's clock.  dt is not checked against the CFL
+ * condition.  Queued without host synchronisation. */
+MWDG_API mwdg_status mwdg_dg2_step_dt(mwdg_ctx *ctx, double dt);
+
 /* nsteps steps queued without any host synchronisation. */
 MWDG_API mwdg_status mwdg_run_steps(mwdg_ctx *ctx, int64_t nsteps);
 
@@ -240,12 +248,19 @@ MWDG_API mwdg_status mwdg_launch_count(mwdg_ctx *ctx, int64_t *n);
  * all queued on cuda_stream.  It allocates nothing: its per-block partial
  * sums live in a fixed file-scope device array (128 KB, held by every GPU
  * that loads the library until the process exits).  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) and
- * should come before any stream capture on that device.  Calls share the
- * array: calls whose work overlaps on the GPU race.  Errors: MWDG_ERR_ARG
- * (NULL pointer with n > 0, dx <= 0, L outside 0..MWDG_LMAX, n < 0),
- * MWDG_ERR_CAPACITY when n exceeds MWDG_VOLUME_NOALLOC_MAX, MWDG_ERR_CUDA
- * when the address lookup or a launch fails. */
+ * device looks up that array's device address (cudaGetSymbolAddress); with
+ * lazy module loading that is also when the array is committed, so the
+ * first call must come before the host hands all device memory to its own
+ * pool (an n = 0 call at start-up does it).  Calls share the array: calls
+ * whose work overlaps on the GPU race.  Every level must lie in 0..L: the
+ * call waits for its own work on cuda_stream to check that, and a level
+ * outside it makes the call return MWDG_ERR_ARG with *volume set to NaN.
+ * Errors: MWDG_ERR_ARG (NULL pointer with n > 0, dx <= 0, L outside
+ * 0..MWDG_LMAX, n < 0, a level outside 0..L), MWDG_ERR_CAPACITY when n
+ * exceeds MWDG_VOLUME_NOALLOC_MAX, MWDG_ERR_CUDA when the address lookup or
+ * one of its launches fails, or when a CUDA error from earlier work is
+ * pending at entry (that error is not cleared, so its owner still sees
+ * it). */
 #define MWDG_VOLUME_NOALLOC_MAX 67108864LL
 MWDG_API mwdg_status mwdg_volume_noalloc(const double *h0, const int32_t *level, int64_t n, double dx,
                                          int32_t L, double *volume, void *cuda_stream);

@@ -18,7 +18,7 @@ WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 EXPORTS = (
     "mwdg_params_default", "mwdg_create", "mwdg_destroy", "mwdg_load_dem", "mwdg_load_roughness",
     "mwdg_set_roughness_scalar", "mwdg_load_initial", "mwdg_set_inflow", "mwdg_set_rain",
-    "mwdg_mra_encode", "mwdg_mra_adapt", "mwdg_dg2_step", "mwdg_run_steps", "mwdg_run_to_time",
+    "mwdg_mra_encode", "mwdg_mra_adapt", "mwdg_dg2_step", "mwdg_dg2_step_dt", "mwdg_run_steps", "mwdg_run_to_time",
     "mwdg_read_fields", "mwdg_read_fields_dev", "mwdg_read_active", "mwdg_get_time",
     "mwdg_get_volume", "mwdg_profile", "mwdg_kernel_times", "mwdg_launch_count",
     "mwdg_last_error", "mwdg_status_string", "mwdg_state_bytes", "mwdg_save_state",
@@ -71,6 +71,7 @@ def lib(build: bool = True):
         "mwdg_mra_encode": [vp],
         "mwdg_mra_adapt": [vp, C.c_double, lp],
         "mwdg_dg2_step": [vp, dp],
+        "mwdg_dg2_step_dt": [vp, C.c_double],
         "mwdg_run_steps": [vp, C.c_int64],
         "mwdg_run_to_time": [vp, C.c_double, lp],
         "mwdg_read_fields": [vp, dp, dp, dp],
@@ -210,6 +211,10 @@ class Solver:
         dt = C.c_double()
         self._ck(self._lib.mwdg_dg2_step(self._h, C.byref(dt)), "mwdg_dg2_step")
         return dt.value
+
+    def dg2_step_dt(self, dt):
+        """one step of the prescribed length dt (no CFL condition)"""
+        self._ck(self._lib.mwdg_dg2_step_dt(self._h, float(dt)), "mwdg_dg2_step_dt")
 
     def run_steps(self, n):
         self._ck(self._lib.mwdg_run_steps(self._h, int(n)), "mwdg_run_steps")

@@ -155,6 +155,43 @@ __device__ __forceinline__ void hll(T hL, T unL, T utL, T hR, T unR, T utR, T g,
   }
 }
 
+// Outflow limited by content (Sect. 2.1.1: the wet/dry treatment keeps
+// depths non-negative).  The donor leaf's content h0 dx^2 is split among its
+// four interfaces in proportion to e_f = max(0, outward average velocity
+// through f) + sqrt(g h0), and the volume that leaves through one interface
+// during a forward-Euler stage of length dt is limited to its share: the
+// draining time step of Bollermann, Chen, Kurganov & Noelle (2013), applied
+// per interface so that both sides of an interface evaluate the same limit.
+// F (per unit length, along +x or +y; F0 > 0 means the donor is the west or
+// south side) is scaled as a whole so that |F0| dt <= share * h0 dx.  The
+// donor is given by its flux-view averages: depth h0, discharge qn normal to
+// the interface (along +x or +y) and qt along it.  A donor without content
+// passes nothing.
+template <typename T>
+__device__ __forceinline__ void drain_limit(T &F0, T &F1, T &F2, T h0, T qn, T qt, T g, T hd, T dx, T dt) {
+  if (!(h0 > T(0))) {
+    F0 = F1 = F2 = T(0);
+    return;
+  }
+  T un = T(0), ut = T(0);
+  if (h0 > hd) {
+    un = qn / h0;
+    ut = qt / h0;
+  }
+  const T c = tsqrt(g * h0);
+  const T out = F0 > T(0) ? un : -un;
+  const T e = tmax(out, T(0)) + c;
+  const T S = (tabs(un) + tabs(ut)) + T(4) * c;
+  const T cap = (h0 * dx / dt) * (e / S);
+  const T a = tabs(F0);
+  if (a > cap) {
+    const T th = cap / a;
+    F0 = F0 > T(0) ? cap : -cap;
+    F1 = F1 * th;
+    F2 = F2 * th;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T minmod2(T a, T b) {
   if (a > T(0) && b > T(0)) return tmin(a, b);

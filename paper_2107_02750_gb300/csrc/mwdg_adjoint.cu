@@ -433,14 +433,21 @@ __global__ void __launch_bounds__(UT * UT) k_update(Par<T> P, int stage, const T
     const T zf = tmax(lo.z, hi.z);
     const Side<T> sl = revise_h(lo.h, lo.qx, lo.qy, lo.z, zf, P.hd);
     const Side<T> sh = revise_h(hi.h, hi.qx, hi.qy, hi.z, zf, P.hd);
-    T H[3];
+    T H[3], F0, F1, F2;
     if (xf) {
       hll(sl.hs, sl.u, sl.v, sh.hs, sh.u, sh.v, P.g, P.hd, H);
-      sF[q][0] = H[0]; sF[q][1] = H[1]; sF[q][2] = H[2];
+      F0 = H[0]; F1 = H[1]; F2 = H[2];
     } else {
       hll(sl.hs, sl.v, sl.u, sh.hs, sh.v, sh.u, P.g, P.hd, H);
-      sF[q][0] = H[0]; sF[q][1] = H[2]; sF[q][2] = H[1];
+      F0 = H[0]; F1 = H[2]; F2 = H[1];
     }
+    // outflow limit of the donor cell (never a boundary ghost)
+    const long long kd = F0 > T(0) ? (hasLo ? kLo : -1) : (F0 < T(0) && hasHi ? kHi : -1);
+    if (kd >= 0) {
+      const T qx0 = Wfx[3 * n + kd], qy0 = Wfx[6 * n + kd];
+      drain_limit(F0, F1, F2, Wfx[kd], xf ? qx0 : qy0, xf ? qy0 : qx0, P.g, P.hd, P.dx, (T)dts[step]);
+    }
+    sF[q][0] = F0; sF[q][1] = F1; sF[q][2] = F2;
     sR[q][0] = sl.hs; sR[q][1] = sl.u; sR[q][2] = sl.v; sR[q][3] = sl.zr;
     sR[q][4] = sh.hs; sR[q][5] = sh.u; sR[q][6] = sh.v; sR[q][7] = sh.zr;
   }
@@ -808,11 +815,66 @@ __device__ double ghost_rev(const Par<T> &P, int e, int along, const Lim<T> &o, 
   return 0.0;
 }
 
+// reverse of drain_limit(): from the cotangent lG of the limited flux, the
+// cotangent of the flux it limited (lF) and of the donor's averages (h0,
+// q_n0, q_t0) in ld; F is the flux before the limit
+template <typename T>
+__device__ void drain_rev(const T F[3], T h0, T qn, T qt, T g, T hd, T dx, T dt, const T lG[3], T lF[3],
+                          T ld[3]) {
+  ld[0] = ld[1] = ld[2] = T(0);
+  if (!(h0 > T(0))) {  // a donor without content passes nothing
+    lF[0] = lF[1] = lF[2] = T(0);
+    return;
+  }
+  T un = T(0), ut = T(0);
+  const bool wet = h0 > hd;
+  if (wet) {
+    un = qn / h0;
+    ut = qt / h0;
+  }
+  const T c = tsqrt(g * h0);
+  const bool fwd = F[0] > T(0);
+  const T out = fwd ? un : -un;
+  const T e = tmax(out, T(0)) + c;
+  const T S = (tabs(un) + tabs(ut)) + T(4) * c;
+  const T R = h0 * dx / dt, Q = e / S;
+  const T cap = R * Q;
+  const T a = tabs(F[0]);
+  if (!(a > cap)) {
+    lF[0] = lG[0]; lF[1] = lG[1]; lF[2] = lG[2];
+    return;
+  }
+  const T th = cap / a;
+  const T sg = fwd ? T(1) : T(-1);
+  T lcap = sg * lG[0];
+  lF[1] = lG[1] * th;
+  lF[2] = lG[2] * th;
+  const T lth = lG[1] * F[1] + lG[2] * F[2];
+  lcap += lth / a;
+  lF[0] = -lth * th / a * sg;
+  const T lR = lcap * Q, lQ = lcap * R;
+  T lh0 = lR * dx / dt;
+  const T le = lQ / S, lS = -lQ * Q / S;
+  T lun = lS * (un > T(0) ? T(1) : un < T(0) ? T(-1) : T(0));
+  const T lut = lS * (ut > T(0) ? T(1) : ut < T(0) ? T(-1) : T(0));
+  T lc = T(4) * lS + le;
+  if (out > T(0)) lun += fwd ? le : -le;
+  lh0 += lc * g * T(0.5) / c;
+  if (wet) {
+    ld[1] = lun / h0;
+    ld[2] = lut / h0;
+    lh0 -= (lun * qn + lut * qt) / (h0 * h0);
+  }
+  ld[0] = lh0;
+}
+
 // Per interface: the flux cotangent from both cells, HLL and the two
 // revisions in reverse, the interface bed split, the ghost folded into the
 // boundary cell.  Output per face: the cotangents of the low side's limit
-// (slots 0-3: h, qx, qy, z) and the high side's (slots 4-7); `lq`, per
-// boundary cell of the inflow edge, the cotangent of Q(t).
+// (slots 0-3: h, qx, qy, z) and the high side's (slots 4-7), and those of the
+// flux-view averages (h0, qx0, qy0) of the low (slots 8-10) and high (slots
+// 11-13) cell through the outflow limit (non-zero for its donor only); `lq`,
+// per boundary cell of the inflow edge, the cotangent of Q(t).
 template <typename T, bool XF>
 __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const double *dts, const double *tt, int step,
                                                   const T *Wfx, const T *Zfx, const T *lY, const T *Y,
@@ -858,6 +920,28 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
     cell_face_cot(P, fHi, lL, sHi, opp, f3, cHi);
     lF[0] += f3[0]; lF[1] += f3[1]; lF[2] += f3[2];
   }
+  // the outflow limit in reverse: the flux before it and the donor's averages
+  T dLo[3] = {T(0), T(0), T(0)}, dHi[3] = {T(0), T(0), T(0)};
+  {
+    T H[3], F[3];
+    if (XF) {
+      hll(sLo.hs, sLo.u, sLo.v, sHi.hs, sHi.u, sHi.v, P.g, P.hd, H);
+      F[0] = H[0]; F[1] = H[1]; F[2] = H[2];
+    } else {
+      hll(sLo.hs, sLo.v, sLo.u, sHi.hs, sHi.v, sHi.u, P.g, P.hd, H);
+      F[0] = H[0]; F[1] = H[2]; F[2] = H[1];
+    }
+    const long long kd = F[0] > T(0) ? (hasLo ? kLo : -1) : (F[0] < T(0) && hasHi ? kHi : -1);
+    if (kd >= 0) {
+      const T qx0 = Wfx[3 * n + kd], qy0 = Wfx[6 * n + kd];
+      T lG[3] = {lF[0], lF[1], lF[2]}, ld[3];
+      drain_rev(F, Wfx[kd], XF ? qx0 : qy0, XF ? qy0 : qx0, P.g, P.hd, P.dx, dt, lG, lF, ld);
+      T *dd = F[0] > T(0) ? dLo : dHi;  // the low side is the donor of an outflow along +x / +y
+      dd[0] = ld[0];
+      dd[1] = XF ? ld[1] : ld[2];
+      dd[2] = XF ? ld[2] : ld[1];
+    }
+  }
   T l6[6];
   if (XF) {
     hll_rev(sLo.hs, sLo.u, sLo.v, sHi.hs, sHi.u, sHi.v, P.g, P.hd, lF, l6);
@@ -898,6 +982,11 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
   for (int q = 0; q < 4; q++) {
     lim[q * nf + fi] = gLo[q];
     lim[(4 + q) * nf + fi] = gHi[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    lim[(8 + q) * nf + fi] = dLo[q];
+    lim[(11 + q) * nf + fi] = dHi[q];
   }
 }
 
@@ -971,6 +1060,12 @@ __global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, int stage, const do
     if (v < 3) { lw[3 * v] = a; lw[3 * v + 1] = bx; lw[3 * v + 2] = by; }
     else { lz[0] = a; lz[1] = bx; lz[2] = by; }
   }
+  // the averages' cotangents from the outflow limit of the four interfaces
+  // (this cell is the low side of E and N, the high side of W and S)
+#pragma unroll
+  for (int v = 0; v < 3; v++)
+    lw[3 * v] += ((limx[(8 + v) * nfx + fE] + limx[(11 + v) * nfx + fW]) + limy[(8 + v) * nfy + fN]) +
+                 limy[(11 + v) * nfy + fS];
   // the stage's output cotangent: the stored view's share (stage 2 also
   // passes half to the stage-1 view) and the slope bed sources
   // S1 = c2 h1 (h1 + z1) of the flux view
@@ -1456,8 +1551,8 @@ mwdg_status mwdg_adj_create(const mwdg_adj_params *p, mwdg_adj **out) {
   alloc(&a->Z2, SV * 3 * n, E);
   for (void **w : {&a->W1, &a->W2, &a->lU, &a->lX, &a->lW1, &a->lXo}) alloc(w, 9 * n, E);
   alloc(&a->lnb, 12 * n, E);
-  alloc(&a->limx, 8 * nfx, E);
-  alloc(&a->limy, 8 * nfy, E);
+  alloc(&a->limx, 14 * nfx, E);
+  alloc(&a->limy, 14 * nfy, E);
   alloc((void **)&a->lq, nedge, sizeof(double));
   if (ok) {
     const unsigned long long inf = 0x7ff0000000000000ull;

@@ -308,6 +308,7 @@ __global__ void k_fill_nm(T *nm, long long off, long long n, const double *src, 
 }
 
 __global__ void k_set_tend(Ctl *c, double t_end) { c->t_end = t_end; }
+__global__ void k_set_dt_fixed(Ctl *c, double dt) { c->dt_fixed = dt; }
 
 }  // namespace
 
@@ -653,6 +654,21 @@ mwdg_status mwdg_dg2_step(mwdg_ctx *c, double *dt_out) {
   return MWDG_OK;
 }
 
+mwdg_status mwdg_dg2_step_dt(mwdg_ctx *c, double dt) {
+  LIVE(c);
+  if (!c->initial) return fail(c, MWDG_ERR_STATE, "no initial state");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, MWDG_ERR_ARG, "dt must be positive and finite");
+  k_set_dt_fixed<<<1, 1, 0, c->st>>>(c->ctl, dt);
+  c->launches++;
+  mwdg_status s = queue_step(c);
+  // the prescribed step is withdrawn on every path
+  k_set_dt_fixed<<<1, 1, 0, c->st>>>(c->ctl, 0.0);
+  c->launches++;
+  if (s) return s;
+  CHECK_LAUNCH();
+  return MWDG_OK;
+}
+
 mwdg_status mwdg_run_steps(mwdg_ctx *c, int64_t nsteps) {
   LIVE(c);
   if (!c->initial) return fail(c, MWDG_ERR_STATE, "no initial state");
@@ -675,18 +691,20 @@ mwdg_status mwdg_run_to_time(mwdg_ctx *c, double t_end, int64_t *steps_out) {
   k_set_tend<<<1, 1, 0, c->st>>>(c->ctl, t_end);
   c->launches++;
   int batch = 8;
-  while (h.t < t_end) {
+  while (s == MWDG_OK && h.t < t_end) {
     const long long before = h.steps;
-    for (int k = 0; k < batch; k++)
-      if ((s = queue_step(c))) return s;
-    if ((s = read_ctl(c, &h))) return s;
-    if (h.steps == before) break;  // dt reached zero
+    for (int k = 0; k < batch && s == MWDG_OK; k++) s = queue_step(c);
+    if (s == MWDG_OK) s = read_ctl(c, &h);
+    if (s != MWDG_OK || h.steps == before) break;  // a failure, or dt reached zero
     // queue about as many steps as the last step length says are left
     double left = (h.dt > 0.0) ? (t_end - h.t) / h.dt : 1.0;
     batch = (int)std::max(1.0, std::min(256.0, std::ceil(left * 1.05) + 1.0));
   }
+  // the end time is withdrawn on every path, so that later steps are not
+  // clamped to it
   k_set_tend<<<1, 1, 0, c->st>>>(c->ctl, 1e300);
   c->launches++;
+  if (s) return s;
   CHECK_LAUNCH();
   if (steps_out) *steps_out = h.steps - start;
   return MWDG_OK;

@@ -30,6 +30,7 @@ struct Ctl {
   int rain_on;
   int pad_;
   double rain_inc;
+  double dt_fixed;             // > 0: the next steps take this dt instead of the CFL step
 };
 
 // Geometry and parameters of the level hierarchy (passed by value).

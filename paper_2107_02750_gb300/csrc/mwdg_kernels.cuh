@@ -458,6 +458,7 @@ __device__ __forceinline__ void begin_step(const Geo &g, Ctl *c, const int *nlea
   double best = __longlong_as_double((long long)c->dtmin);
   double dt = g.dt_max;
   if (best < __longlong_as_double(0x7ff0000000000000LL)) dt = fmin(dt, g.cfl * best);
+  if (c->dt_fixed > 0.0) dt = c->dt_fixed;  // a prescribed step (mwdg_dg2_step_dt)
   dt = fmin(dt, c->t_end - c->t);
   c->dt = dt > 0.0 ? dt : 0.0;
   c->dt_f = (float)c->dt;
@@ -1791,10 +1792,11 @@ __device__ __forceinline__ bool nbr_locate(const Geo &g, const Ptrs<T> &p, int l
 }
 
 // limit (first variable, qx, qy, z) of the same-level view of neighbour k
-// (kind kd) across face f of leaf (l, i, j)
+// (kind kd) across face f of leaf (l, i, j), then the view's averages (depth,
+// qx, qy): out[4..6]
 template <typename T>
 __device__ void nbr_view(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, long long k, uint8_t kd,
-                         T out[4]) {
+                         T out[7]) {
   const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
   const int fo = f ^ 1;
   if (kd == K_SIG && g.mode == MWDG_STATIC) {
@@ -1815,6 +1817,7 @@ __device__ void nbr_view(const Geo &g, const Ptrs<T> &p, int l, int i, int j, in
       out[v] = T(0.5) * (face_value(r1[3 * v], r1[3 * v + 1], r1[3 * v + 2], fo) +
                          face_value(r2[3 * v], r2[3 * v + 1], r2[3 * v + 2], fo));
     out[3] = T(0.5) * (face_value(r1[9], r1[10], r1[11], fo) + face_value(r2[9], r2[10], r2[11], fo));
+    for (int v = 0; v < 3; v++) out[4 + v] = T(0.5) * (r1[3 * v] + r2[3 * v]);
     return;
   }
   if (kd == K_BELOW) {
@@ -1841,6 +1844,7 @@ __device__ void nbr_view(const Geo &g, const Ptrs<T> &p, int l, int i, int j, in
         sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
       }
       out[v] = face_value(sv[0], sv[1], sv[2], fo);
+      if (v < 3) out[4 + v] = sv[0];
     }
     if (Form<T>::eta) out[0] = out[0] + out[3];  // depth + bed = free surface
     return;
@@ -1850,6 +1854,7 @@ __device__ void nbr_view(const Geo &g, const Ptrs<T> &p, int l, int i, int j, in
   out[0] = first_face(r[0], r[1], r[2], r[9], fo);
   for (int v = 1; v < 3; v++) out[v] = face_value(r[3 * v], r[3 * v + 1], r[3 * v + 2], fo);
   out[3] = face_value(r[9], r[10], r[11], fo);
+  for (int v = 0; v < 3; v++) out[4 + v] = r[3 * v];
 }
 
 // the same from the leaf's neighbour code (no kind reads, no walk)
@@ -1902,9 +1907,50 @@ __device__ void nbr_view_code(const Geo &g, const Ptrs<T> &p, int l, int i, int 
   out[3] = face_value(r[9], r[10], r[11], fo);
 }
 
-// both: the neighbour's view limit across face f; false on the boundary
+// the averages (depth, qx, qy) of the same view, evaluated only where the
+// neighbour is the donor of an interface's outflow limit: the leaf's or
+// encoded node's own, the prolonged plane's, or on a static grid's coarse
+// side the mean of the two finer leaves'
 template <typename T>
-__device__ __forceinline__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, T out[4]) {
+__device__ __forceinline__ void nbr_avg_code(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f,
+                                             long long code, T avg[3]) {
+  const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
+  const int type = nb_type(code);
+  const long long k = nb_node(code);
+  if (type == NB_REFINED && g.mode == MWDG_STATIC) {
+    int c1, c2;
+    if (f == 0) { c1 = 0; c2 = 2; }
+    else if (f == 1) { c1 = 1; c2 = 3; }
+    else if (f == 2) { c1 = 0; c2 = 1; }
+    else { c1 = 2; c2 = 3; }
+    const long long k1 = nid(g, l + 1, 2 * a + (c1 & 1), 2 * b + (c1 >> 1));
+    const long long k2 = nid(g, l + 1, 2 * a + (c2 & 1), 2 * b + (c2 >> 1));
+    for (int v = 0; v < 3; v++) avg[v] = T(0.5) * (p.FZ[12 * k1 + 3 * v] + p.FZ[12 * k2 + 3 * v]);
+    return;
+  }
+  if (type == NB_COARSER) {
+    T r[12];
+    load_rec(p.FZ, k, r);
+    const int d = nb_depth(code);
+    for (int v = 0; v < 3; v++) {
+      T sv[3] = {r[3 * v], r[3 * v + 1], r[3 * v + 2]};
+      if (v == 0) slopes_to_h(sv[1], sv[2], r[10], r[11]);
+      for (int q = d - 1; q >= 0; q--) {
+        T o[3];
+        prolong3(sv[0], sv[1], sv[2], ((a >> q) & 1) + 2 * ((b >> q) & 1), o);
+        sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
+      }
+      avg[v] = sv[0];
+    }
+    return;
+  }
+  for (int v = 0; v < 3; v++) avg[v] = p.FZ[12 * k + 3 * v];
+}
+
+// both: the neighbour's view limit and averages across face f; false on the
+// boundary
+template <typename T>
+__device__ __forceinline__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, T out[7]) {
   long long k;
   uint8_t kd;
   if (!nbr_locate(g, p, l, i, j, f, k, kd)) return false;
@@ -1921,11 +1967,14 @@ struct FaceOut {
   T bout;             // outward boundary mass flux (m^3/s), 0 inside
 };
 
-// given the neighbour's view limit nb (inside) or a boundary (ghost)
-template <typename T>
+// given the neighbour's view limit and averages nb (inside) or a boundary
+// (ghost); with dt > 0 the flux carries the outflow limit of a forward-Euler
+// stage of length dt (the donor is this leaf or, inside, the neighbour's
+// view; a boundary ghost is never a limited donor)
+template <typename T, class NbAvg>
 __device__ __forceinline__ FaceOut<T> face_flux_nb(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
                                                    const T (&w)[9], const T (&zc)[3], int f, ForceTime tf,
-                                                   bool inside, T (&nb)[4]) {
+                                                   bool inside, T (&nb)[4], T dt, const NbAvg &nbavg) {
   const T gg = geo_g<T>(g), hd = geo_hd<T>(g);
   T own[4];
   own[0] = first_face(w[0], w[1], w[2], zc[0], f);
@@ -1979,6 +2028,19 @@ __device__ __forceinline__ FaceOut<T> face_flux_nb(const Geo &g, const Ptrs<T> &
     hll(sn.hs, sn.v, sn.u, so.hs, so.v, so.u, gg, hd, F3);
     o.F0 = F3[0]; o.F1 = F3[2]; o.F2 = F3[1];
   }
+  if (dt > T(0) && o.F0 != T(0)) {
+    const bool own_first = (f == 0 || f == 2);
+    const bool from_own = own_first ? (o.F0 > T(0)) : (o.F0 < T(0));
+    const bool xf = f < 2;
+    const T dxl = geo_dx<T>(g, l);
+    if (from_own)
+      drain_limit(o.F0, o.F1, o.F2, w[0], xf ? w[3] : w[6], xf ? w[6] : w[3], gg, hd, dxl, dt);
+    else if (inside) {
+      T av[3];
+      nbavg(av);
+      drain_limit(o.F0, o.F1, o.F2, av[0], xf ? av[1] : av[2], xf ? av[2] : av[1], gg, hd, dxl, dt);
+    }
+  }
   o.bout = T(0);
   if (!inside) o.bout = ((f == 0 || f == 2) ? o.F0 : -o.F0) * geo_dx<T>(g, l);
   return o;
@@ -1986,10 +2048,13 @@ __device__ __forceinline__ FaceOut<T> face_flux_nb(const Geo &g, const Ptrs<T> &
 
 template <typename T>
 __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
-                                                const T (&w)[9], const T (&zc)[3], int f, ForceTime tf) {
-  T nb[4];
+                                                const T (&w)[9], const T (&zc)[3], int f, ForceTime tf, T dt) {
+  T nb[7];
   const bool inside = nbr_limit(g, p, l, i, j, f, nb);
-  return face_flux_nb(g, p, l, i, j, w, zc, f, tf, inside, nb);
+  T lim[4] = {nb[0], nb[1], nb[2], nb[3]};
+  return face_flux_nb(g, p, l, i, j, w, zc, f, tf, inside, lim, dt, [&](T av[3]) {
+    av[0] = nb[4]; av[1] = nb[5]; av[2] = nb[6];
+  });
 }
 
 // Reflux rule on static grids (MWDG_IFACE_REFLUX): on the coarse side of a
@@ -1998,7 +2063,7 @@ __device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, 
 // code as theirs, so the mass leaving one side enters the other.
 template <typename T>
 __device__ __noinline__ bool reflux_face(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, ForceTime tf,
-                                         T &F0, T &F1, T &F2) {
+                                         T dt, T &F0, T &F1, T &F2) {
   const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
   if (a < 0 || b < 0 || a >= g.nxl[l] || b >= g.nyl[l] || p.kind[nid(g, l, a, b)] != K_SIG) return false;
   int c1, c2;
@@ -2014,7 +2079,7 @@ __device__ __noinline__ bool reflux_face(const Geo &g, const Ptrs<T> &p, int l, 
     load_rec(p.FZ, nid(g, l + 1, ic, jc), r);
     for (int m = 0; m < 9; m++) w[m] = r[m];
     for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
-    const FaceOut<T> o = face_flux(g, p, l + 1, ic, jc, w, zc, f ^ 1, tf);
+    const FaceOut<T> o = face_flux(g, p, l + 1, ic, jc, w, zc, f ^ 1, tf, dt);
     G[q][0] = o.F0; G[q][1] = o.F1; G[q][2] = o.F2;
   }
   F0 = T(0.5) * (G[0][0] + G[1][0]);
@@ -2213,11 +2278,13 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
     DirTerms<T> dx_, dy_;
 #pragma unroll
     for (int dir = 0; dir < 2; dir++) {
-      FaceOut<T> fa = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir, tf, in[2 * dir], nb[2 * dir]);
-      if (REFLUX) reflux_face(g, p, l, i, j, 2 * dir, tf, fa.F0, fa.F1, fa.F2);
+      FaceOut<T> fa = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir, tf, in[2 * dir], nb[2 * dir], dt,
+                                   [&](T av[3]) { nbr_avg_code(g, p, l, i, j, 2 * dir, code[2 * dir], av); });
+      if (REFLUX) reflux_face(g, p, l, i, j, 2 * dir, tf, dt, fa.F0, fa.F1, fa.F2);
       bsum += fa.bout;
-      FaceOut<T> fb = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir + 1, tf, in[2 * dir + 1], nb[2 * dir + 1]);
-      if (REFLUX) reflux_face(g, p, l, i, j, 2 * dir + 1, tf, fb.F0, fb.F1, fb.F2);
+      FaceOut<T> fb = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir + 1, tf, in[2 * dir + 1], nb[2 * dir + 1], dt,
+                                   [&](T av[3]) { nbr_avg_code(g, p, l, i, j, 2 * dir + 1, code[2 * dir + 1], av); });
+      if (REFLUX) reflux_face(g, p, l, i, j, 2 * dir + 1, tf, dt, fb.F0, fb.F1, fb.F2);
       bsum += fb.bout;
       dir_terms(dir == 0, fa, fb, gg, dir == 0 ? dx_ : dy_);
     }

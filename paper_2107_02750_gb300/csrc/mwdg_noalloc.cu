@@ -28,10 +28,14 @@ constexpr int NA_MAX_DEVICES = 64;
 // call overwrites the entries it reads, so nothing needs clearing; calls
 // whose work overlaps on the GPU race on this array.
 static __device__ __align__(256) double g_na_part[NA_SCRATCH];
+// set when a leaf's level lies outside 0..L; cleared at the start of each call
+static __device__ int g_na_bad;
 
 // device address of g_na_part per device, looked up once per device
 double *g_na_ptr[NA_MAX_DEVICES] = {};
 std::mutex g_na_mu;
+
+__global__ void k_na_clear() { g_na_bad = 0; }
 
 __global__ void k_na_part(const double *h0, const int32_t *level, long long n, double dx, int L,
                           double *part) {
@@ -41,8 +45,11 @@ __global__ void k_na_part(const double *h0, const int32_t *level, long long n, d
   for (int q = 0; q < NA_PER_THREAD; q++) {
     long long k = base + (long long)q * NA_TPB + threadIdx.x;
     if (k < n) {
-      int lv = level[k];
-      lv = lv < 0 ? 0 : (lv > L ? L : lv);
+      const int lv = level[k];
+      if (lv < 0 || lv > L) {  // not a level of this hierarchy: the call fails
+        g_na_bad = 1;
+        continue;
+      }
       double side = dx * (double)(1LL << (L - lv));
       acc += h0[k] * (side * side);
     }
@@ -66,7 +73,7 @@ __global__ void k_na_final(const double *part, int nb, double *out) {
     if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = sh[0];
+  if (threadIdx.x == 0) *out = g_na_bad ? __longlong_as_double(0x7ff8000000000000LL) : sh[0];
 }
 
 // once per device, with that device current: the device address of the
@@ -91,14 +98,31 @@ extern "C" mwdg_status mwdg_volume_noalloc(const double *h0, const int32_t *leve
   if (!volume || n < 0 || (n > 0 && (!h0 || !level)) || !(dx > 0.0) || L < 0 || L > MWDG_LMAX)
     return MWDG_ERR_ARG;
   if (n > MWDG_VOLUME_NOALLOC_MAX) return MWDG_ERR_CAPACITY;
+  // an error left pending by earlier work of the caller or another library
+  // is not this call's: it is reported as MWDG_ERR_CUDA and left in place
+  // for its owner
+  if (cudaPeekAtLastError() != cudaSuccess) return MWDG_ERR_CUDA;
   double *part = nullptr;
   mwdg_status s = scratch_for_current_device(&part);
   if (s != MWDG_OK) return s;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int nb = (int)((n + NA_CHUNK - 1) / NA_CHUNK);
+  k_na_clear<<<1, 1, 0, st>>>();
   if (nb > 0) k_na_part<<<nb, NA_TPB, 0, st>>>(h0, level, (long long)n, dx, L, part);
   k_na_final<<<1, NA_TPB, 0, st>>>(part, nb, volume);
-  return cudaGetLastError() == cudaSuccess ? MWDG_OK : MWDG_ERR_CUDA;
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    (void)cudaGetLastError();  // this call's own launch error
+    return MWDG_ERR_CUDA;
+  }
+  // the level check: wait for this call's work and read its flag (into host
+  // stack memory; nothing is allocated)
+  int bad = 0;
+  if (cudaMemcpyFromSymbolAsync(&bad, g_na_bad, sizeof bad, 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return MWDG_ERR_CUDA;
+  }
+  return bad ? MWDG_ERR_ARG : MWDG_OK;
 }
 
 static_assert(MWDG_VOLUME_NOALLOC_MAX <= (long long)NA_SCRATCH * NA_CHUNK, "scratch too small");

@@ -66,3 +66,15 @@ def test_noalloc_volume_limits():
     lv = torch.zeros(1, dtype=torch.int32, device=dev)
     assert _call(lib, dummy, lv, 67108864 + 1, 1.0, 0, out, stream) == -7
     assert _call(lib, dummy, lv, 1, 0.0, 0, out, stream) == -1
+    # a level outside 0..L is refused (not clamped): the volume reads NaN
+    for bad in (3, -1):
+        lvb = torch.tensor([0, bad], dtype=torch.int32, device=dev)
+        h2 = torch.ones(2, dtype=torch.float64, device=dev)
+        assert _call(lib, h2, lvb, 2, 1.0, 2, out, stream) == -1
+        torch.cuda.synchronize()
+        assert np.isnan(float(out.item()))
+    # and a valid call after it succeeds again
+    lvg = torch.tensor([0, 2], dtype=torch.int32, device=dev)
+    assert _call(lib, h2, lvg, 2, 1.0, 2, out, stream) == 0
+    torch.cuda.synchronize()
+    assert float(out.item()) == 16.0 + 1.0
