@@ -709,8 +709,32 @@ void orc_adapt(orc_sim *s) {
         }
       }
   }
-  /* Eq. 9 recursively from level L, keeping every detail */
-  encode_flow_all(s, s->U, L, 1);
+  /* Eq. 9 from the leaves upwards, keeping the details: a refined node's
+   * scale coefficients and details come from its children's coefficients;
+   * a leaf keeps its own, and a node at or below a leaf carries no flow
+   * detail (its data are the prolongation of the leaf's plane, whose
+   * details vanish) */
+  for (int l = L - 1; l >= 0; l--) {
+    size_t nl = nn(s, l), nf = nn(s, l + 1);
+    for (int j = 0; j < s->ny[l]; j++)
+      for (int i = 0; i < s->nx[l]; i++) {
+        size_t k = id(s, l, i, j);
+        if (s->kind[l][k] != K_SIG) {
+          for (int q = 0; q < 27; q++) s->D[l][q * nl + k] = 0.0;
+          continue;
+        }
+        for (int v = 0; v < 3; v++) {
+          double ch[12], sp[3], d[9];
+          for (int c = 0; c < 4; c++) {
+            size_t kc = id(s, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
+            for (int m = 0; m < 3; m++) ch[3 * c + m] = s->U[l + 1][(3 * v + m) * nf + kc];
+          }
+          encode_node_scheme(s, ch, sp, d);
+          for (int m = 0; m < 3; m++) s->U[l][(3 * v + m) * nl + k] = sp[m];
+          for (int q = 0; q < 9; q++) s->D[l][(9 * v + q) * nl + k] = d[q];
+        }
+      }
+  }
   /* normalised details against epsilon; topography details are static */
   for (int l = 0; l < L; l++) {
     size_t n = nn(s, l);
@@ -741,26 +765,14 @@ void orc_adapt(orc_sim *s) {
   }
   closure(s);
   kinds_from_flags(s);
-  /* Eq. 10 from level 0: children of every refined node are decoded with
-   * its kept details; decoding stops at active leaves */
-  for (int l = 0; l < L; l++) {
-    size_t n = nn(s, l), nf = nn(s, l + 1);
-    for (int j = 0; j < s->ny[l]; j++)
-      for (int i = 0; i < s->nx[l]; i++) {
-        size_t k = id(s, l, i, j);
-        if (s->kind[l][k] != K_SIG) continue;
-        for (int v = 0; v < 3; v++) {
-          double sp[3], d[9], ch[12];
-          for (int m = 0; m < 3; m++) sp[m] = s->U[l][(3 * v + m) * n + k];
-          for (int q = 0; q < 9; q++) d[q] = s->D[l][(9 * v + q) * n + k];
-          decode_node_scheme(s, sp, d, ch);
-          for (int c = 0; c < 4; c++) {
-            size_t kc = id(s, l + 1, 2 * i + (c & 1), 2 * j + (c >> 1));
-            for (int m = 0; m < 3; m++) s->U[l + 1][(3 * v + m) * nf + kc] = ch[3 * c + m];
-          }
-        }
-      }
-  }
+  /* Eq. 10: the new leaves' coefficients.  Decoding from level 0 with the
+   * kept details reproduces, at every node, the coefficients the encode
+   * gave it (Eq. 9 and Eq. 10 are inverse); those are already in place: a
+   * leaf that stays keeps its coefficients, a coarsened leaf has its
+   * encoded scale coefficients, and a refined leaf the prolongation of its
+   * old leaf's plane.  So the decode is taken as that identity, exactly,
+   * rather than recomputed with rounding (orc_decode_node states it and the
+   * tests pin the round trip). */
 }
 
 /* ------------------------------------------------------------------------ */

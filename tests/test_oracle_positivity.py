@@ -86,20 +86,15 @@ def _valley_window(mode):
 
 @pytest.mark.parametrize("mode", [S.UNIFORM, S.ADAPTIVE])
 def test_valley_window_through_the_inflow(mode):
-    """The rapid-flow valley's window through the inflow for 10 min: no depth
-    is clipped on the uniform grid; on the adaptive grid the only clipped
-    depths are the rounding residue (|h| ~ 1e-24 m) that the oracle's
-    top-down decode (Eq. 10) leaves in dry leaves.  The budget closes with no
-    clipped volume in it."""
+    """The rapid-flow valley's window through the inflow for 10 min, uniform
+    and MWDG2: no depth is clipped, and the budget closes with no clipped
+    volume in it."""
     p = _valley_window(mode)
     s = oracle_sim(p)
     v0 = s.diag()["volume"]
     s.run_to(600.0)
     d = s.diag()
-    if mode == S.UNIFORM:
-        assert d["n_clip"] == 0 and d["v_clip"] == 0.0
-    else:
-        assert d["v_clip"] <= 1e-12 * d["v_in"]
+    assert d["n_clip"] == 0 and d["v_clip"] == 0.0
     budget = v0 + d["v_in"] - d["v_out"] + d["v_rain"]
     assert abs(d["volume"] - budget) <= 1e-12 * d["volume"]
     assert d["v_in"] > 4.0e4
