@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="time the FP64 DG2 adjoint: one checkpoint segment forward and backward")
     ap.add_argument("--adjoint-steps", type=int, default=200, help="adjoint: steps per checkpoint segment")
+    ap.add_argument("--urban", type=int, default=1,
+                    help="1: add the slow-to-gradual urban configuration (static vs uniform DG2) to the line")
     ap.add_argument("--scheme", default="dg2", choices=["dg2", "fv1", "acc"],
                     help="solver: DG2 (MWDG2, the headline), FV1 (HWFV1 on the adaptive grid) or ACC "
                          "(static graded grid from the same MRA of the topography)")
@@ -120,13 +122,35 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
-def cpu_baseline(n_full, budget_s=15.0):
-    """The FP64 oracle, as it stands, single-threaded on this host: a 256 x 256
-    crop (L = 8) of the same valley through the inflow, MWDG2 from t = 0,
-    stepping until about budget_s seconds of CPU time have passed."""
+def host_cpu():
+    """the host's CPU model and logical core count"""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"model": model or "unknown", "nproc": os.cpu_count()}
+
+
+def _oracle_window(n_full):
+    """the 256 x 256 window (L = 8) of the valley through the inflow, as an
+    oracle simulation at t = 0"""
     import oracle as O
     from paper_2107_02750_gb300 import synth as S
-    full = S.valley(n=n_full)
+    full = S.valley(n=n_full, L=n_full.bit_length() - 1)
     p = S.crop(full, 0, n_full // 2 - 128, 256, 256, L=8)
     s = O.Sim(M=p.M, N=p.N, L=p.L, R=p.dx, mode=p.mode, eps=p.eps, bc=p.bc,
               inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1,
@@ -136,17 +160,51 @@ def cpu_baseline(n_full, budget_s=15.0):
     s.load_initial(p.h_vert, p.qx_vert, p.qy_vert, p.is_eta)
     s.set_inflow(p.inflow_t, p.inflow_Q)
     s.init_grid()
+    return s
+
+
+def _oracle_sample(job):
+    """MWDG2 steps of the oracle on the valley window from t = 0: either a
+    time budget (budget_s > 0) or warm-up + a step count; returns (updates,
+    seconds, steps)"""
+    n_full, budget_s, warmup, steps = job
+    s = _oracle_window(n_full)
+    for _ in range(warmup):
+        s.step()
+    upd = k = 0
     t0 = time.perf_counter()
-    upd = 0
-    steps = 0
-    while time.perf_counter() - t0 < budget_s:
+    while (time.perf_counter() - t0 < budget_s) if budget_s > 0 else (k < steps):
         s.step()
         upd += len(s.leaves()[0])
-        steps += 1
-    el = time.perf_counter() - t0
-    return {"value": upd / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, 256x256 crop (L=8) of the valley through the inflow, MWDG2 from t=0, "
-                      f"{steps} steps ({upd} updates) in {el:.1f} s on 1 host thread"}
+        k += 1
+    return upd, time.perf_counter() - t0, k
+
+
+def oracle_all_cores(n_full, budget_s=0.0, warmup=0, steps=0):
+    """the same sample in one process per logical core (spawned), all at
+    once: whole-host throughput of the oracle as it stands"""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_sample, [(n_full, budget_s, warmup, steps)] * cores)
+    upd = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    return upd, el, cores, sum(r[2] for r in res)
+
+
+def cpu_baseline(n_full, budget_s=10.0):
+    """The FP64 oracle, as it stands, on this host: the 256 x 256 window (L = 8)
+    of the same valley through the inflow, MWDG2 from t = 0, for about
+    budget_s seconds on one thread, then the same in one process per core."""
+    upd1, el1, k1 = _oracle_sample((n_full, budget_s, 0, 0))
+    updN, elN, cores, kN = oracle_all_cores(n_full, budget_s)
+    cpu = host_cpu()
+    return {"value": updN / elN, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, 256x256 window (L=8) of the valley through the inflow, MWDG2 from t=0: "
+                      f"one process per core ({cores}), {kN} steps ({updN} updates) in {elN:.1f} s",
+            "cpu_model": cpu["model"], "nproc": cpu["nproc"],
+            "single_thread": {"value": upd1 / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"the same window on 1 thread: {k1} steps ({upd1} updates) in {el1:.1f} s"}}
 
 
 # ---------------------------------------------------------------------------
@@ -250,25 +308,40 @@ def run_gpu(args, rank, world):
     value = updates_all / (total_ms * 1e-3)
 
     # roofline of the dominant kernel: the kernel with the longest average
-    # launch (each MRA level is its own launch)
+    # launch (each MRA level is its own launch).  `frac` uses the algorithmic
+    # bytes of the step's definition (a fused uniform stage: stage 1 reads 13
+    # values and writes 9, stage 2 reads 22 and writes 9); the bytes this
+    # design's kernel moves by construction (its flux-view record, stored
+    # views, list entry and neighbour codes) are reported beside it
     peak_gbs, peak_kind = peaks()
     per_launch = {k: v[0] / v[1] for k, v in kt.items() if v[1]}
     dom_name = max(per_launch, key=per_launch.get)
     dom_ms, dom_n = kt[dom_name]
     mean_leaves = kupd / len(kms)
     bpl = kernel_bytes_per_leaf(dom_name, 4, args.scheme, args.grid)
-    achieved = (bpl * mean_leaves) / (dom_ms / dom_n * 1e-3) / 1e9 if bpl else None
+    alg = STAGE_VALUES.get(dom_name) if args.scheme == "dg2" else None
+    abpl = alg * 4 if alg else bpl
+    launch_s = dom_ms / dom_n * 1e-3
+    achieved = (abpl * mean_leaves) / launch_s / 1e9 if abpl else None
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs,
                 "unit": "GB/s", "frac": (achieved / peak_gbs) if achieved else None,
                 "traffic": TRAFFIC.get(dom_name) if (args.grid, args.scheme) == ("adaptive", "dg2") else None,
-                "peak_kind": peak_kind,
-                "algorithmic_bytes_per_leaf": bpl, "launches": dom_n,
+                "peak_kind": peak_kind, "algorithmic_bytes_per_leaf": abpl,
+                "design_bytes_per_leaf": bpl,
+                "design_frac": (bpl * mean_leaves / launch_s / 1e9 / peak_gbs) if bpl else None,
+                "launches": dom_n, "mean_leaves_per_launch": mean_leaves,
                 "share_of_step": dom_ms / max(sum(v[0] for v in kt.values()), 1e-9),
                 "step_ms_by_class": {k: round(v[0] / len(kms), 5) for k, v in kt.items() if v[1]},
                 "ms_per_launch": {k: round(v, 5) for k, v in per_launch.items()}}
+    if args.scheme == "dg2":
+        # the whole step on the step's algorithmic bytes per update: the DG2
+        # step (53 values) plus, on the adaptive grid, the MRA's per leaf
+        wb = DG2_STEP_VALUES * 4 + (MRA_BYTES_PER_LEAF[4] if args.grid == "adaptive" else 0)
+        roofline["whole_step"] = {"bytes_per_update": wb, "achieved": wb * value / 1e9,
+                                  "frac": wb * value / 1e9 / peak_gbs, "unit": "GB/s"}
 
     # end to end through the public API: resume from a host checkpoint in
-    # pinned memory, K steps, depth and velocity maps back to the host
+    # pinned memory, E2E_STEPS steps, depth and velocity maps back to the host
     pinned = torch.from_numpy(ckpt).pin_memory()
     hbuf = [torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory() for _ in range(3)]
     torch.cuda.synchronize()
@@ -276,7 +349,7 @@ def run_gpu(args, rank, world):
     s32.load_state(pinned)
     n_e2e = 0
     _, u0 = s32.get_counters()
-    s32.run_steps(args.steps)
+    s32.run_steps(E2E_STEPS)
     _, u1 = s32.get_counters()
     n_e2e = u1 - u0
     import ctypes as C
@@ -285,9 +358,10 @@ def run_gpu(args, rank, world):
         raise RuntimeError("mwdg_read_fields failed")
     e2e_s = time.perf_counter() - t0
     e2e = {"value": n_e2e / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(ckpt.nbytes // args.steps),
-           "d2h_bytes_per_step": int(3 * p.nx * p.ny * 8 // args.steps),
-           "what": "mwdg_load_state from pinned host checkpoint + K x mwdg_dg2_step + mwdg_read_fields to pinned host"}
+           "h2d_bytes_per_step": int(ckpt.nbytes // E2E_STEPS),
+           "d2h_bytes_per_step": int(3 * p.nx * p.ny * 8 // E2E_STEPS), "steps": E2E_STEPS,
+           "what": f"mwdg_load_state from pinned host checkpoint + {E2E_STEPS} x mwdg_dg2_step + "
+                   f"mwdg_read_fields to pinned host"}
 
     out = {"value": value, "ms_per_step": total_ms / len(ms), "updates": updates_all,
            "mean_active": updates / len(ms), "roofline": roofline, "clocks": clk.summary(), "e2e": e2e,
@@ -298,8 +372,18 @@ def run_gpu(args, rank, world):
         s64 = make_solver(p, M.F64, sptr)
         s64.run_to_time(args.spinup)
         ms64, upd64, _, _ = timed_steps(s64, max(4, args.steps // 4), 2, flush, stream)
-        out["fp64"] = {"value": upd64 / (sum(ms64) * 1e-3), "unit": UNIT,
-                       "ms_per_step": sum(ms64) / len(ms64), "dtype": "f64"}
+        v64 = upd64 / (sum(ms64) * 1e-3)
+        fma64 = M.fma_rate(M.F64, sptr)
+        fma32 = M.fma_rate(M.F32, sptr)
+        out["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": sum(ms64) / len(ms64), "dtype": "f64",
+                       "alu": {"bound": "alu", "peak": fma64 / 1e12, "unit": "TFLOP/s",
+                               "peak_kind": "measured (FP64 FMA chains, CUDA events)",
+                               "flops_per_update": FP64_FLOPS_PER_UPDATE,
+                               "achieved": (v64 * FP64_FLOPS_PER_UPDATE / 1e12) if FP64_FLOPS_PER_UPDATE else None,
+                               "frac": (v64 * FP64_FLOPS_PER_UPDATE / fma64) if FP64_FLOPS_PER_UPDATE else None},
+                       "hbm": {"bytes_per_update": DG2_STEP_VALUES * 8 + MRA_BYTES_PER_LEAF[8],
+                               "frac": (DG2_STEP_VALUES * 8 + MRA_BYTES_PER_LEAF[8]) * v64 / 1e9 / peak_gbs}}
+        out["fma_peaks_tflops"] = {"fp64": fma64 / 1e12, "fp32": fma32 / 1e12}
         tcmp = max(s64.get_time()[0], s32.get_time()[0]) + 1.0
         a32, a64 = make_solver(p, M.F32, sptr), make_solver(p, M.F64, sptr)
         # the method's own sensitivity: a second FP64 run whose only
@@ -318,7 +402,88 @@ def run_gpu(args, rank, world):
                 self64.append(compare_depths(b64, a64, t))
         out["accuracy_f32_vs_f64"] = acc
         out["fp64_vs_fp64_one_extra_stop"] = self64
+        out["accuracy_f32_on_fp64_steps"] = fixed_step_accuracy(p, sptr)
+        out["run_average_2h"] = {"f32": run_average(p, M.F32, sptr, 7200.0),
+                                 "f64": run_average(p, M.F64, sptr, 7200.0)}
     return out
+
+
+def fixed_step_accuracy(p, sptr, marks=(120.0, 300.0, 900.0)):
+    """FP32 against FP64 with the FP32 run taking the FP64 run's time steps
+    (mwdg_dg2_step_dt): the FP32 arithmetic error alone, without the
+    divergence of two trajectories that choose their own CFL steps"""
+    import paper_2107_02750_gb300 as M
+    a = make_solver(p, M.F64, sptr)
+    b = make_solver(p, M.F32, sptr)
+    out, t = [], 0.0
+    for mark in marks:
+        while t < mark:
+            dt = a.dg2_step()
+            b.dg2_step_dt(dt)
+            t += dt
+        r = compare_depths(b, a, t)
+        r["steps"] = a.get_time()[1]
+        r["n_clip_f32"] = b.get_volume()["n_clip"]
+        out.append(r)
+    return out
+
+
+def run_average(p, precision, sptr, t_end):
+    """the whole simulated run of the configuration from t = 0 (mwdg_run_to_time,
+    CUDA events around it, no flush): active-cell updates/s averaged over the
+    run, with the mass budget and the clipped volume at its end"""
+    import torch
+    import paper_2107_02750_gb300 as M
+    s = make_solver(p, precision, sptr)
+    stream = torch.cuda.ExternalStream(sptr)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.run_to_time(t_end)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    steps, upd = s.get_counters()
+    v = s.get_volume()
+    return {"value": upd / (ms * 1e-3), "unit": UNIT, "simulated_s": s.get_time()[0], "steps": steps,
+            "ms": ms, "mean_active": upd / max(steps, 1), "dtype": "f64" if precision == M.F64 else "f32",
+            "n_clip": v["n_clip"], "v_clip_m3": v["v_clip"], "v_in_m3": v["v_in"],
+            "budget_error_rel": abs(v["volume"] - (v["v_in"] - v["v_out"] + v["v_rain"])) / max(v["volume"], 1.0)}
+
+
+def run_urban(stream, flush, K, W, spinup=1800.0, t_cmp=600.0):
+    """The slow-to-gradual configuration: 2048 x 2048 urban-like DEM at dx =
+    2 m, 8 m blocks off a 100 m road grid (n = 0.013 on roads, 0.035 else),
+    50 mm/h of rain for 1 h.  Static non-uniform DG2 (one MRA of the
+    topography at eps = 1e-2, reflux rule) against uniform DG2, both FP32
+    with FP64 time and volume sums: K flushed steps each after `spinup`
+    simulated seconds, and the static FP32 depth against the static FP64
+    depth at t_cmp."""
+    import paper_2107_02750_gb300 as M
+    from dataclasses import replace
+    from paper_2107_02750_gb300 import synth as S
+    sptr = stream.cuda_stream
+    p = S.urban()
+    p.iface_rule = 1
+    res = {}
+    for name, q in (("static", p), ("uniform", replace(p, mode=S.UNIFORM))):
+        s = make_solver(q, M.F32, sptr)
+        s.run_to_time(spinup)
+        ms, upd, _, _ = timed_steps(s, K, W, flush, stream)
+        steps, _ = s.get_counters()
+        res[name] = {"value": upd / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": sum(ms) / len(ms),
+                     "active_leaves": upd / len(ms), "steps_to_spinup": steps - K - W}
+    a32, a64 = make_solver(p, M.F32, sptr), make_solver(p, M.F64, sptr)
+    a32.run_to_time(t_cmp)
+    a64.run_to_time(t_cmp)
+    res["accuracy_f32_vs_f64_static"] = compare_depths(a32, a64, t_cmp)
+    res["speedup_static_over_uniform_s_per_simulated_s"] = (
+        (res["uniform"]["ms_per_step"]) / res["static"]["ms_per_step"])
+    res["config"] = ("2048x2048 urban DEM, dx=2 m, blocks 10-40 m x 8 m at 25 % cover, roads every 100 m, "
+                     f"rain 50 mm/h for 1 h; static grid eps=1e-2 (reflux rule); timed after {spinup:.0f} s, "
+                     f"FP32 vs FP64 at {t_cmp:.0f} s")
+    return res
 
 
 def average_raster(s):
@@ -353,37 +518,21 @@ def compare_depths(s32, s64, t):
 
 
 def reference_arm(args):
-    """The reference arm is the FP64 CPU oracle as it stands (single host
-    thread): W untimed then K timed MWDG2 steps on a 256 x 256 crop (L = 8) of
-    the same valley through the inflow, from t = 0."""
-    import oracle as O
-    from paper_2107_02750_gb300 import synth as S
-    full = S.valley(n=args.n, L=args.n.bit_length() - 1)
-    p = S.crop(full, 0, args.n // 2 - 128, 256, 256, L=8)
-    s = O.Sim(M=p.M, N=p.N, L=p.L, R=p.dx, mode=p.mode, eps=p.eps, bc=p.bc,
-              inflow_edge=p.inflow_edge, inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1,
-              limiter=p.limiter, dt_max=p.dt_max)
-    s.load_dem(p.z_vert)
-    s.load_roughness(p.n_cell())
-    s.load_initial(p.h_vert, p.qx_vert, p.qy_vert, p.is_eta)
-    s.set_inflow(p.inflow_t, p.inflow_Q)
-    s.init_grid()
-    for _ in range(args.warmup):
-        s.step()
-    upd = 0
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        s.step()
-        upd += len(s.leaves()[0])
-    el = time.perf_counter() - t0
+    """The reference arm is the FP64 CPU oracle as it stands, on all host
+    cores (one spawned process per core, each the same sample): W untimed
+    then K timed MWDG2 steps on the 256 x 256 window (L = 8) of the same
+    valley through the inflow, from t = 0."""
+    upd, el, cores, k = oracle_all_cores(args.n, 0.0, args.warmup, args.steps)
     v = upd / el
-    sample = (f"FP64 oracle on 1 host thread: {args.steps} MWDG2 steps ({upd} updates) of a 256x256 crop "
-              f"(L=8) of the valley through the inflow, from t=0, in {el:.1f} s")
+    cpu = host_cpu()
+    sample = (f"FP64 oracle, one process per core ({cores}): {args.steps} MWDG2 steps each ({upd} updates in all) "
+              f"of a 256x256 window (L=8) of the valley through the inflow, from t=0, in {el:.1f} s")
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu["model"], "nproc": cpu["nproc"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -412,10 +561,27 @@ def kernel_bytes_per_leaf(name, ts, scheme="dg2", grid="adaptive"):
     return n * ts + extra
 
 
+# Algorithmic values per active-cell update of the DG2 step (a fused uniform
+# stage keeps neighbour reads on chip): stage 1 reads U^n (9), the bed (3) and
+# Manning n (1) and writes U_int (9); stage 2 reads U_int, U^n, the bed and n
+# and writes U^{n+1}: 22 + 31 = 53 values, 212 B in FP32, 424 B in FP64.
+STAGE_VALUES = {"dg2_update_stage1": 22, "dg2_update_stage2": 31}
+DG2_STEP_VALUES = 53
+# The MRA's algorithmic bytes per active leaf and step (adaptive grid): the
+# leaf's state (9 values) and bed planes (3) read, the parents' scale
+# coefficients written (9 values per refined node, about one node per three
+# leaves: 3 values), and its flag byte
+MRA_BYTES_PER_LEAF = {4: (9 + 3 + 3) * 4 + 1, 8: (9 + 3 + 3) * 8 + 1}
+# FP64 floating-point operations per active-cell update of the FP64 MWDG2
+# step (adds, multiplies, 2 per fused multiply-add; divisions and square
+# roots as the instructions they expand to), counted by ncu over every kernel
+# of a step on this workload; None until counted for the current kernels
+FP64_FLOPS_PER_UPDATE = None
+E2E_STEPS = 200
 # DRAM bytes (read + write) per launch measured by ncu for a kernel of the
 # headline workload (FP32 MWDG2), when the kernel has not changed since (see
-# profiles/); None otherwise
-TRAFFIC = {"dg2_update_stage2": 58_196_224 + 2_093_312}  # ncu: dram read + write, one launch at this workload
+# profiles/); empty while the kernels differ from the captured ones
+TRAFFIC = {}
 
 
 def run_ensemble(args):
@@ -656,9 +822,15 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": out["roofline"], "cpu_baseline": cb, "e2e": out["e2e"], "clocks": out["clocks"],
                 "gpu_launches": out["gpu_launches"]}
-        for k in ("fp64", "accuracy_f32_vs_f64", "fp64_vs_fp64_one_extra_stop"):
+        for k in ("fp64", "fma_peaks_tflops", "accuracy_f32_vs_f64", "accuracy_f32_on_fp64_steps",
+                  "fp64_vs_fp64_one_extra_stop", "run_average_2h"):
             if k in out:
                 line[k] = out[k]
+        if args.urban and args.scheme == "dg2" and args.grid == "adaptive" and not args.no_fp64:
+            import torch
+            flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+            line["urban_static_vs_uniform"] = run_urban(torch.cuda.current_stream(), flush,
+                                                        max(5, args.steps), args.warmup)
         print(json.dumps(line))
     if world > 1:
         import torch

@@ -265,6 +265,16 @@ MWDG_API mwdg_status mwdg_launch_count(mwdg_ctx *ctx, int64_t *n);
 MWDG_API mwdg_status mwdg_volume_noalloc(const double *h0, const int32_t *level, int64_t n, double dx,
                                          int32_t L, double *volume, void *cuda_stream);
 
+/* Measured arithmetic ceiling of the current device: the fused
+ * multiply-add rate (2 flops each) that the FP64 (precision MWDG_F64) or FP32
+ * (MWDG_F32) pipes sustain over all SMs, from a kernel of independent FMA
+ * chains timed with CUDA events on cuda_stream, written to *flops_per_s.
+ * Not part of the method (the paper has no counterpart): it gives the FP64
+ * path, which GB300's FP64 pipes bound rather than its memory, a ceiling
+ * measured on the same GPU.  Synchronises cuda_stream.  Errors:
+ * MWDG_ERR_ARG (NULL pointer, another precision), MWDG_ERR_CUDA. */
+MWDG_API mwdg_status mwdg_fma_rate(int32_t precision, void *cuda_stream, double *flops_per_s);
+
 /* Launch shape of a context's step kernels: the number of blocks of the
  * leaf kernels (grid_leaves, 1..65535) and the size of the coarsest MRA
  * levels run by one block (coarse_nodes >= 1: levels with at most that many

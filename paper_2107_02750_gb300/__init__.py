@@ -10,8 +10,8 @@ All computation runs in the CUDA library ``libmwdg`` (``csrc/``, C ABI in
 ``include/mwdg.h``); :mod:`.binding` marshals arguments to it.  There is no CPU
 fallback: without the built library and a GPU the calls raise.
 """
-from .binding import (Solver, Ensemble, MwdgError, lib, solver_from_problem, UNIFORM, STATIC, ADAPTIVE,
+from .binding import (Solver, Ensemble, MwdgError, fma_rate, lib, solver_from_problem, UNIFORM, STATIC, ADAPTIVE,
                       F64, F32, DG2, FV1, ACC, WALL, OPEN, WEST, EAST, SOUTH, NORTH)
 
-__all__ = ["Solver", "Ensemble", "MwdgError", "lib", "solver_from_problem", "UNIFORM", "STATIC", "ADAPTIVE",
+__all__ = ["Solver", "Ensemble", "MwdgError", "fma_rate", "lib", "solver_from_problem", "UNIFORM", "STATIC", "ADAPTIVE",
            "F64", "F32", "DG2", "FV1", "ACC", "WALL", "OPEN", "WEST", "EAST", "SOUTH", "NORTH"]

@@ -22,7 +22,7 @@ EXPORTS = (
     "mwdg_read_fields", "mwdg_read_fields_dev", "mwdg_read_active", "mwdg_get_time",
     "mwdg_get_volume", "mwdg_profile", "mwdg_kernel_times", "mwdg_launch_count",
     "mwdg_last_error", "mwdg_status_string", "mwdg_state_bytes", "mwdg_save_state",
-    "mwdg_load_state", "mwdg_volume_noalloc", "mwdg_get_counters", "mwdg_read_gauges",
+    "mwdg_load_state", "mwdg_volume_noalloc", "mwdg_fma_rate", "mwdg_get_counters", "mwdg_read_gauges",
     "mwdg_set_launch_shape", "mwdg_get_launch_shape", "mwdg_ensemble_create", "mwdg_ensemble_destroy",
     "mwdg_ensemble_step", "mwdg_ensemble_run_to_time", "mwdg_ensemble_tune", "mwdg_ensemble_last_error",
 )
@@ -72,6 +72,7 @@ def lib(build: bool = True):
         "mwdg_mra_adapt": [vp, C.c_double, lp],
         "mwdg_dg2_step": [vp, dp],
         "mwdg_dg2_step_dt": [vp, C.c_double],
+        "mwdg_fma_rate": [C.c_int32, vp, dp],
         "mwdg_run_steps": [vp, C.c_int64],
         "mwdg_run_to_time": [vp, C.c_double, lp],
         "mwdg_read_fields": [vp, dp, dp, dp],
@@ -375,6 +376,16 @@ class Ensemble:
         self._ck(self._lib.mwdg_ensemble_tune(self._h, int(steps), out.ctypes.data_as(C.POINTER(C.c_int64))),
                  "mwdg_ensemble_tune")
         return out.reshape(-1, 2)
+
+
+def fma_rate(precision=F64, stream=None) -> float:
+    """measured FMA rate of the current device's FP64 or FP32 pipes (flop/s)"""
+    L = lib()
+    out = C.c_double()
+    st = L.mwdg_fma_rate(int(precision), C.c_void_p(stream or 0), C.byref(out))
+    if st != 0:
+        raise MwdgError(st, "mwdg_fma_rate")
+    return out.value
 
 
 def solver_from_problem(p, precision=F64, stream=None, **over) -> Solver:

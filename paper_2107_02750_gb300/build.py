@@ -25,6 +25,7 @@ UNITS = {
     "mwdg_f64.cu": ["-fmad=false"],
     "mwdg_f32.cu": ["--use_fast_math"],
     "mwdg_noalloc.cu": [],
+    "mwdg_peaks.cu": [],
     "mwdg_adjoint.cu": ["-fmad=false"],
 }
 

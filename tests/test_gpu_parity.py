@@ -135,22 +135,18 @@ def test_config3_urban_static_rain_f64_and_f32(rule):
     lev, _, _, c = g.read_active()
     assert len(np.unique(lev)) >= 3 and len(lev) < p.nx * p.ny
     assert (c[:, 0] > 1e-2).sum() > 100  # ponded water
-    # FP32 against FP64 on cell-average depths: pointwise at t = 8 s, the
-    # bulk (99th percentile, wet extent) at the end of the horizon.  A nearly
-    # dry leaf cut by a wall can be stored as flat depth in one precision and
-    # as flat free surface in the other (its average agrees; its plane does
-    # not), so planes are not compared pointwise here.  At 8 s the rain film
-    # is about 8 mm deep, at the 0.01 m wet threshold, so the extent is
-    # compared at the end only.
-    f8, d8 = gpu_sim(p, precision=1), gpu_sim(p)
-    f8.run_to_time(8.0)
-    d8.run_to_time(8.0)
-    a32, a64 = average_raster(f8), average_raster(d8)
+    # FP32 against FP64 on cell-average depths over the whole horizon, the
+    # FP32 run taking the FP64 run's time steps (mwdg_dg2_step_dt), so that
+    # the comparison sees the FP32 arithmetic alone: max <= 1e-3 m and CSI
+    # >= 0.99 (the benchmark spec's bar).  A nearly dry leaf cut by a wall can be
+    # stored as flat depth in one precision and as flat free surface in the
+    # other (its average agrees, its plane does not), so planes are not
+    # compared pointwise here.
+    d64, f = gpu_sim(p), gpu_sim(p, precision=1)
+    for _ in range(100):
+        f.dg2_step_dt(d64.dg2_step())
+    a32, a64 = average_raster(f), average_raster(d64)
     assert np.abs(a32 - a64).max() <= TOL32_H
-    f = gpu_sim(p, precision=1)
-    f.run_to_time(g.get_time()[0])
-    a32, a64 = average_raster(f), average_raster(g)
-    assert np.quantile(np.abs(a32 - a64), 0.99) <= 5e-3
     assert O.extent_scores(a32, a64)[2] >= 0.99
     assert g.get_volume()["n_clip"] == 0
     for sim, tol in ((g, 1e-12), (f, 1e-5)):
@@ -406,25 +402,46 @@ def test_full_size_adaptive_mass_budget(valley_full, precision):
     assert area == 1024 * 1024
 
 
-def test_full_size_f32_matches_f64_gpu():
-    """Benchmark workload, 1024 x 1024 MWDG2, FP32 against FP64 on the GPU at
-    t = 120 s: same wet extent (CSI), volumes within 1e-3 relative and a wet
-    RMSE below 1e-2 m.  Pointwise agreement to 1e-3 m holds until the two
-    runs take a wet/dry decision differently; after that the local
-    differences are reported by the benchmark, not asserted here."""
-    p = S.valley(n=1024, L=10, mode=S.ADAPTIVE, eps=1e-3)
+def _f32_on_f64_steps(p, t_end):
+    """FP64 and FP32 runs of p to t_end, the FP32 run taking the FP64 run's
+    CFL steps (mwdg_dg2_step_dt): (FP64 depth raster, FP32 depth raster,
+    FP64 volume, FP32 volume)"""
     a, b = gpu_sim(p, precision=0), gpu_sim(p, precision=1)
-    a.run_to_time(120.0)
-    b.run_to_time(120.0)
+    t = 0.0
+    while t < t_end:
+        dt = a.dg2_step()
+        b.dg2_step_dt(dt)
+        t += dt
     ha, _, _ = a.read_fields()
     hb, _, _ = b.read_fields()
-    _, _, csi = O.extent_scores(hb, ha)
-    assert csi >= 0.99, csi
-    va, vb = a.get_volume()["volume"], b.get_volume()["volume"]
-    assert abs(vb - va) <= 1e-3 * va
-    wet = (ha > 0.01) | (hb > 0.01)
-    assert wet.sum() > 0
-    assert np.sqrt(np.mean((ha - hb)[wet] ** 2)) <= 1e-2
+    return ha, hb, a.get_volume()["volume"], b.get_volume()["volume"]
+
+
+def test_full_size_f32_on_f64_steps_meets_the_bar_before_the_front():
+    """Benchmark workload, 1024 x 1024 MWDG2: FP32 against FP64 on the GPU at
+    t = 120 s with the FP32 run on the FP64 run's time steps, so that the
+    comparison sees the FP32 arithmetic alone: max depth error <= 1e-3 m and
+    CSI >= 0.99 (the benchmark spec's bar), volumes within 1e-6 relative."""
+    p = S.valley(n=1024, L=10, mode=S.ADAPTIVE, eps=1e-3)
+    ha, hb, va, vb = _f32_on_f64_steps(p, 120.0)
+    assert ((ha > 0.01) | (hb > 0.01)).sum() > 0
+    assert np.abs(ha - hb).max() <= TOL32_H
+    assert O.extent_scores(hb, ha)[2] >= 0.99
+    assert abs(vb - va) <= 1e-6 * va
+
+
+@pytest.mark.xfail(strict=True, reason="the FP32 path does not meet the 1e-3 m / CSI 0.99 bar once the flood "
+                   "front runs down the channel: at 300 s, on the FP64 run's own steps, max 1.15 m and CSI "
+                   "0.94 over about 100 wet cells (a leaf within rounding of the 1e-3 m dry depth takes the "
+                   "other wet/dry branch and the front moves by a cell); CSI is back above 0.99 from 900 s on "
+                   "while the maximum stays at 0.1-0.5 m")
+def test_full_size_f32_on_f64_steps_after_the_front_forms():
+    """The same comparison at t = 300 s, held to the same bar (known not to be
+    met; the benchmark reports the figures over the run)."""
+    p = S.valley(n=1024, L=10, mode=S.ADAPTIVE, eps=1e-3)
+    ha, hb, va, vb = _f32_on_f64_steps(p, 300.0)
+    assert np.abs(ha - hb).max() <= TOL32_H
+    assert O.extent_scores(hb, ha)[2] >= 0.99
 
 
 # ---------------------------------------------------------------------------
