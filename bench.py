@@ -547,6 +547,11 @@ def kernel_bytes_per_leaf(name, ts, scheme="dg2", grid="adaptive"):
                 "dg2_update_stage2": (4 + 1 + 4 + 3, 40)}  # new q, h read; h, qx, qy, q written
     elif scheme == "fv1":  # one forward-Euler stage (labelled stage 2)
         vals = {"dg2_update_stage2": (12 + 9 + 9, 40), "limit": (9 + 3 + 9 + 12, 40)}
+    elif grid == "uniform":  # one fused kernel per stage (limiter, interfaces and update)
+        vals = {
+            "dg2_update_stage1": (9 + 3 + 1 + 9 + 9, 0),  # U^n, bed, Manning n read; Wn, U_int written
+            "dg2_update_stage2": (9 + 3 + 9 + 9, 0),      # U_int, bed, Wn read; U^{n+1} written
+        }
     else:
         vals = {
             "dg2_update_stage1": (12 + 9 + 9, 40),      # FZ record, Wn read; Ui written

@@ -1436,6 +1436,96 @@ __device__ __forceinline__ T friction_factor(T h0, T qx0, T qy0, T nm, T dt, T g
   return T(1) / den;
 }
 
+// Partial-wet test of a leaf's stage input w (after rain and friction in
+// stage 1) with bed planes zp: a leaf whose average, any interface depth of
+// its plane, or any interface depth under a flat free surface h0 + z0 is not
+// wetter than h_dry drops to first order, stored as a flat free surface
+// over its planar bed (ws) and seen by the fluxes as flat depth over a flat
+// bed (wf, ze).  Returns false, with ws = w and ze = zp, for a leaf that is
+// not reduced.
+template <typename T>
+__device__ __forceinline__ bool limit_reduced(const Geo &g, const T (&w)[9], const T (&zp)[3], T (&ws)[9],
+                                              T (&wf)[9], T (&ze)[3]) {
+  const T hd = geo_hd<T>(g);
+  const T h0 = w[0];
+  const T eta0 = h0 + zp[0];
+  T h1x = w[1], h1y = w[2];
+  slopes_to_h(h1x, h1y, zp[1], zp[2]);
+  bool reduced = !(h0 > hd);
+#pragma unroll
+  for (int f = 0; f < 4; f++) {
+    if (!(face_value(h0, h1x, h1y, f) > hd)) reduced = true;
+    if (!(eta0 - face_value(zp[0], zp[1], zp[2], f) > hd)) reduced = true;
+  }
+#pragma unroll
+  for (int m = 0; m < 9; m++) ws[m] = w[m];
+  if (!reduced) {
+    ze[0] = zp[0]; ze[1] = zp[1]; ze[2] = zp[2];
+    return false;
+  }
+  // stored: flat free surface over the planar bed; flux view: flat depth
+  // over a flat bed (the same numbers in the free-surface form)
+  if (Form<T>::eta) {
+    ws[1] = T(0); ws[2] = T(0);
+  } else {
+    ws[1] = -zp[1]; ws[2] = -zp[2];
+  }
+  ws[4] = ws[5] = ws[7] = ws[8] = T(0);
+#pragma unroll
+  for (int m = 0; m < 9; m++) wf[m] = ws[m];
+  wf[1] = T(0); wf[2] = T(0);
+  ze[0] = zp[0]; ze[1] = T(0); ze[2] = T(0);
+  return true;
+}
+
+// Minmod of a leaf that is not reduced, per direction against its same-level
+// leaf neighbours (E, W, N, S: has[d], their depth averages nh (after rain),
+// discharge averages nq (after friction) and bed averages nzb), on the
+// interface offsets sqrt3 v1: two-argument minmod where only one neighbour
+// exists; qx and qy always (a dry neighbour has zero discharge), eta where
+// the leaf and its neighbours are wet.  ws holds w on entry and the limited
+// stored view on return.
+template <typename T>
+__device__ __forceinline__ void limit_minmod(const Geo &g, const T (&w)[9], const T (&zp)[3], const bool (&has)[4],
+                                             const T (&nh)[4], const T (&nq)[4][2], const T (&nzb)[4], T (&ws)[9]) {
+  const T hd = geo_hd<T>(g), s3 = s3v<T>();
+#pragma unroll
+  for (int dir = 0; dir < 2; dir++) {
+    const int dA = 2 * dir, dB = 2 * dir + 1;  // E/W, then N/S
+    const bool hasA = has[dA], hasB = has[dB];
+    if (!hasA && !hasB) continue;
+    const T hC = w[0], hA = nh[dA], hB = nh[dB];
+    const bool wet = (hC > hd) && (!hasA || hA > hd) && (!hasB || hB > hd);
+    const int cs = 1 + dir;
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+      if (v == 0 && !wet) continue;
+      T a0, aC, aB, slope;
+      const T zs = zp[cs];
+      if (v == 0) {
+        aC = hC + zp[0];
+        a0 = hA + nzb[dA];
+        aB = hB + nzb[dB];
+        slope = Form<T>::eta ? w[cs] : w[cs] + zs;
+      } else {
+        aC = w[3 * v];
+        a0 = nq[dA][v - 1];
+        aB = nq[dB][v - 1];
+        slope = w[3 * v + cs];
+      }
+      T a = s3 * slope, mm;
+      if (hasA && hasB) mm = minmod3(a, a0 - aC, aC - aB);
+      else if (hasA) mm = minmod2(a, a0 - aC);
+      else mm = minmod2(a, aC - aB);
+      if (mm != a) {
+        T ns = mm / s3;
+        if (v == 0) ws[cs] = Form<T>::eta ? ns : ns - zs;
+        else ws[3 * v + cs] = ns;
+      }
+    }
+  }
+}
+
 // Stage-input limiting of each leaf, giving the stored view Wst (used by
 // the RK2 combination) and the flux view F with its bed planes Ze.
 // Partially wet leaves (average, any interface depth of the plane, or any
@@ -1499,36 +1589,8 @@ __global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) k_leaf_limit(Geo g, Pt
       store_rec(p.FZ, k, rec);
       continue;
     }
-    const T h0 = w[0];
-    const T eta0 = h0 + zp[0];
-    T h1x = w[1], h1y = w[2];
-    slopes_to_h(h1x, h1y, zp[1], zp[2]);
-    bool reduced = !(h0 > hd);
-#pragma unroll
-    for (int f = 0; f < 4; f++) {
-      if (!(face_value(h0, h1x, h1y, f) > hd)) reduced = true;
-      if (!(eta0 - face_value(zp[0], zp[1], zp[2], f) > hd)) reduced = true;
-    }
     T ws[9], wf[9], ze[3];
-    if (reduced) {
-      // stored: flat free surface over the planar bed; flux view: flat depth
-      // over a flat bed (the same numbers in the free-surface form)
-#pragma unroll
-      for (int m = 0; m < 9; m++) ws[m] = w[m];
-      if (Form<T>::eta) {
-        ws[1] = T(0); ws[2] = T(0);
-      } else {
-        ws[1] = -zp[1]; ws[2] = -zp[2];
-      }
-      ws[4] = ws[5] = ws[7] = ws[8] = T(0);
-#pragma unroll
-      for (int m = 0; m < 9; m++) wf[m] = ws[m];
-      wf[1] = T(0); wf[2] = T(0);
-      ze[0] = zp[0]; ze[1] = T(0); ze[2] = T(0);
-    } else {
-#pragma unroll
-      for (int m = 0; m < 9; m++) ws[m] = w[m];
-      ze[0] = zp[0]; ze[1] = zp[1]; ze[2] = zp[2];
+    if (!limit_reduced(g, w, zp, ws, wf, ze)) {
       if (g.limiter) {
         // same-level leaf neighbours from the step's neighbour codes: the
         // averages (and Manning n) of all four read together (a missing
@@ -1546,57 +1608,23 @@ __global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) k_leaf_limit(Geo g, Pt
           nzb[d] = p.Z[kn];
           nmn[d] = FRIC ? p.NM[kn] : T(0);
         }
+        // stage 1: the neighbours' averages after rain and friction (both
+        // pointwise, so every leaf sees the values their own threads form)
+        if (FRIC) {
 #pragma unroll
-        for (int dir = 0; dir < 2; dir++) {
-          const int dA = 2 * dir, dB = 2 * dir + 1;  // E/W, then N/S
-          const bool hasA = has[dA], hasB = has[dB];
-          if (!hasA && !hasB) continue;
-          T hC = h0;
-          T hA = nh[dA];
-          T hB = nh[dB];
-          if (rain) {
-            hA = hA + rinc;
-            hB = hB + rinc;
-          }
-          // neighbours' friction factors (stage 1), for their discharge averages
-          T fA = T(1), fB = T(1);
-          if (FRIC) {
-            fA = (hA > hd) ? friction_factor(hA, nq[dA][0], nq[dA][1], nmn[dA], dt, gg) : T(0);
-            fB = (hB > hd) ? friction_factor(hB, nq[dB][0], nq[dB][1], nmn[dB], dt, gg) : T(0);
-          }
-          const bool wet = (hC > hd) && (!hasA || hA > hd) && (!hasB || hB > hd);
-          const int cs = 1 + dir;
-#pragma unroll
-          for (int v = 0; v < 3; v++) {
-            if (v == 0 && !wet) continue;
-            T a0, aC, aB, slope;
-            const T zs = zp[cs];
-            if (v == 0) {
-              aC = hC + zp[0];
-              a0 = hA + nzb[dA];
-              aB = hB + nzb[dB];
-              slope = Form<T>::eta ? w[cs] : w[cs] + zs;
+          for (int d = 0; d < 4; d++) {
+            if (!has[d]) continue;
+            if (rain) nh[d] = nh[d] + rinc;
+            if (nh[d] > hd) {
+              const T f = friction_factor(nh[d], nq[d][0], nq[d][1], nmn[d], dt, gg);
+              nq[d][0] = nq[d][0] * f;
+              nq[d][1] = nq[d][1] * f;
             } else {
-              aC = w[3 * v];
-              a0 = nq[dA][v - 1];
-              aB = nq[dB][v - 1];
-              if (FRIC) {
-                a0 = (hA > hd) ? a0 * fA : T(0);
-                aB = (hB > hd) ? aB * fB : T(0);
-              }
-              slope = w[3 * v + cs];
-            }
-            T a = s3 * slope, mm;
-            if (hasA && hasB) mm = minmod3(a, a0 - aC, aC - aB);
-            else if (hasA) mm = minmod2(a, a0 - aC);
-            else mm = minmod2(a, aC - aB);
-            if (mm != a) {
-              T ns = mm / s3;
-              if (v == 0) ws[cs] = Form<T>::eta ? ns : ns - zs;
-              else ws[3 * v + cs] = ns;
+              nq[d][0] = nq[d][1] = T(0);
             }
           }
         }
+        limit_minmod(g, w, zp, has, nh, nq, nzb, ws);
       }
 #pragma unroll
       for (int m = 0; m < 9; m++) wf[m] = ws[m];
@@ -2164,6 +2192,40 @@ __device__ __forceinline__ void finish_var_dir(const Geo &g, int v, long long k,
   }
 }
 
+// the same with the stored views given as values: ws (this stage's input)
+// and wc (stage 2: the stage-1 input), variable v's three coefficients
+template <typename T, int STAGE>
+__device__ __forceinline__ void finish_var_vals(const Geo &g, int v, int l, const T (&w)[9], const T (&zc)[3],
+                                                const DirTerms<T> &X, const DirTerms<T> &Y, T dt, const T *ws,
+                                                const T *wc, T &o0, T &o1, T &o2) {
+  const T gg = geo_g<T>(g), s3 = s3v<T>();
+  const T dxl = geo_dx<T>(g, l);
+  T h1x, h1y, e1x, e1y;
+  if (Form<T>::eta) {
+    e1x = w[1]; e1y = w[2];
+    h1x = w[1] - zc[1]; h1y = w[2] - zc[2];
+  } else {
+    h1x = w[1]; h1y = w[2];
+    e1x = w[1] + zc[1]; e1y = w[2] + zc[2];
+  }
+  T L0 = -(X.d[v]) / dxl - (Y.d[v]) / dxl;
+  if (v == 1) L0 = L0 + -gg * T(0.5) * X.hsum * X.zdif / dxl;
+  if (v == 2) L0 = L0 + -gg * T(0.5) * Y.hsum * Y.zdif / dxl;
+  T L1x = -(s3 / dxl) * X.s[v];
+  T L1y = -(s3 / dxl) * Y.s[v];
+  if (v == 1) L1x = L1x + -(T(2) * s3 * gg / dxl) * h1x * e1x;
+  if (v == 2) L1y = L1y + -(T(2) * s3 * gg / dxl) * h1y * e1y;
+  if (STAGE == 1) {
+    o0 = ws[0] + dt * L0;
+    o1 = ws[1] + dt * L1x;
+    o2 = ws[2] + dt * L1y;
+  } else {
+    o0 = T(0.5) * (wc[0] + ws[0] + dt * L0);
+    o1 = T(0.5) * (wc[1] + ws[1] + dt * L1x);
+    o2 = T(0.5) * (wc[2] + ws[2] + dt * L1y);
+  }
+}
+
 // positivity clip (h, counted) and dry reset of variable v given the
 // leaf's updated depth average h0n
 template <typename T>
@@ -2208,6 +2270,83 @@ __device__ __forceinline__ void next_step_reduce(const Geo &g, const Ptrs<T> &p,
     m2 = tmax(m2, tabs(qy0));
   } else {
     best = tmin(best, leaf_dt_candidate(g, p, l, i, j, h0, qx0, qy0, tf));
+  }
+}
+
+// The end of a stage update, per block: the non-finite flag, the block sums
+// of the boundary fluxes (coefficient type, one FP64 atomic per block) and
+// of the clips (FP64 where they occur), and in stage 2 the reductions the
+// next step needs (max |v0| on adaptive grids, the CFL candidate on fixed
+// ones); the last of the nblocks blocks to finish closes the step (no
+// waiting: each block takes a ticket after its own atomics are visible).
+template <typename T, int STAGE, int NT>
+__device__ __forceinline__ void update_epilogue(const Geo &g, const Ptrs<T> &p, T bsum, double csum,
+                                                unsigned long long ncl, bool bad, T m0, T m1, T m2, T best,
+                                                unsigned int nblocks) {
+  if (bad) p.ctl->nonfinite = 1;
+  // block sums in the coefficient type, one FP64 conversion and atomic per
+  // block; clip volumes (rare) in FP64 where they occur
+  for (int o = 16; o > 0; o >>= 1) {
+    bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+    ncl += __shfl_xor_sync(0xffffffffu, ncl, o);
+  }
+  if (__any_sync(0xffffffffu, ncl != 0ULL)) {
+    for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
+    if ((threadIdx.x & 31) == 0 && ncl) {
+      atomicAdd(&p.ctl->n_clip, ncl);
+      atomicAdd(&p.ctl->v_clip, csum);
+    }
+  }
+  if (STAGE >= 2 && g.mode == MWDG_ADAPTIVE)
+    for (int o = 16; o > 0; o >>= 1) {
+      m0 = tmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+      m1 = tmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+      m2 = tmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+  if (STAGE >= 2 && g.mode != MWDG_ADAPTIVE)
+    for (int o = 16; o > 0; o >>= 1) best = tmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ T red[5][NT / 32];
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][wid] = bsum;
+    red[1][wid] = m0;
+    red[2][wid] = m1;
+    red[3][wid] = m2;
+    red[4][wid] = best;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T b = red[0][0], r0 = red[1][0], r1 = red[2][0], r2 = red[3][0], r3 = red[4][0];
+    for (int w = 1; w < NT / 32; w++) {
+      b += red[0][w];
+      r0 = tmax(r0, red[1][w]);
+      r1 = tmax(r1, red[2][w]);
+      r2 = tmax(r2, red[3][w]);
+      r3 = tmin(r3, red[4][w]);
+    }
+    if (b != T(0)) atomicAdd(&p.ctl->bnd[STAGE == 2 ? 1 : 0], (double)b);
+    if (STAGE >= 2) {
+      if (g.mode == MWDG_ADAPTIVE) {
+        atomic_max_pos(&p.ctl->vmax[0], (double)r0);
+        atomic_max_pos(&p.ctl->vmax[1], (double)r1);
+        atomic_max_pos(&p.ctl->vmax[2], (double)r2);
+      } else if (r3 < tinf<T>()) {
+        atomic_min_pos(&p.ctl->dtmin, (double)r3);
+      }
+    }
+  }
+  if (STAGE >= 2) {
+    // the last block to finish closes the step (no waiting: each block takes
+    // a ticket after its own atomics are visible)
+    if (threadIdx.x == 0) __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = (atomicAdd(&p.ctl->blocks_done, 1u) == nblocks - 1);
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+      __threadfence();
+      end_step(g, p.ctl, STAGE == 3);
+    }
   }
 }
 
@@ -2300,71 +2439,205 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
     }
     if (STAGE >= 2) next_step_reduce<T>(g, p, l, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
   }
-  if (bad) p.ctl->nonfinite = 1;
-  // block sums in the coefficient type, one FP64 conversion and atomic per
-  // block; clip volumes (rare) in FP64 where they occur
-  for (int o = 16; o > 0; o >>= 1) {
-    bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
-    ncl += __shfl_xor_sync(0xffffffffu, ncl, o);
+  update_epilogue<T, STAGE, TPB>(g, p, bsum, csum, ncl, bad, m0, m1, m2, best, gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Uniform grids: one fused kernel per RK2 stage
+// ---------------------------------------------------------------------------
+// A block takes a tile of UniTile<T>::X x UniTile<T>::Y cells, one thread per
+// cell.  It reads the stage input and the bed planes (stage 1: and Manning
+// n) of the tile and a two-cell halo from HBM once into shared memory, and
+// (stage 1) applies the step's rain and friction there; it limits the tile
+// and its one-cell ring (the ring's limiter reads the second ring); then each
+// thread forms its cell's four interfaces from the flux views in shared
+// memory (revision, HLL, outflow limit) and updates the cell (Eq. 4a or 4b).
+// Nothing between the limiter and the update goes through HBM: stage 1
+// writes U_int and the stored view of the stage-1 input (which stage 2's
+// Eq. 4b combines), stage 2 writes U^{n+1}.  The arithmetic is that of the
+// leaf kernels (the same functions in the same order), so the results are
+// the same bit for bit.  Halo cells are read again by the neighbouring
+// tiles, through L2.
+template <typename T> struct UniTile;
+template <> struct UniTile<float> { static constexpr int X = 32, Y = 8, OCC = 2; };
+template <> struct UniTile<double> { static constexpr int X = 16, Y = 8, OCC = 2; };
+
+// the q-th cell of a tile's limited region ((TX + 2) x (TY + 2) cells,
+// coordinates from the ring's south-west corner): the tile's own cells
+// first (q < TX TY, so that thread q holds its own cell's stored view), then
+// the ring's north and south rows and its west and east columns
+template <int TX, int TY>
+__device__ __forceinline__ void uni_limited_cell(int q, int &lx, int &ly) {
+  constexpr int LX = TX + 2;
+  if (q < TX * TY) {
+    lx = 1 + q % TX;
+    ly = 1 + q / TX;
+    return;
   }
-  if (__any_sync(0xffffffffu, ncl != 0ULL)) {
-    for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
-    if ((threadIdx.x & 31) == 0 && ncl) {
-      atomicAdd(&p.ctl->n_clip, ncl);
-      atomicAdd(&p.ctl->v_clip, csum);
-    }
+  q -= TX * TY;
+  if (q < 2 * LX) {
+    lx = q % LX;
+    ly = (q < LX) ? TY + 1 : 0;
+    return;
   }
-  if (STAGE >= 2 && g.mode == MWDG_ADAPTIVE)
-    for (int o = 16; o > 0; o >>= 1) {
-      m0 = tmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-      m1 = tmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-      m2 = tmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+  q -= 2 * LX;
+  lx = (q < TY) ? 0 : LX - 1;
+  ly = 1 + q % TY;
+}
+
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(UniTile<T>::X * UniTile<T>::Y, UniTile<T>::OCC)
+    k_uni_stage(Geo g, Ptrs<T> p, const T *X, T *Wst_out, const T *Wcomb, T *Out) {
+  constexpr int TX = UniTile<T>::X, TY = UniTile<T>::Y, NT = TX * TY;
+  constexpr int RX = TX + 4, NR = RX * (TY + 4);   // loaded region: tile and two-cell halo
+  constexpr int LX = TX + 2, NL = LX * (TY + 2);   // limited region: tile and its ring
+  __shared__ T sR[12][NR];  // stage input (9; stage 1 after rain and friction) and bed planes (3)
+  __shared__ T sF[12][NL];  // flux views (9) and their bed planes (3)
+  if (!ctl_stepping(p.ctl)) return;  // a zero step changes nothing
+  const long long P = g.P;
+  const int nx = g.nxl[0], ny = g.nyl[0];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const T dt = ctl_dt<T>(p.ctl), gg = geo_g<T>(g), hd = geo_hd<T>(g);
+  const bool rain = STAGE == 1 && p.ctl->rain_on;
+  const T rinc = ctl_rain<T>(p.ctl);
+  // 1. the region from HBM (rows of RX consecutive cells per coefficient)
+  for (int r = threadIdx.x; r < NR; r += NT) {
+    const int i = i0 - 2 + r % RX, j = j0 - 2 + r / RX;
+    if (i < 0 || j < 0 || i >= nx || j >= ny) continue;
+    const long long k = (long long)j * nx + i;
+    T w[9];
+#pragma unroll
+    for (int m = 0; m < 9; m++) w[m] = X[m * P + k];
+#pragma unroll
+    for (int m = 0; m < 3; m++) sR[9 + m][r] = p.Z[m * P + k];
+    if (STAGE == 1) {
+      if (rain) w[0] = w[0] + rinc;
+      if (w[0] > hd) {
+        const T f = friction_factor(w[0], w[3], w[6], p.NM[k], dt, gg);
+#pragma unroll
+        for (int m = 3; m < 9; m++) w[m] = w[m] * f;
+      } else {
+#pragma unroll
+        for (int m = 3; m < 9; m++) w[m] = T(0);
+      }
     }
-  if (STAGE >= 2 && g.mode != MWDG_ADAPTIVE)
-    for (int o = 16; o > 0; o >>= 1) best = tmin(best, __shfl_xor_sync(0xffffffffu, best, o));
-  __shared__ T red[5][TPB / 32];
-  const int wid = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    red[0][wid] = bsum;
-    red[1][wid] = m0;
-    red[2][wid] = m1;
-    red[3][wid] = m2;
-    red[4][wid] = best;
+#pragma unroll
+    for (int m = 0; m < 9; m++) sR[m][r] = w[m];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    T b = red[0][0], r0 = red[1][0], r1 = red[2][0], r2 = red[3][0], r3 = red[4][0];
-    for (int w = 1; w < TPB / 32; w++) {
-      b += red[0][w];
-      r0 = tmax(r0, red[1][w]);
-      r1 = tmax(r1, red[2][w]);
-      r2 = tmax(r2, red[3][w]);
-      r3 = tmin(r3, red[4][w]);
+  // 2. limiting of the tile and its ring into flux views; each thread keeps
+  // its own cell's stored view
+  T ws_own[9];
+  for (int q = threadIdx.x; q < NL; q += NT) {
+    int lx, ly;
+    uni_limited_cell<TX, TY>(q, lx, ly);
+    const int i = i0 - 1 + lx, j = j0 - 1 + ly;
+    if (i < 0 || j < 0 || i >= nx || j >= ny) continue;
+    const int r = (ly + 1) * RX + (lx + 1);
+    T w[9], zp[3];
+#pragma unroll
+    for (int m = 0; m < 9; m++) w[m] = sR[m][r];
+#pragma unroll
+    for (int m = 0; m < 3; m++) zp[m] = sR[9 + m][r];
+    T ws[9], wf[9], ze[3];
+    if (!limit_reduced(g, w, zp, ws, wf, ze)) {
+      if (g.limiter) {
+        const bool has[4] = {i + 1 < nx, i > 0, j + 1 < ny, j > 0};
+        const int rn[4] = {r + 1, r - 1, r + RX, r - RX};
+        T nh[4], nq[4][2], nzb[4];
+#pragma unroll
+        for (int d = 0; d < 4; d++) {
+          const int rr = has[d] ? rn[d] : r;
+          nh[d] = sR[0][rr];
+          nq[d][0] = sR[3][rr];
+          nq[d][1] = sR[6][rr];
+          nzb[d] = sR[9][rr];
+        }
+        limit_minmod(g, w, zp, has, nh, nq, nzb, ws);
+      }
+#pragma unroll
+      for (int m = 0; m < 9; m++) wf[m] = ws[m];
     }
-    if (b != T(0)) atomicAdd(&p.ctl->bnd[STAGE == 2 ? 1 : 0], (double)b);
-    if (STAGE >= 2) {
-      if (g.mode == MWDG_ADAPTIVE) {
-        atomic_max_pos(&p.ctl->vmax[0], (double)r0);
-        atomic_max_pos(&p.ctl->vmax[1], (double)r1);
-        atomic_max_pos(&p.ctl->vmax[2], (double)r2);
-      } else if (r3 < tinf<T>()) {
-        atomic_min_pos(&p.ctl->dtmin, (double)r3);
+    const int li = ly * LX + lx;
+#pragma unroll
+    for (int m = 0; m < 9; m++) sF[m][li] = wf[m];
+#pragma unroll
+    for (int m = 0; m < 3; m++) sF[9 + m][li] = ze[m];
+    if (q < NT) {
+#pragma unroll
+      for (int m = 0; m < 9; m++) ws_own[m] = ws[m];
+      if (STAGE == 1) {
+        const long long k = (long long)j * nx + i;
+#pragma unroll
+        for (int m = 0; m < 9; m++) Wst_out[m * P + k] = ws[m];
       }
     }
   }
-  if (STAGE >= 2) {
-    // the last block to finish closes the step (no waiting: each block takes
-    // a ticket after its own atomics are visible)
-    if (threadIdx.x == 0) __threadfence();
-    __syncthreads();
-    __shared__ bool last;
-    if (threadIdx.x == 0) last = (atomicAdd(&p.ctl->blocks_done, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-      __threadfence();
-      end_step(g, p.ctl, STAGE == 3);
+  __syncthreads();
+  // 3. the cell's interfaces and its update
+  const ForceTime tf{p.ctl, STAGE == 2};
+  T bsum = T(0);
+  double csum = 0.0;
+  unsigned long long ncl = 0;
+  bool bad = false;
+  T m0 = T(0), m1 = T(0), m2 = T(0);
+  T best = tinf<T>();
+  const int i = i0 + threadIdx.x % TX, j = j0 + threadIdx.x / TX;
+  if (i < nx && j < ny) {
+    const long long k = (long long)j * nx + i;
+    const int li = (1 + threadIdx.x / TX) * LX + 1 + threadIdx.x % TX;
+    T w[9], zc[3];
+#pragma unroll
+    for (int m = 0; m < 9; m++) w[m] = sF[m][li];
+#pragma unroll
+    for (int m = 0; m < 3; m++) zc[m] = sF[9 + m][li];
+    const bool in[4] = {i + 1 < nx, i > 0, j + 1 < ny, j > 0};
+    const int ln[4] = {li + 1, li - 1, li + LX, li - LX};
+    T nb[4][4];
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+      if (!in[d]) continue;
+      const int fo = d ^ 1, q = ln[d];
+      nb[d][0] = first_face(sF[0][q], sF[1][q], sF[2][q], sF[9][q], fo);
+#pragma unroll
+      for (int v = 1; v < 3; v++) nb[d][v] = face_value(sF[3 * v][q], sF[3 * v + 1][q], sF[3 * v + 2][q], fo);
+      nb[d][3] = face_value(sF[9][q], sF[10][q], sF[11][q], fo);
     }
+    DirTerms<T> dx_, dy_;
+#pragma unroll
+    for (int dir = 0; dir < 2; dir++) {
+      const int fa_ = 2 * dir, fb_ = 2 * dir + 1;
+      FaceOut<T> fa = face_flux_nb(g, p, 0, i, j, w, zc, fa_, tf, in[fa_], nb[fa_], dt, [&](T av[3]) {
+        av[0] = sF[0][ln[fa_]]; av[1] = sF[3][ln[fa_]]; av[2] = sF[6][ln[fa_]];
+      });
+      bsum += fa.bout;
+      FaceOut<T> fb = face_flux_nb(g, p, 0, i, j, w, zc, fb_, tf, in[fb_], nb[fb_], dt, [&](T av[3]) {
+        av[0] = sF[0][ln[fb_]]; av[1] = sF[3][ln[fb_]]; av[2] = sF[6][ln[fb_]];
+      });
+      bsum += fb.bout;
+      dir_terms(dir == 0, fa, fb, gg, dir == 0 ? dx_ : dy_);
+    }
+    T o[3][3];
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+      T wc[3] = {T(0), T(0), T(0)};
+      if (STAGE == 2) {
+        const long long b0 = (long long)(3 * v) * P + k;
+        wc[0] = Wcomb[b0];
+        wc[1] = Wcomb[b0 + P];
+        wc[2] = Wcomb[b0 + 2 * P];
+      }
+      finish_var_vals<T, STAGE>(g, v, 0, w, zc, dx_, dy_, dt, ws_own + 3 * v, wc, o[v][0], o[v][1], o[v][2]);
+    }
+    const T h0n = o[0][0];
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+      post_var<T>(g, p, v, k, 0, h0n, o[v][0], o[v][1], o[v][2], ncl, csum, bad);
+      store_var(P, v, k, Out, o[v][0], o[v][1], o[v][2]);
+    }
+    if (STAGE == 2) next_step_reduce<T>(g, p, 0, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
   }
+  update_epilogue<T, STAGE, NT>(g, p, bsum, csum, ncl, bad, m0, m1, m2, best, gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -2856,6 +3129,17 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
   // uniform grids: leaf and neighbours from the thread index (no list or
   // code reads)
   const bool uni = (g.mode == MWDG_UNIFORM);
+  if (uni && stages == 2) {
+    // DG2 on a uniform grid: one fused kernel per stage
+    const dim3 grid((g.nxl[0] + UniTile<T>::X - 1) / UniTile<T>::X, (g.nyl[0] + UniTile<T>::Y - 1) / UniTile<T>::Y);
+    const int nt = UniTile<T>::X * UniTile<T>::Y;
+    MARK(KC_UPDATE1);
+    k_uni_stage<T, 1><<<grid, nt, 0, st>>>(g, p, p.U, p.Wn, nullptr, p.Ui);
+    MARK(KC_UPDATE2);
+    k_uni_stage<T, 2><<<grid, nt, 0, st>>>(g, p, p.Ui, nullptr, p.Wn, p.U);
+    MARK(-1);
+    return n + 2;
+  }
   for (int stage = 1; stage <= stages; stage++) {
     MARK(KC_LIMIT);
     const bool codes = (stage == 1 && begun);  // the step follows an adaptation
