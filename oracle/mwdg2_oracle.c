@@ -680,6 +680,33 @@ static void prolong_child(const double *sp /*3*/, int c, double *sc /*3*/) {
   }
 }
 
+/* Positivity of a refined leaf's depth (Sect. 2.1.1 and 2.3: the wet/dry
+ * treatment keeps depths non-negative; a leaf stored as a flat free surface
+ * over a steep bed, or one with a steep depth plane, would otherwise give
+ * children of negative average depth).  Before a depth plane sp is prolonged
+ * to its children, its slopes are scaled about its average so that none of
+ * the four children's averages is negative: the scaling limiter of Zhang &
+ * Shu (2010) applied at the children's centres.  A plane whose children are
+ * all non-negative is prolonged as it is; one without content loses its
+ * slopes. */
+static void depth_plane_for_children(double sp[3]) {
+  double m = INFINITY;
+  for (int c = 0; c < 4; c++) {
+    double sc[3];
+    prolong_child(sp, c, sc);
+    m = fmin(m, sc[0]);
+  }
+  if (!(m < 0.0)) return;
+  if (sp[0] > 0.0) {
+    double th = sp[0] / (sp[0] - m);
+    sp[1] = sp[1] * th;
+    sp[2] = sp[2] * th;
+  } else {
+    sp[1] = 0.0;
+    sp[2] = 0.0;
+  }
+}
+
 void orc_adapt(orc_sim *s) {
   int L = s->L;
   if (s->p.mode != ORC_ADAPTIVE || L == 0) return;
@@ -704,7 +731,10 @@ void orc_adapt(orc_sim *s) {
         for (int v = 0; v < 3; v++) {
           double sp[3], sc[3];
           for (int m = 0; m < 3; m++) sp[m] = s->U[l - 1][(3 * v + m) * np + kp];
+          if (v == 0) depth_plane_for_children(sp);
           prolong_child(sp, c, sc);
+          /* rounding residue of a child brought to zero depth */
+          if (v == 0) sc[0] = fmax(sc[0], 0.0);
           for (int m = 0; m < 3; m++) s->U[l][(3 * v + m) * n + k] = sc[m];
         }
       }

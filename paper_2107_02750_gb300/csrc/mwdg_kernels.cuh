@@ -1257,8 +1257,34 @@ __device__ __noinline__ void coarse_flags(const Geo &g, const Ptrs<T> &p, int ta
 // leaf's plane (one level at a time, flow in depth form).  Each block counts
 // its new leaves (the scatter turns the counts into offsets), and every new
 // leaf contributes its CFL candidate for the coming step.
+// The depth plane (s0, s1x, s1y) of a parent before it is prolonged to its
+// children: its slopes scaled about the average so that no child's average
+// is negative (the wet/dry treatment keeps depths non-negative; scaling
+// limiter of Zhang & Shu 2010 at the children's centres), or dropped when
+// the parent holds no water; unchanged when every child is non-negative.
+template <typename T>
+__device__ __forceinline__ void depth_plane_for_children(T &s0, T &s1x, T &s1y) {
+  T m = tinf<T>();
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    T o[3];
+    prolong3(s0, s1x, s1y, c, o);
+    m = tmin(m, o[0]);
+  }
+  if (!(m < T(0))) return;
+  if (s0 > T(0)) {
+    const T th = s0 / (s0 - m);
+    s1x = s1x * th;
+    s1y = s1y * th;
+  } else {
+    s1x = T(0);
+    s1y = T(0);
+  }
+}
+
 // prolongation (Eq. 10) into new leaf k (level l, i, j) from the old leaf
-// above it (flow in depth form, one level at a time)
+// above it (flow in depth form, one level at a time; the depth plane kept
+// non-negative at every level)
 template <typename T>
 __device__ __noinline__ void prolong_from_old_leaf(const Geo &g, const Ptrs<T> &p, long long k, int l, int i,
                                                    int j) {
@@ -1287,7 +1313,9 @@ __device__ __noinline__ void prolong_from_old_leaf(const Geo &g, const Ptrs<T> &
     if (v == 0) slopes_to_h(sv[1], sv[2], za1, za2);
     for (int qq = d - 1; qq >= 0; qq--) {  // child at level l - qq: bits qq of i and j
       T o[3];
+      if (v == 0) depth_plane_for_children(sv[0], sv[1], sv[2]);
       prolong3(sv[0], sv[1], sv[2], ((i >> qq) & 1) + 2 * ((j >> qq) & 1), o);
+      if (v == 0) o[0] = tmax(o[0], T(0));  // rounding residue brought to zero depth
       sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
     }
     if (v == 0) slopes_from_h(sv[1], sv[2], zk1, zk2);
@@ -2459,7 +2487,7 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
 // the same bit for bit.  Halo cells are read again by the neighbouring
 // tiles, through L2.
 template <typename T> struct UniTile;
-template <> struct UniTile<float> { static constexpr int X = 32, Y = 8, OCC = 2; };
+template <> struct UniTile<float> { static constexpr int X = 32, Y = 8, OCC = 3; };
 template <> struct UniTile<double> { static constexpr int X = 16, Y = 8, OCC = 2; };
 
 // the q-th cell of a tile's limited region ((TX + 2) x (TY + 2) cells,
@@ -2491,90 +2519,16 @@ __global__ void __launch_bounds__(UniTile<T>::X * UniTile<T>::Y, UniTile<T>::OCC
   constexpr int TX = UniTile<T>::X, TY = UniTile<T>::Y, NT = TX * TY;
   constexpr int RX = TX + 4, NR = RX * (TY + 4);   // loaded region: tile and two-cell halo
   constexpr int LX = TX + 2, NL = LX * (TY + 2);   // limited region: tile and its ring
-  __shared__ T sR[12][NR];  // stage input (9; stage 1 after rain and friction) and bed planes (3)
-  __shared__ T sF[12][NL];  // flux views (9) and their bed planes (3)
+  __shared__ T sR[12][NR];   // stage input (9; stage 1 after rain and friction) and bed planes (3)
+  __shared__ T sF[12][NL];   // flux views (9) and their bed planes (3)
+  __shared__ T sW[STAGE == 2 ? 9 : 1][STAGE == 2 ? NT : 1];  // stage 2: the tile's stage-1 stored view
   if (!ctl_stepping(p.ctl)) return;  // a zero step changes nothing
   const long long P = g.P;
   const int nx = g.nxl[0], ny = g.nyl[0];
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tiles_x = (nx + TX - 1) / TX, tiles = tiles_x * ((ny + TY - 1) / TY);
   const T dt = ctl_dt<T>(p.ctl), gg = geo_g<T>(g), hd = geo_hd<T>(g);
   const bool rain = STAGE == 1 && p.ctl->rain_on;
   const T rinc = ctl_rain<T>(p.ctl);
-  // 1. the region from HBM (rows of RX consecutive cells per coefficient)
-  for (int r = threadIdx.x; r < NR; r += NT) {
-    const int i = i0 - 2 + r % RX, j = j0 - 2 + r / RX;
-    if (i < 0 || j < 0 || i >= nx || j >= ny) continue;
-    const long long k = (long long)j * nx + i;
-    T w[9];
-#pragma unroll
-    for (int m = 0; m < 9; m++) w[m] = X[m * P + k];
-#pragma unroll
-    for (int m = 0; m < 3; m++) sR[9 + m][r] = p.Z[m * P + k];
-    if (STAGE == 1) {
-      if (rain) w[0] = w[0] + rinc;
-      if (w[0] > hd) {
-        const T f = friction_factor(w[0], w[3], w[6], p.NM[k], dt, gg);
-#pragma unroll
-        for (int m = 3; m < 9; m++) w[m] = w[m] * f;
-      } else {
-#pragma unroll
-        for (int m = 3; m < 9; m++) w[m] = T(0);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < 9; m++) sR[m][r] = w[m];
-  }
-  __syncthreads();
-  // 2. limiting of the tile and its ring into flux views; each thread keeps
-  // its own cell's stored view
-  T ws_own[9];
-  for (int q = threadIdx.x; q < NL; q += NT) {
-    int lx, ly;
-    uni_limited_cell<TX, TY>(q, lx, ly);
-    const int i = i0 - 1 + lx, j = j0 - 1 + ly;
-    if (i < 0 || j < 0 || i >= nx || j >= ny) continue;
-    const int r = (ly + 1) * RX + (lx + 1);
-    T w[9], zp[3];
-#pragma unroll
-    for (int m = 0; m < 9; m++) w[m] = sR[m][r];
-#pragma unroll
-    for (int m = 0; m < 3; m++) zp[m] = sR[9 + m][r];
-    T ws[9], wf[9], ze[3];
-    if (!limit_reduced(g, w, zp, ws, wf, ze)) {
-      if (g.limiter) {
-        const bool has[4] = {i + 1 < nx, i > 0, j + 1 < ny, j > 0};
-        const int rn[4] = {r + 1, r - 1, r + RX, r - RX};
-        T nh[4], nq[4][2], nzb[4];
-#pragma unroll
-        for (int d = 0; d < 4; d++) {
-          const int rr = has[d] ? rn[d] : r;
-          nh[d] = sR[0][rr];
-          nq[d][0] = sR[3][rr];
-          nq[d][1] = sR[6][rr];
-          nzb[d] = sR[9][rr];
-        }
-        limit_minmod(g, w, zp, has, nh, nq, nzb, ws);
-      }
-#pragma unroll
-      for (int m = 0; m < 9; m++) wf[m] = ws[m];
-    }
-    const int li = ly * LX + lx;
-#pragma unroll
-    for (int m = 0; m < 9; m++) sF[m][li] = wf[m];
-#pragma unroll
-    for (int m = 0; m < 3; m++) sF[9 + m][li] = ze[m];
-    if (q < NT) {
-#pragma unroll
-      for (int m = 0; m < 9; m++) ws_own[m] = ws[m];
-      if (STAGE == 1) {
-        const long long k = (long long)j * nx + i;
-#pragma unroll
-        for (int m = 0; m < 9; m++) Wst_out[m * P + k] = ws[m];
-      }
-    }
-  }
-  __syncthreads();
-  // 3. the cell's interfaces and its update
   const ForceTime tf{p.ctl, STAGE == 2};
   T bsum = T(0);
   double csum = 0.0;
@@ -2582,62 +2536,150 @@ __global__ void __launch_bounds__(UniTile<T>::X * UniTile<T>::Y, UniTile<T>::OCC
   bool bad = false;
   T m0 = T(0), m1 = T(0), m2 = T(0);
   T best = tinf<T>();
-  const int i = i0 + threadIdx.x % TX, j = j0 + threadIdx.x / TX;
-  if (i < nx && j < ny) {
-    const long long k = (long long)j * nx + i;
-    const int li = (1 + threadIdx.x / TX) * LX + 1 + threadIdx.x % TX;
-    T w[9], zc[3];
+  // the block strides over the tiles (so that the step's per-block reductions
+  // and completion ticket stay few)
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int i0 = (tile % tiles_x) * TX, j0 = (tile / tiles_x) * TY;
+    // 1. the region from HBM (rows of RX consecutive cells per coefficient)
+    for (int r = threadIdx.x; r < NR; r += NT) {
+      const int i = i0 - 2 + r % RX, j = j0 - 2 + r / RX;
+      if (i < 0 || j < 0 || i >= nx || j >= ny) continue;
+      const long long k = (long long)j * nx + i;
+      T w[9];
 #pragma unroll
-    for (int m = 0; m < 9; m++) w[m] = sF[m][li];
+      for (int m = 0; m < 9; m++) w[m] = X[m * P + k];
 #pragma unroll
-    for (int m = 0; m < 3; m++) zc[m] = sF[9 + m][li];
-    const bool in[4] = {i + 1 < nx, i > 0, j + 1 < ny, j > 0};
-    const int ln[4] = {li + 1, li - 1, li + LX, li - LX};
-    T nb[4][4];
+      for (int m = 0; m < 3; m++) sR[9 + m][r] = p.Z[m * P + k];
+      if (STAGE == 1) {
+        if (rain) w[0] = w[0] + rinc;
+        if (w[0] > hd) {
+          const T f = friction_factor(w[0], w[3], w[6], p.NM[k], dt, gg);
 #pragma unroll
-    for (int d = 0; d < 4; d++) {
-      if (!in[d]) continue;
-      const int fo = d ^ 1, q = ln[d];
-      nb[d][0] = first_face(sF[0][q], sF[1][q], sF[2][q], sF[9][q], fo);
+          for (int m = 3; m < 9; m++) w[m] = w[m] * f;
+        } else {
 #pragma unroll
-      for (int v = 1; v < 3; v++) nb[d][v] = face_value(sF[3 * v][q], sF[3 * v + 1][q], sF[3 * v + 2][q], fo);
-      nb[d][3] = face_value(sF[9][q], sF[10][q], sF[11][q], fo);
-    }
-    DirTerms<T> dx_, dy_;
-#pragma unroll
-    for (int dir = 0; dir < 2; dir++) {
-      const int fa_ = 2 * dir, fb_ = 2 * dir + 1;
-      FaceOut<T> fa = face_flux_nb(g, p, 0, i, j, w, zc, fa_, tf, in[fa_], nb[fa_], dt, [&](T av[3]) {
-        av[0] = sF[0][ln[fa_]]; av[1] = sF[3][ln[fa_]]; av[2] = sF[6][ln[fa_]];
-      });
-      bsum += fa.bout;
-      FaceOut<T> fb = face_flux_nb(g, p, 0, i, j, w, zc, fb_, tf, in[fb_], nb[fb_], dt, [&](T av[3]) {
-        av[0] = sF[0][ln[fb_]]; av[1] = sF[3][ln[fb_]]; av[2] = sF[6][ln[fb_]];
-      });
-      bsum += fb.bout;
-      dir_terms(dir == 0, fa, fb, gg, dir == 0 ? dx_ : dy_);
-    }
-    T o[3][3];
-#pragma unroll
-    for (int v = 0; v < 3; v++) {
-      T wc[3] = {T(0), T(0), T(0)};
-      if (STAGE == 2) {
-        const long long b0 = (long long)(3 * v) * P + k;
-        wc[0] = Wcomb[b0];
-        wc[1] = Wcomb[b0 + P];
-        wc[2] = Wcomb[b0 + 2 * P];
+          for (int m = 3; m < 9; m++) w[m] = T(0);
+        }
       }
-      finish_var_vals<T, STAGE>(g, v, 0, w, zc, dx_, dy_, dt, ws_own + 3 * v, wc, o[v][0], o[v][1], o[v][2]);
-    }
-    const T h0n = o[0][0];
 #pragma unroll
-    for (int v = 0; v < 3; v++) {
-      post_var<T>(g, p, v, k, 0, h0n, o[v][0], o[v][1], o[v][2], ncl, csum, bad);
-      store_var(P, v, k, Out, o[v][0], o[v][1], o[v][2]);
+      for (int m = 0; m < 9; m++) sR[m][r] = w[m];
     }
-    if (STAGE == 2) next_step_reduce<T>(g, p, 0, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
+    if (STAGE == 2) {
+      const int i = i0 + threadIdx.x % TX, j = j0 + threadIdx.x / TX;
+      if (i < nx && j < ny) {
+        const long long k = (long long)j * nx + i;
+#pragma unroll
+        for (int m = 0; m < 9; m++) sW[m][threadIdx.x] = Wcomb[m * P + k];
+      }
+    }
+    __syncthreads();
+    // 2. limiting of the tile and its ring into flux views; each thread keeps
+    // its own cell's stored view
+    T ws_own[9];
+    for (int q = threadIdx.x; q < NL; q += NT) {
+      int lx, ly;
+      uni_limited_cell<TX, TY>(q, lx, ly);
+      const int i = i0 - 1 + lx, j = j0 - 1 + ly;
+      if (i < 0 || j < 0 || i >= nx || j >= ny) continue;
+      const int r = (ly + 1) * RX + (lx + 1);
+      T w[9], zp[3];
+#pragma unroll
+      for (int m = 0; m < 9; m++) w[m] = sR[m][r];
+#pragma unroll
+      for (int m = 0; m < 3; m++) zp[m] = sR[9 + m][r];
+      T ws[9], wf[9], ze[3];
+      if (!limit_reduced(g, w, zp, ws, wf, ze)) {
+        if (g.limiter) {
+          const bool has[4] = {i + 1 < nx, i > 0, j + 1 < ny, j > 0};
+          const int rn[4] = {r + 1, r - 1, r + RX, r - RX};
+          T nh[4], nq[4][2], nzb[4];
+#pragma unroll
+          for (int d = 0; d < 4; d++) {
+            const int rr = has[d] ? rn[d] : r;
+            nh[d] = sR[0][rr];
+            nq[d][0] = sR[3][rr];
+            nq[d][1] = sR[6][rr];
+            nzb[d] = sR[9][rr];
+          }
+          limit_minmod(g, w, zp, has, nh, nq, nzb, ws);
+        }
+#pragma unroll
+        for (int m = 0; m < 9; m++) wf[m] = ws[m];
+      }
+      const int li = ly * LX + lx;
+#pragma unroll
+      for (int m = 0; m < 9; m++) sF[m][li] = wf[m];
+#pragma unroll
+      for (int m = 0; m < 3; m++) sF[9 + m][li] = ze[m];
+      if (q < NT) {
+#pragma unroll
+        for (int m = 0; m < 9; m++) ws_own[m] = ws[m];
+        if (STAGE == 1) {
+          const long long k = (long long)j * nx + i;
+#pragma unroll
+          for (int m = 0; m < 9; m++) Wst_out[m * P + k] = ws[m];
+        }
+      }
+    }
+    __syncthreads();
+    // 3. the cell's interfaces and its update
+    const int i = i0 + threadIdx.x % TX, j = j0 + threadIdx.x / TX;
+    if (i < nx && j < ny) {
+      const long long k = (long long)j * nx + i;
+      const int li = (1 + threadIdx.x / TX) * LX + 1 + threadIdx.x % TX;
+      T w[9], zc[3];
+#pragma unroll
+      for (int m = 0; m < 9; m++) w[m] = sF[m][li];
+#pragma unroll
+      for (int m = 0; m < 3; m++) zc[m] = sF[9 + m][li];
+      const bool in[4] = {i + 1 < nx, i > 0, j + 1 < ny, j > 0};
+      const int ln[4] = {li + 1, li - 1, li + LX, li - LX};
+      T nb[4][4];
+#pragma unroll
+      for (int d = 0; d < 4; d++) {
+        if (!in[d]) continue;
+        const int fo = d ^ 1, q = ln[d];
+        nb[d][0] = first_face(sF[0][q], sF[1][q], sF[2][q], sF[9][q], fo);
+#pragma unroll
+        for (int v = 1; v < 3; v++) nb[d][v] = face_value(sF[3 * v][q], sF[3 * v + 1][q], sF[3 * v + 2][q], fo);
+        nb[d][3] = face_value(sF[9][q], sF[10][q], sF[11][q], fo);
+      }
+      DirTerms<T> dx_, dy_;
+#pragma unroll
+      for (int dir = 0; dir < 2; dir++) {
+        const int fa_ = 2 * dir, fb_ = 2 * dir + 1;
+        FaceOut<T> fa = face_flux_nb(g, p, 0, i, j, w, zc, fa_, tf, in[fa_], nb[fa_], dt, [&](T av[3]) {
+          av[0] = sF[0][ln[fa_]]; av[1] = sF[3][ln[fa_]]; av[2] = sF[6][ln[fa_]];
+        });
+        bsum += fa.bout;
+        FaceOut<T> fb = face_flux_nb(g, p, 0, i, j, w, zc, fb_, tf, in[fb_], nb[fb_], dt, [&](T av[3]) {
+          av[0] = sF[0][ln[fb_]]; av[1] = sF[3][ln[fb_]]; av[2] = sF[6][ln[fb_]];
+        });
+        bsum += fb.bout;
+        dir_terms(dir == 0, fa, fb, gg, dir == 0 ? dx_ : dy_);
+      }
+      T o[3][3];
+#pragma unroll
+      for (int v = 0; v < 3; v++) {
+        T wc[3] = {T(0), T(0), T(0)};
+        if (STAGE == 2) {
+          wc[0] = sW[3 * v][threadIdx.x];
+          wc[1] = sW[3 * v + 1][threadIdx.x];
+          wc[2] = sW[3 * v + 2][threadIdx.x];
+        }
+        finish_var_vals<T, STAGE>(g, v, 0, w, zc, dx_, dy_, dt, ws_own + 3 * v, wc, o[v][0], o[v][1], o[v][2]);
+      }
+      const T h0n = o[0][0];
+#pragma unroll
+      for (int v = 0; v < 3; v++) {
+        post_var<T>(g, p, v, k, 0, h0n, o[v][0], o[v][1], o[v][2], ncl, csum, bad);
+        store_var(P, v, k, Out, o[v][0], o[v][1], o[v][2]);
+      }
+      if (STAGE == 2) next_step_reduce<T>(g, p, 0, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
+    }
+    __syncthreads();  // the shared arrays are refilled by the next tile
   }
-  update_epilogue<T, STAGE, NT>(g, p, bsum, csum, ncl, bad, m0, m1, m2, best, gridDim.x * gridDim.y);
+  update_epilogue<T, STAGE, NT>(g, p, bsum, csum, ncl, bad, m0, m1, m2, best, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -3131,7 +3173,13 @@ int Launch<T>::step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_
   const bool uni = (g.mode == MWDG_UNIFORM);
   if (uni && stages == 2) {
     // DG2 on a uniform grid: one fused kernel per stage
-    const dim3 grid((g.nxl[0] + UniTile<T>::X - 1) / UniTile<T>::X, (g.nyl[0] + UniTile<T>::Y - 1) / UniTile<T>::Y);
+    const long long tiles = (long long)((g.nxl[0] + UniTile<T>::X - 1) / UniTile<T>::X) *
+                            ((g.nyl[0] + UniTile<T>::Y - 1) / UniTile<T>::Y);
+    // one resident wave of blocks, each striding over the tiles
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<long long>(tiles, (long long)std::max(sms, 1) * UniTile<T>::OCC);
     const int nt = UniTile<T>::X * UniTile<T>::Y;
     MARK(KC_UPDATE1);
     k_uni_stage<T, 1><<<grid, nt, 0, st>>>(g, p, p.U, p.Wn, nullptr, p.Ui);

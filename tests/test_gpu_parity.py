@@ -290,6 +290,22 @@ def test_valley_window_through_the_inflow_mwdg2_10min_f64():
     assert v["v_in"] > 4.0e4
 
 
+@pytest.mark.parametrize("mode", [S.UNIFORM, S.ADAPTIVE])
+def test_valley_window_2h_keeps_depths_nonnegative_f64(mode):
+    """The valley window through the inflow over the configuration's whole 2 h
+    (the hydrograph's rise, peak and recession; MWDG2 refines and coarsens
+    around the shrinking flood): no depth is clipped and the mass budget
+    closes to round-off with no clipped volume in it."""
+    from dataclasses import replace
+    full = S.valley(n=1024)
+    p = replace(S.crop(full, 0, 1024 // 2 - 128, 256, 256, L=8 if mode == S.ADAPTIVE else 0), mode=mode)
+    g = gpu_sim(p)
+    g.run_to_time(7200.0)
+    v = g.get_volume()
+    assert v["n_clip"] == 0 and v["v_clip"] == 0.0
+    assert abs(v["volume"] - (v["v_in"] - v["v_out"])) <= 1e-11 * v["v_in"]
+
+
 def test_full_valley_benchmark_configuration_f64():
     """The benchmark's own configuration: the 1024 x 1024 valley at L = 10,
     eps = 1e-3 (five levels of 16 x 16 MRA tiles, a coarse tail of 341 nodes
@@ -307,7 +323,7 @@ def test_full_valley_benchmark_configuration_f64():
             assert_same_leaves(g, o, what=f"step {k + 1}")
     lev, _, _, c = g.read_active()
     assert len(np.unique(lev)) >= 2 and len(lev) > 200000
-    assert (c[:, 0] > 1e-3).sum() > 50
+    assert (c[:, 0] > 1e-3).sum() > 10  # the flood has entered
     assert g.get_volume()["n_clip"] == 0
 
 
