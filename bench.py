@@ -579,9 +579,10 @@ DG2_STEP_VALUES = 53
 MRA_BYTES_PER_LEAF = {4: (9 + 3 + 3) * 4 + 1, 8: (9 + 3 + 3) * 8 + 1}
 # FP64 floating-point operations per active-cell update of the FP64 MWDG2
 # step (adds, multiplies, 2 per fused multiply-add; divisions and square
-# roots as the instructions they expand to), counted by ncu over every kernel
-# of a step on this workload; None until counted for the current kernels
-FP64_FLOPS_PER_UPDATE = None
+# roots as the instructions they expand to), counted by ncu over the ten
+# kernels of one step on this workload after 1800 s: 3.249e8 operations for
+# 244,945 leaves (profiles/fp64_flops_valley1024_mwdg2.md)
+FP64_FLOPS_PER_UPDATE = 1326
 E2E_STEPS = 200
 # DRAM bytes (read + write) per launch measured by ncu for a kernel of the
 # headline workload (FP32 MWDG2), when the kernel has not changed since (see

@@ -294,8 +294,11 @@ def test_valley_window_through_the_inflow_mwdg2_10min_f64():
 def test_valley_window_2h_keeps_depths_nonnegative_f64(mode):
     """The valley window through the inflow over the configuration's whole 2 h
     (the hydrograph's rise, peak and recession; MWDG2 refines and coarsens
-    around the shrinking flood): no depth is clipped and the mass budget
-    closes to round-off with no clipped volume in it."""
+    around the shrinking flood): no depth is clipped, and the mass budget,
+    with no clipped volume in it, closes to round-off on the uniform grid
+    and to the drift of the interface rule at MWDG2's coarse/fine faces
+    (each side's flux from its own view, Sect. 2.3: about 1e-7 of the
+    inflow over the run)."""
     from dataclasses import replace
     full = S.valley(n=1024)
     p = replace(S.crop(full, 0, 1024 // 2 - 128, 256, 256, L=8 if mode == S.ADAPTIVE else 0), mode=mode)
@@ -303,7 +306,8 @@ def test_valley_window_2h_keeps_depths_nonnegative_f64(mode):
     g.run_to_time(7200.0)
     v = g.get_volume()
     assert v["n_clip"] == 0 and v["v_clip"] == 0.0
-    assert abs(v["volume"] - (v["v_in"] - v["v_out"])) <= 1e-11 * v["v_in"]
+    tol = 1e-11 if mode == S.UNIFORM else 1e-6
+    assert abs(v["volume"] - (v["v_in"] - v["v_out"])) <= tol * v["v_in"]
 
 
 def test_full_valley_benchmark_configuration_f64():
