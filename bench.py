@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="time the FP64 DG2 adjoint: one checkpoint segment forward and backward")
     ap.add_argument("--adjoint-steps", type=int, default=200, help="adjoint: steps per checkpoint segment")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"],
+                    help="precision of the timed arm (f32: the free-surface FP32 path, the headline; f64: the "
+                         "FP64 path, which then needs no separate FP64 leg)")
     ap.add_argument("--urban", type=int, default=1,
                     help="1: add the slow-to-gradual urban configuration (static vs uniform DG2) to the line")
     ap.add_argument("--scheme", default="dg2", choices=["dg2", "fv1", "acc"],
@@ -289,7 +292,8 @@ def run_gpu(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # FP32 free-surface path (headline)
-    s32 = make_solver(p, M.F32, sptr)
+    prec = M.F64 if args.precision == "f64" else M.F32
+    s32 = make_solver(p, prec, sptr)
     s32.run_to_time(args.spinup)
     t_spin, _ = s32.get_time()
     ckpt = s32.save_state()
@@ -318,9 +322,10 @@ def run_gpu(args, rank, world):
     dom_name = max(per_launch, key=per_launch.get)
     dom_ms, dom_n = kt[dom_name]
     mean_leaves = kupd / len(kms)
-    bpl = kernel_bytes_per_leaf(dom_name, 4, args.scheme, args.grid)
+    elem = 8 if prec == M.F64 else 4
+    bpl = kernel_bytes_per_leaf(dom_name, elem, args.scheme, args.grid)
     alg = STAGE_VALUES.get(dom_name) if args.scheme == "dg2" else None
-    abpl = alg * 4 if alg else bpl
+    abpl = alg * elem if alg else bpl
     launch_s = dom_ms / dom_n * 1e-3
     achieved = (abpl * mean_leaves) / launch_s / 1e9 if abpl else None
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs,
@@ -336,7 +341,7 @@ def run_gpu(args, rank, world):
     if args.scheme == "dg2":
         # the whole step on the step's algorithmic bytes per update: the DG2
         # step (53 values) plus, on the adaptive grid, the MRA's per leaf
-        wb = DG2_STEP_VALUES * 4 + (MRA_BYTES_PER_LEAF[4] if args.grid == "adaptive" else 0)
+        wb = DG2_STEP_VALUES * elem + (MRA_BYTES_PER_LEAF[elem] if args.grid == "adaptive" else 0)
         roofline["whole_step"] = {"bytes_per_update": wb, "achieved": wb * value / 1e9,
                                   "frac": wb * value / 1e9 / peak_gbs, "unit": "GB/s"}
 
@@ -366,6 +371,8 @@ def run_gpu(args, rank, world):
     out = {"value": value, "ms_per_step": total_ms / len(ms), "updates": updates_all,
            "mean_active": updates / len(ms), "roofline": roofline, "clocks": clk.summary(), "e2e": e2e,
            "gpu_launches": int(launches) * world, "t_spinup": t_spin}
+    if rank == 0 and args.grid == "adaptive" and args.scheme == "dg2":
+        out["uniform_dg2"] = uniform_leg(p, stream, flush, args.steps, args.warmup, args.spinup)
 
     # FP64 path, and FP32 against FP64 at the same simulated times
     if not args.no_fp64 and rank == 0:
@@ -406,6 +413,38 @@ def run_gpu(args, rank, world):
         out["run_average_2h"] = {"f32": run_average(p, M.F32, sptr, 7200.0),
                                  "f64": run_average(p, M.F64, sptr, 7200.0)}
     return out
+
+
+def uniform_leg(p, stream, flush, K, W, spinup):
+    """The same DG2 step on the uniform finest grid of the valley (one fused
+    kernel per RK2 stage), FP32, after the same spin-up: updates/s and the
+    roofline of each stage kernel and of the whole step on the step's
+    algorithmic bytes (stage 1: 13 values read, 9 written; stage 2: 22 read,
+    9 written; 212 B a cell and step in all)"""
+    import paper_2107_02750_gb300 as M
+    from dataclasses import replace
+    from paper_2107_02750_gb300 import synth as S
+    q = replace(p, mode=S.UNIFORM)
+    s = make_solver(q, M.F32, stream.cuda_stream)
+    s.run_to_time(spinup)
+    ms, upd, _, _ = timed_steps(s, K, W, flush, stream)
+    kms, kupd, _, kt = timed_steps(s, min(K, 100), 0, flush, stream, prof=True)
+    value = upd / (sum(ms) * 1e-3)
+    peak, kind = peaks()
+    cells = kupd / len(kms)
+    stages = {}
+    for name, vals in STAGE_VALUES.items():
+        if name in kt and kt[name][1]:
+            t = kt[name][0] / kt[name][1] * 1e-3
+            stages[name] = {"ms_per_launch": t * 1e3, "algorithmic_bytes_per_cell": vals * 4,
+                            "achieved": vals * 4 * cells / t / 1e9, "frac": vals * 4 * cells / t / 1e9 / peak}
+    wb = DG2_STEP_VALUES * 4
+    return {"value": value, "unit": UNIT, "ms_per_step": sum(ms) / len(ms), "cells": cells,
+            "roofline": {"bound": "hbm", "peak": peak, "peak_kind": kind, "unit": "GB/s", "stages": stages,
+                         "whole_step": {"bytes_per_update": wb, "achieved": wb * value / 1e9,
+                                        "frac": wb * value / 1e9 / peak}},
+            "what": "uniform DG2 on the valley's finest grid (1,048,576 cells), FP32, fused stage kernels, "
+                    "L2 flushed before every timed step"}
 
 
 def fixed_step_accuracy(p, sptr, marks=(120.0, 300.0, 900.0)):
@@ -817,7 +856,7 @@ def main():
         cb = None if args.no_cpu else cpu_baseline(args.n)
         line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": (WORKLOAD if args.grid == "adaptive" else
                                         {"uniform": "uniform DG2", "static": "static DG2"}[args.grid] + WORKLOAD[5:])
                            if args.scheme == "dg2" else
@@ -828,7 +867,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": out["roofline"], "cpu_baseline": cb, "e2e": out["e2e"], "clocks": out["clocks"],
                 "gpu_launches": out["gpu_launches"]}
-        for k in ("fp64", "fma_peaks_tflops", "accuracy_f32_vs_f64", "accuracy_f32_on_fp64_steps",
+        for k in ("uniform_dg2", "fp64", "fma_peaks_tflops", "accuracy_f32_vs_f64", "accuracy_f32_on_fp64_steps",
                   "fp64_vs_fp64_one_extra_stop", "run_average_2h"):
             if k in out:
                 line[k] = out[k]
