@@ -624,9 +624,9 @@ MRA_BYTES_PER_LEAF = {4: (9 + 3 + 3) * 4 + 1, 8: (9 + 3 + 3) * 8 + 1}
 FP64_FLOPS_PER_UPDATE = 1326
 E2E_STEPS = 200
 # DRAM bytes (read + write) per launch measured by ncu for a kernel of the
-# headline workload (FP32 MWDG2), when the kernel has not changed since (see
-# profiles/); empty while the kernels differ from the captured ones
-TRAFFIC = {}
+# headline workload (FP32 MWDG2), when the kernel has not changed since
+# (profiles/mwdg2_valley1024_f32_launches.md); absent while it has
+TRAFFIC = {"dg2_update_stage2": 58_214_912 + 2_988_544}
 
 
 def run_ensemble(args):
@@ -778,8 +778,9 @@ ADJ_VALUES_PER_CELL = {"friction": 19, "limit": 33, "update": 34.5, "cfl": 3, "r
 ADJ_FLAG_BYTES = {"update": 1, "rev_face": 1, "rev_limit": 1}
 # DRAM bytes (read + write) per launch measured by ncu for the FP32 adjoint
 # kernels at this workload, while the kernel is unchanged (see profiles/)
-ADJ_TRAFFIC = {"update": 108_080_000 + 33_630_000,     # ncu: mean of 6 stage launches, dram read + write
-               "rev_face": 64_010_000 * 2 + 4_800_000 + 3_190_000}  # ncu: the x and y kernels of a stage
+# (captured before the interfaces' outflow limit was added to these kernels:
+# none is current, so the adjoint line reports no traffic)
+ADJ_TRAFFIC = {}
 
 
 def adjoint_roofline(times, cells, elem):
