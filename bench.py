@@ -358,7 +358,7 @@ def run_gpu(args, rank, world):
     _, u1 = s32.get_counters()
     n_e2e = u1 - u0
     import ctypes as C
-    st = s32._lib.mwdg_read_fields(s32._h, *(C.cast(C.c_void_p(b.data_ptr()), C.POINTER(C.c_double)) for b in hbuf))
+    st = s32._lib.mwdg_read_fields(s32._h, *(C.cast(C.c_void_p(b.data_ptr()), C.POINTER(C.c_double)) for b in hbuf), 0)
     if st:
         raise RuntimeError("mwdg_read_fields failed")
     e2e_s = time.perf_counter() - t0

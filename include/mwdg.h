@@ -107,27 +107,43 @@ MWDG_API mwdg_status mwdg_params_default(mwdg_params *p);
 MWDG_API mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out);
 MWDG_API void mwdg_destroy(mwdg_ctx *ctx);
 
-/* Topography from a vertex raster z_vert[(ny+1)(nx+1)] (host): planar
+/* Rasters are row-major, row j south to north, column i west to east, with
+ * a row stride ld in elements (ld >= the row length; ld = 0: rows packed).
+ * Host rasters are copied in and stay the caller's.  The _dev variants take
+ * device pointers of the current device (e.g. torch data_ptr()s), read on
+ * the context's stream; the caller keeps ownership and must not change them
+ * until the call returns (every load synchronises the context's stream).
+ * A raster with a non-finite value gives MWDG_ERR_NONFINITE (device rasters
+ * are checked on the device); ld below the row length MWDG_ERR_ARG. */
+
+/* Topography from a vertex raster z_vert[(ny+1) rows x (nx+1)]: planar
  * coefficients by Eq. 8 on the finest grid (the interface-centre values are
  * means of the two vertices, so z is continuous at interface centres), the
  * full static pyramid by Eq. 9 and each node's normalised topography detail
- * max|d| / max(1, max|z0|) (Sect. 2.2).  MWDG_ERR_NONFINITE on NaN/Inf. */
-MWDG_API mwdg_status mwdg_load_dem(mwdg_ctx *ctx, const double *z_vert);
+ * max|d| / max(1, max|z0|) (Sect. 2.2). */
+MWDG_API mwdg_status mwdg_load_dem(mwdg_ctx *ctx, const double *z_vert, int64_t ld);
+MWDG_API mwdg_status mwdg_load_dem_dev(mwdg_ctx *ctx, const double *z_vert, int64_t ld);
 
-/* Manning coefficient n_M (Eq. 1) per finest cell, n_cell[ny*nx] (host);
+/* Manning coefficient n_M (Eq. 1) per finest cell, n_cell[ny rows x nx];
  * coarser elements use the mean of their finest cells. */
-MWDG_API mwdg_status mwdg_load_roughness(mwdg_ctx *ctx, const double *n_cell);
+MWDG_API mwdg_status mwdg_load_roughness(mwdg_ctx *ctx, const double *n_cell, int64_t ld);
+MWDG_API mwdg_status mwdg_load_roughness_dev(mwdg_ctx *ctx, const double *n_cell, int64_t ld);
 MWDG_API mwdg_status mwdg_set_roughness_scalar(mwdg_ctx *ctx, double n);
 
-/* Initial condition from vertex rasters (host, (ny+1)(nx+1) each) of depth
+/* Initial condition from vertex rasters ((ny+1) rows x (nx+1) each) of depth
  * h (or free surface eta = h + z when is_eta != 0) and discharges qx, qy,
  * projected like the topography (Sect. 2.1.4).  With is_eta, elements whose
  * average free surface is not above their average bed start dry.  Requires
  * mwdg_load_dem first.  Uniform and adaptive runs start on the finest grid;
  * a static run builds its graded grid here from the topography (as
- * mwdg_mra_adapt does) and encodes the state onto it.  Resets time to 0. */
+ * mwdg_mra_adapt does) and encodes the state onto it.  Resets time to 0.
+ * The host form takes packed rasters; the device form a common row stride
+ * ld, and a non-finite value found in its second or third raster leaves the
+ * context without an initial state. */
 MWDG_API mwdg_status mwdg_load_initial(mwdg_ctx *ctx, const double *h_vert, const double *qx_vert,
                               const double *qy_vert, int32_t is_eta);
+MWDG_API mwdg_status mwdg_load_initial_dev(mwdg_ctx *ctx, const double *h_vert, const double *qx_vert,
+                                           const double *qy_vert, int64_t ld, int32_t is_eta);
 
 /* Inflow hydrograph Q(t) (m^3/s, piecewise linear through nknots knots,
  * held constant outside) entering through finest cells c0..c1 of an edge;
@@ -179,12 +195,15 @@ MWDG_API mwdg_status mwdg_run_steps(mwdg_ctx *ctx, int64_t nsteps);
  * to land on it).  *steps_out (may be NULL) receives the number of steps. */
 MWDG_API mwdg_status mwdg_run_to_time(mwdg_ctx *ctx, double t_end, int64_t *steps_out);
 
-/* Finest-resolution fields h, u, v (host, ny*nx each; any may be NULL):
- * each active leaf's plane evaluated at the centres of the finest cells it
- * covers; velocities are q/h where h > h_dry, else 0. */
-MWDG_API mwdg_status mwdg_read_fields(mwdg_ctx *ctx, double *h, double *u, double *v);
-/* Same into device buffers (FP64, ny*nx each, any may be NULL). */
-MWDG_API mwdg_status mwdg_read_fields_dev(mwdg_ctx *ctx, double *h, double *u, double *v);
+/* Finest-resolution fields h, u, v (host, ny rows x nx with row stride ld,
+ * ld = 0: packed; any may be NULL): each active leaf's plane evaluated at
+ * the centres of the finest cells it covers; velocities are q/h where
+ * h > h_dry, else 0.  Synchronises the context's stream.  MWDG_ERR_ARG when
+ * ld is below nx. */
+MWDG_API mwdg_status mwdg_read_fields(mwdg_ctx *ctx, double *h, double *u, double *v, int64_t ld);
+/* Same into device buffers of the current device (FP64), queued on the
+ * context's stream without synchronising; the caller keeps ownership. */
+MWDG_API mwdg_status mwdg_read_fields_dev(mwdg_ctx *ctx, double *h, double *u, double *v, int64_t ld);
 
 /* Gauge time series (Sect. 3, depth and velocity at gauge points): h, u, v
  * (host, n each, any may be NULL) at n finest cells given as (i, j) pairs in

@@ -17,6 +17,7 @@ WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 
 EXPORTS = (
     "mwdg_params_default", "mwdg_create", "mwdg_destroy", "mwdg_load_dem", "mwdg_load_roughness",
+    "mwdg_load_dem_dev", "mwdg_load_roughness_dev", "mwdg_load_initial_dev",
     "mwdg_set_roughness_scalar", "mwdg_load_initial", "mwdg_set_inflow", "mwdg_set_rain",
     "mwdg_mra_encode", "mwdg_mra_adapt", "mwdg_dg2_step", "mwdg_dg2_step_dt", "mwdg_run_steps", "mwdg_run_to_time",
     "mwdg_read_fields", "mwdg_read_fields_dev", "mwdg_read_active", "mwdg_get_time",
@@ -62,8 +63,11 @@ def lib(build: bool = True):
     sig = {
         "mwdg_params_default": [C.POINTER(Params)],
         "mwdg_create": [C.POINTER(Params), C.POINTER(C.c_void_p)],
-        "mwdg_load_dem": [vp, dp],
-        "mwdg_load_roughness": [vp, dp],
+        "mwdg_load_dem": [vp, dp, C.c_int64],
+        "mwdg_load_dem_dev": [vp, vp, C.c_int64],
+        "mwdg_load_roughness": [vp, dp, C.c_int64],
+        "mwdg_load_roughness_dev": [vp, vp, C.c_int64],
+        "mwdg_load_initial_dev": [vp, vp, vp, vp, C.c_int64, C.c_int32],
         "mwdg_set_roughness_scalar": [vp, C.c_double],
         "mwdg_load_initial": [vp, dp, dp, dp, C.c_int32],
         "mwdg_set_inflow": [vp, C.c_int32, C.c_int32, C.c_int32, dp, dp, C.c_int32],
@@ -75,8 +79,8 @@ def lib(build: bool = True):
         "mwdg_fma_rate": [C.c_int32, vp, dp],
         "mwdg_run_steps": [vp, C.c_int64],
         "mwdg_run_to_time": [vp, C.c_double, lp],
-        "mwdg_read_fields": [vp, dp, dp, dp],
-        "mwdg_read_fields_dev": [vp, vp, vp, vp],
+        "mwdg_read_fields": [vp, dp, dp, dp, C.c_int64],
+        "mwdg_read_fields_dev": [vp, vp, vp, vp, C.c_int64],
         "mwdg_read_gauges": [vp, ip, C.c_int32, dp, dp, dp],
         "mwdg_set_launch_shape": [vp, C.c_int32, C.c_int64],
         "mwdg_get_launch_shape": [vp, ip, lp],
@@ -174,11 +178,39 @@ class Solver:
     def load_dem(self, z_vert):
         z = _f64(z_vert)
         assert z.shape == (self.ny + 1, self.nx + 1)
-        self._ck(self._lib.mwdg_load_dem(self._h, _dp(z)), "mwdg_load_dem")
+        self._ck(self._lib.mwdg_load_dem(self._h, _dp(z), 0), "mwdg_load_dem")
 
     def load_roughness(self, n_cell):
         a = _f64(np.broadcast_to(np.asarray(n_cell, np.float64), (self.ny, self.nx)))
-        self._ck(self._lib.mwdg_load_roughness(self._h, _dp(a)), "mwdg_load_roughness")
+        self._ck(self._lib.mwdg_load_roughness(self._h, _dp(a), 0), "mwdg_load_roughness")
+
+    @staticmethod
+    def _dev2d(t, rows, cols, what):
+        """a CUDA FP64 tensor of rows x cols whose rows are contiguous: its
+        pointer and row stride"""
+        if t.dtype != __import__("torch").float64 or not t.is_cuda or t.dim() != 2 or tuple(t.shape) != (rows, cols) \
+                or t.stride(1) != 1:
+            raise ValueError(f"{what}: expected a CUDA float64 tensor of shape ({rows}, {cols}) with unit column "
+                             "stride")
+        return C.c_void_p(t.data_ptr()), t.stride(0)
+
+    def load_dem_dev(self, z_vert):
+        """the DEM from a CUDA tensor (ny+1, nx+1), rows possibly strided"""
+        zp, ld = self._dev2d(z_vert, self.ny + 1, self.nx + 1, "z_vert")
+        self._ck(self._lib.mwdg_load_dem_dev(self._h, zp, ld), "mwdg_load_dem_dev")
+
+    def load_roughness_dev(self, n_cell):
+        """Manning n from a CUDA tensor (ny, nx), rows possibly strided"""
+        np_, ld = self._dev2d(n_cell, self.ny, self.nx, "n_cell")
+        self._ck(self._lib.mwdg_load_roughness_dev(self._h, np_, ld), "mwdg_load_roughness_dev")
+
+    def load_initial_dev(self, h_vert, qx_vert, qy_vert, is_eta=False):
+        """the initial state from three CUDA tensors (ny+1, nx+1) with one row stride"""
+        ptrs = [self._dev2d(t, self.ny + 1, self.nx + 1, "initial raster") for t in (h_vert, qx_vert, qy_vert)]
+        if len({ld for _, ld in ptrs}) != 1:
+            raise ValueError("the three initial rasters must share one row stride")
+        self._ck(self._lib.mwdg_load_initial_dev(self._h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[0][1],
+                                                 int(is_eta)), "mwdg_load_initial_dev")
 
     def set_roughness_scalar(self, n):
         self._ck(self._lib.mwdg_set_roughness_scalar(self._h, float(n)), "mwdg_set_roughness_scalar")
@@ -228,13 +260,19 @@ class Solver:
     # --- outputs -------------------------------------------------------------
     def read_fields(self):
         h, u, v = (np.empty((self.ny, self.nx)) for _ in range(3))
-        self._ck(self._lib.mwdg_read_fields(self._h, _dp(h), _dp(u), _dp(v)), "mwdg_read_fields")
+        self._ck(self._lib.mwdg_read_fields(self._h, _dp(h), _dp(u), _dp(v), 0), "mwdg_read_fields")
         return h, u, v
 
     def read_fields_dev(self, h=None, u=None, v=None):
-        """fill FP64 CUDA tensors of shape (ny, nx) (any may be None)"""
+        """fill FP64 CUDA tensors of shape (ny, nx) (any may be None; rows
+        possibly strided, one row stride for all)"""
+        given = [x for x in (h, u, v) if x is not None]
+        lds = {self._dev2d(x, self.ny, self.nx, "field")[1] for x in given}
+        if len(lds) > 1:
+            raise ValueError("the field tensors must share one row stride")
+        ld = lds.pop() if lds else 0
         ptr = lambda x: None if x is None else C.c_void_p(x.data_ptr())
-        self._ck(self._lib.mwdg_read_fields_dev(self._h, ptr(h), ptr(u), ptr(v)), "mwdg_read_fields_dev")
+        self._ck(self._lib.mwdg_read_fields_dev(self._h, ptr(h), ptr(u), ptr(v), ld), "mwdg_read_fields_dev")
 
     def read_gauges(self, cells):
         """h, u, v at finest cells given as an (n, 2) array of (i, j)"""

@@ -310,6 +310,40 @@ __global__ void k_fill_nm(T *nm, long long off, long long n, const double *src, 
 __global__ void k_set_tend(Ctl *c, double t_end) { c->t_end = t_end; }
 __global__ void k_set_dt_fixed(Ctl *c, double dt) { c->dt_fixed = dt; }
 
+__global__ void k_check_finite(const double *a, long long n, int *flag) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(a[k])) *flag = 1;
+}
+
+// A raster of rows x cols doubles with a row stride of ld elements (0: cols)
+// from the caller's memory (host, or device when on_device) into the
+// contiguous device buffer dst; a raster with a non-finite value is refused
+// (a device raster is checked on the device, which synchronises).
+mwdg_status stage_raster(mwdg_ctx *c, const double *src, size_t rows, size_t cols, int64_t ld, bool on_device,
+                         double *dst, const char *what) {
+  if (ld == 0) ld = (int64_t)cols;
+  if (ld < (int64_t)cols) return fail(c, MWDG_ERR_ARG, "%s: row stride %lld is below the row length %zu", what,
+                                      (long long)ld, cols);
+  const size_t pitch = (size_t)ld * sizeof(double), width = cols * sizeof(double);
+  if (!on_device) {
+    for (size_t r = 0; r < rows; r++)
+      if (!all_finite(src + r * (size_t)ld, cols)) return fail(c, MWDG_ERR_NONFINITE, "non-finite %s value", what);
+    CK(cudaMemcpy2DAsync(dst, width, src, pitch, width, rows, cudaMemcpyHostToDevice, c->st));
+    return MWDG_OK;
+  }
+  CK(cudaMemcpy2DAsync(dst, width, src, pitch, width, rows, cudaMemcpyDeviceToDevice, c->st));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&c->ctl->bad_input, &flag, sizeof flag, cudaMemcpyHostToDevice, c->st));
+  const long long n = (long long)(rows * cols);
+  k_check_finite<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, c->st>>>(dst, n, &c->ctl->bad_input);
+  c->launches++;
+  CHECK_LAUNCH();
+  CK(cudaMemcpyAsync(&flag, &c->ctl->bad_input, sizeof flag, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (flag) return fail(c, MWDG_ERR_NONFINITE, "non-finite %s value", what);
+  return MWDG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -443,13 +477,13 @@ void mwdg_destroy(mwdg_ctx *c) {
   delete c;
 }
 
-mwdg_status mwdg_load_dem(mwdg_ctx *c, const double *z_vert) {
+static mwdg_status load_dem(mwdg_ctx *c, const double *z_vert, int64_t ld, bool on_device) {
   LIVE(c);
   if (!z_vert) return fail(c, MWDG_ERR_ARG, "z_vert is NULL");
   const Geo &g = c->g;
-  const size_t nv = (size_t)(g.nxl[g.L] + 1) * (g.nyl[g.L] + 1);
-  if (!all_finite(z_vert, nv)) return fail(c, MWDG_ERR_NONFINITE, "non-finite DEM value");
-  CK(cudaMemcpyAsync(c->d_vert, z_vert, nv * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  mwdg_status st = stage_raster(c, z_vert, (size_t)g.nyl[g.L] + 1, (size_t)g.nxl[g.L] + 1, ld, on_device,
+                                c->d_vert, "DEM");
+  if (st) return st;
   unsigned long long zero = 0;
   CK(cudaMemcpyAsync(&c->ctl->vmax[0], &zero, sizeof zero, cudaMemcpyHostToDevice, c->st));
   c->launches += dispatch(c, [&](auto &p, auto *) {
@@ -466,13 +500,17 @@ mwdg_status mwdg_load_dem(mwdg_ctx *c, const double *z_vert) {
   return MWDG_OK;
 }
 
-mwdg_status mwdg_load_roughness(mwdg_ctx *c, const double *n_cell) {
+mwdg_status mwdg_load_dem(mwdg_ctx *c, const double *z_vert, int64_t ld) { return load_dem(c, z_vert, ld, false); }
+mwdg_status mwdg_load_dem_dev(mwdg_ctx *c, const double *z_vert, int64_t ld) { return load_dem(c, z_vert, ld, true); }
+
+static mwdg_status load_roughness(mwdg_ctx *c, const double *n_cell, int64_t ld, bool on_device) {
   LIVE(c);
   if (!n_cell) return fail(c, MWDG_ERR_ARG, "n_cell is NULL");
   const Geo &g = c->g;
   const size_t n = (size_t)g.nxl[g.L] * g.nyl[g.L];
-  if (!all_finite(n_cell, n)) return fail(c, MWDG_ERR_NONFINITE, "non-finite roughness");
-  CK(cudaMemcpyAsync(c->d_vert, n_cell, n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  mwdg_status st = stage_raster(c, n_cell, (size_t)g.nyl[g.L], (size_t)g.nxl[g.L], ld, on_device, c->d_vert,
+                                "roughness");
+  if (st) return st;
   c->launches += dispatch(c, [&](auto &p, auto *) {
     using T = std::remove_pointer_t<decltype(p.U)>;
     k_fill_nm<T><<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(p.NM, g.off[g.L], (long long)n, c->d_vert, 0.0);
@@ -481,6 +519,13 @@ mwdg_status mwdg_load_roughness(mwdg_ctx *c, const double *n_cell) {
   CHECK_LAUNCH();
   CK(cudaStreamSynchronize(c->st));
   return MWDG_OK;
+}
+
+mwdg_status mwdg_load_roughness(mwdg_ctx *c, const double *n_cell, int64_t ld) {
+  return load_roughness(c, n_cell, ld, false);
+}
+mwdg_status mwdg_load_roughness_dev(mwdg_ctx *c, const double *n_cell, int64_t ld) {
+  return load_roughness(c, n_cell, ld, true);
 }
 
 mwdg_status mwdg_set_roughness_scalar(mwdg_ctx *c, double nval) {
@@ -496,18 +541,22 @@ mwdg_status mwdg_set_roughness_scalar(mwdg_ctx *c, double nval) {
   return MWDG_OK;
 }
 
-mwdg_status mwdg_load_initial(mwdg_ctx *c, const double *h_vert, const double *qx_vert,
-                              const double *qy_vert, int32_t is_eta) {
+static mwdg_status load_initial(mwdg_ctx *c, const double *h_vert, const double *qx_vert, const double *qy_vert,
+                                int64_t ld, int32_t is_eta, bool on_device) {
   LIVE(c);
   if (!h_vert || !qx_vert || !qy_vert) return fail(c, MWDG_ERR_ARG, "NULL initial raster");
   if (!c->dem) return fail(c, MWDG_ERR_STATE, "mwdg_load_dem must come first");
   const Geo &g = c->g;
-  const size_t nv = (size_t)(g.nxl[g.L] + 1) * (g.nyl[g.L] + 1);
+  const size_t nvx = (size_t)g.nxl[g.L] + 1, nvy = (size_t)g.nyl[g.L] + 1;
   const double *src[3] = {h_vert, qx_vert, qy_vert};
-  for (int v = 0; v < 3; v++)
-    if (!all_finite(src[v], nv)) return fail(c, MWDG_ERR_NONFINITE, "non-finite initial value");
+  if (!on_device)  // every raster checked before any of them is used
+    for (int v = 0; v < 3; v++)
+      for (size_t r = 0; r < nvy; r++)
+        if (!all_finite(src[v] + r * (size_t)(ld ? ld : (int64_t)nvx), nvx))
+          return fail(c, MWDG_ERR_NONFINITE, "non-finite initial value");
   for (int v = 0; v < 3; v++) {
-    CK(cudaMemcpyAsync(c->d_vert, src[v], nv * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    mwdg_status st = stage_raster(c, src[v], nvy, nvx, ld, on_device, c->d_vert, "initial");
+    if (st) return st;
     c->launches += dispatch(c, [&](auto &p, auto *) {
       using T = std::remove_pointer_t<decltype(p.U)>;
       const long long P = g.P, o = g.off[g.L];
@@ -551,6 +600,15 @@ mwdg_status mwdg_load_initial(mwdg_ctx *c, const double *h_vert, const double *q
   c->stepped = false;
   c->encoded = false;
   return MWDG_OK;
+}
+
+mwdg_status mwdg_load_initial(mwdg_ctx *c, const double *h_vert, const double *qx_vert, const double *qy_vert,
+                              int32_t is_eta) {
+  return load_initial(c, h_vert, qx_vert, qy_vert, 0, is_eta, false);
+}
+mwdg_status mwdg_load_initial_dev(mwdg_ctx *c, const double *h_vert, const double *qx_vert, const double *qy_vert,
+                                  int64_t ld, int32_t is_eta) {
+  return load_initial(c, h_vert, qx_vert, qy_vert, ld, is_eta, true);
 }
 
 mwdg_status mwdg_set_inflow(mwdg_ctx *c, int32_t edge, int32_t c0, int32_t c1, const double *t,
@@ -710,30 +768,64 @@ mwdg_status mwdg_run_to_time(mwdg_ctx *c, double t_end, int64_t *steps_out) {
   return MWDG_OK;
 }
 
-mwdg_status mwdg_read_fields_dev(mwdg_ctx *c, double *h, double *u, double *v) {
-  LIVE(c);
-  const Geo &g = c->g;
-  c->launches += dispatch(c, [&](auto &p, auto *) {
-    using T = std::remove_pointer_t<decltype(p.U)>;
-    return Launch<T>::fields(g, p, h, u, v, c->st);
-  });
-  CHECK_LAUNCH();
-  return MWDG_OK;
-}
-
-mwdg_status mwdg_read_fields(mwdg_ctx *c, double *h, double *u, double *v) {
-  LIVE(c);
+// the three finest rasters into the context's contiguous read-back buffer
+static mwdg_status fields_to_buffer(mwdg_ctx *c) {
   const Geo &g = c->g;
   const size_t n = (size_t)g.nxl[g.L] * g.nyl[g.L];
   if (!c->d_fields) {
     mwdg_status s = alloc(c, &c->d_fields, 3 * n);
     if (s) return s;
   }
-  mwdg_status s = mwdg_read_fields_dev(c, c->d_fields, c->d_fields + n, c->d_fields + 2 * n);
-  if (s) return s;
+  double *b = c->d_fields;
+  c->launches += dispatch(c, [&](auto &p, auto *) {
+    using T = std::remove_pointer_t<decltype(p.U)>;
+    return Launch<T>::fields(g, p, b, b + n, b + 2 * n, c->st);
+  });
+  CHECK_LAUNCH();
+  return MWDG_OK;
+}
+
+// from the read-back buffer to the caller's rasters (row stride ld; 0: nx)
+static mwdg_status fields_out(mwdg_ctx *c, double *h, double *u, double *v, int64_t ld, cudaMemcpyKind kind) {
+  const Geo &g = c->g;
+  const size_t nx = (size_t)g.nxl[g.L], ny = (size_t)g.nyl[g.L], n = nx * ny;
   double *dst[3] = {h, u, v};
   for (int q = 0; q < 3; q++)
-    if (dst[q]) CK(cudaMemcpyAsync(dst[q], c->d_fields + q * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (dst[q])
+      CK(cudaMemcpy2DAsync(dst[q], (size_t)ld * sizeof(double), c->d_fields + q * n, nx * sizeof(double),
+                           nx * sizeof(double), ny, kind, c->st));
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_read_fields_dev(mwdg_ctx *c, double *h, double *u, double *v, int64_t ld) {
+  LIVE(c);
+  const Geo &g = c->g;
+  const int64_t nx = g.nxl[g.L];
+  if (ld != 0 && ld < nx) return fail(c, MWDG_ERR_ARG, "row stride %lld is below the row length %lld",
+                                      (long long)ld, (long long)nx);
+  if (ld == 0 || ld == nx) {  // straight into the caller's rasters
+    c->launches += dispatch(c, [&](auto &p, auto *) {
+      using T = std::remove_pointer_t<decltype(p.U)>;
+      return Launch<T>::fields(g, p, h, u, v, c->st);
+    });
+    CHECK_LAUNCH();
+    return MWDG_OK;
+  }
+  mwdg_status s = fields_to_buffer(c);
+  if (s) return s;
+  return fields_out(c, h, u, v, ld, cudaMemcpyDeviceToDevice);
+}
+
+mwdg_status mwdg_read_fields(mwdg_ctx *c, double *h, double *u, double *v, int64_t ld) {
+  LIVE(c);
+  const Geo &g = c->g;
+  const int64_t nx = g.nxl[g.L];
+  if (ld == 0) ld = nx;
+  if (ld < nx) return fail(c, MWDG_ERR_ARG, "row stride %lld is below the row length %lld", (long long)ld,
+                           (long long)nx);
+  mwdg_status s = fields_to_buffer(c);
+  if (s) return s;
+  if ((s = fields_out(c, h, u, v, ld, cudaMemcpyDeviceToHost))) return s;
   CK(cudaStreamSynchronize(c->st));
   return MWDG_OK;
 }

@@ -31,6 +31,8 @@ struct Ctl {
   int pad_;
   double rain_inc;
   double dt_fixed;             // > 0: the next steps take this dt instead of the CFL step
+  int bad_input;               // set by the finiteness check of a raster read from device memory
+  int pad2_;
 };
 
 // Geometry and parameters of the level hierarchy (passed by value).
