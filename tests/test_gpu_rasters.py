@@ -17,7 +17,7 @@ def _padded(a, pad=7):
     """a CUDA float64 view of a whose rows lie pad elements apart beyond their length"""
     import torch
     t = torch.full((a.shape[0], a.shape[1] + pad), float("nan"), dtype=torch.float64, device="cuda")
-    t[:, :a.shape[1]] = torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64)
+    t[:, :a.shape[1]] = torch.as_tensor(np.array(a, dtype=np.float64))
     return t[:, :a.shape[1]]
 
 
@@ -83,6 +83,11 @@ def test_device_rasters_are_checked():
     with pytest.raises(M.MwdgError) as e:
         s.load_dem_dev(z)
     assert e.value.status == -4
+    # a refused input leaves the context in its error state (MWDG_ERR_STATE after)
+    with pytest.raises(M.MwdgError) as e:
+        s.load_dem_dev(_padded(p.z_vert))
+    assert e.value.status == -6
+    s = M.Solver(M=p.M, N=p.N, L=p.L, dx=p.dx, mode=p.mode)
     s.load_dem_dev(_padded(p.z_vert))
     h = _padded(p.h_vert)
     q = _padded(p.qx_vert)
@@ -91,5 +96,6 @@ def test_device_rasters_are_checked():
         s.load_initial_dev(h, q, _padded(p.qy_vert), False)
     assert e.value.status == -4
     # host rasters with a row stride below the row length are refused
+    s = M.Solver(M=p.M, N=p.N, L=p.L, dx=p.dx, mode=p.mode)
     zz = np.ascontiguousarray(p.z_vert)
     assert s._lib.mwdg_load_dem(s._h, zz.ctypes.data_as(C.POINTER(C.c_double)), p.nx) == -1
