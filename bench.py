@@ -57,7 +57,8 @@ def parse():
                     help="precision of the timed arm (f32: the free-surface FP32 path, the headline; f64: the "
                          "FP64 path, which then needs no separate FP64 leg)")
     ap.add_argument("--urban", type=int, default=1,
-                    help="1: add the slow-to-gradual urban configuration (static vs uniform DG2) to the line")
+                    help="1: add the slow-to-gradual urban configuration (static vs uniform DG2) to the line; "
+                         "2: with its whole 3 h run (static and uniform, FP32; minutes)")
     ap.add_argument("--scheme", default="dg2", choices=["dg2", "fv1", "acc"],
                     help="solver: DG2 (MWDG2, the headline), FV1 (HWFV1 on the adaptive grid) or ACC "
                          "(static graded grid from the same MRA of the topography)")
@@ -491,7 +492,7 @@ def run_average(p, precision, sptr, t_end):
             "budget_error_rel": abs(v["volume"] - (v["v_in"] - v["v_out"] + v["v_rain"])) / max(v["volume"], 1.0)}
 
 
-def run_urban(stream, flush, K, W, spinup=1800.0, t_cmp=600.0):
+def run_urban(stream, flush, K, W, spinup=1800.0, t_cmp=600.0, full=False):
     """The slow-to-gradual configuration: 2048 x 2048 urban-like DEM at dx =
     2 m, 8 m blocks off a 100 m road grid (n = 0.013 on roads, 0.035 else),
     50 mm/h of rain for 1 h.  Static non-uniform DG2 (one MRA of the
@@ -522,6 +523,10 @@ def run_urban(stream, flush, K, W, spinup=1800.0, t_cmp=600.0):
     res["config"] = ("2048x2048 urban DEM, dx=2 m, blocks 10-40 m x 8 m at 25 % cover, roads every 100 m, "
                      f"rain 50 mm/h for 1 h; static grid eps=1e-2 (reflux rule); timed after {spinup:.0f} s, "
                      f"FP32 vs FP64 at {t_cmp:.0f} s")
+    if full:
+        # the configuration's whole 3 h from t = 0, FP32, static and uniform
+        res["run_3h"] = {name: run_average(q, M.F32, sptr, 3.0 * 3600.0)
+                         for name, q in (("static", p), ("uniform", replace(p, mode=S.UNIFORM)))}
     return res
 
 
@@ -876,7 +881,7 @@ def main():
             import torch
             flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
             line["urban_static_vs_uniform"] = run_urban(torch.cuda.current_stream(), flush,
-                                                        max(5, args.steps), args.warmup)
+                                                        max(5, args.steps), args.warmup, full=args.urban >= 2)
         print(json.dumps(line))
     if world > 1:
         import torch
