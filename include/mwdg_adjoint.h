@@ -1,6 +1,8 @@
 /*
- * mwdg_adjoint.h -- C ABI of the discrete adjoint of the uniform-grid DG2
- * step (GB300, sm_103a; FP64 and FP32).
+ * mwdg_adjoint.h -- C ABI of the discrete adjoint of the DG2 step on a
+ * uniform grid and on a frozen non-uniform grid (static graded, or MWDG2
+ * held fixed over a segment; mwdg_adj_create_frozen) (GB300, sm_103a; FP64
+ * and FP32).
  *
  * The step is the DG2 shallow-water step of Sharifian & Kesserwani, arXiv
  * 2107.02750, Sect. 2.1.1 (Eq. 1-4) on a uniform grid of nx x ny cells:
@@ -86,6 +88,37 @@ MWDG_API mwdg_status mwdg_adj_params_default(mwdg_adj_params *p);
  * < 1, nx ny > 2^28, dx <= 0 or max_steps < 1; MWDG_ERR_ARG on a bad edge,
  * inflow range or parameter; MWDG_ERR_CUDA when the allocation fails. */
 MWDG_API mwdg_status mwdg_adj_create(const mwdg_adj_params *p, mwdg_adj **out);
+
+/* The adjoint on a frozen non-uniform grid: a static graded grid (mode
+ * MWDG_STATIC, Sect. 2.2.1) or an MWDG2 grid held fixed over the segment
+ * (MWDG_ADAPTIVE, Sect. 2.3).  M x N roots, L levels below them; p->nx =
+ * M 2^L, p->ny = N 2^L and p->dx describe the finest level (p->inflow_c0,
+ * c1 in finest cells).  The n_leaves active leaves are (level[q], i[q],
+ * j[q]) (host arrays, read during the call): level 0..L, column i west to
+ * east and row j south to north among the level's (M 2^l) x (N 2^l) nodes.
+ * They must tile the domain (every finest cell under exactly one leaf),
+ * else MWDG_ERR_ARG; MWDG_ERR_DIMS when nx, ny disagree with M, N, L.
+ *
+ * The step is the DG2 step of mwdg_adj_create on the leaves, each with its
+ * own cell size, with the interface rule of the grid's kind: a leaf reads
+ * across each face the view of the same-level node there -- a leaf's flux
+ * view, a coarser leaf's planes prolonged to that level (Eq. 10 with zero
+ * details), a refined node's leaves encoded up to it (Eq. 9; MWDG2) or on a
+ * static grid the mean of the face limits of its two children on the face.
+ * Limiting uses same-level leaf neighbours only; the bed of a level is the
+ * encoding of the finest bed planes (Eq. 9), Manning's n the mean of the
+ * children's.  No regridding: it is the map that the adaptive solver's
+ * steps follow between two adaptations.
+ *
+ * With such a context, mwdg_adj_forward and mwdg_adj_backward take U0,
+ * U_out, gU_K and gU0 as 9 x n_leaves coefficient arrays (component m of
+ * leaf q at [m n_leaves + q], leaves in the order given here) and z, n, gz,
+ * gn on the finest level (3 x nx ny and nx ny) as before; the dts are the
+ * CFL steps over the leaves or given ones.  The tape and work arrays cover
+ * every node of every level (4/3 nx ny at most). */
+MWDG_API mwdg_status mwdg_adj_create_frozen(const mwdg_adj_params *p, int32_t M, int32_t N, int32_t L,
+                                            int32_t mode, int64_t n_leaves, const int32_t *level,
+                                            const int32_t *i, const int32_t *j, mwdg_adj **out);
 MWDG_API void mwdg_adj_destroy(mwdg_adj *a);
 
 /* Eq. 8: vertex raster (ny+1) x (nx+1), double -> planes out (3 x n

@@ -7,6 +7,10 @@ U (9, ny, nx) in the component order (h0, h1x, h1y, qx0, qx1x, qx1y, qy0,
 qy1x, qy1y), bed planes z (3, ny, nx), Manning n (ny, nx), hydrograph knots
 (k,).  Work is queued on torch's current CUDA stream.
 
+On a frozen non-uniform grid (``Dg2Adjoint.frozen``: a static graded grid or
+an MWDG2 grid held fixed over the segment) U is (9, n_leaves), the leaves in
+the order given; z and n stay on the finest level.
+
 ``Dg2Run`` is a ``torch.autograd.Function`` over one segment of K steps: its
 forward records the CFL time steps (or takes given ones), its backward
 recomputes the segment from its input state (the checkpoint) and returns the
@@ -17,10 +21,10 @@ from __future__ import annotations
 
 import ctypes as C
 
-from .binding import MwdgError, lib as _lib, WALL, F64, F32
+from .binding import MwdgError, lib as _lib, WALL, F64, F32, STATIC, ADAPTIVE
 
 ADJ_EXPORTS = (
-    "mwdg_adj_params_default", "mwdg_adj_create", "mwdg_adj_destroy", "mwdg_adj_project",
+    "mwdg_adj_params_default", "mwdg_adj_create", "mwdg_adj_create_frozen", "mwdg_adj_destroy", "mwdg_adj_project",
     "mwdg_adj_project_transpose", "mwdg_adj_forward", "mwdg_adj_backward", "mwdg_adj_last_error",
     "mwdg_adj_profile", "mwdg_adj_kernel_times",
 )
@@ -45,6 +49,8 @@ def lib():
         vp, dp, i32 = C.c_void_p, C.c_double, C.c_int32
         L.mwdg_adj_params_default.argtypes = [C.POINTER(AdjParams)]
         L.mwdg_adj_create.argtypes = [C.POINTER(AdjParams), C.POINTER(vp)]
+        L.mwdg_adj_create_frozen.argtypes = [C.POINTER(AdjParams), i32, i32, i32, i32, C.c_int64, vp, vp, vp,
+                                             C.POINTER(vp)]
         L.mwdg_adj_destroy.argtypes = [vp]
         L.mwdg_adj_destroy.restype = None
         L.mwdg_adj_project.argtypes = [vp, vp, vp, vp]
@@ -55,7 +61,7 @@ def lib():
         L.mwdg_adj_last_error.restype = C.c_char_p
         L.mwdg_adj_profile.argtypes = [vp, i32]
         L.mwdg_adj_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
-        for name in ("mwdg_adj_params_default", "mwdg_adj_create", "mwdg_adj_project",
+        for name in ("mwdg_adj_params_default", "mwdg_adj_create", "mwdg_adj_create_frozen", "mwdg_adj_project",
                      "mwdg_adj_project_transpose", "mwdg_adj_forward", "mwdg_adj_backward",
                      "mwdg_adj_profile", "mwdg_adj_kernel_times"):
             getattr(L, name).restype = C.c_int
@@ -77,7 +83,8 @@ class Dg2Adjoint:
 
     def __init__(self, nx, ny, dx, *, g=9.80665, h_dry=1e-3, cfl=0.33, dt_max=1.0, limiter=1,
                  bc=(WALL, WALL, WALL, WALL), inflow_edge=-1, inflow_c0=0, inflow_c1=-1, rain_rate=0.0,
-                 rain_t_end=0.0, max_steps=200, precision=F64, tape_views=False):
+                 rain_t_end=0.0, max_steps=200, precision=F64, tape_views=False, _frozen=None):
+        import numpy as np
         import torch
         if not torch.cuda.is_available():
             raise MwdgError(-3, "Dg2Adjoint", "no CUDA device")
@@ -92,14 +99,37 @@ class Dg2Adjoint:
         p.precision = precision
         p.tape_views = int(bool(tape_views))
         h = C.c_void_p()
-        st = L.mwdg_adj_create(C.byref(p), C.byref(h))
+        self.n_leaves = None
+        if _frozen is None:
+            st = L.mwdg_adj_create(C.byref(p), C.byref(h))
+        else:
+            M, N, Lv, mode, lev, ii, jj = _frozen
+            lev, ii, jj = (np.ascontiguousarray(a, dtype=np.int32) for a in (lev, ii, jj))
+            if not (lev.shape == ii.shape == jj.shape and lev.ndim == 1):
+                raise MwdgError(-1, "Dg2Adjoint.frozen", "level, i, j differ in shape")
+            st = L.mwdg_adj_create_frozen(C.byref(p), int(M), int(N), int(Lv), int(mode), int(lev.size),
+                                          lev.ctypes.data_as(C.c_void_p), ii.ctypes.data_as(C.c_void_p),
+                                          jj.ctypes.data_as(C.c_void_p), C.byref(h))
+            self.n_leaves = int(lev.size)
         if st != 0:
-            raise MwdgError(st, "mwdg_adj_create")
+            raise MwdgError(st, "mwdg_adj_create" if _frozen is None else "mwdg_adj_create_frozen")
         self._h = h
         self.p = p
         self.nx, self.ny, self.dx, self.max_steps = nx, ny, dx, max_steps
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.dtype = torch.float32 if precision == F32 else torch.float64
+
+    @classmethod
+    def frozen(cls, M, N, L, dx, mode, level, i, j, **kw):
+        """A context on a frozen non-uniform grid: M x N roots, L levels, finest
+        cell size dx; mode STATIC (graded grid, Sect. 2.2.1) or ADAPTIVE (an
+        MWDG2 grid held fixed, Sect. 2.3); the active leaves (level, i, j)."""
+        if mode not in (STATIC, ADAPTIVE):
+            raise MwdgError(-1, "Dg2Adjoint.frozen", "mode must be STATIC or ADAPTIVE")
+        return cls(M << L, N << L, dx, _frozen=(M, N, L, mode, level, i, j), **kw)
+
+    def _state_shape(self):
+        return (9, self.n_leaves) if self.n_leaves is not None else (9, self.ny, self.nx)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -149,7 +179,7 @@ class Dg2Adjoint:
 
     def _common(self, U0, z, n, knot_t, knot_Q):
         import torch
-        U0 = self._t(U0, (9, self.ny, self.nx))
+        U0 = self._t(U0, self._state_shape())
         z = self._t(z, (3, self.ny, self.nx))
         n = self._t(n, (self.ny, self.nx))
         kt = self._t(knot_t, dtype=torch.float64) if knot_t is not None else None
@@ -182,7 +212,7 @@ class Dg2Adjoint:
         self._tape_token = None
         U0, z, n, kt, kQ, nk = self._common(U0, z, n, knot_t, knot_Q)
         d = self._t(dts, dtype=torch.float64)
-        g = self._t(gUK, (9, self.ny, self.nx))
+        g = self._t(gUK, self._state_shape())
         gU0 = torch.empty_like(U0)
         gz = torch.zeros_like(z)
         gn = torch.zeros_like(n)

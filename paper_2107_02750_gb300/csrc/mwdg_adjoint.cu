@@ -58,11 +58,19 @@ template <typename T> __device__ __forceinline__ T tie_rel();
 template <> __device__ __forceinline__ double tie_rel<double>() { return 1e-10; }
 template <> __device__ __forceinline__ float tie_rel<float>() { return 1e-5f; }
 
-// parameters passed to the kernels by value
+// parameters passed to the kernels by value.  On a frozen non-uniform grid
+// every level is a dense array of nx x ny nodes (nx = M 2^l) in one
+// coefficient array per component, levels one after another; a launch works
+// on one level, with its pointers offset to the level's first node.
 template <typename T>
 struct Par {
   int nx, ny;
-  long long n;
+  long long n;          // nodes of this level (cells of a uniform grid)
+  long long ns;         // stride between components (n on a uniform grid)
+  int sh;               // levels from this one down to the finest (0: uniform)
+  int stat;             // 1: static graded grid (two-children mean, Sect. 2.2.1)
+  const uint8_t *kind;  // per node of the level: K_BELOW, K_LEAF, K_SIG; NULL: all leaves
+  long long dn, dp;     // nodes from this level's first to the next's, from the previous's to this
   T dx, g, hd;
   double dxd, cfl, dt_max;
   int limiter;
@@ -91,14 +99,26 @@ __device__ double hydro(const Par<T> &P, double t, int &k0, int &k1, double &r) 
   return Qk + (Qk1 - Qk) * (t - tk) / (tk1 - tk);
 }
 
-// unit discharge through the boundary face of cell `along` on edge e
+// finest inflow cells under the boundary face of node `along` of this level
+// on edge e (0 or 1 on a uniform grid)
+template <typename T>
+__device__ __forceinline__ long long inflow_overlap(const Par<T> &P, int e, int along) {
+  if (P.inflow_edge != e || P.nknots < 1) return 0;
+  const long long a = (long long)along << P.sh, b = (long long)(along + 1) << P.sh;
+  const long long lo = a > P.c0 ? a : (long long)P.c0, hi = b < (long long)P.c1 + 1 ? b : (long long)P.c1 + 1;
+  return hi > lo ? hi - lo : 0;
+}
+
+// unit discharge through the boundary face of node `along` on edge e: the
+// hydrograph spread over the inflow cells, times the face's overlap with them
 template <typename T>
 __device__ double inflow_unit(const Par<T> &P, int e, int along, double t) {
-  if (P.inflow_edge != e || P.nknots < 1 || along < P.c0 || along > P.c1) return 0.0;
+  const long long ov = inflow_overlap(P, e, along);
+  if (ov <= 0) return 0.0;
   int k0, k1;
   double r;
   const double Q = hydro(P, t, k0, k1, r);
-  return Q * 1.0 / ((double)(P.c1 - P.c0 + 1) * P.dxd);
+  return Q * (double)ov / ((double)(P.c1 - P.c0 + 1) * P.dxd);
 }
 
 // ---------------------------------------------------------------------------
@@ -147,16 +167,57 @@ __device__ Lim<T> ghost(const Par<T> &P, int e, int along, const Lim<T> &o, doub
   return gl;
 }
 
-// the limits on the other side of face f of cell (i, j): the neighbour's
-// flux view, or the ghost on the boundary
+// node kinds of a frozen grid: below a coarser leaf, an active leaf, or
+// refined (an ancestor of leaves)
+constexpr uint8_t K_BELOW = 0, K_LEAF = 1, K_SIG = 2;
+
 template <typename T>
-__device__ Lim<T> other_side(const Par<T> &P, const T *W, const T *Z, int i, int j, int f, const Lim<T> &own,
-                             double t) {
-  const int di = f == 0 ? 1 : f == 1 ? -1 : 0, dj = f == 2 ? 1 : f == 3 ? -1 : 0;
-  const int a = i + di, b = j + dj;
-  if (a >= 0 && b >= 0 && a < P.nx && b < P.ny) return cell_lim(W, Z, P.n, (long long)b * P.nx + a, f ^ 1);
-  const int e = edge_of(f);
-  return ghost(P, e, e < 2 ? j : i, own, t);
+__device__ __forceinline__ bool is_leaf(const Par<T> &P, long long k) {
+  return !P.kind || P.kind[k] == K_LEAF;
+}
+
+// children (c = cx + 2 cy) of a node that touch its face f: E (cx = 1), W,
+// N (cy = 1), S
+__device__ __forceinline__ void face_children(int f, int &c1, int &c2) {
+  c1 = f == 0 ? 1 : f == 1 ? 0 : f == 2 ? 2 : 0;
+  c2 = f == 0 ? 3 : f == 1 ? 2 : f == 2 ? 3 : 1;
+}
+
+// index in the next level of child c of node (i, j)
+template <typename T>
+__device__ __forceinline__ long long child_of(const Par<T> &P, int i, int j, int c) {
+  return P.dn + (long long)(2 * j + (c >> 1)) * (2 * P.nx) + (2 * i + (c & 1));
+}
+
+// What the other side of an interface sees of node (i, j) on the node's face
+// f: the limits (h, qx, qy, z) of its view and the averages (h0, qx0, qy0)
+// that the outflow limit takes when the node is the donor.  The view is the
+// node's flux view (a leaf; on a frozen MWDG2 grid also the encoding of a
+// refined node's leaves or the prolongation of a coarser leaf, Sect. 2.3),
+// and on a static grid for a refined node the mean of its two children that
+// touch the face (Sect. 2.2.1).
+template <typename T>
+__device__ __forceinline__ Lim<T> node_lim(const Par<T> &P, const T *W, const T *Z, int i, int j, int f, T avg[3]) {
+  const long long k = (long long)j * P.nx + i, n = P.ns;
+  if (P.stat && P.kind && P.kind[k] == K_SIG) {
+    int c1, c2;
+    face_children(f, c1, c2);
+    const long long k1 = child_of(P, i, j, c1), k2 = child_of(P, i, j, c2);
+    const Lim<T> a = cell_lim(W, Z, n, k1, f), b = cell_lim(W, Z, n, k2, f);
+    Lim<T> m;
+    m.h = T(0.5) * (a.h + b.h);
+    m.qx = T(0.5) * (a.qx + b.qx);
+    m.qy = T(0.5) * (a.qy + b.qy);
+    m.z = T(0.5) * (a.z + b.z);
+    avg[0] = T(0.5) * (W[k1] + W[k2]);
+    avg[1] = T(0.5) * (W[3 * n + k1] + W[3 * n + k2]);
+    avg[2] = T(0.5) * (W[6 * n + k1] + W[6 * n + k2]);
+    return m;
+  }
+  avg[0] = W[k];
+  avg[1] = W[3 * n + k];
+  avg[2] = W[6 * n + k];
+  return cell_lim(W, Z, n, k, f);
 }
 
 // limiter record of one cell: partial-wet reduction and, per direction and
@@ -174,7 +235,7 @@ struct LimRec {
 template <typename T>
 __device__ void limit_cell(const Par<T> &P, const T *X, const T *Z, int i, int j, T w_st[9], T w_fx[9], T ze[3],
                            LimRec &r) {
-  const long long n = P.n, k = (long long)j * P.nx + i;
+  const long long n = P.ns, k = (long long)j * P.nx + i;
   const T hd = P.hd, s3 = s3v<T>();
 #pragma unroll
   for (int m = 0; m < 9; m++) w_st[m] = X[m * n + k];
@@ -207,7 +268,9 @@ __device__ void limit_cell(const Par<T> &P, const T *X, const T *Z, int i, int j
   if (P.limiter) {
     for (int d = 0; d < 2; d++) {
       const int ia = i + (d == 0), ja = j + (d == 1), ib = i - (d == 0), jb = j - (d == 1);
-      const bool hasA = ia < P.nx && ja < P.ny, hasB = ib >= 0 && jb >= 0;
+      // neighbours: same-level leaves only (Sect. 2.2.1)
+      const bool hasA = ia < P.nx && ja < P.ny && is_leaf(P, (long long)ja * P.nx + ia);
+      const bool hasB = ib >= 0 && jb >= 0 && is_leaf(P, (long long)jb * P.nx + ib);
       if (!hasA && !hasB) continue;
       const long long ka = hasA ? (long long)ja * P.nx + ia : k, kb = hasB ? (long long)jb * P.nx + ib : k;
       const T hC = X[k], hA = X[ka], hB = X[kb];
@@ -253,30 +316,6 @@ __device__ void limit_cell(const Par<T> &P, const T *X, const T *Z, int i, int j
   for (int m = 0; m < 9; m++) w_fx[m] = w_st[m];
 }
 
-// flux through face f of a cell with own limits o and other side b (already
-// the ghost on the boundary); own revised limits in so
-template <typename T>
-__device__ __forceinline__ void face_flux(const Par<T> &P, const Lim<T> &o, const Lim<T> &b, int f, T F[3],
-                                          Side<T> &so) {
-  const T zf = tmax(o.z, b.z);
-  so = revise_h(o.h, o.qx, o.qy, o.z, zf, P.hd);
-  const Side<T> sb = revise_h(b.h, b.qx, b.qy, b.z, zf, P.hd);
-  T H[3];
-  if (f == 0) {
-    hll(so.hs, so.u, so.v, sb.hs, sb.u, sb.v, P.g, P.hd, H);
-    F[0] = H[0]; F[1] = H[1]; F[2] = H[2];
-  } else if (f == 1) {
-    hll(sb.hs, sb.u, sb.v, so.hs, so.u, so.v, P.g, P.hd, H);
-    F[0] = H[0]; F[1] = H[1]; F[2] = H[2];
-  } else if (f == 2) {
-    hll(so.hs, so.v, so.u, sb.hs, sb.v, sb.u, P.g, P.hd, H);
-    F[0] = H[0]; F[1] = H[2]; F[2] = H[1];
-  } else {
-    hll(sb.hs, sb.v, sb.u, so.hs, so.v, so.u, P.g, P.hd, H);
-    F[0] = H[0]; F[1] = H[2]; F[2] = H[1];
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ bool cell_of(const Par<T> &P, long long &k, int &i, int &j) {
   k = (long long)blockIdx.x * TPB + threadIdx.x;
@@ -304,8 +343,8 @@ __global__ void __launch_bounds__(TPB) k_cfl(Par<T> P, const T *U, const double 
   long long k;
   int i, j;
   T c = tinf<T>();
-  if (cell_of(P, k, i, j)) {
-    const long long n = P.n;
+  if (cell_of(P, k, i, j) && is_leaf(P, k)) {
+    const long long n = P.ns;
     const T h0 = U[k], dx = P.dx, g = P.g;
     if (h0 > P.hd) {
       const T u = U[3 * n + k] / h0, v = U[6 * n + k] / h0;
@@ -349,13 +388,18 @@ __global__ void __launch_bounds__(TPB) k_friction(Par<T> P, const T *U, const T 
   long long k;
   int i, j;
   if (!cell_of(P, k, i, j)) return;
-  const long long n = P.n;
+  const long long n = P.ns;
   const T dt = (T)dts[step], g = P.g;
   const double t = tt[step];
   const double rain = (t < P.rain_t_end) ? P.rain_rate : 0.0;
   T w[9];
 #pragma unroll
   for (int m = 0; m < 9; m++) w[m] = U[m * n + k];
+  if (!is_leaf(P, k)) {  // not a leaf of a frozen grid: still water, read by no leaf
+#pragma unroll
+    for (int m = 0; m < 9; m++) Un[m * n + k] = w[m];
+    return;
+  }
   if (rain > 0.0) w[0] = w[0] + (T)(rain * dts[step]);
   const T h0 = w[0];
   if (h0 > P.hd) {
@@ -379,7 +423,7 @@ __global__ void __launch_bounds__(TPB) k_limit(Par<T> P, const T *X, const T *Z,
   long long k;
   int i, j;
   if (!cell_of(P, k, i, j)) return;
-  const long long n = P.n;
+  const long long n = P.ns;
   T ws[9], wf[9], ze[3];
   LimRec r;
   limit_cell(P, X, Z, i, j, ws, wf, ze, r);
@@ -390,6 +434,116 @@ __global__ void __launch_bounds__(TPB) k_limit(Par<T> P, const T *X, const T *Z,
   }
 #pragma unroll
   for (int m = 0; m < 3; m++) Zfx[m * n + k] = ze[m];
+}
+
+// ---------------------------------------------------------------------------
+// views of a frozen non-uniform grid (Sect. 2.3): every node of every level
+// gets the same-level view that a neighbouring leaf reads -- a leaf its
+// flux view (k_limit), a refined node the encoding of its children's views
+// (Eq. 9, bottom-up), a node below a coarser leaf the prolongation of its
+// parent's view (Eq. 10 with zero details, top-down).  V holds the 9 flow
+// planes, Vz the 3 bed planes.  Sums run in the order of the oracle, so
+// that FP64 rounds the same way.
+// ---------------------------------------------------------------------------
+// Eq. 9 (scale coefficients only): the parent's planes from its children's
+// ch[c] = (c0, c1x, c1y), c = cx + 2 cy
+template <typename T>
+__device__ __forceinline__ void encode3(const T ch[4][3], T sp[3]) {
+  const T H = T(0.5) * s3v<T>();
+  sp[0] = T(0.25) * (((ch[0][0] + ch[1][0]) + ch[2][0]) + ch[3][0]);
+  T a = (-H) * ch[0][0];
+  a = a + T(0.5) * ch[0][1];
+  a = a + H * ch[1][0];
+  a = a + T(0.5) * ch[1][1];
+  a = a + (-H) * ch[2][0];
+  a = a + T(0.5) * ch[2][1];
+  a = a + H * ch[3][0];
+  a = a + T(0.5) * ch[3][1];
+  sp[1] = T(0.25) * a;
+  T b = (-H) * ch[0][0];
+  b = b + T(0.5) * ch[0][2];
+  b = b + (-H) * ch[1][0];
+  b = b + T(0.5) * ch[1][2];
+  b = b + H * ch[2][0];
+  b = b + T(0.5) * ch[2][2];
+  b = b + H * ch[3][0];
+  b = b + T(0.5) * ch[3][2];
+  sp[2] = T(0.25) * b;
+}
+
+// transpose of encode3: the children's cotangents (added) from the parent's
+template <typename T>
+__device__ __forceinline__ void encode3_t(const T gp[3], int c, T gc[3]) {
+  const T H = T(0.5) * s3v<T>();
+  const T sx = (c & 1) ? H : -H, sy = (c & 2) ? H : -H;
+  gc[0] += T(0.25) * ((gp[0] + sx * gp[1]) + sy * gp[2]);
+  gc[1] += T(0.125) * gp[1];
+  gc[2] += T(0.125) * gp[2];
+}
+
+// Eq. 10 with zero details: child c's planes from its parent's
+template <typename T>
+__device__ __forceinline__ void prolong3(const T sp[3], int c, T sc[3]) {
+  const T H = T(0.5) * s3v<T>();
+  const T sx = (c & 1) ? H : -H, sy = (c & 2) ? H : -H;
+  sc[0] = (sp[0] + sx * sp[1]) + sy * sp[2];
+  sc[1] = T(0.5) * sp[1];
+  sc[2] = T(0.5) * sp[2];
+}
+
+// transpose of prolong3: the parent's cotangents (added) from child c's
+template <typename T>
+__device__ __forceinline__ void prolong3_t(const T gc[3], int c, T gp[3]) {
+  const T H = T(0.5) * s3v<T>();
+  const T sx = (c & 1) ? H : -H, sy = (c & 2) ? H : -H;
+  gp[0] += gc[0];
+  gp[1] += sx * gc[0] + T(0.5) * gc[1];
+  gp[2] += sy * gc[0] + T(0.5) * gc[2];
+}
+
+// refined nodes of this level: the encoding of their children's views
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_view_encode(Par<T> P, T *V, T *Vz) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j) || P.kind[k] != K_SIG) return;
+  const long long n = P.ns;
+#pragma unroll 1
+  for (int v = 0; v < 4; v++) {
+    T *A = v < 3 ? V + 3 * v * n : Vz;
+    T ch[4][3], sp[3];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const long long kc = child_of(P, i, j, c);
+#pragma unroll
+      for (int m = 0; m < 3; m++) ch[c][m] = A[m * n + kc];
+    }
+    encode3(ch, sp);
+#pragma unroll
+    for (int m = 0; m < 3; m++) A[m * n + k] = sp[m];
+  }
+}
+
+// nodes of this level below a coarser leaf: the prolongation of their
+// parent's view
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_view_prolong(Par<T> P, T *V, T *Vz) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j) || P.kind[k] != K_BELOW) return;
+  const long long n = P.ns;
+  const long long kp = -P.dp + (long long)(j >> 1) * (P.nx >> 1) + (i >> 1);
+  const int c = (i & 1) + 2 * (j & 1);
+#pragma unroll 1
+  for (int v = 0; v < 4; v++) {
+    T *A = v < 3 ? V + 3 * v * n : Vz;
+    T sp[3], sc[3];
+#pragma unroll
+    for (int m = 0; m < 3; m++) sp[m] = A[m * n + kp];
+    prolong3(sp, c, sc);
+#pragma unroll
+    for (int m = 0; m < 3; m++) A[m * n + k] = sc[m];
+  }
 }
 
 // One RK2 stage (Eq. 4a for stage 1, Eq. 4b for stage 2) on a tile of
@@ -411,7 +565,7 @@ __global__ void __launch_bounds__(UT * UT) k_update(Par<T> P, int stage, const T
   __shared__ T sF[UFX + UFY][3];
   __shared__ T sR[UFX + UFY][8];  // low side (hs, u, v, zr), high side (hs, u, v, zr)
   const int i0 = blockIdx.x * UT, j0 = blockIdx.y * UT;
-  const long long n = P.n;
+  const long long n = P.ns;
   const double t = stage == 1 ? tt[step] : tt[step] + dts[step];
   for (int q = threadIdx.x; q < UFX + UFY; q += UT * UT) {
     const bool xf = q < UFX;
@@ -423,11 +577,10 @@ __global__ void __launch_bounds__(UT * UT) k_update(Par<T> P, int stage, const T
     const bool hasLo = xf ? gi > 0 : gj > 0;
     const bool hasHi = xf ? gi < P.nx : gj < P.ny;
     const int along = xf ? gj : gi;
-    const long long kHi = (long long)gj * P.nx + gi;
-    const long long kLo = xf ? kHi - 1 : kHi - P.nx;
     Lim<T> lo, hi;
-    if (hasLo) lo = cell_lim(Wfx, Zfx, n, kLo, xf ? 0 : 2);
-    if (hasHi) hi = cell_lim(Wfx, Zfx, n, kHi, xf ? 1 : 3);
+    T aLo[3], aHi[3];  // the sides' averages for the outflow limit
+    if (hasLo) lo = node_lim(P, Wfx, Zfx, xf ? gi - 1 : gi, xf ? gj : gj - 1, xf ? 0 : 2, aLo);
+    if (hasHi) hi = node_lim(P, Wfx, Zfx, gi, gj, xf ? 1 : 3, aHi);
     if (!hasLo) lo = ghost(P, xf ? 0 : 2, along, hi, t);
     if (!hasHi) hi = ghost(P, xf ? 1 : 3, along, lo, t);
     const T zf = tmax(lo.z, hi.z);
@@ -442,10 +595,10 @@ __global__ void __launch_bounds__(UT * UT) k_update(Par<T> P, int stage, const T
       F0 = H[0]; F1 = H[2]; F2 = H[1];
     }
     // outflow limit of the donor cell (never a boundary ghost)
-    const long long kd = F0 > T(0) ? (hasLo ? kLo : -1) : (F0 < T(0) && hasHi ? kHi : -1);
-    if (kd >= 0) {
-      const T qx0 = Wfx[3 * n + kd], qy0 = Wfx[6 * n + kd];
-      drain_limit(F0, F1, F2, Wfx[kd], xf ? qx0 : qy0, xf ? qy0 : qx0, P.g, P.hd, P.dx, (T)dts[step]);
+    const bool dLo = F0 > T(0) && hasLo, dHi = F0 < T(0) && hasHi;
+    if (dLo || dHi) {
+      const T h0 = dLo ? aLo[0] : aHi[0], qx0 = dLo ? aLo[1] : aHi[1], qy0 = dLo ? aLo[2] : aHi[2];
+      drain_limit(F0, F1, F2, h0, xf ? qx0 : qy0, xf ? qy0 : qx0, P.g, P.hd, P.dx, (T)dts[step]);
     }
     sF[q][0] = F0; sF[q][1] = F1; sF[q][2] = F2;
     sR[q][0] = sl.hs; sR[q][1] = sl.u; sR[q][2] = sl.v; sR[q][3] = sl.zr;
@@ -456,6 +609,13 @@ __global__ void __launch_bounds__(UT * UT) k_update(Par<T> P, int stage, const T
   const int i = i0 + ci, j = j0 + cj;
   if (i >= P.nx || j >= P.ny) return;
   const long long k = (long long)j * P.nx + i;
+  if (!is_leaf(P, k)) {  // a node of a frozen grid that is not a leaf: still water
+    Out[k] = T(1);
+#pragma unroll
+    for (int m = 1; m < 9; m++) Out[m * n + k] = T(0);
+    clip[k] = 0;
+    return;
+  }
   const T dt = (T)dts[step];
   const T g = P.g, s3 = s3v<T>(), dxl = P.dx;
   // faces E, W (x faces (ci+1, cj), (ci, cj)) and N, S (y faces (ci, cj+1),
@@ -571,7 +731,12 @@ __global__ void __launch_bounds__(TPB) k_project_t(Par<T> P, const T *gp, T *gv)
 template <typename T>
 __device__ __forceinline__ void stage_cot(const Par<T> &P, int stage, T dt, const T *lY, const T *Y,
                                           const uint8_t *clip, long long k, T lo[9], T lL[9]) {
-  const long long n = P.n;
+  const long long n = P.ns;
+  if (!is_leaf(P, k)) {  // a frozen grid's non-leaf node: its output is constant
+#pragma unroll
+    for (int m = 0; m < 9; m++) lo[m] = lL[m] = T(0);
+    return;
+  }
   const bool clipped = (clip[k] >> (stage - 1)) & 1u;
   const bool dry = !(Y[k] > P.hd);
   const T wL = stage == 2 ? T(0.5) * dt : dt;
@@ -589,13 +754,13 @@ __device__ __forceinline__ void stage_cot(const Par<T> &P, int stage, T dt, cons
 template <typename T>
 __device__ __forceinline__ Side<T> own_revised(const Par<T> &P, const T *W, const T *Z, int i, int j, int f) {
   const long long k = (long long)j * P.nx + i;
-  const Lim<T> o = cell_lim(W, Z, P.n, k, f);
+  const Lim<T> o = cell_lim(W, Z, P.ns, k, f);
   const int di = f == 0 ? 1 : f == 1 ? -1 : 0, dj = f == 2 ? 1 : f == 3 ? -1 : 0;
   const int a = i + di, b = j + dj;
   T zb = o.z;
   if (a >= 0 && b >= 0 && a < P.nx && b < P.ny) {
-    const long long kb = (long long)b * P.nx + a;
-    zb = face_value(Z[kb], Z[P.n + kb], Z[2 * P.n + kb], f ^ 1);
+    T avg[3];
+    zb = node_lim(P, W, Z, a, b, f ^ 1, avg).z;
   }
   return revise_h(o.h, o.qx, o.qy, o.z, tmax(o.z, zb), P.hd);
 }
@@ -803,7 +968,7 @@ __device__ double ghost_rev(const Par<T> &P, int e, int along, const Lim<T> &o, 
     else lq += lg[0] / (T(3) * hc * hc) * (T(2) * q / P.g);
     const T sg = (e == 0 || e == 2) ? T(1) : T(-1);
     lq += sg * (e < 2 ? lg[1] : lg[2]);
-    return (double)lq * 1.0 / ((double)(P.c1 - P.c0 + 1) * P.dxd);
+    return (double)lq * (double)inflow_overlap(P, e, along) / ((double)(P.c1 - P.c0 + 1) * P.dxd);
   }
   if (P.bc[e] == MWDG_OPEN) {
     lo[0] += lg[0]; lo[1] += lg[1]; lo[2] += lg[2];
@@ -882,7 +1047,6 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
   const long long nf = XF ? (long long)P.ny * (P.nx + 1) : (long long)(P.ny + 1) * P.nx;
   const long long fi = (long long)blockIdx.x * TPB + threadIdx.x;
   if (fi >= nf) return;
-  const long long n = P.n;
   const double t = stage == 1 ? tt[step] : tt[step] + dts[step];
   int i, j;  // the high-side cell (i, j); the low side is (i-1, j) or (i, j-1)
   if (XF) { j = (int)(fi / (P.nx + 1)); i = (int)(fi - (long long)j * (P.nx + 1)); }
@@ -895,8 +1059,9 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
   const long long kHi = (long long)j * P.nx + i;
   const int along = XF ? j : i;
   Lim<T> lo, hi;
-  if (hasLo) lo = cell_lim(Wfx, Zfx, n, kLo, fLo);
-  if (hasHi) hi = cell_lim(Wfx, Zfx, n, kHi, fHi);
+  T aLo[3], aHi[3];
+  if (hasLo) lo = node_lim(P, Wfx, Zfx, XF ? i - 1 : i, XF ? j : j - 1, fLo, aLo);
+  if (hasHi) hi = node_lim(P, Wfx, Zfx, i, j, fHi, aHi);
   if (!hasLo) lo = ghost(P, eLo, along, hi, t);
   if (!hasHi) hi = ghost(P, eHi, along, lo, t);
   const T zf = tmax(lo.z, hi.z);
@@ -906,14 +1071,14 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
   // cotangents of its own revised limits at this face
   const T dt = (T)dts[step];
   T lF[3] = {T(0), T(0), T(0)}, cLo[4] = {T(0), T(0), T(0), T(0)}, cHi[4] = {T(0), T(0), T(0), T(0)};
-  if (hasLo) {
+  if (hasLo && is_leaf(P, kLo)) {
     T lo_[9], lL[9], f3[3];
     stage_cot(P, stage, dt, lY, Y, clip, kLo, lo_, lL);
     const Side<T> opp = own_revised(P, Wfx, Zfx, XF ? i - 1 : i, XF ? j : j - 1, fLo ^ 1);
     cell_face_cot(P, fLo, lL, sLo, opp, f3, cLo);
     lF[0] += f3[0]; lF[1] += f3[1]; lF[2] += f3[2];
   }
-  if (hasHi) {
+  if (hasHi && is_leaf(P, kHi)) {
     T lo_[9], lL[9], f3[3];
     stage_cot(P, stage, dt, lY, Y, clip, kHi, lo_, lL);
     const Side<T> opp = own_revised(P, Wfx, Zfx, i, j, fHi ^ 1);
@@ -931,11 +1096,11 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
       hll(sLo.hs, sLo.v, sLo.u, sHi.hs, sHi.v, sHi.u, P.g, P.hd, H);
       F[0] = H[0]; F[1] = H[2]; F[2] = H[1];
     }
-    const long long kd = F[0] > T(0) ? (hasLo ? kLo : -1) : (F[0] < T(0) && hasHi ? kHi : -1);
-    if (kd >= 0) {
-      const T qx0 = Wfx[3 * n + kd], qy0 = Wfx[6 * n + kd];
+    const bool donLo = F[0] > T(0) && hasLo, donHi = F[0] < T(0) && hasHi;
+    if (donLo || donHi) {
+      const T h0 = donLo ? aLo[0] : aHi[0], qx0 = donLo ? aLo[1] : aHi[1], qy0 = donLo ? aLo[2] : aHi[2];
       T lG[3] = {lF[0], lF[1], lF[2]}, ld[3];
-      drain_rev(F, Wfx[kd], XF ? qx0 : qy0, XF ? qy0 : qx0, P.g, P.hd, P.dx, dt, lG, lF, ld);
+      drain_rev(F, h0, XF ? qx0 : qy0, XF ? qy0 : qx0, P.g, P.hd, P.dx, dt, lG, lF, ld);
       T *dd = F[0] > T(0) ? dLo : dHi;  // the low side is the donor of an outflow along +x / +y
       dd[0] = ld[0];
       dd[1] = XF ? ld[1] : ld[2];
@@ -999,7 +1164,7 @@ __global__ void k_rev_knots(Par<T> P, int stage, const double *dts, const double
   const int nedge = (P.inflow_edge < 2) ? P.ny : P.nx;
   double acc = 0.0;
   for (int a = threadIdx.x; a < nedge; a += TPB)
-    if (a >= P.c0 && a <= P.c1) acc += lq[a];
+    if (inflow_overlap(P, P.inflow_edge, a) > 0) acc += lq[a];
   sh[threadIdx.x] = acc;
   __syncthreads();
   for (int s = TPB / 2; s > 0; s >>= 1) {
@@ -1021,26 +1186,16 @@ __global__ void k_rev_knots(Par<T> P, int stage, const double *dts, const double
   }
 }
 
-// Face-limit transpose and the limiter in reverse for one cell: the
-// cotangent of the stage input X of this cell (lXo) and the shares of its
-// neighbours' averages (lnb: direction, side A/B, variable), the bed's own
-// cotangents added to gz.
+// The cotangents of a cell's flux-view planes (9 flow, 3 bed) from its four
+// faces: the face-limit transpose of the limits' cotangents (E = low side of
+// x face (j, i + 1), W = high side of x face (j, i), N = low side of y face
+// (j + 1, i), S = high side of y face (j, i)) and the averages' cotangents
+// from the outflow limit of the four interfaces.
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, int stage, const double *dts, int step, const T *X,
-                                                   const T *Z, const T *lY, const T *Y, const uint8_t *clip, T *lW1,
-                                                   const T *limx, const T *limy, T *lXo, T *lnb, T *gz) {
-  long long k;
-  int i, j;
-  if (!cell_of(P, k, i, j)) return;
-  const long long n = P.n;
+__device__ __forceinline__ void face_plane_cot(const Par<T> &P, int i, int j, const T *limx, const T *limy, T lw[9],
+                                               T lz[3]) {
   const long long nfx = (long long)P.ny * (P.nx + 1), nfy = (long long)(P.ny + 1) * P.nx;
-  const T s3 = s3v<T>(), rs3 = T(1) / s3v<T>();
-  T ws[9], wf[9], ze[3];
-  LimRec r;
-  limit_cell(P, X, Z, i, j, ws, wf, ze, r);
-  // cotangents of the face limits: E = low side of x face (j, i + 1), W =
-  // high side of x face (j, i), N = low side of y face (j + 1, i), S = high
-  // side of y face (j, i)
+  const T s3 = s3v<T>();
   T lf[4][4];
   const long long fE = (long long)j * (P.nx + 1) + i + 1, fW = (long long)j * (P.nx + 1) + i;
   const long long fN = (long long)(j + 1) * P.nx + i, fS = (long long)j * P.nx + i;
@@ -1051,7 +1206,6 @@ __global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, int stage, const do
     lf[2][q] = limy[q * nfy + fN];
     lf[3][q] = limy[(4 + q) * nfy + fS];
   }
-  T lw[9], lz[3];
 #pragma unroll
   for (int v = 0; v < 4; v++) {
     const T a = lf[0][v] + lf[1][v] + lf[2][v] + lf[3][v];
@@ -1060,12 +1214,50 @@ __global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, int stage, const do
     if (v < 3) { lw[3 * v] = a; lw[3 * v + 1] = bx; lw[3 * v + 2] = by; }
     else { lz[0] = a; lz[1] = bx; lz[2] = by; }
   }
-  // the averages' cotangents from the outflow limit of the four interfaces
-  // (this cell is the low side of E and N, the high side of W and S)
 #pragma unroll
   for (int v = 0; v < 3; v++)
     lw[3 * v] += ((limx[(8 + v) * nfx + fE] + limx[(11 + v) * nfx + fW]) + limy[(8 + v) * nfy + fN]) +
                  limy[(11 + v) * nfy + fS];
+}
+
+// Face-limit transpose and the limiter in reverse for one cell: the
+// cotangent of the stage input X of this cell (lXo) and the shares of its
+// neighbours' averages (lnb: direction, side A/B, variable), the bed's own
+// cotangents added to gz.  GV: the flux-view planes' cotangents come
+// gathered in gV (12 planes: a frozen grid, where views pass them between
+// levels), else from the cell's four faces.
+template <typename T, bool GV>
+__global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, int stage, const double *dts, int step, const T *X,
+                                                   const T *Z, const T *lY, const T *Y, const uint8_t *clip, T *lW1,
+                                                   const T *limx, const T *limy, const T *gV, T *lXo, T *lnb,
+                                                   T *gz) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j)) return;
+  const long long n = P.ns;
+  if (!is_leaf(P, k)) {  // no cotangent reaches a frozen grid's non-leaf node
+#pragma unroll
+    for (int m = 0; m < 9; m++) {
+      lXo[m * n + k] = T(0);
+      if (stage == 2) lW1[m * n + k] = T(0);
+    }
+#pragma unroll
+    for (int m = 0; m < 12; m++) lnb[m * n + k] = T(0);
+    return;
+  }
+  const T rs3 = T(1) / s3v<T>();
+  T ws[9], wf[9], ze[3];
+  LimRec r;
+  limit_cell(P, X, Z, i, j, ws, wf, ze, r);
+  T lw[9], lz[3];
+  if (GV) {
+#pragma unroll
+    for (int m = 0; m < 9; m++) lw[m] = gV[m * n + k];
+#pragma unroll
+    for (int m = 0; m < 3; m++) lz[m] = gV[(9 + m) * n + k];
+  } else {
+    face_plane_cot(P, i, j, limx, limy, lw, lz);
+  }
   // the stage's output cotangent: the stored view's share (stage 2 also
   // passes half to the stage-1 view) and the slope bed sources
   // S1 = c2 h1 (h1 + z1) of the flux view
@@ -1081,7 +1273,7 @@ __global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, int stage, const do
     }
   }
   {
-    const T c2 = -(T(2) * s3 * P.g / P.dx);
+    const T c2 = -(T(2) * s3v<T>() * P.g / P.dx);
     lw[1] += lL[4] * c2 * (T(2) * wf[1] + ze[1]);
     lw[2] += lL[8] * c2 * (T(2) * wf[2] + ze[2]);
     lz[1] += lL[4] * c2 * wf[1];
@@ -1145,7 +1337,12 @@ __global__ void __launch_bounds__(TPB) k_rev_gather(Par<T> P, const T *lXo, cons
   long long k;
   int i, j;
   if (!cell_of(P, k, i, j)) return;
-  const long long n = P.n;
+  const long long n = P.ns;
+  if (!is_leaf(P, k)) {
+#pragma unroll
+    for (int m = 0; m < 9; m++) lX[m * n + k] = T(0);
+    return;
+  }
   T in[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int v = 0; v < 3; v++) {
@@ -1171,7 +1368,12 @@ __global__ void __launch_bounds__(TPB) k_rev_friction(Par<T> P, const T *U, cons
   long long k;
   int i, j;
   if (!cell_of(P, k, i, j)) return;
-  const long long n = P.n;
+  const long long n = P.ns;
+  if (!is_leaf(P, k)) {
+#pragma unroll
+    for (int m = 0; m < 9; m++) lU[m * n + k] = T(0);
+    return;
+  }
   const T dt = (T)dts[step], g = P.g;
   const double t = tt[step];
   const double rain = (t < P.rain_t_end) ? P.rain_rate : 0.0;
@@ -1225,6 +1427,206 @@ __global__ void __launch_bounds__(TPB) k_rev_friction(Par<T> P, const T *U, cons
 }
 
 // ---------------------------------------------------------------------------
+// frozen non-uniform grids: the views in reverse, leaves in and out, and the
+// level pyramids of the bed (Eq. 9) and of Manning's n (children's mean)
+// ---------------------------------------------------------------------------
+// The cotangent of every node's view planes (gV: 9 flow, 3 bed) from the
+// interfaces of its level: its four faces (face_plane_cot), except where
+// the node's faces show the mean of its children (a refined node of a static
+// grid).  A child of such a node takes half of the cotangent of the mean on
+// each of its parent's faces that it touches (the parent level's slots px,
+// py).
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_rev_view_gather(Par<T> P, const T *limx, const T *limy, const T *px,
+                                                         const T *py, T *gV) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j)) return;
+  const long long n = P.ns;
+  T lw[9], lz[3];
+  if (P.stat && P.kind[k] == K_SIG) {
+#pragma unroll
+    for (int m = 0; m < 9; m++) lw[m] = T(0);
+    lz[0] = lz[1] = lz[2] = T(0);
+  } else {
+    face_plane_cot(P, i, j, limx, limy, lw, lz);
+  }
+  if (P.stat && P.dp > 0) {
+    const int pnx = P.nx >> 1, pny = P.ny >> 1, pi = i >> 1, pj = j >> 1;
+    if (P.kind[-P.dp + (long long)pj * pnx + pi] == K_SIG) {
+      const long long pfx = (long long)pny * (pnx + 1), pfy = (long long)(pny + 1) * pnx;
+      const T s3 = s3v<T>();
+      // the parent's face in x (E when the node is an east child: the low
+      // side of x face (pj, pi + 1); else W, the high side of (pj, pi)) and
+      // in y (N / S likewise)
+      const bool east = i & 1, north = j & 1;
+      const long long fx = (long long)pj * (pnx + 1) + pi + (east ? 1 : 0);
+      const long long fy = (long long)(pj + (north ? 1 : 0)) * pnx + pi;
+      const int sx = east ? 0 : 4, sy = north ? 0 : 4;     // limit slots of the parent's side
+      const int ax = east ? 8 : 11, ay = north ? 8 : 11;   // average slots
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const T lx = T(0.5) * px[(sx + q) * pfx + fx], ly = T(0.5) * py[(sy + q) * pfy + fy];
+        T *c = q < 3 ? lw + 3 * q : lz;
+        c[0] += lx + ly;
+        c[1] += east ? s3 * lx : -(s3 * lx);
+        c[2] += north ? s3 * ly : -(s3 * ly);
+      }
+#pragma unroll
+      for (int v = 0; v < 3; v++) lw[3 * v] += T(0.5) * px[(ax + v) * pfx + fx] + T(0.5) * py[(ay + v) * pfy + fy];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 9; m++) gV[m * n + k] = lw[m];
+#pragma unroll
+  for (int m = 0; m < 3; m++) gV[(9 + m) * n + k] = lz[m];
+}
+
+// transpose of the prolongation: a leaf or a node below a coarser leaf (this
+// level) takes the cotangents of its children that are below it (the next
+// level); run from the finest level up
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_rev_prolong(Par<T> P, T *gV) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j) || P.kind[k] == K_SIG) return;
+  const long long n = P.ns;
+  T acc[12];
+#pragma unroll
+  for (int m = 0; m < 12; m++) acc[m] = gV[m * n + k];
+  bool any = false;
+#pragma unroll 1
+  for (int c = 0; c < 4; c++) {
+    const long long kc = child_of(P, i, j, c);
+    if (P.kind[kc] != K_BELOW) continue;
+    any = true;
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      T gc[3];
+#pragma unroll
+      for (int m = 0; m < 3; m++) gc[m] = gV[(3 * v + m) * n + kc];
+      prolong3_t(gc, c, acc + 3 * v);
+    }
+  }
+  if (!any) return;
+#pragma unroll
+  for (int m = 0; m < 12; m++) gV[m * n + k] = acc[m];
+}
+
+// transpose of the encoding: a child of a refined node (this level) takes
+// its share of the parent's cotangents (the previous level); run from the
+// coarsest level down
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_rev_encode(Par<T> P, T *gV) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j)) return;
+  const long long kp = -P.dp + (long long)(j >> 1) * (P.nx >> 1) + (i >> 1);
+  if (P.kind[kp] != K_SIG) return;
+  const long long n = P.ns;
+  const int c = (i & 1) + 2 * (j & 1);
+#pragma unroll
+  for (int v = 0; v < 4; v++) {
+    T gp[3], gc[3];
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+      gp[m] = gV[(3 * v + m) * n + kp];
+      gc[m] = gV[(3 * v + m) * n + k];
+    }
+    encode3_t(gp, c, gc);
+#pragma unroll
+    for (int m = 0; m < 3; m++) gV[(3 * v + m) * n + k] = gc[m];
+  }
+}
+
+// every node of every level to still water (h0 = 1, the rest 0)
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_still(long long nt, T *U) {
+  const long long k = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (k >= nt) return;
+  U[k] = T(1);
+#pragma unroll
+  for (int m = 1; m < 9; m++) U[m * nt + k] = T(0);
+}
+
+// leaf coefficients (9 x nl, component-major) to / from their nodes in the
+// level arrays (9 x nt); `node` gives each leaf's node
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_leaves_to_nodes(long long nl, long long nt, const long long *node,
+                                                         const T *src, T *dst) {
+  const long long q = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (q >= nl) return;
+  const long long k = node[q];
+#pragma unroll
+  for (int m = 0; m < 9; m++) dst[m * nt + k] = src[m * nl + q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_nodes_to_leaves(long long nl, long long nt, const long long *node,
+                                                         const T *src, T *dst) {
+  const long long q = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (q >= nl) return;
+  const long long k = node[q];
+#pragma unroll
+  for (int m = 0; m < 9; m++) dst[m * nl + q] = src[m * nt + k];
+}
+
+// the finest level's planes (C components of stride nfin) into the level
+// arrays (stride nt, offset off), or back with add = 1 (dst += src)
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_copy_planes(int C, long long cnt, const T *src, long long ss, T *dst,
+                                                     long long ds, int add) {
+  const long long k = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (k >= cnt) return;
+  for (int m = 0; m < C; m++) dst[m * ds + k] = add ? dst[m * ds + k] + src[m * ss + k] : src[m * ss + k];
+}
+
+// one level of the bed pyramid (Eq. 9 on the bed planes) and of Manning's n
+// (the mean of the children), from the next finer level
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_pyramid_level(Par<T> P, T *Z, T *N) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j)) return;
+  const long long n = P.ns;
+  T ch[4][3], sp[3], nc[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    const long long kc = child_of(P, i, j, c);
+#pragma unroll
+    for (int m = 0; m < 3; m++) ch[c][m] = Z[m * n + kc];
+    nc[c] = N[kc];
+  }
+  encode3(ch, sp);
+#pragma unroll
+  for (int m = 0; m < 3; m++) Z[m * n + k] = sp[m];
+  N[k] = T(0.25) * (((nc[0] + nc[1]) + nc[2]) + nc[3]);
+}
+
+// its transpose: the children (this level) take their shares of the
+// parent's (the previous level) bed and Manning cotangents; run from the
+// coarsest level down
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_pyramid_level_t(Par<T> P, T *gZ, T *gN) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j)) return;
+  const long long n = P.ns;
+  const long long kp = -P.dp + (long long)(j >> 1) * (P.nx >> 1) + (i >> 1);
+  const int c = (i & 1) + 2 * (j & 1);
+  T gp[3], gc[3];
+#pragma unroll
+  for (int m = 0; m < 3; m++) {
+    gp[m] = gZ[m * n + kp];
+    gc[m] = gZ[m * n + k];
+  }
+  encode3_t(gp, c, gc);
+#pragma unroll
+  for (int m = 0; m < 3; m++) gZ[m * n + k] = gc[m];
+  gN[k] = gN[k] + T(0.25) * gN[kp];
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 inline unsigned blocks(long long items) { return (unsigned)((items + TPB - 1) / TPB); }
@@ -1254,6 +1656,15 @@ struct mwdg_adj {
   void *lU = nullptr, *lX = nullptr, *lW1 = nullptr, *limx = nullptr, *limy = nullptr, *lXo = nullptr,
        *lnb = nullptr;
   double *lq = nullptr;
+  // a frozen non-uniform grid (levels = L + 1 > 0; 0 on a uniform grid):
+  // per level its first node, x face, y face and boundary entry in the
+  // concatenated arrays (the last entry: the totals)
+  int levels = 0, mode = 0, gM = 0, gN = 0;
+  std::vector<long long> off, fxo, fyo, lqo;
+  long long nl = 0, nfin = 0;     // leaves; finest cells
+  uint8_t *kind = nullptr;        // node kinds (K_BELOW, K_LEAF, K_SIG)
+  long long *node = nullptr;      // each leaf's node
+  void *zp = nullptr, *np = nullptr, *gzp = nullptr, *gnp = nullptr, *gV = nullptr;
   std::string err;
 };
 
@@ -1290,7 +1701,8 @@ struct Timed {
 void free_all(mwdg_adj *a) {
   free_events(a);
   void *ptrs[] = {a->tape, a->clip, a->tt, a->dtbuf, a->best, a->Un, a->Ui, a->W1, a->F1, a->Z1, a->W2,
-                  a->F2, a->Z2, a->lU, a->lX, a->lW1, a->limx, a->limy, a->lXo, a->lnb, a->lq};
+                  a->F2, a->Z2, a->lU, a->lX, a->lW1, a->limx, a->limy, a->lXo, a->lnb, a->lq,
+                  a->kind, a->node, a->zp, a->np, a->gzp, a->gnp, a->gV};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -1306,13 +1718,20 @@ mwdg_status cuda_check(mwdg_adj *a, const char *where) {
   return fail(a, MWDG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// parameters of the finest (uniform) grid; for a frozen grid's level l see
+// level_par
 template <typename T>
 Par<T> make_par(const mwdg_adj *a, int nknots, const double *kt, const double *kQ) {
   Par<T> P;
   const mwdg_adj_params &p = a->p;
   P.nx = p.nx;
   P.ny = p.ny;
-  P.n = a->n;
+  P.n = (long long)p.nx * p.ny;
+  P.ns = P.n;
+  P.sh = 0;
+  P.stat = 0;
+  P.kind = nullptr;
+  P.dn = P.dp = 0;
   P.dx = (T)p.dx;
   P.g = (T)p.g;
   P.hd = (T)p.h_dry;
@@ -1329,6 +1748,29 @@ Par<T> make_par(const mwdg_adj *a, int nknots, const double *kt, const double *k
   P.rain_t_end = p.rain_t_end;
   P.kt = kt;
   P.kQ = kQ;
+  return P;
+}
+
+int nlev(const mwdg_adj *a) { return a->levels ? a->levels : 1; }
+long long loff(const mwdg_adj *a, int l) { return a->levels ? a->off[l] : 0; }
+
+// parameters of level l (the whole grid on a uniform grid)
+template <typename T>
+Par<T> level_par(const mwdg_adj *a, int l, int nknots, const double *kt, const double *kQ) {
+  Par<T> P = make_par<T>(a, nknots, kt, kQ);
+  if (!a->levels) return P;
+  const int L = a->levels - 1;
+  P.nx = a->gM << l;
+  P.ny = a->gN << l;
+  P.n = (long long)P.nx * P.ny;
+  P.ns = a->n;
+  P.sh = L - l;
+  P.stat = a->mode == MWDG_STATIC;
+  P.kind = a->kind + a->off[l];
+  P.dn = l < L ? a->off[l + 1] - a->off[l] : 0;
+  P.dp = l > 0 ? a->off[l] - a->off[l - 1] : 0;
+  P.dxd = a->p.dx * (double)(1LL << (L - l));
+  P.dx = (T)P.dxd;
   return P;
 }
 
@@ -1349,51 +1791,111 @@ StageArrays<T> stage_arrays(const mwdg_adj *a, int s) {
                         ptr<T>(a->Z1) + o3, ptr<T>(a->F2) + o9, ptr<T>(a->Z2) + o3};
 }
 
-// friction, limit, stage 1 and limit of step s: the two stage inputs (Un, Ui)
-// and their stored and flux views
+// the views of the flux-view planes (F, Zf) of a frozen grid: encodings of
+// refined nodes from the finest level up, then prolongations from the
+// coarsest down
 template <typename T>
-void recompute_stages(mwdg_adj *a, const Par<T> &P, const T *U, const T *z, const T *nman, int s, const double *dts,
-                      uint8_t *clip, cudaStream_t st) {
-  const unsigned nb = blocks(a->n);
+void launch_views(const mwdg_adj *a, const Par<T> *PL, T *F, T *Zf, cudaStream_t st) {
+  if (!a->levels) return;
+  const int L = a->levels - 1;
+  for (int l = L - 1; l >= 0; l--)
+    k_view_encode<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], F + loff(a, l), Zf + loff(a, l));
+  for (int l = 1; l <= L; l++)
+    k_view_prolong<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], F + loff(a, l), Zf + loff(a, l));
+}
+
+template <typename T>
+void launch_update(const mwdg_adj *a, const Par<T> *PL, int stage, const T *F, const T *Zf, const T *Wst,
+                   const T *W1, const double *dts, int s, T *Out, uint8_t *clip, cudaStream_t st) {
+  for (int l = 0; l < nlev(a); l++) {
+    const long long o = loff(a, l);
+    const dim3 tiles((PL[l].nx + UT - 1) / UT, (PL[l].ny + UT - 1) / UT);
+    k_update<T><<<tiles, UT * UT, 0, st>>>(PL[l], stage, F + o, Zf + o, Wst + o, W1 ? W1 + o : nullptr, dts, a->tt,
+                                           s, Out + o, clip + o);
+  }
+}
+
+template <typename T>
+void launch_limit(const mwdg_adj *a, const Par<T> *PL, const T *X, const T *z, T *Wst, T *F, T *Zf,
+                  cudaStream_t st) {
+  for (int l = 0; l < nlev(a); l++) {
+    const long long o = loff(a, l);
+    k_limit<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], X + o, z + o, Wst + o, F + o, Zf + o);
+  }
+  launch_views<T>(a, PL, F, Zf, st);
+}
+
+// friction, limit, stage 1 and limit of step s: the two stage inputs (Un, Ui)
+// and their stored and flux views (on a frozen grid the views of every level)
+template <typename T>
+void recompute_stages(mwdg_adj *a, const Par<T> *PL, const T *U, const T *z, const T *nman, int s,
+                      const double *dts, uint8_t *clip, cudaStream_t st) {
   const StageArrays<T> v = stage_arrays<T>(a, s);
   T *Un = v.Un, *Ui = v.Ui, *W1 = ptr<T>(a->W1), *F1 = v.F1, *Z1 = v.Z1;
   T *W2 = ptr<T>(a->W2), *F2 = v.F2, *Z2 = v.Z2;
   {
     Timed tm(a, MWDG_ADJ_KC_FRICTION, st);
-    k_friction<T><<<nb, TPB, 0, st>>>(P, U, nman, dts, a->tt, s, Un);
+    for (int l = 0; l < nlev(a); l++) {
+      const long long o = loff(a, l);
+      k_friction<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], U + o, nman + o, dts, a->tt, s, Un + o);
+    }
   }
   {
     Timed tm(a, MWDG_ADJ_KC_LIMIT, st);
-    k_limit<T><<<nb, TPB, 0, st>>>(P, Un, z, W1, F1, Z1);
+    launch_limit<T>(a, PL, Un, z, W1, F1, Z1, st);
   }
-  const dim3 tiles((P.nx + UT - 1) / UT, (P.ny + UT - 1) / UT);
   {
     Timed tm(a, MWDG_ADJ_KC_UPDATE, st);
-    k_update<T><<<tiles, UT * UT, 0, st>>>(P, 1, F1, Z1, W1, nullptr, dts, a->tt, s, Ui, clip);
+    launch_update<T>(a, PL, 1, F1, Z1, W1, nullptr, dts, s, Ui, clip, st);
   }
   Timed tm(a, MWDG_ADJ_KC_LIMIT, st);
-  k_limit<T><<<nb, TPB, 0, st>>>(P, Ui, z, W2, F2, Z2);
+  launch_limit<T>(a, PL, Ui, z, W2, F2, Z2, st);
 }
 
 // the forward sweep of one step s from tape slot s into slot s + 1
 template <typename T>
-void launch_step(mwdg_adj *a, const Par<T> &P, const T *z, const T *nman, int s, bool cfl, double *dts,
+void launch_step(mwdg_adj *a, const Par<T> *PL, const T *z, const T *nman, int s, bool cfl, double *dts,
                  cudaStream_t st) {
   const long long n = a->n;
   const T *U = ptr<T>(a->tape) + (long long)s * 9 * n;
   T *Unext = ptr<T>(a->tape) + (long long)(s + 1) * 9 * n;
   uint8_t *clip = a->clip + (long long)s * n;
-  const unsigned nb = blocks(n);
   if (cfl) {
     Timed tm(a, MWDG_ADJ_KC_CFL, st);
-    k_cfl<T><<<nb, TPB, 0, st>>>(P, U, a->tt, s, a->best);
-    k_dt<<<1, 1, 0, st>>>(P.cfl, P.dt_max, a->best, dts, a->tt, s);
+    for (int l = 0; l < nlev(a); l++)
+      k_cfl<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], U + loff(a, l), a->tt, s, a->best);
+    k_dt<<<1, 1, 0, st>>>(PL[0].cfl, PL[0].dt_max, a->best, dts, a->tt, s);
   }
-  recompute_stages<T>(a, P, U, z, nman, s, dts, clip, st);
+  recompute_stages<T>(a, PL, U, z, nman, s, dts, clip, st);
   const StageArrays<T> v = stage_arrays<T>(a, s);
-  const dim3 tiles((P.nx + UT - 1) / UT, (P.ny + UT - 1) / UT);
   Timed tm(a, MWDG_ADJ_KC_UPDATE, st);
-  k_update<T><<<tiles, UT * UT, 0, st>>>(P, 2, v.F2, v.Z2, ptr<T>(a->W2), ptr<T>(a->W1), dts, a->tt, s, Unext, clip);
+  launch_update<T>(a, PL, 2, v.F2, v.Z2, ptr<T>(a->W2), ptr<T>(a->W1), dts, s, Unext, clip, st);
+}
+
+// per-level parameters (one entry on a uniform grid)
+template <typename T>
+std::vector<Par<T>> level_pars(const mwdg_adj *a, int nknots, const double *kt, const double *kQ) {
+  std::vector<Par<T>> PL;
+  for (int l = 0; l < nlev(a); l++) PL.push_back(level_par<T>(a, l, nknots, kt, kQ));
+  return PL;
+}
+
+// a frozen grid's bed and Manning pyramids from the finest planes and raster
+template <typename T>
+void launch_pyramids(const mwdg_adj *a, const Par<T> *PL, const T *z, const T *nman, cudaStream_t st) {
+  const int L = a->levels - 1;
+  const long long nt = a->n, nf = a->nfin, oL = a->off[L];
+  k_copy_planes<T><<<blocks(nf), TPB, 0, st>>>(3, nf, z, nf, ptr<T>(a->zp) + oL, nt, 0);
+  k_copy_planes<T><<<blocks(nf), TPB, 0, st>>>(1, nf, nman, nf, ptr<T>(a->np) + oL, nt, 0);
+  for (int l = L - 1; l >= 0; l--)
+    k_pyramid_level<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], ptr<T>(a->zp) + a->off[l], ptr<T>(a->np) + a->off[l]);
+}
+
+// a frozen grid's tape slot 0: still water everywhere, the leaves' coefficients at their nodes
+template <typename T>
+void launch_scatter_state(const mwdg_adj *a, const T *U0, cudaStream_t st) {
+  k_still<T><<<blocks(a->n), TPB, 0, st>>>(a->n, ptr<T>(a->tape));
+  k_leaves_to_nodes<T><<<blocks(a->nl), TPB, 0, st>>>(a->nl, a->n, a->node, U0, ptr<T>(a->tape));
 }
 
 mwdg_status check_run(mwdg_adj *a, const void *U0, const void *z, const void *n, int32_t nknots, const double *kt,
@@ -1410,15 +1912,23 @@ template <typename T>
 mwdg_status forward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int32_t nknots, const double *kt,
                       const double *kQ, double t0, int32_t steps, int32_t fixed_dt, double *dts, T *U_out,
                       cudaStream_t st) {
-  const Par<T> P = make_par<T>(a, nknots, kt, kQ);
+  const std::vector<Par<T>> PL = level_pars<T>(a, nknots, kt, kQ);
   const size_t bytes = (size_t)9 * a->n * sizeof(T);
-  if (cudaMemcpyAsync(a->tape, U0, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  if (a->levels) {
+    launch_pyramids<T>(a, PL.data(), z, nman, st);
+    z = ptr<T>(a->zp);
+    nman = ptr<T>(a->np);
+    launch_scatter_state<T>(a, U0, st);
+  } else if (cudaMemcpyAsync(a->tape, U0, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
     return cuda_check(a, "mwdg_adj_forward copy-in");
+  }
   k_set_t0<<<1, 1, 0, st>>>(a->tt, t0);
   if (fixed_dt) k_times<<<1, 1, 0, st>>>(dts, steps, a->tt);
-  for (int k = 0; k < steps; k++) launch_step<T>(a, P, z, nman, k, !fixed_dt, dts, st);
-  if (cudaMemcpyAsync(U_out, ptr<T>(a->tape) + (long long)steps * 9 * a->n, bytes, cudaMemcpyDeviceToDevice, st) !=
-      cudaSuccess)
+  for (int k = 0; k < steps; k++) launch_step<T>(a, PL.data(), z, nman, k, !fixed_dt, dts, st);
+  const T *UK = ptr<T>(a->tape) + (long long)steps * 9 * a->n;
+  if (a->levels)
+    k_nodes_to_leaves<T><<<blocks(a->nl), TPB, 0, st>>>(a->nl, a->n, a->node, UK, U_out);
+  else if (cudaMemcpyAsync(U_out, UK, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return cuda_check(a, "mwdg_adj_forward copy-out");
   return cuda_check(a, "mwdg_adj_forward");
 }
@@ -1427,28 +1937,51 @@ template <typename T>
 mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int32_t nknots, const double *kt,
                        const double *kQ, double t0, int32_t steps, const double *dts_in, const T *gUK, T *gU0, T *gz,
                        T *gn, double *gQ, bool reuse, cudaStream_t st) {
-  const Par<T> P = make_par<T>(a, nknots, kt, kQ);
+  const std::vector<Par<T>> PL = level_pars<T>(a, nknots, kt, kQ);
   const long long n = a->n;
+  const bool fz = a->levels > 0;
+  const int NL = nlev(a), L = NL - 1;
   const size_t bytes = (size_t)9 * n * sizeof(T);
-  const unsigned nb = blocks(n);
-  const long long nfx = (long long)a->p.ny * (a->p.nx + 1), nfy = (long long)(a->p.ny + 1) * a->p.nx;
   T *lU = ptr<T>(a->lU), *lX = ptr<T>(a->lX), *lW1 = ptr<T>(a->lW1);
   T *limx = ptr<T>(a->limx), *limy = ptr<T>(a->limy), *lXo = ptr<T>(a->lXo), *lnb = ptr<T>(a->lnb);
+  T *gV = ptr<T>(a->gV);
+  // the gradients of a frozen grid's level pyramids, folded to the finest
+  // level at the end
+  T *gzl = gz, *gnl = gn;
+  if (fz) {
+    launch_pyramids<T>(a, PL.data(), z, nman, st);
+    z = ptr<T>(a->zp);
+    nman = ptr<T>(a->np);
+    gzl = ptr<T>(a->gzp);
+    gnl = ptr<T>(a->gnp);
+    if (cudaMemsetAsync(gzl, 0, (size_t)3 * n * sizeof(T), st) != cudaSuccess ||
+        cudaMemsetAsync(gnl, 0, (size_t)n * sizeof(T), st) != cudaSuccess)
+      return cuda_check(a, "mwdg_adj_backward clear");
+  }
   // the tape: the run recomputed from its checkpoint U0 over the given steps,
   // unless the caller states that the last forward call left it in place
   if (steps > 0 && cudaMemcpyAsync(a->dtbuf, dts_in, (size_t)steps * sizeof(double), cudaMemcpyDeviceToDevice,
                                    st) != cudaSuccess)
     return cuda_check(a, "mwdg_adj_backward dts");
   if (!reuse) {
-    if (cudaMemcpyAsync(a->tape, U0, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    if (fz)
+      launch_scatter_state<T>(a, U0, st);
+    else if (cudaMemcpyAsync(a->tape, U0, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return cuda_check(a, "mwdg_adj_backward copy-in");
     k_set_t0<<<1, 1, 0, st>>>(a->tt, t0);
     k_times<<<1, 1, 0, st>>>(a->dtbuf, steps, a->tt);
-    for (int k = 0; k < steps; k++) launch_step<T>(a, P, z, nman, k, false, a->dtbuf, st);
+    for (int k = 0; k < steps; k++) launch_step<T>(a, PL.data(), z, nman, k, false, a->dtbuf, st);
   }
-  if (cudaMemcpyAsync(lU, gUK, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  if (fz) {
+    if (cudaMemsetAsync(lU, 0, bytes, st) != cudaSuccess) return cuda_check(a, "mwdg_adj_backward seed");
+    k_leaves_to_nodes<T><<<blocks(a->nl), TPB, 0, st>>>(a->nl, n, a->node, gUK, lU);
+  } else if (cudaMemcpyAsync(lU, gUK, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
     return cuda_check(a, "mwdg_adj_backward seed");
+  }
   const double *dts = a->dtbuf;
+  auto fx = [&](int l) { return fz ? limx + 14 * a->fxo[l] : limx; };
+  auto fy = [&](int l) { return fz ? limy + 14 * a->fyo[l] : limy; };
+  auto lqo = [&](int l) { return fz ? a->lq + a->lqo[l] : a->lq; };
   for (int k = steps - 1; k >= 0; k--) {
     const T *U = ptr<T>(a->tape) + (long long)k * 9 * n;
     const T *Y2 = ptr<T>(a->tape) + (long long)(k + 1) * 9 * n;
@@ -1456,7 +1989,7 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
     // the stage inputs of step k and their flux views: kept on the tape, or
     // recomputed (stage 1 then rewrites its clip bit with the same value and
     // keeps stage 2's from the tape run)
-    if (!a->views) recompute_stages<T>(a, P, U, z, nman, k, dts, clip, st);
+    if (!a->views) recompute_stages<T>(a, PL.data(), U, z, nman, k, dts, clip, st);
     const StageArrays<T> v = stage_arrays<T>(a, k);
     const T *Un = v.Un, *Ui = v.Ui, *F1 = v.F1, *Z1 = v.Z1, *F2 = v.F2, *Z2 = v.Z2;
     for (int stage = 2; stage >= 1; stage--) {
@@ -1467,27 +2000,122 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
       const T *lY = stage == 2 ? lU : lX;
       {
         Timed tm(a, MWDG_ADJ_KC_REV_FACE, st);
-        k_rev_face<T, true><<<blocks(nfx), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, lY, Y, clip, limx, a->lq);
-        k_rev_face<T, false><<<blocks(nfy), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf, Zf, lY, Y, clip, limy,
-                                                          a->lq);
+        for (int l = 0; l < NL; l++) {
+          const Par<T> &P = PL[l];
+          const long long o = loff(a, l);
+          const long long nfx = (long long)P.ny * (P.nx + 1), nfy = (long long)(P.ny + 1) * P.nx;
+          k_rev_face<T, true><<<blocks(nfx), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf + o, Zf + o, lY + o, Y + o,
+                                                           clip + o, fx(l), lqo(l));
+          k_rev_face<T, false><<<blocks(nfy), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf + o, Zf + o, lY + o, Y + o,
+                                                            clip + o, fy(l), lqo(l));
+        }
       }
-      if (P.nknots > 0) {
+      if (PL[0].nknots > 0) {
         Timed tm(a, MWDG_ADJ_KC_REV_KNOTS, st);
-        k_rev_knots<T><<<1, TPB, 0, st>>>(P, stage, dts, a->tt, k, a->lq, gQ);
+        for (int l = 0; l < NL; l++) k_rev_knots<T><<<1, TPB, 0, st>>>(PL[l], stage, dts, a->tt, k, lqo(l), gQ);
       }
       {
         Timed tm(a, MWDG_ADJ_KC_REV_LIMIT, st);
-        k_rev_limit<T><<<nb, TPB, 0, st>>>(P, stage, dts, k, X, z, lY, Y, clip, lW1, limx, limy, lXo, lnb, gz);
+        if (fz) {
+          // the views in reverse: every node's view-plane cotangents, then
+          // the prolongations (finest level up) and encodings (coarsest
+          // down) transposed onto the leaves
+          for (int l = 0; l <= L; l++)
+            k_rev_view_gather<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], fx(l), fy(l), l > 0 ? fx(l - 1) : nullptr,
+                                                                  l > 0 ? fy(l - 1) : nullptr, gV + loff(a, l));
+          for (int l = L - 1; l >= 0; l--) k_rev_prolong<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gV + loff(a, l));
+          for (int l = 1; l <= L; l++) k_rev_encode<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gV + loff(a, l));
+        }
+        for (int l = 0; l < NL; l++) {
+          const long long o = loff(a, l);
+          if (fz)
+            k_rev_limit<T, true><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], stage, dts, k, X + o, z + o, lY + o, Y + o,
+                                                                  clip + o, lW1 + o, nullptr, nullptr, gV + o, lXo + o,
+                                                                  lnb + o, gzl + o);
+          else
+            k_rev_limit<T, false><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], stage, dts, k, X + o, z + o, lY + o,
+                                                                   Y + o, clip + o, lW1 + o, fx(l), fy(l), nullptr,
+                                                                   lXo + o, lnb + o, gzl + o);
+        }
       }
       Timed tm(a, MWDG_ADJ_KC_REV_GATHER, st);
-      k_rev_gather<T><<<nb, TPB, 0, st>>>(P, lXo, lnb, lX, gz);
+      for (int l = 0; l < NL; l++) {
+        const long long o = loff(a, l);
+        k_rev_gather<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], lXo + o, lnb + o, lX + o, gzl + o);
+      }
     }
     Timed tm(a, MWDG_ADJ_KC_REV_FRICTION, st);
-    k_rev_friction<T><<<nb, TPB, 0, st>>>(P, U, nman, dts, a->tt, k, lX, lU, gn);
+    for (int l = 0; l < NL; l++) {
+      const long long o = loff(a, l);
+      k_rev_friction<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], U + o, nman + o, dts, a->tt, k, lX + o, lU + o,
+                                                         gnl + o);
+    }
   }
-  if (cudaMemcpyAsync(gU0, lU, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  if (fz) {
+    k_nodes_to_leaves<T><<<blocks(a->nl), TPB, 0, st>>>(a->nl, n, a->node, lU, gU0);
+    // the pyramids in reverse, from the coarsest level down; the finest
+    // level's cotangents are the gradients of z and n
+    for (int l = 1; l <= L; l++)
+      k_pyramid_level_t<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gzl + a->off[l], gnl + a->off[l]);
+    const long long nf = a->nfin, oL = a->off[L];
+    k_copy_planes<T><<<blocks(nf), TPB, 0, st>>>(3, nf, gzl + oL, n, gz, nf, 1);
+    k_copy_planes<T><<<blocks(nf), TPB, 0, st>>>(1, nf, gnl + oL, n, gn, nf, 1);
+  } else if (cudaMemcpyAsync(gU0, lU, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
     return cuda_check(a, "mwdg_adj_backward copy-out");
+  }
   return cuda_check(a, "mwdg_adj_backward");
+}
+
+mwdg_status check_params(const mwdg_adj_params *p) {
+  if (p->nx < 1 || p->ny < 1 || (long long)p->nx * p->ny > (1LL << 28) || !(p->dx > 0.0) || p->max_steps < 1)
+    return MWDG_ERR_DIMS;
+  if (!(p->g > 0.0) || !(p->h_dry >= 0.0) || !(p->cfl > 0.0) || !(p->dt_max > 0.0) || p->rain_rate < 0.0)
+    return MWDG_ERR_ARG;
+  if (p->precision != MWDG_F64 && p->precision != MWDG_F32) return MWDG_ERR_ARG;
+  for (int e = 0; e < 4; e++)
+    if (p->bc[e] != MWDG_WALL && p->bc[e] != MWDG_OPEN) return MWDG_ERR_ARG;
+  if (p->inflow_edge >= 4 || p->inflow_edge < -1) return MWDG_ERR_ARG;
+  if (p->inflow_edge >= 0) {
+    const int len = p->inflow_edge < 2 ? p->ny : p->nx;
+    if (p->inflow_c0 < 0 || p->inflow_c1 < p->inflow_c0 || p->inflow_c1 >= len) return MWDG_ERR_ARG;
+  }
+  return MWDG_OK;
+}
+
+// the tape and work arrays of a context with a->n nodes, nfx and nfy faces
+// (all levels) and nedge boundary entries; false when an allocation fails
+bool allocate(mwdg_adj *a, long long nfx, long long nfy, long long nedge) {
+  const mwdg_adj_params *p = &a->p;
+  a->elem = p->precision == MWDG_F32 ? sizeof(float) : sizeof(double);
+  const long long n = a->n, S = p->max_steps;
+  const size_t E = a->elem;
+  bool ok = true;
+  auto alloc = [&](void **ptrp, long long count, size_t elem) {
+    if (ok && cudaMalloc(ptrp, (size_t)count * elem) != cudaSuccess) ok = false;
+  };
+  alloc(&a->tape, (S + 1) * 9 * n, E);
+  alloc((void **)&a->clip, S * n, 1);
+  alloc((void **)&a->tt, S + 1, sizeof(double));
+  alloc((void **)&a->dtbuf, S, sizeof(double));
+  alloc((void **)&a->best, 1, sizeof(unsigned long long));
+  a->views = p->tape_views != 0;
+  const long long SV = a->views ? S : 1;   // copies of the stage arrays
+  for (void **w : {&a->Un, &a->Ui, &a->F1, &a->F2}) alloc(w, SV * 9 * n, E);
+  alloc(&a->Z1, SV * 3 * n, E);
+  alloc(&a->Z2, SV * 3 * n, E);
+  for (void **w : {&a->W1, &a->W2, &a->lU, &a->lX, &a->lW1, &a->lXo}) alloc(w, 9 * n, E);
+  alloc(&a->lnb, 12 * n, E);
+  alloc(&a->limx, 14 * nfx, E);
+  alloc(&a->limy, 14 * nfy, E);
+  alloc((void **)&a->lq, nedge, sizeof(double));
+  if (ok) {
+    const unsigned long long inf = 0x7ff0000000000000ull;
+    ok = cudaMemcpy(a->best, &inf, sizeof inf, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(a->lq, 0, (size_t)nedge * sizeof(double)) == cudaSuccess &&
+         cudaMemset(a->clip, 0, (size_t)(S * n)) == cudaSuccess;
+  }
+  if (!ok) cudaGetLastError();
+  return ok;
 }
 
 }  // namespace
@@ -1514,52 +2142,116 @@ mwdg_status mwdg_adj_params_default(mwdg_adj_params *p) {
 mwdg_status mwdg_adj_create(const mwdg_adj_params *p, mwdg_adj **out) {
   if (!p || !out) return MWDG_ERR_ARG;
   *out = nullptr;
-  if (p->nx < 1 || p->ny < 1 || (long long)p->nx * p->ny > (1LL << 28) || !(p->dx > 0.0) || p->max_steps < 1)
+  const mwdg_status v = check_params(p);
+  if (v != MWDG_OK) return v;
+  mwdg_adj *a = new (std::nothrow) mwdg_adj;
+  if (!a) return MWDG_ERR_CUDA;
+  a->p = *p;
+  a->n = a->nfin = (long long)p->nx * p->ny;
+  const long long nfx = (long long)p->ny * (p->nx + 1), nfy = (long long)(p->ny + 1) * p->nx;
+  if (!allocate(a, nfx, nfy, p->nx > p->ny ? p->nx : p->ny)) {
+    free_all(a);
+    delete a;
+    return MWDG_ERR_CUDA;
+  }
+  *out = a;
+  return MWDG_OK;
+}
+
+mwdg_status mwdg_adj_create_frozen(const mwdg_adj_params *p, int32_t M, int32_t N, int32_t L, int32_t mode,
+                                   int64_t n_leaves, const int32_t *level, const int32_t *ii, const int32_t *jj,
+                                   mwdg_adj **out) {
+  if (!p || !out) return MWDG_ERR_ARG;
+  *out = nullptr;
+  if (M < 1 || N < 1 || L < 0 || L > MWDG_LMAX || ((long long)M << L) != p->nx || ((long long)N << L) != p->ny)
     return MWDG_ERR_DIMS;
-  if (!(p->g > 0.0) || !(p->h_dry >= 0.0) || !(p->cfl > 0.0) || !(p->dt_max > 0.0) || p->rain_rate < 0.0)
-    return MWDG_ERR_ARG;
-  if (p->precision != MWDG_F64 && p->precision != MWDG_F32) return MWDG_ERR_ARG;
-  for (int e = 0; e < 4; e++)
-    if (p->bc[e] != MWDG_WALL && p->bc[e] != MWDG_OPEN) return MWDG_ERR_ARG;
-  if (p->inflow_edge >= 4 || p->inflow_edge < -1) return MWDG_ERR_ARG;
-  if (p->inflow_edge >= 0) {
-    const int len = p->inflow_edge < 2 ? p->ny : p->nx;
-    if (p->inflow_c0 < 0 || p->inflow_c1 < p->inflow_c0 || p->inflow_c1 >= len) return MWDG_ERR_ARG;
+  if (mode != MWDG_STATIC && mode != MWDG_ADAPTIVE) return MWDG_ERR_ARG;
+  const mwdg_status v = check_params(p);
+  if (v != MWDG_OK) return v;
+  if (n_leaves < 1 || !level || !ii || !jj) return MWDG_ERR_ARG;
+  // the levels' geometry and node kinds; the leaves must tile the domain
+  std::vector<long long> off(L + 2), fxo(L + 2), fyo(L + 2), lqo(L + 2);
+  for (int l = 0; l <= L; l++) {
+    const long long nx = (long long)M << l, ny = (long long)N << l;
+    off[l + 1] = off[l] + nx * ny;
+    fxo[l + 1] = fxo[l] + ny * (nx + 1);
+    fyo[l + 1] = fyo[l] + (ny + 1) * nx;
+    lqo[l + 1] = lqo[l] + (nx > ny ? nx : ny);
+  }
+  const long long nt = off[L + 1];
+  std::vector<uint8_t> kind((size_t)nt, K_BELOW);
+  std::vector<long long> node((size_t)n_leaves);
+  for (int64_t q = 0; q < n_leaves; q++) {
+    const int l = level[q];
+    if (l < 0 || l > L) return MWDG_ERR_ARG;
+    const long long nx = (long long)M << l, ny = (long long)N << l;
+    if (ii[q] < 0 || jj[q] < 0 || ii[q] >= nx || jj[q] >= ny) return MWDG_ERR_ARG;
+    const long long k = off[l] + (long long)jj[q] * nx + ii[q];
+    if (kind[(size_t)k] == K_LEAF) return MWDG_ERR_ARG;  // listed twice
+    kind[(size_t)k] = K_LEAF;
+    node[(size_t)q] = k;
+  }
+  // refined: a node with a leaf or a refined node among its children
+  for (int l = L - 1; l >= 0; l--) {
+    const long long nx = (long long)M << l, ny = (long long)N << l;
+    for (long long j = 0; j < ny; j++)
+      for (long long i = 0; i < nx; i++) {
+        const long long k = off[l] + j * nx + i;
+        bool sub = false;
+        for (int c = 0; c < 4; c++) {
+          const long long kc = off[l + 1] + (2 * j + (c >> 1)) * (2 * nx) + 2 * i + (c & 1);
+          sub = sub || kind[(size_t)kc] != K_BELOW;
+        }
+        if (sub) {
+          if (kind[(size_t)k] == K_LEAF) return MWDG_ERR_ARG;  // a leaf above another leaf
+          kind[(size_t)k] = K_SIG;
+        }
+      }
+  }
+  // every root is a leaf or refined, every refined node's children leaves or
+  // refined, so that each finest cell lies under exactly one leaf
+  for (long long k = 0; k < off[1]; k++)
+    if (kind[(size_t)k] == K_BELOW) return MWDG_ERR_ARG;
+  for (int l = 0; l < L; l++) {
+    const long long nx = (long long)M << l, ny = (long long)N << l;
+    for (long long j = 0; j < ny; j++)
+      for (long long i = 0; i < nx; i++) {
+        if (kind[(size_t)(off[l] + j * nx + i)] != K_SIG) continue;
+        for (int c = 0; c < 4; c++) {
+          const long long kc = off[l + 1] + (2 * j + (c >> 1)) * (2 * nx) + 2 * i + (c & 1);
+          if (kind[(size_t)kc] == K_BELOW) return MWDG_ERR_ARG;
+        }
+      }
   }
   mwdg_adj *a = new (std::nothrow) mwdg_adj;
   if (!a) return MWDG_ERR_CUDA;
   a->p = *p;
-  a->n = (long long)p->nx * p->ny;
-  a->elem = p->precision == MWDG_F32 ? sizeof(float) : sizeof(double);
-  const long long n = a->n, S = p->max_steps;
-  const size_t E = a->elem;
-  const long long nfx = (long long)p->ny * (p->nx + 1), nfy = (long long)(p->ny + 1) * p->nx;
-  const long long nedge = p->nx > p->ny ? p->nx : p->ny;
-  bool ok = true;
+  a->levels = L + 1;
+  a->mode = mode;
+  a->gM = M;
+  a->gN = N;
+  a->off = off;
+  a->fxo = fxo;
+  a->fyo = fyo;
+  a->lqo = lqo;
+  a->nl = n_leaves;
+  a->n = nt;
+  a->nfin = (long long)p->nx * p->ny;
+  const size_t E = p->precision == MWDG_F32 ? sizeof(float) : sizeof(double);
+  bool ok = allocate(a, fxo[L + 1], fyo[L + 1], lqo[L + 1]);
   auto alloc = [&](void **ptrp, long long count, size_t elem) {
     if (ok && cudaMalloc(ptrp, (size_t)count * elem) != cudaSuccess) ok = false;
   };
-  alloc(&a->tape, (S + 1) * 9 * n, E);
-  alloc((void **)&a->clip, S * n, 1);
-  alloc((void **)&a->tt, S + 1, sizeof(double));
-  alloc((void **)&a->dtbuf, S, sizeof(double));
-  alloc((void **)&a->best, 1, sizeof(unsigned long long));
-  a->views = p->tape_views != 0;
-  const long long SV = a->views ? S : 1;   // copies of the stage arrays
-  for (void **w : {&a->Un, &a->Ui, &a->F1, &a->F2}) alloc(w, SV * 9 * n, E);
-  alloc(&a->Z1, SV * 3 * n, E);
-  alloc(&a->Z2, SV * 3 * n, E);
-  for (void **w : {&a->W1, &a->W2, &a->lU, &a->lX, &a->lW1, &a->lXo}) alloc(w, 9 * n, E);
-  alloc(&a->lnb, 12 * n, E);
-  alloc(&a->limx, 14 * nfx, E);
-  alloc(&a->limy, 14 * nfy, E);
-  alloc((void **)&a->lq, nedge, sizeof(double));
-  if (ok) {
-    const unsigned long long inf = 0x7ff0000000000000ull;
-    ok = cudaMemcpy(a->best, &inf, sizeof inf, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemset(a->lq, 0, (size_t)nedge * sizeof(double)) == cudaSuccess &&
-         cudaMemset(a->clip, 0, (size_t)(S * n)) == cudaSuccess;
-  }
+  alloc((void **)&a->kind, nt, 1);
+  alloc((void **)&a->node, n_leaves, sizeof(long long));
+  alloc(&a->zp, 3 * nt, E);
+  alloc(&a->np, nt, E);
+  alloc(&a->gzp, 3 * nt, E);
+  alloc(&a->gnp, nt, E);
+  alloc(&a->gV, 12 * nt, E);
+  ok = ok && cudaMemcpy(a->kind, kind.data(), (size_t)nt, cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(a->node, node.data(), (size_t)n_leaves * sizeof(long long), cudaMemcpyHostToDevice) ==
+           cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_all(a);
@@ -1616,7 +2308,7 @@ mwdg_status mwdg_adj_kernel_times(mwdg_adj *a, double *ms, int64_t *count) {
 mwdg_status mwdg_adj_project(mwdg_adj *a, const double *vert, void *out, void *stream) {
   if (!a) return MWDG_ERR_ARG;
   if (!vert || !out) return fail(a, MWDG_ERR_ARG, "NULL pointer");
-  const unsigned nb = blocks(a->n);
+  const unsigned nb = blocks((long long)a->p.nx * a->p.ny);
   if (a->p.precision == MWDG_F32)
     k_project<float><<<nb, TPB, 0, (cudaStream_t)stream>>>(make_par<float>(a, 0, nullptr, nullptr), vert,
                                                             ptr<float>(out));

@@ -128,3 +128,35 @@ def test_create_rejects_bad_combinations_without_device(combo):
     h = C.c_void_p(1)
     assert L.mwdg_create(C.byref(p), C.byref(h)) == want
     assert not h.value
+
+
+def test_frozen_adjoint_grid_is_validated_without_device():
+    """mwdg_adj_create_frozen checks the sizes against M, N, L and that the
+    leaves tile the domain (no gap, no overlap, none listed twice or out of
+    range) before any device work"""
+    import ctypes as C
+    import numpy as np
+    L = adjoint.lib()
+
+    def create(lev, ii, jj, M=1, N=1, Lv=2, mode=1, nx=4, ny=4):
+        p = adjoint.AdjParams()
+        L.mwdg_adj_params_default(C.byref(p))
+        p.nx, p.ny, p.dx = nx, ny, 1.0
+        a = [np.ascontiguousarray(x, dtype=np.int32) for x in (lev, ii, jj)]
+        h = C.c_void_p(7)
+        st = L.mwdg_adj_create_frozen(C.byref(p), M, N, Lv, mode, len(a[0]), *(x.ctypes.data_as(C.c_void_p)
+                                                                               for x in a), C.byref(h))
+        assert st == 0 or not h.value
+        return st
+
+    # one level-1 quadrant refined into four level-2 leaves, three level-1 leaves
+    lev = [1, 1, 1, 2, 2, 2, 2]
+    ii = [1, 0, 1, 0, 1, 0, 1]
+    jj = [0, 1, 1, 0, 0, 1, 1]
+    assert create(lev, ii, jj, nx=8) == -2            # nx is not M 2^L
+    assert create(lev, ii, jj, mode=0) == -1          # uniform is not a frozen grid's mode
+    assert create(lev[:-1], ii[:-1], jj[:-1]) == -1   # a gap
+    assert create(lev + [2], ii + [1], jj + [1]) == -1     # listed twice
+    assert create(lev + [0], ii + [0], jj + [0]) == -1     # a leaf over other leaves
+    assert create(lev[:-1] + [2], ii[:-1] + [4], jj[:-1] + [0]) == -1   # out of range
+    assert create([1, 1, 1, 1], [0, 1, 0, 1], [0, 0, 1, 1], Lv=16) == -2
