@@ -32,10 +32,17 @@ taken, the interface bed max split at ties, zero derivative of the Manning
 speed at rest).  The static reflux rule is not restated (the paper rule
 only).
 
+`regrid` restates the state transfer of the MWDG2 adaptation between two
+such grids (the C oracle's orc_adapt with the new grid it chose), so that a
+run of frozen segments re-frozen at each checkpoint is differentiable.
+
 Pinned by the tests against: the C oracle's steps over recorded time steps,
 bit for bit; central differences of the C oracle's fixed-dt steps with
 respect to DEM vertices, the Manning raster, initial depth vertices (static)
-and hydrograph knots.
+and hydrograph knots; the C oracle's adaptation (regrid) bit for bit, and
+central differences of two frozen segments with the C oracle's regridding
+between them; the refinement's invariants (children's depths non-negative,
+the parent's average kept, planes with non-negative children unchanged).
 """
 from __future__ import annotations
 
@@ -440,6 +447,60 @@ def run(z_vert, n_finest, h_vert, qx_vert, qy_vert, Q, dts, t0, G: LeafGrid):
         U = step(U, zc, nm, Q, float(dt), t, G)
         t = t + float(dt)
     return leaves_of(U, G)
+
+
+# ---------------------------------------------------------------------------
+# regridding at a checkpoint: the MWDG2 adaptation's state transfer from one
+# frozen grid to the next, with its decisions (the new grid) held
+# ---------------------------------------------------------------------------
+def depth_plane_for_children(sp):
+    """The depth plane (c0, c1x, c1y) that a refinement prolongs: where one of
+    its four children's averages (Eq. 10 with zero details) would be
+    negative, its slopes are scaled about its average so that the smallest
+    becomes zero (the scaling limiter of Zhang & Shu 2010 at the children's
+    centres), or dropped when the plane has no content.  The smallest
+    child is taken as the first of them in child order (c = cx + 2 cy)."""
+    c0s = []
+    for c in range(4):
+        sx = 1.0 if c & 1 else -1.0
+        sy = 1.0 if c & 2 else -1.0
+        c0s.append((sp[0] + (HALF_S3 * sx) * sp[1]) + (HALF_S3 * sy) * sp[2])
+    stack = torch.stack(c0s)
+    idx = torch.argmin(stack.detach(), dim=0, keepdim=True)
+    m = torch.gather(stack, 0, idx)[0]
+    neg = m < 0.0
+    pos = sp[0] > 0.0
+    th = sp[0] / _safe(neg & pos, sp[0] - m)
+    zero = torch.zeros_like(sp[0])
+    s1 = _w(neg, _w(pos, sp[1] * th, zero), sp[1])
+    s2 = _w(neg, _w(pos, sp[2] * th, zero), sp[2])
+    return [sp[0], s1, s2]
+
+
+def regrid(coef, G1: LeafGrid, G2: LeafGrid):
+    """The leaves' coefficients on grid G2 from those on G1 (same roots and
+    levels), as the MWDG2 adaptation transfers them (Sect. 2.3): the state is
+    prolonged below G1's leaves down to the finest level (Eq. 10 with zero
+    details; depth planes kept non-negative for the children, a child's
+    rounding residue below zero depth set to zero), encoded up G1's refined
+    nodes (Eq. 9), and read at G2's leaves: a leaf of both grids keeps its
+    coefficients, a coarsened one takes its encoding, a refined one the
+    prolongation of its old leaf.  Summed in the C oracle's order."""
+    L = G1.L
+    U = dense_from_leaves(coef, G1)
+    for l in range(1, L + 1):
+        ny, nx = G1.ny(l), G1.nx(l)
+        par = U[l - 1]
+        pro = prolong_planes(depth_plane_for_children(par[0:3]), ny, nx)
+        pro += prolong_planes(par[3:6], ny, nx) + prolong_planes(par[6:9], ny, nx)
+        pro[0] = _w(pro[0] < 0.0, torch.zeros_like(pro[0]), pro[0])
+        U[l] = [_w(G1.below[l], pro[m], U[l][m]) for m in range(9)]
+    for l in range(L - 1, -1, -1):
+        enc = []
+        for g0 in (0, 3, 6):
+            enc += encode_planes(U[l + 1][g0:g0 + 3])
+        U[l] = [_w(G1.sig[l], enc[m], U[l][m]) for m in range(9)]
+    return leaves_of(U, G2)
 
 
 # ---------------------------------------------------------------------------
