@@ -151,6 +151,26 @@ MWDG_API mwdg_status mwdg_adj_backward(mwdg_adj *a, const void *U0, const void *
                                        int32_t steps, const double *dts, const void *gU_K, void *gU0,
                                        void *gz, void *gn, double *gQ, int32_t reuse_tape, void *cuda_stream);
 
+/* Regridding at a checkpoint between two frozen MWDG2 grids (contexts of
+ * mwdg_adj_create_frozen with the same M, N, L and precision): the state
+ * transfer of the MWDG2 adaptation (Sect. 2.3) with its decision -- the new
+ * grid, `to` -- held.  The old grid's state is prolonged below its leaves
+ * (Eq. 10 with zero details; a depth plane's slopes are first scaled about
+ * its average so that no child's average depth is negative, the scaling
+ * limiter of Zhang & Shu 2010, and a child's rounding residue below zero
+ * is set to zero) and encoded up its refined nodes (Eq. 9); each leaf of
+ * the new grid takes the coefficients of its node: kept, coarsened or
+ * refined.  U_from is 9 x (from's leaves), U_to 9 x (to's leaves).  The
+ * transpose takes U_from too (the scaling's branches are recomputed from
+ * it) and overwrites gU_from with the cotangent of U_from given gU_to.
+ * Both use from's work arrays (not during a call on from).  MWDG_ERR_ARG on
+ * a uniform context, NULL pointers or mixed precisions; MWDG_ERR_DIMS when
+ * the grids differ in roots or levels. */
+MWDG_API mwdg_status mwdg_adj_regrid(mwdg_adj *from, mwdg_adj *to, const void *U_from, void *U_to,
+                                     void *cuda_stream);
+MWDG_API mwdg_status mwdg_adj_regrid_transpose(mwdg_adj *from, mwdg_adj *to, const void *U_from,
+                                               const void *gU_to, void *gU_from, void *cuda_stream);
+
 /* Transpose of Eq. 8: plane cotangents (3 x n) -> vertex cotangents
  * ((ny+1) x (nx+1)), both coefficient arrays, overwritten. */
 MWDG_API mwdg_status mwdg_adj_project_transpose(mwdg_adj *a, const void *g_planes, void *g_vert,

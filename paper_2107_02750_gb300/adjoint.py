@@ -26,7 +26,7 @@ from .binding import MwdgError, lib as _lib, WALL, F64, F32, STATIC, ADAPTIVE
 ADJ_EXPORTS = (
     "mwdg_adj_params_default", "mwdg_adj_create", "mwdg_adj_create_frozen", "mwdg_adj_destroy", "mwdg_adj_project",
     "mwdg_adj_project_transpose", "mwdg_adj_forward", "mwdg_adj_backward", "mwdg_adj_last_error",
-    "mwdg_adj_profile", "mwdg_adj_kernel_times",
+    "mwdg_adj_profile", "mwdg_adj_kernel_times", "mwdg_adj_regrid", "mwdg_adj_regrid_transpose",
 )
 # kernel classes of mwdg_adj_kernel_times, in order
 ADJ_CLASSES = ("cfl", "friction", "limit", "update", "rev_face", "rev_knots", "rev_limit", "rev_gather",
@@ -57,13 +57,16 @@ def lib():
         L.mwdg_adj_project_transpose.argtypes = [vp, vp, vp, vp]
         L.mwdg_adj_forward.argtypes = [vp, vp, vp, vp, i32, vp, vp, dp, i32, i32, vp, vp, vp]
         L.mwdg_adj_backward.argtypes = [vp, vp, vp, vp, i32, vp, vp, dp, i32, vp, vp, vp, vp, vp, vp, i32, vp]
+        L.mwdg_adj_regrid.argtypes = [vp, vp, vp, vp, vp]
+        L.mwdg_adj_regrid_transpose.argtypes = [vp, vp, vp, vp, vp, vp]
         L.mwdg_adj_last_error.argtypes = [vp]
         L.mwdg_adj_last_error.restype = C.c_char_p
         L.mwdg_adj_profile.argtypes = [vp, i32]
         L.mwdg_adj_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in ("mwdg_adj_params_default", "mwdg_adj_create", "mwdg_adj_create_frozen", "mwdg_adj_project",
                      "mwdg_adj_project_transpose", "mwdg_adj_forward", "mwdg_adj_backward",
-                     "mwdg_adj_profile", "mwdg_adj_kernel_times"):
+                     "mwdg_adj_profile", "mwdg_adj_kernel_times", "mwdg_adj_regrid",
+                     "mwdg_adj_regrid_transpose"):
             getattr(L, name).restype = C.c_int
         L._adj_ready = True
     return L
@@ -224,6 +227,27 @@ class Dg2Adjoint:
         return gU0, gz, gn, gQ[:nk]
 
 
+def regrid_forward(src: "Dg2Adjoint", dst: "Dg2Adjoint", U):
+    """the leaves' coefficients on dst's grid from those on src's (the
+    MWDG2 adaptation's state transfer, mwdg_adj_regrid)"""
+    import torch
+    U = src._t(U, src._state_shape())
+    out = torch.empty((9, dst.n_leaves), dtype=src.dtype, device=src.device)
+    src._check(lib().mwdg_adj_regrid(src._h, dst._h, _ptr(U), _ptr(out), _stream()), "mwdg_adj_regrid")
+    return out
+
+
+def regrid_transpose(src: "Dg2Adjoint", dst: "Dg2Adjoint", U, gV):
+    """cotangent of U (on src's grid) given gV, that of its regridding"""
+    import torch
+    U = src._t(U, src._state_shape())
+    gV = dst._t(gV, dst._state_shape())
+    out = torch.empty_like(U)
+    src._check(lib().mwdg_adj_regrid_transpose(src._h, dst._h, _ptr(U), _ptr(gV), _ptr(out), _stream()),
+               "mwdg_adj_regrid_transpose")
+    return out
+
+
 def _autograd_function():
     import torch
 
@@ -255,6 +279,37 @@ def _autograd_function():
 
 
 _DG2RUN = None
+_REGRID = None
+
+
+def _regrid_function():
+    import torch
+
+    class Regrid(torch.autograd.Function):
+        """U on dst's grid from U on src's (a checkpoint's re-freezing)"""
+
+        @staticmethod
+        def forward(ctx, U, src, dst):
+            ctx.save_for_backward(U)
+            ctx.src, ctx.dst = src, dst
+            return regrid_forward(src, dst, U)
+
+        @staticmethod
+        def backward(ctx, gV):
+            (U,) = ctx.saved_tensors
+            return regrid_transpose(ctx.src, ctx.dst, U, gV.contiguous()), None, None
+
+    return Regrid
+
+
+def regrid(src: Dg2Adjoint, dst: Dg2Adjoint, U):
+    """Differentiable state transfer from src's frozen MWDG2 grid to dst's at
+    a checkpoint: chain dg2_run(src) -> regrid -> dg2_run(dst) to
+    differentiate a run whose grid is re-frozen at each checkpoint."""
+    global _REGRID
+    if _REGRID is None:
+        _REGRID = _regrid_function()
+    return _REGRID.apply(U, src, dst)
 
 
 def dg2_run(adj: Dg2Adjoint, U0, z, n, Q, knot_t, t0: float, steps: int, dts=None):

@@ -1627,6 +1627,179 @@ __global__ void __launch_bounds__(TPB) k_pyramid_level_t(Par<T> P, T *gZ, T *gN)
 }
 
 // ---------------------------------------------------------------------------
+// regridding at a checkpoint: the MWDG2 adaptation's state transfer from one
+// frozen grid to the next (Sect. 2.3), and its transpose.  D holds the state
+// on every node of every level of the old grid: its leaves' coefficients,
+// prolonged below them (Eq. 10 with zero details; a depth plane is first
+// kept non-negative for its children) and encoded up its refined nodes
+// (Eq. 9); the new grid's leaves read it at their nodes.
+// ---------------------------------------------------------------------------
+// The depth plane that a refinement prolongs: where a child's average would
+// be negative, the slopes are scaled about the average so that the
+// smallest child (the first in child order) is at zero depth (the scaling
+// limiter of Zhang & Shu 2010), or dropped when the plane has no content.
+// m and cm return that child's average and index (m >= 0: unchanged).
+template <typename T>
+__device__ __forceinline__ void depth_for_children(const T sp[3], T out[3], T &m, int &cm) {
+  const T H = T(0.5) * s3v<T>();
+  m = tinf<T>();
+  cm = 0;
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    const T sx = (c & 1) ? H : -H, sy = (c & 2) ? H : -H;
+    const T c0 = (sp[0] + sx * sp[1]) + sy * sp[2];
+    if (c0 < m) { m = c0; cm = c; }
+  }
+  out[0] = sp[0];
+  out[1] = sp[1];
+  out[2] = sp[2];
+  if (!(m < T(0))) return;
+  if (sp[0] > T(0)) {
+    const T th = sp[0] / (sp[0] - m);
+    out[1] = sp[1] * th;
+    out[2] = sp[2] * th;
+  } else {
+    out[1] = T(0);
+    out[2] = T(0);
+  }
+}
+
+// nodes of this level below a leaf of the old grid: the parent's planes
+// prolonged, depth kept non-negative (top-down)
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_regrid_prolong(Par<T> P, T *D) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j) || P.kind[k] != K_BELOW) return;
+  const long long n = P.ns;
+  const long long kp = -P.dp + (long long)(j >> 1) * (P.nx >> 1) + (i >> 1);
+  const int c = (i & 1) + 2 * (j & 1);
+#pragma unroll
+  for (int v = 0; v < 3; v++) {
+    T sp[3], sc[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) sp[q] = D[(3 * v + q) * n + kp];
+    if (v == 0) {
+      T dp[3], m;
+      int cm;
+      depth_for_children(sp, dp, m, cm);
+      prolong3(dp, c, sc);
+      if (sc[0] < T(0)) sc[0] = T(0);  // a rounding residue below zero depth
+    } else {
+      prolong3(sp, c, sc);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; q++) D[(3 * v + q) * n + k] = sc[q];
+  }
+}
+
+// refined nodes of the old grid on this level: the encoding of their
+// children (bottom-up)
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_regrid_encode(Par<T> P, T *D) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j) || P.kind[k] != K_SIG) return;
+  const long long n = P.ns;
+#pragma unroll 1
+  for (int v = 0; v < 3; v++) {
+    T ch[4][3], sp[3];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const long long kc = child_of(P, i, j, c);
+#pragma unroll
+      for (int q = 0; q < 3; q++) ch[c][q] = D[(3 * v + q) * n + kc];
+    }
+    encode3(ch, sp);
+#pragma unroll
+    for (int q = 0; q < 3; q++) D[(3 * v + q) * n + k] = sp[q];
+  }
+}
+
+// transpose of the encoding: a child of a refined node of the old grid (this
+// level) takes its share of the parent's cotangent (top-down)
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_regrid_encode_t(Par<T> P, T *gD) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j)) return;
+  const long long kp = -P.dp + (long long)(j >> 1) * (P.nx >> 1) + (i >> 1);
+  if (P.kind[kp] != K_SIG) return;
+  const long long n = P.ns;
+  const int c = (i & 1) + 2 * (j & 1);
+#pragma unroll
+  for (int v = 0; v < 3; v++) {
+    T gp[3], gc[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      gp[q] = gD[(3 * v + q) * n + kp];
+      gc[q] = gD[(3 * v + q) * n + k];
+    }
+    encode3_t(gp, c, gc);
+#pragma unroll
+    for (int q = 0; q < 3; q++) gD[(3 * v + q) * n + k] = gc[q];
+  }
+}
+
+// transpose of the prolongation: a leaf or a node below a leaf of the old
+// grid (this level) takes the cotangents of its children below it, through
+// the children's zero-depth cut and the depth plane's scaling (bottom-up)
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_regrid_prolong_t(Par<T> P, const T *D, T *gD) {
+  long long k;
+  int i, j;
+  if (!cell_of(P, k, i, j) || P.kind[k] == K_SIG) return;
+  const long long n = P.ns;
+  T sp[3], dp[3], m;
+  int cm;
+#pragma unroll
+  for (int q = 0; q < 3; q++) sp[q] = D[q * n + k];
+  depth_for_children(sp, dp, m, cm);
+  T gd[3] = {T(0), T(0), T(0)}, gq[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  bool any = false;
+#pragma unroll 1
+  for (int c = 0; c < 4; c++) {
+    const long long kc = child_of(P, i, j, c);
+    if (P.kind[kc] != K_BELOW) continue;
+    any = true;
+    T g[3], sc[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) g[q] = gD[q * n + kc];
+    prolong3(dp, c, sc);
+    if (sc[0] < T(0)) g[0] = T(0);
+    prolong3_t(g, c, gd);
+#pragma unroll
+    for (int v = 1; v < 3; v++) {
+#pragma unroll
+      for (int q = 0; q < 3; q++) g[q] = gD[(3 * v + q) * n + kc];
+      prolong3_t(g, c, gq + 3 * (v - 1));
+    }
+  }
+  if (!any) return;
+  // the depth plane's scaling in reverse (the smallest child's index held)
+  T gs[3] = {gd[0], gd[1], gd[2]};
+  if (m < T(0)) {
+    if (sp[0] > T(0)) {
+      const T d = sp[0] - m, th = sp[0] / d;
+      const T gth = gd[1] * sp[1] + gd[2] * sp[2];
+      const T H = T(0.5) * s3v<T>();
+      const T sx = (cm & 1) ? H : -H, sy = (cm & 2) ? H : -H;
+      const T dsp0 = -m / (d * d), dm = sp[0] / (d * d);
+      gs[1] = gd[1] * th + gth * dm * sx;
+      gs[2] = gd[2] * th + gth * dm * sy;
+      gs[0] = gd[0] + gth * dsp0 + gth * dm;
+    } else {
+      gs[1] = T(0);
+      gs[2] = T(0);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; q++) gD[q * n + k] += gs[q];
+#pragma unroll
+  for (int q = 0; q < 6; q++) gD[(3 + q) * n + k] += gq[q];
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 inline unsigned blocks(long long items) { return (unsigned)((items + TPB - 1) / TPB); }
@@ -2066,6 +2239,47 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
   return cuda_check(a, "mwdg_adj_backward");
 }
 
+// the old grid's state on every node of its levels (D, 9 x nodes) from its
+// leaves' coefficients
+template <typename T>
+void launch_regrid_state(const mwdg_adj *f, const T *U_from, T *D, cudaStream_t st) {
+  const int L = f->levels - 1;
+  const std::vector<Par<T>> PL = level_pars<T>(f, 0, nullptr, nullptr);
+  k_still<T><<<blocks(f->n), TPB, 0, st>>>(f->n, D);
+  k_leaves_to_nodes<T><<<blocks(f->nl), TPB, 0, st>>>(f->nl, f->n, f->node, U_from, D);
+  for (int l = 1; l <= L; l++) k_regrid_prolong<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], D + f->off[l]);
+  for (int l = L - 1; l >= 0; l--) k_regrid_encode<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], D + f->off[l]);
+}
+
+template <typename T>
+void launch_regrid(mwdg_adj *f, mwdg_adj *t, const T *U_from, T *U_to, cudaStream_t st) {
+  T *D = ptr<T>(f->lXo);
+  launch_regrid_state<T>(f, U_from, D, st);
+  k_nodes_to_leaves<T><<<blocks(t->nl), TPB, 0, st>>>(t->nl, f->n, t->node, D, U_to);
+}
+
+template <typename T>
+void launch_regrid_t(mwdg_adj *f, mwdg_adj *t, const T *U_from, const T *gU_to, T *gU_from, cudaStream_t st) {
+  const int L = f->levels - 1;
+  const std::vector<Par<T>> PL = level_pars<T>(f, 0, nullptr, nullptr);
+  T *D = ptr<T>(f->lXo), *gD = ptr<T>(f->lX);
+  launch_regrid_state<T>(f, U_from, D, st);
+  cudaMemsetAsync(gD, 0, (size_t)9 * f->n * sizeof(T), st);
+  k_leaves_to_nodes<T><<<blocks(t->nl), TPB, 0, st>>>(t->nl, f->n, t->node, gU_to, gD);
+  for (int l = 1; l <= L; l++) k_regrid_encode_t<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gD + f->off[l]);
+  for (int l = L - 1; l >= 0; l--)
+    k_regrid_prolong_t<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], D + f->off[l], gD + f->off[l]);
+  k_nodes_to_leaves<T><<<blocks(f->nl), TPB, 0, st>>>(f->nl, f->n, f->node, gD, gU_from);
+}
+
+mwdg_status check_pair(mwdg_adj *f, mwdg_adj *t) {
+  if (!f || !t) return MWDG_ERR_ARG;
+  if (!f->levels || !t->levels) return fail(f, MWDG_ERR_ARG, "regridding needs two frozen-grid contexts");
+  if (f->levels != t->levels || f->gM != t->gM || f->gN != t->gN) return fail(f, MWDG_ERR_DIMS, "grids differ in roots or levels");
+  if (f->p.precision != t->p.precision) return fail(f, MWDG_ERR_ARG, "contexts differ in precision");
+  return MWDG_OK;
+}
+
 mwdg_status check_params(const mwdg_adj_params *p) {
   if (p->nx < 1 || p->ny < 1 || (long long)p->nx * p->ny > (1LL << 28) || !(p->dx > 0.0) || p->max_steps < 1)
     return MWDG_ERR_DIMS;
@@ -2329,6 +2543,33 @@ mwdg_status mwdg_adj_project_transpose(mwdg_adj *a, const void *gp, void *gv, vo
     k_project_t<double><<<nb, TPB, 0, (cudaStream_t)stream>>>(make_par<double>(a, 0, nullptr, nullptr),
                                                                 static_cast<const double *>(gp), ptr<double>(gv));
   return cuda_check(a, "mwdg_adj_project_transpose");
+}
+
+mwdg_status mwdg_adj_regrid(mwdg_adj *from, mwdg_adj *to, const void *U_from, void *U_to, void *stream) {
+  const mwdg_status s = check_pair(from, to);
+  if (s != MWDG_OK) return s;
+  if (!U_from || !U_to) return fail(from, MWDG_ERR_ARG, "NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (from->p.precision == MWDG_F32)
+    launch_regrid<float>(from, to, static_cast<const float *>(U_from), ptr<float>(U_to), st);
+  else
+    launch_regrid<double>(from, to, static_cast<const double *>(U_from), ptr<double>(U_to), st);
+  return cuda_check(from, "mwdg_adj_regrid");
+}
+
+mwdg_status mwdg_adj_regrid_transpose(mwdg_adj *from, mwdg_adj *to, const void *U_from, const void *gU_to,
+                                      void *gU_from, void *stream) {
+  const mwdg_status s = check_pair(from, to);
+  if (s != MWDG_OK) return s;
+  if (!U_from || !gU_to || !gU_from) return fail(from, MWDG_ERR_ARG, "NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (from->p.precision == MWDG_F32)
+    launch_regrid_t<float>(from, to, static_cast<const float *>(U_from), static_cast<const float *>(gU_to),
+                           ptr<float>(gU_from), st);
+  else
+    launch_regrid_t<double>(from, to, static_cast<const double *>(U_from), static_cast<const double *>(gU_to),
+                            ptr<double>(gU_from), st);
+  return cuda_check(from, "mwdg_adj_regrid_transpose");
 }
 
 mwdg_status mwdg_adj_forward(mwdg_adj *a, const void *U0, const void *z, const void *nman, int32_t nknots,

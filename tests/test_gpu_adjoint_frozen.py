@@ -13,7 +13,11 @@ held fixed over a segment (Sect. 2.3), against the FP64 oracles.
   * a frozen grid whose leaves are all on the finest level gives the uniform
     context's run and gradients bit for bit;
   * two segments chained by autograd give the one-segment gradients;
-  * FP32 tracks the FP64 oracle (steps, depths, gradient correlation).
+  * FP32 tracks the FP64 oracle (steps, depths, gradient correlation);
+  * re-freezing at a checkpoint (mwdg_adj_regrid, the MWDG2 adaptation's
+    state transfer to the grid the C oracle chose) reproduces the C oracle
+    bit for bit, also where refined depth planes need scaling, and its
+    transpose and the chain's gradients equal the oracle's to 1e-9.
 """
 from dataclasses import replace
 
@@ -268,3 +272,96 @@ def test_fp32_tracks_the_fp64_oracle():
         g, w = got.ravel().astype(np.float64), want.ravel()
         assert np.corrcoef(g, w)[0, 1] >= 0.999
         assert np.quantile(np.abs(g - w), 0.99) <= 0.02 * np.abs(w).max()
+
+
+def _segment(coef, zc, nm, Q, dts, t0, G):
+    import torch
+    U = AS.dense_from_leaves(coef, G)
+    t = t0
+    for dt in dts:
+        U = AS.step(U, zc, nm, Q, float(dt), t, G)
+        t = t + float(dt)
+    return AS.leaves_of(U, G)
+
+
+def test_refrozen_segments_match_the_oracles():
+    """Two frozen MWDG2 segments with the grid re-frozen between them
+    (mwdg_adj_regrid: the adaptation's state transfer to the grid the C
+    oracle chose): the run is the C oracle's bit for bit, and the gradients
+    of the chain (dg2_run, regrid, dg2_run through autograd) equal the
+    non-uniform oracle's to 1e-9."""
+    import torch
+    from paper_2107_02750_gb300.adjoint import dg2_run, regrid
+    p = adaptive_reach(32, 3, 5e-2)
+    s, dt_cfl = start(p)
+    dt = 0.8 * dt_cfl
+    l1, i1, j1, c0 = s.leaves()
+    K1, K2 = 4, 4
+    for _ in range(K1):
+        s.step_frozen(dt)
+    s.adapt()
+    l2, i2, j2, cm = s.leaves()
+    for _ in range(K2):
+        s.step_frozen(dt)
+    cK = s.leaves()[3]
+    G1, G2 = grid_of(p, l1, i1, j1), grid_of(p, l2, i2, j2)
+    assert sum(int((G1.leaf[l] != G2.leaf[l]).sum()) for l in range(p.L + 1)) > 0
+    a1, a2 = context(p, l1, i1, j1, K1), context(p, l2, i2, j2, K2)
+    U0, z, n, kt, kQ = device_inputs(a1, s, p, c0)
+    d1 = torch.full((K1,), dt, dtype=torch.float64, device=a1.device)
+    d2 = torch.full((K2,), dt, dtype=torch.float64, device=a1.device)
+    W = np.random.default_rng(23).standard_normal((len(l2), 9))
+    u, zz, nn, Q = (x.clone().requires_grad_(True) for x in (U0, z, n, kQ))
+    x, _, t = dg2_run(a1, u, zz, nn, Q, kt, 0.0, K1, d1)
+    xm = regrid(a1, a2, x)
+    assert np.array_equal(xm.detach().cpu().numpy().T, cm)
+    y, _, _ = dg2_run(a2, xm, zz, nn, Q, kt, t, K2, d2)
+    assert np.array_equal(y.detach().cpu().numpy().T, cK)
+    (y * torch.tensor(np.ascontiguousarray(W.T), device=a1.device)).sum().backward()
+
+    def leaf(a):
+        return torch.tensor(np.array(a, dtype=np.float64), requires_grad=True)
+    coef, zp, nf, QQ = leaf(c0), leaf(s.z_level(p.L)[0].reshape(3, p.ny, p.nx)), leaf(p.n_cell()), leaf(p.inflow_Q)
+    zc = AS.pyramid([zp[0], zp[1], zp[2]], p.L)
+    nm = AS.manning_levels(nf, p.L)
+    mid = _segment(coef, zc, nm, QQ, [dt] * K1, 0.0, G1)
+    out = _segment(AS.regrid(mid, G1, G2), zc, nm, QQ, [dt] * K2, K1 * dt, G2)
+    (out * torch.as_tensor(W)).sum().backward()
+    _close(u.grad.cpu().numpy().T, coef.grad.numpy(), "U0")
+    _close(zz.grad.cpu().numpy(), zp.grad.numpy(), "z")
+    _close(nn.grad.cpu().numpy(), nf.grad.numpy(), "n")
+    _close(Q.grad.cpu().numpy(), QQ.grad.numpy(), "Q")
+
+
+def test_regrid_with_refined_depth_planes_matches_the_oracles():
+    """The transfer where the new grid refines coarse, partly wet leaves whose
+    depth planes need scaling (a dam break over a steep dry slope): the C
+    oracle's adaptation bit for bit, and the transpose equal to the
+    oracle's reverse-mode derivative to 1e-9."""
+    import torch
+    from paper_2107_02750_gb300.adjoint import regrid_forward, regrid_transpose
+    from test_oracle_adjoint_nonuniform import steep_slope_adaptive, _refined_below_negative
+    p = steep_slope_adaptive()
+    s = oracle_sim(p)
+    for _ in range(2):
+        dt = s.step()
+        for _ in range(3):
+            s.step_frozen(dt)
+        s.adapt()
+    s.step()
+    for _ in range(3):
+        s.step_frozen(dt)
+    l1, i1, j1, cb = s.leaves()
+    s.adapt()
+    l2, i2, j2, ca = s.leaves()
+    G1, G2 = grid_of(p, l1, i1, j1), grid_of(p, l2, i2, j2)
+    assert _refined_below_negative(cb, G1, G2) > 0
+    a1, a2 = context(p, l1, i1, j1, 1), context(p, l2, i2, j2, 1)
+    U = torch.tensor(np.ascontiguousarray(cb.T), device=a1.device)
+    V = regrid_forward(a1, a2, U)
+    assert np.array_equal(V.cpu().numpy().T, ca)
+    W = np.random.default_rng(29).standard_normal((len(l2), 9))
+    g = regrid_transpose(a1, a2, U, torch.tensor(np.ascontiguousarray(W.T), device=a1.device))
+    coef = torch.tensor(cb, requires_grad=True)
+    (AS.regrid(coef, G1, G2) * torch.as_tensor(W)).sum().backward()
+    _close(g.cpu().numpy().T, coef.grad.numpy(), "U")
