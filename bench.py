@@ -756,6 +756,7 @@ def run_adjoint(args):
 
     r32 = measure(M.F32, prof=True)
     r64 = None if args.no_fp64 else measure(M.F64)
+    frozen = run_adjoint_frozen(args, min(K, 100))
     roof = adjoint_roofline(r32.pop("kernel_ms"), cells, 4)
     cb = None if args.no_cpu else adjoint_cpu_baseline(args.n)
     line = {"metric": "DG2 adjoint cell-steps/s (forward + reverse sweep of one checkpoint segment)",
@@ -768,10 +769,75 @@ def run_adjoint(args):
                        "tape": "each step's state, stage inputs and flux views (51 coefficients per cell)"},
             "forward_ms": r32["forward_ms"], "backward_ms": r32["backward_ms"], "simulated_s": r32["simulated_s"],
             "max_abs_grad": r32["max_abs_grad"], "gpu_launches": 18 * K + 1, "clocks": r32["clocks"],
-            "roofline": roof, "fp64": r64, "cpu_baseline": cb}
+            "roofline": roof, "fp64": r64, "cpu_baseline": cb, "frozen_mwdg2": frozen}
     if r64 is not None:
         r64.pop("kernel_ms", None)
     return line
+
+
+def run_adjoint_frozen(args, K):
+    """The adjoint on the benchmark workload's own MWDG2 grid, frozen: the
+    1024 x 1024 valley's active leaves and state after 1800 s of the FP32
+    solver, one checkpoint segment of K steps from there (CFL steps over the
+    leaves), the squared depth misfit at 16 seeded wet leaves, forward and
+    backward sweeps timed with CUDA events, FP32 and FP64.  One unit = one
+    active leaf carried through one step forward and back."""
+    import torch
+    import paper_2107_02750_gb300 as M
+    from paper_2107_02750_gb300 import synth as S
+    from paper_2107_02750_gb300.adjoint import Dg2Adjoint, dg2_run
+    p = S.valley(n=args.n, L=args.n.bit_length() - 1)
+    sol = make_solver(p, M.F32, torch.cuda.current_stream().cuda_stream)
+    sol.run_to_time(1800.0)
+    t0 = sol.get_time()[0]
+    lev, ii, jj, co = sol.read_active()
+    del sol
+    nl = len(lev)
+    nodes = sum((p.M << l) * (p.N << l) for l in range(p.L + 1))
+    pick = np.random.default_rng(3).choice(np.flatnonzero(co[:, 0] > 0.5), size=16, replace=False)
+    res = {"workload": f"{p.nx}x{p.ny} valley (seed 1), MWDG2 eps={p.eps} grid and state of the FP32 solver at "
+                       f"t={t0:.0f} s, frozen; segment {K} CFL steps; squared depth misfit at 16 wet leaves",
+           "leaves": nl, "level_nodes": nodes, "unit": "leaf-steps/s"}
+    for name, prec in (("f32", M.F32), ("f64", M.F64)):
+        if prec == M.F64 and args.no_fp64:
+            continue
+        adj = Dg2Adjoint.frozen(p.M, p.N, p.L, p.dx, M.ADAPTIVE, lev, ii, jj, cfl=p.cfl, dt_max=p.dt_max,
+                                limiter=p.limiter, bc=tuple(p.bc), inflow_edge=p.inflow_edge,
+                                inflow_c0=p.inflow_c0, inflow_c1=p.inflow_c1, rain_rate=p.rain_rate,
+                                rain_t_end=p.rain_t_end, max_steps=K, precision=prec, tape_views=True)
+        dev = adj.device
+        U0 = torch.tensor(np.ascontiguousarray(co.T), dtype=adj.dtype, device=dev)
+        z = adj.project(p.z_vert)
+        n = torch.tensor(p.n_cell(), dtype=adj.dtype, device=dev)
+        kt = torch.tensor(p.inflow_t, dtype=torch.float64, device=dev)
+        kQ = torch.tensor(p.inflow_Q, dtype=torch.float64, device=dev)
+        gidx = torch.tensor(pick, device=dev)
+        h_obs = U0[0, gidx] + 0.05
+
+        def segment(steps):
+            leaves = [x.clone().requires_grad_(True) for x in (U0, z, n, kQ)]
+            UK, d, t = dg2_run(adj, leaves[0], leaves[1], leaves[2], leaves[3], kt, t0, steps)
+            return leaves, ((UK[0, gidx] - h_obs) ** 2).sum(), t
+
+        for _ in range(max(3, args.warmup)):
+            _, J, _ = segment(min(K, 10))
+            J.backward()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with Clocks(dev.index) as clk:
+            ev[0].record()
+            leaves, J, t_seg = segment(K)
+            ev[1].record()
+            J.backward()
+            ev[2].record()
+            torch.cuda.synchronize()
+        ms_f, ms_b = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        res[name] = {"value": nl * K / ((ms_f + ms_b) * 1e-3), "ms_per_step": (ms_f + ms_b) / K,
+                     "forward_ms": ms_f, "backward_ms": ms_b, "simulated_s": t_seg - t0,
+                     "max_abs_grad": {k: float(x.grad.abs().max()) for k, x in zip(("U0", "z", "n", "Q"), leaves)},
+                     "clocks": clk.summary()}
+        del adj
+    return res
 
 
 # algorithmic coefficients moved per cell by one launch of each adjoint kernel

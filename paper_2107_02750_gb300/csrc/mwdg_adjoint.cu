@@ -422,7 +422,8 @@ template <typename T>
 __global__ void __launch_bounds__(TPB) k_limit(Par<T> P, const T *X, const T *Z, T *Wst, T *Wfx, T *Zfx) {
   long long k;
   int i, j;
-  if (!cell_of(P, k, i, j)) return;
+  // a frozen grid's non-leaf node gets its view from the view kernels
+  if (!cell_of(P, k, i, j) || !is_leaf(P, k)) return;
   const long long n = P.ns;
   T ws[9], wf[9], ze[3];
   LimRec r;
@@ -577,6 +578,10 @@ __global__ void __launch_bounds__(UT * UT) k_update(Par<T> P, int stage, const T
     const bool hasLo = xf ? gi > 0 : gj > 0;
     const bool hasHi = xf ? gi < P.nx : gj < P.ny;
     const int along = xf ? gj : gi;
+    if (P.kind) {  // a frozen grid's face that no leaf reads
+      const long long kH = (long long)gj * P.nx + gi, kL = xf ? kH - 1 : kH - P.nx;
+      if (!(hasLo && P.kind[kL] == K_LEAF) && !(hasHi && P.kind[kH] == K_LEAF)) continue;
+    }
     Lim<T> lo, hi;
     T aLo[3], aHi[3];  // the sides' averages for the outflow limit
     if (hasLo) lo = node_lim(P, Wfx, Zfx, xf ? gi - 1 : gi, xf ? gj : gj - 1, xf ? 0 : 2, aLo);
@@ -1058,6 +1063,13 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
   const long long kLo = XF ? (long long)j * P.nx + (i - 1) : (long long)(j - 1) * P.nx + i;
   const long long kHi = (long long)j * P.nx + i;
   const int along = XF ? j : i;
+  if (P.kind && !(hasLo && P.kind[kLo] == K_LEAF) && !(hasHi && P.kind[kHi] == K_LEAF)) {
+    // a frozen grid's face between non-leaf nodes: no operator reads it
+#pragma unroll
+    for (int q = 0; q < 14; q++) lim[q * nf + fi] = T(0);
+    if ((!hasLo && P.inflow_edge == eLo) || (!hasHi && P.inflow_edge == eHi)) lq[along] = 0.0;
+    return;
+  }
   Lim<T> lo, hi;
   T aLo[3], aHi[3];
   if (hasLo) lo = node_lim(P, Wfx, Zfx, XF ? i - 1 : i, XF ? j : j - 1, fLo, aLo);
