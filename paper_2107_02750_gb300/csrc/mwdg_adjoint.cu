@@ -60,13 +60,18 @@ template <> __device__ __forceinline__ float tie_rel<float>() { return 1e-5f; }
 
 // parameters passed to the kernels by value.  On a frozen non-uniform grid
 // every level is a dense array of nx x ny nodes (nx = M 2^l) in one
-// coefficient array per component, levels one after another; a launch works
-// on one level, with its pointers offset to the level's first node.
+// coefficient array per component, levels one after another.  A kernel
+// working on one level takes its pointers offset to the level's first node;
+// one working on all levels (a Levels table) offsets them itself by off.
 template <typename T>
 struct Par {
   int nx, ny;
   long long n;          // nodes of this level (cells of a uniform grid)
   long long ns;         // stride between components (n on a uniform grid)
+  long long off;        // the level's first node in the level arrays (0: uniform)
+  long long fx, fy;     // its first x face and y face among all levels' faces
+  long long fxp, fyp;   // the previous level's (its parents')
+  long long lqo;        // its first boundary entry
   int sh;               // levels from this one down to the finest (0: uniform)
   int stat;             // 1: static graded grid (two-children mean, Sect. 2.2.1)
   const uint8_t *kind;  // per node of the level: K_BELOW, K_LEAF, K_SIG; NULL: all leaves
@@ -325,6 +330,43 @@ __device__ __forceinline__ bool cell_of(const Par<T> &P, long long &k, int &i, i
   return true;
 }
 
+// One launch over every level of a frozen grid (one level on a uniform grid):
+// the levels' parameters and, per level, its first block; each block works
+// on one level.
+constexpr int MAXLV = MWDG_LMAX + 1;
+template <typename T>
+struct Levels {
+  int n;
+  unsigned bstart[MAXLV + 1];
+  Par<T> P[MAXLV];
+};
+
+// the level of this block (its parameters copied to shared memory) and the
+// block's index within the level; ML = false: one level (a uniform grid),
+// read in place
+template <bool ML, typename T>
+__device__ __forceinline__ const Par<T> &block_level(const Levels<T> &LV, Par<T> &sP, unsigned &b) {
+  if (!ML) {
+    b = blockIdx.x;
+    return LV.P[0];
+  }
+  int l = 0;
+  while (l + 1 < LV.n && blockIdx.x >= LV.bstart[l + 1]) l++;
+  b = blockIdx.x - LV.bstart[l];
+  if (threadIdx.x == 0) sP = LV.P[l];
+  __syncthreads();
+  return sP;
+}
+
+template <typename T>
+__device__ __forceinline__ bool node_of(const Par<T> &P, unsigned b, long long &k, int &i, int &j) {
+  k = (long long)b * TPB + threadIdx.x;
+  if (k >= P.n) return false;
+  j = (int)(k / P.nx);
+  i = (int)(k - (long long)j * P.nx);
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // forward sweep
 // ---------------------------------------------------------------------------
@@ -336,14 +378,18 @@ __global__ void k_times(const double *dts, int steps, double *tt) {
 
 // CFL candidate of every cell (Sect. 2.1.1), with the inflow ghost at the
 // critical depth; the smallest goes to *best as the bits of a positive double
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_cfl(Par<T> P, const T *U, const double *tt, int step,
+template <typename T, bool ML>
+__global__ void __launch_bounds__(TPB) k_cfl(const Levels<T> LV, const T *U, const double *tt, int step,
                                              unsigned long long *best) {
   __shared__ T sh[TPB];
+  __shared__ Par<T> sP;
+  unsigned bl;
+  const Par<T> &P = block_level<ML>(LV, sP, bl);
+  U += P.off;
   long long k;
   int i, j;
   T c = tinf<T>();
-  if (cell_of(P, k, i, j) && is_leaf(P, k)) {
+  if (node_of(P, bl, k, i, j) && is_leaf(P, k)) {
     const long long n = P.ns;
     const T h0 = U[k], dx = P.dx, g = P.g;
     if (h0 > P.hd) {
@@ -382,12 +428,18 @@ __global__ void k_dt(double cfl, double dt_max, unsigned long long *best, double
 }
 
 // rain depth of the step, then split implicit Manning friction
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_friction(Par<T> P, const T *U, const T *nman, const double *dts,
-                                                  const double *tt, int step, T *Un) {
+template <typename T, bool ML>
+__global__ void __launch_bounds__(TPB) k_friction(const Levels<T> LV, const T *U, const T *nman,
+                                                  const double *dts, const double *tt, int step, T *Un) {
+  __shared__ Par<T> sP;
+  unsigned bl;
+  const Par<T> &P = block_level<ML>(LV, sP, bl);
+  U += P.off;
+  nman += P.off;
+  Un += P.off;
   long long k;
   int i, j;
-  if (!cell_of(P, k, i, j)) return;
+  if (!node_of(P, bl, k, i, j)) return;
   const long long n = P.ns;
   const T dt = (T)dts[step], g = P.g;
   const double t = tt[step];
@@ -418,12 +470,21 @@ __global__ void __launch_bounds__(TPB) k_friction(Par<T> P, const T *U, const T 
   for (int m = 0; m < 9; m++) Un[m * n + k] = w[m];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_limit(Par<T> P, const T *X, const T *Z, T *Wst, T *Wfx, T *Zfx) {
+template <typename T, bool ML>
+__global__ void __launch_bounds__(TPB) k_limit(const Levels<T> LV, const T *X, const T *Z, T *Wst, T *Wfx,
+                                               T *Zfx) {
+  __shared__ Par<T> sP;
+  unsigned bl;
+  const Par<T> &P = block_level<ML>(LV, sP, bl);
+  X += P.off;
+  Z += P.off;
+  Wst += P.off;
+  Wfx += P.off;
+  Zfx += P.off;
   long long k;
   int i, j;
   // a frozen grid's non-leaf node gets its view from the view kernels
-  if (!cell_of(P, k, i, j) || !is_leaf(P, k)) return;
+  if (!node_of(P, bl, k, i, j) || !is_leaf(P, k)) return;
   const long long n = P.ns;
   T ws[9], wf[9], ze[3];
   LimRec r;
@@ -559,13 +620,23 @@ __global__ void __launch_bounds__(TPB) k_view_prolong(Par<T> P, T *V, T *Vz) {
 constexpr int UT = 16;
 constexpr int UFX = (UT + 1) * UT, UFY = UT * (UT + 1);
 
-template <typename T>
-__global__ void __launch_bounds__(UT * UT) k_update(Par<T> P, int stage, const T *Wfx, const T *Zfx, const T *Wst,
-                                                    const T *W1, const double *dts, const double *tt, int step,
-                                                    T *Out, uint8_t *clip) {
+template <typename T, bool ML>
+__global__ void __launch_bounds__(UT * UT) k_update(const Levels<T> LV, int stage, const T *Wfx, const T *Zfx,
+                                                    const T *Wst, const T *W1, const double *dts, const double *tt,
+                                                    int step, T *Out, uint8_t *clip) {
   __shared__ T sF[UFX + UFY][3];
   __shared__ T sR[UFX + UFY][8];  // low side (hs, u, v, zr), high side (hs, u, v, zr)
-  const int i0 = blockIdx.x * UT, j0 = blockIdx.y * UT;
+  __shared__ Par<T> sP;
+  unsigned bl;
+  const Par<T> &P = block_level<ML>(LV, sP, bl);
+  Wfx += P.off;
+  Zfx += P.off;
+  Wst += P.off;
+  if (W1) W1 += P.off;
+  Out += P.off;
+  clip += P.off;
+  const int tx = (P.nx + UT - 1) / UT;
+  const int i0 = (int)(bl % tx) * UT, j0 = (int)(bl / tx) * UT;
   const long long n = P.ns;
   const double t = stage == 1 ? tt[step] : tt[step] + dts[step];
   for (int q = threadIdx.x; q < UFX + UFY; q += UT * UT) {
@@ -1045,12 +1116,22 @@ __device__ void drain_rev(const T F[3], T h0, T qn, T qt, T g, T hd, T dx, T dt,
 // flux-view averages (h0, qx0, qy0) of the low (slots 8-10) and high (slots
 // 11-13) cell through the outflow limit (non-zero for its donor only); `lq`,
 // per boundary cell of the inflow edge, the cotangent of Q(t).
-template <typename T, bool XF>
-__global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const double *dts, const double *tt, int step,
-                                                  const T *Wfx, const T *Zfx, const T *lY, const T *Y,
+template <typename T, bool XF, bool ML>
+__global__ void __launch_bounds__(TPB) k_rev_face(const Levels<T> LV, int stage, const double *dts, const double *tt,
+                                                  int step, const T *Wfx, const T *Zfx, const T *lY, const T *Y,
                                                   const uint8_t *clip, T *lim, double *lq) {
+  __shared__ Par<T> sP;
+  unsigned bl;
+  const Par<T> &P = block_level<ML>(LV, sP, bl);
+  Wfx += P.off;
+  Zfx += P.off;
+  lY += P.off;
+  Y += P.off;
+  clip += P.off;
+  lim += 14 * (XF ? P.fx : P.fy);
+  lq += P.lqo;
   const long long nf = XF ? (long long)P.ny * (P.nx + 1) : (long long)(P.ny + 1) * P.nx;
-  const long long fi = (long long)blockIdx.x * TPB + threadIdx.x;
+  const long long fi = (long long)bl * TPB + threadIdx.x;
   if (fi >= nf) return;
   const double t = stage == 1 ? tt[step] : tt[step] + dts[step];
   int i, j;  // the high-side cell (i, j); the low side is (i-1, j) or (i, j-1)
@@ -1170,31 +1251,38 @@ __global__ void __launch_bounds__(TPB) k_rev_face(Par<T> P, int stage, const dou
 // hydrograph knots: the cotangent of Q(t) summed over the inflow edge in a
 // fixed order, spread over the two knots around t
 template <typename T>
-__global__ void k_rev_knots(Par<T> P, int stage, const double *dts, const double *tt, int step, const double *lq,
-                            double *gQ) {
+__global__ void k_rev_knots(const Levels<T> LV, int stage, const double *dts, const double *tt, int step,
+                            const double *lq, double *gQ) {
   __shared__ double sh[TPB];
-  const int nedge = (P.inflow_edge < 2) ? P.ny : P.nx;
-  double acc = 0.0;
-  for (int a = threadIdx.x; a < nedge; a += TPB)
-    if (inflow_overlap(P, P.inflow_edge, a) > 0) acc += lq[a];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int s = TPB / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+  __shared__ Par<T> sP;
+  for (int l = 0; l < LV.n; l++) {  // levels in order, each its own sum
+    if (threadIdx.x == 0) sP = LV.P[l];
     __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double t = stage == 1 ? tt[step] : tt[step] + dts[step];
-    int k0, k1;
-    double r;
-    hydro(P, t, k0, k1, r);
-    const double l = sh[0];
-    if (k0 == k1) {
-      gQ[k0] += l;
-    } else {
-      gQ[k0] += l - l * r;
-      gQ[k1] += l * r;
+    const Par<T> &P = sP;
+    const int nedge = (P.inflow_edge < 2) ? P.ny : P.nx;
+    double acc = 0.0;
+    for (int a = threadIdx.x; a < nedge; a += TPB)
+      if (inflow_overlap(P, P.inflow_edge, a) > 0) acc += lq[P.lqo + a];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = TPB / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+      __syncthreads();
     }
+    if (threadIdx.x == 0) {
+      const double t = stage == 1 ? tt[step] : tt[step] + dts[step];
+      int k0, k1;
+      double r;
+      hydro(P, t, k0, k1, r);
+      const double v = sh[0];
+      if (k0 == k1) {
+        gQ[k0] += v;
+      } else {
+        gQ[k0] += v - v * r;
+        gQ[k1] += v * r;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -1239,13 +1327,30 @@ __device__ __forceinline__ void face_plane_cot(const Par<T> &P, int i, int j, co
 // gathered in gV (12 planes: a frozen grid, where views pass them between
 // levels), else from the cell's four faces.
 template <typename T, bool GV>
-__global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, int stage, const double *dts, int step, const T *X,
-                                                   const T *Z, const T *lY, const T *Y, const uint8_t *clip, T *lW1,
-                                                   const T *limx, const T *limy, const T *gV, T *lXo, T *lnb,
-                                                   T *gz) {
+__global__ void __launch_bounds__(TPB) k_rev_limit(const Levels<T> LV, int stage, const double *dts, int step,
+                                                   const T *X, const T *Z, const T *lY, const T *Y,
+                                                   const uint8_t *clip, T *lW1, const T *limx, const T *limy,
+                                                   const T *gV, T *lXo, T *lnb, T *gz) {
+  __shared__ Par<T> sP;
+  unsigned bl;
+  const Par<T> &P = block_level<GV>(LV, sP, bl);
+  X += P.off;
+  Z += P.off;
+  lY += P.off;
+  Y += P.off;
+  clip += P.off;
+  lW1 += P.off;
+  if (GV) gV += P.off;
+  else {
+    limx += 14 * P.fx;
+    limy += 14 * P.fy;
+  }
+  lXo += P.off;
+  lnb += P.off;
+  gz += P.off;
   long long k;
   int i, j;
-  if (!cell_of(P, k, i, j)) return;
+  if (!node_of(P, bl, k, i, j)) return;
   const long long n = P.ns;
   if (!is_leaf(P, k)) {  // no cotangent reaches a frozen grid's non-leaf node
 #pragma unroll
@@ -1344,11 +1449,18 @@ __global__ void __launch_bounds__(TPB) k_rev_limit(Par<T> P, int stage, const do
 // (a cell's side-A neighbour in x is (i+1, j): the share it holds for this
 // cell sits with (i-1, j) under side A, and so on); the average of eta in
 // the limiter is h0 + z0, so the bed average takes the eta shares too
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_rev_gather(Par<T> P, const T *lXo, const T *lnb, T *lX, T *gz) {
+template <typename T, bool ML>
+__global__ void __launch_bounds__(TPB) k_rev_gather(const Levels<T> LV, const T *lXo, const T *lnb, T *lX, T *gz) {
+  __shared__ Par<T> sP;
+  unsigned bl;
+  const Par<T> &P = block_level<ML>(LV, sP, bl);
+  lXo += P.off;
+  lnb += P.off;
+  lX += P.off;
+  gz += P.off;
   long long k;
   int i, j;
-  if (!cell_of(P, k, i, j)) return;
+  if (!node_of(P, bl, k, i, j)) return;
   const long long n = P.ns;
   if (!is_leaf(P, k)) {
 #pragma unroll
@@ -1374,12 +1486,21 @@ __global__ void __launch_bounds__(TPB) k_rev_gather(Par<T> P, const T *lXo, cons
 
 // friction (and rain) in reverse: lU = cotangent of the step's input state,
 // Manning n's share added to gn
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_rev_friction(Par<T> P, const T *U, const T *nman, const double *dts,
-                                                      const double *tt, int step, const T *lUn, T *lU, T *gn) {
+template <typename T, bool ML>
+__global__ void __launch_bounds__(TPB) k_rev_friction(const Levels<T> LV, const T *U, const T *nman,
+                                                      const double *dts, const double *tt, int step, const T *lUn,
+                                                      T *lU, T *gn) {
+  __shared__ Par<T> sP;
+  unsigned bl;
+  const Par<T> &P = block_level<ML>(LV, sP, bl);
+  U += P.off;
+  nman += P.off;
+  lUn += P.off;
+  lU += P.off;
+  gn += P.off;
   long long k;
   int i, j;
-  if (!cell_of(P, k, i, j)) return;
+  if (!node_of(P, bl, k, i, j)) return;
   const long long n = P.ns;
   if (!is_leaf(P, k)) {
 #pragma unroll
@@ -1449,11 +1570,18 @@ __global__ void __launch_bounds__(TPB) k_rev_friction(Par<T> P, const T *U, cons
 // each of its parent's faces that it touches (the parent level's slots px,
 // py).
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_rev_view_gather(Par<T> P, const T *limx, const T *limy, const T *px,
-                                                         const T *py, T *gV) {
+__global__ void __launch_bounds__(TPB) k_rev_view_gather(const Levels<T> LV, const T *limx, const T *limy,
+                                                         T *gV) {
+  __shared__ Par<T> sP;
+  unsigned bl;
+  const Par<T> &P = block_level<true>(LV, sP, bl);
+  const T *px = limx + 14 * P.fxp, *py = limy + 14 * P.fyp;  // the parent level's faces
+  limx += 14 * P.fx;
+  limy += 14 * P.fy;
+  gV += P.off;
   long long k;
   int i, j;
-  if (!cell_of(P, k, i, j)) return;
+  if (!node_of(P, bl, k, i, j)) return;
   const long long n = P.ns;
   T lw[9], lz[3];
   if (P.stat && P.kind[k] == K_SIG) {
@@ -1913,6 +2041,7 @@ Par<T> make_par(const mwdg_adj *a, int nknots, const double *kt, const double *k
   P.ny = p.ny;
   P.n = (long long)p.nx * p.ny;
   P.ns = P.n;
+  P.off = P.fx = P.fy = P.fxp = P.fyp = P.lqo = 0;
   P.sh = 0;
   P.stat = 0;
   P.kind = nullptr;
@@ -1956,7 +2085,29 @@ Par<T> level_par(const mwdg_adj *a, int l, int nknots, const double *kt, const d
   P.dp = l > 0 ? a->off[l] - a->off[l - 1] : 0;
   P.dxd = a->p.dx * (double)(1LL << (L - l));
   P.dx = (T)P.dxd;
+  P.off = a->off[l];
+  P.fx = a->fxo[l];
+  P.fy = a->fyo[l];
+  P.fxp = l > 0 ? a->fxo[l - 1] : 0;
+  P.fyp = l > 0 ? a->fyo[l - 1] : 0;
+  P.lqo = a->lqo[l];
   return P;
+}
+
+// launch tables over all levels: per level its first block
+template <typename T, class F>
+Levels<T> make_levels(const std::vector<Par<T>> &PL, F &&blocks_of, unsigned &total) {
+  Levels<T> LV{};
+  LV.n = (int)PL.size();
+  unsigned b = 0;
+  for (int l = 0; l < LV.n; l++) {
+    LV.bstart[l] = b;
+    LV.P[l] = PL[l];
+    b += (unsigned)blocks_of(PL[l]);
+  }
+  LV.bstart[LV.n] = b;
+  total = b;
+  return LV;
 }
 
 template <typename T> T *ptr(void *p) { return static_cast<T *>(p); }
@@ -1989,57 +2140,60 @@ void launch_views(const mwdg_adj *a, const Par<T> *PL, T *F, T *Zf, cudaStream_t
     k_view_prolong<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], F + loff(a, l), Zf + loff(a, l));
 }
 
+// the launch tables of one call: cells, update tiles, x and y faces of
+// every level
 template <typename T>
-void launch_update(const mwdg_adj *a, const Par<T> *PL, int stage, const T *F, const T *Zf, const T *Wst,
+struct Tabs {
+  std::vector<Par<T>> PL;
+  Levels<T> cells, tiles, fxs, fys;
+  unsigned nc = 0, nt = 0, nfx = 0, nfy = 0;
+};
+
+template <typename T>
+void launch_update(const mwdg_adj *a, const Tabs<T> &TB, int stage, const T *F, const T *Zf, const T *Wst,
                    const T *W1, const double *dts, int s, T *Out, uint8_t *clip, cudaStream_t st) {
-  for (int l = 0; l < nlev(a); l++) {
-    const long long o = loff(a, l);
-    const dim3 tiles((PL[l].nx + UT - 1) / UT, (PL[l].ny + UT - 1) / UT);
-    k_update<T><<<tiles, UT * UT, 0, st>>>(PL[l], stage, F + o, Zf + o, Wst + o, W1 ? W1 + o : nullptr, dts, a->tt,
-                                           s, Out + o, clip + o);
-  }
+  if (a->levels)
+    k_update<T, true><<<TB.nt, UT * UT, 0, st>>>(TB.tiles, stage, F, Zf, Wst, W1, dts, a->tt, s, Out, clip);
+  else
+    k_update<T, false><<<TB.nt, UT * UT, 0, st>>>(TB.tiles, stage, F, Zf, Wst, W1, dts, a->tt, s, Out, clip);
 }
 
 template <typename T>
-void launch_limit(const mwdg_adj *a, const Par<T> *PL, const T *X, const T *z, T *Wst, T *F, T *Zf,
+void launch_limit(const mwdg_adj *a, const Tabs<T> &TB, const T *X, const T *z, T *Wst, T *F, T *Zf,
                   cudaStream_t st) {
-  for (int l = 0; l < nlev(a); l++) {
-    const long long o = loff(a, l);
-    k_limit<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], X + o, z + o, Wst + o, F + o, Zf + o);
-  }
-  launch_views<T>(a, PL, F, Zf, st);
+  if (a->levels) k_limit<T, true><<<TB.nc, TPB, 0, st>>>(TB.cells, X, z, Wst, F, Zf);
+  else k_limit<T, false><<<TB.nc, TPB, 0, st>>>(TB.cells, X, z, Wst, F, Zf);
+  launch_views<T>(a, TB.PL.data(), F, Zf, st);
 }
 
 // friction, limit, stage 1 and limit of step s: the two stage inputs (Un, Ui)
 // and their stored and flux views (on a frozen grid the views of every level)
 template <typename T>
-void recompute_stages(mwdg_adj *a, const Par<T> *PL, const T *U, const T *z, const T *nman, int s,
+void recompute_stages(mwdg_adj *a, const Tabs<T> &TB, const T *U, const T *z, const T *nman, int s,
                       const double *dts, uint8_t *clip, cudaStream_t st) {
   const StageArrays<T> v = stage_arrays<T>(a, s);
   T *Un = v.Un, *Ui = v.Ui, *W1 = ptr<T>(a->W1), *F1 = v.F1, *Z1 = v.Z1;
   T *W2 = ptr<T>(a->W2), *F2 = v.F2, *Z2 = v.Z2;
   {
     Timed tm(a, MWDG_ADJ_KC_FRICTION, st);
-    for (int l = 0; l < nlev(a); l++) {
-      const long long o = loff(a, l);
-      k_friction<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], U + o, nman + o, dts, a->tt, s, Un + o);
-    }
+    if (a->levels) k_friction<T, true><<<TB.nc, TPB, 0, st>>>(TB.cells, U, nman, dts, a->tt, s, Un);
+    else k_friction<T, false><<<TB.nc, TPB, 0, st>>>(TB.cells, U, nman, dts, a->tt, s, Un);
   }
   {
     Timed tm(a, MWDG_ADJ_KC_LIMIT, st);
-    launch_limit<T>(a, PL, Un, z, W1, F1, Z1, st);
+    launch_limit<T>(a, TB, Un, z, W1, F1, Z1, st);
   }
   {
     Timed tm(a, MWDG_ADJ_KC_UPDATE, st);
-    launch_update<T>(a, PL, 1, F1, Z1, W1, nullptr, dts, s, Ui, clip, st);
+    launch_update<T>(a, TB, 1, F1, Z1, W1, nullptr, dts, s, Ui, clip, st);
   }
   Timed tm(a, MWDG_ADJ_KC_LIMIT, st);
-  launch_limit<T>(a, PL, Ui, z, W2, F2, Z2, st);
+  launch_limit<T>(a, TB, Ui, z, W2, F2, Z2, st);
 }
 
 // the forward sweep of one step s from tape slot s into slot s + 1
 template <typename T>
-void launch_step(mwdg_adj *a, const Par<T> *PL, const T *z, const T *nman, int s, bool cfl, double *dts,
+void launch_step(mwdg_adj *a, const Tabs<T> &TB, const T *z, const T *nman, int s, bool cfl, double *dts,
                  cudaStream_t st) {
   const long long n = a->n;
   const T *U = ptr<T>(a->tape) + (long long)s * 9 * n;
@@ -2047,17 +2201,29 @@ void launch_step(mwdg_adj *a, const Par<T> *PL, const T *z, const T *nman, int s
   uint8_t *clip = a->clip + (long long)s * n;
   if (cfl) {
     Timed tm(a, MWDG_ADJ_KC_CFL, st);
-    for (int l = 0; l < nlev(a); l++)
-      k_cfl<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], U + loff(a, l), a->tt, s, a->best);
-    k_dt<<<1, 1, 0, st>>>(PL[0].cfl, PL[0].dt_max, a->best, dts, a->tt, s);
+    if (a->levels) k_cfl<T, true><<<TB.nc, TPB, 0, st>>>(TB.cells, U, a->tt, s, a->best);
+    else k_cfl<T, false><<<TB.nc, TPB, 0, st>>>(TB.cells, U, a->tt, s, a->best);
+    k_dt<<<1, 1, 0, st>>>(TB.PL[0].cfl, TB.PL[0].dt_max, a->best, dts, a->tt, s);
   }
-  recompute_stages<T>(a, PL, U, z, nman, s, dts, clip, st);
+  recompute_stages<T>(a, TB, U, z, nman, s, dts, clip, st);
   const StageArrays<T> v = stage_arrays<T>(a, s);
   Timed tm(a, MWDG_ADJ_KC_UPDATE, st);
-  launch_update<T>(a, PL, 2, v.F2, v.Z2, ptr<T>(a->W2), ptr<T>(a->W1), dts, s, Unext, clip, st);
+  launch_update<T>(a, TB, 2, v.F2, v.Z2, ptr<T>(a->W2), ptr<T>(a->W1), dts, s, Unext, clip, st);
 }
 
-// per-level parameters (one entry on a uniform grid)
+// per-level parameters (one entry on a uniform grid) and the launch tables
+template <typename T>
+Tabs<T> make_tabs(const mwdg_adj *a, int nknots, const double *kt, const double *kQ) {
+  Tabs<T> TB;
+  for (int l = 0; l < nlev(a); l++) TB.PL.push_back(level_par<T>(a, l, nknots, kt, kQ));
+  TB.cells = make_levels(TB.PL, [](const Par<T> &P) { return blocks(P.n); }, TB.nc);
+  TB.tiles = make_levels(TB.PL, [](const Par<T> &P) {
+    return (long long)((P.nx + UT - 1) / UT) * ((P.ny + UT - 1) / UT); }, TB.nt);
+  TB.fxs = make_levels(TB.PL, [](const Par<T> &P) { return blocks((long long)P.ny * (P.nx + 1)); }, TB.nfx);
+  TB.fys = make_levels(TB.PL, [](const Par<T> &P) { return blocks((long long)(P.ny + 1) * P.nx); }, TB.nfy);
+  return TB;
+}
+
 template <typename T>
 std::vector<Par<T>> level_pars(const mwdg_adj *a, int nknots, const double *kt, const double *kQ) {
   std::vector<Par<T>> PL;
@@ -2097,10 +2263,10 @@ template <typename T>
 mwdg_status forward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int32_t nknots, const double *kt,
                       const double *kQ, double t0, int32_t steps, int32_t fixed_dt, double *dts, T *U_out,
                       cudaStream_t st) {
-  const std::vector<Par<T>> PL = level_pars<T>(a, nknots, kt, kQ);
+  const Tabs<T> TB = make_tabs<T>(a, nknots, kt, kQ);
   const size_t bytes = (size_t)9 * a->n * sizeof(T);
   if (a->levels) {
-    launch_pyramids<T>(a, PL.data(), z, nman, st);
+    launch_pyramids<T>(a, TB.PL.data(), z, nman, st);
     z = ptr<T>(a->zp);
     nman = ptr<T>(a->np);
     launch_scatter_state<T>(a, U0, st);
@@ -2109,7 +2275,7 @@ mwdg_status forward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int32
   }
   k_set_t0<<<1, 1, 0, st>>>(a->tt, t0);
   if (fixed_dt) k_times<<<1, 1, 0, st>>>(dts, steps, a->tt);
-  for (int k = 0; k < steps; k++) launch_step<T>(a, PL.data(), z, nman, k, !fixed_dt, dts, st);
+  for (int k = 0; k < steps; k++) launch_step<T>(a, TB, z, nman, k, !fixed_dt, dts, st);
   const T *UK = ptr<T>(a->tape) + (long long)steps * 9 * a->n;
   if (a->levels)
     k_nodes_to_leaves<T><<<blocks(a->nl), TPB, 0, st>>>(a->nl, a->n, a->node, UK, U_out);
@@ -2122,7 +2288,8 @@ template <typename T>
 mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int32_t nknots, const double *kt,
                        const double *kQ, double t0, int32_t steps, const double *dts_in, const T *gUK, T *gU0, T *gz,
                        T *gn, double *gQ, bool reuse, cudaStream_t st) {
-  const std::vector<Par<T>> PL = level_pars<T>(a, nknots, kt, kQ);
+  const Tabs<T> TB = make_tabs<T>(a, nknots, kt, kQ);
+  const std::vector<Par<T>> &PL = TB.PL;
   const long long n = a->n;
   const bool fz = a->levels > 0;
   const int NL = nlev(a), L = NL - 1;
@@ -2155,7 +2322,7 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
       return cuda_check(a, "mwdg_adj_backward copy-in");
     k_set_t0<<<1, 1, 0, st>>>(a->tt, t0);
     k_times<<<1, 1, 0, st>>>(a->dtbuf, steps, a->tt);
-    for (int k = 0; k < steps; k++) launch_step<T>(a, PL.data(), z, nman, k, false, a->dtbuf, st);
+    for (int k = 0; k < steps; k++) launch_step<T>(a, TB, z, nman, k, false, a->dtbuf, st);
   }
   if (fz) {
     if (cudaMemsetAsync(lU, 0, bytes, st) != cudaSuccess) return cuda_check(a, "mwdg_adj_backward seed");
@@ -2164,9 +2331,6 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
     return cuda_check(a, "mwdg_adj_backward seed");
   }
   const double *dts = a->dtbuf;
-  auto fx = [&](int l) { return fz ? limx + 14 * a->fxo[l] : limx; };
-  auto fy = [&](int l) { return fz ? limy + 14 * a->fyo[l] : limy; };
-  auto lqo = [&](int l) { return fz ? a->lq + a->lqo[l] : a->lq; };
   for (int k = steps - 1; k >= 0; k--) {
     const T *U = ptr<T>(a->tape) + (long long)k * 9 * n;
     const T *Y2 = ptr<T>(a->tape) + (long long)(k + 1) * 9 * n;
@@ -2174,7 +2338,7 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
     // the stage inputs of step k and their flux views: kept on the tape, or
     // recomputed (stage 1 then rewrites its clip bit with the same value and
     // keeps stage 2's from the tape run)
-    if (!a->views) recompute_stages<T>(a, PL.data(), U, z, nman, k, dts, clip, st);
+    if (!a->views) recompute_stages<T>(a, TB, U, z, nman, k, dts, clip, st);
     const StageArrays<T> v = stage_arrays<T>(a, k);
     const T *Un = v.Un, *Ui = v.Ui, *F1 = v.F1, *Z1 = v.Z1, *F2 = v.F2, *Z2 = v.Z2;
     for (int stage = 2; stage >= 1; stage--) {
@@ -2185,19 +2349,21 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
       const T *lY = stage == 2 ? lU : lX;
       {
         Timed tm(a, MWDG_ADJ_KC_REV_FACE, st);
-        for (int l = 0; l < NL; l++) {
-          const Par<T> &P = PL[l];
-          const long long o = loff(a, l);
-          const long long nfx = (long long)P.ny * (P.nx + 1), nfy = (long long)(P.ny + 1) * P.nx;
-          k_rev_face<T, true><<<blocks(nfx), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf + o, Zf + o, lY + o, Y + o,
-                                                           clip + o, fx(l), lqo(l));
-          k_rev_face<T, false><<<blocks(nfy), TPB, 0, st>>>(P, stage, dts, a->tt, k, Wf + o, Zf + o, lY + o, Y + o,
-                                                            clip + o, fy(l), lqo(l));
+        if (fz) {
+          k_rev_face<T, true, true><<<TB.nfx, TPB, 0, st>>>(TB.fxs, stage, dts, a->tt, k, Wf, Zf, lY, Y, clip,
+                                                            limx, a->lq);
+          k_rev_face<T, false, true><<<TB.nfy, TPB, 0, st>>>(TB.fys, stage, dts, a->tt, k, Wf, Zf, lY, Y, clip,
+                                                             limy, a->lq);
+        } else {
+          k_rev_face<T, true, false><<<TB.nfx, TPB, 0, st>>>(TB.fxs, stage, dts, a->tt, k, Wf, Zf, lY, Y, clip,
+                                                             limx, a->lq);
+          k_rev_face<T, false, false><<<TB.nfy, TPB, 0, st>>>(TB.fys, stage, dts, a->tt, k, Wf, Zf, lY, Y, clip,
+                                                              limy, a->lq);
         }
       }
       if (PL[0].nknots > 0) {
         Timed tm(a, MWDG_ADJ_KC_REV_KNOTS, st);
-        for (int l = 0; l < NL; l++) k_rev_knots<T><<<1, TPB, 0, st>>>(PL[l], stage, dts, a->tt, k, lqo(l), gQ);
+        k_rev_knots<T><<<1, TPB, 0, st>>>(TB.cells, stage, dts, a->tt, k, a->lq, gQ);
       }
       {
         Timed tm(a, MWDG_ADJ_KC_REV_LIMIT, st);
@@ -2205,36 +2371,23 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
           // the views in reverse: every node's view-plane cotangents, then
           // the prolongations (finest level up) and encodings (coarsest
           // down) transposed onto the leaves
-          for (int l = 0; l <= L; l++)
-            k_rev_view_gather<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], fx(l), fy(l), l > 0 ? fx(l - 1) : nullptr,
-                                                                  l > 0 ? fy(l - 1) : nullptr, gV + loff(a, l));
+          k_rev_view_gather<T><<<TB.nc, TPB, 0, st>>>(TB.cells, limx, limy, gV);
           for (int l = L - 1; l >= 0; l--) k_rev_prolong<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gV + loff(a, l));
           for (int l = 1; l <= L; l++) k_rev_encode<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gV + loff(a, l));
-        }
-        for (int l = 0; l < NL; l++) {
-          const long long o = loff(a, l);
-          if (fz)
-            k_rev_limit<T, true><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], stage, dts, k, X + o, z + o, lY + o, Y + o,
-                                                                  clip + o, lW1 + o, nullptr, nullptr, gV + o, lXo + o,
-                                                                  lnb + o, gzl + o);
-          else
-            k_rev_limit<T, false><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], stage, dts, k, X + o, z + o, lY + o,
-                                                                   Y + o, clip + o, lW1 + o, fx(l), fy(l), nullptr,
-                                                                   lXo + o, lnb + o, gzl + o);
+          k_rev_limit<T, true><<<TB.nc, TPB, 0, st>>>(TB.cells, stage, dts, k, X, z, lY, Y, clip, lW1, nullptr,
+                                                      nullptr, gV, lXo, lnb, gzl);
+        } else {
+          k_rev_limit<T, false><<<TB.nc, TPB, 0, st>>>(TB.cells, stage, dts, k, X, z, lY, Y, clip, lW1, limx, limy,
+                                                       nullptr, lXo, lnb, gzl);
         }
       }
       Timed tm(a, MWDG_ADJ_KC_REV_GATHER, st);
-      for (int l = 0; l < NL; l++) {
-        const long long o = loff(a, l);
-        k_rev_gather<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], lXo + o, lnb + o, lX + o, gzl + o);
-      }
+      if (fz) k_rev_gather<T, true><<<TB.nc, TPB, 0, st>>>(TB.cells, lXo, lnb, lX, gzl);
+      else k_rev_gather<T, false><<<TB.nc, TPB, 0, st>>>(TB.cells, lXo, lnb, lX, gzl);
     }
     Timed tm(a, MWDG_ADJ_KC_REV_FRICTION, st);
-    for (int l = 0; l < NL; l++) {
-      const long long o = loff(a, l);
-      k_rev_friction<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], U + o, nman + o, dts, a->tt, k, lX + o, lU + o,
-                                                         gnl + o);
-    }
+    if (fz) k_rev_friction<T, true><<<TB.nc, TPB, 0, st>>>(TB.cells, U, nman, dts, a->tt, k, lX, lU, gnl);
+    else k_rev_friction<T, false><<<TB.nc, TPB, 0, st>>>(TB.cells, U, nman, dts, a->tt, k, lX, lU, gnl);
   }
   if (fz) {
     k_nodes_to_leaves<T><<<blocks(a->nl), TPB, 0, st>>>(a->nl, n, a->node, lU, gU0);
