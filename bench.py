@@ -32,7 +32,10 @@ if ROOT not in sys.path:
 
 METRIC = "MWDG2/DG2 active-cell updates/s & % HBM roofline, FP32 vs FP64 at <=1e-3 m"
 UNIT = "active-cell updates/s"
-WORKLOAD = "MWDG2 1024x1024 fractal valley, dx=10 m, L=10, eps=1e-3, n=0.035, 400 m3/s inflow"
+def workload(n=1024, kind="MWDG2"):
+    """the valley workload's description at side n (L = log2 n)"""
+    return (f"{kind} {n}x{n} fractal valley, dx=10 m, L={n.bit_length() - 1}, eps=1e-3, n=0.035, "
+            "400 m3/s inflow")
 
 
 def parse():
@@ -388,7 +391,10 @@ def run_gpu(args, rank, world):
                                "peak_kind": "measured (FP64 FMA chains, CUDA events)",
                                "flops_per_update": FP64_FLOPS_PER_UPDATE,
                                "achieved": (v64 * FP64_FLOPS_PER_UPDATE / 1e12) if FP64_FLOPS_PER_UPDATE else None,
-                               "frac": (v64 * FP64_FLOPS_PER_UPDATE / fma64) if FP64_FLOPS_PER_UPDATE else None},
+                               "frac": (v64 * FP64_FLOPS_PER_UPDATE / fma64) if FP64_FLOPS_PER_UPDATE else None,
+                               # the FMA peak counts FMAs; the FP64 pipe's occupancy, measured by ncu,
+                               # is the binding figure for this add/multiply/compare mix
+                               "pipe_busy_pct_of_active_cycles": FP64_PIPE_BUSY},
                        "hbm": {"bytes_per_update": DG2_STEP_VALUES * 8 + MRA_BYTES_PER_LEAF[8],
                                "frac": (DG2_STEP_VALUES * 8 + MRA_BYTES_PER_LEAF[8]) * v64 / 1e9 / peak_gbs}}
         out["fma_peaks_tflops"] = {"fp64": fma64 / 1e12, "fp32": fma32 / 1e12}
@@ -444,7 +450,7 @@ def uniform_leg(p, stream, flush, K, W, spinup):
             "roofline": {"bound": "hbm", "peak": peak, "peak_kind": kind, "unit": "GB/s", "stages": stages,
                          "whole_step": {"bytes_per_update": wb, "achieved": wb * value / 1e9,
                                         "frac": wb * value / 1e9 / peak}},
-            "what": "uniform DG2 on the valley's finest grid (1,048,576 cells), FP32, fused stage kernels, "
+            "what": f"uniform DG2 on the valley's finest grid ({int(cells):,} cells), FP32, fused stage kernels, "
                     "L2 flushed before every timed step"}
 
 
@@ -574,7 +580,7 @@ def reference_arm(args):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": {"workload": workload(args.n)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                              "cpu_model": cpu["model"], "nproc": cpu["nproc"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -847,6 +853,10 @@ def run_adjoint_frozen(args, K):
 ADJ_VALUES_PER_CELL = {"friction": 19, "limit": 33, "update": 34.5, "cfl": 3, "rev_face": 49, "rev_limit": 67,
                        "rev_gather": 32, "rev_friction": 30}
 ADJ_FLAG_BYTES = {"update": 1, "rev_face": 1, "rev_limit": 1}
+# FP64 pipe busy (% of active cycles) over the FP64 step's kernels, from ncu
+# (profiles/fp64_pipe_valley512_mwdg2.md), while those kernels are unchanged
+FP64_PIPE_BUSY = {"min": 57.4, "max": 72.0, "stage_update": 72.0, "significance_encode": 62.1}
+
 # DRAM bytes (read + write) per launch measured by ncu for the FP32 adjoint
 # kernels at this workload, while the kernel is unchanged (see profiles/)
 # (captured before the interfaces' outflow limit was added to these kernels:
@@ -929,10 +939,10 @@ def main():
         line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-                "config": {"workload": (WORKLOAD if args.grid == "adaptive" else
-                                        {"uniform": "uniform DG2", "static": "static DG2"}[args.grid] + WORKLOAD[5:])
-                           if args.scheme == "dg2" else
-                           {"fv1": "HWFV1", "acc": "static-grid ACC"}[args.scheme] + WORKLOAD[5:],
+                "config": {"workload": workload(args.n, ({"adaptive": "MWDG2", "uniform": "uniform DG2",
+                                                          "static": "static DG2"}[args.grid]
+                                                         if args.scheme == "dg2" else
+                                                         {"fv1": "HWFV1", "acc": "static-grid ACC"}[args.scheme])),
                            "nx": args.n, "ny": args.n, "L": args.n.bit_length() - 1,
                            "eps": 1e-3, "spinup_s": out["t_spinup"], "mean_active_leaves": out["mean_active"],
                            "l2": "flushed (256 MB write) before every timed step",
