@@ -645,9 +645,10 @@ def run_ensemble(args):
     M in {1, 3}), per-member Manning n and inflow scale, FP32 MWDG2 at
     eps = 1e-3.  All members run to the spin-up time, the launch shapes are
     autotuned (unless --no-tune), then K ensemble steps (one graph launch
-    each) are timed with CUDA events, bracketed by an L2 flush.  The same K
-    steps with the members queued one after another (each its own graph)
-    are timed for comparison."""
+    each, the members in batched launches over a (member, block) work list)
+    are timed with CUDA events, bracketed by an L2 flush.  For comparison,
+    K steps of the same ensemble with one graph branch per member, and K
+    steps with the members queued one after another (each its own graph)."""
     import torch
     import paper_2107_02750_gb300 as M
     from paper_2107_02750_gb300 import synth as S
@@ -678,6 +679,23 @@ def run_ensemble(args):
         ev[1][1].record(stream)
         torch.cuda.synchronize()
         u2 = sum(m.get_counters()[1] for m in members)
+        # batched groups of g members (one launch per kernel and group)
+        batched = {}
+        for grp in (4, 8, 16, 64):
+            ens.set_batch(grp)
+            ens.step(args.warmup)
+            torch.cuda.synchronize()
+            ua = sum(m.get_counters()[1] for m in members)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(float(grp))
+            e0.record(stream)
+            ens.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ub = sum(m.get_counters()[1] for m in members)
+            ms = e0.elapsed_time(e1)
+            batched[str(grp)] = {"value": (ub - ua) / (ms * 1e-3), "ms_per_step": ms / args.steps}
+        ens.set_batch(0)
     ms_ens = ev[0][0].elapsed_time(ev[0][1])
     ms_seq = ev[1][0].elapsed_time(ev[1][1])
     sides = [p.nx for p in probs]
@@ -688,6 +706,10 @@ def run_ensemble(args):
             "config": {"workload": f"{len(probs)} seeded fractal valleys, sides {sorted(set(sides))} "
                                    f"(total {sum(x * x for x in sides)} finest cells), eps=1e-3",
                        "spinup_s": args.spinup, "tuned_shapes": chosen},
+            "batched_groups": {"unit": UNIT, "by_group_size": batched,
+                               "what": "the same ensemble with its members in batched groups of g (one launch "
+                                       "per kernel over a (member, block) work list per group, groups on "
+                                       "parallel branches)"},
             "sequential": {"value": (u2 - u1) / (ms_seq * 1e-3), "unit": UNIT,
                            "ms_per_step": ms_seq / args.steps,
                            "what": "the same steps with members queued one after another"}}

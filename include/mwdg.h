@@ -305,8 +305,9 @@ MWDG_API mwdg_status mwdg_get_launch_shape(mwdg_ctx *ctx, int32_t *grid_leaves, 
 
 /* Ensembles (batched scenarios of uneven sizes).  An ensemble steps n
  * independent contexts together: one CUDA graph per ensemble step holds
- * every member's step as a parallel branch, so small members share the GPU
- * instead of each leaving most of it idle.  Members are created and loaded
+ * every member's step as a parallel branch (or, with
+ * mwdg_ensemble_set_batched, groups of members as batched launches), so
+ * small members share the GPU instead of each leaving most of it idle.  Members are created and loaded
  * as usual (any mode, precision and size, same device); the ensemble
  * borrows them (the caller keeps ownership and must not destroy a member
  * while the ensemble exists).  Each member keeps its own time step; in
@@ -337,6 +338,19 @@ MWDG_API mwdg_status mwdg_ensemble_run_to_time(mwdg_ensemble *ens, double t_end,
  * steps are unchanged up to the FP32 contraction order of the coarsest MRA
  * levels (FP64: identical). */
 MWDG_API mwdg_status mwdg_ensemble_tune(mwdg_ensemble *ens, int32_t steps, int64_t *chosen);
+/* Batched launches: group = 2..64 puts the members on adaptive DG2 grids
+ * (MWDG2, Sect. 2.3) of one precision in groups of up to `group`; each
+ * group's step is one launch per kernel of the step (encode,
+ * regularisation, decode, compaction, limiter, flux views, stage updates;
+ * Eq. 9-10, Eq. 4) over a work list of (member, block): block b of the
+ * launch works as block b - s_m of member m, whose blocks start at s_m, with
+ * that member's own launch shape.  Groups and the other members are
+ * parallel graph branches.  group = 0 (the default) or 1: one branch per
+ * member.  Results are the same either way (each member's arithmetic and
+ * order are its own); the member tables live in device memory of the
+ * ensemble and are rebuilt with the graph.  MWDG_ERR_ARG for group outside
+ * 0..64. */
+MWDG_API mwdg_status mwdg_ensemble_set_batched(mwdg_ensemble *ens, int32_t group);
 MWDG_API const char *mwdg_ensemble_last_error(const mwdg_ensemble *ens);
 
 MWDG_API const char *mwdg_last_error(const mwdg_ctx *ctx);

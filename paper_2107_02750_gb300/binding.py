@@ -25,7 +25,8 @@ EXPORTS = (
     "mwdg_last_error", "mwdg_status_string", "mwdg_state_bytes", "mwdg_save_state",
     "mwdg_load_state", "mwdg_volume_noalloc", "mwdg_fma_rate", "mwdg_get_counters", "mwdg_read_gauges",
     "mwdg_set_launch_shape", "mwdg_get_launch_shape", "mwdg_ensemble_create", "mwdg_ensemble_destroy",
-    "mwdg_ensemble_step", "mwdg_ensemble_run_to_time", "mwdg_ensemble_tune", "mwdg_ensemble_last_error",
+    "mwdg_ensemble_step", "mwdg_ensemble_run_to_time", "mwdg_ensemble_tune", "mwdg_ensemble_set_batched",
+    "mwdg_ensemble_last_error",
 )
 
 
@@ -88,6 +89,7 @@ def lib(build: bool = True):
         "mwdg_ensemble_step": [vp, C.c_int64],
         "mwdg_ensemble_run_to_time": [vp, C.c_double, lp],
         "mwdg_ensemble_tune": [vp, C.c_int32, lp],
+        "mwdg_ensemble_set_batched": [vp, C.c_int32],
         "mwdg_read_active": [vp, ip, ip, ip, dp, C.c_int64, lp],
         "mwdg_get_time": [vp, dp, lp],
         "mwdg_get_counters": [vp, lp, lp],
@@ -370,10 +372,12 @@ class Solver:
 
 
 class Ensemble:
-    """Members (Solver objects on one device) stepped together: one CUDA graph
-    per ensemble step with every member's step as a parallel branch."""
+    """Members (Solver objects on one device) stepped together, one CUDA graph
+    per ensemble step: each member's step a parallel branch, or with batch = g
+    >= 2 the adaptive DG2 members of one precision in groups of g, each group's
+    step one launch per kernel over its members' blocks."""
 
-    def __init__(self, members, stream=None):
+    def __init__(self, members, stream=None, batch=0):
         self._lib = lib()
         self.members = list(members)  # keeps them alive
         n = len(self.members)
@@ -383,6 +387,12 @@ class Ensemble:
         if st != 0:
             raise MwdgError(st, "mwdg_ensemble_create", self._lib.mwdg_status_string(st).decode())
         self._h = h
+        if batch:
+            self.set_batch(batch)
+
+    def set_batch(self, group: int):
+        """members per batched group (0: one graph branch per member)"""
+        self._ck(self._lib.mwdg_ensemble_set_batched(self._h, int(group)), "mwdg_ensemble_set_batched")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1120,6 +1120,11 @@ struct mwdg_ensemble {
   std::vector<int64_t> gen;           // member generations the graph was built from
   std::vector<int> nk;                // kernels per member in one ensemble step
   bool own_st = false;                // st created here (no caller stream)
+  // batched launches: members of the adaptive DG2 pipeline with the same
+  // precision step together, one launch per kernel over all their blocks
+  int batch = 0;                                // members per batched group (0: none)
+  std::vector<std::vector<int>> groups;         // members of each batched group
+  std::vector<std::vector<BatchLaunch>> plans;  // its launches and member tables
   std::string err;
 };
 
@@ -1146,6 +1151,61 @@ mwdg_status efail(mwdg_ensemble *e, mwdg_status s, const char *fmt, ...) {
 void ens_drop_graph(mwdg_ensemble *e) {
   if (e->graph) cudaGraphExecDestroy(e->graph);
   e->graph = nullptr;
+}
+
+// the batched groups' member tables (after the work that reads them)
+void ens_free_plans(mwdg_ensemble *e) {
+  if (!e->plans.empty() && e->st) cudaStreamSynchronize(e->st);
+  for (auto &pl : e->plans)
+    for (BatchLaunch &b : pl)
+      if (b.tab) cudaFree(b.tab);
+  e->plans.clear();
+  e->groups.clear();
+}
+
+bool batchable(const mwdg_ctx *c) {
+  return c->g.mode == MWDG_ADAPTIVE && c->g.scheme == MWDG_DG2 && c->g.L >= 1;
+}
+
+// groups of up to BMAX batchable members of one precision (two or more)
+// and their launch plans
+mwdg_status ens_plan(mwdg_ensemble *e) {
+  ens_free_plans(e);
+  if (e->batch < 2) return MWDG_OK;
+  for (int prec : {MWDG_F32, MWDG_F64}) {
+    std::vector<int> cand;
+    for (size_t k = 0; k < e->m.size(); k++)
+      if (batchable(e->m[k]) && e->m[k]->g.prec == prec) cand.push_back((int)k);
+    for (size_t a = 0; a < cand.size(); a += (size_t)e->batch) {
+      const size_t b = std::min(cand.size(), a + (size_t)e->batch);
+      if (b - a >= 2) e->groups.emplace_back(cand.begin() + a, cand.begin() + b);
+    }
+  }
+  for (const std::vector<int> &grp : e->groups) {
+    e->plans.emplace_back();
+    std::vector<const Geo *> gs;
+    std::vector<int> gl;
+    for (int k : grp) {
+      gs.push_back(&e->m[k]->g);
+      gl.push_back(e->m[k]->grid_leaves);
+    }
+    bool ok;
+    if (e->m[grp[0]]->g.prec == MWDG_F64) {
+      std::vector<const Ptrs<double> *> ps;
+      for (int k : grp) ps.push_back(&e->m[k]->pd);
+      ok = Launch<double>::batch_plan((int)grp.size(), gs.data(), ps.data(), gl.data(), e->plans.back());
+    } else {
+      std::vector<const Ptrs<float> *> ps;
+      for (int k : grp) ps.push_back(&e->m[k]->pf);
+      ok = Launch<float>::batch_plan((int)grp.size(), gs.data(), ps.data(), gl.data(), e->plans.back());
+    }
+    if (!ok) {
+      cudaGetLastError();
+      ens_free_plans(e);
+      return efail(e, MWDG_ERR_CUDA, "ensemble: batched launch tables could not be allocated");
+    }
+  }
+  return MWDG_OK;
 }
 
 // members ready to step (reductions of their current leaves), and ensemble
@@ -1187,10 +1247,29 @@ mwdg_status ens_graph(mwdg_ensemble *e) {
   for (size_t k = 0; k < e->m.size() && !stale; k++) stale = e->gen[k] != e->m[k]->generation;
   if (!stale) return MWDG_OK;
   ens_drop_graph(e);
+  mwdg_status ps = ens_plan(e);
+  if (ps != MWDG_OK) return ps;
+  std::vector<char> grouped(e->m.size(), 0);
+  for (const std::vector<int> &grp : e->groups)
+    for (int k : grp) grouped[k] = 1;
   cudaGraph_t gr = nullptr;
   ECK(cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaEventRecord(e->fork, e->st);
+  // each batched group on the branch of its first member
+  for (size_t q = 0; q < e->groups.size() && err == cudaSuccess; q++) {
+    const int k0 = e->groups[q][0];
+    err = cudaStreamWaitEvent(e->br[k0], e->fork, 0);
+    if (err != cudaSuccess) break;
+    const int nl = e->m[k0]->g.prec == MWDG_F64 ? Launch<double>::batch_step(e->plans[q], e->br[k0])
+                                                : Launch<float>::batch_step(e->plans[q], e->br[k0]);
+    for (int k : e->groups[q]) e->nk[k] = 0;
+    e->nk[k0] = nl;
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaEventRecord(e->ev[k0], e->br[k0]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(e->st, e->ev[k0], 0);
+  }
   for (size_t k = 0; k < e->m.size() && err == cudaSuccess; k++) {
+    if (grouped[k]) continue;
     mwdg_ctx *c = e->m[k];
     err = cudaStreamWaitEvent(e->br[k], e->fork, 0);
     if (err != cudaSuccess) break;
@@ -1264,6 +1343,7 @@ void mwdg_ensemble_destroy(mwdg_ensemble *e) {
   if (!e) return;
   if (e->st) cudaStreamSynchronize(e->st);
   ens_drop_graph(e);
+  ens_free_plans(e);
   for (cudaStream_t s : e->br) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
@@ -1389,6 +1469,20 @@ mwdg_status mwdg_ensemble_tune(mwdg_ensemble *e, int32_t steps, int64_t *chosen)
   cudaEventDestroy(t1);
   ens_drop_graph(e);
   return s;
+}
+
+mwdg_status mwdg_ensemble_set_batched(mwdg_ensemble *e, int32_t group) {
+  if (!e) return MWDG_ERR_ARG;
+  if (group < 0 || group > BMAX) return efail(e, MWDG_ERR_ARG, "group size outside 0..%d", BMAX);
+  if (group == 1) group = 0;
+  if (e->batch != group) {
+    e->batch = group;
+    if (e->st) cudaStreamSynchronize(e->st);
+    ens_drop_graph(e);
+    ens_free_plans(e);
+    std::fill(e->gen.begin(), e->gen.end(), -1);
+  }
+  return MWDG_OK;
 }
 
 const char *mwdg_ensemble_last_error(const mwdg_ensemble *e) { return e ? e->err.c_str() : "null ensemble"; }

@@ -2,6 +2,8 @@
 // per-precision kernel translation units (mwdg_f64.cu, mwdg_f32.cu).
 #pragma once
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "mwdg.h"
@@ -85,6 +87,32 @@ struct Ptrs {
   const double *knot_t, *knot_Q;
 };
 
+// Batched ensemble steps: members that share the adaptive DG2 pipeline step
+// together, one launch per kernel (and MRA chunk) over all their blocks.
+// Block b of such a launch belongs to the member whose block range
+// [bstart, bstart + nblk) holds it and works as that member's block
+// b - bstart of nblk; the members' records (geometry, arrays, the launch's
+// per-member arguments) live in device memory, their first blocks in the
+// kernel's parameters.
+constexpr int BMAX = 64;  // members per batched launch
+struct BStarts {
+  int n;
+  unsigned s[BMAX + 1];  // first block of each member, then the total
+};
+template <typename T>
+struct BMember {
+  Geo g;
+  Ptrs<T> p;
+  int a[4];  // per-member arguments: MRA chunk (top level, levels, tail), view tail
+  unsigned bstart, nblk;
+};
+enum BKind { BK_SIG = 0, BK_REG, BK_DECODE, BK_SCATTER, BK_LIMIT1, BK_VIEW, BK_UPD1, BK_LIMIT2, BK_UPD2 };
+struct BatchLaunch {
+  int kind;
+  BStarts bs;
+  void *tab;  // device array of bs.n member records (owned by the ensemble)
+};
+
 // Launchers implemented per precision (explicit instantiations in
 // mwdg_f64.cu and mwdg_f32.cu).  All queue work on `st` and return the
 // number of kernels they launched.
@@ -118,6 +146,13 @@ template <typename T> struct Launch {
                          double *coef, cudaStream_t st);
   static int volume(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st);
   static int dt_only(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st);
+  // the batched launches of one step of n <= BMAX adaptive DG2 members (the
+  // sequence of adapt + step for each, with its own launch shapes); the
+  // member tables are allocated and filled here (synchronous host work).
+  // false when an allocation or copy fails (plan then holds what to free)
+  static bool batch_plan(int n, const Geo *const *g, const Ptrs<T> *const *p, const int *grid_leaves,
+                         std::vector<BatchLaunch> &plan);
+  static int batch_step(const std::vector<BatchLaunch> &plan, cudaStream_t st);
 };
 
 // kernel classes reported by the per-kernel timer

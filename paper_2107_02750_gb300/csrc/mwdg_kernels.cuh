@@ -437,13 +437,13 @@ static __global__ void k_compact_scan(int nb, int *blk, int *total) { block_scan
 
 // true in exactly one block, the last to get here; every block's global
 // writes before this point are visible to that block's L2 reads afterwards
-__device__ __forceinline__ bool last_block(unsigned int *ticket) {
+__device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned nblk) {
   __shared__ int last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int v = atomicAdd(ticket, 1u);
-    last = (v == gridDim.x - 1);
+    last = (v == nblk - 1);
     if (last) {
       *ticket = 0u;  // ready for the next launch
       __threadfence();
@@ -559,16 +559,17 @@ static_assert(CPT == 8, "one 8-byte word of kinds per thread");
 // block with the highest index writes the total to *nleaf before it takes
 // its completion ticket, and with begin the last block to finish starts the
 // step on the new leaves.
-static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *blk, long long *leaves,
-                                         uint8_t *kind_out, Ctl *ctl, int *nleaf, int begin) {
+__device__ __forceinline__ void compact_scatter(const Geo &g, const uint8_t *kind, const int *blk, long long *leaves,
+                                                uint8_t *kind_out, Ctl *ctl, int *nleaf, int begin, unsigned bid,
+                                                unsigned nblk) {
   const long long P = g.P;
-  const long long base = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
+  const long long base = (long long)bid * CTILE + (long long)threadIdx.x * CPT;
   const bool full = base + CPT <= P;
   // the counts of the blocks before this one (their loads in flight with
   // the kinds')
   int before = 0;
   if (ctl)
-    for (int r = threadIdx.x; r < (int)blockIdx.x; r += TPB) before += blk[r];
+    for (int r = threadIdx.x; r < (int)bid; r += TPB) before += blk[r];
   uint8_t kk[CPT];
   uint2 w8 = make_uint2(0u, 0u);
   if (full) {
@@ -615,9 +616,9 @@ static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *
     off = 0;
 #pragma unroll
     for (int w = 0; w < TPB / 32; w++) off += wb[w];
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == TPB - 1) *nleaf = off + ws[TPB / 32 - 1];
+    if (bid == nblk - 1 && threadIdx.x == TPB - 1) *nleaf = off + ws[TPB / 32 - 1];
   } else {
-    off = blk[blockIdx.x];
+    off = blk[bid];
   }
   int pos = off + x - c + ((threadIdx.x >> 5) ? ws[(threadIdx.x >> 5) - 1] : 0);
   for (int q = 0; q < CPT; q++) {
@@ -628,7 +629,12 @@ static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *
     }
   }
   // the last block to finish sees the total and starts the step
-  if (ctl && last_block(&ctl->ticket) && begin && threadIdx.x == 0) begin_step(g, ctl, nleaf);
+  if (ctl && last_block(&ctl->ticket, nblk) && begin && threadIdx.x == 0) begin_step(g, ctl, nleaf);
+}
+
+static __global__ void k_compact_scatter(Geo g, const uint8_t *kind, const int *blk, long long *leaves,
+                                         uint8_t *kind_out, Ctl *ctl, int *nleaf, int begin) {
+  compact_scatter(g, kind, blk, leaves, kind_out, ctl, nleaf, begin, blockIdx.x, gridDim.x);
 }
 
 // the four face-neighbour codes of every active leaf (one thread per leaf)
@@ -678,9 +684,11 @@ __device__ __forceinline__ double inflow_q(const Geo &g, const double *kt, const
 // ---------------------------------------------------------------------------
 // Step kernels (leaf-list, fixed grid striding over the device count)
 // ---------------------------------------------------------------------------
-#define FOR_LEAVES(p)                                                              \
+#define FOR_LEAVES(p) FOR_LEAVES_B(p, blockIdx.x, gridDim.x)
+// the same for block bid of nblk (a batched launch's member-local block)
+#define FOR_LEAVES_B(p, bid, nblk)                                                 \
   const int _nl = *(p).nleaf;                                                      \
-  for (int _q = blockIdx.x * blockDim.x + threadIdx.x; _q < _nl; _q += gridDim.x * blockDim.x)
+  for (int _q = (int)(bid) * blockDim.x + threadIdx.x; _q < _nl; _q += (int)(nblk) * blockDim.x)
 
 // max |v0| over the leaves of h, qx, qy (normalisation of flow details)
 template <typename T>
@@ -808,9 +816,10 @@ struct Tile { int ltop, nlev, bx, by; };
 // most 64 registers a thread; FP64 keeps its registers)
 template <typename T> struct MraOcc { static constexpr int blocks = std::is_same<T, float>::value ? 4 : 1; };
 
-__device__ __forceinline__ Tile tile_of_block(const Geo &g, int ltop, int nlev) {
+// the tile of block bid of a launch over the tiles of level ltop
+__device__ __forceinline__ Tile tile_of_block(const Geo &g, int ltop, int nlev, unsigned bid) {
   const int tiles_x = (g.nxl[ltop] + MT - 1) / MT;
-  return Tile{ltop, nlev, (int)(blockIdx.x % tiles_x), (int)(blockIdx.x / tiles_x)};
+  return Tile{ltop, nlev, (int)(bid % tiles_x), (int)(bid / tiles_x)};
 }
 
 // the coarsest levels fit one tile (run from shared memory by the last block)
@@ -1123,12 +1132,18 @@ __device__ __forceinline__ void sig_tail(const Geo &g, const Ptrs<T> &p, int tai
 // encode + significance flags: levels ltop..ltop-nlev+1 in tiles, then
 // (tail >= 0) levels tail..0 in the last block
 template <typename T, bool FV1>
-__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_sig(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+__device__ __forceinline__ void mra_sig(const Geo &g, const Ptrs<T> &p, int ltop, int nlev, int tail, unsigned bid,
+                                        unsigned nblk) {
   __shared__ SigStage<T> sh;
   if (!ADAPT_LIVE(p)) return;
-  if (nlev > 0) sig_tile<false, FV1>(g, p, tile_of_block(g, ltop, nlev), sh);
-  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+  if (nlev > 0) sig_tile<false, FV1>(g, p, tile_of_block(g, ltop, nlev, bid), sh);
+  if (tail < 0 || !last_block(&p.ctl->ticket, nblk)) return;
   sig_tail<FV1>(g, p, tail, sh);
+}
+
+template <typename T, bool FV1>
+__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_sig(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+  mra_sig<T, FV1>(g, p, ltop, nlev, tail, blockIdx.x, gridDim.x);
 }
 
 struct RegStage {
@@ -1225,13 +1240,19 @@ __device__ __forceinline__ void reg_tail(const Geo &g, const Ptrs<T> &p, int tai
 // regularised flags, same chunking; the CFL minimum is reset here for the
 // decode pass that follows
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_mra_regularise(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+__device__ __forceinline__ void mra_regularise(const Geo &g, const Ptrs<T> &p, int ltop, int nlev, int tail,
+                                               unsigned bid, unsigned nblk) {
   __shared__ RegStage sh;
-  if (ltop == g.L - 1 && blockIdx.x == 0 && threadIdx.x == 0) p.ctl->dtmin = 0x7ff0000000000000ULL;
+  if (ltop == g.L - 1 && bid == 0 && threadIdx.x == 0) p.ctl->dtmin = 0x7ff0000000000000ULL;
   if (!ADAPT_LIVE(p)) return;
-  if (nlev > 0) reg_tile<false>(g, p, tile_of_block(g, ltop, nlev), sh);
-  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+  if (nlev > 0) reg_tile<false>(g, p, tile_of_block(g, ltop, nlev, bid), sh);
+  if (tail < 0 || !last_block(&p.ctl->ticket, nblk)) return;
   reg_tail(g, p, tail, sh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_mra_regularise(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+  mra_regularise<T>(g, p, ltop, nlev, tail, blockIdx.x, gridDim.x);
 }
 
 // The regularisation's coarsest levels tail..0, run by the first block of
@@ -1336,10 +1357,10 @@ __device__ __forceinline__ uint8_t byte_of(uint2 w, int q) {
 // ftail >= 0: the first block first runs the coarsest levels ftail..0 of
 // the regularisation (coarse_flags).
 template <typename T>
-__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_decode(Geo g, Ptrs<T> p, int ftail) {
+__device__ __forceinline__ void mra_decode(const Geo &g, const Ptrs<T> &p, int ftail, unsigned bid) {
   const long long P = g.P;
-  if (ftail >= 0 && blockIdx.x == 0 && ADAPT_LIVE(p)) coarse_flags<T>(g, p, ftail);
-  const long long k0 = (long long)blockIdx.x * CTILE + (long long)threadIdx.x * CPT;
+  if (ftail >= 0 && bid == 0 && ADAPT_LIVE(p)) coarse_flags<T>(g, p, ftail);
+  const long long k0 = (long long)bid * CTILE + (long long)threadIdx.x * CPT;
   const ForceTime t{p.ctl, false};
   int cnt = 0;
   T best = tinf<T>();
@@ -1430,9 +1451,14 @@ __global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_decode(Geo g, Pt
       sum += ws[w];
       b = tmin(b, wb[w]);
     }
-    p.blk[blockIdx.x] = sum;
+    p.blk[bid] = sum;
     if (b < tinf<T>()) atomic_min_pos(&p.ctl->dtmin, (double)b);  // one FP64 conversion per block
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) k_mra_decode(Geo g, Ptrs<T> p, int ftail) {
+  mra_decode<T>(g, p, ftail, blockIdx.x);
 }
 
 static __global__ void k_begin_step(Geo g, Ctl *c, const int *nleaf) { begin_step(g, c, nleaf); }
@@ -1573,13 +1599,14 @@ __device__ __forceinline__ void limit_minmod(const Geo &g, const T (&w)[9], cons
 template <typename T> struct LimOcc { static constexpr int blocks = std::is_same<T, float>::value ? 4 : 1; };
 // UNI: a uniform grid (uniform_leaf instead of the active list and codes)
 template <typename T, bool FRIC, bool FV1, bool CODES, bool UNI>
-__global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
+__device__ __forceinline__ void leaf_limit(const Geo &g, const Ptrs<T> &p, const T *X, T *Wst, unsigned bid,
+                                           unsigned nblk) {
   const long long P = g.P;
   const T hd = geo_hd<T>(g), s3 = s3v<T>(), gg = geo_g<T>(g);
   const T dt = ctl_dt<T>(p.ctl);
   const bool rain = FRIC && p.ctl->rain_on;
   const T rinc = ctl_rain<T>(p.ctl);
-  FOR_LEAVES(p) {
+  FOR_LEAVES_B(p, bid, nblk) {
     int l, i, j;
     long long code[4];
     const long long k = UNI ? uniform_leaf(g, _q, l, i, j, code) : unpack_leaf(g, p.leaves[_q], l, i, j);
@@ -1666,6 +1693,11 @@ __global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) k_leaf_limit(Geo g, Pt
     for (int m = 0; m < 3; m++) rec[9 + m] = ze[m];
     store_rec(p.FZ, k, rec);
   }
+}
+
+template <typename T, bool FRIC, bool FV1, bool CODES, bool UNI>
+__global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) k_leaf_limit(Geo g, Ptrs<T> p, const T *X, T *Wst) {
+  leaf_limit<T, FRIC, FV1, CODES, UNI>(g, p, X, Wst, blockIdx.x, gridDim.x);
 }
 
 // local encoding (Eq. 9) of the flux view and its beds onto a refined node
@@ -1793,10 +1825,11 @@ __device__ __forceinline__ void view_tile(const Geo &g, const Ptrs<T> &p, const 
 // tiles of a 512 x 512 level run in one wave; FP64 keeps its registers)
 template <typename T> struct ViewOcc { static constexpr int blocks = std::is_same<T, float>::value ? 7 : 1; };
 template <typename T, bool FV1>
-__global__ void __launch_bounds__(TPB, ViewOcc<T>::blocks) k_view_tiles(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+__device__ __forceinline__ void view_tiles(const Geo &g, const Ptrs<T> &p, int ltop, int nlev, int tail, unsigned bid,
+                                           unsigned nblk) {
   __shared__ ViewStage<T> sh;
-  if (nlev > 0) view_tile<false, FV1>(g, p, tile_of_block(g, ltop, nlev), sh);
-  if (tail < 0 || !last_block(&p.ctl->ticket)) return;
+  if (nlev > 0) view_tile<false, FV1>(g, p, tile_of_block(g, ltop, nlev, bid), sh);
+  if (tail < 0 || !last_block(&p.ctl->ticket, nblk)) return;
   if (tail_is_tile(g, tail)) {
     view_tile<true, FV1>(g, p, Tile{tail, tail + 1, 0, 0}, sh);
     return;
@@ -1806,6 +1839,11 @@ __global__ void __launch_bounds__(TPB, ViewOcc<T>::blocks) k_view_tiles(Geo g, P
     for (int r = threadIdx.x; r < n; r += blockDim.x) encode_view_node<FV1>(g, p, l, r % g.nxl[l], r / g.nxl[l]);
     __syncthreads();
   }
+}
+
+template <typename T, bool FV1>
+__global__ void __launch_bounds__(TPB, ViewOcc<T>::blocks) k_view_tiles(Geo g, Ptrs<T> p, int ltop, int nlev, int tail) {
+  view_tiles<T, FV1>(g, p, ltop, nlev, tail, blockIdx.x, gridDim.x);
 }
 
 // Flux-view encode of the coarsest levels tail..0, run by the first block of
@@ -2398,11 +2436,11 @@ template <typename T> struct UpdOcc { static constexpr int blocks = std::is_same
 // instantiations do not contain the call.
 // UNI: a uniform grid (uniform_leaf instead of the active list and codes)
 template <typename T, int STAGE, bool REFLUX, bool VIEWS, bool UNI>
-__global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out,
-                                                                      int vtail) {
+__device__ __forceinline__ void leaf_update(const Geo &g, const Ptrs<T> &p, const T *Wst, const T *Wcomb, T *Out,
+                                            int vtail, unsigned bid, unsigned nblk) {
   const long long P = g.P;
   if (!ctl_stepping(p.ctl)) return;  // a zero step changes nothing (end_step ignores it too)
-  if (VIEWS && vtail >= 0 && blockIdx.x == 0) coarse_views<T>(g, p, vtail);
+  if (VIEWS && vtail >= 0 && bid == 0) coarse_views<T>(g, p, vtail);
   const T dt = ctl_dt<T>(p.ctl), gg = geo_g<T>(g), hd = geo_hd<T>(g), s3 = s3v<T>();
   const ForceTime tf{p.ctl, STAGE == 2};
   T bsum = T(0);  // per-thread sum of a few boundary fluxes; FP64 from the block sum on
@@ -2416,8 +2454,7 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
   T best = tinf<T>();
   const int nl = *p.nleaf;
   // one thread per leaf: the four interfaces, then the three variables
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nl;
-       q += (long long)gridDim.x * blockDim.x) {
+  for (long long q = bid * (long long)blockDim.x + threadIdx.x; q < nl; q += (long long)nblk * blockDim.x) {
     int l, i, j;
     long long code[4];
     const long long k = UNI ? uniform_leaf(g, q, l, i, j, code) : unpack_leaf(g, p.leaves[q], l, i, j);
@@ -2467,7 +2504,13 @@ __global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, P
     }
     if (STAGE >= 2) next_step_reduce<T>(g, p, l, i, j, o[0][0], o[1][0], o[2][0], tf, m0, m1, m2, best);
   }
-  update_epilogue<T, STAGE, TPB>(g, p, bsum, csum, ncl, bad, m0, m1, m2, best, gridDim.x);
+  update_epilogue<T, STAGE, TPB>(g, p, bsum, csum, ncl, bad, m0, m1, m2, best, nblk);
+}
+
+template <typename T, int STAGE, bool REFLUX, bool VIEWS, bool UNI>
+__global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out,
+                                                                      int vtail) {
+  leaf_update<T, STAGE, REFLUX, VIEWS, UNI>(g, p, Wst, Wcomb, Out, vtail, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -3262,6 +3305,199 @@ int Launch<T>::volume(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStrea
   k_volume_part<T><<<grid_leaves, TPB, 0, st>>>(g, p);
   k_volume_final<<<1, TPB, 0, st>>>(p.part, grid_leaves, p.ctl);
   return 2;
+}
+
+// ---------------------------------------------------------------------------
+// Batched ensemble steps: the kernels of an adaptive DG2 step, each launched
+// once over the blocks of all members (a work list of (member, block)).
+// ---------------------------------------------------------------------------
+// the member of this block (its record copied to shared memory) and the
+// block's index within the member's range
+template <typename T>
+__device__ __forceinline__ unsigned batch_member(const BMember<T> *tab, const BStarts &bs, BMember<T> &m) {
+  __shared__ int mi;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = bs.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (bs.s[mid] <= blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    mi = lo;
+  }
+  __syncthreads();
+  constexpr int W = (int)(sizeof(BMember<T>) / sizeof(unsigned));
+  const unsigned *src = reinterpret_cast<const unsigned *>(tab + mi);
+  unsigned *dst = reinterpret_cast<unsigned *>(&m);
+  for (int w = threadIdx.x; w < W; w += blockDim.x) dst[w] = src[w];
+  __syncthreads();
+  return blockIdx.x - m.bstart;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) kb_sig(const BMember<T> *tab, const BStarts bs) {
+  __shared__ BMember<T> m;
+  const unsigned b = batch_member(tab, bs, m);
+  mra_sig<T, false>(m.g, m.p, m.a[0], m.a[1], m.a[2], b, m.nblk);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) kb_reg(const BMember<T> *tab, const BStarts bs) {
+  __shared__ BMember<T> m;
+  const unsigned b = batch_member(tab, bs, m);
+  mra_regularise<T>(m.g, m.p, m.a[0], m.a[1], m.a[2], b, m.nblk);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB, MraOcc<T>::blocks) kb_decode(const BMember<T> *tab, const BStarts bs) {
+  __shared__ BMember<T> m;
+  const unsigned b = batch_member(tab, bs, m);
+  mra_decode<T>(m.g, m.p, m.a[0], b);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) kb_scatter(const BMember<T> *tab, const BStarts bs) {
+  __shared__ BMember<T> m;
+  const unsigned b = batch_member(tab, bs, m);
+  compact_scatter(m.g, m.p.kind_new, m.p.blk, m.p.leaves, m.p.kind, m.p.ctl, m.p.nleaf, 1, b, m.nblk);
+}
+
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(TPB, LimOcc<T>::blocks) kb_limit(const BMember<T> *tab, const BStarts bs) {
+  __shared__ BMember<T> m;
+  const unsigned b = batch_member(tab, bs, m);
+  if (STAGE == 1) leaf_limit<T, true, false, true, false>(m.g, m.p, m.p.U, m.p.Wn, b, m.nblk);
+  else leaf_limit<T, false, false, false, false>(m.g, m.p, m.p.Ui, m.p.Wi, b, m.nblk);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB, ViewOcc<T>::blocks) kb_view(const BMember<T> *tab, const BStarts bs) {
+  __shared__ BMember<T> m;
+  const unsigned b = batch_member(tab, bs, m);
+  view_tiles<T, false>(m.g, m.p, m.a[0], m.a[1], m.a[2], b, m.nblk);
+}
+
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) kb_update(const BMember<T> *tab, const BStarts bs) {
+  __shared__ BMember<T> m;
+  const unsigned b = batch_member(tab, bs, m);
+  if (STAGE == 1) leaf_update<T, 1, false, true, false>(m.g, m.p, m.p.Wn, nullptr, m.p.Ui, m.a[3], b, m.nblk);
+  else leaf_update<T, 2, false, true, false>(m.g, m.p, m.p.Wi, m.p.Wn, m.p.U, m.a[3], b, m.nblk);
+}
+
+// The launches of Launch<T>::adapt (begin = 1) and Launch<T>::step
+// (begun = 1) for every member, in their order and with their arguments:
+// encode and regularisation per chunk, decode, scatter (which starts the
+// step), then per stage the limiter, the flux views per chunk and the
+// update.  A member takes part in the j-th chunk launch of a pass when it
+// has that many chunks.
+template <typename T>
+bool Launch<T>::batch_plan(int n, const Geo *const *g, const Ptrs<T> *const *p, const int *grid_leaves,
+                           std::vector<BatchLaunch> &plan) {
+  struct Ch { int ltop, nlev, tail, blocks; };
+  std::vector<std::vector<Ch>> sig(n), reg(n), view(n);
+  std::vector<int> ftail(n), vtail(n), nb(n);
+  size_t ns = 0, nr = 0, nv = 0;
+  for (int m = 0; m < n; m++) {
+    const Geo &G = *g[m];
+    const int lc = coarse_top(G);
+    const bool defer = lc >= 0 && lc < G.L - 1 && G.off[lc + 2] <= CTILE;
+    for_chunks(G, [&](int ltop, int nlev, int tail, int blocks) { sig[m].push_back({ltop, nlev, tail, blocks}); });
+    for_chunks(G, [&](int ltop, int nlev, int tail, int blocks) {
+      reg[m].push_back({ltop, nlev, defer ? -1 : tail, blocks});
+    });
+    ftail[m] = defer ? lc : -1;
+    nb[m] = (int)((G.P + CTILE - 1) / CTILE);
+    vtail[m] = (lc >= 0 && lc < G.L - 1 && lvl(G, lc) <= TPB) ? lc : -1;
+    for_chunks(G, [&](int ltop, int nlev, int tail, int blocks) {
+      view[m].push_back({ltop, nlev, vtail[m] >= 0 ? -1 : tail, blocks});
+    });
+    ns = std::max(ns, sig[m].size());
+    nr = std::max(nr, reg[m].size());
+    nv = std::max(nv, view[m].size());
+  }
+  bool ok = true;
+  // one launch: the members for which rec(m, r) fills a record
+  auto add = [&](int kind, auto &&rec) {
+    if (!ok) return;
+    std::vector<BMember<T>> recs;
+    BatchLaunch bl{};
+    bl.kind = kind;
+    unsigned b = 0;
+    for (int m = 0; m < n; m++) {
+      BMember<T> r{};
+      r.g = *g[m];
+      r.p = *p[m];
+      r.a[0] = r.a[1] = r.a[2] = r.a[3] = -1;
+      if (!rec(m, r) || r.nblk == 0) continue;
+      r.bstart = b;
+      bl.bs.s[recs.size()] = b;
+      b += r.nblk;
+      recs.push_back(r);
+    }
+    if (recs.empty()) return;
+    bl.bs.n = (int)recs.size();
+    bl.bs.s[bl.bs.n] = b;
+    if (cudaMalloc(&bl.tab, recs.size() * sizeof(BMember<T>)) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    plan.push_back(bl);
+    ok = cudaMemcpy(bl.tab, recs.data(), recs.size() * sizeof(BMember<T>), cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  auto chunk = [&](const std::vector<std::vector<Ch>> &c, size_t j) {
+    return [&c, j](int m, BMember<T> &r) {
+      if (j >= c[m].size()) return false;
+      r.a[0] = c[m][j].ltop;
+      r.a[1] = c[m][j].nlev;
+      r.a[2] = c[m][j].tail;
+      r.nblk = (unsigned)c[m][j].blocks;
+      return true;
+    };
+  };
+  auto leaves = [&](int m, BMember<T> &r) {
+    r.a[3] = vtail[m];
+    r.nblk = (unsigned)grid_leaves[m];
+    return true;
+  };
+  for (size_t j = 0; j < ns; j++) add(BK_SIG, chunk(sig, j));
+  for (size_t j = 0; j < nr; j++) add(BK_REG, chunk(reg, j));
+  add(BK_DECODE, [&](int m, BMember<T> &r) {
+    r.a[0] = ftail[m];
+    r.nblk = (unsigned)nb[m];
+    return true;
+  });
+  add(BK_SCATTER, [&](int m, BMember<T> &r) {
+    r.nblk = (unsigned)nb[m];
+    return true;
+  });
+  add(BK_LIMIT1, leaves);
+  for (size_t j = 0; j < nv; j++) add(BK_VIEW, chunk(view, j));
+  add(BK_UPD1, leaves);
+  add(BK_LIMIT2, leaves);
+  for (size_t j = 0; j < nv; j++) add(BK_VIEW, chunk(view, j));
+  add(BK_UPD2, leaves);
+  return ok;
+}
+
+template <typename T>
+int Launch<T>::batch_step(const std::vector<BatchLaunch> &plan, cudaStream_t st) {
+  for (const BatchLaunch &b : plan) {
+    const BMember<T> *tab = static_cast<const BMember<T> *>(b.tab);
+    const unsigned nbk = b.bs.s[b.bs.n];
+    switch (b.kind) {
+      case BK_SIG: kb_sig<T><<<nbk, TPB, 0, st>>>(tab, b.bs); break;
+      case BK_REG: kb_reg<T><<<nbk, TPB, 0, st>>>(tab, b.bs); break;
+      case BK_DECODE: kb_decode<T><<<nbk, TPB, 0, st>>>(tab, b.bs); break;
+      case BK_SCATTER: kb_scatter<T><<<nbk, TPB, 0, st>>>(tab, b.bs); break;
+      case BK_LIMIT1: kb_limit<T, 1><<<nbk, TPB, 0, st>>>(tab, b.bs); break;
+      case BK_VIEW: kb_view<T><<<nbk, TPB, 0, st>>>(tab, b.bs); break;
+      case BK_UPD1: kb_update<T, 1><<<nbk, TPB, 0, st>>>(tab, b.bs); break;
+      case BK_LIMIT2: kb_limit<T, 2><<<nbk, TPB, 0, st>>>(tab, b.bs); break;
+      default: kb_update<T, 2><<<nbk, TPB, 0, st>>>(tab, b.bs); break;
+    }
+  }
+  return (int)plan.size();
 }
 
 #undef MARK

@@ -1,7 +1,8 @@
 """Ensembles (batched scenarios of uneven sizes, one CUDA graph per ensemble
 step): every member ends exactly where it ends when stepped alone, through
 step counts, run_to_time, interleaved member calls and the launch-shape
-autotuner."""
+autotuner, with the adaptive members in batched launches over a (member,
+block) work list or as one graph branch each."""
 import numpy as np
 import pytest
 
@@ -124,3 +125,38 @@ def test_ensemble_members_match_the_oracle():
         assert np.abs(cg - co).max() <= 1e-9, f"member {k}"
         t, steps = members[k].get_time()
         assert steps == 40 and abs(t - o.t) <= 1e-9 * o.t
+
+
+@pytest.mark.parametrize("batch", [0, 2, 64])
+def test_batched_and_branch_ensembles_equal_members_alone(batch):
+    """A mixed ensemble: three FP32 and two FP64 MWDG2 members of uneven sizes
+    (in batched groups of up to `batch` members of one precision), a
+    static-grid and a uniform-grid member (graph branches either way); 25
+    ensemble steps, then run_to_time, every member bit for bit as when
+    stepped alone."""
+    import paper_2107_02750_gb300 as M
+    from dataclasses import replace
+
+    def build():
+        probs = S.ensemble(count=5, seed=6, sides=(64, 96, 128, 192), eps=1e-2)
+        extra = [replace(S.ensemble(count=1, seed=8, sides=(64,), eps=1e-2)[0], mode=S.STATIC),
+                 replace(S.ensemble(count=1, seed=9, sides=(64,), eps=1e-2)[0], mode=S.UNIFORM)]
+        precs = [M.F32, M.F64, M.F32, M.F64, M.F32, M.F64, M.F32]
+        return [M.solver_from_problem(q, precision=precs[k]) for k, q in enumerate(probs + extra)]
+
+    members, alone = build(), build()
+    e = M.Ensemble(members, batch=batch)
+    e.step(25)
+    for k, s in enumerate(alone):
+        s.run_steps(25)
+        _same(members[k], s, f"member {k}")
+    e.run_to_time(35.0)
+    for k, s in enumerate(alone):
+        s.run_to_time(35.0)
+        _same(members[k], s, f"member {k} after run_to_time")
+    # switching mid-run keeps the results
+    e.set_batch(0 if batch else 3)
+    e.step(5)
+    for k, s in enumerate(alone):
+        s.run_steps(5)
+        _same(members[k], s, f"member {k} after switching")
