@@ -334,7 +334,8 @@ def run_gpu(args, rank, world):
     achieved = (abpl * mean_leaves) / launch_s / 1e9 if abpl else None
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak_gbs,
                 "unit": "GB/s", "frac": (achieved / peak_gbs) if achieved else None,
-                "traffic": TRAFFIC.get(dom_name) if (args.grid, args.scheme) == ("adaptive", "dg2") else None,
+                "traffic": (TRAFFIC.get(dom_name) if (args.grid, args.scheme, args.precision, args.n) ==
+                            ("adaptive", "dg2", "f32", 1024) else None),
                 "peak_kind": peak_kind, "algorithmic_bytes_per_leaf": abpl,
                 "design_bytes_per_leaf": bpl,
                 "design_frac": (bpl * mean_leaves / launch_s / 1e9 / peak_gbs) if bpl else None,
