@@ -17,7 +17,10 @@ held fixed over a segment (Sect. 2.3), against the FP64 oracles.
   * re-freezing at a checkpoint (mwdg_adj_regrid, the MWDG2 adaptation's
     state transfer to the grid the C oracle chose) reproduces the C oracle
     bit for bit, also where refined depth planes need scaling, and its
-    transpose and the chain's gradients equal the oracle's to 1e-9.
+    transpose and the chain's gradients equal the oracle's to 1e-9;
+  * on the benchmark's own MWDG2 grid (1024 x 1024, 10 levels), which the
+    oracle cannot run, central differences of the FP64 forward converge to
+    the FP64 gradients and FP32 tracks FP64.
 """
 from dataclasses import replace
 
@@ -365,3 +368,76 @@ def test_regrid_with_refined_depth_planes_matches_the_oracles():
     coef = torch.tensor(cb, requires_grad=True)
     (AS.regrid(coef, G1, G2) * torch.as_tensor(W)).sum().backward()
     _close(g.cpu().numpy().T, coef.grad.numpy(), "U")
+
+
+def test_full_size_frozen_mwdg2_gradients():
+    """The benchmark's own grid: the 1024 x 1024 valley's MWDG2 leaves and
+    state after 600 s of the FP64 solver, frozen, one 10-step segment with a
+    seeded functional of the leaves.  The oracle cannot run this size, so
+    properties that hold at any size stand in: central differences of the
+    FP64 forward (steps held, 1e-6 to 1e-8) converge to the FP64 gradients
+    at sampled depth coefficients of wet leaves and Manning entries of wet
+    finest cells, and the FP32 gradients track the FP64 ones (correlation
+    >= 0.999)."""
+    import torch
+    import paper_2107_02750_gb300 as M
+    p = S.valley(n=1024, L=10)
+    sol = M.solver_from_problem(p, precision=M.F64)
+    sol.run_to_time(600.0)
+    t0 = sol.get_time()[0]
+    lev, ii, jj, co = sol.read_active()
+    del sol
+    K = 10
+    out = {}
+    for precision in (M.F64, M.F32):
+        adj = context(p, lev, ii, jj, K, precision=precision)
+        dev = adj.device
+        U0 = torch.tensor(np.ascontiguousarray(co.T), dtype=adj.dtype, device=dev)
+        z = adj.project(p.z_vert)
+        n = torch.tensor(p.n_cell(), dtype=adj.dtype, device=dev)
+        kt = torch.tensor(p.inflow_t, dtype=torch.float64, device=dev)
+        kQ = torch.tensor(p.inflow_Q, dtype=torch.float64, device=dev)
+        if precision == M.F64:
+            _, d = adj.forward(U0, z, n, kt, kQ, t0, K)
+        seed = torch.zeros((9, len(lev)), dtype=adj.dtype, device=dev)
+        seed[0] = torch.randn(len(lev), generator=torch.Generator().manual_seed(4)).to(seed)
+        out[precision] = (adj, U0, z, n, kt, kQ, seed, adj.backward(U0, z, n, kt, kQ, t0, d, seed))
+        del adj
+    adj, U0, z, n, kt, kQ, seed, (gU0, gz, gn, gQ) = out[M.F64]
+
+    def J(U0_=U0, n_=n):
+        UK, _ = adj.forward(U0_, z, n_, kt, kQ, t0, K, dts=d)
+        return float((UK * seed).sum())
+
+    def best(ad, arr, idx, scale, which):
+        fs = []
+        for rel in (1e-6, 1e-7, 1e-8):
+            a, b = arr.clone(), arr.clone()
+            a[idx] += rel * scale
+            b[idx] -= rel * scale
+            fs.append((J(**{which: a}) - J(**{which: b})) / (2.0 * rel * scale))
+        return min(fs, key=lambda f: abs(f - ad))
+
+    rng = np.random.default_rng(31)
+    gh, gnn = gU0.cpu().numpy()[0], gn.cpu().numpy()
+    h0 = co[:, 0]
+    checks = []
+    cand = np.flatnonzero((np.abs(gh) > 1e-2 * np.abs(gh).max()) & (h0 > 0.05))
+    for q in rng.choice(cand, 3, replace=False):
+        ad = float(gh[q])
+        checks.append(("U0", ad, best(ad, U0, (0, int(q)), 1.0, "U0_")))
+    # Manning n: finest cells under wet finest-level leaves
+    fine = np.flatnonzero((lev == p.L) & (h0 > 0.05))
+    cells = [(int(jj[q]), int(ii[q])) for q in fine]
+    gcell = np.array([gnn[j, i] for j, i in cells])
+    big = np.flatnonzero(np.abs(gcell) > 1e-2 * np.abs(gnn).max())
+    for c in rng.choice(big, 2, replace=False):
+        j, i = cells[int(c)]
+        ad = float(gnn[j, i])
+        checks.append(("n", ad, best(ad, n, (j, i), float(n[j, i]), "n_")))
+    for what, ad, f in checks:
+        assert abs(ad - f) <= 1e-4 * abs(ad), (what, ad, f)
+    g32 = out[M.F32][-1]
+    for a, b, what in zip(g32[:3], (gU0, gz, gn), ("U0", "z", "n")):
+        x, y = a.double().cpu().numpy().ravel(), b.cpu().numpy().ravel()
+        assert np.corrcoef(x, y)[0, 1] >= 0.999, what
