@@ -35,6 +35,7 @@
 // keeps time, time steps, the hydrograph and its gradient in FP64 (a few
 // operations per boundary cell) and everything else in FP32, so that the
 // per-cell work runs on the FP32 pipes.
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -565,10 +566,8 @@ __device__ __forceinline__ void prolong3_t(const T gc[3], int c, T gp[3]) {
 
 // refined nodes of this level: the encoding of their children's views
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_view_encode(Par<T> P, T *V, T *Vz) {
-  long long k;
-  int i, j;
-  if (!cell_of(P, k, i, j) || P.kind[k] != K_SIG) return;
+__device__ __forceinline__ void view_encode_node(const Par<T> &P, T *V, T *Vz, long long k, int i, int j) {
+  if (P.kind[k] != K_SIG) return;
   const long long n = P.ns;
 #pragma unroll 1
   for (int v = 0; v < 4; v++) {
@@ -586,13 +585,18 @@ __global__ void __launch_bounds__(TPB) k_view_encode(Par<T> P, T *V, T *Vz) {
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_view_encode(Par<T> P, T *V, T *Vz) {
+  long long k;
+  int i, j;
+  if (cell_of(P, k, i, j)) view_encode_node(P, V, Vz, k, i, j);
+}
+
 // nodes of this level below a coarser leaf: the prolongation of their
 // parent's view
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_view_prolong(Par<T> P, T *V, T *Vz) {
-  long long k;
-  int i, j;
-  if (!cell_of(P, k, i, j) || P.kind[k] != K_BELOW) return;
+__device__ __forceinline__ void view_prolong_node(const Par<T> &P, T *V, T *Vz, long long k, int i, int j) {
+  if (P.kind[k] != K_BELOW) return;
   const long long n = P.ns;
   const long long kp = -P.dp + (long long)(j >> 1) * (P.nx >> 1) + (i >> 1);
   const int c = (i & 1) + 2 * (j & 1);
@@ -606,6 +610,13 @@ __global__ void __launch_bounds__(TPB) k_view_prolong(Par<T> P, T *V, T *Vz) {
 #pragma unroll
     for (int m = 0; m < 3; m++) A[m * n + k] = sc[m];
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_view_prolong(Par<T> P, T *V, T *Vz) {
+  long long k;
+  int i, j;
+  if (cell_of(P, k, i, j)) view_prolong_node(P, V, Vz, k, i, j);
 }
 
 // One RK2 stage (Eq. 4a for stage 1, Eq. 4b for stage 2) on a tile of
@@ -1626,10 +1637,8 @@ __global__ void __launch_bounds__(TPB) k_rev_view_gather(const Levels<T> LV, con
 // level) takes the cotangents of its children that are below it (the next
 // level); run from the finest level up
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_rev_prolong(Par<T> P, T *gV) {
-  long long k;
-  int i, j;
-  if (!cell_of(P, k, i, j) || P.kind[k] == K_SIG) return;
+__device__ __forceinline__ void rev_prolong_node(const Par<T> &P, T *gV, long long k, int i, int j) {
+  if (P.kind[k] == K_SIG) return;
   const long long n = P.ns;
   T acc[12];
 #pragma unroll
@@ -1653,14 +1662,18 @@ __global__ void __launch_bounds__(TPB) k_rev_prolong(Par<T> P, T *gV) {
   for (int m = 0; m < 12; m++) gV[m * n + k] = acc[m];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_rev_prolong(Par<T> P, T *gV) {
+  long long k;
+  int i, j;
+  if (cell_of(P, k, i, j)) rev_prolong_node(P, gV, k, i, j);
+}
+
 // transpose of the encoding: a child of a refined node (this level) takes
 // its share of the parent's cotangents (the previous level); run from the
 // coarsest level down
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_rev_encode(Par<T> P, T *gV) {
-  long long k;
-  int i, j;
-  if (!cell_of(P, k, i, j)) return;
+__device__ __forceinline__ void rev_encode_node(const Par<T> &P, T *gV, long long k, int i, int j) {
   const long long kp = -P.dp + (long long)(j >> 1) * (P.nx >> 1) + (i >> 1);
   if (P.kind[kp] != K_SIG) return;
   const long long n = P.ns;
@@ -1676,6 +1689,39 @@ __global__ void __launch_bounds__(TPB) k_rev_encode(Par<T> P, T *gV) {
     encode3_t(gp, c, gc);
 #pragma unroll
     for (int m = 0; m < 3; m++) gV[(3 * v + m) * n + k] = gc[m];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_rev_encode(Par<T> P, T *gV) {
+  long long k;
+  int i, j;
+  if (cell_of(P, k, i, j)) rev_encode_node(P, gV, k, i, j);
+}
+
+// The view passes (and their transposes) of the coarse levels, one level
+// after the other in one block: levels from l0 to l1 (step +1 or -1), each
+// finished before the next starts.  A and B: the flow and bed view planes
+// of the forward passes, or A the view cotangents of the reverse ones.
+constexpr int VP_ENCODE = 0, VP_PROLONG = 1, VP_REV_PROLONG = 2, VP_REV_ENCODE = 3;
+constexpr int CTPB = 512;
+template <typename T, int PASS>
+__global__ void __launch_bounds__(CTPB) k_views_coarse(const Levels<T> LV, T *A, T *B, int l0, int l1) {
+  __shared__ Par<T> sP;
+  const int step = l1 >= l0 ? 1 : -1;
+  for (int l = l0;; l += step) {
+    if (threadIdx.x == 0) sP = LV.P[l];
+    __syncthreads();
+    const Par<T> &P = sP;
+    for (long long k = threadIdx.x; k < P.n; k += CTPB) {
+      const int j = (int)(k / P.nx), i = (int)(k - (long long)j * P.nx);
+      if (PASS == VP_ENCODE) view_encode_node(P, A + P.off, B + P.off, k, i, j);
+      else if (PASS == VP_PROLONG) view_prolong_node(P, A + P.off, B + P.off, k, i, j);
+      else if (PASS == VP_REV_PROLONG) rev_prolong_node(P, A + P.off, k, i, j);
+      else rev_encode_node(P, A + P.off, k, i, j);
+    }
+    __syncthreads();
+    if (l == l1) break;
   }
 }
 
@@ -2130,13 +2176,24 @@ StageArrays<T> stage_arrays(const mwdg_adj *a, int s) {
 // the views of the flux-view planes (F, Zf) of a frozen grid: encodings of
 // refined nodes from the finest level up, then prolongations from the
 // coarsest down
+// the coarse levels of a frozen grid: those of at most COARSE_NODES nodes,
+// whose view passes run in one block (-1: none)
+constexpr long long COARSE_NODES = 1024;
+int coarse_level(const mwdg_adj *a) {
+  int lc = -1;
+  while (lc + 1 < a->levels && ((long long)a->gM << (lc + 1)) * ((long long)a->gN << (lc + 1)) <= COARSE_NODES) lc++;
+  return lc;
+}
+
 template <typename T>
-void launch_views(const mwdg_adj *a, const Par<T> *PL, T *F, T *Zf, cudaStream_t st) {
+void launch_views(const mwdg_adj *a, const Levels<T> &LV, const Par<T> *PL, T *F, T *Zf, cudaStream_t st) {
   if (!a->levels) return;
-  const int L = a->levels - 1;
-  for (int l = L - 1; l >= 0; l--)
+  const int L = a->levels - 1, lc = coarse_level(a);
+  for (int l = L - 1; l > lc; l--)
     k_view_encode<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], F + loff(a, l), Zf + loff(a, l));
-  for (int l = 1; l <= L; l++)
+  if (std::min(lc, L - 1) >= 0) k_views_coarse<T, VP_ENCODE><<<1, CTPB, 0, st>>>(LV, F, Zf, std::min(lc, L - 1), 0);
+  if (std::min(lc, L) >= 1) k_views_coarse<T, VP_PROLONG><<<1, CTPB, 0, st>>>(LV, F, Zf, 1, std::min(lc, L));
+  for (int l = std::max(lc + 1, 1); l <= L; l++)
     k_view_prolong<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], F + loff(a, l), Zf + loff(a, l));
 }
 
@@ -2163,7 +2220,7 @@ void launch_limit(const mwdg_adj *a, const Tabs<T> &TB, const T *X, const T *z, 
                   cudaStream_t st) {
   if (a->levels) k_limit<T, true><<<TB.nc, TPB, 0, st>>>(TB.cells, X, z, Wst, F, Zf);
   else k_limit<T, false><<<TB.nc, TPB, 0, st>>>(TB.cells, X, z, Wst, F, Zf);
-  launch_views<T>(a, TB.PL.data(), F, Zf, st);
+  launch_views<T>(a, TB.cells, TB.PL.data(), F, Zf, st);
 }
 
 // friction, limit, stage 1 and limit of step s: the two stage inputs (Un, Ui)
@@ -2372,8 +2429,14 @@ mwdg_status backward_t(mwdg_adj *a, const T *U0, const T *z, const T *nman, int3
           // the prolongations (finest level up) and encodings (coarsest
           // down) transposed onto the leaves
           k_rev_view_gather<T><<<TB.nc, TPB, 0, st>>>(TB.cells, limx, limy, gV);
-          for (int l = L - 1; l >= 0; l--) k_rev_prolong<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gV + loff(a, l));
-          for (int l = 1; l <= L; l++) k_rev_encode<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gV + loff(a, l));
+          const int lc = coarse_level(a);
+          for (int l = L - 1; l > lc; l--) k_rev_prolong<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gV + loff(a, l));
+          if (std::min(lc, L - 1) >= 0)
+            k_views_coarse<T, VP_REV_PROLONG><<<1, CTPB, 0, st>>>(TB.cells, gV, nullptr, std::min(lc, L - 1), 0);
+          if (std::min(lc, L) >= 1)
+            k_views_coarse<T, VP_REV_ENCODE><<<1, CTPB, 0, st>>>(TB.cells, gV, nullptr, 1, std::min(lc, L));
+          for (int l = std::max(lc + 1, 1); l <= L; l++)
+            k_rev_encode<T><<<blocks(PL[l].n), TPB, 0, st>>>(PL[l], gV + loff(a, l));
           k_rev_limit<T, true><<<TB.nc, TPB, 0, st>>>(TB.cells, stage, dts, k, X, z, lY, Y, clip, lW1, nullptr,
                                                       nullptr, gV, lXo, lnb, gzl);
         } else {
