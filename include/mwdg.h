@@ -299,7 +299,10 @@ MWDG_API mwdg_status mwdg_fma_rate(int32_t precision, void *cuda_stream, double 
  * levels run by one block (coarse_nodes >= 1: levels with at most that many
  * nodes).  Neither changes the arithmetic of a leaf or node; both change
  * only how the work is spread.  Either argument <= 0 keeps the current
- * value.  mwdg_get_launch_shape reads them (any pointer may be NULL). */
+ * value.  By default grid_leaves is min(nodes / 256, 1216), and for a
+ * static grid, once mwdg_load_initial has built it, about one block per 256
+ * leaves (152 to 4864), unless set here before.  mwdg_get_launch_shape
+ * reads them (any pointer may be NULL). */
 MWDG_API mwdg_status mwdg_set_launch_shape(mwdg_ctx *ctx, int32_t grid_leaves, int64_t coarse_nodes);
 MWDG_API mwdg_status mwdg_get_launch_shape(mwdg_ctx *ctx, int32_t *grid_leaves, int64_t *coarse_nodes);
 

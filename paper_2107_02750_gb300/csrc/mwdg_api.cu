@@ -45,6 +45,8 @@ struct mwdg_ctx {
   double *d_gauge_out = nullptr;
   int gauge_cap = 0;
   int grid_leaves = 0;
+  int part_cap = 0;          // entries of the volume's per-block partial sums
+  bool shape_set = false;    // the caller chose grid_leaves
   bool dem = false, initial = false, stepped = false, failed = false, encoded = false;
   bool vmax_fresh = false;   // max |v0| on the device is that of the current leaves
   // one captured step (CUDA graph), replayed while the parameters it bakes in
@@ -167,6 +169,7 @@ mwdg_status allocate_state(mwdg_ctx *c) {
     return s;
   const size_t nb = (P + 2048 - 1) / 2048 + 1;
   if ((s = alloc(c, &p.blk, nb)) || (s = alloc(c, &p.part, (size_t)c->grid_leaves))) return s;
+  c->part_cap = c->grid_leaves;
   CK(cudaMemsetAsync(p.U, 0, 9 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.Ui, 0, 9 * P * sizeof(T), c->st));
   CK(cudaMemsetAsync(p.Wn, 0, 9 * P * sizeof(T), c->st));
@@ -596,6 +599,14 @@ static mwdg_status load_initial(mwdg_ctx *c, const double *h_vert, const double 
   CK(cudaMemcpyAsync(c->ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->st));
   if ((s = prime(c))) return s;
   CK(cudaStreamSynchronize(c->st));
+  if (g.mode == MWDG_STATIC && !c->shape_set) {
+    // a static grid's leaves are fixed: about one leaf per thread of the
+    // leaf kernels (152 to 4864 blocks), unless the caller chose a shape
+    int nl = 0;
+    CK(cudaMemcpy(&nl, g.prec == MWDG_F64 ? c->pd.nleaf : c->pf.nleaf, sizeof nl, cudaMemcpyDeviceToHost));
+    c->grid_leaves = (int)std::min<long long>(std::max<long long>((nl + 255) / 256, 152), 152 * 32);
+    drop_graph(c);
+  }
   c->initial = true;
   c->stepped = false;
   c->encoded = false;
@@ -920,7 +931,9 @@ mwdg_status mwdg_get_volume(mwdg_ctx *c, double *V, double *V_in, double *V_out,
   const Geo &g = c->g;
   c->launches += dispatch(c, [&](auto &p, auto *) {
     using T = std::remove_pointer_t<decltype(p.U)>;
-    return Launch<T>::volume(g, p, c->grid_leaves, c->st);
+    // as many blocks as the partial sums hold (the kernel strides over the
+    // leaves, so any count covers them; the launch shape may have grown)
+    return Launch<T>::volume(g, p, std::min(c->grid_leaves, c->part_cap), c->st);
   });
   CHECK_LAUNCH();
   Ctl h;
@@ -1097,7 +1110,10 @@ const char *mwdg_last_error(const mwdg_ctx *c) { return c ? c->err.c_str() : "no
 mwdg_status mwdg_set_launch_shape(mwdg_ctx *c, int32_t grid_leaves, int64_t coarse_nodes) {
   LIVE(c);
   if (grid_leaves > 65535) return fail(c, MWDG_ERR_ARG, "grid_leaves above 65535");
-  if (grid_leaves > 0) c->grid_leaves = grid_leaves;
+  if (grid_leaves > 0) {
+    c->grid_leaves = grid_leaves;
+    c->shape_set = true;
+  }
   if (coarse_nodes > 0) c->g.coarse_nodes = coarse_nodes;
   drop_graph(c);
   return MWDG_OK;

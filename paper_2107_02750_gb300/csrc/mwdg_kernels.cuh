@@ -2484,11 +2484,13 @@ __device__ __forceinline__ void leaf_update(const Geo &g, const Ptrs<T> &p, cons
     for (int dir = 0; dir < 2; dir++) {
       FaceOut<T> fa = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir, tf, in[2 * dir], nb[2 * dir], dt,
                                    [&](T av[3]) { nbr_avg_code(g, p, l, i, j, 2 * dir, code[2 * dir], av); });
-      if (REFLUX) reflux_face(g, p, l, i, j, 2 * dir, tf, dt, fa.F0, fa.F1, fa.F2);
+      // (only across a refined neighbour: its code says so without a load)
+      if (REFLUX && nb_type(code[2 * dir]) == NB_REFINED) reflux_face(g, p, l, i, j, 2 * dir, tf, dt, fa.F0, fa.F1, fa.F2);
       bsum += fa.bout;
       FaceOut<T> fb = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir + 1, tf, in[2 * dir + 1], nb[2 * dir + 1], dt,
                                    [&](T av[3]) { nbr_avg_code(g, p, l, i, j, 2 * dir + 1, code[2 * dir + 1], av); });
-      if (REFLUX) reflux_face(g, p, l, i, j, 2 * dir + 1, tf, dt, fb.F0, fb.F1, fb.F2);
+      if (REFLUX && nb_type(code[2 * dir + 1]) == NB_REFINED)
+        reflux_face(g, p, l, i, j, 2 * dir + 1, tf, dt, fb.F0, fb.F1, fb.F2);
       bsum += fb.bout;
       dir_terms(dir == 0, fa, fb, gg, dir == 0 ? dx_ : dy_);
     }

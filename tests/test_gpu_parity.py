@@ -590,3 +590,23 @@ def test_adaptive_coarse_level_schedules_f64(coarse_nodes):
         assert abs(dg - do) <= 1e-9 * do, (k, dg, do)
         if (k + 1) % 20 == 0:
             assert_same_leaves(g, o, what=f"coarse_nodes {coarse_nodes}, step {k + 1}")
+
+
+def test_grown_launch_shape_keeps_results_and_volume():
+    """A launch shape larger than the one the context was created with (the
+    volume's per-block partial sums keep their size; the volume launch uses
+    no more blocks than they hold): steps and the FP64 volume equal those of
+    the default shape."""
+    import paper_2107_02750_gb300 as M
+    p = S.valley(n=128, L=7, mode=S.ADAPTIVE, eps=1e-2, peak_Q=200.0, t_peak=100.0)
+    a, b = gpu_sim(p), gpu_sim(p)
+    b.set_launch_shape(grid_leaves=8192)
+    assert b.launch_shape()[0] == 8192 and a.launch_shape()[0] < 8192
+    for s in (a, b):
+        s.run_steps(30)
+    la, _, _, ca = a.read_active()
+    lb, _, _, cb = b.read_active()
+    np.testing.assert_array_equal(la, lb)
+    np.testing.assert_array_equal(ca, cb)
+    va, vb = a.get_volume()["volume"], b.get_volume()["volume"]
+    assert abs(va - vb) <= 1e-12 * va
