@@ -1873,85 +1873,11 @@ __device__ __forceinline__ T first_face(T c0, T c1, T c2, T ze0, int f) {
   return Form<T>::eta ? face_value(c0 + ze0, c1, c2, f) : face_value(c0, c1, c2, f);
 }
 
-// neighbour node k across face f of leaf (l, i, j) and its kind; false on
-// the domain boundary
-template <typename T>
-__device__ __forceinline__ bool nbr_locate(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f,
-                                           long long &k, uint8_t &kd) {
-  const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
-  if (a < 0 || b < 0 || a >= g.nxl[l] || b >= g.nyl[l]) return false;
-  k = nid(g, l, a, b);
-  kd = p.kind[k];
-  return true;
-}
-
-// limit (first variable, qx, qy, z) of the same-level view of neighbour k
-// (kind kd) across face f of leaf (l, i, j), then the view's averages (depth,
-// qx, qy): out[4..6]
-template <typename T>
-__device__ void nbr_view(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, long long k, uint8_t kd,
-                         T out[7]) {
-  const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
-  const int fo = f ^ 1;
-  if (kd == K_SIG && g.mode == MWDG_STATIC) {
-    // Sect. 2.2.1: the coarse side interpolates the limit from the two finer
-    // interface centres (graded grid: both are level l+1 leaves)
-    int c1, c2;
-    if (f == 0) { c1 = 0; c2 = 2; }
-    else if (f == 1) { c1 = 1; c2 = 3; }
-    else if (f == 2) { c1 = 0; c2 = 1; }
-    else { c1 = 2; c2 = 3; }
-    long long k1 = nid(g, l + 1, 2 * a + (c1 & 1), 2 * b + (c1 >> 1));
-    long long k2 = nid(g, l + 1, 2 * a + (c2 & 1), 2 * b + (c2 >> 1));
-    T r1[12], r2[12];
-    load_rec(p.FZ, k1, r1);
-    load_rec(p.FZ, k2, r2);
-    out[0] = T(0.5) * (first_face(r1[0], r1[1], r1[2], r1[9], fo) + first_face(r2[0], r2[1], r2[2], r2[9], fo));
-    for (int v = 1; v < 3; v++)
-      out[v] = T(0.5) * (face_value(r1[3 * v], r1[3 * v + 1], r1[3 * v + 2], fo) +
-                         face_value(r2[3 * v], r2[3 * v + 1], r2[3 * v + 2], fo));
-    out[3] = T(0.5) * (face_value(r1[9], r1[10], r1[11], fo) + face_value(r2[9], r2[10], r2[11], fo));
-    for (int v = 0; v < 3; v++) out[4 + v] = T(0.5) * (r1[3 * v] + r2[3 * v]);
-    return;
-  }
-  if (kd == K_BELOW) {
-    // prolongation of the covering coarser leaf's plane down to this node
-    int path[MWDG_LMAX + 1];
-    int d = 0, aa = a, bb = b, la = l;
-    long long ka = k;
-    while (la > 0 && p.kind[ka] == K_BELOW) {
-      path[d++] = (aa & 1) + 2 * (bb & 1);
-      aa >>= 1;
-      bb >>= 1;
-      la--;
-      ka = nid(g, la, aa, bb);
-    }
-    // beds (v = 3) first, then the flow planes in depth form
-    T ra[12];
-    load_rec(p.FZ, ka, ra);
-    for (int v = 3; v >= 0; v--) {
-      T sv[3] = {ra[3 * v], ra[3 * v + 1], ra[3 * v + 2]};
-      if (v == 0) slopes_to_h(sv[1], sv[2], ra[10], ra[11]);
-      for (int q = d - 1; q >= 0; q--) {
-        T o[3];
-        prolong3(sv[0], sv[1], sv[2], path[q], o);
-        sv[0] = o[0]; sv[1] = o[1]; sv[2] = o[2];
-      }
-      out[v] = face_value(sv[0], sv[1], sv[2], fo);
-      if (v < 3) out[4 + v] = sv[0];
-    }
-    if (Form<T>::eta) out[0] = out[0] + out[3];  // depth + bed = free surface
-    return;
-  }
-  T r[12];
-  load_rec(p.FZ, k, r);
-  out[0] = first_face(r[0], r[1], r[2], r[9], fo);
-  for (int v = 1; v < 3; v++) out[v] = face_value(r[3 * v], r[3 * v + 1], r[3 * v + 2], fo);
-  out[3] = face_value(r[9], r[10], r[11], fo);
-  for (int v = 0; v < 3; v++) out[4 + v] = r[3 * v];
-}
-
-// the same from the leaf's neighbour code (no kind reads, no walk)
+// limit (first variable, qx, qy, z) of the same-level view of the neighbour
+// across face f of leaf (l, i, j), from the leaf's neighbour code: the
+// leaf's or encoded node's record, the prolongation of the covering
+// coarser leaf's record down to the neighbour node, or on a static grid's
+// coarse side the mean of the two finer leaves' interface limits
 template <typename T>
 __device__ void nbr_view_code(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, long long code,
                               T out[4]) {
@@ -2039,17 +1965,6 @@ __device__ __forceinline__ void nbr_avg_code(const Geo &g, const Ptrs<T> &p, int
     return;
   }
   for (int v = 0; v < 3; v++) avg[v] = p.FZ[12 * k + 3 * v];
-}
-
-// both: the neighbour's view limit and averages across face f; false on the
-// boundary
-template <typename T>
-__device__ __forceinline__ bool nbr_limit(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, T out[7]) {
-  long long k;
-  uint8_t kd;
-  if (!nbr_locate(g, p, l, i, j, f, k, kd)) return false;
-  nbr_view(g, p, l, i, j, f, k, kd, out);
-  return true;
 }
 
 // Interface f of a leaf: its own limit, the neighbour's (same-level view or
@@ -2140,46 +2055,64 @@ __device__ __forceinline__ FaceOut<T> face_flux_nb(const Geo &g, const Ptrs<T> &
   return o;
 }
 
-template <typename T>
-__device__ __forceinline__ FaceOut<T> face_flux(const Geo &g, const Ptrs<T> &p, int l, int i, int j,
-                                                const T (&w)[9], const T (&zc)[3], int f, ForceTime tf, T dt) {
-  T nb[7];
-  const bool inside = nbr_limit(g, p, l, i, j, f, nb);
-  T lim[4] = {nb[0], nb[1], nb[2], nb[3]};
-  return face_flux_nb(g, p, l, i, j, w, zc, f, tf, inside, lim, dt, [&](T av[3]) {
-    av[0] = nb[4]; av[1] = nb[5]; av[2] = nb[6];
-  });
-}
-
 // Reflux rule on static grids (MWDG_IFACE_REFLUX): on the coarse side of a
 // face whose neighbour is refined, the flux is the mean of the two fine
-// leaves' own fluxes through their halves of the face, computed by the same
-// code as theirs, so the mass leaving one side enters the other.
+// leaves' own fluxes through their halves of the face, computed with the
+// same operands and operations as theirs, so the mass leaving one side
+// enters the other.  The grid is graded, so both fine leaves lie one level
+// below this leaf (node k) and see it through a one-level prolongation of
+// its flux-view record; the three records are read together.
 template <typename T>
-__device__ __noinline__ bool reflux_face(const Geo &g, const Ptrs<T> &p, int l, int i, int j, int f, ForceTime tf,
-                                         T dt, T &F0, T &F1, T &F2) {
+__device__ __forceinline__ void reflux_face(const Geo &g, const Ptrs<T> &p, int l, int i, int j, long long k, int f,
+                                         ForceTime tf, T dt, T &F0, T &F1, T &F2) {
   const int a = i + (f == 0) - (f == 1), b = j + (f == 2) - (f == 3);
-  if (a < 0 || b < 0 || a >= g.nxl[l] || b >= g.nyl[l] || p.kind[nid(g, l, a, b)] != K_SIG) return false;
   int c1, c2;
   if (f == 0) { c1 = 0; c2 = 2; }
   else if (f == 1) { c1 = 1; c2 = 3; }
   else if (f == 2) { c1 = 0; c2 = 1; }
   else { c1 = 2; c2 = 3; }
-  T G[2][3];
+  const int fo = f ^ 1;  // the fine leaves' face towards this leaf
+  int ic[2], jc[2];
+  T rc[12], r[2][12];
+#pragma unroll
   for (int q = 0; q < 2; q++) {
     const int cq = q ? c2 : c1;
-    const int ic = 2 * a + (cq & 1), jc = 2 * b + (cq >> 1);
-    T r[12], w[9], zc[3];
-    load_rec(p.FZ, nid(g, l + 1, ic, jc), r);
-    for (int m = 0; m < 9; m++) w[m] = r[m];
-    for (int m = 0; m < 3; m++) zc[m] = r[9 + m];
-    const FaceOut<T> o = face_flux(g, p, l + 1, ic, jc, w, zc, f ^ 1, tf, dt);
+    ic[q] = 2 * a + (cq & 1);
+    jc[q] = 2 * b + (cq >> 1);
+    load_rec(p.FZ, nid(g, l + 1, ic[q], jc[q]), r[q]);
+  }
+  load_rec(p.FZ, k, rc);
+  T G[2][3];
+#pragma unroll
+  for (int q = 0; q < 2; q++) {
+    // the node across the fine leaf's face, at its level, lies under this
+    // leaf: its child index in the prolongation
+    const int an = ic[q] + (fo == 0) - (fo == 1), bn = jc[q] + (fo == 2) - (fo == 3);
+    const int path = (an & 1) + 2 * (bn & 1);
+    T nb[4], av[3];
+    // beds (v = 3) first, then the flow planes in depth form
+    for (int v = 3; v >= 0; v--) {
+      T sv[3] = {rc[3 * v], rc[3 * v + 1], rc[3 * v + 2]};
+      if (v == 0) slopes_to_h(sv[1], sv[2], rc[10], rc[11]);
+      T o[3];
+      prolong3(sv[0], sv[1], sv[2], path, o);
+      nb[v] = face_value(o[0], o[1], o[2], f);
+      if (v < 3) av[v] = o[0];
+    }
+    if (Form<T>::eta) nb[0] = nb[0] + nb[3];  // depth + bed = free surface
+    T w[9], zc[3];
+#pragma unroll
+    for (int m = 0; m < 9; m++) w[m] = r[q][m];
+#pragma unroll
+    for (int m = 0; m < 3; m++) zc[m] = r[q][9 + m];
+    const FaceOut<T> o = face_flux_nb(g, p, l + 1, ic[q], jc[q], w, zc, fo, tf, true, nb, dt, [&](T x[3]) {
+      x[0] = av[0]; x[1] = av[1]; x[2] = av[2];
+    });
     G[q][0] = o.F0; G[q][1] = o.F1; G[q][2] = o.F2;
   }
   F0 = T(0.5) * (G[0][0] + G[1][0]);
   F1 = T(0.5) * (G[0][1] + G[1][1]);
   F2 = T(0.5) * (G[0][2] + G[1][2]);
-  return true;
 }
 
 // The operator and update of variable v (0 h, 1 qx, 2 qy) of one leaf:
@@ -2429,6 +2362,10 @@ __device__ __forceinline__ void update_epilogue(const Geo &g, const Ptrs<T> &p, 
 // resident blocks per SM asked of the update (FP32: at most 64 registers a
 // thread, four blocks; FP64 keeps its registers)
 template <typename T> struct UpdOcc { static constexpr int blocks = std::is_same<T, float>::value ? 4 : 1; };
+// with the reflux rule inlined, one block fewer (FP32: 80 registers a thread)
+template <typename T, bool REFLUX> struct UpdOccR {
+  static constexpr int blocks = (REFLUX && UpdOcc<T>::blocks > 1) ? UpdOcc<T>::blocks - 1 : UpdOcc<T>::blocks;
+};
 
 // REFLUX: compiled with the reflux interface rule (static grids only).
 // VIEWS (adaptive grids): with vtail >= 0 the first block first encodes the
@@ -2485,12 +2422,12 @@ __device__ __forceinline__ void leaf_update(const Geo &g, const Ptrs<T> &p, cons
       FaceOut<T> fa = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir, tf, in[2 * dir], nb[2 * dir], dt,
                                    [&](T av[3]) { nbr_avg_code(g, p, l, i, j, 2 * dir, code[2 * dir], av); });
       // (only across a refined neighbour: its code says so without a load)
-      if (REFLUX && nb_type(code[2 * dir]) == NB_REFINED) reflux_face(g, p, l, i, j, 2 * dir, tf, dt, fa.F0, fa.F1, fa.F2);
+      if (REFLUX && nb_type(code[2 * dir]) == NB_REFINED) reflux_face(g, p, l, i, j, k, 2 * dir, tf, dt, fa.F0, fa.F1, fa.F2);
       bsum += fa.bout;
       FaceOut<T> fb = face_flux_nb(g, p, l, i, j, w, zc, 2 * dir + 1, tf, in[2 * dir + 1], nb[2 * dir + 1], dt,
                                    [&](T av[3]) { nbr_avg_code(g, p, l, i, j, 2 * dir + 1, code[2 * dir + 1], av); });
       if (REFLUX && nb_type(code[2 * dir + 1]) == NB_REFINED)
-        reflux_face(g, p, l, i, j, 2 * dir + 1, tf, dt, fb.F0, fb.F1, fb.F2);
+        reflux_face(g, p, l, i, j, k, 2 * dir + 1, tf, dt, fb.F0, fb.F1, fb.F2);
       bsum += fb.bout;
       dir_terms(dir == 0, fa, fb, gg, dir == 0 ? dx_ : dy_);
     }
@@ -2510,7 +2447,7 @@ __device__ __forceinline__ void leaf_update(const Geo &g, const Ptrs<T> &p, cons
 }
 
 template <typename T, int STAGE, bool REFLUX, bool VIEWS, bool UNI>
-__global__ void __launch_bounds__(TPB, UpdOcc<T>::blocks) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out,
+__global__ void __launch_bounds__(TPB, UpdOccR<T, REFLUX>::blocks) k_leaf_update(Geo g, Ptrs<T> p, const T *Wst, const T *Wcomb, T *Out,
                                                                       int vtail) {
   leaf_update<T, STAGE, REFLUX, VIEWS, UNI>(g, p, Wst, Wcomb, Out, vtail, blockIdx.x, gridDim.x);
 }
