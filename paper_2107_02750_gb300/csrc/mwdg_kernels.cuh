@@ -803,10 +803,14 @@ constexpr int MT_LEVELS = 5;   // levels per chunk: 16, 8, 4, 2, 1 nodes per sid
 static_assert(MT * MT == TPB, "one thread per node of a tile's finest level");
 
 // first shared-memory slot of tile level s (levels stacked finest first)
+// (the geometric sum MT^2 + (MT/2)^2 + ... of the s finer levels, in closed
+// form: no recursion at run time)
 __host__ __device__ constexpr int tbase(int s) {
-  return s == 0 ? 0 : tbase(s - 1) + (MT >> (s - 1)) * (MT >> (s - 1));
+  return (4 * MT * MT - ((4 * MT * MT) >> (2 * s))) / 3;
 }
 constexpr int MT_NODES = tbase(MT_LEVELS);  // 341 nodes in a full tile
+static_assert(tbase(1) == 256 && tbase(2) == 320 && tbase(3) == 336 && tbase(4) == 340 && MT_NODES == 341,
+              "tile levels of 16, 8, 4, 2 and 1 nodes a side");
 static_assert(MT_NODES <= 2 * TPB, "two staged slots per thread");
 constexpr uint8_t K_OUT = 0xff;             // slot outside its level
 
