@@ -429,6 +429,7 @@ def uniform_leg(p, stream, flush, K, W, spinup):
     roofline of each stage kernel and of the whole step on the step's
     algorithmic bytes (stage 1: 13 values read, 9 written; stage 2: 22 read,
     9 written; 212 B a cell and step in all)"""
+    import torch
     import paper_2107_02750_gb300 as M
     from dataclasses import replace
     from paper_2107_02750_gb300 import synth as S
@@ -447,10 +448,25 @@ def uniform_leg(p, stream, flush, K, W, spinup):
             stages[name] = {"ms_per_launch": t * 1e3, "algorithmic_bytes_per_cell": vals * 4,
                             "achieved": vals * 4 * cells / t / 1e9, "frac": vals * 4 * cells / t / 1e9 / peak}
     wb = DG2_STEP_VALUES * 4
+    # the instruction-issue ceiling (four warp schedulers per SM, one warp
+    # instruction each per cycle, at the maximum SM clock) with the stage
+    # kernels' instruction counts from ncu: the bound these kernels meet first
+    ipeak = torch.cuda.get_device_properties(0).multi_processor_count * 4 * ISSUE_CLOCK_MHZ * 1e6 / 1e9
+    for name, st in stages.items():
+        ipc = UNI_WARP_INSTR_PER_CELL.get(name)
+        if ipc is not None:
+            a = ipc * cells / (st["ms_per_launch"] * 1e-3) / 1e9
+            st["issue"] = {"warp_instr_per_cell": ipc, "achieved": a, "peak": ipeak, "unit": "G warp instr/s",
+                           "frac": a / ipeak}
+    ipc_step = sum(UNI_WARP_INSTR_PER_CELL.values())
     return {"value": value, "unit": UNIT, "ms_per_step": sum(ms) / len(ms), "cells": cells,
             "roofline": {"bound": "hbm", "peak": peak, "peak_kind": kind, "unit": "GB/s", "stages": stages,
                          "whole_step": {"bytes_per_update": wb, "achieved": wb * value / 1e9,
                                         "frac": wb * value / 1e9 / peak}},
+            "issue_roofline": {"bound": "alu", "unit": "G warp instr/s", "peak": ipeak,
+                               "peak_kind": f"derived: SMs x 4 schedulers x 1 warp instruction/cycle x {ISSUE_CLOCK_MHZ} MHz",
+                               "warp_instr_per_cell_step": ipc_step, "achieved": ipc_step * value / 1e9,
+                               "frac": ipc_step * value / 1e9 / ipeak},
             "what": f"uniform DG2 on the valley's finest grid ({int(cells):,} cells), FP32, fused stage kernels, "
                     "L2 flushed before every timed step"}
 
@@ -876,6 +892,13 @@ def run_adjoint_frozen(args, K):
 ADJ_VALUES_PER_CELL = {"friction": 19, "limit": 33, "update": 34.5, "cfl": 3, "rev_face": 49, "rev_limit": 67,
                        "rev_gather": 32, "rev_friction": 30}
 ADJ_FLAG_BYTES = {"update": 1, "rev_face": 1, "rev_limit": 1}
+# warp instructions executed per cell by the uniform grid's fused stage
+# kernels, counted by ncu at this workload
+# (profiles/issue_rate_valley1024_f32.md), while those kernels are unchanged;
+# the SM clock of the issue ceiling (GB300's maximum, which the benchmark's
+# clock record shows under load)
+UNI_WARP_INSTR_PER_CELL = {"dg2_update_stage1": 28.43, "dg2_update_stage2": 34.09}
+ISSUE_CLOCK_MHZ = 2070
 # FP64 pipe busy (% of active cycles) over the FP64 step's kernels, from ncu
 # (profiles/fp64_pipe_valley512_mwdg2.md), while those kernels are unchanged
 FP64_PIPE_BUSY = {"min": 57.4, "max": 72.0, "stage_update": 72.0, "significance_encode": 62.1}
