@@ -53,6 +53,8 @@ struct mwdg_ctx {
   // are unchanged; not used on the legacy default stream or while profiling
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
+  // the adaptation's fork (a second stream and two events, made on first use)
+  Fork fk{nullptr, nullptr, nullptr};
   int graph_launches = 0;
   int64_t generation = 0;   // bumped whenever the captured step becomes stale
   int static_eta = 0;   // static run with a free-surface initial state
@@ -253,7 +255,7 @@ int launch_step(mwdg_ctx *c, int with_maxabs) {
     using T = std::remove_pointer_t<decltype(p.U)>;
     int n = 0;
     const int adaptive = (g.mode == MWDG_ADAPTIVE);
-    if (adaptive) n += Launch<T>::adapt(g, p, 0, with_maxabs, c->st, mark_cb, c, 1);
+    if (adaptive) n += Launch<T>::adapt(g, p, 0, with_maxabs, c->st, mark_cb, c, 1, c->fk.join ? &c->fk : nullptr);
     n += Launch<T>::step(g, p, c->grid_leaves, c->st, mark_cb, c, adaptive);
     return n;
   });
@@ -452,6 +454,14 @@ mwdg_status mwdg_create(const mwdg_params *p, mwdg_ctx **out) {
     mwdg_destroy(c);
     return s;
   }
+  if (g.mode == MWDG_ADAPTIVE) {  // the adaptation's fork
+    if (cudaStreamCreateWithFlags(&c->fk.aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fk.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fk.join, cudaEventDisableTiming) != cudaSuccess) {
+      mwdg_destroy(c);
+      return MWDG_ERR_CUDA;
+    }
+  }
   Ctl h = fresh_ctl();
   if (cudaMemcpyAsync(c->ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->st) != cudaSuccess) {
     mwdg_destroy(c);
@@ -474,6 +484,12 @@ void mwdg_destroy(mwdg_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
   drop_graph(c);
+  if (c->fk.aux) {
+    cudaStreamSynchronize(c->fk.aux);
+    cudaStreamDestroy(c->fk.aux);
+  }
+  if (c->fk.fork) cudaEventDestroy(c->fk.fork);
+  if (c->fk.join) cudaEventDestroy(c->fk.join);
   for (void *q : c->allocs) cudaFree(q);
   for (auto &m : c->marks) cudaEventDestroy(m.second);
   for (auto ev : c->pool) cudaEventDestroy(ev);

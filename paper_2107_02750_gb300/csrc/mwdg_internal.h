@@ -113,6 +113,14 @@ struct BatchLaunch {
   void *tab;  // device array of bs.n member records (owned by the ensemble)
 };
 
+// a fork of the launch stream: work queued on aux after fork is recorded on
+// the launch stream runs beside what follows there, until the launch stream
+// waits on join
+struct Fork {
+  cudaStream_t aux;
+  cudaEvent_t fork, join;
+};
+
 // Launchers implemented per precision (explicit instantiations in
 // mwdg_f64.cu and mwdg_f32.cu).  All queue work on `st` and return the
 // number of kernels they launched.
@@ -130,9 +138,12 @@ template <typename T> struct Launch {
   static int kinds(const Geo &g, const Ptrs<T> &p, const uint8_t *flag, cudaStream_t st);
   static int all_finest(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
   static int compact(const Geo &g, const Ptrs<T> &p, cudaStream_t st);
-  // begin: the adaptation's last kernel also starts the step that follows
+  // begin: the adaptation's last kernel also starts the step that follows;
+  // fk: a second stream and two events on which the encode's coarsest
+  // levels run beside the regularisation (nullptr: all on st)
   static int adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_maxabs,
-                   cudaStream_t st, void (*mark)(void *, int), void *mark_arg, int begin = 0);
+                   cudaStream_t st, void (*mark)(void *, int), void *mark_arg, int begin = 0,
+                   const Fork *fk = nullptr);
   // begun: the step was started by the adaptation
   static int step(const Geo &g, const Ptrs<T> &p, int grid_leaves, cudaStream_t st,
                   void (*mark)(void *, int), void *mark_arg, int begun = 0);

@@ -3075,7 +3075,7 @@ int for_chunks(const Geo &g, F &&f) {
 
 template <typename T>
 int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_maxabs, cudaStream_t st,
-                     void (*mark)(void *, int), void *mark_arg, int begin) {
+                     void (*mark)(void *, int), void *mark_arg, int begin, const Fork *fk) {
   int n = 0;
   const int grid = (int)std::min<long long>(nblk(g.P), 152 * 8);
   if (with_maxabs) {
@@ -3087,11 +3087,25 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
   // block when every node that reads them (levels up to lc + 1) is its own
   const int lc = coarse_top(g);
   const bool defer = !encode_only && lc >= 0 && lc < g.L - 1 && g.off[lc + 2] <= CTILE;
+  // with the regularisation's coarsest levels deferred, the encode's
+  // coarsest levels (the last chunk's tail) run as one block on the fork,
+  // beside the regularisation's tiles, which read only finer levels; the
+  // decode, whose first block reads both, waits for the join
+  const bool forked = fk && defer;
   // bottom-up encode + significance
   n += for_chunks(g, [&](int ltop, int nlev, int tail, int blocks) {
     MARK(KC_ENCODE);
-    if (g.scheme == MWDG_FV1) k_mra_sig<T, true><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
-    else k_mra_sig<T, false><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
+    const int t = (forked && nlev > 0) ? -1 : tail;
+    if (g.scheme == MWDG_FV1) k_mra_sig<T, true><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, t);
+    else k_mra_sig<T, false><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, t);
+    if (t != tail) {
+      cudaEventRecord(fk->fork, st);
+      cudaStreamWaitEvent(fk->aux, fk->fork, 0);
+      if (g.scheme == MWDG_FV1) k_mra_sig<T, true><<<1, TPB, 0, fk->aux>>>(g, p, ltop, 0, tail);
+      else k_mra_sig<T, false><<<1, TPB, 0, fk->aux>>>(g, p, ltop, 0, tail);
+      cudaEventRecord(fk->join, fk->aux);
+      n++;
+    }
   });
   if (encode_only) return n;
   // prediction + closure
@@ -3100,6 +3114,7 @@ int Launch<T>::adapt(const Geo &g, const Ptrs<T> &p, int encode_only, int with_m
     if (defer) tail = -1;
     k_mra_regularise<T><<<blocks, TPB, 0, st>>>(g, p, ltop, nlev, tail);
   });
+  if (forked) cudaStreamWaitEvent(st, fk->join, 0);
   // new kinds, decode, counts and offsets; then the scatter, which also
   // makes the new kinds current
   MARK(KC_DECODE);
