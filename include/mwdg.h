@@ -16,6 +16,11 @@
  *    params.cuda_stream has finished; the caller keeps ownership.
  *  - All device work is queued on params.cuda_stream (NULL: the legacy
  *    default stream).  Functions that return host data synchronise it.
+ *    An adaptive context also owns a second stream: within each step the
+ *    encode's coarsest levels run there, forked from params.cuda_stream
+ *    by an event and joined back before the step continues, so work the
+ *    caller orders on params.cuda_stream (or captures from it into a graph)
+ *    stays ordered after the whole step.
  *  - Every function returns an mwdg_status; nothing throws or aborts across
  *    the boundary.  After MWDG_ERR_CUDA or MWDG_ERR_NONFINITE the context is
  *    in an error state: later calls on it return MWDG_ERR_STATE.
