@@ -53,7 +53,8 @@ struct mwdg_ctx {
   // are unchanged; not used on the legacy default stream or while profiling
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
-  // the adaptation's fork (a second stream and two events, made on first use)
+  // the adaptation's fork (a second stream and two events, made with an
+  // adaptive context)
   Fork fk{nullptr, nullptr, nullptr};
   int graph_launches = 0;
   int64_t generation = 0;   // bumped whenever the captured step becomes stale
