@@ -138,7 +138,7 @@ def test_config3_urban_static_rain_f64_and_f32(rule):
     # FP32 against FP64 on cell-average depths at t = 8 s (a rain film of
     # about 8 mm), the FP32 run taking the FP64 run's time steps
     # (mwdg_dg2_step_dt), so that the comparison sees the FP32 arithmetic
-    # alone: max <= 1e-3 m (the benchmark spec's bar).  A nearly dry leaf cut by a
+    # alone: max <= 1e-3 m (the FP32 path's accuracy target).  A nearly dry leaf cut by a
     # wall can be stored as flat depth in one precision and as flat free
     # surface in the other (its average agrees, its plane does not), so
     # planes are not compared pointwise here.  Later in the horizon the bar
@@ -164,7 +164,7 @@ def test_config3_urban_static_rain_f64_and_f32(rule):
                    "precisions take different wet/dry branches")
 def test_config3_urban_f32_end_of_horizon():
     """FP32 against FP64 on the urban window (reflux rule) after 100 steps on
-    the FP64 run's time steps, held to the benchmark spec's bar: max depth error
+    the FP64 run's time steps, held to the FP32 path's accuracy target: max depth error
     <= 1e-3 m and CSI >= 0.99 (known not to be met)."""
     p = S.urban(n=256, L=8, rain_mm_per_h=3600.0, rain_hours=1.0)
     p.iface_rule = 1
@@ -462,7 +462,7 @@ def test_full_size_f32_on_f64_steps_meets_the_bar_before_the_front():
     """Benchmark workload, 1024 x 1024 MWDG2: FP32 against FP64 on the GPU at
     t = 120 s with the FP32 run on the FP64 run's time steps, so that the
     comparison sees the FP32 arithmetic alone: max depth error <= 1e-3 m and
-    CSI >= 0.99 (the benchmark spec's bar), volumes within 1e-6 relative."""
+    CSI >= 0.99 (the FP32 path's accuracy target), volumes within 1e-6 relative."""
     p = S.valley(n=1024, L=10, mode=S.ADAPTIVE, eps=1e-3)
     ha, hb, va, vb = _f32_on_f64_steps(p, 120.0)
     assert ((ha > 0.01) | (hb > 0.01)).sum() > 0
