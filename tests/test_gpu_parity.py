@@ -48,7 +48,7 @@ def run_parity(p, nsteps, check_every=1, precision=0):
     return g, o
 
 
-def test_config1_uniform_dam_break_f64_full_run():
+def test_circular_dam_break_128_uniform_f64_full_run():
     """128 x 128 circular dam break to t = 5 s (about 77 steps): lockstep for
     the first 60 steps, then both run to 5 s (last step clamped)."""
     p = S.dam_break_circular()
@@ -63,7 +63,7 @@ def test_config1_uniform_dam_break_f64_full_run():
     assert v["n_clip"] == 0
 
 
-def test_config1_mra_lossless_at_zero_epsilon():
+def test_circular_dam_break_128_mra_lossless_at_zero_epsilon():
     """MRA at L = 7, epsilon = 0: encode then decode keeps every finest
     coefficient (the GPU gathers scale coefficients, so exactly)."""
     p = S.dam_break_circular(L=7, eps=0.0, mode=S.ADAPTIVE)
@@ -119,7 +119,7 @@ def test_static_valley_reflux_f64():
 
 
 @pytest.mark.parametrize("rule", [0, 1])
-def test_config3_urban_static_rain_f64_and_f32(rule):
+def test_urban_window_256_static_rain_f64_and_f32(rule):
     """Urban-like DEM (random-walk terrain, 8 m blocks off a 100 m road grid,
     per-cell Manning n 0.013 / 0.035), static grid from one MRA of the
     topography at eps = 1e-2, uniform rain: a 256 x 256 window at dx = 2 m.
@@ -142,7 +142,7 @@ def test_config3_urban_static_rain_f64_and_f32(rule):
     # wall can be stored as flat depth in one precision and as flat free
     # surface in the other (its average agrees, its plane does not), so
     # planes are not compared pointwise here.  Later in the horizon the bar
-    # is not met (test_config3_urban_f32_end_of_horizon).
+    # is not met (test_urban_window_256_f32_end_of_horizon).
     d64, f = gpu_sim(p), gpu_sim(p, precision=1)
     t = 0.0
     while t < 8.0:
@@ -162,7 +162,7 @@ def test_config3_urban_static_rain_f64_and_f32(rule):
                    "100-step horizon even on the FP64 run's steps: max 0.025-0.028 m (cell averages) where rain "
                    "films against the 8 m walls are within rounding of the 1e-3 m dry depth and the two "
                    "precisions take different wet/dry branches")
-def test_config3_urban_f32_end_of_horizon():
+def test_urban_window_256_f32_end_of_horizon():
     """FP32 against FP64 on the urban window (reflux rule) after 100 steps on
     the FP64 run's time steps, held to the FP32 path's accuracy target: max depth error
     <= 1e-3 m and CSI >= 0.99 (known not to be met)."""

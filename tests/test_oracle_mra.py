@@ -132,7 +132,7 @@ def test_plane_has_zero_details():
     assert np.abs(d).max() < 1e-15
 
 
-def test_lossless_multilevel_decode_config1():
+def test_lossless_multilevel_decode_circular_dam_break_128():
     """Dam-break initial state at L = 7, epsilon = 0: encode to level 0 and
     decode back (one MWDG2 adaptation) reproduces the finest coefficients."""
     p = S.dam_break_circular(L=7, eps=0.0, mode=S.ADAPTIVE)
