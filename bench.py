@@ -901,6 +901,9 @@ UNI_WARP_INSTR_PER_CELL = {"dg2_update_stage1": 28.43, "dg2_update_stage2": 34.0
 ISSUE_CLOCK_MHZ = 2070
 # FP64 pipe busy (% of active cycles) over the FP64 step's kernels, from ncu
 # (profiles/fp64_pipe_valley512_mwdg2.md), while those kernels are unchanged
+# (the encode's and the flux views' figures were taken before their tile
+# slot offsets became a closed form, an integer-only change that left their
+# FP64 instructions as they were)
 FP64_PIPE_BUSY = {"min": 57.4, "max": 72.0, "stage_update": 72.0, "significance_encode": 62.1}
 
 # DRAM bytes (read + write) per launch measured by ncu for the FP32 adjoint
